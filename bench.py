@@ -1,0 +1,395 @@
+"""Benchmark of the Hough-Transform hot path on GB300 (one JSON line).
+
+Workload: paper-scale events (Sec. 2: <= 5000 hits on a 12-layer barrel,
+M_H binned 4 x 16 x 1024 x 1024), synthetic and seeded: 396 helix tracks +
+238 noise hits = 4990 hits per event, threshold 10.  One step = one event
+through the whole hot path: slice admission + counting sort, vote fill
+(privatised), threshold + local-maxima scan and ordered compaction.
+
+  value   events/s with hits already resident in HBM (device pointers),
+          CUDA events on the launching stream around the timed steps.
+  e2e     the same through the C ABI with host buffers: every step copies
+          its hits host->device and reads the peak list back.
+  roofline  the dominant kernel's algorithmic bytes / live launch time.
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload.
+
+`--impl reference` times the CPU oracle (the reference arm) instead.
+Under torchrun each rank runs its own events (independent replicas, weak
+scaling); rank 0 prints max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1507_03074_gb300 import synth  # noqa: E402
+
+WORKLOAD = "paper-scale event: 4990 hits (396 tracks + 238 noise), M_H 4x16x1024x1024 u32, threshold 10"
+METRIC = "events/s"
+N_POOL = 8              # distinct resident events cycled through the steps
+THRESHOLD = 10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--naive", action="store_true", help="time the naive global-atomic fill")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# Distributed plumbing (replicas only; no collective on the data path)
+# ---------------------------------------------------------------------------
+
+def dist_init(n):
+    rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------
+
+REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+               0x100: "display_clock_setting"}
+
+
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.samples = []
+        if self.proc is None:
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            try:
+                self.samples.append((float(parts[0]), float(parts[1]), float(parts[2]), int(parts[3], 16)))
+            except Exception:
+                pass
+
+    def summary(self):
+        s = getattr(self, "samples", [])
+        if not s:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        busy = [x for x in s if not (x[3] & 0x1)] or s
+        reasons = set()
+        for x in busy:
+            for bit, name in REASON_BITS.items():
+                if x[3] & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(x[0] for x in busy), "sm_max_mhz": max(x[1] for x in s),
+                "power_w_max": max(x[2] for x in s), "reasons": sorted(reasons), "samples": len(s)}
+
+
+# ---------------------------------------------------------------------------
+# Peaks and profile summaries
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("ht_kernels.cu", "ht_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1507_03074_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was captured from the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_1507_03074_gb300 import ht
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    events = [synth.paper_event(seed=1 + rank * 1000 + k) for k in range(N_POOL)]
+    max_hits = max(e.n_hits for e in events)
+    ctx = ht.Context(b, r, threshold=THRESHOLD, max_hits=max_hits)
+    st = torch.cuda.Stream()
+    cap = 1 << 16
+    dev = []
+    with torch.cuda.stream(st):
+        for e in events:
+            dev.append(tuple(torch.from_numpy(a).cuda() for a in (e.x, e.y, e.z)))
+        out = torch.empty(cap * 8, dtype=torch.int32, device="cuda")
+        cnt = torch.empty(1, dtype=torch.int32, device="cuda")
+        M = torch.empty(b.n_cells, dtype=torch.int32, device="cuda")
+    st.synchronize()
+
+    # votes per pool event (outside the timed region)
+    votes, peaks = [], []
+    for k in range(N_POOL):
+        ctx.fill(*dev[k], naive=args.naive, stream=st)
+        ctx.find_maxima(capacity=cap, out=out, count=cnt, stream=st)
+        ctx.matrix_into(M, stream=st)
+        st.synchronize()
+        votes.append(int(M.to(torch.int64).sum().item()))
+        peaks.append(int(cnt.item()))
+    ctx.sync()
+    del M
+
+    def step(k):
+        ctx.fill(*dev[k % N_POOL], naive=args.naive, stream=st)
+        ctx.find_maxima(capacity=cap, out=out, count=cnt, stream=st)
+
+    for k in range(args.warmup):
+        step(k)
+    st.synchronize()
+
+    # ---- device-resident timed region --------------------------------------
+    K = args.steps
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+        ctx.profile(True)
+        launches0 = ctx.launches
+        with torch.cuda.stream(st):
+            marks[0].record(st)
+            for k in range(K):
+                step(k)
+                marks[k + 1].record(st)
+        st.synchronize()
+        launches = ctx.launches - launches0
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        torch.cuda.synchronize()
+        barrier(world)
+        # e2e: host buffers through the C ABI, copies inside the timed region
+        K2 = max(1, K // 4)
+        host_cap = 4096
+        e2e_times = []
+        n_peaks_e2e = 0
+        t0 = time.perf_counter()
+        for k in range(K2):
+            e = events[k % N_POOL]
+            ts = time.perf_counter()
+            ctx.fill(e.x, e.y, e.z)
+            pk, n = ctx.find_maxima(capacity=host_cap)
+            e2e_times.append(time.perf_counter() - ts)
+            n_peaks_e2e += len(pk)
+        e2e_s = time.perf_counter() - t0
+    total_ms = marks[0].elapsed_time(marks[K])
+    per_step = [marks[k].elapsed_time(marks[k + 1]) for k in range(K)]
+
+    t_dev = max_over_ranks(total_ms / 1e3, world)
+    t_e2e = max_over_ranks(e2e_s, world)
+    if rank != 0:
+        ctx.close()
+        return None
+
+    kern = {kname: {"launches": n, "avg_us": (ms / n * 1e3 if n else None)} for kname, (n, ms) in prof.items() if n}
+    # dominant kernel: largest total device time
+    dom = max(((kname, ms) for kname, (n, ms) in prof.items() if n), key=lambda t: t[1])[0]
+    hbm_peak, peak_src = measured_peaks()
+    cells_bytes = b.n_cells * 4
+    algo = {"k_fill_priv": cells_bytes, "k_scan": cells_bytes, "k_clear": cells_bytes,
+            "k_fill_naive": None, "k_prep": None, "k_order": None}
+    n_dom, ms_dom = prof[dom]
+    avg_s = ms_dom / n_dom / 1e3
+    roofline = None
+    if algo.get(dom):
+        ach = algo[dom] / avg_s / 1e9
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
+                    "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": profiled_traffic(dom),
+                    "algorithmic_bytes_per_launch": algo[dom], "avg_launch_us": round(avg_s * 1e6, 2),
+                    "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    mean_votes = float(np.mean(votes))
+    value = K * world / t_dev
+    res = {
+        "metric": METRIC, "value": round(value, 2), "unit": "events/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(t_dev * 1e3 / K, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 vote arithmetic, u32 counters",
+        "data": "synthetic (seeded helix events; the paper's dataset is not available)",
+        "config": {"workload": WORKLOAD, "events_resident": N_POOL, "fill": "naive" if args.naive else "privatised",
+                   "l2": "inputs larger than L2: each step writes and reads a 256 MiB M_H",
+                   "parallelism": f"replicas x{world}"},
+        "gvotes_per_s": round(value * mean_votes / 1e9, 3),
+        "votes_per_event": int(mean_votes), "peaks_per_event": float(np.mean(peaks)),
+        "latency_ms": {"device_p50": round(float(np.percentile(per_step, 50)), 4),
+                       "device_p99": round(float(np.percentile(per_step, 99)), 4),
+                              "e2e_p50": round(float(np.percentile(e2e_times, 50)) * 1e3, 4),
+                       "e2e_p99": round(float(np.percentile(e2e_times, 99)) * 1e3, 4)},
+        "e2e": {"value": round(K2 * world / t_e2e, 2), "unit": "events/s",
+                "h2d_bytes_per_step": int(12 * np.mean([e.n_hits for e in events])),
+                "d2h_bytes_per_step": int(4 + 4 + 32 * n_peaks_e2e / K2),
+                "api": "ht_fill(host x,y,z) + ht_find_maxima(host out)"},
+        "gpu_launches": int(launches),
+        "kernels": kern,
+        "roofline": roofline,
+        "clocks": clk.summary(),
+    }
+    ctx.close()
+    if not args.no_cpu_baseline and world == 1:
+        res["cpu_baseline"] = cpu_baseline(budget_s=10.0)
+    return res
+
+
+def _oracle_event(ob, orr, e):
+    import oracle
+    M, votes = oracle.fill(ob, orr, e.x, e.y, e.z)
+    pk, n = oracle.find_maxima(ob, orr, M, THRESHOLD)
+    return votes, n
+
+
+def cpu_baseline(budget_s=10.0):
+    """The oracle as it stands, single-threaded, on whole paper-scale events
+    until budget_s of CPU work has run."""
+    import oracle
+    ob, orr = oracle.Binning(*synth.PAPER_BINNING), oracle.Ranges()
+    n, t0 = 0, time.perf_counter()
+    while True:
+        e = synth.paper_event(seed=5000 + n)
+        _oracle_event(ob, orr, e)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(n / dt, 4), "unit": "events/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} whole paper-scale events (fill + maxima), single thread, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the CPU oracle, bounded samples per step
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    import oracle
+    if rank != 0:
+        return None
+    ob, orr = oracle.Binning(*synth.PAPER_BINNING), oracle.Ranges()
+    n_sl = ob.n_slices
+    e = synth.paper_event(seed=1)
+    # calibrate: one slice (fill restricted to it + its maxima)
+    one = oracle.Binning(1, 1, ob.n_a, ob.n_b)
+
+    def slice_step(s):
+        Ms, _ = oracle.fill_slices(ob, orr, e.x, e.y, e.z, [s])
+        oracle.find_maxima(one, orr, Ms[0], THRESHOLD)
+
+    t = time.perf_counter()
+    slice_step(0)
+    t_slice = max(time.perf_counter() - t, 1e-4)
+    budget_per_step = min(1.0, 120.0 / max(1, args.steps + args.warmup))
+    per = int(min(n_sl, max(1, round(budget_per_step / t_slice))))
+    for k in range(args.warmup):
+        slice_step((k * per) % n_sl)
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(args.steps):
+        for q in range(per):
+            slice_step((k * per + q) % n_sl)
+            done += 1
+    dt = time.perf_counter() - t0
+    value = (done / n_sl) / dt
+    return {"metric": METRIC, "value": round(value, 4), "unit": "events/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "impl": "reference",
+            "dtype": "f32 vote arithmetic, u32 counters", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": round(value, 4), "unit": "events/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per} of {n_sl} (theta,phi) slices of a paper-scale event per step "
+                                       "(fill restricted to the slice + its maxima), extrapolated to events"},
+            "e2e": {"value": round(value, 4), "unit": "events/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args.gpus)
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, world)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

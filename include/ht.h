@@ -1,0 +1,192 @@
+/*
+ * ht.h -- C ABI of the GB300 Hough-Transform track finder (libht_gb300.so).
+ *
+ * The method (arXiv 1507.03074, Sec. 2): every hit (x, y, z) votes, for every
+ * admitted (theta, phi) bin and every A bin, for the B of the circle
+ * x^2 + y^2 - 2Ax - 2By = 0 through the hit and the interaction point; the
+ * cell M_H(theta, phi, A, B) is incremented by one.  Cells holding at least
+ * `threshold` votes that are local maxima of their (A, B) neighbourhood are the
+ * track candidates ("peaks").  Sec. 3 gives the GPU split into a fill step and
+ * a maxima step and the transfer of the maxima back to the host.
+ *
+ * Conventions for every call:
+ *   - Status codes: HT_OK (0) or a positive informational code on success,
+ *     a negative HT_E_* code on failure.  No call aborts or throws; the
+ *     message of the last failure on the calling thread is ht_last_error().
+ *   - After HT_E_CUDA a context is poisoned: every later call on it returns
+ *     HT_E_STATE (destroy it and create a new one).
+ *   - Streams are cudaStream_t passed as void*; NULL means the object's own
+ *     (non-blocking) stream.  Calls taking device pointers only enqueue work
+ *     on that stream and return; the caller keeps the pointers valid until
+ *     the stream has run the work.
+ *   - Layout of the vote matrix M_H: uint32 M[theta][phi][A][B], B fastest;
+ *     linear index ((itheta*n_phi + iphi)*n_a + ia)*n_b + ib.
+ *   - The arithmetic of the vote is fixed (FP32, IEEE round-to-nearest, no
+ *     fused multiply-add, in this order) so that results are bit-exact:
+ *       dA = (a_max - a_min) / n_a,  dB = (b_max - b_min) / n_b
+ *       A_i = a_min + ((float)i + 0.5f) * dA
+ *       r2 = x*x + y*y,  d = 2*y
+ *       B = (r2 - (2*A_i)*x) / d,  t = (B - b_min) / dB
+ *       vote in bin floor(t) iff 0 <= t < n_b (out-of-range and NaN drop).
+ *   - Slice admission: the hit's polar angle (from +z) and azimuth select
+ *     its (theta, phi) bin, found by comparing FP32 pseudo-angles (built from
+ *     + - / sqrt only) with edge tables (see ht_get_edges); +-win_theta and
+ *     +-win_phi neighbouring bins are admitted too (phi wraps only when the
+ *     phi range is the full circle).  Hits with x = y = 0 are dropped.
+ *   - Peak rule: votes >= threshold, and > every one of the 8 (A,B)
+ *     neighbours (same slice) with a smaller linear index, and >= every
+ *     neighbour with a larger one.  Peaks come in ascending linear index.
+ */
+#ifndef HT_H
+#define HT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ht_ctx ht_ctx;
+typedef struct ht_batch ht_batch;
+typedef struct ht_server ht_server;
+
+/* Sizes of M_H (Sec. 2: the four Hough dimensions, binned 4 x 16 x 1024 x
+ * 1024 for (theta, phi, A, B)) and the slice admission half-windows.
+ * Limits: 1 <= n_theta, n_phi <= 1024; n_theta*n_phi <= 8192;
+ * 1 <= n_a, n_b <= 65535; n_theta*n_phi*n_a*n_b < 2^32. */
+typedef struct {
+    uint32_t n_theta, n_phi, n_a, n_b;
+    uint32_t win_theta, win_phi;
+} ht_binning;
+
+/* Ranges: theta in [0, pi] (rad, from +z), phi in [-pi, pi] (rad), A and B
+ * (mm, the circle centre).  Float endpoints within float rounding of a
+ * multiple of pi/4 are taken as that exact multiple.  min < max for all. */
+typedef struct {
+    float theta_min, theta_max, phi_min, phi_max;
+    float a_min, a_max, b_min, b_max;
+} ht_ranges;
+
+/* One peak (32 bytes).  a_c, b_c are the cell centres
+ * a_min + (ia + 0.5) dA and b_min + (ib + 0.5) dB in FP32. */
+typedef struct {
+    uint32_t itheta, iphi, ia, ib, votes;
+    float a_c, b_c;
+    uint32_t event;          /* event index within a batch; 0 otherwise */
+} ht_peak;
+
+typedef enum {
+    HT_OK = 0,
+    HT_PENDING = 1,          /* ht_poll: result not ready before the timeout */
+    HT_TRUNCATED = 2,        /* more peaks than capacity; first ones returned */
+    HT_E_INVAL = -1,         /* bad argument (NULL, size, range, flag) */
+    HT_E_NOMEM = -2,         /* device or pinned allocation failed */
+    HT_E_CUDA = -3,          /* a CUDA call or a kernel failed; object poisoned */
+    HT_E_BUSY = -4,          /* no admission possible within the memory budget */
+    HT_E_TIMEOUT = -5,       /* a bounded device-side wait gave up */
+    HT_E_STATE = -6          /* object poisoned by an earlier HT_E_CUDA */
+} ht_status;
+
+/* Flags. */
+enum {
+    HT_MEM_HOST = 0,         /* pointers are host memory (default) */
+    HT_MEM_DEVICE = 1,       /* pointers are device memory; call is async */
+    HT_ACCUMULATE = 2,       /* ht_fill: add to M_H instead of overwriting it */
+    HT_FILL_NAIVE = 4        /* ht_fill: clear + one global atomic per vote */
+};
+
+/* Thread-local text of the last failure (never NULL). */
+const char *ht_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Single-event context (Sec. 3: one fill kernel, one maxima kernel).        */
+/* ------------------------------------------------------------------------ */
+
+/* Create a context on the current CUDA device.  It owns the resident M_H,
+ * the sorted-hit workspace for up to max_hits hits per fill (accumulated
+ * fills count together), the peak scratch, pinned staging and a stream.
+ * threshold >= 1.  Errors: HT_E_INVAL, HT_E_NOMEM, HT_E_CUDA. */
+ht_status ht_create(const ht_binning *binning, const ht_ranges *ranges, uint32_t threshold,
+                    uint32_t max_hits, ht_ctx **out);
+
+/* Wait for the context's work and free everything it owns.  NULL is a no-op. */
+ht_status ht_destroy(ht_ctx *ctx);
+
+/* Step 1 (Sec. 2): fill M_H from n_hits hits given as three float arrays
+ * (mm).  Unless HT_ACCUMULATE is set M_H is overwritten (cleared in place).
+ * HT_MEM_HOST: the hits are copied to pinned staging before the call returns
+ * (the caller may reuse its arrays at once).  HT_MEM_DEVICE: device arrays,
+ * kept valid by the caller until the stream has run the work.
+ * HT_FILL_NAIVE selects the reference-design fill (explicit clear, then one
+ * global atomicAdd per vote).  n_hits may be 0 (M_H becomes all zero).
+ * Errors: HT_E_INVAL (NULL pointer with n_hits > 0, n_hits > max_hits, or
+ * accumulated hits beyond max_hits), HT_E_CUDA, HT_E_STATE. */
+ht_status ht_fill(ht_ctx *ctx, const float *x, const float *y, const float *z, uint32_t n_hits,
+                  uint32_t flags, void *stream);
+
+/* Step 2 (Sec. 2, Sec. 3): threshold + local-maxima scan of M_H.
+ * HT_MEM_HOST: blocks until done; writes min(total, capacity) peaks to out
+ * and the total to *n_found; returns HT_TRUNCATED if total > capacity.
+ * HT_MEM_DEVICE: out (capacity entries) and n_found are device pointers; the
+ * call only enqueues; *n_found receives the total (may exceed capacity).
+ * Errors: HT_E_INVAL, HT_E_CUDA, HT_E_TIMEOUT, HT_E_STATE. */
+ht_status ht_find_maxima(ht_ctx *ctx, ht_peak *out, uint32_t capacity, uint32_t *n_found,
+                         uint32_t flags, void *stream);
+
+/* Wait for the context's stream (or `stream`) and report any device-side
+ * failure flagged by its kernels (HT_E_TIMEOUT). */
+ht_status ht_sync(ht_ctx *ctx, void *stream);
+
+/* Copy M_H (n_cells must equal the matrix size) to host (HT_MEM_HOST,
+ * blocking) or device (HT_MEM_DEVICE, async) memory.  For tests. */
+ht_status ht_copy_matrix(ht_ctx *ctx, uint32_t *dst, uint64_t n_cells, uint32_t flags,
+                         void *stream);
+
+/* The FP32 pseudo-angle edge tables the context bins hits with (host
+ * arrays of n_theta+1 and n_phi+1 floats).  For tests. */
+ht_status ht_get_edges(ht_ctx *ctx, float *theta_edges, float *phi_edges);
+
+/* Overwrite M_H with n_cells counters from host (HT_MEM_HOST, blocking) or
+ * device (HT_MEM_DEVICE, async) memory, e.g. to run ht_find_maxima on a
+ * hand-built matrix.  For tests. */
+ht_status ht_set_matrix(ht_ctx *ctx, const uint32_t *src, uint64_t n_cells, uint32_t flags,
+                        void *stream);
+
+/* Kernel launches the context has issued since creation (for accounting). */
+uint64_t ht_launch_count(const ht_ctx *ctx);
+
+/* Per-kernel device time.  ht_profile(ctx, 1) resets the totals and, from
+ * then on, records a pair of CUDA events on the launching stream around
+ * every kernel launch of the context; ht_profile(ctx, 0) stops recording.
+ * ht_profile_read waits for the recorded events and writes up to cap
+ * entries (one per kernel kind: k_prep, k_fill_priv, k_clear, k_fill_naive,
+ * k_scan, k_order) with their launch count and summed duration. */
+typedef struct {
+    char name[32];
+    uint64_t launches;
+    double total_ms;
+} ht_kernel_time;
+
+ht_status ht_profile(ht_ctx *ctx, int enable);
+ht_status ht_profile_read(ht_ctx *ctx, ht_kernel_time *out, uint32_t cap, uint32_t *n);
+
+/* ------------------------------------------------------------------------ */
+/* Host-only helpers (no device needed).                                     */
+/* ------------------------------------------------------------------------ */
+
+/* HT_OK if (binning, ranges, threshold) is accepted by ht_create, else
+ * HT_E_INVAL with the reason in ht_last_error(). */
+ht_status ht_validate(const ht_binning *binning, const ht_ranges *ranges, uint32_t threshold);
+
+/* The FP32 pseudo-angle edge tables of a binning (what ht_get_edges of a
+ * context with these arguments returns): n_theta+1 and n_phi+1 floats.
+ * Edge k is the pseudo-angle of the k-th uniform angle edge, evaluated in
+ * double and rounded once; multiples of pi/4 are exact. */
+ht_status ht_compute_edges(const ht_binning *binning, const ht_ranges *ranges, float *theta_edges,
+                           float *phi_edges);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HT_H */

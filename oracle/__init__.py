@@ -57,6 +57,8 @@ def _load():
         lib.ho_admit_hits.restype = ctypes.c_int
         lib.ho_fill.argtypes = [P, P, P, P, P, ctypes.c_int64, P]
         lib.ho_fill.restype = ctypes.c_int64
+        lib.ho_fill_slices.argtypes = [P, P, P, P, P, ctypes.c_int64, P, ctypes.c_int64, P]
+        lib.ho_fill_slices.restype = ctypes.c_int64
         lib.ho_find_maxima.argtypes = [P, P, P, ctypes.c_uint32, P, P, ctypes.c_int64]
         lib.ho_find_maxima.restype = ctypes.c_int64
         lib.ho_bins_f32_vs_f64.argtypes = [P, P, P, P, P, ctypes.c_int64, P, P, ctypes.c_int64]
@@ -158,6 +160,21 @@ def fill(b: Binning, r: Ranges, x, y, z, M: np.ndarray | None = None):
         M = np.zeros(b.shape(), np.uint32)
     assert M.dtype == np.uint32 and M.flags.c_contiguous and M.size == b.n_cells
     votes = lib.ho_fill(_p(_bins(b)), _p(_rng(r)), _p(x), _p(y), _p(z), x.size, _p(M))
+    if votes < 0:
+        raise ValueError("bad binning")
+    return M, int(votes)
+
+
+def fill_slices(b: Binning, r: Ranges, x, y, z, slices, count_only: bool = False):
+    """Step 1 restricted to the given slice ids (itheta * n_phi + iphi).
+
+    Returns (Msel[len(slices), n_a, n_b] or None, votes cast into those slices)."""
+    lib = _load()
+    x, y, z = _f32(x), _f32(y), _f32(z)
+    sel = np.ascontiguousarray(slices, dtype=np.uint32)
+    M = None if count_only else np.zeros((sel.size, b.n_a, b.n_b), np.uint32)
+    votes = lib.ho_fill_slices(_p(_bins(b)), _p(_rng(r)), _p(x), _p(y), _p(z), x.size, _p(sel),
+                               sel.size, None if M is None else _p(M))
     if votes < 0:
         raise ValueError("bad binning")
     return M, int(votes)

@@ -349,6 +349,49 @@ int64_t ho_fill(const uint32_t *bins, const float *rng, const float *x, const fl
     return votes;
 }
 
+/* Step 1 restricted to the slices sel[0..n_sel): Msel[k] is the n_a x n_b
+ * matrix of slice sel[k] (accumulated into, not cleared); Msel == NULL only
+ * counts.  The loops are those of ho_fill; votes for other slices are not
+ * cast.  Returns the number of votes cast into the selected slices. */
+int64_t ho_fill_slices(const uint32_t *bins, const float *rng, const float *x, const float *y,
+                       const float *z, int64_t n, const uint32_t *sel, int64_t n_sel, uint32_t *Msel)
+{
+    ho_geom g;
+    if (ho_geom_init(&g, bins, rng))
+        return -1;
+    uint32_t *adm = (uint32_t *)malloc(sizeof(uint32_t) * ho_max_admit(&g));
+    float nbf = (float)g.nb;
+    int64_t votes = 0;
+    for (int64_t h = 0; h < n; ++h) {
+        float xh = x[h], yh = y[h];
+        uint32_t na = ho_admit(&g, xh, yh, z[h], adm);
+        for (uint32_t k = 0; k < na; ++k) {
+            int64_t which = -1;
+            for (int64_t q = 0; q < n_sel; ++q)
+                if (sel[q] == adm[k]) { which = q; break; }
+            if (which < 0)
+                continue;
+            float r2 = xh * xh + yh * yh;
+            float d = 2.0f * yh;
+            for (uint32_t i = 0; i < g.na; ++i) {
+                float A = g.a_min + ((float)i + 0.5f) * g.da;
+                float twoA = 2.0f * A;
+                float num = r2 - twoA * xh;
+                float B = num / d;
+                float t = (B - g.b_min) / g.db;
+                if (t >= 0.0f && t < nbf) {
+                    if (Msel)
+                        Msel[(uint64_t)which * g.na * g.nb + (uint64_t)i * g.nb + (uint32_t)t] += 1u;
+                    ++votes;
+                }
+            }
+        }
+    }
+    free(adm);
+    ho_geom_free(&g);
+    return votes;
+}
+
 /* Step 2 (Sec. 2, Sec. 3): threshold + local maxima with the tie rule R7.
  * Writes up to cap peaks in ascending linear index:
  *   ids[5*k .. 5*k+4] = {itheta, iphi, ia, ib, votes}

@@ -1,0 +1,324 @@
+// C ABI: single-event context (ht_create / ht_fill / ht_find_maxima ...).
+//
+// Sec. 3 allocates M_H once and re-initialises it for every event; here the
+// context keeps M_H, the sorted-hit workspace and the peak scratch resident
+// on the device, and pinned host staging for host-side hits and results.
+#include "ht_engine.h"
+#include "ht_geom.h"
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+ht_status set_err(ht_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+} // namespace
+
+namespace hte {
+// Shared with the batch and server objects.
+ht_status report(ht_status s, const std::string &msg) { return set_err(s, msg); }
+} // namespace hte
+
+struct ht_ctx {
+    hte::Engine E;
+    cudaStream_t stream = nullptr;
+    float *d_in = nullptr;        // 3 * max_hits device staging
+    float *h_in = nullptr;        // 3 * max_hits pinned staging
+    uint32_t *h_small = nullptr;  // pinned: [0] count, [1] status
+    uint32_t *d_small = nullptr;  // device: [0] count
+    htk::Peak *d_peaks = nullptr;
+    uint32_t peaks_cap = 0;
+    cudaEvent_t ev_in = nullptr;
+    bool ev_in_pending = false;
+    uint32_t acc_hits = 0;
+    bool poisoned = false;
+};
+
+static ht_status cuda_fail(ht_ctx *c, cudaError_t e, const char *what)
+{
+    if (c)
+        c->poisoned = true;
+    char buf[320];
+    std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    return set_err(HT_E_CUDA, buf);
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return cuda_fail(ctx, e_, #call);                                                      \
+    } while (0)
+
+static ht_status check_ctx(ht_ctx *ctx)
+{
+    if (!ctx)
+        return set_err(HT_E_INVAL, "context is NULL");
+    if (ctx->poisoned)
+        return set_err(HT_E_STATE, "context failed earlier (HT_E_CUDA); destroy it");
+    return HT_OK;
+}
+
+// Read and clear the device status word; map its bits to a status.
+static ht_status read_status(ht_ctx *ctx, cudaStream_t st)
+{
+    uint32_t *d_status = hte::engine_status(ctx->E);
+    CK(cudaMemcpyAsync(ctx->h_small + 1, d_status, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const uint32_t s = ctx->h_small[1];
+    if (!s)
+        return HT_OK;
+    // reset the status and every counter the kernels may have left behind
+    CK(cudaMemsetAsync(ctx->E.d_ctr, 0, (3 + ctx->E.max_events) * 4, st));
+    CK(cudaStreamSynchronize(st));
+    if (s & htk::ST_WAIT_TIMEOUT)
+        return set_err(HT_E_TIMEOUT, "a bounded device-side wait gave up (scan pipeline)");
+    if (s & htk::ST_SCRATCH_OVERFLOW)
+        return set_err(HT_E_NOMEM, "peak scratch overflow");
+    return set_err(HT_E_CUDA, "kernel reported an invalid argument");
+}
+
+extern "C" {
+
+const char *ht_last_error(void) { return g_last_error.c_str(); }
+
+ht_status ht_create(const ht_binning *binning, const ht_ranges *ranges, uint32_t threshold,
+                    uint32_t max_hits, ht_ctx **out)
+{
+    if (!out)
+        return set_err(HT_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (max_hits < 1)
+        return set_err(HT_E_INVAL, "max_hits must be >= 1");
+    ht_ctx *ctx = new (std::nothrow) ht_ctx();
+    if (!ctx)
+        return set_err(HT_E_NOMEM, "host allocation failed");
+    std::string why;
+    ht_status s = hte::engine_create(ctx->E, binning, ranges, threshold, 1, max_hits, nullptr, &why);
+    if (s != HT_OK) {
+        delete ctx;
+        return set_err(s, why);
+    }
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->d_in, (size_t)max_hits * 12 + 64)) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->d_small, 16)) != cudaSuccess ||
+        (e = cudaMallocHost(&ctx->h_in, (size_t)max_hits * 12 + 64)) != cudaSuccess ||
+        (e = cudaMallocHost(&ctx->h_small, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        ht_destroy(ctx);
+        return set_err(HT_E_NOMEM, std::string("allocation failed: ") + cudaGetErrorString(e));
+    }
+    *out = ctx;
+    return HT_OK;
+}
+
+ht_status ht_destroy(ht_ctx *ctx)
+{
+    if (!ctx)
+        return HT_OK;
+    if (ctx->stream)
+        cudaStreamSynchronize(ctx->stream);
+    hte::engine_destroy(ctx->E);
+    cudaFree(ctx->d_in);
+    cudaFree(ctx->d_small);
+    cudaFree(ctx->d_peaks);
+    cudaFreeHost(ctx->h_in);
+    cudaFreeHost(ctx->h_small);
+    if (ctx->ev_in)
+        cudaEventDestroy(ctx->ev_in);
+    if (ctx->stream)
+        cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return HT_OK;
+}
+
+ht_status ht_fill(ht_ctx *ctx, const float *x, const float *y, const float *z, uint32_t n_hits,
+                  uint32_t flags, void *stream)
+{
+    ht_status s = check_ctx(ctx);
+    if (s != HT_OK)
+        return s;
+    if (flags & ~(uint32_t)(HT_MEM_DEVICE | HT_ACCUMULATE | HT_FILL_NAIVE))
+        return set_err(HT_E_INVAL, "unknown flag");
+    if (n_hits && (!x || !y || !z))
+        return set_err(HT_E_INVAL, "hit arrays must not be NULL");
+    const bool accumulate = (flags & HT_ACCUMULATE) != 0;
+    const uint64_t acc = (accumulate ? (uint64_t)ctx->acc_hits : 0ull) + n_hits;
+    if (acc > ctx->E.max_hits)
+        return set_err(HT_E_INVAL, "more hits than max_hits (accumulated fills count together)");
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+
+    const float *px = x, *py = y, *pz = z;
+    if (!(flags & HT_MEM_DEVICE) && n_hits) {
+        if (ctx->ev_in_pending)
+            CK(cudaEventSynchronize(ctx->ev_in));       // staging free again
+        const size_t bytes = (size_t)n_hits * 4;
+        std::memcpy(ctx->h_in, x, bytes);
+        std::memcpy(ctx->h_in + n_hits, y, bytes);
+        std::memcpy(ctx->h_in + 2 * (size_t)n_hits, z, bytes);
+        CK(cudaMemcpyAsync(ctx->d_in, ctx->h_in, 3 * bytes, cudaMemcpyHostToDevice, st));
+        CK(cudaEventRecord(ctx->ev_in, st));
+        ctx->ev_in_pending = true;
+        px = ctx->d_in;
+        py = ctx->d_in + n_hits;
+        pz = ctx->d_in + 2 * (size_t)n_hits;
+    }
+    CK(hte::engine_fill(ctx->E, px, py, pz, nullptr, n_hits, 1, flags & ~(uint32_t)HT_MEM_DEVICE, st));
+    ctx->acc_hits = (uint32_t)acc;
+    return HT_OK;
+}
+
+ht_status ht_find_maxima(ht_ctx *ctx, ht_peak *out, uint32_t capacity, uint32_t *n_found,
+                         uint32_t flags, void *stream)
+{
+    ht_status s = check_ctx(ctx);
+    if (s != HT_OK)
+        return s;
+    if (flags & ~(uint32_t)HT_MEM_DEVICE)
+        return set_err(HT_E_INVAL, "unknown flag");
+    if (!n_found || (capacity && !out))
+        return set_err(HT_E_INVAL, "out (capacity > 0) and n_found must not be NULL");
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    if (flags & HT_MEM_DEVICE) {
+        CK(hte::engine_scan(ctx->E, 1, reinterpret_cast<htk::Peak *>(out), capacity, n_found, st));
+        return HT_OK;
+    }
+    if (capacity > ctx->peaks_cap) {
+        CK(cudaStreamSynchronize(st));
+        cudaFree(ctx->d_peaks);
+        ctx->d_peaks = nullptr;
+        ctx->peaks_cap = 0;
+        CK(cudaMalloc(&ctx->d_peaks, (size_t)capacity * sizeof(htk::Peak)));
+        ctx->peaks_cap = capacity;
+    }
+    CK(hte::engine_scan(ctx->E, 1, ctx->d_peaks, capacity, ctx->d_small, st));
+    CK(cudaMemcpyAsync(ctx->h_small, ctx->d_small, 4, cudaMemcpyDeviceToHost, st));
+    s = read_status(ctx, st);   // synchronises the stream
+    if (s != HT_OK)
+        return s;
+    const uint32_t n = ctx->h_small[0];
+    const uint32_t k = n < capacity ? n : capacity;
+    if (k) {
+        CK(cudaMemcpyAsync(out, ctx->d_peaks, (size_t)k * sizeof(ht_peak), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    *n_found = n;
+    return n > capacity ? HT_TRUNCATED : HT_OK;
+}
+
+ht_status ht_sync(ht_ctx *ctx, void *stream)
+{
+    ht_status s = check_ctx(ctx);
+    if (s != HT_OK)
+        return s;
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    return read_status(ctx, st);
+}
+
+ht_status ht_copy_matrix(ht_ctx *ctx, uint32_t *dst, uint64_t n_cells, uint32_t flags, void *stream)
+{
+    ht_status s = check_ctx(ctx);
+    if (s != HT_OK)
+        return s;
+    if (!dst || n_cells != ctx->E.n_cells)
+        return set_err(HT_E_INVAL, "dst must hold exactly n_theta*n_phi*n_a*n_b cells");
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    const cudaMemcpyKind kind = (flags & HT_MEM_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(dst, ctx->E.d_M, n_cells * 4, kind, st));
+    if (!(flags & HT_MEM_DEVICE))
+        CK(cudaStreamSynchronize(st));
+    return HT_OK;
+}
+
+ht_status ht_get_edges(ht_ctx *ctx, float *theta_edges, float *phi_edges)
+{
+    if (!ctx || !theta_edges || !phi_edges)
+        return set_err(HT_E_INVAL, "NULL argument");
+    std::memcpy(theta_edges, ctx->E.et.data(), ctx->E.et.size() * 4);
+    std::memcpy(phi_edges, ctx->E.ep.data(), ctx->E.ep.size() * 4);
+    return HT_OK;
+}
+
+ht_status ht_set_matrix(ht_ctx *ctx, const uint32_t *src, uint64_t n_cells, uint32_t flags, void *stream)
+{
+    ht_status s = check_ctx(ctx);
+    if (s != HT_OK)
+        return s;
+    if (!src || n_cells != ctx->E.n_cells)
+        return set_err(HT_E_INVAL, "src must hold exactly n_theta*n_phi*n_a*n_b cells");
+    std::string why;
+    if ((s = hte::engine_ensure_any_matrix(ctx->E, &why)) != HT_OK)
+        return set_err(s, why);
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    const cudaMemcpyKind kind = (flags & HT_MEM_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(ctx->E.d_M, src, n_cells * 4, kind, st));
+    if (!(flags & HT_MEM_DEVICE))
+        CK(cudaStreamSynchronize(st));
+    return HT_OK;
+}
+
+uint64_t ht_launch_count(const ht_ctx *ctx) { return ctx ? ctx->E.launches : 0; }
+
+ht_status ht_profile(ht_ctx *ctx, int enable)
+{
+    ht_status s = check_ctx(ctx);
+    if (s != HT_OK)
+        return s;
+    CK(hte::prof_enable(ctx->E, enable != 0));
+    return HT_OK;
+}
+
+ht_status ht_profile_read(ht_ctx *ctx, ht_kernel_time *out, uint32_t cap, uint32_t *n)
+{
+    ht_status s = check_ctx(ctx);
+    if (s != HT_OK)
+        return s;
+    if (!n || (cap && !out))
+        return set_err(HT_E_INVAL, "NULL argument");
+    CK(hte::prof_collect(ctx->E));
+    uint32_t k = 0;
+    for (int i = 0; i < hte::K_NKINDS; ++i) {
+        if (k < cap) {
+            std::memset(&out[k], 0, sizeof(ht_kernel_time));
+            std::strncpy(out[k].name, hte::kKernelNames[i], sizeof(out[k].name) - 1);
+            out[k].launches = ctx->E.prof.n[i];
+            out[k].total_ms = ctx->E.prof.ms[i];
+        }
+        ++k;
+    }
+    *n = k;
+    return HT_OK;
+}
+
+ht_status ht_validate(const ht_binning *binning, const ht_ranges *ranges, uint32_t threshold)
+{
+    std::string why;
+    if (!htg::validate(binning, ranges, threshold, &why))
+        return set_err(HT_E_INVAL, why);
+    return HT_OK;
+}
+
+ht_status ht_compute_edges(const ht_binning *binning, const ht_ranges *ranges, float *theta_edges,
+                           float *phi_edges)
+{
+    std::string why;
+    if (!theta_edges || !phi_edges)
+        return set_err(HT_E_INVAL, "edge arrays must not be NULL");
+    if (!htg::validate(binning, ranges, 1, &why))
+        return set_err(HT_E_INVAL, why);
+    htg::theta_edges(ranges->theta_min, ranges->theta_max, binning->n_theta, theta_edges);
+    htg::phi_edges(ranges->phi_min, ranges->phi_max, binning->n_phi, phi_edges);
+    return HT_OK;
+}
+
+} // extern "C"

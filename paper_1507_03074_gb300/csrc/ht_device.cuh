@@ -1,0 +1,265 @@
+// Device-side definitions shared by the Hough-Transform kernels.
+//
+// Every floating-point operation on the vote path uses an explicit
+// round-to-nearest intrinsic (__fadd_rn, __fsub_rn, __fmul_rn, __fdiv_rn,
+// __fsqrt_rn): these are never contracted into FMA, so the FP32 result of each
+// step is the IEEE-754 binary32 result the C ABI documents.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace htk {
+
+// Status word bits (device -> host).
+enum : uint32_t {
+    ST_WAIT_TIMEOUT = 1u,      // a bounded mbarrier wait gave up
+    ST_SCRATCH_OVERFLOW = 2u,  // peak scratch or descriptor table too small
+    ST_BAD_ARG = 4u            // a kernel saw an impossible size
+};
+
+// Per-binning constants (by value in every launch).
+struct Geom {
+    uint32_t nt, np, na, nb, wt, wp;
+    uint32_t n_slices;      // nt * np
+    uint32_t phi_full;      // phi range is the full circle: wrap the window
+    uint32_t max_admit;     // slices one hit can enter
+    uint32_t threshold;
+    float a_min, b_min, da, db, nbf;
+    const float *et;        // device: nt + 1 theta pseudo-angle edges
+    const float *ep;        // device: np + 1 phi pseudo-angle edges
+};
+
+// Device buffers of one batch of events (a single-event context is a batch
+// of one).  Event e owns M[e * n_cells ...], slice_off[e * (n_slices + 1)],
+// and the sorted-hit region hits4[hit_off[e] * max_admit ...].
+struct Work {
+    const float *x, *y, *z;     // concatenated hits
+    const uint32_t *hit_off;    // [n_events + 1] or nullptr: one event, n_hits0 hits
+    uint32_t n_hits0;
+    uint32_t n_events;
+    float4 *hits4;              // sorted by slice: {x, x^2+y^2, 2y, slice as bits}
+    uint32_t *slice_off;        // exclusive prefix of admitted hits per slice
+    uint32_t *M;                // vote matrices
+    uint64_t n_cells;           // per event
+    uint32_t *status;
+};
+
+// One peak as the scan emits it: {lin within event, event, votes, 0}.
+// Output record (matches ht_peak of the C ABI, 32 bytes).
+struct Peak {
+    uint32_t itheta, iphi, ia, ib, votes;
+    float a_c, b_c;
+    uint32_t event;
+};
+
+__device__ __forceinline__ uint32_t ev_hit_begin(const Work &w, uint32_t e)
+{
+    return w.hit_off ? w.hit_off[e] : 0u;
+}
+__device__ __forceinline__ uint32_t ev_hit_end(const Work &w, uint32_t e)
+{
+    return w.hit_off ? w.hit_off[e + 1] : w.n_hits0;
+}
+
+// ---------------------------------------------------------------------------
+// Pseudo-angles.  Polar: rho/(z+rho) for z >= 0, else 1 + (-z)/(rho-z); 0 on
+// +z, 1 in the transverse plane, 2 on -z.  Azimuthal: the quadrant "diamond
+// angle" of (u, v) = (-x, -y), 0 at phi = -pi rising to 4 at phi = +pi.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float theta_pseudo(float rho, float z)
+{
+    if (z >= 0.0f)
+        return __fdiv_rn(rho, __fadd_rn(z, rho));
+    return __fadd_rn(1.0f, __fdiv_rn(-z, __fsub_rn(rho, z)));
+}
+
+__device__ __forceinline__ float phi_pseudo(float x, float y)
+{
+    const float u = -x, v = -y;
+    if (v >= 0.0f) {
+        if (u >= 0.0f)
+            return __fdiv_rn(v, __fadd_rn(u, v));
+        return __fadd_rn(1.0f, __fdiv_rn(-u, __fadd_rn(-u, v)));
+    }
+    if (u < 0.0f)
+        return __fadd_rn(2.0f, __fdiv_rn(-v, __fadd_rn(-u, -v)));
+    return __fadd_rn(3.0f, __fdiv_rn(u, __fadd_rn(u, -v)));
+}
+
+// Number of edges e[1..n-1] that are <= D (edges non-decreasing): the bin.
+__device__ __forceinline__ uint32_t edge_bin(float D, const float *e, uint32_t n)
+{
+    uint32_t lo = 1, hi = n;            // search in [1, n)
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (D >= e[mid])
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo - 1;
+}
+
+// Slice admission of one hit.  Returns false if the hit is dropped; else
+// the theta bin range [t0, t1] and the phi centre bin / window to visit.
+struct Admit {
+    uint32_t t0, t1;        // theta bins, inclusive
+    int32_t p_lo, p_hi;     // phi offsets window relative to ip (inclusive)
+    uint32_t ip;
+    bool all_phi;           // every phi bin once
+};
+
+__device__ __forceinline__ bool admit_hit(const Geom &g, const float *et, const float *ep, float x,
+                                          float y, float z, float &r2, Admit &a)
+{
+    r2 = __fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y));
+    const float rho = __fsqrt_rn(r2);
+    if (!(rho > 0.0f))
+        return false;
+    const float dt = theta_pseudo(rho, z);
+    const float dp = phi_pseudo(x, y);
+    if (!(dt >= et[0] && dt <= et[g.nt]))
+        return false;
+    if (!(dp >= ep[0] && dp <= ep[g.np]))
+        return false;
+    const uint32_t it = edge_bin(dt, et, g.nt);
+    const uint32_t ip = edge_bin(dp, ep, g.np);
+    a.t0 = it > g.wt ? it - g.wt : 0u;
+    a.t1 = min(it + g.wt, g.nt - 1);
+    a.ip = ip;
+    if (g.phi_full) {
+        a.all_phi = 2 * g.wp + 1 >= g.np;
+        a.p_lo = -(int32_t)g.wp;
+        a.p_hi = (int32_t)g.wp;
+    } else {
+        a.all_phi = false;
+        a.p_lo = -(int32_t)min(ip, g.wp);
+        a.p_hi = (int32_t)min(g.np - 1 - ip, g.wp);
+    }
+    return true;
+}
+
+template <class F>
+__device__ __forceinline__ void for_each_slice(const Geom &g, const Admit &a, F &&f)
+{
+    for (uint32_t t = a.t0; t <= a.t1; ++t) {
+        if (a.all_phi) {
+            for (uint32_t p = 0; p < g.np; ++p)
+                f(t * g.np + p);
+        } else {
+            for (int32_t d = a.p_lo; d <= a.p_hi; ++d) {
+                int32_t p = (int32_t)a.ip + d;
+                if (p < 0)
+                    p += (int32_t)g.np;
+                else if (p >= (int32_t)g.np)
+                    p -= (int32_t)g.np;
+                f(t * g.np + (uint32_t)p);
+            }
+        }
+    }
+}
+
+// A bin centre A_i = a_min + ((float)i + 0.5) * dA.
+__device__ __forceinline__ float a_centre(const Geom &g, uint32_t i)
+{
+    return __fadd_rn(g.a_min, __fmul_rn(__fadd_rn(__uint2float_rn(i), 0.5f), g.da));
+}
+__device__ __forceinline__ float b_centre(const Geom &g, uint32_t j)
+{
+    return __fadd_rn(g.b_min, __fmul_rn(__fadd_rn(__uint2float_rn(j), 0.5f), g.db));
+}
+
+// The vote of one (hit, A bin): returns the B bin, or -1 if out of range.
+//   B = (r2 - (2 A) x) / d,  t = (B - b_min) / dB,  bin = floor(t) if 0 <= t < N_B.
+__device__ __forceinline__ int vote_bin(const Geom &g, float twoA, float x, float r2, float d)
+{
+    const float num = __fsub_rn(r2, __fmul_rn(twoA, x));
+    const float B = __fdiv_rn(num, d);
+    const float t = __fdiv_rn(__fsub_rn(B, g.b_min), g.db);
+    if (t >= 0.0f && t < g.nbf)
+        return (int)__float2uint_rz(t);
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + bulk-copy (TMA, non-tensor) wrappers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> this CTA's shared memory, completing on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: gives up after kWaitIters polls or about one second.
+constexpr uint32_t kWaitIters = 1u << 24;
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1; it < kWaitIters; ++it) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if ((it & 255u) == 0 && global_ns() - t0 > kWaitNs)
+            return false;
+    }
+    return false;
+}
+
+} // namespace htk

@@ -1,0 +1,440 @@
+// Engine: resident workspace and launch shapes for the two steps.
+#include "ht_engine.h"
+#include "ht_geom.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+namespace hte {
+
+static uint32_t round_up(uint32_t v, uint32_t m) { return (v + m - 1) / m * m; }
+
+static const size_t kSmemMax = 227 * 1024;     // per CTA on sm_100-class parts
+static const uint32_t kScanThreads = 256;
+static const uint32_t kPeakBuf = 2048;         // K: entries buffered per scan CTA
+
+const char *const kKernelNames[K_NKINDS] = {"k_prep", "k_fill_priv", "k_clear",
+                                             "k_fill_naive", "k_scan", "k_order"};
+
+static cudaEvent_t prof_event(Engine &E)
+{
+    if (!E.prof.pool.empty()) {
+        cudaEvent_t ev = E.prof.pool.back();
+        E.prof.pool.pop_back();
+        return ev;
+    }
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreate(&ev) != cudaSuccess)
+        return nullptr;
+    return ev;
+}
+
+cudaError_t prof_collect(Engine &E)
+{
+    Prof &P = E.prof;
+    if (P.pending.empty())
+        return cudaSuccess;
+    cudaError_t e = cudaEventSynchronize(P.pending.back().b);
+    if (e != cudaSuccess)
+        return e;
+    for (auto &r : P.pending) {
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, r.a, r.b)) != cudaSuccess)
+            return e;
+        P.ms[r.kind] += ms;
+        P.n[r.kind] += 1;
+        P.pool.push_back(r.a);
+        P.pool.push_back(r.b);
+    }
+    P.pending.clear();
+    return cudaSuccess;
+}
+
+cudaError_t prof_enable(Engine &E, bool on)
+{
+    cudaError_t e = prof_collect(E);
+    E.prof.on = on;
+    if (on)
+        for (int k = 0; k < K_NKINDS; ++k) {
+            E.prof.ms[k] = 0.0;
+            E.prof.n[k] = 0;
+        }
+    return e;
+}
+
+// Record around one launch when profiling is on.
+struct ProfScope {
+    Engine &E;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    ProfScope(Engine &E_, int k, cudaStream_t s) : E(E_), kind(k), st(s)
+    {
+        if (E.prof.on && (a = prof_event(E)))
+            cudaEventRecord(a, st);
+    }
+    ~ProfScope()
+    {
+        if (!a)
+            return;
+        cudaEvent_t b = prof_event(E);
+        if (!b)
+            return;
+        cudaEventRecord(b, st);
+        E.prof.pending.push_back({kind, a, b});
+        if (E.prof.pending.size() >= 4096)
+            prof_collect(E);
+    }
+};
+
+uint32_t fill_launches(const Engine &E, uint32_t flags)
+{
+    if ((flags & HT_FILL_NAIVE) || !E.fill_priv_ok)
+        return (flags & HT_ACCUMULATE) ? 2u : 3u;   // prep, [clear], naive
+    return 2u;                                      // prep, privatised fill
+}
+
+template <class T>
+static cudaError_t dalloc(T **p, size_t bytes, size_t *acc)
+{
+    *acc += bytes;
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes ? bytes : 16);
+}
+
+ht_status engine_configure(Engine &E, std::string *why)
+{
+    const ht_binning &b = E.b;
+    const Tuning &t = E.tune;
+    char buf[256];
+
+    // --- privatised fill -------------------------------------------------
+    htk::FillCfg f{};
+    f.threads = t.fill_threads ? t.fill_threads : 512;
+    f.HC = t.fill_HC ? t.fill_HC : 512;
+    f.pitch16 = round_up((b.n_b + 1) / 2, 32);
+    f.pitch32 = round_up(b.n_b, 32);
+    uint32_t W = t.fill_W;
+    if (!W) {
+        // aim at ~64 KB tiles so that three CTAs share an SM
+        W = 64;
+        while (W > 2 && (size_t)W * f.pitch16 * 4 > 64 * 1024)
+            W >>= 1;
+    }
+    while (W > 2 && (size_t)W * f.pitch16 * 4 + (size_t)f.HC * 16 > kSmemMax)
+        W >>= 1;
+    f.W = W;
+    f.tile_words = W * f.pitch16;
+    f.strips = (b.n_a + W - 1) / W;
+    E.fill_priv_ok = (W >= 2) && (f.threads % W == 0) &&
+                     ((size_t)f.tile_words * 4 + (size_t)f.HC * 16 <= kSmemMax);
+    E.fill = f;
+    if (E.fill_priv_ok) {
+        int occ = 0;
+        cudaError_t e = htk::fill_occupancy(f, &occ);
+        if (e != cudaSuccess || occ < 1) {
+            std::snprintf(buf, sizeof buf, "fill occupancy query failed: %s", cudaGetErrorString(e));
+            *why = buf;
+            return HT_E_CUDA;
+        }
+        if (t.fill_blocks_per_sm)
+            occ = std::min<int>(occ, (int)t.fill_blocks_per_sm);
+        E.fill_grid = (uint32_t)E.num_sms * (uint32_t)occ;
+    }
+    E.clear_grid = (uint32_t)E.num_sms * 4;
+    E.naive_grid = (uint32_t)E.num_sms * 16;
+
+    // --- scan --------------------------------------------------------------
+    htk::ScanArgs &s = E.scan;
+    const size_t row_bytes = (size_t)b.n_b * 4;
+    const size_t fixed = 16 * 16 + (size_t)kPeakBuf * 16;
+    s.K = kPeakBuf;
+    E.scan_tma = false;
+    if ((b.n_b & 3u) == 0) {
+        size_t target = t.scan_stage_bytes ? t.scan_stage_bytes : (row_bytes >= 8192 ? 65536 : 32768);
+        uint32_t rows = (uint32_t)std::max<size_t>(3, target / row_bytes);     // R + 2
+        uint32_t S = t.scan_slots ? t.scan_slots : 4;
+        while (S > 2 && fixed + (size_t)S * rows * row_bytes > kSmemMax)
+            --S;
+        while (rows > 3 && fixed + (size_t)S * rows * row_bytes > kSmemMax)
+            --rows;
+        if (fixed + (size_t)S * rows * row_bytes <= kSmemMax && rows * row_bytes < (1u << 20)) {
+            E.scan_tma = true;
+            s.S = S;
+            s.R = rows - 2;
+            s.slot_words = rows * b.n_b;
+        }
+    }
+    if (!E.scan_tma) {
+        s.S = 0;
+        s.R = 64;
+        s.slot_words = 0;
+    }
+    int occ = 0;
+    cudaError_t e = htk::scan_occupancy(E.scan_tma, htk::scan_smem_bytes(s), &occ);
+    if (e != cudaSuccess || occ < 1) {
+        std::snprintf(buf, sizeof buf, "scan occupancy query failed: %s", cudaGetErrorString(e));
+        *why = buf;
+        return HT_E_CUDA;
+    }
+    if (t.scan_blocks_per_sm)
+        occ = std::min<int>(occ, (int)t.scan_blocks_per_sm);
+    E.scan_grid_max = (uint32_t)E.num_sms * (uint32_t)occ;
+    return HT_OK;
+}
+
+ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint32_t threshold,
+                        uint32_t max_events, uint32_t max_hits, const Tuning *tune, std::string *why)
+{
+    char buf[256];
+    if (!htg::validate(b, r, threshold, why))
+        return HT_E_INVAL;
+    if (max_events < 1 || max_events > 4096) {
+        *why = "need 1 <= max_events <= 4096";
+        return HT_E_INVAL;
+    }
+    if (max_hits > (1u << 26)) {
+        *why = "max_hits must be <= 2^26";
+        return HT_E_INVAL;
+    }
+    E.b = *b;
+    E.r = *r;
+    E.threshold = threshold;
+    E.max_events = max_events;
+    E.max_hits = max_hits;
+    E.max_admit = htg::max_admit(*b);
+    E.n_cells = (uint64_t)b->n_theta * b->n_phi * b->n_a * b->n_b;
+    if (tune)
+        E.tune = *tune;
+
+    cudaError_t e = cudaGetDevice(&E.device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&E.num_sms, cudaDevAttrMultiProcessorCount, E.device);
+    if (e != cudaSuccess) {
+        std::snprintf(buf, sizeof buf, "no usable CUDA device: %s", cudaGetErrorString(e));
+        *why = buf;
+        return HT_E_CUDA;
+    }
+
+    E.et.resize(b->n_theta + 1);
+    E.ep.resize(b->n_phi + 1);
+    htg::theta_edges(r->theta_min, r->theta_max, b->n_theta, E.et.data());
+    htg::phi_edges(r->phi_min, r->phi_max, b->n_phi, E.ep.data());
+
+    htk::Geom &g = E.geom;
+    g.nt = b->n_theta;
+    g.np = b->n_phi;
+    g.na = b->n_a;
+    g.nb = b->n_b;
+    g.wt = b->win_theta;
+    g.wp = b->win_phi;
+    g.n_slices = b->n_theta * b->n_phi;
+    g.phi_full = htg::phi_is_full_circle(r->phi_min, r->phi_max) ? 1u : 0u;
+    g.max_admit = E.max_admit;
+    g.threshold = threshold;
+    g.a_min = r->a_min;
+    g.b_min = r->b_min;
+    {   // dA = fl((a_max - a_min) / n_a), dB likewise, in FP32
+        volatile float da = r->a_max - r->a_min, db = r->b_max - r->b_min;
+        volatile float fa = (float)b->n_a, fb = (float)b->n_b;
+        g.da = da / fa;
+        g.db = db / fb;
+        g.nbf = (float)b->n_b;
+    }
+
+    ht_status st = engine_configure(E, why);
+    if (st != HT_OK)
+        return st;
+
+    // --- scan bookkeeping sizes ------------------------------------------------
+    htk::ScanArgs &s = E.scan;
+    const uint64_t rows_ev = (uint64_t)g.n_slices * g.na;
+    const uint64_t G_max = rows_ev * max_events;
+    const uint64_t grid_max = std::max<uint64_t>(1, std::min<uint64_t>(E.scan_grid_max, G_max));
+    const uint64_t rows_per_cta = (G_max + grid_max - 1) / grid_max + 1;
+    const uint64_t per_round_max = 4ull * kScanThreads;
+    const uint64_t peaks_run = rows_per_cta * ((g.nb + 1) / 2);
+    s.seq_max = (uint32_t)std::min<uint64_t>(peaks_run / (s.K - per_round_max) + 2, 1u << 20);
+    // A peak holds >= threshold votes and no two peaks are neighbours, so
+    // peaks <= min(votes / T, ceil(n_a/2) ceil(n_b/2) per slice).
+    const uint64_t by_votes = (uint64_t)std::max<uint32_t>(max_hits, 1) * E.max_admit * g.na / threshold + 1;
+    const uint64_t by_space = (uint64_t)g.n_slices * ((g.na + 1) / 2) * ((g.nb + 1) / 2) * max_events;
+    s.entries_cap = (uint32_t)std::min<uint64_t>(std::min(by_votes, by_space) + per_round_max, 0xffffffffull);
+
+    size_t acc = 0;
+    const size_t hits_cap = (size_t)std::max<uint32_t>(max_hits, 1) * E.max_admit;
+    const uint32_t ctr_words = 3 + max_events;
+    if ((e = dalloc(&E.d_edges, (E.et.size() + E.ep.size()) * 4, &acc)) != cudaSuccess ||
+        (e = dalloc(&E.d_M, (size_t)E.n_cells * 4 * max_events + 256, &acc)) != cudaSuccess ||
+        (e = dalloc(&E.d_hits4, hits_cap * 16, &acc)) != cudaSuccess ||
+        (e = dalloc(&E.d_slice_off, (size_t)(g.n_slices + 1) * 4 * max_events, &acc)) != cudaSuccess ||
+        (e = dalloc(&E.d_entries, (size_t)s.entries_cap * 16, &acc)) != cudaSuccess ||
+        (e = dalloc(&E.d_desc, (size_t)grid_max * s.seq_max * 8, &acc)) != cudaSuccess ||
+        (e = dalloc(&E.d_cta, (size_t)grid_max * 8, &acc)) != cudaSuccess ||
+        (e = dalloc(&E.d_ctr, (size_t)ctr_words * 4, &acc)) != cudaSuccess) {
+        std::snprintf(buf, sizeof buf, "device allocation of %zu bytes failed: %s", acc,
+                      cudaGetErrorString(e));
+        *why = buf;
+        cudaGetLastError();
+        engine_destroy(E);
+        return HT_E_NOMEM;
+    }
+    E.device_bytes = acc;
+    g.et = E.d_edges;
+    g.ep = E.d_edges + E.et.size();
+    if ((e = cudaMemcpy(E.d_edges, E.et.data(), E.et.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(E.d_edges + E.et.size(), E.ep.data(), E.ep.size() * 4, cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemset(E.d_ctr, 0, (size_t)ctr_words * 4)) != cudaSuccess ||
+        (e = cudaMemset(E.d_M, 0, (size_t)E.n_cells * 4 * max_events)) != cudaSuccess) {
+        std::snprintf(buf, sizeof buf, "device initialisation failed: %s", cudaGetErrorString(e));
+        *why = buf;
+        engine_destroy(E);
+        return HT_E_CUDA;
+    }
+    s.entries = E.d_entries;
+    s.g_count = E.d_ctr;
+    s.desc = E.d_desc;
+    s.cta_nseq = E.d_cta;
+    s.cta_total = E.d_cta + grid_max;
+    s.ev_count = E.d_ctr + 3;
+    s.grid = (uint32_t)grid_max;
+    return HT_OK;
+}
+
+ht_status engine_ensure_any_matrix(Engine &E, std::string *why)
+{
+    const htk::Geom &g = E.geom;
+    const uint64_t by_space = (uint64_t)g.n_slices * ((g.na + 1) / 2) * ((g.nb + 1) / 2) * E.max_events +
+                              4ull * kScanThreads;
+    if (by_space <= E.scan.entries_cap)
+        return HT_OK;
+    if (by_space > 0xffffffffull) {
+        *why = "matrix too large for an arbitrary-content peak scan";
+        return HT_E_NOMEM;
+    }
+    uint4 *p = nullptr;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMalloc(&p, by_space * 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *why = std::string("peak scratch allocation failed: ") + cudaGetErrorString(e);
+        return HT_E_NOMEM;
+    }
+    cudaFree(E.d_entries);
+    E.device_bytes += (by_space - E.scan.entries_cap) * 16;
+    E.d_entries = p;
+    E.scan.entries = p;
+    E.scan.entries_cap = (uint32_t)by_space;
+    return HT_OK;
+}
+
+void engine_destroy(Engine &E)
+{
+    prof_collect(E);
+    for (cudaEvent_t ev : E.prof.pool)
+        cudaEventDestroy(ev);
+    E.prof.pool.clear();
+    cudaFree(E.d_edges);
+    cudaFree(E.d_M);
+    cudaFree(E.d_hits4);
+    cudaFree(E.d_slice_off);
+    cudaFree(E.d_entries);
+    cudaFree(E.d_desc);
+    cudaFree(E.d_cta);
+    cudaFree(E.d_ctr);
+    E.d_edges = nullptr;
+    E.d_M = nullptr;
+    E.d_hits4 = nullptr;
+    E.d_slice_off = nullptr;
+    E.d_entries = nullptr;
+    E.d_desc = nullptr;
+    E.d_cta = nullptr;
+    E.d_ctr = nullptr;
+}
+
+static htk::Work make_work(Engine &E, const float *x, const float *y, const float *z,
+                           const uint32_t *d_hit_off, uint32_t n_hits0, uint32_t n_events)
+{
+    htk::Work w{};
+    w.x = x;
+    w.y = y;
+    w.z = z;
+    w.hit_off = d_hit_off;
+    w.n_hits0 = n_hits0;
+    w.n_events = n_events;
+    w.hits4 = E.d_hits4;
+    w.slice_off = E.d_slice_off;
+    w.M = E.d_M;
+    w.n_cells = E.n_cells;
+    w.status = engine_status(E);
+    return w;
+}
+
+cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *z,
+                        const uint32_t *d_hit_off, uint32_t n_hits0, uint32_t n_events,
+                        uint32_t flags, cudaStream_t st)
+{
+    htk::Work w = make_work(E, x, y, z, d_hit_off, n_hits0, n_events);
+    cudaError_t e;
+    {
+        ProfScope ps(E, K_PREP, st);
+        e = htk::launch_prep(E.geom, w, st);
+    }
+    if (e != cudaSuccess)
+        return e;
+    ++E.launches;
+    const bool accumulate = (flags & HT_ACCUMULATE) != 0;
+    if ((flags & HT_FILL_NAIVE) || !E.fill_priv_ok) {
+        if (!accumulate) {
+            ProfScope ps(E, K_CLEAR, st);
+            if ((e = htk::launch_clear(E.d_M, E.n_cells * n_events, E.clear_grid, st)) != cudaSuccess)
+                return e;
+            ++E.launches;
+        }
+        ProfScope ps(E, K_FILL_NAIVE, st);
+        e = htk::launch_fill_naive(E.geom, w, E.naive_grid, st);
+        ++E.launches;
+        return e;
+    }
+    htk::FillCfg f = E.fill;
+    f.accumulate = accumulate ? 1u : 0u;
+    const uint64_t items = (uint64_t)n_events * E.geom.n_slices * f.strips;
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.fill_grid, items));
+    ProfScope ps(E, K_FILL_PRIV, st);
+    e = htk::launch_fill_priv(E.geom, w, f, grid, st);
+    ++E.launches;
+    return e;
+}
+
+cudaError_t engine_scan(Engine &E, uint32_t n_events, htk::Peak *out, uint32_t capacity,
+                        uint32_t *counts, cudaStream_t st)
+{
+    htk::Work w = make_work(E, nullptr, nullptr, nullptr, nullptr, 0, n_events);
+    htk::ScanArgs a = E.scan;
+    const uint64_t G = (uint64_t)E.geom.n_slices * E.geom.na * n_events;
+    a.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(a.grid, G));
+    htk::OrderArgs o{};
+    o.out = out;
+    o.capacity = capacity;
+    o.counts = counts;
+    o.ev_count = E.d_ctr + 3;
+    o.ticket = E.d_ctr + 1;
+    cudaError_t e;
+    {
+        ProfScope ps(E, K_SCAN, st);
+        e = htk::launch_scan(E.geom, w, a, E.scan_tma, st);
+    }
+    if (e != cudaSuccess)
+        return e;
+    ++E.launches;
+    {
+        ProfScope ps(E, K_ORDER, st);
+        e = htk::launch_order(E.geom, w, a, o, st);
+    }
+    ++E.launches;
+    return e;
+}
+
+} // namespace hte

@@ -1,0 +1,109 @@
+// Engine: the resident device workspace for up to max_events events of one
+// binning, and the enqueue functions of the two steps.  Internal; the C ABI
+// objects (context, batch, server) are built on it.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ht.h"
+#include "ht_internal.h"
+
+namespace hte {
+
+struct Tuning {
+    uint32_t fill_W = 0;         // 0: automatic
+    uint32_t fill_threads = 512;
+    uint32_t fill_HC = 512;
+    uint32_t fill_blocks_per_sm = 0;  // 0: occupancy limit
+    uint32_t scan_stage_bytes = 0;    // 0: automatic
+    uint32_t scan_slots = 0;
+    uint32_t scan_blocks_per_sm = 0;
+};
+
+// Optional per-kernel timing with CUDA events recorded on the launching
+// stream around every launch (enabled by ht_profile).
+enum KernelKind { K_PREP, K_FILL_PRIV, K_CLEAR, K_FILL_NAIVE, K_SCAN, K_ORDER, K_NKINDS };
+extern const char *const kKernelNames[K_NKINDS];
+
+struct Prof {
+    bool on = false;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[K_NKINDS] = {};
+    uint64_t n[K_NKINDS] = {};
+};
+
+struct Engine {
+    ht_binning b{};
+    ht_ranges r{};
+    uint32_t threshold = 1;
+    uint32_t max_events = 1;
+    uint32_t max_hits = 0;       // total hits over all events of one launch
+    uint32_t max_admit = 1;
+    uint64_t n_cells = 0;        // per event
+    int device = 0;
+    int num_sms = 0;
+    std::vector<float> et, ep;
+
+    htk::Geom geom{};
+    htk::FillCfg fill{};
+    bool fill_priv_ok = false;   // the tile fits in shared memory
+    uint32_t fill_grid = 0;
+    htk::ScanArgs scan{};
+    bool scan_tma = false;
+    uint32_t scan_grid_max = 0;
+    uint32_t clear_grid = 0, naive_grid = 0;
+    Tuning tune;
+
+    float *d_edges = nullptr;
+    uint32_t *d_M = nullptr;
+    float4 *d_hits4 = nullptr;
+    uint32_t *d_slice_off = nullptr;
+    uint4 *d_entries = nullptr;
+    uint2 *d_desc = nullptr;
+    uint32_t *d_cta = nullptr;   // [2][grid]: nseq, total
+    uint32_t *d_ctr = nullptr;   // [0] g_count, [1] ticket, [2] status, [3..) ev_count
+    size_t device_bytes = 0;
+    uint64_t launches = 0;
+    Prof prof;
+};
+
+// Profiling: enable (resets totals) / disable; read folds every completed
+// record into the totals (synchronises on the last recorded event).
+cudaError_t prof_enable(Engine &E, bool on);
+cudaError_t prof_collect(Engine &E);
+
+// Create / destroy.  Returns HT_OK, HT_E_INVAL or HT_E_NOMEM / HT_E_CUDA with *why.
+ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint32_t threshold,
+                        uint32_t max_events, uint32_t max_hits, const Tuning *tune, std::string *why);
+void engine_destroy(Engine &E);
+
+// Re-derive launch shapes after changing E.tune (the autotuner does this).
+ht_status engine_configure(Engine &E, std::string *why);
+
+// Step 1 for n_events events whose hits (device pointers) are concatenated;
+// d_hit_off (device, n_events + 1) or nullptr for one event of n_hits0 hits.
+cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *z,
+                        const uint32_t *d_hit_off, uint32_t n_hits0, uint32_t n_events,
+                        uint32_t flags, cudaStream_t st);
+
+// Step 2: peaks of every event into out[e * capacity ...], totals into counts[e].
+cudaError_t engine_scan(Engine &E, uint32_t n_events, htk::Peak *out, uint32_t capacity,
+                        uint32_t *counts, cudaStream_t st);
+
+// Grow the peak-entry scratch to the bound that holds for any matrix (no two
+// peaks are neighbours): needed once M_H is written by something else than
+// engine_fill (ht_set_matrix).
+ht_status engine_ensure_any_matrix(Engine &E, std::string *why);
+
+// Device status word (bits of htk::ST_*).
+inline uint32_t *engine_status(Engine &E) { return E.d_ctr + 2; }
+
+// Kernel launches engine_fill / engine_scan enqueue for the given flags.
+uint32_t fill_launches(const Engine &E, uint32_t flags);
+inline uint32_t scan_launches() { return 2; }
+
+} // namespace hte

@@ -1,0 +1,18 @@
+// Host-side geometry helpers (validation, edge tables).  Internal.
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/ht.h"
+
+namespace htg {
+
+double snap_quarter(double a);
+void theta_edges(float lo, float hi, uint32_t n, float *e);
+void phi_edges(float lo, float hi, uint32_t n, float *e);
+bool phi_is_full_circle(float lo, float hi);
+uint32_t max_admit(const ht_binning &b);
+bool validate(const ht_binning *b, const ht_ranges *r, uint32_t threshold, std::string *why);
+
+} // namespace htg

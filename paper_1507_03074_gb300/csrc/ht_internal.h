@@ -1,0 +1,64 @@
+// Internal host/device interface between the C ABI (ht_api.cu) and the
+// kernels (ht_kernels.cu).  Not installed; not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ht_device.cuh"
+
+namespace htk {
+
+// Privatised fill: A-strip of W rows per work item (u16 counters; W/2 rows
+// per pass when a slice holds >= 65536 hits and needs u32 counters).
+struct FillCfg {
+    uint32_t W;           // rows per item (power of two, divides threads)
+    uint32_t strips;      // ceil(n_a / W)
+    uint32_t pitch16;     // tile words per row in u16 mode (multiple of 32)
+    uint32_t pitch32;     // tile words per row in u32 mode (multiple of 32)
+    uint32_t HC;          // hits staged in shared memory per chunk
+    uint32_t tile_words;  // W * pitch16
+    uint32_t threads;     // block size
+    uint32_t accumulate;  // add the tile to M_H instead of storing it
+};
+
+// Scan (and its chunk bookkeeping).  Shared with k_order.
+struct ScanArgs {
+    uint32_t grid;        // persistent CTAs (each owns a contiguous run of rows)
+    uint32_t R;           // own rows per pipeline stage
+    uint32_t S;           // stages in the shared-memory ring (<= 8)
+    uint32_t K;           // peak entries buffered in shared memory (>= 4*256)
+    uint32_t slot_words;  // (R + 2) * n_b
+    uint32_t seq_max;     // chunk descriptors per CTA
+    uint32_t entries_cap; // global entry scratch capacity
+    uint4 *entries;       // {lin within event, event, votes, 0}
+    uint32_t *g_count;    // entries used (reset by k_order)
+    uint2 *desc;          // [grid][seq_max] {base, n}
+    uint32_t *cta_nseq;   // [grid]
+    uint32_t *cta_total;  // [grid]
+    uint32_t *ev_count;   // [n_events] peaks per event (reset by k_order)
+};
+
+struct OrderArgs {
+    Peak *out;            // [n_events][capacity]
+    uint32_t capacity;
+    uint32_t *counts;     // [n_events] total peaks per event
+    uint32_t *ev_count;
+    uint32_t *ticket;     // last-CTA detection (reset by k_order)
+};
+
+cudaError_t launch_prep(const Geom &g, const Work &w, cudaStream_t st);
+size_t fill_smem_bytes(const FillCfg &c);
+cudaError_t launch_fill_priv(const Geom &g, const Work &w, const FillCfg &c, uint32_t grid,
+                             cudaStream_t st);
+cudaError_t launch_clear(uint32_t *M, uint64_t words, uint32_t grid, cudaStream_t st);
+cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
+size_t scan_smem_bytes(const ScanArgs &a);
+cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, bool tma, cudaStream_t st);
+cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const OrderArgs &o,
+                         cudaStream_t st);
+cudaError_t scan_occupancy(bool tma, size_t smem, int *blocks_per_sm);
+cudaError_t fill_occupancy(const FillCfg &c, int *blocks_per_sm);
+
+} // namespace htk

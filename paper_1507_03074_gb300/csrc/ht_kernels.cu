@@ -1,0 +1,700 @@
+// Hough-Transform kernels for sm_103a (GB300).
+//
+//   k_prep        per event: slice admission of every hit + counting sort of
+//                 the admitted hits by (theta, phi) slice (Sec. 2: the angles
+//                 select the slice of the vote).
+//   k_fill_priv   Step 1 (Sec. 2), privatised: one CTA owns an (event, slice,
+//                 A-strip) tile of M_H in shared memory, votes every hit of
+//                 the slice into it with shared-memory atomics, and writes
+//                 the tile to HBM once (coalesced 16-byte stores).  Every
+//                 cell is written, so M_H needs no separate clear.
+//   k_clear,      Step 1 as the paper's CUDA design (Sec. 3): an explicit
+//   k_fill_naive  clear, then a 1-D grid over hits, a thread block over A,
+//                 and one global atomicAdd per vote.
+//   k_scan        Step 2 (Sec. 2, Sec. 3): threshold + local maxima.  Each
+//                 persistent CTA streams a contiguous run of M_H rows through
+//                 a ring of shared-memory stages filled by 1-D bulk copies
+//                 (TMA, mbarrier-completed); candidates (>= threshold) are
+//                 checked against their 8 (A,B) neighbours; peaks are
+//                 compacted in order into per-CTA chunks.
+//   k_order       places every CTA's chunks at their global rank: ascending
+//                 linear index per event, expanded to 32-byte peak records.
+#include "ht_device.cuh"
+#include "ht_internal.h"
+
+namespace htk {
+
+// ---------------------------------------------------------------------------
+// Block-wide helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o)
+            v += n;
+    }
+    return v;
+}
+
+// Exclusive scan of n values in shared memory (in place); returns the total.
+// All threads of the block must call it.  wsum: >= 32 words of scratch.
+__device__ uint32_t block_exclusive_scan(uint32_t *a, uint32_t n, uint32_t *wsum)
+{
+    const uint32_t tid = threadIdx.x, bd = blockDim.x;
+    const uint32_t per = (n + bd - 1) / bd;
+    const uint32_t b0 = min(tid * per, n), b1 = min(b0 + per, n);
+    uint32_t s = 0;
+    for (uint32_t i = b0; i < b1; ++i)
+        s += a[i];
+    const uint32_t incl = warp_incl_scan(s);
+    const uint32_t warp = tid >> 5, lane = tid & 31u, nw = (bd + 31) >> 5;
+    if (lane == 31u)
+        wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = lane < nw ? wsum[lane] : 0u;
+        const uint32_t vi = warp_incl_scan(v);
+        wsum[lane] = vi - v;
+        if (lane == 31u)
+            wsum[32] = vi;
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp] + incl - s;
+    for (uint32_t i = b0; i < b1; ++i) {
+        const uint32_t v = a[i];
+        a[i] = run;
+        run += v;
+    }
+    const uint32_t total = wsum[32];
+    __syncthreads();
+    return total;
+}
+
+// ---------------------------------------------------------------------------
+// k_prep: one CTA per event.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_prep(Geom g, Work w)
+{
+    extern __shared__ uint32_t sm[];
+    uint32_t *hist = sm;                               // n_slices
+    uint32_t *wsum = hist + g.n_slices;                // 33
+    float *et = reinterpret_cast<float *>(wsum + 33);  // nt + 1
+    float *ep = et + g.nt + 1;                         // np + 1
+
+    const uint32_t e = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+    const uint32_t h0 = ev_hit_begin(w, e), h1 = ev_hit_end(w, e);
+    for (uint32_t i = tid; i < g.n_slices; i += bd)
+        hist[i] = 0;
+    for (uint32_t i = tid; i <= g.nt; i += bd)
+        et[i] = g.et[i];
+    for (uint32_t i = tid; i <= g.np; i += bd)
+        ep[i] = g.ep[i];
+    __syncthreads();
+
+    for (uint32_t h = h0 + tid; h < h1; h += bd) {
+        float r2;
+        Admit a;
+        if (admit_hit(g, et, ep, w.x[h], w.y[h], w.z[h], r2, a))
+            for_each_slice(g, a, [&](uint32_t s) { atomicAdd(&hist[s], 1u); });
+    }
+    __syncthreads();
+    const uint32_t total = block_exclusive_scan(hist, g.n_slices, wsum);
+    uint32_t *so = w.slice_off + (size_t)e * (g.n_slices + 1);
+    for (uint32_t i = tid; i < g.n_slices; i += bd)
+        so[i] = hist[i];
+    if (tid == 0)
+        so[g.n_slices] = total;
+    __syncthreads();
+
+    float4 *out = w.hits4 + (size_t)h0 * g.max_admit;
+    for (uint32_t h = h0 + tid; h < h1; h += bd) {
+        float r2;
+        Admit a;
+        const float x = w.x[h], y = w.y[h];
+        if (admit_hit(g, et, ep, x, y, w.z[h], r2, a)) {
+            const float d = __fmul_rn(2.0f, y);
+            for_each_slice(g, a, [&](uint32_t s) {
+                const uint32_t pos = atomicAdd(&hist[s], 1u);
+                out[pos] = make_float4(x, r2, d, __uint_as_float(s));
+            });
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_fill_priv
+// ---------------------------------------------------------------------------
+// Row swizzle inside 32-word blocks of the shared tile: spreads the banks
+// of a warp whose lanes (consecutive A rows) vote into the same B column.
+__device__ __forceinline__ uint32_t row_hash(uint32_t r)
+{
+    return (r * 0x9E3779B9u) >> 27;  // 5 bits
+}
+
+template <bool U16>
+__device__ __forceinline__ void vote_rows(const Geom &g, uint32_t *tile, const float4 *hs, uint32_t nc,
+                                          uint32_t r, uint32_t i, uint32_t hl, uint32_t hstride,
+                                          uint32_t pitch)
+{
+    const float twoA = __fmul_rn(2.0f, a_centre(g, i));
+    const uint32_t rowbase = r * pitch;
+    const uint32_t sw = U16 ? (row_hash(r) & 0x1Eu) : (row_hash(r) & 0x1Cu);
+#pragma unroll 4
+    for (uint32_t h = hl; h < nc; h += hstride) {
+        const float4 hv = hs[h];
+        const int j = vote_bin(g, twoA, hv.x, hv.y, hv.z);
+        if (j >= 0) {
+            if (U16) {
+                const uint32_t word = rowbase + ((uint32_t(j) >> 1) ^ sw);
+                atomicAdd(&tile[word], 1u << ((uint32_t(j) & 1u) << 4));
+            } else {
+                atomicAdd(&tile[rowbase + (uint32_t(j) ^ sw)], 1u);
+            }
+        }
+    }
+}
+
+template <bool U16>
+__device__ __forceinline__ void flush_rows(const Geom &g, uint32_t *tile, uint32_t *dst, uint32_t rows,
+                                           uint32_t pitch, bool accumulate)
+{
+    const uint32_t tid = threadIdx.x, bd = blockDim.x;
+    if ((g.nb & 3u) == 0) {
+        const uint32_t q = g.nb >> 2;  // 16-byte units per row
+        const uint32_t units = rows * q;
+        for (uint32_t u = tid; u < units; u += bd) {
+            const uint32_t r = u / q, c4 = u - r * q;
+            uint4 v;
+            if (U16) {
+                const uint32_t sw = row_hash(r) & 0x1Eu;
+                uint2 *p = reinterpret_cast<uint2 *>(&tile[r * pitch + ((2u * c4) ^ sw)]);
+                const uint2 pr = *p;
+                *p = make_uint2(0u, 0u);
+                v = make_uint4(pr.x & 0xffffu, pr.x >> 16, pr.y & 0xffffu, pr.y >> 16);
+            } else {
+                const uint32_t sw = row_hash(r) & 0x1Cu;
+                uint4 *p = reinterpret_cast<uint4 *>(&tile[r * pitch + ((4u * c4) ^ sw)]);
+                v = *p;
+                *p = make_uint4(0u, 0u, 0u, 0u);
+            }
+            uint4 *o = reinterpret_cast<uint4 *>(dst) + u;
+            if (accumulate) {
+                const uint4 old = *o;
+                v.x += old.x; v.y += old.y; v.z += old.z; v.w += old.w;
+            }
+            *o = v;
+        }
+    } else {
+        const uint32_t units = rows * g.nb;
+        for (uint32_t u = tid; u < units; u += bd) {
+            const uint32_t r = u / g.nb, j = u - r * g.nb;
+            uint32_t v;
+            if (U16) {
+                const uint32_t word = r * pitch + ((j >> 1) ^ (row_hash(r) & 0x1Eu));
+                v = (tile[word] >> ((j & 1u) << 4)) & 0xffffu;
+            } else {
+                const uint32_t word = r * pitch + (j ^ (row_hash(r) & 0x1Cu));
+                v = tile[word];
+            }
+            dst[u] = accumulate ? dst[u] + v : v;
+        }
+        __syncthreads();
+        // clear the tile after every thread has read its cells
+        const uint32_t words = U16 ? rows * pitch : rows * pitch;
+        for (uint32_t k = tid; k < words; k += bd)
+            tile[k] = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(512) k_fill_priv(Geom g, Work w, FillCfg c)
+{
+    extern __shared__ uint4 sm4[];
+    uint32_t *tile = reinterpret_cast<uint32_t *>(sm4);
+    float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
+
+    const uint32_t tid = threadIdx.x, bd = blockDim.x;
+    for (uint32_t k = tid; k < c.tile_words / 4; k += bd)
+        sm4[k] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+
+    const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
+    for (uint64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const uint32_t k = (uint32_t)(item % c.strips);
+        const uint64_t rest = item / c.strips;
+        const uint32_t s = (uint32_t)(rest % g.n_slices);
+        const uint32_t e = (uint32_t)(rest / g.n_slices);
+        const uint32_t *so = w.slice_off + (size_t)e * (g.n_slices + 1);
+        const uint32_t hb = so[s], n_s = so[s + 1] - hb;
+        const float4 *hits = w.hits4 + (size_t)ev_hit_begin(w, e) * g.max_admit + hb;
+        const uint32_t i0 = k * c.W;
+        const uint32_t rows = min(c.W, g.na - i0);
+        const bool u16 = n_s < 65536u;
+        const uint32_t rpass = u16 ? c.W : c.W / 2;
+        const uint32_t pitch = u16 ? c.pitch16 : c.pitch32;
+        uint32_t *Mrow = w.M + (size_t)e * w.n_cells + ((size_t)s * g.na + i0) * g.nb;
+
+        for (uint32_t p0 = 0; p0 < rows; p0 += rpass) {
+            const uint32_t pr = min(rpass, rows - p0);
+            const uint32_t r = tid % rpass, hl = tid / rpass, hstride = bd / rpass;
+            for (uint32_t c0 = 0; c0 < n_s; c0 += c.HC) {
+                const uint32_t nc = min(c.HC, n_s - c0);
+                __syncthreads();
+                for (uint32_t q = tid; q < nc; q += bd)
+                    hs[q] = hits[c0 + q];
+                __syncthreads();
+                if (r < pr) {
+                    if (u16)
+                        vote_rows<true>(g, tile, hs, nc, r, i0 + p0 + r, hl, hstride, pitch);
+                    else
+                        vote_rows<false>(g, tile, hs, nc, r, i0 + p0 + r, hl, hstride, pitch);
+                }
+            }
+            __syncthreads();
+            if (u16)
+                flush_rows<true>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, c.accumulate != 0);
+            else
+                flush_rows<false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, c.accumulate != 0);
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Naive path (the paper's CUDA fill): clear + global atomics.
+// ---------------------------------------------------------------------------
+__global__ void k_clear(uint32_t *M, uint64_t words)
+{
+    const uint64_t n4 = words >> 2;
+    uint4 *M4 = reinterpret_cast<uint4 *>(M);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n4; k += stride)
+        M4[k] = make_uint4(0u, 0u, 0u, 0u);
+    for (uint64_t k = (n4 << 2) + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < words; k += stride)
+        M[k] = 0u;
+}
+
+__global__ void k_fill_naive(Geom g, Work w)
+{
+    for (uint32_t e = 0; e < w.n_events; ++e) {
+        const uint32_t *so = w.slice_off + (size_t)e * (g.n_slices + 1);
+        const uint32_t n_adm = so[g.n_slices];
+        const float4 *hits = w.hits4 + (size_t)ev_hit_begin(w, e) * g.max_admit;
+        uint32_t *M = w.M + (size_t)e * w.n_cells;
+        for (uint32_t k = blockIdx.x; k < n_adm; k += gridDim.x) {
+            const float4 hv = hits[k];
+            const uint32_t s = __float_as_uint(hv.w);
+            uint32_t *Ms = M + (size_t)s * g.na * g.nb;
+            for (uint32_t i = threadIdx.x; i < g.na; i += blockDim.x) {
+                const float twoA = __fmul_rn(2.0f, a_centre(g, i));
+                const int j = vote_bin(g, twoA, hv.x, hv.y, hv.z);
+                if (j >= 0)
+                    atomicAdd(&Ms[(size_t)i * g.nb + (uint32_t)j], 1u);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_scan
+// ---------------------------------------------------------------------------
+// Peak test of the cell at column j of `row` (value v >= threshold).
+// up / dn are the neighbouring rows of the same slice or nullptr.
+template <class P>
+__device__ __forceinline__ bool is_peak(P row, P up, P dn, uint32_t j, uint32_t nb, uint32_t v)
+{
+    const bool hl = j > 0, hr = j + 1 < nb;
+    if (up) {
+        if (hl && !(v > up[j - 1])) return false;
+        if (!(v > up[j])) return false;
+        if (hr && !(v > up[j + 1])) return false;
+    }
+    if (hl && !(v > row[j - 1])) return false;
+    if (hr && !(v >= row[j + 1])) return false;
+    if (dn) {
+        if (hl && !(v >= dn[j - 1])) return false;
+        if (!(v >= dn[j])) return false;
+        if (hr && !(v >= dn[j + 1])) return false;
+    }
+    return true;
+}
+
+struct ScanSmem {
+    uint32_t wsum[40];
+    uint32_t round_total;
+    uint32_t chunk_base;
+    uint32_t abort;
+    uint32_t pad;
+};
+
+// Flush the CTA's buffered peaks as one chunk.
+__device__ __forceinline__ void flush_chunk(const ScanArgs &a, ScanSmem &ss, const uint4 *pbuf,
+                                            uint32_t &buf_n, uint32_t &nseq, uint32_t *status)
+{
+    if (buf_n == 0)
+        return;
+    if (threadIdx.x == 0) {
+        ss.chunk_base = atomicAdd(a.g_count, buf_n);
+        if (nseq < a.seq_max)
+            a.desc[(size_t)blockIdx.x * a.seq_max + nseq] = make_uint2(ss.chunk_base, buf_n);
+        if (nseq >= a.seq_max || ss.chunk_base + buf_n > a.entries_cap)
+            atomicOr(status, (uint32_t)ST_SCRATCH_OVERFLOW);
+    }
+    __syncthreads();
+    const uint32_t base = ss.chunk_base;
+    for (uint32_t k = threadIdx.x; k < buf_n; k += blockDim.x)
+        if (base + k < a.entries_cap)
+            a.entries[base + k] = pbuf[k];
+    nseq += 1;
+    buf_n = 0;
+    __syncthreads();
+}
+
+// Ordered compaction of one round: each thread holds cnt (<= 4) peaks in
+// pk/pv (columns of `row_lin0`); appends them to pbuf in thread order.
+__device__ __forceinline__ void compact_round(ScanSmem &ss, uint4 *pbuf, uint32_t &buf_n, uint32_t cnt,
+                                              const uint32_t *pj, const uint32_t *pv, uint32_t row_lin0,
+                                              uint32_t event, uint32_t *ev_count)
+{
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+    const uint32_t nw = (blockDim.x + 31) >> 5;
+    const uint32_t incl = warp_incl_scan(cnt);
+    if (lane == 31u)
+        ss.wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = lane < nw ? ss.wsum[lane] : 0u;
+        const uint32_t vi = warp_incl_scan(v);
+        ss.wsum[lane] = vi - v;
+        if (lane == 31u) {
+            ss.round_total = vi;
+            atomicAdd(&ev_count[event], vi);
+        }
+    }
+    __syncthreads();
+    uint32_t pos = buf_n + ss.wsum[warp] + incl - cnt;
+    for (uint32_t k = 0; k < cnt; ++k)
+        pbuf[pos + k] = make_uint4(row_lin0 + pj[k], event, pv[k], 0u);
+    buf_n += ss.round_total;
+    __syncthreads();
+}
+
+template <bool TMA>
+__global__ void __launch_bounds__(256) k_scan(Geom g, Work w, ScanArgs a)
+{
+    extern __shared__ uint4 sm4[];
+    // layout: [0, 192) ScanSmem | [192, 256) 8 mbarriers | K peak entries | S stage slots
+    ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm4 + 12);
+    uint4 *pbuf = sm4 + 16;
+    uint32_t *slots = reinterpret_cast<uint32_t *>(pbuf + a.K);
+
+    const uint32_t tid = threadIdx.x, bd = blockDim.x;
+    const uint32_t nb = g.nb, T = g.threshold;
+    const uint64_t rows_ev = (uint64_t)g.n_slices * g.na;
+    const uint64_t G = rows_ev * w.n_events;
+    const uint64_t g0 = G * blockIdx.x / gridDim.x, g1 = G * (blockIdx.x + 1) / gridDim.x;
+    const uint32_t VEC = TMA ? 4u : 1u;
+    const uint32_t units = nb / VEC;
+    const uint32_t rounds = (units + bd - 1) / bd;
+
+    uint32_t buf_n = 0, nseq = 0, total = 0;
+
+    // --- pipeline state (TMA) ---
+    const uint32_t R = a.R;
+    const uint64_t n_stages = (g1 - g0 + R - 1) / R;
+    if (TMA) {
+        if (tid == 0) {
+            ss.abort = 0;
+            for (uint32_t q = 0; q < a.S; ++q)
+                mbar_init(&bars[q], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
+    auto issue = [&](uint64_t k) {
+        // stage k: own rows [ra, rb), buffer rows [ba, bb)
+        const uint64_t ra = g0 + k * R, rb = min(ra + R, g1);
+        const uint64_t ba = ra > 0 ? ra - 1 : 0, bb = min(rb + 1, G);
+        const uint32_t q = (uint32_t)(k % a.S);
+        const uint32_t bytes = (uint32_t)((bb - ba) * nb * 4u);
+        mbar_arrive_expect_tx(&bars[q], bytes);
+        bulk_load(slots + (size_t)q * a.slot_words, w.M + ba * nb, bytes, &bars[q]);
+    };
+    if (TMA && tid == 0) {
+        for (uint64_t k = 0; k < n_stages && k < a.S; ++k)
+            issue(k);
+    }
+
+    uint64_t k_abort = 0;
+    for (uint64_t k = 0; k < n_stages; ++k) {
+        const uint64_t ra = g0 + k * R, rb = min(ra + R, g1);
+        const uint64_t ba = ra > 0 ? ra - 1 : 0;
+        const uint32_t q = TMA ? (uint32_t)(k % a.S) : 0u;
+        const uint32_t *slot = slots + (size_t)q * a.slot_words;
+        if (TMA) {
+            if (!mbar_wait_bounded(&bars[q], (uint32_t)((k / a.S) & 1u)))
+                atomicOr(&ss.abort, 1u);
+            __syncthreads();
+            if (ss.abort) {
+                k_abort = k;
+                break;
+            }
+        }
+        for (uint64_t gr = ra; gr < rb; ++gr) {
+            const uint32_t i = (uint32_t)(gr % g.na);
+            const uint32_t ev = (uint32_t)(gr / rows_ev);
+            const uint32_t row_lin0 = (uint32_t)((gr - (uint64_t)ev * rows_ev) * nb);
+            const uint32_t *row = TMA ? slot + (gr - ba) * nb : w.M + gr * nb;
+            const uint32_t *up = i > 0 ? row - nb : nullptr;
+            const uint32_t *dn = i + 1 < g.na ? row + nb : nullptr;
+            for (uint32_t rd = 0; rd < rounds; ++rd) {
+                const uint32_t u = rd * bd + tid;
+                uint32_t cnt = 0, pj[4], pv[4];
+                if (u < units) {
+                    if (TMA) {
+                        const uint4 v4 = reinterpret_cast<const uint4 *>(row)[u];
+                        const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+                        if (max(max(v4.x, v4.y), max(v4.z, v4.w)) >= T) {
+#pragma unroll
+                            for (uint32_t c = 0; c < 4; ++c) {
+                                const uint32_t j = 4 * u + c;
+                                if (vv[c] >= T && is_peak(row, up, dn, j, nb, vv[c])) {
+                                    pj[cnt] = j;
+                                    pv[cnt] = vv[c];
+                                    ++cnt;
+                                }
+                            }
+                        }
+                    } else {
+                        const uint32_t v = row[u];
+                        if (v >= T && is_peak(row, up, dn, u, nb, v)) {
+                            pj[0] = u;
+                            pv[0] = v;
+                            cnt = 1;
+                        }
+                    }
+                }
+                if (__syncthreads_or(cnt)) {
+                    if (buf_n + 4 * bd > a.K)
+                        flush_chunk(a, ss, pbuf, buf_n, nseq, w.status);
+                    compact_round(ss, pbuf, buf_n, cnt, pj, pv, row_lin0, ev, a.ev_count);
+                    total += ss.round_total;
+                }
+            }
+        }
+        if (TMA) {
+            __syncthreads();  // every thread is done with slot q
+            if (tid == 0 && k + a.S < n_stages) {
+                fence_proxy_async_smem();
+                issue(k + a.S);
+            }
+        }
+    }
+    if (TMA && ss.abort) {
+        // let the copies still in flight (bounded wait) land before the CTA exits
+        if (tid == 0) {
+            atomicOr(w.status, (uint32_t)ST_WAIT_TIMEOUT);
+            const uint64_t k_end = min(n_stages, k_abort + a.S);
+            for (uint64_t kk = k_abort; kk < k_end; ++kk)
+                (void)mbar_wait_bounded(&bars[kk % a.S], (uint32_t)((kk / a.S) & 1u));
+        }
+        __syncthreads();
+    }
+    flush_chunk(a, ss, pbuf, buf_n, nseq, w.status);
+    if (tid == 0) {
+        a.cta_nseq[blockIdx.x] = min(nseq, a.seq_max);
+        a.cta_total[blockIdx.x] = total;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_order: same grid as k_scan.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, OrderArgs o)
+{
+    extern __shared__ uint32_t smo[];
+    uint32_t *ev_base = smo;                  // n_events + 1
+    uint32_t *red = ev_base + w.n_events + 1; // 40
+    __shared__ uint32_t s_last;
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, c = blockIdx.x;
+
+    // rank of this CTA's first entry
+    uint32_t part = 0;
+    for (uint32_t q = tid; q < c; q += bd)
+        part += a.cta_total[q];
+    part = warp_incl_scan(part);
+    if ((tid & 31u) == 31u)
+        red[tid >> 5] = part;
+    // per-event exclusive bases
+    for (uint32_t e = tid; e < w.n_events; e += bd)
+        ev_base[e] = o.ev_count[e];
+    __syncthreads();
+    uint32_t prefix = 0;
+    for (uint32_t q = 0; q < (bd + 31) / 32; ++q)
+        prefix += red[q];
+    __syncthreads();
+    block_exclusive_scan(ev_base, w.n_events, red);
+
+    const uint32_t nseq = a.cta_nseq[c];
+    uint32_t P = prefix;
+    for (uint32_t q = 0; q < nseq; ++q) {
+        const uint2 d = a.desc[(size_t)c * a.seq_max + q];
+        for (uint32_t k = tid; k < d.y; k += bd) {
+            if (d.x + k >= a.entries_cap)
+                break;
+            const uint4 en = a.entries[d.x + k];
+            const uint32_t e = en.y;
+            const uint32_t pos = P + k - ev_base[e];
+            if (pos < o.capacity) {
+                const uint32_t lin = en.x;
+                const uint32_t s = lin / (g.na * g.nb);
+                const uint32_t rem = lin - s * (g.na * g.nb);
+                const uint32_t i = rem / g.nb, j = rem - i * g.nb;
+                Peak pk;
+                pk.itheta = s / g.np;
+                pk.iphi = s - pk.itheta * g.np;
+                pk.ia = i;
+                pk.ib = j;
+                pk.votes = en.z;
+                pk.a_c = a_centre(g, i);
+                pk.b_c = b_centre(g, j);
+                pk.event = e;
+                o.out[(size_t)e * o.capacity + pos] = pk;
+            }
+        }
+        P += d.y;
+    }
+    if (c == 0)
+        for (uint32_t e = tid; e < w.n_events; e += bd)
+            o.counts[e] = o.ev_count[e];
+
+    // The last CTA to finish resets the counters for the next scan.
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(o.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (uint32_t e = tid; e < w.n_events; e += bd)
+            o.ev_count[e] = 0u;
+        if (tid == 0) {
+            *a.g_count = 0u;
+            *o.ticket = 0u;
+        }
+    }
+}
+
+} // namespace htk
+
+// ---------------------------------------------------------------------------
+// Launchers (host).
+// ---------------------------------------------------------------------------
+namespace htk {
+
+cudaError_t launch_prep(const Geom &g, const Work &w, cudaStream_t st)
+{
+    const size_t smem = (g.n_slices + 33 + g.nt + 1 + g.np + 1) * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    k_prep<<<w.n_events, 1024, smem, st>>>(g, w);
+    return cudaGetLastError();
+}
+
+size_t fill_smem_bytes(const FillCfg &c)
+{
+    return (size_t)c.tile_words * 4 + (size_t)c.HC * 16;
+}
+
+cudaError_t launch_fill_priv(const Geom &g, const Work &w, const FillCfg &c, uint32_t grid,
+                             cudaStream_t st)
+{
+    const size_t smem = fill_smem_bytes(c);
+    cudaError_t e = cudaFuncSetAttribute(k_fill_priv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    k_fill_priv<<<grid, c.threads, smem, st>>>(g, w, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clear(uint32_t *M, uint64_t words, uint32_t grid, cudaStream_t st)
+{
+    k_clear<<<grid, 512, 0, st>>>(M, words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st)
+{
+    const uint32_t threads = g.na >= 1024 ? 1024 : ((g.na + 31) / 32) * 32;
+    k_fill_naive<<<grid, threads, 0, st>>>(g, w);
+    return cudaGetLastError();
+}
+
+size_t scan_smem_bytes(const ScanArgs &a)
+{
+    return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)a.S * a.slot_words * 4;
+}
+
+cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, bool tma, cudaStream_t st)
+{
+    const size_t smem = scan_smem_bytes(a);
+    cudaError_t e;
+    if (tma) {
+        e = cudaFuncSetAttribute(k_scan<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        k_scan<true><<<a.grid, 256, smem, st>>>(g, w, a);
+    } else {
+        e = cudaFuncSetAttribute(k_scan<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        k_scan<false><<<a.grid, 256, smem, st>>>(g, w, a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const OrderArgs &o,
+                         cudaStream_t st)
+{
+    const size_t smem = (w.n_events + 1 + 40) * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    k_order<<<a.grid, 256, smem, st>>>(g, w, a, o);
+    return cudaGetLastError();
+}
+
+cudaError_t scan_occupancy(bool tma, size_t smem, int *blocks_per_sm)
+{
+    cudaError_t e;
+    if (tma) {
+        e = cudaFuncSetAttribute(k_scan<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_scan<true>, 256, smem);
+    }
+    e = cudaFuncSetAttribute(k_scan<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_scan<false>, 256, smem);
+}
+
+cudaError_t fill_occupancy(const FillCfg &c, int *blocks_per_sm)
+{
+    const size_t smem = fill_smem_bytes(c);
+    cudaError_t e = cudaFuncSetAttribute(k_fill_priv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fill_priv, c.threads, smem);
+}
+
+} // namespace htk

@@ -1,0 +1,283 @@
+"""Thin Python binding of the C ABI in include/ht.h (argument marshalling only).
+
+Every step of the Hough Transform runs in the CUDA library libht_gb300.so;
+this module only converts numpy arrays / torch tensors into pointers and
+sizes.  It raises if the library has not been built: there is no CPU
+fallback.  Names follow the C ABI (ht_create -> Context, ht_fill -> fill,
+ht_find_maxima -> find_maxima, ...).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libht_gb300.so")
+
+HT_OK, HT_PENDING, HT_TRUNCATED = 0, 1, 2
+HT_E_INVAL, HT_E_NOMEM, HT_E_CUDA, HT_E_BUSY, HT_E_TIMEOUT, HT_E_STATE = -1, -2, -3, -4, -5, -6
+HT_MEM_HOST, HT_MEM_DEVICE, HT_ACCUMULATE, HT_FILL_NAIVE = 0, 1, 2, 4
+STATUS_NAMES = {0: "HT_OK", 1: "HT_PENDING", 2: "HT_TRUNCATED", -1: "HT_E_INVAL", -2: "HT_E_NOMEM",
+                -3: "HT_E_CUDA", -4: "HT_E_BUSY", -5: "HT_E_TIMEOUT", -6: "HT_E_STATE"}
+
+
+class HTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class c_binning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("n_theta", "n_phi", "n_a", "n_b", "win_theta", "win_phi")]
+
+
+class c_ranges(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in ("theta_min", "theta_max", "phi_min", "phi_max",
+                                              "a_min", "a_max", "b_min", "b_max")]
+
+
+class c_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
+PEAK_DTYPE = np.dtype([("itheta", np.uint32), ("iphi", np.uint32), ("ia", np.uint32),
+                       ("ib", np.uint32), ("votes", np.uint32), ("a_c", np.float32),
+                       ("b_c", np.float32), ("event", np.uint32)])
+assert PEAK_DTYPE.itemsize == 32
+
+
+@dataclass(frozen=True)
+class Binning:
+    n_theta: int
+    n_phi: int
+    n_a: int
+    n_b: int
+    win_theta: int = 0
+    win_phi: int = 0
+
+    @property
+    def n_cells(self) -> int:
+        return self.n_theta * self.n_phi * self.n_a * self.n_b
+
+    def shape(self):
+        return (self.n_theta, self.n_phi, self.n_a, self.n_b)
+
+    def c(self) -> c_binning:
+        return c_binning(self.n_theta, self.n_phi, self.n_a, self.n_b, self.win_theta, self.win_phi)
+
+
+@dataclass(frozen=True)
+class Ranges:
+    theta_min: float = 0.0
+    theta_max: float = float(np.float32(np.pi))
+    phi_min: float = float(np.float32(-np.pi))
+    phi_max: float = float(np.float32(np.pi))
+    a_min: float = -2000.0
+    a_max: float = 2000.0
+    b_min: float = -2000.0
+    b_max: float = 2000.0
+
+    def c(self) -> c_ranges:
+        return c_ranges(self.theta_min, self.theta_max, self.phi_min, self.phi_max,
+                        self.a_min, self.a_max, self.b_min, self.b_max)
+
+
+_lib = None
+
+
+def lib():
+    """Load libht_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, U32, U64, I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    sig = {
+        "ht_last_error": ([], ctypes.c_char_p),
+        "ht_create": ([ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), U32, U32, P], I),
+        "ht_destroy": ([P], I),
+        "ht_fill": ([P, P, P, P, U32, U32, P], I),
+        "ht_find_maxima": ([P, P, U32, P, U32, P], I),
+        "ht_sync": ([P, P], I),
+        "ht_copy_matrix": ([P, P, U64, U32, P], I),
+        "ht_get_edges": ([P, P, P], I),
+        "ht_launch_count": ([P], U64),
+        "ht_set_matrix": ([P, P, U64, U32, P], I),
+        "ht_validate": ([ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), U32], I),
+        "ht_compute_edges": ([ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), P, P], I),
+        "ht_profile": ([P, I], I),
+        "ht_profile_read": ([P, P, U32, P], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes, f.restype = args, res
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the C ABI functions declared in include/ht.h that the library exports."""
+    L = lib()
+    return [n for n in dir(L) if n.startswith("ht_")]
+
+
+def validate(binning: Binning, ranges: Ranges = Ranges(), threshold: int = 10) -> int:
+    """ht_validate: HT_OK or HT_E_INVAL (host only)."""
+    b, r = binning.c(), ranges.c()
+    return int(lib().ht_validate(ctypes.byref(b), ctypes.byref(r), threshold))
+
+
+def compute_edges(binning: Binning, ranges: Ranges = Ranges()):
+    """ht_compute_edges: the FP32 pseudo-angle edge tables (host only)."""
+    et = np.zeros(binning.n_theta + 1, np.float32)
+    ep = np.zeros(binning.n_phi + 1, np.float32)
+    b, r = binning.c(), ranges.c()
+    check(lib().ht_compute_edges(ctypes.byref(b), ctypes.byref(r), et.ctypes.data_as(ctypes.c_void_p),
+                                 ep.ctypes.data_as(ctypes.c_void_p)))
+    return et, ep
+
+
+def last_error() -> str:
+    return lib().ht_last_error().decode()
+
+
+def check(status: int, ok=(HT_OK,)) -> int:
+    if status not in ok:
+        raise HTError(status, last_error())
+    return status
+
+
+# ---------------------------------------------------------------------------
+# Pointer marshalling
+# ---------------------------------------------------------------------------
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr_and_mem(a, dtype):
+    """(pointer, HT_MEM_* flag, keepalive) for a numpy array or a torch tensor."""
+    if _is_torch(a):
+        import torch
+        want = {np.float32: torch.float32, np.uint32: torch.int32, np.int32: torch.int32}[dtype]
+        if a.dtype != want and not (dtype == np.uint32 and a.dtype in (torch.int32, torch.uint8)):
+            raise TypeError(f"tensor dtype {a.dtype} does not match {dtype}")
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), (HT_MEM_DEVICE if a.is_cuda else HT_MEM_HOST), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(ctypes.c_void_p), HT_MEM_HOST, arr
+
+
+class Context:
+    """One event at a time (ht_create / ht_fill / ht_find_maxima)."""
+
+    def __init__(self, binning: Binning, ranges: Ranges = Ranges(), threshold: int = 10,
+                 max_hits: int = 65536):
+        self.binning, self.ranges, self.threshold = binning, ranges, threshold
+        self._h = ctypes.c_void_p()
+        b, r = binning.c(), ranges.c()
+        check(lib().ht_create(ctypes.byref(b), ctypes.byref(r), threshold, max_hits, ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            lib().ht_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def launches(self) -> int:
+        return int(lib().ht_launch_count(self._h))
+
+    def profile(self, enable: bool = True):
+        """ht_profile: start (resetting totals) or stop per-kernel event timing."""
+        check(lib().ht_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """ht_profile_read: {kernel: (launches, total_ms)} (synchronises)."""
+        arr = (c_kernel_time * 16)()
+        n = ctypes.c_uint32()
+        check(lib().ht_profile_read(self._h, ctypes.cast(arr, ctypes.c_void_p), 16, ctypes.byref(n)))
+        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
+                for i in range(min(n.value, 16))}
+
+    def fill(self, x, y, z, accumulate: bool = False, naive: bool = False, stream=None):
+        n = int(x.numel() if _is_torch(x) else np.asarray(x).size)
+        px, mx, kx = _ptr_and_mem(x, np.float32)
+        py, my, ky = _ptr_and_mem(y, np.float32)
+        pz, mz, kz = _ptr_and_mem(z, np.float32)
+        if not (mx == my == mz):
+            raise ValueError("x, y, z must all be host or all be device arrays")
+        flags = mx | (HT_ACCUMULATE if accumulate else 0) | (HT_FILL_NAIVE if naive else 0)
+        check(lib().ht_fill(self._h, px, py, pz, n, flags, _stream_ptr(stream)))
+        self._keep = (kx, ky, kz)
+
+    def find_maxima(self, capacity: int = 1 << 16, out=None, count=None, stream=None):
+        """Host mode (out is None): returns (peaks structured array, total).
+        Device mode: ``out`` is a CUDA tensor of >= capacity*32 bytes and
+        ``count`` a CUDA int32 tensor; the call only enqueues."""
+        L = lib()
+        if out is not None:
+            if out.numel() * out.element_size() < capacity * 32:
+                raise ValueError("out is smaller than capacity * 32 bytes")
+            check(L.ht_find_maxima(self._h, ctypes.c_void_p(out.data_ptr()), capacity,
+                                   ctypes.c_void_p(count.data_ptr()), HT_MEM_DEVICE, _stream_ptr(stream)))
+            return None
+        buf = np.zeros(max(capacity, 1), PEAK_DTYPE)
+        n = ctypes.c_uint32()
+        check(L.ht_find_maxima(self._h, buf.ctypes.data_as(ctypes.c_void_p), capacity, ctypes.byref(n),
+                               HT_MEM_HOST, _stream_ptr(stream)), ok=(HT_OK, HT_TRUNCATED))
+        return buf[: min(n.value, capacity)].copy(), int(n.value)
+
+    def sync(self, stream=None):
+        check(lib().ht_sync(self._h, _stream_ptr(stream)))
+
+    def matrix(self) -> np.ndarray:
+        M = np.zeros(self.binning.shape(), np.uint32)
+        check(lib().ht_copy_matrix(self._h, M.ctypes.data_as(ctypes.c_void_p), M.size, HT_MEM_HOST, None))
+        return M
+
+    def matrix_into(self, dst, stream=None):
+        check(lib().ht_copy_matrix(self._h, ctypes.c_void_p(dst.data_ptr()), self.binning.n_cells,
+                                   HT_MEM_DEVICE, _stream_ptr(stream)))
+
+    def set_matrix(self, M, stream=None):
+        """Overwrite M_H (numpy uint32 array, or CUDA tensor of n_cells int32)."""
+        if _is_torch(M):
+            check(lib().ht_set_matrix(self._h, ctypes.c_void_p(M.data_ptr()), self.binning.n_cells,
+                                      HT_MEM_DEVICE if M.is_cuda else HT_MEM_HOST, _stream_ptr(stream)))
+            return
+        A = np.ascontiguousarray(M, dtype=np.uint32)
+        assert A.size == self.binning.n_cells
+        check(lib().ht_set_matrix(self._h, A.ctypes.data_as(ctypes.c_void_p), A.size, HT_MEM_HOST, None))
+
+    def edges(self):
+        et = np.zeros(self.binning.n_theta + 1, np.float32)
+        ep = np.zeros(self.binning.n_phi + 1, np.float32)
+        check(lib().ht_get_edges(self._h, et.ctypes.data_as(ctypes.c_void_p), ep.ctypes.data_as(ctypes.c_void_p)))
+        return et, ep

@@ -1,0 +1,267 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Vote matrices and peak lists must be bit-exact (integer votes; FP32 vote
+arithmetic fixed by the ABI, so bins agree exactly).  Shapes span several
+fill tiles and scan stages with ragged tails (n_a not a multiple of the
+strip, n_b not a multiple of 4), both fill kernels, host and device inputs,
+windows, partial ranges, u32 counter tiles, and the paper-scale and
+upgrade-scale binnings at full size.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1507_03074_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+PEAK_FIELDS = ("itheta", "iphi", "ia", "ib", "votes", "a_c", "b_c")
+
+
+@pytest.fixture(scope="module")
+def ht():
+    import torch
+    from paper_1507_03074_gb300 import build
+    build.build()
+    from paper_1507_03074_gb300 import ht as _ht
+    torch.cuda.init()
+    return _ht
+
+
+def _ob(b):
+    return oracle.Binning(b.n_theta, b.n_phi, b.n_a, b.n_b, b.win_theta, b.win_phi)
+
+
+def _orr(r):
+    return oracle.Ranges(**r.__dict__)
+
+
+def assert_peaks_equal(got, want):
+    assert len(got) == len(want)
+    for f in PEAK_FIELDS:
+        assert np.array_equal(got[f], want[f]), f
+
+
+def random_hits(n, seed, rmax=1100.0):
+    rng = np.random.default_rng(seed)
+    rad = rng.uniform(20.0, rmax, n)
+    ph = rng.uniform(-np.pi, np.pi, n)
+    x = (rad * np.cos(ph)).astype(np.float32)
+    y = (rad * np.sin(ph)).astype(np.float32)
+    z = rng.uniform(-2500, 2500, n).astype(np.float32)
+    return x, y, z
+
+
+def run_gpu(ht, b, r, T, x, y, z, naive=False, device=True, capacity=1 << 20, max_hits=None):
+    import torch
+    with ht.Context(b, r, threshold=T, max_hits=max_hits or max(len(x), 1)) as ctx:
+        if device:
+            ctx.fill(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), torch.from_numpy(z).cuda(),
+                     naive=naive)
+        else:
+            ctx.fill(x, y, z, naive=naive)
+        pk, n = ctx.find_maxima(capacity=capacity)
+        M = ctx.matrix()
+        launches = ctx.launches
+    return M, pk, n, launches
+
+
+def event_cases():
+    ev = synth.tiny_event()
+    yield "tiny", synth.TINY_BINNING, {}, 8, (ev.x, ev.y, ev.z)
+    ev = synth.paper_event(seed=1)
+    yield "paper", synth.PAPER_BINNING, {}, 10, (ev.x, ev.y, ev.z)
+    yield "ragged_nb", (3, 5, 37, 29), dict(a_min=-1500.0, a_max=1700.0, b_min=-900.0, b_max=2100.0), \
+        2, random_hits(700, 3)
+    ev = synth.paper_event(seed=5, n_tracks=150, n_noise=50)
+    yield "ragged_na", (4, 8, 100, 96), {}, 4, (ev.x, ev.y, ev.z)
+    yield "windows", (4, 16, 128, 128, 1, 1), {}, 5, (ev.x, ev.y, ev.z)
+    yield "partial_ranges", (3, 6, 80, 64, 1, 2), dict(theta_min=0.4, theta_max=2.6, phi_min=-2.0,
+                                                       phi_max=1.5), 3, (ev.x, ev.y, ev.z)
+    yield "wide_b", (2, 2, 40, 2048), {}, 3, (ev.x, ev.y, ev.z)
+
+
+CASES = list(event_cases())
+
+
+@pytest.mark.parametrize("naive", [False, True], ids=["priv", "naive"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_fill_and_maxima_match_oracle(ht, case, naive):
+    name, bins, rng, T, (x, y, z) = case
+    b, r = ht.Binning(*bins), ht.Ranges(**rng)
+    M_ref, votes = oracle.fill(_ob(b), _orr(r), x, y, z)
+    pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, T)
+    M, pk, n, _ = run_gpu(ht, b, r, T, x, y, z, naive=naive, device=(name != "tiny"))
+    assert int(M.sum(dtype=np.uint64)) == votes
+    assert np.array_equal(M, M_ref)
+    assert n == n_ref
+    assert_peaks_equal(pk, pk_ref)
+    assert np.all(pk["event"] == 0)
+
+
+def test_u32_counter_tiles(ht):
+    # > 65535 hits in one slice: the fill switches that slice to u32 counters
+    b, r = ht.Binning(1, 1, 64, 96), ht.Ranges()
+    x, y, z = random_hits(70000, 9, rmax=400.0)
+    # half the hits on one circle so that cells exceed 16 bits
+    x[:35000], y[:35000] = np.float32(300.0), np.float32(250.0)
+    M_ref, _ = oracle.fill(_ob(b), _orr(r), x, y, z)
+    assert M_ref.max() >= 35000
+    pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, 50)
+    M, pk, n, _ = run_gpu(ht, b, r, 50, x, y, z)
+    assert np.array_equal(M, M_ref)
+    assert n == n_ref
+    assert_peaks_equal(pk, pk_ref)
+
+
+def test_empty_event_clears_in_place(ht):
+    import torch
+    b, r = ht.Binning(*synth.TINY_BINNING), ht.Ranges()
+    ev = synth.tiny_event()
+    with ht.Context(b, r, threshold=8, max_hits=256) as ctx:
+        ctx.fill(ev.x, ev.y, ev.z)
+        assert ctx.matrix().sum() > 0
+        e = torch.empty(0, dtype=torch.float32, device="cuda")
+        for naive in (False, True):
+            ctx.fill(ev.x, ev.y, ev.z, naive=not naive)
+            ctx.fill(e, e, e, naive=naive)
+            assert ctx.matrix().sum() == 0
+            pk, n = ctx.find_maxima(capacity=16)
+            assert n == 0 and len(pk) == 0
+
+
+def test_permutation_and_accumulate(ht):
+    b, r = ht.Binning(4, 16, 256, 256), ht.Ranges()
+    ev = synth.paper_event(seed=8, n_tracks=200, n_noise=60)
+    M_ref, _ = oracle.fill(_ob(b), _orr(r), ev.x, ev.y, ev.z)
+    perm = np.random.default_rng(1).permutation(ev.n_hits)
+    with ht.Context(b, r, threshold=6, max_hits=ev.n_hits) as ctx:
+        ctx.fill(ev.x[perm], ev.y[perm], ev.z[perm])
+        assert np.array_equal(ctx.matrix(), M_ref)
+        for naive in (False, True):
+            k = ev.n_hits // 3
+            ctx.fill(ev.x[:k], ev.y[:k], ev.z[:k], naive=naive)
+            ctx.fill(ev.x[k:], ev.y[k:], ev.z[k:], accumulate=True, naive=naive)
+            assert np.array_equal(ctx.matrix(), M_ref)
+        with pytest.raises(ht.HTError):
+            ctx.fill(ev.x, ev.y, ev.z, accumulate=True)      # beyond max_hits
+
+
+def test_truncation_and_repeat(ht):
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    ev = synth.paper_event(seed=1)
+    M_ref, _ = oracle.fill(_ob(b), _orr(r), ev.x, ev.y, ev.z)
+    pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, 10)
+    assert n_ref > 5
+    with ht.Context(b, r, threshold=10, max_hits=ev.n_hits) as ctx:
+        ctx.fill(ev.x, ev.y, ev.z)
+        for cap in (5, 0, n_ref, n_ref + 7):
+            pk, n = ctx.find_maxima(capacity=cap)
+            assert n == n_ref
+            assert_peaks_equal(pk, pk_ref[:cap])
+
+
+def test_device_mode_on_torch_stream(ht):
+    import torch
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    ev = synth.paper_event(seed=2)
+    M_ref, _ = oracle.fill(_ob(b), _orr(r), ev.x, ev.y, ev.z)
+    pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, 10)
+    s = torch.cuda.Stream()
+    cap = 4096
+    with ht.Context(b, r, threshold=10, max_hits=8192) as ctx, torch.cuda.stream(s):
+        x, y, z = (torch.from_numpy(a).cuda() for a in (ev.x, ev.y, ev.z))
+        out = torch.zeros(cap * 8, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        Md = torch.zeros(b.n_cells, dtype=torch.int32, device="cuda")
+        ctx.fill(x, y, z, stream=s)
+        ctx.find_maxima(capacity=cap, out=out, count=cnt, stream=s)
+        ctx.matrix_into(Md, stream=s)
+        s.synchronize()
+        ctx.sync()
+    assert int(cnt.item()) == n_ref
+    got = out.cpu().numpy().view(ht.PEAK_DTYPE)[:n_ref]
+    assert_peaks_equal(got, pk_ref)
+    assert np.array_equal(Md.cpu().numpy().view(np.uint32).reshape(b.shape()), M_ref)
+
+
+# ---------------------------------------------------------------------------
+# The scan alone on hand-built and random matrices
+# ---------------------------------------------------------------------------
+
+with open(os.path.join(HERE, "golden", "maxima_cases.json")) as _f:
+    GOLD = json.load(_f)
+
+
+@pytest.mark.parametrize("nb", [6, 8], ids=["nb6_scalar_scan", "nb8_bulk_scan"])
+def test_golden_maxima_on_gpu(ht, nb):
+    nt, np_, na, nb0 = GOLD["binning"]
+    b = ht.Binning(nt, np_, na, nb)
+    # a context's threshold is fixed: one context per case
+    for case in GOLD["cases"]:
+        M = np.zeros(b.shape(), np.uint32)
+        for t, p, i, j, v in case["cells"]:
+            M[t, p, i, j] = v
+        with ht.Context(b, ht.Ranges(), threshold=case["threshold"], max_hits=16) as ctx:
+            ctx.set_matrix(M)
+            pk, n = ctx.find_maxima(capacity=64)
+        got = [[int(q[f]) for f in ("itheta", "iphi", "ia", "ib", "votes")] for q in pk]
+        assert got == case["expected"], case["name"]
+
+
+@pytest.mark.parametrize("shape,vmax,seed", [
+    ((2, 3, 300, 64), 4, 0), ((2, 3, 97, 50), 3, 1), ((1, 1, 4096, 1024), 3, 2),
+    ((1, 2, 333, 2048), 5, 3), ((3, 1, 50, 7), 3, 4)])
+def test_random_matrix_scan(ht, shape, vmax, seed):
+    rng = np.random.default_rng(seed)
+    M = rng.integers(0, vmax, shape).astype(np.uint32)
+    b = ht.Binning(*shape)
+    for T in (1, vmax - 1):
+        ref, n_ref = oracle.find_maxima(_ob(b), oracle.Ranges(), M, T)
+        with ht.Context(b, ht.Ranges(), threshold=T, max_hits=1) as ctx:
+            ctx.set_matrix(M)
+            pk, n = ctx.find_maxima(capacity=n_ref + 10)
+            pk2, n2 = ctx.find_maxima(capacity=n_ref + 10)      # counters reset between scans
+        assert n == n_ref == n2
+        assert_peaks_equal(pk, ref)
+        assert_peaks_equal(pk2, ref)
+
+
+# ---------------------------------------------------------------------------
+# Full-size upgrade binning (4 GiB matrix): sampled slices vs the oracle
+# ---------------------------------------------------------------------------
+
+def test_upgrade_full_size_sampled(ht):
+    import torch
+    b, r = ht.Binning(*synth.UPGRADE_BINNING), ht.Ranges()
+    ev = synth.upgrade_event(0)
+    ob, orr = _ob(b), _orr(r)
+    _, votes_ref = oracle.fill_slices(ob, orr, ev.x, ev.y, ev.z, np.arange(256), count_only=True)
+    sl, _ = oracle.admit(ob, orr, ev.x, ev.y, ev.z)
+    counts = np.bincount(sl[:, 0][sl[:, 0] >= 0], minlength=256)
+    busiest = int(np.argmax(counts))
+    sample = sorted({0, 17, 100, 131, 255, busiest})
+    Msel, _ = oracle.fill_slices(ob, orr, ev.x, ev.y, ev.z, sample)
+    with ht.Context(b, r, threshold=10, max_hits=ev.n_hits) as ctx:
+        ctx.fill(*(torch.from_numpy(a).cuda() for a in (ev.x, ev.y, ev.z)))
+        Md = torch.empty(b.n_cells, dtype=torch.int32, device="cuda")
+        ctx.matrix_into(Md)
+        ctx.sync()
+        pk, n = ctx.find_maxima(capacity=1 << 20)
+    assert int(Md.to(torch.int64).sum().item()) == votes_ref
+    Md = Md.view(256, b.n_a * b.n_b)
+    for k, s in enumerate(sample):
+        got = Md[s].cpu().numpy().view(np.uint32).reshape(b.n_a, b.n_b)
+        assert np.array_equal(got, Msel[k]), s
+        one = oracle.Binning(1, 1, b.n_a, b.n_b)
+        ref, _ = oracle.find_maxima(one, orr, Msel[k], 10)
+        mine = pk[(pk["itheta"] * b.n_phi + pk["iphi"]) == s]
+        for f in ("ia", "ib", "votes", "a_c", "b_c"):
+            assert np.array_equal(mine[f], ref[f]), (s, f)
+    # ordering of the whole list: ascending linear index
+    lin = ((pk["itheta"].astype(np.int64) * b.n_phi + pk["iphi"]) * b.n_a + pk["ia"]) * b.n_b + pk["ib"]
+    assert np.all(np.diff(lin) > 0)
