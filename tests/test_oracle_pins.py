@@ -338,3 +338,19 @@ def test_mirror_symmetry():
     Mmap = np.roll(Mm, -b.n_phi // 2, axis=1)[:, :, ::-1, ::-1]
     d = np.abs(M.astype(np.int64) - Mmap.astype(np.int64)).sum()
     assert d <= 1e-4 * v, (d, v)
+
+
+def test_fill_slices_equals_full_fill():
+    # the slice-restricted fill (used for sampled full-size checks) is the
+    # pinned full fill restricted to those slices
+    ev = synth.paper_event(seed=9, n_tracks=120, n_noise=30)
+    b = Binning(4, 16, 64, 128, win_theta=1, win_phi=1)
+    M, v = oracle.fill(b, R, ev.x, ev.y, ev.z)
+    sel = [0, 5, 17, 63, 40]
+    Ms, vs = oracle.fill_slices(b, R, ev.x, ev.y, ev.z, sel)
+    flat = M.reshape(b.n_slices, b.n_a, b.n_b)
+    for k, s in enumerate(sel):
+        assert np.array_equal(Ms[k], flat[s])
+    assert vs == int(flat[sel].sum())
+    _, vall = oracle.fill_slices(b, R, ev.x, ev.y, ev.z, np.arange(b.n_slices), count_only=True)
+    assert vall == v
