@@ -173,7 +173,7 @@ ht_status ht_fill(ht_ctx *ctx, const float *x, const float *y, const float *z, u
         py = ctx->d_in + n_hits;
         pz = ctx->d_in + 2 * (size_t)n_hits;
     }
-    CK(hte::engine_fill(ctx->E, px, py, pz, nullptr, n_hits, 1, flags & ~(uint32_t)HT_MEM_DEVICE, st));
+    CK(hte::engine_fill(ctx->E, px, py, pz, nullptr, n_hits, 1, n_hits, flags & ~(uint32_t)HT_MEM_DEVICE, st));
     ctx->acc_hits = (uint32_t)acc;
     return HT_OK;
 }

@@ -31,19 +31,22 @@ struct Geom {
 };
 
 // Device buffers of one batch of events (a single-event context is a batch
-// of one).  Event e owns M[e * n_cells ...], slice_off[e * (n_slices + 1)],
-// and the sorted-hit region hits4[hit_off[e] * max_admit ...].
+// of one).  Event e owns M[e * n_cells ...] and the hits [hit_off[e],
+// hit_off[e + 1]) of the concatenated arrays.
 struct Work {
     const float *x, *y, *z;     // concatenated hits
     const uint32_t *hit_off;    // [n_events + 1] or nullptr: one event, n_hits0 hits
     uint32_t n_hits0;
     uint32_t n_events;
-    float4 *hits4;              // sorted by slice: {x, x^2+y^2, 2y, slice as bits}
-    uint32_t *slice_off;        // exclusive prefix of admitted hits per slice
+    float4 *hits4;              // per hit: {x, x^2 + y^2, 2y, 0}
+    uint32_t *codes;            // per hit: (itheta << 16) | iphi, or kDropped
     uint32_t *M;                // vote matrices
     uint64_t n_cells;           // per event
     uint32_t *status;
 };
+
+constexpr uint32_t kDropped = 0xffffffffu;
+
 
 // One peak as the scan emits it: {lin within event, event, votes, 0}.
 // Output record (matches ht_peak of the C ABI, 32 bytes).
@@ -101,61 +104,66 @@ __device__ __forceinline__ uint32_t edge_bin(float D, const float *e, uint32_t n
     return lo - 1;
 }
 
-// Slice admission of one hit.  Returns false if the hit is dropped; else
-// the theta bin range [t0, t1] and the phi centre bin / window to visit.
-struct Admit {
-    uint32_t t0, t1;        // theta bins, inclusive
-    int32_t p_lo, p_hi;     // phi offsets window relative to ip (inclusive)
-    uint32_t ip;
-    bool all_phi;           // every phi bin once
-};
-
-__device__ __forceinline__ bool admit_hit(const Geom &g, const float *et, const float *ep, float x,
-                                          float y, float z, float &r2, Admit &a)
+// Bin code of one hit: (itheta << 16) | iphi of its own slice, or kDropped
+// (rho == 0, NaN, or outside the angle ranges).  Also returns r2 = x^2 + y^2.
+__device__ __forceinline__ uint32_t bin_code(const Geom &g, const float *et, const float *ep, float x,
+                                             float y, float z, float &r2)
 {
     r2 = __fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y));
     const float rho = __fsqrt_rn(r2);
     if (!(rho > 0.0f))
-        return false;
+        return kDropped;
     const float dt = theta_pseudo(rho, z);
     const float dp = phi_pseudo(x, y);
     if (!(dt >= et[0] && dt <= et[g.nt]))
-        return false;
+        return kDropped;
     if (!(dp >= ep[0] && dp <= ep[g.np]))
-        return false;
-    const uint32_t it = edge_bin(dt, et, g.nt);
-    const uint32_t ip = edge_bin(dp, ep, g.np);
-    a.t0 = it > g.wt ? it - g.wt : 0u;
-    a.t1 = min(it + g.wt, g.nt - 1);
-    a.ip = ip;
-    if (g.phi_full) {
-        a.all_phi = 2 * g.wp + 1 >= g.np;
-        a.p_lo = -(int32_t)g.wp;
-        a.p_hi = (int32_t)g.wp;
-    } else {
-        a.all_phi = false;
-        a.p_lo = -(int32_t)min(ip, g.wp);
-        a.p_hi = (int32_t)min(g.np - 1 - ip, g.wp);
-    }
-    return true;
+        return kDropped;
+    return (edge_bin(dt, et, g.nt) << 16) | edge_bin(dp, ep, g.np);
 }
 
-template <class F>
-__device__ __forceinline__ void for_each_slice(const Geom &g, const Admit &a, F &&f)
+// Is slice (ts, ps) among the slices a hit of bin code `code` votes in: its
+// own bin, +-win_theta (clipped), +-win_phi (cyclic on the full circle,
+// clipped otherwise), each slice at most once.
+__device__ __forceinline__ bool admits(const Geom &g, uint32_t code, uint32_t ts, uint32_t ps)
 {
-    for (uint32_t t = a.t0; t <= a.t1; ++t) {
-        if (a.all_phi) {
+    if (code == kDropped)
+        return false;
+    const uint32_t it = code >> 16, ip = code & 0xffffu;
+    const uint32_t dt = ts > it ? ts - it : it - ts;
+    if (dt > g.wt)
+        return false;
+    uint32_t dp = ps > ip ? ps - ip : ip - ps;
+    if (g.phi_full && g.np - dp < dp)
+        dp = g.np - dp;
+    return dp <= g.wp;
+}
+
+// Visit every slice id (itheta * n_phi + iphi) a hit of bin code `code` votes in.
+template <class F>
+__device__ __forceinline__ void for_each_slice(const Geom &g, uint32_t code, F &&f)
+{
+    if (code == kDropped)
+        return;
+    const uint32_t it = code >> 16, ip = code & 0xffffu;
+    const uint32_t t0 = it > g.wt ? it - g.wt : 0u, t1 = min(it + g.wt, g.nt - 1);
+    for (uint32_t t = t0; t <= t1; ++t) {
+        if (g.phi_full && 2 * g.wp + 1 >= g.np) {
             for (uint32_t p = 0; p < g.np; ++p)
                 f(t * g.np + p);
-        } else {
-            for (int32_t d = a.p_lo; d <= a.p_hi; ++d) {
-                int32_t p = (int32_t)a.ip + d;
+        } else if (g.phi_full) {
+            for (int32_t d = -(int32_t)g.wp; d <= (int32_t)g.wp; ++d) {
+                int32_t p = (int32_t)ip + d;
                 if (p < 0)
                     p += (int32_t)g.np;
                 else if (p >= (int32_t)g.np)
                     p -= (int32_t)g.np;
                 f(t * g.np + (uint32_t)p);
             }
+        } else {
+            const uint32_t p0 = ip > g.wp ? ip - g.wp : 0u, p1 = min(ip + g.wp, g.np - 1);
+            for (uint32_t p = p0; p <= p1; ++p)
+                f(t * g.np + p);
         }
     }
 }

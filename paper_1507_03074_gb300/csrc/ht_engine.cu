@@ -12,9 +12,9 @@ static uint32_t round_up(uint32_t v, uint32_t m) { return (v + m - 1) / m * m; }
 
 static const size_t kSmemMax = 227 * 1024;     // per CTA on sm_100-class parts
 static const uint32_t kScanThreads = 256;
-static const uint32_t kPeakBuf = 2048;         // K: entries buffered per scan CTA
+static const uint32_t kPeakBuf = 1024;         // K: entries buffered per scan CTA
 
-const char *const kKernelNames[K_NKINDS] = {"k_prep", "k_fill_priv", "k_clear",
+const char *const kKernelNames[K_NKINDS] = {"k_bin", "k_fill_priv", "k_clear",
                                              "k_fill_naive", "k_scan", "k_order"};
 
 static cudaEvent_t prof_event(Engine &E)
@@ -111,7 +111,7 @@ ht_status engine_configure(Engine &E, std::string *why)
     // --- privatised fill -------------------------------------------------
     htk::FillCfg f{};
     f.threads = t.fill_threads ? t.fill_threads : 512;
-    f.HC = t.fill_HC ? t.fill_HC : 512;
+    f.HC = std::max(t.fill_HC ? t.fill_HC : 512u, f.threads);   // select_hits needs HC >= threads
     f.pitch16 = round_up((b.n_b + 1) / 2, 32);
     f.pitch32 = round_up(b.n_b, 32);
     uint32_t W = t.fill_W;
@@ -252,7 +252,7 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
     const uint64_t G_max = rows_ev * max_events;
     const uint64_t grid_max = std::max<uint64_t>(1, std::min<uint64_t>(E.scan_grid_max, G_max));
     const uint64_t rows_per_cta = (G_max + grid_max - 1) / grid_max + 1;
-    const uint64_t per_round_max = 4ull * kScanThreads;
+    const uint64_t per_round_max = 2ull * kScanThreads;   // <= 2 peaks per 4 consecutive cells
     const uint64_t peaks_run = rows_per_cta * ((g.nb + 1) / 2);
     s.seq_max = (uint32_t)std::min<uint64_t>(peaks_run / (s.K - per_round_max) + 2, 1u << 20);
     // A peak holds >= threshold votes and no two peaks are neighbours, so
@@ -262,12 +262,12 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
     s.entries_cap = (uint32_t)std::min<uint64_t>(std::min(by_votes, by_space) + per_round_max, 0xffffffffull);
 
     size_t acc = 0;
-    const size_t hits_cap = (size_t)std::max<uint32_t>(max_hits, 1) * E.max_admit;
+    const size_t hits_cap = (size_t)std::max<uint32_t>(max_hits, 1);
     const uint32_t ctr_words = 3 + max_events;
     if ((e = dalloc(&E.d_edges, (E.et.size() + E.ep.size()) * 4, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_M, (size_t)E.n_cells * 4 * max_events + 256, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_hits4, hits_cap * 16, &acc)) != cudaSuccess ||
-        (e = dalloc(&E.d_slice_off, (size_t)(g.n_slices + 1) * 4 * max_events, &acc)) != cudaSuccess ||
+        (e = dalloc(&E.d_codes, hits_cap * 4, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_entries, (size_t)s.entries_cap * 16, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_desc, (size_t)grid_max * s.seq_max * 8, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_cta, (size_t)grid_max * 8, &acc)) != cudaSuccess ||
@@ -339,7 +339,7 @@ void engine_destroy(Engine &E)
     cudaFree(E.d_edges);
     cudaFree(E.d_M);
     cudaFree(E.d_hits4);
-    cudaFree(E.d_slice_off);
+    cudaFree(E.d_codes);
     cudaFree(E.d_entries);
     cudaFree(E.d_desc);
     cudaFree(E.d_cta);
@@ -347,7 +347,7 @@ void engine_destroy(Engine &E)
     E.d_edges = nullptr;
     E.d_M = nullptr;
     E.d_hits4 = nullptr;
-    E.d_slice_off = nullptr;
+    E.d_codes = nullptr;
     E.d_entries = nullptr;
     E.d_desc = nullptr;
     E.d_cta = nullptr;
@@ -365,7 +365,7 @@ static htk::Work make_work(Engine &E, const float *x, const float *y, const floa
     w.n_hits0 = n_hits0;
     w.n_events = n_events;
     w.hits4 = E.d_hits4;
-    w.slice_off = E.d_slice_off;
+    w.codes = E.d_codes;
     w.M = E.d_M;
     w.n_cells = E.n_cells;
     w.status = engine_status(E);
@@ -374,13 +374,14 @@ static htk::Work make_work(Engine &E, const float *x, const float *y, const floa
 
 cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *z,
                         const uint32_t *d_hit_off, uint32_t n_hits0, uint32_t n_events,
-                        uint32_t flags, cudaStream_t st)
+                        uint32_t n_total, uint32_t flags, cudaStream_t st)
 {
     htk::Work w = make_work(E, x, y, z, d_hit_off, n_hits0, n_events);
     cudaError_t e;
     {
-        ProfScope ps(E, K_PREP, st);
-        e = htk::launch_prep(E.geom, w, st);
+        ProfScope ps(E, K_BIN, st);
+        const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((n_total + 255) / 256, E.num_sms * 8));
+        e = htk::launch_bin(E.geom, w, grid, st);
     }
     if (e != cudaSuccess)
         return e;

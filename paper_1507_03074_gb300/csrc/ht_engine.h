@@ -15,7 +15,7 @@ namespace hte {
 struct Tuning {
     uint32_t fill_W = 0;         // 0: automatic
     uint32_t fill_threads = 512;
-    uint32_t fill_HC = 512;
+    uint32_t fill_HC = 0;         // 0: max(512, threads)
     uint32_t fill_blocks_per_sm = 0;  // 0: occupancy limit
     uint32_t scan_stage_bytes = 0;    // 0: automatic
     uint32_t scan_slots = 0;
@@ -24,7 +24,7 @@ struct Tuning {
 
 // Optional per-kernel timing with CUDA events recorded on the launching
 // stream around every launch (enabled by ht_profile).
-enum KernelKind { K_PREP, K_FILL_PRIV, K_CLEAR, K_FILL_NAIVE, K_SCAN, K_ORDER, K_NKINDS };
+enum KernelKind { K_BIN, K_FILL_PRIV, K_CLEAR, K_FILL_NAIVE, K_SCAN, K_ORDER, K_NKINDS };
 extern const char *const kKernelNames[K_NKINDS];
 
 struct Prof {
@@ -61,7 +61,7 @@ struct Engine {
     float *d_edges = nullptr;
     uint32_t *d_M = nullptr;
     float4 *d_hits4 = nullptr;
-    uint32_t *d_slice_off = nullptr;
+    uint32_t *d_codes = nullptr;
     uint4 *d_entries = nullptr;
     uint2 *d_desc = nullptr;
     uint32_t *d_cta = nullptr;   // [2][grid]: nseq, total
@@ -86,9 +86,10 @@ ht_status engine_configure(Engine &E, std::string *why);
 
 // Step 1 for n_events events whose hits (device pointers) are concatenated;
 // d_hit_off (device, n_events + 1) or nullptr for one event of n_hits0 hits.
+// n_total (host) is the total hit count; it sizes the binning grid.
 cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *z,
                         const uint32_t *d_hit_off, uint32_t n_hits0, uint32_t n_events,
-                        uint32_t flags, cudaStream_t st);
+                        uint32_t n_total, uint32_t flags, cudaStream_t st);
 
 // Step 2: peaks of every event into out[e * capacity ...], totals into counts[e].
 cudaError_t engine_scan(Engine &E, uint32_t n_events, htk::Peak *out, uint32_t capacity,

@@ -17,7 +17,7 @@ struct FillCfg {
     uint32_t strips;      // ceil(n_a / W)
     uint32_t pitch16;     // tile words per row in u16 mode (multiple of 32)
     uint32_t pitch32;     // tile words per row in u32 mode (multiple of 32)
-    uint32_t HC;          // hits staged in shared memory per chunk
+    uint32_t HC;          // hits staged in shared memory per chunk (>= threads)
     uint32_t tile_words;  // W * pitch16
     uint32_t threads;     // block size
     uint32_t accumulate;  // add the tile to M_H instead of storing it
@@ -28,7 +28,7 @@ struct ScanArgs {
     uint32_t grid;        // persistent CTAs (each owns a contiguous run of rows)
     uint32_t R;           // own rows per pipeline stage
     uint32_t S;           // stages in the shared-memory ring (<= 8)
-    uint32_t K;           // peak entries buffered in shared memory (>= 4*256)
+    uint32_t K;           // peak entries buffered in shared memory (>= 2*256)
     uint32_t slot_words;  // (R + 2) * n_b
     uint32_t seq_max;     // chunk descriptors per CTA
     uint32_t entries_cap; // global entry scratch capacity
@@ -48,7 +48,7 @@ struct OrderArgs {
     uint32_t *ticket;     // last-CTA detection (reset by k_order)
 };
 
-cudaError_t launch_prep(const Geom &g, const Work &w, cudaStream_t st);
+cudaError_t launch_bin(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
 size_t fill_smem_bytes(const FillCfg &c);
 cudaError_t launch_fill_priv(const Geom &g, const Work &w, const FillCfg &c, uint32_t grid,
                              cudaStream_t st);

@@ -1,22 +1,30 @@
 // Hough-Transform kernels for sm_103a (GB300).
 //
-//   k_prep        per event: slice admission of every hit + counting sort of
-//                 the admitted hits by (theta, phi) slice (Sec. 2: the angles
-//                 select the slice of the vote).
-//   k_fill_priv   Step 1 (Sec. 2), privatised: one CTA owns an (event, slice,
-//                 A-strip) tile of M_H in shared memory, votes every hit of
-//                 the slice into it with shared-memory atomics, and writes
-//                 the tile to HBM once (coalesced 16-byte stores).  Every
-//                 cell is written, so M_H needs no separate clear.
+//   k_bin         one thread per hit (all events of a launch): the bin code
+//                 of the hit's own (theta, phi) slice, found from FP32
+//                 pseudo-angles and the edge tables (Sec. 2: the angles
+//                 select the slice a hit votes in), and the per-hit terms
+//                 x, x^2 + y^2, 2y of the vote.
+//   k_fill_priv   Step 1 (Sec. 2), privatised.  Work item = (event, slice,
+//                 strip of W A-rows); each CTA takes a contiguous range of
+//                 items.  It selects the event's hits admitted to the slice
+//                 (ballot compaction into shared memory, cached while the
+//                 CTA stays on that slice), votes them into a shared-memory
+//                 u16 (or u32) tile with shared-memory atomics, and writes
+//                 the tile to HBM once with 16-byte stores that also zero it.
+//                 Every cell is written, so M_H needs no separate clear.
 //   k_clear,      Step 1 as the paper's CUDA design (Sec. 3): an explicit
 //   k_fill_naive  clear, then a 1-D grid over hits, a thread block over A,
 //                 and one global atomicAdd per vote.
-//   k_scan        Step 2 (Sec. 2, Sec. 3): threshold + local maxima.  Each
+//   k_scan_tma    Step 2 (Sec. 2, Sec. 3): threshold + local maxima.  Each
 //                 persistent CTA streams a contiguous run of M_H rows through
 //                 a ring of shared-memory stages filled by 1-D bulk copies
-//                 (TMA, mbarrier-completed); candidates (>= threshold) are
-//                 checked against their 8 (A,B) neighbours; peaks are
-//                 compacted in order into per-CTA chunks.
+//                 (TMA, mbarrier-completed).  A stage with no cell >= T (the
+//                 common case) costs one 16-byte load per thread and row and
+//                 one block vote; only stages holding candidates check the 8
+//                 (A,B) neighbours and compact peaks, in order, into per-CTA
+//                 chunks.  k_scan_direct is the same without staging, for
+//                 n_b not a multiple of 4.
 //   k_order       places every CTA's chunks at their global rank: ascending
 //                 linear index per event, expanded to 32-byte peak records.
 #include "ht_device.cuh"
@@ -40,7 +48,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
 }
 
 // Exclusive scan of n values in shared memory (in place); returns the total.
-// All threads of the block must call it.  wsum: >= 32 words of scratch.
+// All threads of the block must call it.  wsum: >= 33 words of scratch.
 __device__ uint32_t block_exclusive_scan(uint32_t *a, uint32_t n, uint32_t *wsum)
 {
     const uint32_t tid = threadIdx.x, bd = blockDim.x;
@@ -74,53 +82,23 @@ __device__ uint32_t block_exclusive_scan(uint32_t *a, uint32_t n, uint32_t *wsum
 }
 
 // ---------------------------------------------------------------------------
-// k_prep: one CTA per event.
+// k_bin: one thread per hit.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_prep(Geom g, Work w)
+__global__ void __launch_bounds__(256) k_bin(Geom g, Work w)
 {
-    extern __shared__ uint32_t sm[];
-    uint32_t *hist = sm;                               // n_slices
-    uint32_t *wsum = hist + g.n_slices;                // 33
-    float *et = reinterpret_cast<float *>(wsum + 33);  // nt + 1
-    float *ep = et + g.nt + 1;                         // np + 1
-
-    const uint32_t e = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
-    const uint32_t h0 = ev_hit_begin(w, e), h1 = ev_hit_end(w, e);
-    for (uint32_t i = tid; i < g.n_slices; i += bd)
-        hist[i] = 0;
-    for (uint32_t i = tid; i <= g.nt; i += bd)
+    __shared__ float et[1025], ep[1025];
+    for (uint32_t i = threadIdx.x; i <= g.nt; i += blockDim.x)
         et[i] = g.et[i];
-    for (uint32_t i = tid; i <= g.np; i += bd)
+    for (uint32_t i = threadIdx.x; i <= g.np; i += blockDim.x)
         ep[i] = g.ep[i];
     __syncthreads();
-
-    for (uint32_t h = h0 + tid; h < h1; h += bd) {
-        float r2;
-        Admit a;
-        if (admit_hit(g, et, ep, w.x[h], w.y[h], w.z[h], r2, a))
-            for_each_slice(g, a, [&](uint32_t s) { atomicAdd(&hist[s], 1u); });
-    }
-    __syncthreads();
-    const uint32_t total = block_exclusive_scan(hist, g.n_slices, wsum);
-    uint32_t *so = w.slice_off + (size_t)e * (g.n_slices + 1);
-    for (uint32_t i = tid; i < g.n_slices; i += bd)
-        so[i] = hist[i];
-    if (tid == 0)
-        so[g.n_slices] = total;
-    __syncthreads();
-
-    float4 *out = w.hits4 + (size_t)h0 * g.max_admit;
-    for (uint32_t h = h0 + tid; h < h1; h += bd) {
-        float r2;
-        Admit a;
+    const uint32_t n = w.hit_off ? w.hit_off[w.n_events] : w.n_hits0;
+    for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
         const float x = w.x[h], y = w.y[h];
-        if (admit_hit(g, et, ep, x, y, w.z[h], r2, a)) {
-            const float d = __fmul_rn(2.0f, y);
-            for_each_slice(g, a, [&](uint32_t s) {
-                const uint32_t pos = atomicAdd(&hist[s], 1u);
-                out[pos] = make_float4(x, r2, d, __uint_as_float(s));
-            });
-        }
+        float r2;
+        const uint32_t code = bin_code(g, et, ep, x, y, w.z[h], r2);
+        w.hits4[h] = make_float4(x, r2, __fmul_rn(2.0f, y), 0.0f);
+        w.codes[h] = code;
     }
 }
 
@@ -203,53 +181,102 @@ __device__ __forceinline__ void flush_rows(const Geom &g, uint32_t *tile, uint32
         }
         __syncthreads();
         // clear the tile after every thread has read its cells
-        const uint32_t words = U16 ? rows * pitch : rows * pitch;
-        for (uint32_t k = tid; k < words; k += bd)
+        for (uint32_t k = tid; k < rows * pitch; k += bd)
             tile[k] = 0u;
     }
+}
+
+// Select, from hit `pos` on in [pos, h1), the hits admitted to slice
+// (ts, ps) into hs[0 .. returned count), stopping before fewer than
+// blockDim free entries would remain.  Advances `pos` (uniform) by at least
+// blockDim while pos < h1: the caller guarantees cap >= blockDim.
+__device__ __forceinline__ uint32_t select_hits(const Geom &g, const Work &w, float4 *hs, uint32_t cap,
+                                                uint32_t &pos, uint32_t h1, uint32_t ts, uint32_t ps,
+                                                uint32_t *s_n)
+{
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, lane = tid & 31u;
+    __syncthreads();
+    if (tid == 0)
+        *s_n = 0;
+    __syncthreads();
+    uint32_t n = 0;
+    while (pos < h1 && n + bd <= cap) {
+        const uint32_t h = pos + tid;
+        const bool ok = h < h1 && admits(g, w.codes[h], ts, ps);
+        const uint32_t m = __ballot_sync(0xffffffffu, ok);
+        uint32_t base = 0;
+        if (lane == 0 && m)
+            base = atomicAdd(s_n, (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ok)
+            hs[base + __popc(m & ((1u << lane) - 1u))] = w.hits4[h];
+        pos += bd;
+        n += __syncthreads_count(ok);   // uniform count; also the block barrier
+    }
+    return n;
 }
 
 __global__ void __launch_bounds__(512) k_fill_priv(Geom g, Work w, FillCfg c)
 {
     extern __shared__ uint4 sm4[];
+    __shared__ uint32_t s_n;
     uint32_t *tile = reinterpret_cast<uint32_t *>(sm4);
     float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
 
     const uint32_t tid = threadIdx.x, bd = blockDim.x;
     for (uint32_t k = tid; k < c.tile_words / 4; k += bd)
         sm4[k] = make_uint4(0u, 0u, 0u, 0u);
-    __syncthreads();
 
     const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
-    for (uint64_t item = blockIdx.x; item < items; item += gridDim.x) {
+    const uint64_t it0 = items * blockIdx.x / gridDim.x, it1 = items * (blockIdx.x + 1) / gridDim.x;
+    uint64_t cached_es = ~0ull;   // (event, slice) whose whole selection is in hs
+    uint32_t cached_n = 0;
+
+    for (uint64_t item = it0; item < it1; ++item) {
         const uint32_t k = (uint32_t)(item % c.strips);
-        const uint64_t rest = item / c.strips;
-        const uint32_t s = (uint32_t)(rest % g.n_slices);
-        const uint32_t e = (uint32_t)(rest / g.n_slices);
-        const uint32_t *so = w.slice_off + (size_t)e * (g.n_slices + 1);
-        const uint32_t hb = so[s], n_s = so[s + 1] - hb;
-        const float4 *hits = w.hits4 + (size_t)ev_hit_begin(w, e) * g.max_admit + hb;
+        const uint64_t es = item / c.strips;
+        const uint32_t s = (uint32_t)(es % g.n_slices);
+        const uint32_t e = (uint32_t)(es / g.n_slices);
+        const uint32_t ts = s / g.np, ps = s - ts * g.np;
+        const uint32_t h0 = ev_hit_begin(w, e), h1 = ev_hit_end(w, e);
         const uint32_t i0 = k * c.W;
         const uint32_t rows = min(c.W, g.na - i0);
-        const bool u16 = n_s < 65536u;
+        // u16 counters are exact while the slice holds < 65536 hits; the
+        // event's hit count bounds that.
+        const bool u16 = (h1 - h0) < 65536u;
         const uint32_t rpass = u16 ? c.W : c.W / 2;
         const uint32_t pitch = u16 ? c.pitch16 : c.pitch32;
         uint32_t *Mrow = w.M + (size_t)e * w.n_cells + ((size_t)s * g.na + i0) * g.nb;
+        const uint32_t r = tid % rpass, hl = tid / rpass, hstride = bd / rpass;
 
         for (uint32_t p0 = 0; p0 < rows; p0 += rpass) {
             const uint32_t pr = min(rpass, rows - p0);
-            const uint32_t r = tid % rpass, hl = tid / rpass, hstride = bd / rpass;
-            for (uint32_t c0 = 0; c0 < n_s; c0 += c.HC) {
-                const uint32_t nc = min(c.HC, n_s - c0);
-                __syncthreads();
-                for (uint32_t q = tid; q < nc; q += bd)
-                    hs[q] = hits[c0 + q];
+            const uint32_t i = i0 + p0 + r;
+            if (cached_es == es) {
                 __syncthreads();
                 if (r < pr) {
                     if (u16)
-                        vote_rows<true>(g, tile, hs, nc, r, i0 + p0 + r, hl, hstride, pitch);
+                        vote_rows<true>(g, tile, hs, cached_n, r, i, hl, hstride, pitch);
                     else
-                        vote_rows<false>(g, tile, hs, nc, r, i0 + p0 + r, hl, hstride, pitch);
+                        vote_rows<false>(g, tile, hs, cached_n, r, i, hl, hstride, pitch);
+                }
+            } else {
+                cached_es = ~0ull;       // hs is about to be overwritten
+                uint32_t pos = h0;
+                bool first = true;
+                while (first || pos < h1) {
+                    const uint32_t nsel = select_hits(g, w, hs, c.HC, pos, h1, ts, ps, &s_n);
+                    if (first && pos >= h1) {
+                        cached_es = es;   // the whole selection fits: keep it
+                        cached_n = nsel;
+                    }
+                    first = false;
+                    if (r < pr) {
+                        if (u16)
+                            vote_rows<true>(g, tile, hs, nsel, r, i, hl, hstride, pitch);
+                        else
+                            vote_rows<false>(g, tile, hs, nsel, r, i, hl, hstride, pitch);
+                    }
                 }
             }
             __syncthreads();
@@ -257,7 +284,6 @@ __global__ void __launch_bounds__(512) k_fill_priv(Geom g, Work w, FillCfg c)
                 flush_rows<true>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, c.accumulate != 0);
             else
                 flush_rows<false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, c.accumulate != 0);
-            __syncthreads();
         }
     }
 }
@@ -276,34 +302,34 @@ __global__ void k_clear(uint32_t *M, uint64_t words)
         M[k] = 0u;
 }
 
+// 1-D grid over hits, a thread block over A, one atomicAdd per vote.
 __global__ void k_fill_naive(Geom g, Work w)
 {
     for (uint32_t e = 0; e < w.n_events; ++e) {
-        const uint32_t *so = w.slice_off + (size_t)e * (g.n_slices + 1);
-        const uint32_t n_adm = so[g.n_slices];
-        const float4 *hits = w.hits4 + (size_t)ev_hit_begin(w, e) * g.max_admit;
+        const uint32_t h0 = ev_hit_begin(w, e), h1 = ev_hit_end(w, e);
         uint32_t *M = w.M + (size_t)e * w.n_cells;
-        for (uint32_t k = blockIdx.x; k < n_adm; k += gridDim.x) {
-            const float4 hv = hits[k];
-            const uint32_t s = __float_as_uint(hv.w);
-            uint32_t *Ms = M + (size_t)s * g.na * g.nb;
-            for (uint32_t i = threadIdx.x; i < g.na; i += blockDim.x) {
-                const float twoA = __fmul_rn(2.0f, a_centre(g, i));
-                const int j = vote_bin(g, twoA, hv.x, hv.y, hv.z);
-                if (j >= 0)
-                    atomicAdd(&Ms[(size_t)i * g.nb + (uint32_t)j], 1u);
-            }
+        for (uint32_t h = h0 + blockIdx.x; h < h1; h += gridDim.x) {
+            const float4 hv = w.hits4[h];
+            for_each_slice(g, w.codes[h], [&](uint32_t s) {
+                uint32_t *Ms = M + (size_t)s * g.na * g.nb;
+                for (uint32_t i = threadIdx.x; i < g.na; i += blockDim.x) {
+                    const float twoA = __fmul_rn(2.0f, a_centre(g, i));
+                    const int j = vote_bin(g, twoA, hv.x, hv.y, hv.z);
+                    if (j >= 0)
+                        atomicAdd(&Ms[(size_t)i * g.nb + (uint32_t)j], 1u);
+                }
+            });
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// k_scan
+// Scan
 // ---------------------------------------------------------------------------
 // Peak test of the cell at column j of `row` (value v >= threshold).
 // up / dn are the neighbouring rows of the same slice or nullptr.
-template <class P>
-__device__ __forceinline__ bool is_peak(P row, P up, P dn, uint32_t j, uint32_t nb, uint32_t v)
+__device__ __forceinline__ bool is_peak(const uint32_t *row, const uint32_t *up, const uint32_t *dn,
+                                        uint32_t j, uint32_t nb, uint32_t v)
 {
     const bool hl = j > 0, hr = j + 1 < nb;
     if (up) {
@@ -352,8 +378,9 @@ __device__ __forceinline__ void flush_chunk(const ScanArgs &a, ScanSmem &ss, con
     __syncthreads();
 }
 
-// Ordered compaction of one round: each thread holds cnt (<= 4) peaks in
-// pk/pv (columns of `row_lin0`); appends them to pbuf in thread order.
+// Ordered compaction of one round: each thread holds cnt peaks in pj/pv
+// (columns of the row starting at row_lin0); appends them to pbuf in
+// thread order and counts them for their event.
 __device__ __forceinline__ void compact_round(ScanSmem &ss, uint4 *pbuf, uint32_t &buf_n, uint32_t cnt,
                                               const uint32_t *pj, const uint32_t *pv, uint32_t row_lin0,
                                               uint32_t event, uint32_t *ev_count)
@@ -374,15 +401,60 @@ __device__ __forceinline__ void compact_round(ScanSmem &ss, uint4 *pbuf, uint32_
         }
     }
     __syncthreads();
-    uint32_t pos = buf_n + ss.wsum[warp] + incl - cnt;
+    const uint32_t pos = buf_n + ss.wsum[warp] + incl - cnt;
     for (uint32_t k = 0; k < cnt; ++k)
         pbuf[pos + k] = make_uint4(row_lin0 + pj[k], event, pv[k], 0u);
     buf_n += ss.round_total;
     __syncthreads();
 }
 
-template <bool TMA>
-__global__ void __launch_bounds__(256) k_scan(Geom g, Work w, ScanArgs a)
+// Detailed pass over global rows [ra, rb): candidates, neighbour tests and
+// ordered compaction.  Rows [ra - 1, rb + 1) (clipped) are readable at
+// base + (gr - b_first) * nb.  Each thread takes VEC consecutive cells.
+template <int VEC>
+__device__ void scan_rows_slow(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss, uint4 *pbuf,
+                               uint32_t &buf_n, uint32_t &nseq, uint32_t &total, uint64_t ra, uint64_t rb,
+                               const uint32_t *base, uint64_t b_first)
+{
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb, T = g.threshold;
+    const uint64_t rows_ev = (uint64_t)g.n_slices * g.na;
+    const uint32_t units = nb / VEC;
+    const uint32_t rounds = (units + bd - 1) / bd;
+    for (uint64_t gr = ra; gr < rb; ++gr) {
+        const uint32_t i = (uint32_t)(gr % g.na);
+        const uint32_t ev = (uint32_t)(gr / rows_ev);
+        const uint32_t row_lin0 = (uint32_t)((gr - (uint64_t)ev * rows_ev) * nb);
+        const uint32_t *row = base + (gr - b_first) * nb;
+        const uint32_t *up = i > 0 ? row - nb : nullptr;
+        const uint32_t *dn = i + 1 < g.na ? row + nb : nullptr;
+        for (uint32_t rd = 0; rd < rounds; ++rd) {
+            const uint32_t u = rd * bd + tid;
+            uint32_t cnt = 0, pj[VEC], pv[VEC];
+            if (u < units) {
+#pragma unroll
+                for (uint32_t c = 0; c < (uint32_t)VEC; ++c) {
+                    const uint32_t j = VEC * u + c;
+                    const uint32_t v = row[j];
+                    if (v >= T && is_peak(row, up, dn, j, nb, v)) {
+                        pj[cnt] = j;
+                        pv[cnt] = v;
+                        ++cnt;
+                    }
+                }
+            }
+            if (__syncthreads_or(cnt)) {
+                // at most 2 peaks among 4 consecutive cells (no two peaks are neighbours)
+                if (buf_n + (VEC > 1 ? 2u : 1u) * bd > a.K)
+                    flush_chunk(a, ss, pbuf, buf_n, nseq, w.status);
+                compact_round(ss, pbuf, buf_n, cnt, pj, pv, row_lin0, ev, a.ev_count);
+                total += ss.round_total;
+            }
+        }
+    }
+}
+
+// TMA-staged scan (n_b % 4 == 0).
+__global__ void __launch_bounds__(256) k_scan_tma(Geom g, Work w, ScanArgs a)
 {
     extern __shared__ uint4 sm4[];
     // layout: [0, 192) ScanSmem | [192, 256) 8 mbarriers | K peak entries | S stage slots
@@ -393,113 +465,69 @@ __global__ void __launch_bounds__(256) k_scan(Geom g, Work w, ScanArgs a)
 
     const uint32_t tid = threadIdx.x, bd = blockDim.x;
     const uint32_t nb = g.nb, T = g.threshold;
-    const uint64_t rows_ev = (uint64_t)g.n_slices * g.na;
-    const uint64_t G = rows_ev * w.n_events;
+    const uint64_t G = (uint64_t)g.n_slices * g.na * w.n_events;
     const uint64_t g0 = G * blockIdx.x / gridDim.x, g1 = G * (blockIdx.x + 1) / gridDim.x;
-    const uint32_t VEC = TMA ? 4u : 1u;
-    const uint32_t units = nb / VEC;
-    const uint32_t rounds = (units + bd - 1) / bd;
-
+    const uint32_t R = a.R, S = a.S;
+    const uint64_t n_stages = (g1 - g0 + R - 1) / R;
     uint32_t buf_n = 0, nseq = 0, total = 0;
 
-    // --- pipeline state (TMA) ---
-    const uint32_t R = a.R;
-    const uint64_t n_stages = (g1 - g0 + R - 1) / R;
-    if (TMA) {
-        if (tid == 0) {
-            ss.abort = 0;
-            for (uint32_t q = 0; q < a.S; ++q)
-                mbar_init(&bars[q], 1);
-            fence_mbar_init();
-        }
-        __syncthreads();
+    if (tid == 0) {
+        ss.abort = 0;
+        for (uint32_t q = 0; q < S; ++q)
+            mbar_init(&bars[q], 1);
+        fence_mbar_init();
     }
+    __syncthreads();
+    // stage k: own rows [g0 + kR, min(g0 + (k+1)R, g1)), loaded with one
+    // halo row on each side (clipped to the matrix).
     auto issue = [&](uint64_t k) {
-        // stage k: own rows [ra, rb), buffer rows [ba, bb)
         const uint64_t ra = g0 + k * R, rb = min(ra + R, g1);
         const uint64_t ba = ra > 0 ? ra - 1 : 0, bb = min(rb + 1, G);
-        const uint32_t q = (uint32_t)(k % a.S);
+        const uint32_t q = (uint32_t)(k % S);
         const uint32_t bytes = (uint32_t)((bb - ba) * nb * 4u);
         mbar_arrive_expect_tx(&bars[q], bytes);
         bulk_load(slots + (size_t)q * a.slot_words, w.M + ba * nb, bytes, &bars[q]);
     };
-    if (TMA && tid == 0) {
-        for (uint64_t k = 0; k < n_stages && k < a.S; ++k)
+    if (tid == 0)
+        for (uint64_t k = 0; k < n_stages && k < S; ++k)
             issue(k);
-    }
 
     uint64_t k_abort = 0;
     for (uint64_t k = 0; k < n_stages; ++k) {
         const uint64_t ra = g0 + k * R, rb = min(ra + R, g1);
         const uint64_t ba = ra > 0 ? ra - 1 : 0;
-        const uint32_t q = TMA ? (uint32_t)(k % a.S) : 0u;
+        const uint32_t q = (uint32_t)(k % S);
         const uint32_t *slot = slots + (size_t)q * a.slot_words;
-        if (TMA) {
-            if (!mbar_wait_bounded(&bars[q], (uint32_t)((k / a.S) & 1u)))
-                atomicOr(&ss.abort, 1u);
-            __syncthreads();
-            if (ss.abort) {
-                k_abort = k;
-                break;
-            }
+        if (!mbar_wait_bounded(&bars[q], (uint32_t)((k / S) & 1u)))
+            atomicOr(&ss.abort, 1u);
+        __syncthreads();
+        if (ss.abort) {
+            k_abort = k;
+            break;
         }
-        for (uint64_t gr = ra; gr < rb; ++gr) {
-            const uint32_t i = (uint32_t)(gr % g.na);
-            const uint32_t ev = (uint32_t)(gr / rows_ev);
-            const uint32_t row_lin0 = (uint32_t)((gr - (uint64_t)ev * rows_ev) * nb);
-            const uint32_t *row = TMA ? slot + (gr - ba) * nb : w.M + gr * nb;
-            const uint32_t *up = i > 0 ? row - nb : nullptr;
-            const uint32_t *dn = i + 1 < g.na ? row + nb : nullptr;
-            for (uint32_t rd = 0; rd < rounds; ++rd) {
-                const uint32_t u = rd * bd + tid;
-                uint32_t cnt = 0, pj[4], pv[4];
-                if (u < units) {
-                    if (TMA) {
-                        const uint4 v4 = reinterpret_cast<const uint4 *>(row)[u];
-                        const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
-                        if (max(max(v4.x, v4.y), max(v4.z, v4.w)) >= T) {
-#pragma unroll
-                            for (uint32_t c = 0; c < 4; ++c) {
-                                const uint32_t j = 4 * u + c;
-                                if (vv[c] >= T && is_peak(row, up, dn, j, nb, vv[c])) {
-                                    pj[cnt] = j;
-                                    pv[cnt] = vv[c];
-                                    ++cnt;
-                                }
-                            }
-                        }
-                    } else {
-                        const uint32_t v = row[u];
-                        if (v >= T && is_peak(row, up, dn, u, nb, v)) {
-                            pj[0] = u;
-                            pv[0] = v;
-                            cnt = 1;
-                        }
-                    }
-                }
-                if (__syncthreads_or(cnt)) {
-                    if (buf_n + 4 * bd > a.K)
-                        flush_chunk(a, ss, pbuf, buf_n, nseq, w.status);
-                    compact_round(ss, pbuf, buf_n, cnt, pj, pv, row_lin0, ev, a.ev_count);
-                    total += ss.round_total;
-                }
-            }
+        // fast path: any cell >= T among the stage's own rows?
+        const uint4 *own = reinterpret_cast<const uint4 *>(slot + (ra - ba) * nb);
+        const uint32_t n4 = (uint32_t)(rb - ra) * (nb >> 2);
+        uint32_t hot = 0;
+        for (uint32_t u = tid; u < n4; u += bd) {
+            const uint4 v = own[u];
+            hot |= (max(max(v.x, v.y), max(v.z, v.w)) >= T);
         }
-        if (TMA) {
-            __syncthreads();  // every thread is done with slot q
-            if (tid == 0 && k + a.S < n_stages) {
-                fence_proxy_async_smem();
-                issue(k + a.S);
-            }
+        if (__syncthreads_or(hot))
+            scan_rows_slow<4>(g, w, a, ss, pbuf, buf_n, nseq, total, ra, rb, slot, ba);
+        __syncthreads();  // every thread is done with slot q
+        if (tid == 0 && k + S < n_stages) {
+            fence_proxy_async_smem();
+            issue(k + S);
         }
     }
-    if (TMA && ss.abort) {
+    if (ss.abort) {
         // let the copies still in flight (bounded wait) land before the CTA exits
         if (tid == 0) {
             atomicOr(w.status, (uint32_t)ST_WAIT_TIMEOUT);
-            const uint64_t k_end = min(n_stages, k_abort + a.S);
+            const uint64_t k_end = min(n_stages, k_abort + S);
             for (uint64_t kk = k_abort; kk < k_end; ++kk)
-                (void)mbar_wait_bounded(&bars[kk % a.S], (uint32_t)((kk / a.S) & 1u));
+                (void)mbar_wait_bounded(&bars[kk % S], (uint32_t)((kk / S) & 1u));
         }
         __syncthreads();
     }
@@ -510,8 +538,37 @@ __global__ void __launch_bounds__(256) k_scan(Geom g, Work w, ScanArgs a)
     }
 }
 
+// Direct-load scan for any n_b (no staging).
+__global__ void __launch_bounds__(256) k_scan_direct(Geom g, Work w, ScanArgs a)
+{
+    extern __shared__ uint4 sm4[];
+    ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
+    uint4 *pbuf = sm4 + 16;
+    const uint32_t tid = threadIdx.x, bd = blockDim.x;
+    const uint32_t nb = g.nb, T = g.threshold;
+    const uint64_t G = (uint64_t)g.n_slices * g.na * w.n_events;
+    const uint64_t g0 = G * blockIdx.x / gridDim.x, g1 = G * (blockIdx.x + 1) / gridDim.x;
+    const uint32_t R = a.R;
+    uint32_t buf_n = 0, nseq = 0, total = 0;
+    for (uint64_t ra = g0; ra < g1; ra += R) {
+        const uint64_t rb = min(ra + R, g1);
+        const uint32_t *own = w.M + ra * nb;
+        const uint64_t n = (rb - ra) * nb;
+        uint32_t hot = 0;
+        for (uint64_t u = tid; u < n; u += bd)
+            hot |= own[u] >= T;
+        if (__syncthreads_or(hot))
+            scan_rows_slow<1>(g, w, a, ss, pbuf, buf_n, nseq, total, ra, rb, w.M, 0);
+    }
+    flush_chunk(a, ss, pbuf, buf_n, nseq, w.status);
+    if (tid == 0) {
+        a.cta_nseq[blockIdx.x] = min(nseq, a.seq_max);
+        a.cta_total[blockIdx.x] = total;
+    }
+}
+
 // ---------------------------------------------------------------------------
-// k_order: same grid as k_scan.
+// k_order: same grid as the scan.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, OrderArgs o)
 {
@@ -528,7 +585,6 @@ __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, Order
     part = warp_incl_scan(part);
     if ((tid & 31u) == 31u)
         red[tid >> 5] = part;
-    // per-event exclusive bases
     for (uint32_t e = tid; e < w.n_events; e += bd)
         ev_base[e] = o.ev_count[e];
     __syncthreads();
@@ -596,15 +652,9 @@ __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, Order
 // ---------------------------------------------------------------------------
 namespace htk {
 
-cudaError_t launch_prep(const Geom &g, const Work &w, cudaStream_t st)
+cudaError_t launch_bin(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st)
 {
-    const size_t smem = (g.n_slices + 33 + g.nt + 1 + g.np + 1) * sizeof(uint32_t);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-    }
-    k_prep<<<w.n_events, 1024, smem, st>>>(g, w);
+    k_bin<<<grid, 256, 0, st>>>(g, w);
     return cudaGetLastError();
 }
 
@@ -647,15 +697,15 @@ cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, bool tm
     const size_t smem = scan_smem_bytes(a);
     cudaError_t e;
     if (tma) {
-        e = cudaFuncSetAttribute(k_scan<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_scan_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        k_scan<true><<<a.grid, 256, smem, st>>>(g, w, a);
+        k_scan_tma<<<a.grid, 256, smem, st>>>(g, w, a);
     } else {
-        e = cudaFuncSetAttribute(k_scan<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_scan_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        k_scan<false><<<a.grid, 256, smem, st>>>(g, w, a);
+        k_scan_direct<<<a.grid, 256, smem, st>>>(g, w, a);
     }
     return cudaGetLastError();
 }
@@ -677,15 +727,15 @@ cudaError_t scan_occupancy(bool tma, size_t smem, int *blocks_per_sm)
 {
     cudaError_t e;
     if (tma) {
-        e = cudaFuncSetAttribute(k_scan<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_scan_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_scan<true>, 256, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_scan_tma, 256, smem);
     }
-    e = cudaFuncSetAttribute(k_scan<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_scan_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_scan<false>, 256, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_scan_direct, 256, smem);
 }
 
 cudaError_t fill_occupancy(const FillCfg &c, int *blocks_per_sm)

@@ -83,6 +83,8 @@ def event_cases():
     yield "partial_ranges", (3, 6, 80, 64, 1, 2), dict(theta_min=0.4, theta_max=2.6, phi_min=-2.0,
                                                        phi_max=1.5), 3, (ev.x, ev.y, ev.z)
     yield "wide_b", (2, 2, 40, 2048), {}, 3, (ev.x, ev.y, ev.z)
+    # thousands of hits per slice: the fill selects them in several chunks
+    yield "dense_slices", (1, 2, 70, 128), {}, 6, random_hits(5000, 4, rmax=900.0)
 
 
 CASES = list(event_cases())
