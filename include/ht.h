@@ -170,6 +170,28 @@ typedef struct {
 ht_status ht_profile(ht_ctx *ctx, int enable);
 ht_status ht_profile_read(ht_ctx *ctx, ht_kernel_time *out, uint32_t cap, uint32_t *n);
 
+/* Launch shapes.  Every field 0 means automatic; results (M_H and peaks)
+ * are identical for every accepted tuning, only the speed changes.
+ *   fill_rows          A rows per shared-memory vote tile (power of two)
+ *   fill_threads       256, 512 or 1024 threads per fill CTA
+ *   fill_hits_staged   hits staged in shared memory per selection chunk
+ *   fill_blocks_per_sm cap on resident fill CTAs per SM
+ *   scan_kind          HT_SCAN_BULK (1-D bulk-copy ring), HT_SCAN_STREAM
+ *                      (register streaming), HT_SCAN_DIRECT (scalar)
+ *   scan_stage_bytes   bulk-copy stage size; scan_slots: ring depth (2..8)
+ *   scan_blocks_per_sm cap on resident scan CTAs per SM
+ * ht_set_tuning waits for the device, re-derives the shapes and returns
+ * HT_E_INVAL for an impossible value; ht_get_tuning reports the shapes in
+ * effect (0 fields filled in). */
+enum { HT_SCAN_AUTO = 0, HT_SCAN_BULK = 1, HT_SCAN_STREAM = 2, HT_SCAN_DIRECT = 3 };
+typedef struct {
+    uint32_t fill_rows, fill_threads, fill_hits_staged, fill_blocks_per_sm;
+    uint32_t scan_kind, scan_stage_bytes, scan_slots, scan_blocks_per_sm;
+} ht_tuning;
+
+ht_status ht_set_tuning(ht_ctx *ctx, const ht_tuning *tuning);
+ht_status ht_get_tuning(ht_ctx *ctx, ht_tuning *tuning);
+
 /* ------------------------------------------------------------------------ */
 /* Host-only helpers (no device needed).                                     */
 /* ------------------------------------------------------------------------ */

@@ -269,6 +269,58 @@ ht_status ht_set_matrix(ht_ctx *ctx, const uint32_t *src, uint64_t n_cells, uint
 
 uint64_t ht_launch_count(const ht_ctx *ctx) { return ctx ? ctx->E.launches : 0; }
 
+ht_status ht_set_tuning(ht_ctx *ctx, const ht_tuning *t)
+{
+    ht_status s = check_ctx(ctx);
+    if (s != HT_OK)
+        return s;
+    if (!t)
+        return set_err(HT_E_INVAL, "tuning is NULL");
+    if (t->scan_kind > HT_SCAN_DIRECT)
+        return set_err(HT_E_INVAL, "unknown scan_kind");
+    CK(cudaStreamSynchronize(ctx->stream));
+    hte::Tuning old = ctx->E.tune;
+    hte::Tuning &n = ctx->E.tune;
+    n.fill_W = t->fill_rows;
+    n.fill_threads = t->fill_threads;
+    n.fill_HC = t->fill_hits_staged;
+    n.fill_blocks_per_sm = t->fill_blocks_per_sm;
+    n.scan_kind = t->scan_kind;
+    n.scan_stage_bytes = t->scan_stage_bytes;
+    n.scan_slots = t->scan_slots;
+    n.scan_blocks_per_sm = t->scan_blocks_per_sm;
+    std::string why;
+    s = hte::engine_configure(ctx->E, &why);
+    if (s != HT_OK) {
+        ctx->E.tune = old;
+        std::string why2;
+        if (hte::engine_configure(ctx->E, &why2) != HT_OK)
+            ctx->poisoned = true;
+        return set_err(s, why);
+    }
+    return HT_OK;
+}
+
+ht_status ht_get_tuning(ht_ctx *ctx, ht_tuning *t)
+{
+    ht_status s = check_ctx(ctx);
+    if (s != HT_OK)
+        return s;
+    if (!t)
+        return set_err(HT_E_INVAL, "tuning is NULL");
+    const hte::Engine &E = ctx->E;
+    t->fill_rows = E.fill.W;
+    t->fill_threads = E.fill.threads;
+    t->fill_hits_staged = E.fill.HC;
+    t->fill_blocks_per_sm = E.num_sms ? E.fill_grid / (uint32_t)E.num_sms : 0;
+    t->scan_kind = E.scan_kind == htk::SCAN_BULK ? HT_SCAN_BULK
+                 : E.scan_kind == htk::SCAN_LDG ? HT_SCAN_STREAM : HT_SCAN_DIRECT;
+    t->scan_stage_bytes = E.scan.slot_words * 4;
+    t->scan_slots = E.scan.S;
+    t->scan_blocks_per_sm = E.num_sms ? E.scan_grid_max / (uint32_t)E.num_sms : 0;
+    return HT_OK;
+}
+
 ht_status ht_profile(ht_ctx *ctx, int enable)
 {
     ht_status s = check_ctx(ctx);

@@ -106,17 +106,26 @@ ht_status engine_configure(Engine &E, std::string *why)
 {
     const ht_binning &b = E.b;
     const Tuning &t = E.tune;
+    const htk::Geom &g = E.geom;
     char buf[256];
 
     // --- privatised fill -------------------------------------------------
     htk::FillCfg f{};
     f.threads = t.fill_threads ? t.fill_threads : 512;
-    f.HC = std::max(t.fill_HC ? t.fill_HC : 512u, f.threads);   // select_hits needs HC >= threads
+    if (f.threads != 256 && f.threads != 512 && f.threads != 1024) {
+        *why = "fill_threads must be 256, 512 or 1024";
+        return HT_E_INVAL;
+    }
+    f.HC = std::max(t.fill_HC ? t.fill_HC : 1024u, 2 * f.threads);   // select_hits needs HC >= 2 * threads
     f.pitch16 = round_up((b.n_b + 1) / 2, 32);
     f.pitch32 = round_up(b.n_b, 32);
     uint32_t W = t.fill_W;
+    if (W && (W & (W - 1))) {
+        *why = "fill_rows must be a power of two";
+        return HT_E_INVAL;
+    }
     if (!W) {
-        // aim at ~64 KB tiles so that three CTAs share an SM
+        // aim at ~64 KB tiles so that several CTAs share an SM
         W = 64;
         while (W > 2 && (size_t)W * f.pitch16 * 4 > 64 * 1024)
             W >>= 1;
@@ -144,34 +153,40 @@ ht_status engine_configure(Engine &E, std::string *why)
     E.clear_grid = (uint32_t)E.num_sms * 4;
     E.naive_grid = (uint32_t)E.num_sms * 16;
 
-    // --- scan --------------------------------------------------------------
+    // --- scan variant and shape --------------------------------------------
     htk::ScanArgs &s = E.scan;
     const size_t row_bytes = (size_t)b.n_b * 4;
     const size_t fixed = 16 * 16 + (size_t)kPeakBuf * 16;
+    const bool vec = (b.n_b & 3u) == 0;
     s.K = kPeakBuf;
-    E.scan_tma = false;
-    if ((b.n_b & 3u) == 0) {
-        size_t target = t.scan_stage_bytes ? t.scan_stage_bytes : (row_bytes >= 8192 ? 65536 : 32768);
+    int kind = !vec ? htk::SCAN_DIRECT
+             : t.scan_kind == 1 ? htk::SCAN_BULK
+             : t.scan_kind == 3 ? htk::SCAN_DIRECT : htk::SCAN_LDG;
+    if (kind == htk::SCAN_BULK) {
+        const size_t target = t.scan_stage_bytes ? t.scan_stage_bytes : (row_bytes >= 8192 ? 65536 : 32768);
         uint32_t rows = (uint32_t)std::max<size_t>(3, target / row_bytes);     // R + 2
-        uint32_t S = t.scan_slots ? t.scan_slots : 4;
+        uint32_t S = t.scan_slots ? std::min<uint32_t>(std::max<uint32_t>(t.scan_slots, 2), 8) : 4;
         while (S > 2 && fixed + (size_t)S * rows * row_bytes > kSmemMax)
             --S;
         while (rows > 3 && fixed + (size_t)S * rows * row_bytes > kSmemMax)
             --rows;
         if (fixed + (size_t)S * rows * row_bytes <= kSmemMax && rows * row_bytes < (1u << 20)) {
-            E.scan_tma = true;
             s.S = S;
             s.R = rows - 2;
             s.slot_words = rows * b.n_b;
+        } else {
+            kind = htk::SCAN_LDG;
         }
     }
-    if (!E.scan_tma) {
+    if (kind != htk::SCAN_BULK) {
         s.S = 0;
-        s.R = 64;
         s.slot_words = 0;
+        // streaming: a chunk is kLdgUPT 16-byte units per thread
+        s.R = kind == htk::SCAN_LDG ? std::max<uint32_t>(1, htk::kLdgUPT * kScanThreads / (b.n_b / 4)) : 16;
     }
+    E.scan_kind = kind;
     int occ = 0;
-    cudaError_t e = htk::scan_occupancy(E.scan_tma, htk::scan_smem_bytes(s), &occ);
+    cudaError_t e = htk::scan_occupancy(kind, htk::scan_smem_bytes(s), &occ);
     if (e != cudaSuccess || occ < 1) {
         std::snprintf(buf, sizeof buf, "scan occupancy query failed: %s", cudaGetErrorString(e));
         *why = buf;
@@ -180,6 +195,38 @@ ht_status engine_configure(Engine &E, std::string *why)
     if (t.scan_blocks_per_sm)
         occ = std::min<int>(occ, (int)t.scan_blocks_per_sm);
     E.scan_grid_max = (uint32_t)E.num_sms * (uint32_t)occ;
+
+    // --- chunk bookkeeping for the largest launch (max_events events) ---------
+    const uint64_t G_max = (uint64_t)g.n_slices * g.na * E.max_events;
+    const uint64_t grid_max = std::max<uint64_t>(1, std::min<uint64_t>(E.scan_grid_max, G_max));
+    const uint64_t rows_per_cta = (G_max + grid_max - 1) / grid_max + 1;
+    const uint64_t per_round_max = 2ull * kScanThreads;   // <= 2 peaks per 4 consecutive cells
+    const uint64_t peaks_run = rows_per_cta * ((g.nb + 1) / 2);
+    s.seq_max = (uint32_t)std::min<uint64_t>(peaks_run / (s.K - per_round_max) + 2, 1u << 20);
+    const size_t desc_bytes = (size_t)grid_max * s.seq_max * 8, cta_bytes = (size_t)grid_max * 8;
+    if (desc_bytes > E.desc_bytes || cta_bytes > E.cta_bytes) {
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+            *why = std::string("synchronise before re-allocation: ") + cudaGetErrorString(e);
+            return HT_E_CUDA;
+        }
+        cudaFree(E.d_desc);
+        cudaFree(E.d_cta);
+        E.d_desc = nullptr;
+        E.d_cta = nullptr;
+        E.desc_bytes = E.cta_bytes = 0;
+        if ((e = cudaMalloc(&E.d_desc, desc_bytes)) != cudaSuccess ||
+            (e = cudaMalloc(&E.d_cta, cta_bytes)) != cudaSuccess) {
+            cudaGetLastError();
+            *why = std::string("scan bookkeeping allocation failed: ") + cudaGetErrorString(e);
+            return HT_E_NOMEM;
+        }
+        E.desc_bytes = desc_bytes;
+        E.cta_bytes = cta_bytes;
+    }
+    s.desc = E.d_desc;
+    s.cta_nseq = E.d_cta;
+    s.cta_total = E.d_cta + grid_max;
+    s.grid = (uint32_t)grid_max;
     return HT_OK;
 }
 
@@ -243,20 +290,15 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
     }
 
     ht_status st = engine_configure(E, why);
-    if (st != HT_OK)
+    if (st != HT_OK) {
+        engine_destroy(E);
         return st;
+    }
 
-    // --- scan bookkeeping sizes ------------------------------------------------
-    htk::ScanArgs &s = E.scan;
-    const uint64_t rows_ev = (uint64_t)g.n_slices * g.na;
-    const uint64_t G_max = rows_ev * max_events;
-    const uint64_t grid_max = std::max<uint64_t>(1, std::min<uint64_t>(E.scan_grid_max, G_max));
-    const uint64_t rows_per_cta = (G_max + grid_max - 1) / grid_max + 1;
-    const uint64_t per_round_max = 2ull * kScanThreads;   // <= 2 peaks per 4 consecutive cells
-    const uint64_t peaks_run = rows_per_cta * ((g.nb + 1) / 2);
-    s.seq_max = (uint32_t)std::min<uint64_t>(peaks_run / (s.K - per_round_max) + 2, 1u << 20);
     // A peak holds >= threshold votes and no two peaks are neighbours, so
     // peaks <= min(votes / T, ceil(n_a/2) ceil(n_b/2) per slice).
+    htk::ScanArgs &s = E.scan;
+    const uint64_t per_round_max = 2ull * kScanThreads;
     const uint64_t by_votes = (uint64_t)std::max<uint32_t>(max_hits, 1) * E.max_admit * g.na / threshold + 1;
     const uint64_t by_space = (uint64_t)g.n_slices * ((g.na + 1) / 2) * ((g.nb + 1) / 2) * max_events;
     s.entries_cap = (uint32_t)std::min<uint64_t>(std::min(by_votes, by_space) + per_round_max, 0xffffffffull);
@@ -269,8 +311,6 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
         (e = dalloc(&E.d_hits4, hits_cap * 16, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_codes, hits_cap * 4, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_entries, (size_t)s.entries_cap * 16, &acc)) != cudaSuccess ||
-        (e = dalloc(&E.d_desc, (size_t)grid_max * s.seq_max * 8, &acc)) != cudaSuccess ||
-        (e = dalloc(&E.d_cta, (size_t)grid_max * 8, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_ctr, (size_t)ctr_words * 4, &acc)) != cudaSuccess) {
         std::snprintf(buf, sizeof buf, "device allocation of %zu bytes failed: %s", acc,
                       cudaGetErrorString(e));
@@ -279,7 +319,7 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
         engine_destroy(E);
         return HT_E_NOMEM;
     }
-    E.device_bytes = acc;
+    E.device_bytes = acc + E.desc_bytes + E.cta_bytes;
     g.et = E.d_edges;
     g.ep = E.d_edges + E.et.size();
     if ((e = cudaMemcpy(E.d_edges, E.et.data(), E.et.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -294,11 +334,7 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
     }
     s.entries = E.d_entries;
     s.g_count = E.d_ctr;
-    s.desc = E.d_desc;
-    s.cta_nseq = E.d_cta;
-    s.cta_total = E.d_cta + grid_max;
     s.ev_count = E.d_ctr + 3;
-    s.grid = (uint32_t)grid_max;
     return HT_OK;
 }
 
@@ -425,7 +461,7 @@ cudaError_t engine_scan(Engine &E, uint32_t n_events, htk::Peak *out, uint32_t c
     cudaError_t e;
     {
         ProfScope ps(E, K_SCAN, st);
-        e = htk::launch_scan(E.geom, w, a, E.scan_tma, st);
+        e = htk::launch_scan(E.geom, w, a, E.scan_kind, st);
     }
     if (e != cudaSuccess)
         return e;

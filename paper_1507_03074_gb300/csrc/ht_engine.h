@@ -12,14 +12,17 @@
 
 namespace hte {
 
+// Launch-shape knobs (the C ABI's ht_tuning); 0 means automatic.  Results
+// do not depend on them.
 struct Tuning {
-    uint32_t fill_W = 0;         // 0: automatic
-    uint32_t fill_threads = 512;
-    uint32_t fill_HC = 0;         // 0: max(512, threads)
-    uint32_t fill_blocks_per_sm = 0;  // 0: occupancy limit
-    uint32_t scan_stage_bytes = 0;    // 0: automatic
-    uint32_t scan_slots = 0;
-    uint32_t scan_blocks_per_sm = 0;
+    uint32_t fill_W = 0;              // A rows per shared-memory tile (power of two)
+    uint32_t fill_threads = 0;        // 256, 512 or 1024
+    uint32_t fill_HC = 0;             // hits staged per chunk (>= 2 * threads)
+    uint32_t fill_blocks_per_sm = 0;  // cap below the occupancy limit
+    uint32_t scan_kind = 0;           // 0 auto, 1 bulk-copy ring, 2 register streaming, 3 direct
+    uint32_t scan_stage_bytes = 0;    // bulk-copy stage size
+    uint32_t scan_slots = 0;          // bulk-copy ring depth (2..8)
+    uint32_t scan_blocks_per_sm = 0;  // cap below the occupancy limit
 };
 
 // Optional per-kernel timing with CUDA events recorded on the launching
@@ -53,8 +56,10 @@ struct Engine {
     bool fill_priv_ok = false;   // the tile fits in shared memory
     uint32_t fill_grid = 0;
     htk::ScanArgs scan{};
-    bool scan_tma = false;
+    int scan_kind = 0;            // htk::ScanKind in use
     uint32_t scan_grid_max = 0;
+    size_t desc_bytes = 0;        // allocated scan bookkeeping
+    size_t cta_bytes = 0;
     uint32_t clear_grid = 0, naive_grid = 0;
     Tuning tune;
 

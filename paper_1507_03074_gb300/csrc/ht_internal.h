@@ -17,7 +17,7 @@ struct FillCfg {
     uint32_t strips;      // ceil(n_a / W)
     uint32_t pitch16;     // tile words per row in u16 mode (multiple of 32)
     uint32_t pitch32;     // tile words per row in u32 mode (multiple of 32)
-    uint32_t HC;          // hits staged in shared memory per chunk (>= threads)
+    uint32_t HC;          // hits staged in shared memory per chunk (>= 2 * threads)
     uint32_t tile_words;  // W * pitch16
     uint32_t threads;     // block size
     uint32_t accumulate;  // add the tile to M_H instead of storing it
@@ -26,7 +26,7 @@ struct FillCfg {
 // Scan (and its chunk bookkeeping).  Shared with k_order.
 struct ScanArgs {
     uint32_t grid;        // persistent CTAs (each owns a contiguous run of rows)
-    uint32_t R;           // own rows per pipeline stage
+    uint32_t R;           // own rows per stage (bulk) / per chunk (streaming, direct)
     uint32_t S;           // stages in the shared-memory ring (<= 8)
     uint32_t K;           // peak entries buffered in shared memory (>= 2*256)
     uint32_t slot_words;  // (R + 2) * n_b
@@ -55,10 +55,14 @@ cudaError_t launch_fill_priv(const Geom &g, const Work &w, const FillCfg &c, uin
 cudaError_t launch_clear(uint32_t *M, uint64_t words, uint32_t grid, cudaStream_t st);
 cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
 size_t scan_smem_bytes(const ScanArgs &a);
-cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, bool tma, cudaStream_t st);
+// Scan variants: bulk-copy (TMA) ring, register streaming, direct (any n_b).
+// The streaming variant keeps kLdgUPT 16-byte loads per thread in flight.
+constexpr uint32_t kLdgUPT = 4;
+enum ScanKind { SCAN_DIRECT = 0, SCAN_BULK = 1, SCAN_LDG = 2 };
+cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, int kind, cudaStream_t st);
 cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const OrderArgs &o,
                          cudaStream_t st);
-cudaError_t scan_occupancy(bool tma, size_t smem, int *blocks_per_sm);
+cudaError_t scan_occupancy(int kind, size_t smem, int *blocks_per_sm);
 cudaError_t fill_occupancy(const FillCfg &c, int *blocks_per_sm);
 
 } // namespace htk

@@ -187,31 +187,53 @@ __device__ __forceinline__ void flush_rows(const Geom &g, uint32_t *tile, uint32
 }
 
 // Select, from hit `pos` on in [pos, h1), the hits admitted to slice
-// (ts, ps) into hs[0 .. returned count), stopping before fewer than
-// blockDim free entries would remain.  Advances `pos` (uniform) by at least
-// blockDim while pos < h1: the caller guarantees cap >= blockDim.
+// (ts, ps) into hs[0 .. returned count), kSelHPT hits per thread and
+// iteration (codes and records loaded up front, so one global latency per
+// iteration), stopping before fewer than kSelHPT * blockDim free entries
+// would remain.  Advances `pos` (uniform) by at least kSelHPT * blockDim
+// while pos < h1: the caller guarantees cap >= kSelHPT * blockDim.
+constexpr uint32_t kSelHPT = 2;
+
 __device__ __forceinline__ uint32_t select_hits(const Geom &g, const Work &w, float4 *hs, uint32_t cap,
                                                 uint32_t &pos, uint32_t h1, uint32_t ts, uint32_t ps,
                                                 uint32_t *s_n)
 {
     const uint32_t tid = threadIdx.x, bd = blockDim.x, lane = tid & 31u;
+    const uint32_t lt = (1u << lane) - 1u;
     __syncthreads();
     if (tid == 0)
         *s_n = 0;
     __syncthreads();
     uint32_t n = 0;
-    while (pos < h1 && n + bd <= cap) {
-        const uint32_t h = pos + tid;
-        const bool ok = h < h1 && admits(g, w.codes[h], ts, ps);
-        const uint32_t m = __ballot_sync(0xffffffffu, ok);
+    while (pos < h1 && n + kSelHPT * bd <= cap) {
+        uint32_t code[kSelHPT];
+        float4 hv[kSelHPT];
+#pragma unroll
+        for (uint32_t q = 0; q < kSelHPT; ++q) {
+            const uint32_t h = pos + q * bd + tid;
+            code[q] = h < h1 ? w.codes[h] : kDropped;
+            hv[q] = h < h1 ? w.hits4[h] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        uint32_t m[kSelHPT], tot = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < kSelHPT; ++q) {
+            m[q] = __ballot_sync(0xffffffffu, admits(g, code[q], ts, ps));
+            tot += __popc(m[q]);
+        }
         uint32_t base = 0;
-        if (lane == 0 && m)
-            base = atomicAdd(s_n, (uint32_t)__popc(m));
+        if (lane == 0 && tot)
+            base = atomicAdd(s_n, tot);
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (ok)
-            hs[base + __popc(m & ((1u << lane) - 1u))] = w.hits4[h];
-        pos += bd;
-        n += __syncthreads_count(ok);   // uniform count; also the block barrier
+#pragma unroll
+        for (uint32_t q = 0; q < kSelHPT; ++q) {
+            if (m[q] & (1u << lane))
+                hs[base + __popc(m[q] & lt)] = hv[q];
+            base += __popc(m[q]);
+        }
+        pos += kSelHPT * bd;
+        __syncthreads();     // every warp has added its count
+        n = *s_n;
+        __syncthreads();     // every thread has read it before the next atomics
     }
     return n;
 }
@@ -567,6 +589,47 @@ __global__ void __launch_bounds__(256) k_scan_direct(Geom g, Work w, ScanArgs a)
     }
 }
 
+// Register-streaming scan (n_b % 4 == 0): many resident warps per SM, each
+// thread keeps kLdgUPT independent 16-byte streaming loads in flight; a chunk
+// of a.R rows (kLdgUPT 16-byte units per thread) costs one block vote.
+
+__global__ void __launch_bounds__(256) k_scan_ldg(Geom g, Work w, ScanArgs a)
+{
+    extern __shared__ uint4 sm4[];
+    ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
+    uint4 *pbuf = sm4 + 16;
+    const uint32_t tid = threadIdx.x, bd = blockDim.x;
+    const uint32_t nb = g.nb, nb4 = nb >> 2, T = g.threshold;
+    const uint64_t G = (uint64_t)g.n_slices * g.na * w.n_events;
+    const uint64_t g0 = G * blockIdx.x / gridDim.x, g1 = G * (blockIdx.x + 1) / gridDim.x;
+    const uint32_t RC = a.R;
+    uint32_t buf_n = 0, nseq = 0, total = 0;
+    for (uint64_t ra = g0; ra < g1; ra += RC) {
+        const uint64_t rb = min(ra + RC, g1);
+        const uint4 *own = reinterpret_cast<const uint4 *>(w.M + ra * nb);
+        const uint32_t n4 = (uint32_t)(rb - ra) * nb4;
+        uint32_t hot = 0;
+        for (uint32_t u0 = 0; u0 < n4; u0 += kLdgUPT * bd) {
+            uint4 v[kLdgUPT];
+#pragma unroll
+            for (uint32_t q = 0; q < kLdgUPT; ++q) {
+                const uint32_t u = u0 + q * bd + tid;
+                v[q] = u < n4 ? __ldcs(own + u) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (uint32_t q = 0; q < kLdgUPT; ++q)
+                hot |= (max(max(v[q].x, v[q].y), max(v[q].z, v[q].w)) >= T);
+        }
+        if (__syncthreads_or(hot))
+            scan_rows_slow<4>(g, w, a, ss, pbuf, buf_n, nseq, total, ra, rb, w.M, 0);
+    }
+    flush_chunk(a, ss, pbuf, buf_n, nseq, w.status);
+    if (tid == 0) {
+        a.cta_nseq[blockIdx.x] = min(nseq, a.seq_max);
+        a.cta_total[blockIdx.x] = total;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // k_order: same grid as the scan.
 // ---------------------------------------------------------------------------
@@ -692,21 +755,30 @@ size_t scan_smem_bytes(const ScanArgs &a)
     return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)a.S * a.slot_words * 4;
 }
 
-cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, bool tma, cudaStream_t st)
+static const void *scan_kernel(int kind)
+{
+    switch (kind) {
+    case SCAN_BULK:
+        return (const void *)k_scan_tma;
+    case SCAN_LDG:
+        return (const void *)k_scan_ldg;
+    default:
+        return (const void *)k_scan_direct;
+    }
+}
+
+cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, int kind, cudaStream_t st)
 {
     const size_t smem = scan_smem_bytes(a);
-    cudaError_t e;
-    if (tma) {
-        e = cudaFuncSetAttribute(k_scan_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
+    cudaError_t e = cudaFuncSetAttribute(scan_kernel(kind), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    if (kind == SCAN_BULK)
         k_scan_tma<<<a.grid, 256, smem, st>>>(g, w, a);
-    } else {
-        e = cudaFuncSetAttribute(k_scan_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
+    else if (kind == SCAN_LDG)
+        k_scan_ldg<<<a.grid, 256, smem, st>>>(g, w, a);
+    else
         k_scan_direct<<<a.grid, 256, smem, st>>>(g, w, a);
-    }
     return cudaGetLastError();
 }
 
@@ -723,19 +795,13 @@ cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const 
     return cudaGetLastError();
 }
 
-cudaError_t scan_occupancy(bool tma, size_t smem, int *blocks_per_sm)
+cudaError_t scan_occupancy(int kind, size_t smem, int *blocks_per_sm)
 {
-    cudaError_t e;
-    if (tma) {
-        e = cudaFuncSetAttribute(k_scan_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_scan_tma, 256, smem);
-    }
-    e = cudaFuncSetAttribute(k_scan_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void *k = scan_kernel(kind);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_scan_direct, 256, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, 256, smem);
 }
 
 cudaError_t fill_occupancy(const FillCfg &c, int *blocks_per_sm)

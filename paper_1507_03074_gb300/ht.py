@@ -39,6 +39,15 @@ class c_ranges(ctypes.Structure):
                                               "a_min", "a_max", "b_min", "b_max")]
 
 
+TUNING_FIELDS = ("fill_rows", "fill_threads", "fill_hits_staged", "fill_blocks_per_sm",
+                 "scan_kind", "scan_stage_bytes", "scan_slots", "scan_blocks_per_sm")
+HT_SCAN_AUTO, HT_SCAN_BULK, HT_SCAN_STREAM, HT_SCAN_DIRECT = 0, 1, 2, 3
+
+
+class c_tuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in TUNING_FIELDS]
+
+
 class c_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
@@ -113,6 +122,8 @@ def lib():
         "ht_compute_edges": ([ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), P, P], I),
         "ht_profile": ([P, I], I),
         "ht_profile_read": ([P, P, U32, P], I),
+        "ht_set_tuning": ([P, ctypes.POINTER(c_tuning)], I),
+        "ht_get_tuning": ([P, ctypes.POINTER(c_tuning)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -213,6 +224,18 @@ class Context:
     @property
     def launches(self) -> int:
         return int(lib().ht_launch_count(self._h))
+
+    def set_tuning(self, **kw):
+        """ht_set_tuning: launch-shape knobs (see ht_tuning); unspecified = automatic."""
+        t = c_tuning(*[int(kw.pop(n, 0)) for n in TUNING_FIELDS])
+        if kw:
+            raise TypeError(f"unknown tuning fields {sorted(kw)}")
+        check(lib().ht_set_tuning(self._h, ctypes.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = c_tuning()
+        check(lib().ht_get_tuning(self._h, ctypes.byref(t)))
+        return {n: int(getattr(t, n)) for n in TUNING_FIELDS}
 
     def profile(self, enable: bool = True):
         """ht_profile: start (resetting totals) or stop per-kernel event timing."""

@@ -267,3 +267,53 @@ def test_upgrade_full_size_sampled(ht):
     # ordering of the whole list: ascending linear index
     lin = ((pk["itheta"].astype(np.int64) * b.n_phi + pk["iphi"]) * b.n_a + pk["ia"]) * b.n_b + pk["ib"]
     assert np.all(np.diff(lin) > 0)
+
+
+# ---------------------------------------------------------------------------
+# Launch shapes never change results
+# ---------------------------------------------------------------------------
+
+TUNINGS = [
+    dict(), dict(scan_kind=1), dict(scan_kind=2), dict(scan_kind=3),
+    dict(scan_kind=1, scan_slots=2, scan_stage_bytes=16384),
+    dict(scan_kind=1, scan_slots=8, scan_stage_bytes=24576),
+    dict(fill_rows=8, fill_threads=256), dict(fill_rows=64, fill_threads=1024, fill_hits_staged=4096),
+    dict(fill_rows=16, fill_blocks_per_sm=1, scan_blocks_per_sm=1, scan_kind=2),
+]
+
+
+@pytest.fixture(scope="module")
+def paper_ref():
+    ev = synth.paper_event(seed=11)
+    b = oracle.Binning(*synth.PAPER_BINNING)
+    M, _ = oracle.fill(b, oracle.Ranges(), ev.x, ev.y, ev.z)
+    pk, n = oracle.find_maxima(b, oracle.Ranges(), M, 10)
+    return ev, M, pk, n
+
+
+@pytest.mark.parametrize("tuning", TUNINGS, ids=[",".join(f"{k}={v}" for k, v in t.items()) or "auto"
+                                                 for t in TUNINGS])
+def test_tuning_sweep(ht, paper_ref, tuning):
+    ev, M_ref, pk_ref, n_ref = paper_ref
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    with ht.Context(b, r, threshold=10, max_hits=ev.n_hits) as ctx:
+        ctx.set_tuning(**tuning)
+        got = ctx.get_tuning()
+        for k, v in tuning.items():
+            if k in ("scan_kind", "fill_rows", "fill_threads", "scan_slots"):
+                assert got[k] == v, (k, got)
+        ctx.fill(ev.x, ev.y, ev.z)
+        pk, n = ctx.find_maxima(capacity=1 << 16)
+        assert np.array_equal(ctx.matrix(), M_ref)
+    assert n == n_ref
+    assert_peaks_equal(pk, pk_ref)
+
+
+def test_bad_tuning_rejected(ht):
+    with ht.Context(ht.Binning(*synth.TINY_BINNING), ht.Ranges(), threshold=8, max_hits=16) as ctx:
+        for bad in (dict(fill_threads=300), dict(fill_rows=12), dict(scan_kind=9)):
+            with pytest.raises(ht.HTError):
+                ctx.set_tuning(**bad)
+        ev = synth.tiny_event()
+        ctx.fill(ev.x, ev.y, ev.z)           # still usable with the previous shapes
+        assert ctx.find_maxima(capacity=64)[1] > 0
