@@ -238,7 +238,7 @@ __device__ __forceinline__ uint32_t select_hits(const Geom &g, const Work &w, fl
     return n;
 }
 
-__global__ void __launch_bounds__(512) k_fill_priv(Geom g, Work w, FillCfg c)
+__global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
 {
     extern __shared__ uint4 sm4[];
     __shared__ uint32_t s_n;
