@@ -266,7 +266,7 @@ def run_ours(args, rank, world):
     dom = max(((kname, ms) for kname, (n, ms) in prof.items() if n), key=lambda t: t[1])[0]
     hbm_peak, peak_src = measured_peaks()
     cells_bytes = b.n_cells * 4
-    algo = {"k_fill_priv": cells_bytes, "k_scan": cells_bytes, "k_clear": cells_bytes,
+    algo = {"k_fill_priv": cells_bytes, "k_fill_scan": cells_bytes, "k_scan": cells_bytes, "k_clear": cells_bytes,
             "k_fill_naive": None, "k_bin": None, "k_order": None}
     n_dom, ms_dom = prof[dom]
     avg_s = ms_dom / n_dom / 1e3

@@ -180,6 +180,11 @@ ht_status ht_profile_read(ht_ctx *ctx, ht_kernel_time *out, uint32_t cap, uint32
  *                      (register streaming), HT_SCAN_DIRECT (scalar)
  *   scan_stage_bytes   bulk-copy stage size; scan_slots: ring depth (2..8)
  *   scan_blocks_per_sm cap on resident scan CTAs per SM
+ *   fill_fused_scan    1: ht_fill also finds the peaks while each vote tile
+ *                      is still in shared memory (M_H is still written in
+ *                      full), so ht_find_maxima only orders them; 2: never;
+ *                      0: whenever the tile shapes allow (non-accumulating,
+ *                      non-naive fills)
  * ht_set_tuning waits for the device, re-derives the shapes and returns
  * HT_E_INVAL for an impossible value; ht_get_tuning reports the shapes in
  * effect (0 fields filled in). */
@@ -187,6 +192,7 @@ enum { HT_SCAN_AUTO = 0, HT_SCAN_BULK = 1, HT_SCAN_STREAM = 2, HT_SCAN_DIRECT = 
 typedef struct {
     uint32_t fill_rows, fill_threads, fill_hits_staged, fill_blocks_per_sm;
     uint32_t scan_kind, scan_stage_bytes, scan_slots, scan_blocks_per_sm;
+    uint32_t fill_fused_scan;
 } ht_tuning;
 
 ht_status ht_set_tuning(ht_ctx *ctx, const ht_tuning *tuning);

@@ -77,7 +77,9 @@ static ht_status read_status(ht_ctx *ctx, cudaStream_t st)
     if (!s)
         return HT_OK;
     // reset the status and every counter the kernels may have left behind
-    CK(cudaMemsetAsync(ctx->E.d_ctr, 0, (3 + ctx->E.max_events) * 4, st));
+    CK(cudaMemsetAsync(ctx->E.d_ctr, 0, hte::engine_ctr_words(ctx->E) * 4, st));
+    ctx->E.ctr_dirty = false;
+    ctx->E.fused_valid = false;
     CK(cudaStreamSynchronize(st));
     if (s & htk::ST_WAIT_TIMEOUT)
         return set_err(HT_E_TIMEOUT, "a bounded device-side wait gave up (scan pipeline)");
@@ -289,6 +291,7 @@ ht_status ht_set_tuning(ht_ctx *ctx, const ht_tuning *t)
     n.scan_stage_bytes = t->scan_stage_bytes;
     n.scan_slots = t->scan_slots;
     n.scan_blocks_per_sm = t->scan_blocks_per_sm;
+    n.fused = t->fill_fused_scan;
     std::string why;
     s = hte::engine_configure(ctx->E, &why);
     if (s != HT_OK) {
@@ -318,6 +321,7 @@ ht_status ht_get_tuning(ht_ctx *ctx, ht_tuning *t)
     t->scan_stage_bytes = E.scan.slot_words * 4;
     t->scan_slots = E.scan.S;
     t->scan_blocks_per_sm = E.num_sms ? E.scan_grid_max / (uint32_t)E.num_sms : 0;
+    t->fill_fused_scan = E.fused_ok ? 1u : 2u;
     return HT_OK;
 }
 

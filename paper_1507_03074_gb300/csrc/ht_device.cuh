@@ -43,6 +43,7 @@ struct Work {
     uint32_t *M;                // vote matrices
     uint64_t n_cells;           // per event
     uint32_t *status;
+    uint32_t *ctr;              // counter block; k_bin zeroes words [1, 4 + n_events)
 };
 
 constexpr uint32_t kDropped = 0xffffffffu;

@@ -12,11 +12,14 @@ static uint32_t round_up(uint32_t v, uint32_t m) { return (v + m - 1) / m * m; }
 
 static const size_t kSmemMax = 227 * 1024;     // per CTA on sm_100-class parts
 static const uint32_t kScanThreads = 256;
-static const uint32_t kPeakBuf = 1024;         // K: entries buffered per scan CTA
+static const uint32_t kPeakBuf = 1024;         // K: entries buffered per scan / fused CTA
 
-const char *const kKernelNames[K_NKINDS] = {"k_bin", "k_fill_priv", "k_clear",
+const char *const kKernelNames[K_NKINDS] = {"k_bin", "k_fill_priv", "k_fill_scan", "k_clear",
                                              "k_fill_naive", "k_scan", "k_order"};
 
+// ---------------------------------------------------------------------------
+// Profiling
+// ---------------------------------------------------------------------------
 static cudaEvent_t prof_event(Engine &E)
 {
     if (!E.prof.pool.empty()) {
@@ -88,18 +91,20 @@ struct ProfScope {
     }
 };
 
-uint32_t fill_launches(const Engine &E, uint32_t flags)
-{
-    if ((flags & HT_FILL_NAIVE) || !E.fill_priv_ok)
-        return (flags & HT_ACCUMULATE) ? 2u : 3u;   // prep, [clear], naive
-    return 2u;                                      // prep, privatised fill
-}
-
 template <class T>
 static cudaError_t dalloc(T **p, size_t bytes, size_t *acc)
 {
     *acc += bytes;
     return cudaMalloc(reinterpret_cast<void **>(p), bytes ? bytes : 16);
+}
+
+// Chunk descriptors a CTA owning `rows` rows may need: no two peaks are
+// neighbours, so a row holds at most ceil(n_b / 2) peaks; every chunk but
+// the last holds at least K - per_round entries.
+static uint32_t chunks_for(uint64_t rows, uint32_t nb, uint32_t K, uint32_t per_round)
+{
+    const uint64_t peaks = rows * ((nb + 1) / 2);
+    return (uint32_t)std::min<uint64_t>(peaks / (K - per_round) + 2, 1u << 20);
 }
 
 ht_status engine_configure(Engine &E, std::string *why)
@@ -116,7 +121,11 @@ ht_status engine_configure(Engine &E, std::string *why)
         *why = "fill_threads must be 256, 512 or 1024";
         return HT_E_INVAL;
     }
-    f.HC = std::max(t.fill_HC ? t.fill_HC : 1024u, 2 * f.threads);   // select_hits needs HC >= 2 * threads
+    if (t.fused > 2) {
+        *why = "fused must be 0 (auto), 1 (on) or 2 (off)";
+        return HT_E_INVAL;
+    }
+    f.HC = std::max(t.fill_HC ? t.fill_HC : 2048u, 2 * f.threads);   // select_hits needs HC >= 2 * threads
     f.pitch16 = round_up((b.n_b + 1) / 2, 32);
     f.pitch32 = round_up(b.n_b, 32);
     uint32_t W = t.fill_W;
@@ -125,8 +134,8 @@ ht_status engine_configure(Engine &E, std::string *why)
         return HT_E_INVAL;
     }
     if (!W) {
-        // aim at ~64 KB tiles so that several CTAs share an SM
-        W = 64;
+        // aim at ~64 KB tiles so that two CTAs share an SM
+        W = 32;
         while (W > 2 && (size_t)W * f.pitch16 * 4 > 64 * 1024)
             W >>= 1;
     }
@@ -152,6 +161,35 @@ ht_status engine_configure(Engine &E, std::string *why)
     }
     E.clear_grid = (uint32_t)E.num_sms * 4;
     E.naive_grid = (uint32_t)E.num_sms * 16;
+
+    // --- fused fill + maxima ---------------------------------------------------
+    E.fused_ok = false;
+    E.fused_K = kPeakBuf;
+    if (E.fill_priv_ok && t.fused != 2 && W <= 64 && b.n_b <= 4096 && f.threads / 2 + 1 < kPeakBuf) {
+        htk::ScanArgs tmp{};
+        tmp.K = kPeakBuf;
+        htk::FillCfg ff = f;
+        // smaller staging so that two CTAs share an SM, unless tuned explicitly
+        while (!t.fill_HC && ff.HC > 2 * ff.threads && 2 * htk::fill_scan_smem_bytes(ff, tmp, b.n_b) > kSmemMax)
+            ff.HC /= 2;
+        E.fused_fill = ff;
+        if (htk::fill_scan_smem_bytes(ff, tmp, b.n_b) <= kSmemMax) {
+            int occ = 0;
+            cudaError_t e = htk::fill_scan_occupancy(ff, tmp, b.n_b, &occ);
+            if (e == cudaSuccess && occ >= 1) {
+                if (t.fill_blocks_per_sm)
+                    occ = std::min<int>(occ, (int)t.fill_blocks_per_sm);
+                E.fused_ok = true;
+                E.fused_grid = (uint32_t)E.num_sms * (uint32_t)occ;
+            } else {
+                cudaGetLastError();
+            }
+        }
+    }
+    if (t.fused == 1 && !E.fused_ok) {
+        *why = "the fused fill does not fit this binning and tuning";
+        return HT_E_INVAL;
+    }
 
     // --- scan variant and shape --------------------------------------------
     htk::ScanArgs &s = E.scan;
@@ -185,6 +223,11 @@ ht_status engine_configure(Engine &E, std::string *why)
         s.R = kind == htk::SCAN_LDG ? std::max<uint32_t>(1, htk::kLdgUPT * kScanThreads / (b.n_b / 4)) : 16;
     }
     E.scan_kind = kind;
+    const uint64_t G_max = (uint64_t)g.n_slices * g.na * E.max_events;
+    {   // bitmap words for the streaming scan at one CTA per SM (the longest run)
+        const uint64_t rows1 = (G_max + E.num_sms - 1) / E.num_sms + 1;
+        s.hot_words = kind == htk::SCAN_LDG ? (uint32_t)((rows1 + s.R - 1) / s.R / 32 + 2) : 0;
+    }
     int occ = 0;
     cudaError_t e = htk::scan_occupancy(kind, htk::scan_smem_bytes(s), &occ);
     if (e != cudaSuccess || occ < 1) {
@@ -197,36 +240,52 @@ ht_status engine_configure(Engine &E, std::string *why)
     E.scan_grid_max = (uint32_t)E.num_sms * (uint32_t)occ;
 
     // --- chunk bookkeeping for the largest launch (max_events events) ---------
-    const uint64_t G_max = (uint64_t)g.n_slices * g.na * E.max_events;
-    const uint64_t grid_max = std::max<uint64_t>(1, std::min<uint64_t>(E.scan_grid_max, G_max));
-    const uint64_t rows_per_cta = (G_max + grid_max - 1) / grid_max + 1;
-    const uint64_t per_round_max = 2ull * kScanThreads;   // <= 2 peaks per 4 consecutive cells
-    const uint64_t peaks_run = rows_per_cta * ((g.nb + 1) / 2);
-    s.seq_max = (uint32_t)std::min<uint64_t>(peaks_run / (s.K - per_round_max) + 2, 1u << 20);
-    const size_t desc_bytes = (size_t)grid_max * s.seq_max * 8, cta_bytes = (size_t)grid_max * 8;
-    if (desc_bytes > E.desc_bytes || cta_bytes > E.cta_bytes) {
+    const uint32_t scan_grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.scan_grid_max, G_max));
+    const uint64_t items_max = (uint64_t)E.max_events * g.n_slices * f.strips;
+    const uint32_t fused_grid = E.fused_ok ? (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.fused_grid, items_max)) : 0;
+    const uint32_t grid_cap = std::max(scan_grid, fused_grid);
+    uint32_t seq = chunks_for((G_max + scan_grid - 1) / scan_grid + 1, g.nb, s.K, 2 * kScanThreads);
+    if (E.fused_ok) {
+        const uint64_t fused_rows = ((items_max + fused_grid - 1) / fused_grid) * f.W + 1;
+        seq = std::max(seq, chunks_for(fused_rows, g.nb, kPeakBuf, f.threads / 2 + 1));
+    }
+    s.seq_max = seq;
+    const size_t desc_b = (size_t)grid_cap * seq * 8, bnd_b = (size_t)grid_cap * htk::kSeamChunks * 8;
+    const size_t cta_b = (size_t)grid_cap * 3 * 4, done_b = (size_t)grid_cap * 4;
+    const size_t need = desc_b + bnd_b + cta_b + done_b;
+    if (need > E.book_bytes || grid_cap != E.grid_cap) {
         if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
             *why = std::string("synchronise before re-allocation: ") + cudaGetErrorString(e);
             return HT_E_CUDA;
         }
-        cudaFree(E.d_desc);
-        cudaFree(E.d_cta);
-        E.d_desc = nullptr;
-        E.d_cta = nullptr;
-        E.desc_bytes = E.cta_bytes = 0;
-        if ((e = cudaMalloc(&E.d_desc, desc_bytes)) != cudaSuccess ||
-            (e = cudaMalloc(&E.d_cta, cta_bytes)) != cudaSuccess) {
-            cudaGetLastError();
-            *why = std::string("scan bookkeeping allocation failed: ") + cudaGetErrorString(e);
-            return HT_E_NOMEM;
+        if (need > E.book_bytes) {
+            cudaFree(E.d_book);
+            E.d_book = nullptr;
+            E.book_bytes = 0;
+            if ((e = cudaMalloc(&E.d_book, need)) != cudaSuccess) {
+                cudaGetLastError();
+                *why = std::string("scan bookkeeping allocation failed: ") + cudaGetErrorString(e);
+                return HT_E_NOMEM;
+            }
+            E.book_bytes = need;
         }
-        E.desc_bytes = desc_bytes;
-        E.cta_bytes = cta_bytes;
+        if ((e = cudaMemset(E.d_book, 0, need)) != cudaSuccess) {
+            *why = std::string("scan bookkeeping initialisation failed: ") + cudaGetErrorString(e);
+            return HT_E_CUDA;
+        }
+        E.epoch = 0;   // done flags are zero again
+        E.grid_cap = grid_cap;
     }
-    s.desc = E.d_desc;
-    s.cta_nseq = E.d_cta;
-    s.cta_total = E.d_cta + grid_max;
-    s.grid = (uint32_t)grid_max;
+    char *p = static_cast<char *>(E.d_book);
+    s.desc = reinterpret_cast<uint2 *>(p);
+    s.desc_bnd = reinterpret_cast<uint2 *>(p + desc_b);
+    uint32_t *cta = reinterpret_cast<uint32_t *>(p + desc_b + bnd_b);
+    s.cta_nseq = cta;
+    s.cta_total = cta + grid_cap;
+    s.cta_nbnd = cta + 2 * grid_cap;
+    s.done = reinterpret_cast<uint32_t *>(p + desc_b + bnd_b + cta_b);
+    s.grid = scan_grid;
+    E.fused_valid = false;
     return HT_OK;
 }
 
@@ -298,14 +357,14 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
     // A peak holds >= threshold votes and no two peaks are neighbours, so
     // peaks <= min(votes / T, ceil(n_a/2) ceil(n_b/2) per slice).
     htk::ScanArgs &s = E.scan;
-    const uint64_t per_round_max = 2ull * kScanThreads;
+    const uint64_t slack = 2ull * 1024;
     const uint64_t by_votes = (uint64_t)std::max<uint32_t>(max_hits, 1) * E.max_admit * g.na / threshold + 1;
     const uint64_t by_space = (uint64_t)g.n_slices * ((g.na + 1) / 2) * ((g.nb + 1) / 2) * max_events;
-    s.entries_cap = (uint32_t)std::min<uint64_t>(std::min(by_votes, by_space) + per_round_max, 0xffffffffull);
+    s.entries_cap = (uint32_t)std::min<uint64_t>(std::min(by_votes, by_space) + slack, 0xffffffffull);
 
     size_t acc = 0;
     const size_t hits_cap = (size_t)std::max<uint32_t>(max_hits, 1);
-    const uint32_t ctr_words = 3 + max_events;
+    const uint32_t ctr_words = engine_ctr_words(E);
     if ((e = dalloc(&E.d_edges, (E.et.size() + E.ep.size()) * 4, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_M, (size_t)E.n_cells * 4 * max_events + 256, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_hits4, hits_cap * 16, &acc)) != cudaSuccess ||
@@ -319,7 +378,7 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
         engine_destroy(E);
         return HT_E_NOMEM;
     }
-    E.device_bytes = acc + E.desc_bytes + E.cta_bytes;
+    E.device_bytes = acc + E.book_bytes;
     g.et = E.d_edges;
     g.ep = E.d_edges + E.et.size();
     if ((e = cudaMemcpy(E.d_edges, E.et.data(), E.et.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -333,8 +392,9 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
         return HT_E_CUDA;
     }
     s.entries = E.d_entries;
-    s.g_count = E.d_ctr;
-    s.ev_count = E.d_ctr + 3;
+    s.g_count = E.d_ctr + htk::CTR_ENTRIES;
+    s.ev_count = E.d_ctr + htk::CTR_EVENTS;
+    s.fticket = E.d_ctr + htk::CTR_FTICKET;
     return HT_OK;
 }
 
@@ -342,7 +402,8 @@ ht_status engine_ensure_any_matrix(Engine &E, std::string *why)
 {
     const htk::Geom &g = E.geom;
     const uint64_t by_space = (uint64_t)g.n_slices * ((g.na + 1) / 2) * ((g.nb + 1) / 2) * E.max_events +
-                              4ull * kScanThreads;
+                              2ull * 1024;
+    E.fused_valid = false;
     if (by_space <= E.scan.entries_cap)
         return HT_OK;
     if (by_space > 0xffffffffull) {
@@ -377,17 +438,16 @@ void engine_destroy(Engine &E)
     cudaFree(E.d_hits4);
     cudaFree(E.d_codes);
     cudaFree(E.d_entries);
-    cudaFree(E.d_desc);
-    cudaFree(E.d_cta);
+    cudaFree(E.d_book);
     cudaFree(E.d_ctr);
     E.d_edges = nullptr;
     E.d_M = nullptr;
     E.d_hits4 = nullptr;
     E.d_codes = nullptr;
     E.d_entries = nullptr;
-    E.d_desc = nullptr;
-    E.d_cta = nullptr;
+    E.d_book = nullptr;
     E.d_ctr = nullptr;
+    E.book_bytes = 0;
 }
 
 static htk::Work make_work(Engine &E, const float *x, const float *y, const float *z,
@@ -405,6 +465,7 @@ static htk::Work make_work(Engine &E, const float *x, const float *y, const floa
     w.M = E.d_M;
     w.n_cells = E.n_cells;
     w.status = engine_status(E);
+    w.ctr = E.d_ctr;
     return w;
 }
 
@@ -414,6 +475,7 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
 {
     htk::Work w = make_work(E, x, y, z, d_hit_off, n_hits0, n_events);
     cudaError_t e;
+    E.fused_valid = false;
     {
         ProfScope ps(E, K_BIN, st);
         const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((n_total + 255) / 256, E.num_sms * 8));
@@ -422,6 +484,7 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
     if (e != cudaSuccess)
         return e;
     ++E.launches;
+    E.ctr_dirty = false;   // k_bin zeroed the counters
     const bool accumulate = (flags & HT_ACCUMULATE) != 0;
     if ((flags & HT_FILL_NAIVE) || !E.fill_priv_ok) {
         if (!accumulate) {
@@ -438,6 +501,26 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
     htk::FillCfg f = E.fill;
     f.accumulate = accumulate ? 1u : 0u;
     const uint64_t items = (uint64_t)n_events * E.geom.n_slices * f.strips;
+    if (E.fused_ok && !accumulate) {
+        htk::ScanArgs a = E.scan;
+        a.K = E.fused_K;
+        a.epoch = ++E.epoch;
+        htk::FillCfg ff = E.fused_fill;
+        ff.accumulate = 0u;
+        const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.fused_grid, items));
+        {
+            ProfScope ps(E, K_FILL_SCAN, st);
+            e = htk::launch_fill_scan(E.geom, w, ff, a, grid, st);
+        }
+        ++E.launches;
+        if (e == cudaSuccess) {
+            E.fused_valid = true;
+            E.ctr_dirty = true;
+            E.fused_grid_used = grid;
+            E.fused_events = n_events;
+        }
+        return e;
+    }
     const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.fill_grid, items));
     ProfScope ps(E, K_FILL_PRIV, st);
     e = htk::launch_fill_priv(E.geom, w, f, grid, st);
@@ -450,27 +533,43 @@ cudaError_t engine_scan(Engine &E, uint32_t n_events, htk::Peak *out, uint32_t c
 {
     htk::Work w = make_work(E, nullptr, nullptr, nullptr, nullptr, 0, n_events);
     htk::ScanArgs a = E.scan;
-    const uint64_t G = (uint64_t)E.geom.n_slices * E.geom.na * n_events;
-    a.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(a.grid, G));
     htk::OrderArgs o{};
     o.out = out;
     o.capacity = capacity;
     o.counts = counts;
-    o.ev_count = E.d_ctr + 3;
-    o.ticket = E.d_ctr + 1;
+    o.ev_count = E.d_ctr + htk::CTR_EVENTS;
+    o.ticket = E.d_ctr + htk::CTR_OTICKET;
+    o.g_count = E.d_ctr + htk::CTR_ENTRIES;
     cudaError_t e;
-    {
-        ProfScope ps(E, K_SCAN, st);
-        e = htk::launch_scan(E.geom, w, a, E.scan_kind, st);
+    if (E.fused_valid && E.fused_events == n_events) {
+        // the fused fill already found the peaks: only order them
+        a.grid = E.fused_grid_used;
+        E.fused_valid = false;
+    } else {
+        if (E.ctr_dirty) {
+            // an unconsumed fused fill left its counters: start from zero
+            e = cudaMemsetAsync(E.d_ctr + htk::CTR_ENTRIES, 0,
+                                (engine_ctr_words(E) - htk::CTR_ENTRIES) * sizeof(uint32_t), st);
+            if (e != cudaSuccess)
+                return e;
+        }
+        E.fused_valid = false;
+        const uint64_t G = (uint64_t)E.geom.n_slices * E.geom.na * n_events;
+        a.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(a.grid, G));
+        {
+            ProfScope ps(E, K_SCAN, st);
+            e = htk::launch_scan(E.geom, w, a, E.scan_kind, st);
+        }
+        if (e != cudaSuccess)
+            return e;
+        ++E.launches;
     }
-    if (e != cudaSuccess)
-        return e;
-    ++E.launches;
     {
         ProfScope ps(E, K_ORDER, st);
         e = htk::launch_order(E.geom, w, a, o, st);
     }
     ++E.launches;
+    E.ctr_dirty = false;   // the order kernel's last CTA zeroes them
     return e;
 }
 

@@ -23,11 +23,12 @@ struct Tuning {
     uint32_t scan_stage_bytes = 0;    // bulk-copy stage size
     uint32_t scan_slots = 0;          // bulk-copy ring depth (2..8)
     uint32_t scan_blocks_per_sm = 0;  // cap below the occupancy limit
+    uint32_t fused = 0;               // 0 auto (on when possible), 1 on, 2 off
 };
 
 // Optional per-kernel timing with CUDA events recorded on the launching
 // stream around every launch (enabled by ht_profile).
-enum KernelKind { K_BIN, K_FILL_PRIV, K_CLEAR, K_FILL_NAIVE, K_SCAN, K_ORDER, K_NKINDS };
+enum KernelKind { K_BIN, K_FILL_PRIV, K_FILL_SCAN, K_CLEAR, K_FILL_NAIVE, K_SCAN, K_ORDER, K_NKINDS };
 extern const char *const kKernelNames[K_NKINDS];
 
 struct Prof {
@@ -55,22 +56,32 @@ struct Engine {
     htk::FillCfg fill{};
     bool fill_priv_ok = false;   // the tile fits in shared memory
     uint32_t fill_grid = 0;
+    bool fused_ok = false;       // the fused fill + maxima kernel fits
+    htk::FillCfg fused_fill{};   // its tile / staging shape
+    uint32_t fused_grid = 0;
+    uint32_t fused_K = 0;
     htk::ScanArgs scan{};
     int scan_kind = 0;            // htk::ScanKind in use
     uint32_t scan_grid_max = 0;
-    size_t desc_bytes = 0;        // allocated scan bookkeeping
-    size_t cta_bytes = 0;
+    uint32_t grid_cap = 0;        // CTAs the bookkeeping arrays are sized for
+    size_t book_bytes = 0;        // allocated bookkeeping
     uint32_t clear_grid = 0, naive_grid = 0;
     Tuning tune;
+
+    // state of the last fill: peaks already found by the fused kernel
+    bool fused_valid = false;
+    uint32_t fused_grid_used = 0;
+    uint32_t fused_events = 0;
+    uint32_t epoch = 0;
+    bool ctr_dirty = false;      // counters hold an unconsumed fused fill's peaks
 
     float *d_edges = nullptr;
     uint32_t *d_M = nullptr;
     float4 *d_hits4 = nullptr;
     uint32_t *d_codes = nullptr;
     uint4 *d_entries = nullptr;
-    uint2 *d_desc = nullptr;
-    uint32_t *d_cta = nullptr;   // [2][grid]: nseq, total
-    uint32_t *d_ctr = nullptr;   // [0] g_count, [1] ticket, [2] status, [3..) ev_count
+    void *d_book = nullptr;       // desc | desc_bnd | cta arrays | done flags
+    uint32_t *d_ctr = nullptr;    // counter block (htk::CTR_*)
     size_t device_bytes = 0;
     uint64_t launches = 0;
     Prof prof;
@@ -91,7 +102,9 @@ ht_status engine_configure(Engine &E, std::string *why);
 
 // Step 1 for n_events events whose hits (device pointers) are concatenated;
 // d_hit_off (device, n_events + 1) or nullptr for one event of n_hits0 hits.
-// n_total (host) is the total hit count; it sizes the binning grid.
+// n_total (host) is the total hit count; it sizes the binning grid.  Unless
+// HT_ACCUMULATE or HT_FILL_NAIVE is set (or the tuning turns it off), the
+// fused kernel also finds the peaks, which engine_scan then only orders.
 cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *z,
                         const uint32_t *d_hit_off, uint32_t n_hits0, uint32_t n_events,
                         uint32_t n_total, uint32_t flags, cudaStream_t st);
@@ -106,10 +119,9 @@ cudaError_t engine_scan(Engine &E, uint32_t n_events, htk::Peak *out, uint32_t c
 ht_status engine_ensure_any_matrix(Engine &E, std::string *why);
 
 // Device status word (bits of htk::ST_*).
-inline uint32_t *engine_status(Engine &E) { return E.d_ctr + 2; }
+inline uint32_t *engine_status(Engine &E) { return E.d_ctr + htk::CTR_STATUS; }
 
-// Kernel launches engine_fill / engine_scan enqueue for the given flags.
-uint32_t fill_launches(const Engine &E, uint32_t flags);
-inline uint32_t scan_launches() { return 2; }
+// Counter words of the block (status + counters + per-event counts).
+inline uint32_t engine_ctr_words(const Engine &E) { return htk::CTR_EVENTS + E.max_events; }
 
 } // namespace hte

@@ -30,13 +30,19 @@ struct ScanArgs {
     uint32_t S;           // stages in the shared-memory ring (<= 8)
     uint32_t K;           // peak entries buffered in shared memory (>= 2*256)
     uint32_t slot_words;  // (R + 2) * n_b
+    uint32_t hot_words;   // streaming: words of the per-CTA hot-chunk bitmap
     uint32_t seq_max;     // chunk descriptors per CTA
     uint32_t entries_cap; // global entry scratch capacity
     uint4 *entries;       // {lin within event, event, votes, 0}
     uint32_t *g_count;    // entries used (reset by k_order)
     uint2 *desc;          // [grid][seq_max] {base, n}
-    uint32_t *cta_nseq;   // [grid]
-    uint32_t *cta_total;  // [grid]
+    uint32_t *cta_nseq;   // [grid] interior chunks
+    uint32_t *cta_total;  // [grid] entries (seam + interior)
+    uint32_t *cta_nbnd;   // [grid] seam chunks (fused fill only; 0 otherwise)
+    uint2 *desc_bnd;      // [grid][kSeamChunks] seam chunks {base, n}
+    uint32_t *done;       // [grid] epoch once the CTA's rows are in M_H (fused fill)
+    uint32_t *fticket;    // logical CTA index counter of the fused fill
+    uint32_t epoch;       // launch number of the fused fill
     uint32_t *ev_count;   // [n_events] peaks per event (reset by k_order)
 };
 
@@ -46,15 +52,28 @@ struct OrderArgs {
     uint32_t *counts;     // [n_events] total peaks per event
     uint32_t *ev_count;
     uint32_t *ticket;     // last-CTA detection (reset by k_order)
+    uint32_t *g_count;    // entries used (reset by the last CTA)
 };
 
 cudaError_t launch_bin(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
 size_t fill_smem_bytes(const FillCfg &c);
 cudaError_t launch_fill_priv(const Geom &g, const Work &w, const FillCfg &c, uint32_t grid,
                              cudaStream_t st);
+size_t fill_scan_smem_bytes(const FillCfg &c, const ScanArgs &a, uint32_t nb);
+cudaError_t launch_fill_scan(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
+                             cudaStream_t st);
+cudaError_t fill_scan_occupancy(const FillCfg &c, const ScanArgs &a, uint32_t nb, int *blocks_per_sm);
 cudaError_t launch_clear(uint32_t *M, uint64_t words, uint32_t grid, cudaStream_t st);
 cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
 size_t scan_smem_bytes(const ScanArgs &a);
+// Chunks a fused-fill CTA may need for its seam rows (n_b <= 4096).
+constexpr uint32_t kSeamChunks = 8;
+
+// Layout of the counter block: [0] status, [1] entries used, [2] order
+// ticket, [3] fused-fill ticket, [4 ..) peaks per event.  k_bin zeroes
+// words [1, 4 + n_events) before every fill.
+enum : uint32_t { CTR_STATUS = 0, CTR_ENTRIES = 1, CTR_OTICKET = 2, CTR_FTICKET = 3, CTR_EVENTS = 4 };
+
 // Scan variants: bulk-copy (TMA) ring, register streaming, direct (any n_b).
 // The streaming variant keeps kLdgUPT 16-byte loads per thread in flight.
 constexpr uint32_t kLdgUPT = 4;

@@ -91,6 +91,9 @@ __global__ void __launch_bounds__(256) k_bin(Geom g, Work w)
         et[i] = g.et[i];
     for (uint32_t i = threadIdx.x; i <= g.np; i += blockDim.x)
         ep[i] = g.ep[i];
+    if (blockIdx.x == 0 && w.ctr)   // fresh counters for the fill and scan that follow
+        for (uint32_t i = CTR_ENTRIES + threadIdx.x; i < CTR_EVENTS + w.n_events; i += blockDim.x)
+            w.ctr[i] = 0u;
     __syncthreads();
     const uint32_t n = w.hit_off ? w.hit_off[w.n_events] : w.n_hits0;
     for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
@@ -377,17 +380,30 @@ struct ScanSmem {
     uint32_t pad;
 };
 
-// Flush the CTA's buffered peaks as one chunk.
+// Where a CTA registers its chunks: the interior list (a.desc row of the
+// CTA, seq_max entries) or the seam list (a.desc_bnd row, kSeamChunks).
+struct ChunkList {
+    uint2 *desc;
+    uint32_t cap;
+};
+
+__device__ __forceinline__ ChunkList interior_list(const ScanArgs &a, uint32_t cta)
+{
+    return ChunkList{a.desc + (size_t)cta * a.seq_max, a.seq_max};
+}
+
+// Flush the CTA's buffered peaks as one chunk of list L.
 __device__ __forceinline__ void flush_chunk(const ScanArgs &a, ScanSmem &ss, const uint4 *pbuf,
-                                            uint32_t &buf_n, uint32_t &nseq, uint32_t *status)
+                                            uint32_t &buf_n, uint32_t &nseq, const ChunkList &L,
+                                            uint32_t *status)
 {
     if (buf_n == 0)
         return;
     if (threadIdx.x == 0) {
         ss.chunk_base = atomicAdd(a.g_count, buf_n);
-        if (nseq < a.seq_max)
-            a.desc[(size_t)blockIdx.x * a.seq_max + nseq] = make_uint2(ss.chunk_base, buf_n);
-        if (nseq >= a.seq_max || ss.chunk_base + buf_n > a.entries_cap)
+        if (nseq < L.cap)
+            L.desc[nseq] = make_uint2(ss.chunk_base, buf_n);
+        if (nseq >= L.cap || ss.chunk_base + buf_n > a.entries_cap)
             atomicOr(status, (uint32_t)ST_SCRATCH_OVERFLOW);
     }
     __syncthreads();
@@ -467,7 +483,7 @@ __device__ void scan_rows_slow(const Geom &g, const Work &w, const ScanArgs &a, 
             if (__syncthreads_or(cnt)) {
                 // at most 2 peaks among 4 consecutive cells (no two peaks are neighbours)
                 if (buf_n + (VEC > 1 ? 2u : 1u) * bd > a.K)
-                    flush_chunk(a, ss, pbuf, buf_n, nseq, w.status);
+                    flush_chunk(a, ss, pbuf, buf_n, nseq, interior_list(a, blockIdx.x), w.status);
                 compact_round(ss, pbuf, buf_n, cnt, pj, pv, row_lin0, ev, a.ev_count);
                 total += ss.round_total;
             }
@@ -553,10 +569,11 @@ __global__ void __launch_bounds__(256) k_scan_tma(Geom g, Work w, ScanArgs a)
         }
         __syncthreads();
     }
-    flush_chunk(a, ss, pbuf, buf_n, nseq, w.status);
+    flush_chunk(a, ss, pbuf, buf_n, nseq, interior_list(a, blockIdx.x), w.status);
     if (tid == 0) {
         a.cta_nseq[blockIdx.x] = min(nseq, a.seq_max);
         a.cta_total[blockIdx.x] = total;
+        a.cta_nbnd[blockIdx.x] = 0u;
     }
 }
 
@@ -582,10 +599,355 @@ __global__ void __launch_bounds__(256) k_scan_direct(Geom g, Work w, ScanArgs a)
         if (__syncthreads_or(hot))
             scan_rows_slow<1>(g, w, a, ss, pbuf, buf_n, nseq, total, ra, rb, w.M, 0);
     }
-    flush_chunk(a, ss, pbuf, buf_n, nseq, w.status);
+    flush_chunk(a, ss, pbuf, buf_n, nseq, interior_list(a, blockIdx.x), w.status);
     if (tid == 0) {
         a.cta_nseq[blockIdx.x] = min(nseq, a.seq_max);
         a.cta_total[blockIdx.x] = total;
+        a.cta_nbnd[blockIdx.x] = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_fill_scan: Step 1 and Step 2 in one pass over shared-memory tiles.
+//
+// Like k_fill_priv, a CTA owns a contiguous range of (event, slice, strip)
+// items, votes each strip pass into a shared-memory tile and writes it to
+// M_H (which stays complete in HBM).  Before the tile is cleared, the rows of
+// the pass are tested for peaks from shared memory:
+//   - a row whose 8-neighbourhood lies in the tile (or outside the slice) is
+//     tested at once; the pass's last row waits for the next pass of the
+//     same slice, bridged by two carried rows (u32 copies of the last rows);
+//   - the first row of the CTA's range, when it is not a slice's first row,
+//     and the previous CTA's last row form the seam between two CTAs.  This
+//     CTA tests both at its end, reading them back from L2 after the
+//     previous CTA has published (bounded wait on its done flag).
+// Logical CTA indices come from an atomic ticket, so a CTA only ever waits on
+// one that started before it.  Peaks go, in linear order, into per-CTA
+// chunks: a seam chunk (desc_bnd) followed by the interior chunks.
+// ---------------------------------------------------------------------------
+
+// A row of cells in one of the places the fused kernel keeps them.
+struct RowRef {
+    const uint32_t *p;   // row start (u32 array) or tile row base (words)
+    uint32_t kind;       // 0 absent, 1 u32 shared, 2 u16 tile, 3 u32 tile, 4 u32 global
+    uint32_t sw;         // tile swizzle of the row
+    __device__ __forceinline__ uint32_t get(uint32_t j) const
+    {
+        switch (kind) {
+        case 1:
+            return p[j];
+        case 2: {
+            const uint32_t wv = p[(j >> 1) ^ sw];
+            return (wv >> ((j & 1u) << 4)) & 0xffffu;
+        }
+        case 3:
+            return p[j ^ sw];
+        default:
+            return __ldcg(p + j);
+        }
+    }
+};
+
+__device__ __forceinline__ bool is_peak_ref(const RowRef &row, const RowRef &up, const RowRef &dn, uint32_t j,
+                                            uint32_t nb, uint32_t v)
+{
+    const bool hl = j > 0, hr = j + 1 < nb;
+    if (up.kind) {
+        if (hl && !(v > up.get(j - 1))) return false;
+        if (!(v > up.get(j))) return false;
+        if (hr && !(v > up.get(j + 1))) return false;
+    }
+    if (hl && !(v > row.get(j - 1))) return false;
+    if (hr && !(v >= row.get(j + 1))) return false;
+    if (dn.kind) {
+        if (hl && !(v >= dn.get(j - 1))) return false;
+        if (!(v >= dn.get(j))) return false;
+        if (hr && !(v >= dn.get(j + 1))) return false;
+    }
+    return true;
+}
+
+// Test one row (cells >= T against their neighbours) and append its peaks
+// in column order.  All threads of the block call it.
+__device__ void test_row_ref(const Geom &g, const ScanArgs &a, ScanSmem &ss, uint4 *pbuf, uint32_t &buf_n,
+                             uint32_t &nseq, uint32_t &total, const ChunkList &L, uint32_t *status,
+                             const RowRef &up, const RowRef &row, const RowRef &dn, uint32_t row_lin0, uint32_t ev)
+{
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb, T = g.threshold;
+    const uint32_t rounds = (nb + bd - 1) / bd;
+    const uint32_t per_round = bd / 2 + 1;    // no two peaks are neighbours
+    for (uint32_t rd = 0; rd < rounds; ++rd) {
+        const uint32_t j = rd * bd + tid;
+        uint32_t cnt = 0, pj[1], pv[1];
+        if (j < nb) {
+            const uint32_t v = row.get(j);
+            if (v >= T && is_peak_ref(row, up, dn, j, nb, v)) {
+                pj[0] = j;
+                pv[0] = v;
+                cnt = 1;
+            }
+        }
+        if (__syncthreads_or(cnt)) {
+            if (buf_n + per_round > a.K)
+                flush_chunk(a, ss, pbuf, buf_n, nseq, L, status);
+            compact_round(ss, pbuf, buf_n, cnt, pj, pv, row_lin0, ev, a.ev_count);
+            total += ss.round_total;
+        }
+    }
+}
+
+// Flush the tile rows of one pass to M_H without clearing them; mark rows
+// holding a cell >= T in hot[] (bit r of word r / 32).
+template <bool U16>
+__device__ __forceinline__ void flush_rows_mark(const Geom &g, const uint32_t *tile, uint32_t *dst,
+                                                uint32_t rows, uint32_t pitch, uint32_t *hot)
+{
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, T = g.threshold;
+    if ((g.nb & 3u) == 0) {
+        const uint32_t q = g.nb >> 2;
+        const uint32_t units = rows * q;
+        for (uint32_t u = tid; u < units; u += bd) {
+            const uint32_t r = u / q, c4 = u - r * q;
+            uint4 v;
+            if (U16) {
+                const uint2 pr = *reinterpret_cast<const uint2 *>(
+                    &tile[r * pitch + ((2u * c4) ^ (row_hash(r) & 0x1Eu))]);
+                v = make_uint4(pr.x & 0xffffu, pr.x >> 16, pr.y & 0xffffu, pr.y >> 16);
+            } else {
+                v = *reinterpret_cast<const uint4 *>(&tile[r * pitch + ((4u * c4) ^ (row_hash(r) & 0x1Cu))]);
+            }
+            reinterpret_cast<uint4 *>(dst)[u] = v;
+            if (max(max(v.x, v.y), max(v.z, v.w)) >= T)
+                atomicOr(&hot[r >> 5], 1u << (r & 31u));
+        }
+    } else {
+        const uint32_t units = rows * g.nb;
+        for (uint32_t u = tid; u < units; u += bd) {
+            const uint32_t r = u / g.nb, j = u - r * g.nb;
+            uint32_t v;
+            if (U16)
+                v = (tile[r * pitch + ((j >> 1) ^ (row_hash(r) & 0x1Eu))] >> ((j & 1u) << 4)) & 0xffffu;
+            else
+                v = tile[r * pitch + (j ^ (row_hash(r) & 0x1Cu))];
+            dst[u] = v;
+            if (v >= T)
+                atomicOr(&hot[r >> 5], 1u << (r & 31u));
+        }
+    }
+}
+
+__device__ __forceinline__ RowRef tile_row(const uint32_t *tile, uint32_t r, uint32_t pitch, bool u16)
+{
+    RowRef x;
+    x.p = tile + r * pitch;
+    x.kind = u16 ? 2u : 3u;
+    x.sw = u16 ? (row_hash(r) & 0x1Eu) : (row_hash(r) & 0x1Cu);
+    return x;
+}
+
+__global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, ScanArgs a)
+{
+    extern __shared__ uint4 sm4[];
+    // layout: ScanSmem (256 B) | K peak entries | tile | HC staged hits | 2 carried rows
+    ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
+    uint4 *pbuf = sm4 + 16;
+    uint32_t *tile = reinterpret_cast<uint32_t *>(pbuf + a.K);
+    float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
+    uint32_t *carry = reinterpret_cast<uint32_t *>(hs + c.HC);   // [2][nb]
+    __shared__ uint32_t s_n, s_cta, s_hot[2], s_ok;
+
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb;
+    for (uint32_t k = tid; k < c.tile_words / 4; k += bd)
+        sm4[16 + a.K + k] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0)
+        s_cta = atomicAdd(a.fticket, 1u);
+    __syncthreads();
+    const uint32_t cta = s_cta;
+    const ChunkList inner = interior_list(a, cta);
+
+    const uint64_t rows_ev = (uint64_t)g.n_slices * g.na;
+    const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
+    const uint64_t it0 = items * cta / gridDim.x, it1 = items * (cta + 1) / gridDim.x;
+    uint64_t cached_es = ~0ull;
+    uint32_t cached_n = 0;
+    uint32_t buf_n = 0, nseq = 0, total = 0;
+
+    // carry state: carry[1] holds global row gP, carry[0] row gP - 1
+    bool carry1 = false, carry0 = false, pend = false, pend_hot = false;
+    uint64_t gP = 0;
+    bool seam = false;          // the range starts inside a slice
+    uint64_t g_first = 0;       // first global row of the range
+
+    for (uint64_t item = it0; item < it1; ++item) {
+        const uint32_t k = (uint32_t)(item % c.strips);
+        const uint64_t es = item / c.strips;
+        const uint32_t s = (uint32_t)(es % g.n_slices);
+        const uint32_t e = (uint32_t)(es / g.n_slices);
+        const uint32_t ts = s / g.np, ps = s - ts * g.np;
+        const uint32_t h0 = ev_hit_begin(w, e), h1 = ev_hit_end(w, e);
+        const uint32_t i0 = k * c.W;
+        const uint32_t rows = min(c.W, g.na - i0);
+        const bool u16 = (h1 - h0) < 65536u;
+        const uint32_t rpass = u16 ? c.W : c.W / 2;
+        const uint32_t pitch = u16 ? c.pitch16 : c.pitch32;
+        uint32_t *Mrow = w.M + (size_t)e * w.n_cells + ((size_t)s * g.na + i0) * g.nb;
+        const uint32_t r = tid % rpass, hl = tid / rpass, hstride = bd / rpass;
+
+        for (uint32_t p0 = 0; p0 < rows; p0 += rpass) {
+            const uint32_t pr = min(rpass, rows - p0);
+            const uint32_t iA = i0 + p0;
+            const uint64_t gA = es * g.na + iA;
+            if (item == it0 && p0 == 0) {
+                g_first = gA;
+                seam = iA > 0;
+            }
+            if (carry1 && gP + 1 != gA)
+                carry1 = carry0 = false;          // a new slice starts
+            // ---- vote -------------------------------------------------------
+            const uint32_t i = iA + r;
+            if (cached_es == es) {
+                __syncthreads();
+                if (r < pr) {
+                    if (u16)
+                        vote_rows<true>(g, tile, hs, cached_n, r, i, hl, hstride, pitch);
+                    else
+                        vote_rows<false>(g, tile, hs, cached_n, r, i, hl, hstride, pitch);
+                }
+            } else {
+                cached_es = ~0ull;
+                uint32_t pos = h0;
+                bool first = true;
+                while (first || pos < h1) {
+                    const uint32_t nsel = select_hits(g, w, hs, c.HC, pos, h1, ts, ps, &s_n);
+                    if (first && pos >= h1) {
+                        cached_es = es;
+                        cached_n = nsel;
+                    }
+                    first = false;
+                    if (r < pr) {
+                        if (u16)
+                            vote_rows<true>(g, tile, hs, nsel, r, i, hl, hstride, pitch);
+                        else
+                            vote_rows<false>(g, tile, hs, nsel, r, i, hl, hstride, pitch);
+                    }
+                }
+            }
+            if (tid == 0)
+                s_hot[0] = s_hot[1] = 0u;
+            __syncthreads();
+            // ---- write the pass to M_H, mark rows holding a cell >= T -------
+            if (u16)
+                flush_rows_mark<true>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, s_hot);
+            else
+                flush_rows_mark<false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, s_hot);
+            __syncthreads();
+            const uint64_t hotm = (uint64_t)s_hot[0] | ((uint64_t)s_hot[1] << 32);
+            // ---- rows to test now, in order ----------------------------------
+            const bool test_pend = pend && carry1 && gP + 1 == gA;
+            const uint32_t r_first = (iA == 0 || carry1) ? 0u : 1u;   // else row 0 is the seam
+            const bool last_is_end = iA + pr - 1 == g.na - 1;
+            const int32_t r_last = last_is_end ? (int32_t)pr - 1 : (int32_t)pr - 2;
+            uint64_t want = 0;
+            for (int32_t rr = (int32_t)r_first; rr <= r_last; ++rr)
+                want |= 1ull << rr;
+            const uint32_t row_lin_base = (uint32_t)((uint64_t)s * g.na + iA) * nb;
+            if ((test_pend && pend_hot) || (hotm & want)) {
+                const RowRef none{nullptr, 0u, 0u};
+                if (test_pend && pend_hot) {
+                    RowRef up{carry, 1u, 0u}, row{carry + nb, 1u, 0u};
+                    if (!carry0 || (gP % g.na) == 0)
+                        up = none;
+                    test_row_ref(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, up, row,
+                                 tile_row(tile, 0, pitch, u16), row_lin_base - nb, e);
+                }
+                for (int32_t rr = (int32_t)r_first; rr <= r_last; ++rr) {
+                    if (!((hotm >> rr) & 1ull))
+                        continue;
+                    RowRef up = none, dn = none;
+                    if (iA + rr > 0)
+                        up = rr > 0 ? tile_row(tile, rr - 1, pitch, u16) : RowRef{carry + nb, 1u, 0u};
+                    if (iA + rr + 1 < g.na)
+                        dn = tile_row(tile, rr + 1, pitch, u16);
+                    test_row_ref(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, up,
+                                 tile_row(tile, rr, pitch, u16), dn, row_lin_base + (uint32_t)rr * nb, e);
+                }
+            }
+            // ---- carry the last two rows; clear the tile --------------------
+            __syncthreads();
+            if (pr >= 2) {
+                const RowRef ra_ = tile_row(tile, pr - 2, pitch, u16), rb_ = tile_row(tile, pr - 1, pitch, u16);
+                for (uint32_t j = tid; j < nb; j += bd) {
+                    carry[j] = ra_.get(j);
+                    carry[nb + j] = rb_.get(j);
+                }
+                carry0 = true;
+            } else {
+                const RowRef rb_ = tile_row(tile, 0, pitch, u16);
+                for (uint32_t j = tid; j < nb; j += bd) {
+                    carry[j] = carry[nb + j];
+                    carry[nb + j] = rb_.get(j);
+                }
+                carry0 = carry1;
+            }
+            carry1 = true;
+            gP = gA + pr - 1;
+            pend = !last_is_end;
+            pend_hot = (hotm >> (pr - 1)) & 1ull;
+            __syncthreads();
+            for (uint32_t q = tid; q < pr * pitch / 4; q += bd)
+                reinterpret_cast<uint4 *>(tile)[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    flush_chunk(a, ss, pbuf, buf_n, nseq, inner, w.status);
+    // ---- publish: every row of the range is in M_H ---------------------------
+    __threadfence();
+    __syncthreads();
+    if (tid == 0)
+        atomicExch(&a.done[cta], a.epoch);
+    // ---- the seam with the previous CTA --------------------------------------
+    uint32_t nbnd = 0;
+    const ChunkList seam_list{a.desc_bnd + (size_t)cta * kSeamChunks, kSeamChunks};
+    if (seam) {
+        if (tid == 0) {
+            uint32_t ok = 0;
+            const uint64_t t0 = global_ns();
+            for (uint32_t it = 0; it < kWaitIters; ++it) {
+                if (atomicAdd(&a.done[cta - 1], 0u) == a.epoch) {
+                    ok = 1;
+                    break;
+                }
+                if ((it & 255u) == 0 && global_ns() - t0 > kWaitNs)
+                    break;
+            }
+            if (!ok)
+                atomicOr(w.status, (uint32_t)ST_WAIT_TIMEOUT);
+            __threadfence();
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (s_ok) {
+            // rows gQ - 1 (previous CTA's last) and gQ (our first) of one slice
+            const uint64_t gQ = g_first;
+            const uint32_t ev = (uint32_t)(gQ / rows_ev);
+            const uint64_t gl = gQ - (uint64_t)ev * rows_ev;      // row within the event
+            const uint32_t iQ = (uint32_t)(gQ % g.na);
+            const uint32_t *base = w.M + gQ * nb;
+            const RowRef none{nullptr, 0u, 0u};
+            const RowRef rP{base - nb, 4u, 0u}, rQ{base, 4u, 0u};
+            const RowRef upP = iQ >= 2 ? RowRef{base - 2 * nb, 4u, 0u} : none;
+            const RowRef dnQ = iQ + 1 < g.na ? RowRef{base + nb, 4u, 0u} : none;
+            const uint32_t lin_Q = (uint32_t)(gl * nb);
+            // two rows hold at most n_b peaks: with K >= n_b the seam list
+            // needs at most kSeamChunks chunks
+            test_row_ref(g, a, ss, pbuf, buf_n, nbnd, total, seam_list, w.status, upP, rP, rQ, lin_Q - nb, ev);
+            test_row_ref(g, a, ss, pbuf, buf_n, nbnd, total, seam_list, w.status, rP, rQ, dnQ, lin_Q, ev);
+            flush_chunk(a, ss, pbuf, buf_n, nbnd, seam_list, w.status);
+        }
+    }
+    if (tid == 0) {
+        a.cta_nbnd[cta] = min(nbnd, kSeamChunks);
+        a.cta_nseq[cta] = min(nseq, a.seq_max);
+        a.cta_total[cta] = total;
     }
 }
 
@@ -604,29 +966,42 @@ __global__ void __launch_bounds__(256) k_scan_ldg(Geom g, Work w, ScanArgs a)
     const uint64_t g0 = G * blockIdx.x / gridDim.x, g1 = G * (blockIdx.x + 1) / gridDim.x;
     const uint32_t RC = a.R;
     uint32_t buf_n = 0, nseq = 0, total = 0;
-    for (uint64_t ra = g0; ra < g1; ra += RC) {
-        const uint64_t rb = min(ra + RC, g1);
-        const uint4 *own = reinterpret_cast<const uint4 *>(w.M + ra * nb);
-        const uint32_t n4 = (uint32_t)(rb - ra) * nb4;
-        uint32_t hot = 0;
-        for (uint32_t u0 = 0; u0 < n4; u0 += kLdgUPT * bd) {
-            uint4 v[kLdgUPT];
+    // pass 1: stream the run with no block barrier; mark chunks holding a
+    // cell >= T in a shared bitmap (one bit per chunk of RC rows)
+    uint32_t *hot = reinterpret_cast<uint32_t *>(pbuf + a.K);
+    const uint64_t n_chunks = (g1 - g0 + RC - 1) / RC;
+    for (uint32_t k = tid; k < (n_chunks + 31) / 32; k += bd)
+        hot[k] = 0u;
+    __syncthreads();
+    const uint4 *run = reinterpret_cast<const uint4 *>(w.M + g0 * nb);
+    const uint64_t n4 = (g1 - g0) * nb4, per_chunk = (uint64_t)RC * nb4;
+    for (uint64_t u0 = 0; u0 < n4; u0 += (uint64_t)kLdgUPT * bd) {
+        uint4 v[kLdgUPT];
 #pragma unroll
-            for (uint32_t q = 0; q < kLdgUPT; ++q) {
-                const uint32_t u = u0 + q * bd + tid;
-                v[q] = u < n4 ? __ldcs(own + u) : make_uint4(0u, 0u, 0u, 0u);
-            }
-#pragma unroll
-            for (uint32_t q = 0; q < kLdgUPT; ++q)
-                hot |= (max(max(v[q].x, v[q].y), max(v[q].z, v[q].w)) >= T);
+        for (uint32_t q = 0; q < kLdgUPT; ++q) {
+            const uint64_t u = u0 + (uint64_t)q * bd + tid;
+            v[q] = u < n4 ? __ldcs(run + u) : make_uint4(0u, 0u, 0u, 0u);
         }
-        if (__syncthreads_or(hot))
-            scan_rows_slow<4>(g, w, a, ss, pbuf, buf_n, nseq, total, ra, rb, w.M, 0);
+#pragma unroll
+        for (uint32_t q = 0; q < kLdgUPT; ++q)
+            if (max(max(v[q].x, v[q].y), max(v[q].z, v[q].w)) >= T) {
+                const uint64_t c = (u0 + (uint64_t)q * bd + tid) / per_chunk;
+                atomicOr(&hot[c >> 5], 1u << (c & 31u));
+            }
     }
-    flush_chunk(a, ss, pbuf, buf_n, nseq, w.status);
+    __syncthreads();
+    // pass 2: neighbour tests and ordered compaction on the marked chunks only
+    for (uint64_t c = 0; c < n_chunks; ++c) {
+        if (!((hot[c >> 5] >> (c & 31u)) & 1u))
+            continue;
+        const uint64_t ra = g0 + c * RC, rb = min(ra + RC, g1);
+        scan_rows_slow<4>(g, w, a, ss, pbuf, buf_n, nseq, total, ra, rb, w.M, 0);
+    }
+    flush_chunk(a, ss, pbuf, buf_n, nseq, interior_list(a, blockIdx.x), w.status);
     if (tid == 0) {
         a.cta_nseq[blockIdx.x] = min(nseq, a.seq_max);
         a.cta_total[blockIdx.x] = total;
+        a.cta_nbnd[blockIdx.x] = 0u;
     }
 }
 
@@ -657,10 +1032,12 @@ __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, Order
     __syncthreads();
     block_exclusive_scan(ev_base, w.n_events, red);
 
-    const uint32_t nseq = a.cta_nseq[c];
+    // the CTA's seam chunks come before its interior chunks
+    const uint32_t nbnd = a.cta_nbnd[c], nseq = a.cta_nseq[c];
     uint32_t P = prefix;
-    for (uint32_t q = 0; q < nseq; ++q) {
-        const uint2 d = a.desc[(size_t)c * a.seq_max + q];
+    for (uint32_t q = 0; q < nbnd + nseq; ++q) {
+        const uint2 d = q < nbnd ? a.desc_bnd[(size_t)c * kSeamChunks + q]
+                                 : a.desc[(size_t)c * a.seq_max + (q - nbnd)];
         for (uint32_t k = tid; k < d.y; k += bd) {
             if (d.x + k >= a.entries_cap)
                 break;
@@ -702,7 +1079,7 @@ __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, Order
         for (uint32_t e = tid; e < w.n_events; e += bd)
             o.ev_count[e] = 0u;
         if (tid == 0) {
-            *a.g_count = 0u;
+            *o.g_count = 0u;
             *o.ticket = 0u;
         }
     }
@@ -719,6 +1096,32 @@ cudaError_t launch_bin(const Geom &g, const Work &w, uint32_t grid, cudaStream_t
 {
     k_bin<<<grid, 256, 0, st>>>(g, w);
     return cudaGetLastError();
+}
+
+size_t fill_scan_smem_bytes(const FillCfg &c, const ScanArgs &a, uint32_t nb)
+{
+    return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)c.tile_words * 4 + (size_t)c.HC * 16 +
+           (size_t)2 * nb * 4;
+}
+
+cudaError_t launch_fill_scan(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
+                             cudaStream_t st)
+{
+    const size_t smem = fill_scan_smem_bytes(c, a, g.nb);
+    cudaError_t e = cudaFuncSetAttribute(k_fill_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    k_fill_scan<<<grid, c.threads, smem, st>>>(g, w, c, a);
+    return cudaGetLastError();
+}
+
+cudaError_t fill_scan_occupancy(const FillCfg &c, const ScanArgs &a, uint32_t nb, int *blocks_per_sm)
+{
+    const size_t smem = fill_scan_smem_bytes(c, a, nb);
+    cudaError_t e = cudaFuncSetAttribute(k_fill_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fill_scan, c.threads, smem);
 }
 
 size_t fill_smem_bytes(const FillCfg &c)
@@ -752,7 +1155,8 @@ cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t grid, cudaS
 
 size_t scan_smem_bytes(const ScanArgs &a)
 {
-    return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)a.S * a.slot_words * 4;
+    return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)a.S * a.slot_words * 4 +
+           (size_t)a.hot_words * 4;
 }
 
 static const void *scan_kernel(int kind)

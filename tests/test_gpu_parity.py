@@ -279,6 +279,8 @@ TUNINGS = [
     dict(scan_kind=1, scan_slots=8, scan_stage_bytes=24576),
     dict(fill_rows=8, fill_threads=256), dict(fill_rows=64, fill_threads=1024, fill_hits_staged=4096),
     dict(fill_rows=16, fill_blocks_per_sm=1, scan_blocks_per_sm=1, scan_kind=2),
+    dict(fill_fused_scan=2, scan_kind=2), dict(fill_fused_scan=2, scan_kind=1),
+    dict(fill_fused_scan=1, fill_rows=4, fill_threads=256),
 ]
 
 
@@ -300,7 +302,7 @@ def test_tuning_sweep(ht, paper_ref, tuning):
         ctx.set_tuning(**tuning)
         got = ctx.get_tuning()
         for k, v in tuning.items():
-            if k in ("scan_kind", "fill_rows", "fill_threads", "scan_slots"):
+            if k in ("scan_kind", "fill_rows", "fill_threads", "scan_slots", "fill_fused_scan"):
                 assert got[k] == v, (k, got)
         ctx.fill(ev.x, ev.y, ev.z)
         pk, n = ctx.find_maxima(capacity=1 << 16)
@@ -310,10 +312,96 @@ def test_tuning_sweep(ht, paper_ref, tuning):
 
 
 def test_bad_tuning_rejected(ht):
-    with ht.Context(ht.Binning(*synth.TINY_BINNING), ht.Ranges(), threshold=8, max_hits=16) as ctx:
+    with ht.Context(ht.Binning(*synth.TINY_BINNING), ht.Ranges(), threshold=8, max_hits=256) as ctx:
         for bad in (dict(fill_threads=300), dict(fill_rows=12), dict(scan_kind=9)):
             with pytest.raises(ht.HTError):
                 ctx.set_tuning(**bad)
         ev = synth.tiny_event()
         ctx.fill(ev.x, ev.y, ev.z)           # still usable with the previous shapes
         assert ctx.find_maxima(capacity=64)[1] > 0
+
+
+# ---------------------------------------------------------------------------
+# The fused fill + maxima path: seams between strips and between CTAs
+# ---------------------------------------------------------------------------
+
+FUSED_TUNINGS = [dict(fill_fused_scan=2), dict(fill_fused_scan=1), dict(fill_fused_scan=1, fill_rows=4,
+                 fill_threads=256), dict(fill_fused_scan=1, fill_rows=64, fill_threads=1024),
+                 dict(fill_fused_scan=1, fill_rows=8, fill_blocks_per_sm=1)]
+
+
+def _track(A, B, theta, branch):
+    import math
+    Rr = math.hypot(A, B)
+    psi = math.atan2(B, A)
+    xs, ys, zs = [], [], []
+    for rad in synth.LAYER_RADII:
+        ph = psi + branch * math.acos(rad / (2 * Rr))
+        xs.append(rad * math.cos(ph)); ys.append(rad * math.sin(ph)); zs.append(rad / math.tan(theta))
+    return np.float32(xs), np.float32(ys), np.float32(zs)
+
+
+@pytest.mark.parametrize("tuning", FUSED_TUNINGS, ids=[str(t) for t in FUSED_TUNINGS])
+def test_peaks_on_seams(ht, tuning):
+    # tracks whose peaks sit on rows around strip boundaries (rows 3, 4, 7, 8,
+    # 31, 32, 63 of a 64-row slice) plus background hits, binning 2x4x64x64
+    b, r = ht.Binning(2, 4, 64, 64), ht.Ranges()
+    xs, ys, zs = [], [], []
+    import math
+    for ia, ib, branch in [(40, 29, 1), (31, 29, 1), (32, 29, 1), (3, 40, -1), (4, 41, -1), (7, 45, -1),
+                           (8, 46, -1), (63, 52, 1), (20, 45, -1)]:
+        A = -2000 + (ia + 0.5) * 62.5
+        B = -2000 + (ib + 0.5) * 62.5
+        if 2 * math.hypot(A, B) < 1000:
+            continue
+        x, y, z = _track(A, B, 1.5 * math.pi / 2, branch)
+        xs.append(x); ys.append(y); zs.append(z)
+    x, y, z = (np.concatenate(v) for v in (xs, ys, zs))
+    bx, by, bz = random_hits(300, 21)
+    x, y, z = np.concatenate([x, bx]), np.concatenate([y, by]), np.concatenate([z, bz])
+    for T in (3, 8, 12):
+        M_ref, _ = oracle.fill(_ob(b), _orr(r), x, y, z)
+        pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, T)
+        with ht.Context(b, r, threshold=T, max_hits=x.size) as ctx:
+            ctx.set_tuning(**tuning)
+            ctx.fill(x, y, z)
+            pk, n = ctx.find_maxima(capacity=4096)
+            assert np.array_equal(ctx.matrix(), M_ref)
+        assert n == n_ref, (T, n, n_ref)
+        assert_peaks_equal(pk, pk_ref)
+
+
+@pytest.mark.parametrize("tuning", FUSED_TUNINGS[1:3], ids=[str(t) for t in FUSED_TUNINGS[1:3]])
+def test_fused_state_sequences(ht, paper_ref, tuning):
+    ev, M_ref, pk_ref, n_ref = paper_ref
+    ev2 = synth.paper_event(seed=12)
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    M2, _ = oracle.fill(_ob(b), _orr(r), ev2.x, ev2.y, ev2.z)
+    pk2, n2 = oracle.find_maxima(_ob(b), _orr(r), M2, 10)
+    with ht.Context(b, r, threshold=10, max_hits=6000) as ctx:
+        ctx.set_tuning(**tuning)
+        # a fused fill consumed twice: the second call rescans M_H
+        ctx.fill(ev.x, ev.y, ev.z)
+        for _ in range(2):
+            pk, n = ctx.find_maxima(capacity=1 << 16)
+            assert n == n_ref
+            assert_peaks_equal(pk, pk_ref)
+        # two fills in a row: only the second counts
+        ctx.fill(ev.x, ev.y, ev.z)
+        ctx.fill(ev2.x, ev2.y, ev2.z)
+        pk, n = ctx.find_maxima(capacity=1 << 16)
+        assert n == n2
+        assert_peaks_equal(pk, pk2)
+        # an unconsumed fused fill, then a matrix set by hand
+        ctx.fill(ev.x, ev.y, ev.z)
+        ctx.set_matrix(M2)
+        pk, n = ctx.find_maxima(capacity=1 << 16)
+        assert n == n2
+        assert_peaks_equal(pk, pk2)
+        # naive and accumulating fills fall back to the standalone scan
+        ctx.fill(ev.x, ev.y, ev.z)
+        ctx.fill(ev.x[:10], ev.y[:10], ev.z[:10], naive=True)
+        ctx.fill(ev.x[10:], ev.y[10:], ev.z[10:], accumulate=True)
+        pk, n = ctx.find_maxima(capacity=1 << 16)
+        assert n == n_ref
+        assert_peaks_equal(pk, pk_ref)
