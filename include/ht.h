@@ -213,6 +213,13 @@ ht_status ht_validate(const ht_binning *binning, const ht_ranges *ranges, uint32
 ht_status ht_compute_edges(const ht_binning *binning, const ht_ranges *ranges, float *theta_edges,
                            float *phi_edges);
 
+/* The B-bin thresholds the kernels use (n_b + 1 floats): beta[k] is the
+ * smallest float B whose bin floor(fl(fl(B - b_min) / dB)) is >= k, so a vote
+ * is in range iff beta[0] <= B < beta[n_b] and its bin is the number of
+ * beta[1..n_b-1] that are <= B -- identical to the division rule for every
+ * float B. */
+ht_status ht_compute_b_thresholds(const ht_binning *binning, const ht_ranges *ranges, float *beta);
+
 #ifdef __cplusplus
 }
 #endif

@@ -364,6 +364,17 @@ ht_status ht_validate(const ht_binning *binning, const ht_ranges *ranges, uint32
     return HT_OK;
 }
 
+ht_status ht_compute_b_thresholds(const ht_binning *binning, const ht_ranges *ranges, float *beta)
+{
+    std::string why;
+    if (!beta)
+        return set_err(HT_E_INVAL, "beta must not be NULL");
+    if (!htg::validate(binning, ranges, 1, &why))
+        return set_err(HT_E_INVAL, why);
+    htg::b_thresholds(ranges->b_min, htg::delta(ranges->b_min, ranges->b_max, binning->n_b), binning->n_b, beta);
+    return HT_OK;
+}
+
 ht_status ht_compute_edges(const ht_binning *binning, const ht_ranges *ranges, float *theta_edges,
                            float *phi_edges)
 {

@@ -26,8 +26,10 @@ struct Geom {
     uint32_t max_admit;     // slices one hit can enter
     uint32_t threshold;
     float a_min, b_min, da, db, nbf;
+    float inv_db;           // 1 / dB, only to estimate a bin before the exact table test
     const float *et;        // device: nt + 1 theta pseudo-angle edges
     const float *ep;        // device: np + 1 phi pseudo-angle edges
+    const float *bth;       // device: nb + 1 B-bin thresholds (see bin_from_thresholds)
 };
 
 // Device buffers of one batch of events (a single-event context is a batch
@@ -189,6 +191,34 @@ __device__ __forceinline__ int vote_bin(const Geom &g, float twoA, float x, floa
     if (t >= 0.0f && t < g.nbf)
         return (int)__float2uint_rz(t);
     return -1;
+}
+
+// The B bin of the vote from the threshold table beta[0 .. nb]: beta[k] is
+// the smallest float B whose bin floor(fl(fl(B - b_min) / dB)) is >= k, so
+// the bin is max{k : beta[k] <= B} and the vote is in range iff
+// beta[0] <= B < beta[nb] (NaN fails).  Identical to the division rule for
+// every float B; an estimate from 1/dB is corrected by table compares.
+__device__ __forceinline__ int bin_from_thresholds(const Geom &g, const float *beta, float B)
+{
+    if (!(B >= beta[0] && B < beta[g.nb]))
+        return -1;
+    int j = (int)((B - g.b_min) * g.inv_db);
+    j = max(0, min(j, (int)g.nb - 1));
+    while (B < beta[j])
+        --j;
+    while (B >= beta[j + 1])
+        ++j;
+    return j;
+}
+
+// The vote of one (hit, A bin) with the threshold table: B = (r2 - (2A) x) / d
+// by IEEE division, then its bin (or -1).
+__device__ __forceinline__ int vote_bin_tab(const Geom &g, const float *beta, float twoA, float x, float r2,
+                                            float d)
+{
+    const float num = __fsub_rn(r2, __fmul_rn(twoA, x));
+    const float B = __fdiv_rn(num, d);
+    return bin_from_thresholds(g, beta, B);
 }
 
 // ---------------------------------------------------------------------------

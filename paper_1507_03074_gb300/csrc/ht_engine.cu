@@ -128,6 +128,8 @@ ht_status engine_configure(Engine &E, std::string *why)
     f.HC = std::max(t.fill_HC ? t.fill_HC : 2048u, 2 * f.threads);   // select_hits needs HC >= 2 * threads
     f.pitch16 = round_up((b.n_b + 1) / 2, 32);
     f.pitch32 = round_up(b.n_b, 32);
+    f.beta_words = round_up(b.n_b + 1, 4);
+    const size_t beta_bytes = (size_t)f.beta_words * 4;
     uint32_t W = t.fill_W;
     if (W && (W & (W - 1))) {
         *why = "fill_rows must be a power of two";
@@ -139,13 +141,12 @@ ht_status engine_configure(Engine &E, std::string *why)
         while (W > 2 && (size_t)W * f.pitch16 * 4 > 64 * 1024)
             W >>= 1;
     }
-    while (W > 2 && (size_t)W * f.pitch16 * 4 + (size_t)f.HC * 16 > kSmemMax)
+    while (W > 2 && (size_t)W * f.pitch16 * 4 + (size_t)f.HC * 16 + beta_bytes > kSmemMax)
         W >>= 1;
     f.W = W;
     f.tile_words = W * f.pitch16;
     f.strips = (b.n_a + W - 1) / W;
-    E.fill_priv_ok = (W >= 2) && (f.threads % W == 0) &&
-                     ((size_t)f.tile_words * 4 + (size_t)f.HC * 16 <= kSmemMax);
+    E.fill_priv_ok = (W >= 2) && (f.threads % W == 0) && htk::fill_smem_bytes(f) <= kSmemMax;
     E.fill = f;
     if (E.fill_priv_ok) {
         int occ = 0;
@@ -340,13 +341,13 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
     g.threshold = threshold;
     g.a_min = r->a_min;
     g.b_min = r->b_min;
-    {   // dA = fl((a_max - a_min) / n_a), dB likewise, in FP32
-        volatile float da = r->a_max - r->a_min, db = r->b_max - r->b_min;
-        volatile float fa = (float)b->n_a, fb = (float)b->n_b;
-        g.da = da / fa;
-        g.db = db / fb;
-        g.nbf = (float)b->n_b;
-    }
+    // dA = fl((a_max - a_min) / n_a), dB likewise, in FP32
+    g.da = htg::delta(r->a_min, r->a_max, b->n_a);
+    g.db = htg::delta(r->b_min, r->b_max, b->n_b);
+    g.nbf = (float)b->n_b;
+    g.inv_db = (float)(1.0 / (double)g.db);
+    E.bth.resize(b->n_b + 1);
+    htg::b_thresholds(g.b_min, g.db, b->n_b, E.bth.data());
 
     ht_status st = engine_configure(E, why);
     if (st != HT_OK) {
@@ -365,7 +366,7 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
     size_t acc = 0;
     const size_t hits_cap = (size_t)std::max<uint32_t>(max_hits, 1);
     const uint32_t ctr_words = engine_ctr_words(E);
-    if ((e = dalloc(&E.d_edges, (E.et.size() + E.ep.size()) * 4, &acc)) != cudaSuccess ||
+    if ((e = dalloc(&E.d_edges, (E.et.size() + E.ep.size() + E.bth.size()) * 4, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_M, (size_t)E.n_cells * 4 * max_events + 256, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_hits4, hits_cap * 16, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_codes, hits_cap * 4, &acc)) != cudaSuccess ||
@@ -381,9 +382,12 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
     E.device_bytes = acc + E.book_bytes;
     g.et = E.d_edges;
     g.ep = E.d_edges + E.et.size();
+    g.bth = E.d_edges + E.et.size() + E.ep.size();
     if ((e = cudaMemcpy(E.d_edges, E.et.data(), E.et.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(E.d_edges + E.et.size(), E.ep.data(), E.ep.size() * 4, cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
+        (e = cudaMemcpy(E.d_edges + E.et.size() + E.ep.size(), E.bth.data(), E.bth.size() * 4,
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(E.d_ctr, 0, (size_t)ctr_words * 4)) != cudaSuccess ||
         (e = cudaMemset(E.d_M, 0, (size_t)E.n_cells * 4 * max_events)) != cudaSuccess) {
         std::snprintf(buf, sizeof buf, "device initialisation failed: %s", cudaGetErrorString(e));

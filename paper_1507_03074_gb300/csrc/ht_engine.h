@@ -50,7 +50,7 @@ struct Engine {
     uint64_t n_cells = 0;        // per event
     int device = 0;
     int num_sms = 0;
-    std::vector<float> et, ep;
+    std::vector<float> et, ep, bth;   // edge tables, B-bin thresholds
 
     htk::Geom geom{};
     htk::FillCfg fill{};

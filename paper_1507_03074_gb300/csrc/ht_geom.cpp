@@ -74,6 +74,52 @@ void phi_edges(float lo, float hi, uint32_t n, float *e)
     }
 }
 
+// Bin width fl((hi - lo) / n) in FP32.
+float delta(float lo, float hi, uint32_t n)
+{
+    volatile float w = hi - lo, fn = (float)n;
+    volatile float d = w / fn;
+    return d;
+}
+
+// The B bin of the vote, floor(fl(fl(B - b_min) / dB)) for 0 <= t < n_b, is a
+// non-decreasing step function of the float B (each FP32 step is a rounded
+// monotone operation).  beta[k] is the smallest float B whose bin is >= k
+// (k = 0 .. n_b; bin = -1 below range, n_b above), so for any float B:
+//   in range  <=>  beta[0] <= B < beta[n_b],   bin = max{k : beta[k] <= B}.
+// Each threshold is found by stepping float by float from the nearest float
+// to b_min + k dB, evaluating the same FP32 operations as the vote.
+static int b_bin_f32(float B, float b_min, float db, uint32_t nb)
+{
+    volatile float num = B - b_min;
+    volatile float t = num / db;
+    if (!(t >= 0.0f))
+        return -1;
+    if (!(t < (float)nb))
+        return (int)nb;
+    return (int)(uint32_t)t;
+}
+
+void b_thresholds(float b_min, float db, uint32_t nb, float *beta)
+{
+    for (uint32_t k = 0; k <= nb; ++k) {
+        float B = (float)((double)b_min + (double)k * (double)db);
+        if (b_bin_f32(B, b_min, db, nb) >= (int)k) {
+            for (;;) {
+                const float lower = std::nextafter(B, -INFINITY);
+                if (b_bin_f32(lower, b_min, db, nb) >= (int)k)
+                    B = lower;
+                else
+                    break;
+            }
+        } else {
+            while (b_bin_f32(B, b_min, db, nb) < (int)k)
+                B = std::nextafter(B, INFINITY);
+        }
+        beta[k] = B;
+    }
+}
+
 bool phi_is_full_circle(float lo, float hi)
 {
     return snap_quarter(lo) == -kPi && snap_quarter(hi) == kPi;

@@ -12,6 +12,8 @@ double snap_quarter(double a);
 void theta_edges(float lo, float hi, uint32_t n, float *e);
 void phi_edges(float lo, float hi, uint32_t n, float *e);
 bool phi_is_full_circle(float lo, float hi);
+float delta(float lo, float hi, uint32_t n);
+void b_thresholds(float b_min, float db, uint32_t nb, float *beta);
 uint32_t max_admit(const ht_binning &b);
 bool validate(const ht_binning *b, const ht_ranges *r, uint32_t threshold, std::string *why);
 

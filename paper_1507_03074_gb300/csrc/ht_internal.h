@@ -21,6 +21,7 @@ struct FillCfg {
     uint32_t tile_words;  // W * pitch16
     uint32_t threads;     // block size
     uint32_t accumulate;  // add the tile to M_H instead of storing it
+    uint32_t beta_words;  // shared-memory copy of the B-bin thresholds (n_b + 1, rounded to 4)
 };
 
 // Scan (and its chunk bookkeeping).  Shared with k_order.

@@ -116,8 +116,8 @@ __device__ __forceinline__ uint32_t row_hash(uint32_t r)
 }
 
 template <bool U16>
-__device__ __forceinline__ void vote_rows(const Geom &g, uint32_t *tile, const float4 *hs, uint32_t nc,
-                                          uint32_t r, uint32_t i, uint32_t hl, uint32_t hstride,
+__device__ __forceinline__ void vote_rows(const Geom &g, uint32_t *tile, const float4 *hs, const float *beta,
+                                          uint32_t nc, uint32_t r, uint32_t i, uint32_t hl, uint32_t hstride,
                                           uint32_t pitch)
 {
     const float twoA = __fmul_rn(2.0f, a_centre(g, i));
@@ -126,7 +126,7 @@ __device__ __forceinline__ void vote_rows(const Geom &g, uint32_t *tile, const f
 #pragma unroll 4
     for (uint32_t h = hl; h < nc; h += hstride) {
         const float4 hv = hs[h];
-        const int j = vote_bin(g, twoA, hv.x, hv.y, hv.z);
+        const int j = vote_bin_tab(g, beta, twoA, hv.x, hv.y, hv.z);
         if (j >= 0) {
             if (U16) {
                 const uint32_t word = rowbase + ((uint32_t(j) >> 1) ^ sw);
@@ -145,9 +145,10 @@ __device__ __forceinline__ void flush_rows(const Geom &g, uint32_t *tile, uint32
     const uint32_t tid = threadIdx.x, bd = blockDim.x;
     if ((g.nb & 3u) == 0) {
         const uint32_t q = g.nb >> 2;  // 16-byte units per row
+        const uint32_t qs = (q & (q - 1)) ? 32u : (uint32_t)(__ffs(q) - 1);
         const uint32_t units = rows * q;
         for (uint32_t u = tid; u < units; u += bd) {
-            const uint32_t r = u / q, c4 = u - r * q;
+            const uint32_t r = qs < 32u ? u >> qs : u / q, c4 = u - r * q;
             uint4 v;
             if (U16) {
                 const uint32_t sw = row_hash(r) & 0x1Eu;
@@ -247,10 +248,13 @@ __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
     __shared__ uint32_t s_n;
     uint32_t *tile = reinterpret_cast<uint32_t *>(sm4);
     float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
+    float *beta = reinterpret_cast<float *>(hs + c.HC);
 
     const uint32_t tid = threadIdx.x, bd = blockDim.x;
     for (uint32_t k = tid; k < c.tile_words / 4; k += bd)
         sm4[k] = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t k = tid; k <= g.nb; k += bd)
+        beta[k] = g.bth[k];
 
     const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
     const uint64_t it0 = items * blockIdx.x / gridDim.x, it1 = items * (blockIdx.x + 1) / gridDim.x;
@@ -281,9 +285,9 @@ __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
                 __syncthreads();
                 if (r < pr) {
                     if (u16)
-                        vote_rows<true>(g, tile, hs, cached_n, r, i, hl, hstride, pitch);
+                        vote_rows<true>(g, tile, hs, beta,cached_n, r, i, hl, hstride, pitch);
                     else
-                        vote_rows<false>(g, tile, hs, cached_n, r, i, hl, hstride, pitch);
+                        vote_rows<false>(g, tile, hs, beta,cached_n, r, i, hl, hstride, pitch);
                 }
             } else {
                 cached_es = ~0ull;       // hs is about to be overwritten
@@ -298,9 +302,9 @@ __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
                     first = false;
                     if (r < pr) {
                         if (u16)
-                            vote_rows<true>(g, tile, hs, nsel, r, i, hl, hstride, pitch);
+                            vote_rows<true>(g, tile, hs, beta,nsel, r, i, hl, hstride, pitch);
                         else
-                            vote_rows<false>(g, tile, hs, nsel, r, i, hl, hstride, pitch);
+                            vote_rows<false>(g, tile, hs, beta,nsel, r, i, hl, hstride, pitch);
                     }
                 }
             }
@@ -705,9 +709,10 @@ __device__ __forceinline__ void flush_rows_mark(const Geom &g, const uint32_t *t
     const uint32_t tid = threadIdx.x, bd = blockDim.x, T = g.threshold;
     if ((g.nb & 3u) == 0) {
         const uint32_t q = g.nb >> 2;
+        const uint32_t qs = (q & (q - 1)) ? 32u : (uint32_t)(__ffs(q) - 1);
         const uint32_t units = rows * q;
         for (uint32_t u = tid; u < units; u += bd) {
-            const uint32_t r = u / q, c4 = u - r * q;
+            const uint32_t r = qs < 32u ? u >> qs : u / q, c4 = u - r * q;
             uint4 v;
             if (U16) {
                 const uint2 pr = *reinterpret_cast<const uint2 *>(
@@ -754,11 +759,14 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
     uint32_t *tile = reinterpret_cast<uint32_t *>(pbuf + a.K);
     float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
     uint32_t *carry = reinterpret_cast<uint32_t *>(hs + c.HC);   // [2][nb]
+    float *beta = reinterpret_cast<float *>(carry + 2 * g.nb);     // nb + 1 thresholds
     __shared__ uint32_t s_n, s_cta, s_hot[2], s_ok;
 
     const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb;
     for (uint32_t k = tid; k < c.tile_words / 4; k += bd)
         sm4[16 + a.K + k] = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t k = tid; k <= nb; k += bd)
+        beta[k] = g.bth[k];
     if (tid == 0)
         s_cta = atomicAdd(a.fticket, 1u);
     __syncthreads();
@@ -809,9 +817,9 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
                 __syncthreads();
                 if (r < pr) {
                     if (u16)
-                        vote_rows<true>(g, tile, hs, cached_n, r, i, hl, hstride, pitch);
+                        vote_rows<true>(g, tile, hs, beta,cached_n, r, i, hl, hstride, pitch);
                     else
-                        vote_rows<false>(g, tile, hs, cached_n, r, i, hl, hstride, pitch);
+                        vote_rows<false>(g, tile, hs, beta,cached_n, r, i, hl, hstride, pitch);
                 }
             } else {
                 cached_es = ~0ull;
@@ -826,9 +834,9 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
                     first = false;
                     if (r < pr) {
                         if (u16)
-                            vote_rows<true>(g, tile, hs, nsel, r, i, hl, hstride, pitch);
+                            vote_rows<true>(g, tile, hs, beta,nsel, r, i, hl, hstride, pitch);
                         else
-                            vote_rows<false>(g, tile, hs, nsel, r, i, hl, hstride, pitch);
+                            vote_rows<false>(g, tile, hs, beta,nsel, r, i, hl, hstride, pitch);
                     }
                 }
             }
@@ -1101,7 +1109,7 @@ cudaError_t launch_bin(const Geom &g, const Work &w, uint32_t grid, cudaStream_t
 size_t fill_scan_smem_bytes(const FillCfg &c, const ScanArgs &a, uint32_t nb)
 {
     return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)c.tile_words * 4 + (size_t)c.HC * 16 +
-           (size_t)2 * nb * 4;
+           (size_t)2 * nb * 4 + (size_t)c.beta_words * 4;
 }
 
 cudaError_t launch_fill_scan(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
@@ -1126,7 +1134,7 @@ cudaError_t fill_scan_occupancy(const FillCfg &c, const ScanArgs &a, uint32_t nb
 
 size_t fill_smem_bytes(const FillCfg &c)
 {
-    return (size_t)c.tile_words * 4 + (size_t)c.HC * 16;
+    return (size_t)c.tile_words * 4 + (size_t)c.HC * 16 + (size_t)c.beta_words * 4;
 }
 
 cudaError_t launch_fill_priv(const Geom &g, const Work &w, const FillCfg &c, uint32_t grid,

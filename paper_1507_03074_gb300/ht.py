@@ -122,6 +122,7 @@ def lib():
         "ht_compute_edges": ([ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), P, P], I),
         "ht_profile": ([P, I], I),
         "ht_profile_read": ([P, P, U32, P], I),
+        "ht_compute_b_thresholds": ([ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), P], I),
         "ht_set_tuning": ([P, ctypes.POINTER(c_tuning)], I),
         "ht_get_tuning": ([P, ctypes.POINTER(c_tuning)], I),
     }
@@ -152,6 +153,14 @@ def compute_edges(binning: Binning, ranges: Ranges = Ranges()):
     check(lib().ht_compute_edges(ctypes.byref(b), ctypes.byref(r), et.ctypes.data_as(ctypes.c_void_p),
                                  ep.ctypes.data_as(ctypes.c_void_p)))
     return et, ep
+
+
+def compute_b_thresholds(binning: Binning, ranges: Ranges = Ranges()):
+    """ht_compute_b_thresholds: the n_b + 1 B-bin thresholds (host only)."""
+    beta = np.zeros(binning.n_b + 1, np.float32)
+    b, r = binning.c(), ranges.c()
+    check(lib().ht_compute_b_thresholds(ctypes.byref(b), ctypes.byref(r), beta.ctypes.data_as(ctypes.c_void_p)))
+    return beta
 
 
 def last_error() -> str:

@@ -66,3 +66,32 @@ def test_create_rejects_before_touching_device():
     b, r = ht.Binning(0, 4, 8, 8).c(), ht.Ranges().c()
     rc = ht.lib().ht_create(ctypes.byref(b), ctypes.byref(r), 5, 100, ctypes.byref(h))
     assert rc == ht.HT_E_INVAL and not h.value
+
+
+def _bin_by_division(B, b_min, db, nb):
+    # the documented FP32 rule, evaluated with numpy float32 operations
+    t = (B - np.float32(b_min)) / np.float32(db)
+    out = np.full(B.shape, -1, np.int64)
+    ok = (t >= 0) & (t < np.float32(nb))
+    out[ok] = t[ok].astype(np.int64)
+    return out
+
+
+@pytest.mark.parametrize("nb,rng", [(64, dict()), (1024, dict()), (2048, dict()), (29, dict(b_min=-900.0, b_max=2100.0)),
+                                    (1000, dict(b_min=-1234.5, b_max=987.25)), (7, dict(b_min=0.125, b_max=0.5))])
+def test_b_thresholds_equal_division(nb, rng):
+    b, r = ht.Binning(1, 1, 4, nb), ht.Ranges(**rng)
+    beta = ht.compute_b_thresholds(b, r)
+    assert np.all(np.diff(beta) > 0)
+    db = np.float32((np.float32(r.b_max) - np.float32(r.b_min)) / np.float32(nb))
+    g = np.random.default_rng(nb)
+    span = r.b_max - r.b_min
+    B = g.uniform(r.b_min - 0.1 * span, r.b_max + 0.1 * span, 200000).astype(np.float32)
+    # every threshold and its float neighbours, plus the range ends
+    near = np.concatenate([beta, np.nextafter(beta, np.float32(-np.inf)), np.nextafter(beta, np.float32(np.inf)),
+                           np.float32([r.b_min, r.b_max, np.nan, np.inf, -np.inf])])
+    B = np.concatenate([B, near.astype(np.float32)])
+    want = _bin_by_division(B, r.b_min, db, nb)
+    inr = (B >= beta[0]) & (B < beta[nb])
+    got = np.where(inr, np.searchsorted(beta, B, side="right") - 1, -1)
+    assert np.array_equal(np.where(want >= 0, want, -1), got)
