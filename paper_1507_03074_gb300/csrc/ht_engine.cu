@@ -14,7 +14,7 @@ static const size_t kSmemMax = 227 * 1024;     // per CTA on sm_100-class parts
 static const uint32_t kScanThreads = 256;
 static const uint32_t kPeakBuf = 1024;         // K: entries buffered per scan / fused CTA
 
-const char *const kKernelNames[K_NKINDS] = {"k_bin", "k_fill_priv", "k_fill_scan", "k_clear",
+const char *const kKernelNames[K_NKINDS] = {"k_bin", "k_fill_priv", "k_fill_scan", "k_seam", "k_clear",
                                              "k_fill_naive", "k_scan", "k_order"};
 
 // ---------------------------------------------------------------------------
@@ -252,8 +252,8 @@ ht_status engine_configure(Engine &E, std::string *why)
     }
     s.seq_max = seq;
     const size_t desc_b = (size_t)grid_cap * seq * 8, bnd_b = (size_t)grid_cap * htk::kSeamChunks * 8;
-    const size_t cta_b = (size_t)grid_cap * 3 * 4, done_b = (size_t)grid_cap * 4;
-    const size_t need = desc_b + bnd_b + cta_b + done_b;
+    const size_t cta_b = (size_t)grid_cap * 3 * 4;
+    const size_t need = desc_b + bnd_b + cta_b;
     if (need > E.book_bytes || grid_cap != E.grid_cap) {
         if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
             *why = std::string("synchronise before re-allocation: ") + cudaGetErrorString(e);
@@ -274,7 +274,6 @@ ht_status engine_configure(Engine &E, std::string *why)
             *why = std::string("scan bookkeeping initialisation failed: ") + cudaGetErrorString(e);
             return HT_E_CUDA;
         }
-        E.epoch = 0;   // done flags are zero again
         E.grid_cap = grid_cap;
     }
     char *p = static_cast<char *>(E.d_book);
@@ -284,7 +283,6 @@ ht_status engine_configure(Engine &E, std::string *why)
     s.cta_nseq = cta;
     s.cta_total = cta + grid_cap;
     s.cta_nbnd = cta + 2 * grid_cap;
-    s.done = reinterpret_cast<uint32_t *>(p + desc_b + bnd_b + cta_b);
     s.grid = scan_grid;
     E.fused_valid = false;
     return HT_OK;
@@ -398,7 +396,6 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
     s.entries = E.d_entries;
     s.g_count = E.d_ctr + htk::CTR_ENTRIES;
     s.ev_count = E.d_ctr + htk::CTR_EVENTS;
-    s.fticket = E.d_ctr + htk::CTR_FTICKET;
     return HT_OK;
 }
 
@@ -508,7 +505,6 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
     if (E.fused_ok && !accumulate) {
         htk::ScanArgs a = E.scan;
         a.K = E.fused_K;
-        a.epoch = ++E.epoch;
         htk::FillCfg ff = E.fused_fill;
         ff.accumulate = 0u;
         const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.fused_grid, items));
@@ -517,6 +513,11 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
             e = htk::launch_fill_scan(E.geom, w, ff, a, grid, st);
         }
         ++E.launches;
+        if (e == cudaSuccess) {
+            ProfScope ps(E, K_SEAM, st);
+            e = htk::launch_seam(E.geom, w, ff, a, grid, st);
+            ++E.launches;
+        }
         if (e == cudaSuccess) {
             E.fused_valid = true;
             E.ctr_dirty = true;

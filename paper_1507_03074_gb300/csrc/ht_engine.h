@@ -28,7 +28,7 @@ struct Tuning {
 
 // Optional per-kernel timing with CUDA events recorded on the launching
 // stream around every launch (enabled by ht_profile).
-enum KernelKind { K_BIN, K_FILL_PRIV, K_FILL_SCAN, K_CLEAR, K_FILL_NAIVE, K_SCAN, K_ORDER, K_NKINDS };
+enum KernelKind { K_BIN, K_FILL_PRIV, K_FILL_SCAN, K_SEAM, K_CLEAR, K_FILL_NAIVE, K_SCAN, K_ORDER, K_NKINDS };
 extern const char *const kKernelNames[K_NKINDS];
 
 struct Prof {
@@ -72,7 +72,6 @@ struct Engine {
     bool fused_valid = false;
     uint32_t fused_grid_used = 0;
     uint32_t fused_events = 0;
-    uint32_t epoch = 0;
     bool ctr_dirty = false;      // counters hold an unconsumed fused fill's peaks
 
     float *d_edges = nullptr;
@@ -80,7 +79,7 @@ struct Engine {
     float4 *d_hits4 = nullptr;
     uint32_t *d_codes = nullptr;
     uint4 *d_entries = nullptr;
-    void *d_book = nullptr;       // desc | desc_bnd | cta arrays | done flags
+    void *d_book = nullptr;       // desc | desc_bnd | cta arrays
     uint32_t *d_ctr = nullptr;    // counter block (htk::CTR_*)
     size_t device_bytes = 0;
     uint64_t launches = 0;

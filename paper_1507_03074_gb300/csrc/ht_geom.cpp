@@ -12,6 +12,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 
 namespace htg {
 
@@ -87,8 +88,9 @@ float delta(float lo, float hi, uint32_t n)
 // monotone operation).  beta[k] is the smallest float B whose bin is >= k
 // (k = 0 .. n_b; bin = -1 below range, n_b above), so for any float B:
 //   in range  <=>  beta[0] <= B < beta[n_b],   bin = max{k : beta[k] <= B}.
-// Each threshold is found by stepping float by float from the nearest float
-// to b_min + k dB, evaluating the same FP32 operations as the vote.
+// Each threshold is found by a binary search over the floats (in their
+// integer order) between two bracketing values, evaluating the same FP32
+// operations as the vote.
 static int b_bin_f32(float B, float b_min, float db, uint32_t nb)
 {
     volatile float num = B - b_min;
@@ -100,23 +102,42 @@ static int b_bin_f32(float B, float b_min, float db, uint32_t nb)
     return (int)(uint32_t)t;
 }
 
+// Floats in increasing order <-> integers in increasing order (+0 and -0 share 0).
+static int64_t float_key(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return (u & 0x80000000u) ? -(int64_t)(u & 0x7fffffffu) : (int64_t)u;
+}
+
+static float key_float(int64_t k)
+{
+    const uint32_t u = k >= 0 ? (uint32_t)k : (0x80000000u | (uint32_t)(-k));
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
 void b_thresholds(float b_min, float db, uint32_t nb, float *beta)
 {
     for (uint32_t k = 0; k <= nb; ++k) {
-        float B = (float)((double)b_min + (double)k * (double)db);
-        if (b_bin_f32(B, b_min, db, nb) >= (int)k) {
-            for (;;) {
-                const float lower = std::nextafter(B, -INFINITY);
-                if (b_bin_f32(lower, b_min, db, nb) >= (int)k)
-                    B = lower;
-                else
-                    break;
-            }
-        } else {
-            while (b_bin_f32(B, b_min, db, nb) < (int)k)
-                B = std::nextafter(B, INFINITY);
+        // bracket: lo two bins below (bin < k), hi two bins above (bin >= k)
+        float lo = (float)((double)b_min + ((double)k - 2.0) * (double)db);
+        float hi = (float)((double)b_min + ((double)k + 2.0) * (double)db);
+        for (int widen = 0; b_bin_f32(lo, b_min, db, nb) >= (int)k && widen < 64; ++widen)
+            lo = lo - std::fabs(lo) - db;
+        for (int widen = 0; b_bin_f32(hi, b_min, db, nb) < (int)k && widen < 64; ++widen)
+            hi = hi + std::fabs(hi) + db;
+        // smallest float key in (key(lo), key(hi)] whose bin is >= k
+        int64_t a = float_key(lo), c = float_key(hi);
+        while (c - a > 1) {
+            const int64_t m = a + (c - a) / 2;
+            if (b_bin_f32(key_float(m), b_min, db, nb) >= (int)k)
+                c = m;
+            else
+                a = m;
         }
-        beta[k] = B;
+        beta[k] = key_float(c);
     }
 }
 

@@ -41,9 +41,6 @@ struct ScanArgs {
     uint32_t *cta_total;  // [grid] entries (seam + interior)
     uint32_t *cta_nbnd;   // [grid] seam chunks (fused fill only; 0 otherwise)
     uint2 *desc_bnd;      // [grid][kSeamChunks] seam chunks {base, n}
-    uint32_t *done;       // [grid] epoch once the CTA's rows are in M_H (fused fill)
-    uint32_t *fticket;    // logical CTA index counter of the fused fill
-    uint32_t epoch;       // launch number of the fused fill
     uint32_t *ev_count;   // [n_events] peaks per event (reset by k_order)
 };
 
@@ -64,6 +61,8 @@ size_t fill_scan_smem_bytes(const FillCfg &c, const ScanArgs &a, uint32_t nb);
 cudaError_t launch_fill_scan(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
                              cudaStream_t st);
 cudaError_t fill_scan_occupancy(const FillCfg &c, const ScanArgs &a, uint32_t nb, int *blocks_per_sm);
+cudaError_t launch_seam(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
+                        cudaStream_t st);
 cudaError_t launch_clear(uint32_t *M, uint64_t words, uint32_t grid, cudaStream_t st);
 cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
 size_t scan_smem_bytes(const ScanArgs &a);
@@ -71,13 +70,15 @@ size_t scan_smem_bytes(const ScanArgs &a);
 constexpr uint32_t kSeamChunks = 8;
 
 // Layout of the counter block: [0] status, [1] entries used, [2] order
-// ticket, [3] fused-fill ticket, [4 ..) peaks per event.  k_bin zeroes
+// ticket, [3] spare, [4 ..) peaks per event.  k_bin zeroes
 // words [1, 4 + n_events) before every fill.
-enum : uint32_t { CTR_STATUS = 0, CTR_ENTRIES = 1, CTR_OTICKET = 2, CTR_FTICKET = 3, CTR_EVENTS = 4 };
+enum : uint32_t { CTR_STATUS = 0, CTR_ENTRIES = 1, CTR_OTICKET = 2, CTR_SPARE = 3, CTR_EVENTS = 4 };
 
 // Scan variants: bulk-copy (TMA) ring, register streaming, direct (any n_b).
 // The streaming variant keeps kLdgUPT 16-byte loads per thread in flight.
 constexpr uint32_t kLdgUPT = 4;
+// Candidate cells (>= threshold) a streaming-scan CTA lists before testing them.
+constexpr uint32_t kCand = 1024;
 enum ScanKind { SCAN_DIRECT = 0, SCAN_BULK = 1, SCAN_LDG = 2 };
 cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, int kind, cudaStream_t st);
 cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const OrderArgs &o,

@@ -622,12 +622,10 @@ __global__ void __launch_bounds__(256) k_scan_direct(Geom g, Work w, ScanArgs a)
 //     tested at once; the pass's last row waits for the next pass of the
 //     same slice, bridged by two carried rows (u32 copies of the last rows);
 //   - the first row of the CTA's range, when it is not a slice's first row,
-//     and the previous CTA's last row form the seam between two CTAs.  This
-//     CTA tests both at its end, reading them back from L2 after the
-//     previous CTA has published (bounded wait on its done flag).
-// Logical CTA indices come from an atomic ticket, so a CTA only ever waits on
-// one that started before it.  Peaks go, in linear order, into per-CTA
-// chunks: a seam chunk (desc_bnd) followed by the interior chunks.
+//     and the previous CTA's last row form the seam between two CTAs; k_seam
+//     tests both once the whole of M_H is written.
+// Peaks go, in linear order, into per-CTA interior chunks; k_seam adds the
+// seam chunks, which k_order places before the CTA's interior chunks.
 // ---------------------------------------------------------------------------
 
 // A row of cells in one of the places the fused kernel keeps them.
@@ -760,20 +758,16 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
     float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
     uint32_t *carry = reinterpret_cast<uint32_t *>(hs + c.HC);   // [2][nb]
     float *beta = reinterpret_cast<float *>(carry + 2 * g.nb);     // nb + 1 thresholds
-    __shared__ uint32_t s_n, s_cta, s_hot[2], s_ok;
+    __shared__ uint32_t s_n, s_hot[2];
 
     const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb;
     for (uint32_t k = tid; k < c.tile_words / 4; k += bd)
         sm4[16 + a.K + k] = make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t k = tid; k <= nb; k += bd)
         beta[k] = g.bth[k];
-    if (tid == 0)
-        s_cta = atomicAdd(a.fticket, 1u);
-    __syncthreads();
-    const uint32_t cta = s_cta;
+    const uint32_t cta = blockIdx.x;
     const ChunkList inner = interior_list(a, cta);
 
-    const uint64_t rows_ev = (uint64_t)g.n_slices * g.na;
     const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
     const uint64_t it0 = items * cta / gridDim.x, it1 = items * (cta + 1) / gridDim.x;
     uint64_t cached_es = ~0ull;
@@ -783,8 +777,6 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
     // carry state: carry[1] holds global row gP, carry[0] row gP - 1
     bool carry1 = false, carry0 = false, pend = false, pend_hot = false;
     uint64_t gP = 0;
-    bool seam = false;          // the range starts inside a slice
-    uint64_t g_first = 0;       // first global row of the range
 
     for (uint64_t item = it0; item < it1; ++item) {
         const uint32_t k = (uint32_t)(item % c.strips);
@@ -805,10 +797,6 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
             const uint32_t pr = min(rpass, rows - p0);
             const uint32_t iA = i0 + p0;
             const uint64_t gA = es * g.na + iA;
-            if (item == it0 && p0 == 0) {
-                g_first = gA;
-                seam = iA > 0;
-            }
             if (carry1 && gP + 1 != gA)
                 carry1 = carry0 = false;          // a new slice starts
             // ---- vote -------------------------------------------------------
@@ -907,55 +895,137 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
         }
     }
     flush_chunk(a, ss, pbuf, buf_n, nseq, inner, w.status);
-    // ---- publish: every row of the range is in M_H ---------------------------
-    __threadfence();
-    __syncthreads();
-    if (tid == 0)
-        atomicExch(&a.done[cta], a.epoch);
-    // ---- the seam with the previous CTA --------------------------------------
-    uint32_t nbnd = 0;
-    const ChunkList seam_list{a.desc_bnd + (size_t)cta * kSeamChunks, kSeamChunks};
-    if (seam) {
-        if (tid == 0) {
-            uint32_t ok = 0;
-            const uint64_t t0 = global_ns();
-            for (uint32_t it = 0; it < kWaitIters; ++it) {
-                if (atomicAdd(&a.done[cta - 1], 0u) == a.epoch) {
-                    ok = 1;
-                    break;
-                }
-                if ((it & 255u) == 0 && global_ns() - t0 > kWaitNs)
-                    break;
-            }
-            if (!ok)
-                atomicOr(w.status, (uint32_t)ST_WAIT_TIMEOUT);
-            __threadfence();
-            s_ok = ok;
-        }
-        __syncthreads();
-        if (s_ok) {
-            // rows gQ - 1 (previous CTA's last) and gQ (our first) of one slice
-            const uint64_t gQ = g_first;
-            const uint32_t ev = (uint32_t)(gQ / rows_ev);
-            const uint64_t gl = gQ - (uint64_t)ev * rows_ev;      // row within the event
-            const uint32_t iQ = (uint32_t)(gQ % g.na);
-            const uint32_t *base = w.M + gQ * nb;
-            const RowRef none{nullptr, 0u, 0u};
-            const RowRef rP{base - nb, 4u, 0u}, rQ{base, 4u, 0u};
-            const RowRef upP = iQ >= 2 ? RowRef{base - 2 * nb, 4u, 0u} : none;
-            const RowRef dnQ = iQ + 1 < g.na ? RowRef{base + nb, 4u, 0u} : none;
-            const uint32_t lin_Q = (uint32_t)(gl * nb);
-            // two rows hold at most n_b peaks: with K >= n_b the seam list
-            // needs at most kSeamChunks chunks
-            test_row_ref(g, a, ss, pbuf, buf_n, nbnd, total, seam_list, w.status, upP, rP, rQ, lin_Q - nb, ev);
-            test_row_ref(g, a, ss, pbuf, buf_n, nbnd, total, seam_list, w.status, rP, rQ, dnQ, lin_Q, ev);
-            flush_chunk(a, ss, pbuf, buf_n, nbnd, seam_list, w.status);
-        }
+    if (tid == 0) {
+        a.cta_nbnd[cta] = 0u;
+        a.cta_nseq[cta] = min(nseq, a.seq_max);
+        a.cta_total[cta] = total;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_seam: after k_fill_scan (same grid), the two rows at the seam of each
+// fused-fill CTA whose range starts inside a slice: the previous CTA's last
+// row P and this CTA's first row Q, tested from M_H in HBM (all written by
+// now).  Their peaks become the CTA's seam chunks, ordered before its
+// interior chunks.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_seam(Geom g, Work w, FillCfg c, ScanArgs a)
+{
+    extern __shared__ uint4 sm4[];
+    ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
+    uint4 *pbuf = sm4 + 16;
+    const uint32_t tid = threadIdx.x, cta = blockIdx.x, nb = g.nb;
+    const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
+    const uint64_t it0 = items * cta / gridDim.x;
+    const uint64_t es = it0 / c.strips;
+    const uint32_t iQ = (uint32_t)(it0 % c.strips) * c.W;   // first row of the range
+    uint32_t nbnd = 0, total = 0, buf_n = 0;
+    if (iQ > 0) {
+        const uint32_t s = (uint32_t)(es % g.n_slices), ev = (uint32_t)(es / g.n_slices);
+        const uint32_t *base = w.M + (size_t)ev * w.n_cells + ((size_t)s * g.na + iQ) * nb;
+        const RowRef none{nullptr, 0u, 0u};
+        const RowRef rP{base - nb, 4u, 0u}, rQ{base, 4u, 0u};
+        const RowRef upP = iQ >= 2 ? RowRef{base - 2 * nb, 4u, 0u} : none;
+        const RowRef dnQ = iQ + 1 < g.na ? RowRef{base + nb, 4u, 0u} : none;
+        const uint32_t lin_Q = (s * g.na + iQ) * nb;
+        const ChunkList seam_list{a.desc_bnd + (size_t)cta * kSeamChunks, kSeamChunks};
+        // two rows hold at most n_b peaks: with K >= n_b a few chunks suffice
+        test_row_ref(g, a, ss, pbuf, buf_n, nbnd, total, seam_list, w.status, upP, rP, rQ, lin_Q - nb, ev);
+        test_row_ref(g, a, ss, pbuf, buf_n, nbnd, total, seam_list, w.status, rP, rQ, dnQ, lin_Q, ev);
+        flush_chunk(a, ss, pbuf, buf_n, nbnd, seam_list, w.status);
     }
     if (tid == 0) {
         a.cta_nbnd[cta] = min(nbnd, kSeamChunks);
-        a.cta_nseq[cta] = min(nseq, a.seq_max);
-        a.cta_total[cta] = total;
+        a.cta_total[cta] += total;
+    }
+}
+
+// Ascending bitonic sort of n <= kCand words in shared memory (block-wide).
+__device__ void sort_u32(uint32_t *s, uint32_t n)
+{
+    if (n < 2)
+        return;
+    uint32_t P = 1;
+    while (P < n)
+        P <<= 1;
+    for (uint32_t i = n + threadIdx.x; i < P; i += blockDim.x)
+        s[i] = 0xffffffffu;
+    __syncthreads();
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                const uint32_t l = i ^ j;
+                if (l > i) {
+                    const uint32_t x = s[i], y = s[l];
+                    if ((x > y) == ((i & k) == 0)) {
+                        s[i] = y;
+                        s[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Ordered compaction of one entry per thread (has = 0 or 1): appends the
+// entries to pbuf in thread order and counts them for their events.
+__device__ __forceinline__ void compact_entry(ScanSmem &ss, uint4 *pbuf, uint32_t &buf_n, uint32_t has,
+                                              const uint4 &ent, uint32_t *ev_count)
+{
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+    const uint32_t nw = (blockDim.x + 31) >> 5;
+    const uint32_t incl = warp_incl_scan(has);
+    if (lane == 31u)
+        ss.wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = lane < nw ? ss.wsum[lane] : 0u;
+        const uint32_t vi = warp_incl_scan(v);
+        ss.wsum[lane] = vi - v;
+        if (lane == 31u)
+            ss.round_total = vi;
+    }
+    __syncthreads();
+    if (has) {
+        pbuf[buf_n + ss.wsum[warp] + incl - 1] = ent;
+        atomicAdd(&ev_count[ent.y], 1u);
+    }
+    buf_n += ss.round_total;
+    __syncthreads();
+}
+
+// Test sorted candidate cells (run-local indices from global row g0) against
+// their neighbours in M_H and append the peaks in order.
+__device__ void test_candidates(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss, uint4 *pbuf,
+                                uint32_t &buf_n, uint32_t &nseq, uint32_t &total, uint64_t g0,
+                                const uint32_t *cand, uint32_t n)
+{
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb;
+    const uint64_t rows_ev = (uint64_t)g.n_slices * g.na;
+    for (uint32_t base = 0; base < n; base += bd) {
+        const uint32_t k = base + tid;
+        uint32_t has = 0;
+        uint4 ent = make_uint4(0u, 0u, 0u, 0u);
+        if (k < n) {
+            const uint32_t idx = cand[k];
+            const uint64_t gr = g0 + idx / nb;
+            const uint32_t j = idx % nb;
+            const uint32_t i = (uint32_t)(gr % g.na);
+            const uint32_t ev = (uint32_t)(gr / rows_ev);
+            const uint32_t *row = w.M + gr * nb;
+            const uint32_t v = row[j];
+            if (is_peak(row, i > 0 ? row - nb : nullptr, i + 1 < g.na ? row + nb : nullptr, j, nb, v)) {
+                has = 1;
+                ent = make_uint4((uint32_t)((gr - (uint64_t)ev * rows_ev) * nb) + j, ev, v, 0u);
+            }
+        }
+        if (__syncthreads_or(has)) {
+            if (buf_n + bd > a.K)
+                flush_chunk(a, ss, pbuf, buf_n, nseq, interior_list(a, blockIdx.x), w.status);
+            compact_entry(ss, pbuf, buf_n, has, ent, a.ev_count);
+            total += ss.round_total;
+        }
     }
 }
 
@@ -974,12 +1044,17 @@ __global__ void __launch_bounds__(256) k_scan_ldg(Geom g, Work w, ScanArgs a)
     const uint64_t g0 = G * blockIdx.x / gridDim.x, g1 = G * (blockIdx.x + 1) / gridDim.x;
     const uint32_t RC = a.R;
     uint32_t buf_n = 0, nseq = 0, total = 0;
-    // pass 1: stream the run with no block barrier; mark chunks holding a
-    // cell >= T in a shared bitmap (one bit per chunk of RC rows)
+    // pass 1: stream the run with no block barrier; collect the cells >= T
+    // (run-local index) in a shared list, and mark their chunks (RC rows) in
+    // a shared bitmap for when the list overflows
     uint32_t *hot = reinterpret_cast<uint32_t *>(pbuf + a.K);
+    uint32_t *cand = hot + a.hot_words;
+    __shared__ uint32_t s_ncand;
     const uint64_t n_chunks = (g1 - g0 + RC - 1) / RC;
     for (uint32_t k = tid; k < (n_chunks + 31) / 32; k += bd)
         hot[k] = 0u;
+    if (tid == 0)
+        s_ncand = 0u;
     __syncthreads();
     const uint4 *run = reinterpret_cast<const uint4 *>(w.M + g0 * nb);
     const uint64_t n4 = (g1 - g0) * nb4, per_chunk = (uint64_t)RC * nb4;
@@ -993,17 +1068,33 @@ __global__ void __launch_bounds__(256) k_scan_ldg(Geom g, Work w, ScanArgs a)
 #pragma unroll
         for (uint32_t q = 0; q < kLdgUPT; ++q)
             if (max(max(v[q].x, v[q].y), max(v[q].z, v[q].w)) >= T) {
-                const uint64_t c = (u0 + (uint64_t)q * bd + tid) / per_chunk;
+                const uint64_t u = u0 + (uint64_t)q * bd + tid;
+                const uint64_t c = u / per_chunk;
                 atomicOr(&hot[c >> 5], 1u << (c & 31u));
+                const uint32_t vv[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+                for (uint32_t m = 0; m < 4; ++m)
+                    if (vv[m] >= T) {
+                        const uint32_t p = atomicAdd(&s_ncand, 1u);
+                        if (p < kCand)
+                            cand[p] = (uint32_t)(4 * u + m);
+                    }
             }
     }
     __syncthreads();
-    // pass 2: neighbour tests and ordered compaction on the marked chunks only
-    for (uint64_t c = 0; c < n_chunks; ++c) {
-        if (!((hot[c >> 5] >> (c & 31u)) & 1u))
-            continue;
-        const uint64_t ra = g0 + c * RC, rb = min(ra + RC, g1);
-        scan_rows_slow<4>(g, w, a, ss, pbuf, buf_n, nseq, total, ra, rb, w.M, 0);
+    const uint32_t n_cand = s_ncand;
+    if (n_cand <= kCand && (g1 - g0) * nb < (1ull << 32)) {
+        // pass 2: the candidates in linear order, tested one per thread
+        sort_u32(cand, n_cand);
+        test_candidates(g, w, a, ss, pbuf, buf_n, nseq, total, g0, cand, n_cand);
+    } else {
+        // too many: detailed pass over the marked chunks
+        for (uint64_t c = 0; c < n_chunks; ++c) {
+            if (!((hot[c >> 5] >> (c & 31u)) & 1u))
+                continue;
+            const uint64_t ra = g0 + c * RC, rb = min(ra + RC, g1);
+            scan_rows_slow<4>(g, w, a, ss, pbuf, buf_n, nseq, total, ra, rb, w.M, 0);
+        }
     }
     flush_chunk(a, ss, pbuf, buf_n, nseq, interior_list(a, blockIdx.x), w.status);
     if (tid == 0) {
@@ -1123,6 +1214,17 @@ cudaError_t launch_fill_scan(const Geom &g, const Work &w, const FillCfg &c, con
     return cudaGetLastError();
 }
 
+cudaError_t launch_seam(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
+                        cudaStream_t st)
+{
+    const size_t smem = 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4);
+    cudaError_t e = cudaFuncSetAttribute(k_seam, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    k_seam<<<grid, 256, smem, st>>>(g, w, c, a);
+    return cudaGetLastError();
+}
+
 cudaError_t fill_scan_occupancy(const FillCfg &c, const ScanArgs &a, uint32_t nb, int *blocks_per_sm)
 {
     const size_t smem = fill_scan_smem_bytes(c, a, nb);
@@ -1164,7 +1266,7 @@ cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t grid, cudaS
 size_t scan_smem_bytes(const ScanArgs &a)
 {
     return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)a.S * a.slot_words * 4 +
-           (size_t)a.hot_words * 4;
+           (size_t)a.hot_words * 4 + (a.hot_words ? (size_t)kCand * 4 : 0);
 }
 
 static const void *scan_kernel(int kind)
