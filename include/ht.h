@@ -198,6 +198,15 @@ typedef struct {
 ht_status ht_set_tuning(ht_ctx *ctx, const ht_tuning *tuning);
 ht_status ht_get_tuning(ht_ctx *ctx, ht_tuning *tuning);
 
+/* Autotuner: re-runs the hits of the last (non-accumulating) ht_fill under
+ * candidate launch shapes -- fused or two-kernel fill, tile rows, threads,
+ * scan variant -- reps times each, and keeps the fastest.  M_H and the
+ * result of a following ht_find_maxima are those of the last fill.  chosen
+ * (may be NULL) receives the shapes in effect, us_per_event (may be NULL)
+ * the device time per event of fill + maxima.  Blocks.  Errors: HT_E_INVAL
+ * (no fill yet, or the last fill accumulated), HT_E_CUDA, HT_E_NOMEM. */
+ht_status ht_autotune(ht_ctx *ctx, uint32_t reps, ht_tuning *chosen, double *us_per_event);
+
 /* ------------------------------------------------------------------------ */
 /* Host-only helpers (no device needed).                                     */
 /* ------------------------------------------------------------------------ */

@@ -325,6 +325,22 @@ ht_status ht_get_tuning(ht_ctx *ctx, ht_tuning *t)
     return HT_OK;
 }
 
+ht_status ht_autotune(ht_ctx *ctx, uint32_t reps, ht_tuning *chosen, double *us_per_event)
+{
+    ht_status s = check_ctx(ctx);
+    if (s != HT_OK)
+        return s;
+    std::string why;
+    s = hte::engine_autotune(ctx->E, reps, ctx->stream, us_per_event, &why);
+    if (s == HT_E_CUDA)
+        ctx->poisoned = true;
+    if (s != HT_OK)
+        return set_err(s, why);
+    if (chosen)
+        return ht_get_tuning(ctx, chosen);
+    return HT_OK;
+}
+
 ht_status ht_profile(ht_ctx *ctx, int enable)
 {
     ht_status s = check_ctx(ctx);

@@ -486,6 +486,19 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
         return e;
     ++E.launches;
     E.ctr_dirty = false;   // k_bin zeroed the counters
+    E.last_hit_off = d_hit_off;
+    E.last_n_hits0 = n_hits0;
+    E.last_n_events = n_events;
+    E.last_accumulate = (flags & HT_ACCUMULATE) != 0;
+    return engine_vote(E, d_hit_off, n_hits0, n_events, flags, st);
+}
+
+cudaError_t engine_vote(Engine &E, const uint32_t *d_hit_off, uint32_t n_hits0, uint32_t n_events, uint32_t flags,
+                        cudaStream_t st)
+{
+    htk::Work w = make_work(E, nullptr, nullptr, nullptr, d_hit_off, n_hits0, n_events);
+    cudaError_t e;
+    E.fused_valid = false;
     const bool accumulate = (flags & HT_ACCUMULATE) != 0;
     if ((flags & HT_FILL_NAIVE) || !E.fill_priv_ok) {
         if (!accumulate) {
@@ -576,6 +589,101 @@ cudaError_t engine_scan(Engine &E, uint32_t n_events, htk::Peak *out, uint32_t c
     ++E.launches;
     E.ctr_dirty = false;   // the order kernel's last CTA zeroes them
     return e;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner
+// ---------------------------------------------------------------------------
+ht_status engine_autotune(Engine &E, uint32_t reps, cudaStream_t st, double *best_us, std::string *why)
+{
+    if (!E.last_n_events) {
+        *why = "autotune needs a previous fill (it re-times that fill's hits)";
+        return HT_E_INVAL;
+    }
+    if (E.last_accumulate) {
+        *why = "autotune re-runs the last fill alone: not after an accumulating fill";
+        return HT_E_INVAL;
+    }
+    reps = std::max<uint32_t>(reps, 1);
+    const uint32_t n_events = E.last_n_events;
+    uint32_t *d_counts = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_counts, (size_t)n_events * 4)) != cudaSuccess ||
+        (e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess) {
+        cudaFree(d_counts);
+        cudaGetLastError();
+        *why = std::string("autotune set-up failed: ") + cudaGetErrorString(e);
+        return HT_E_NOMEM;
+    }
+    const Tuning user = E.tune;
+    const bool prof_on = E.prof.on;
+    E.prof.on = false;
+
+    // candidates: fused / two-kernel fill, tile rows, threads, scan variant
+    std::vector<Tuning> cands;
+    const uint32_t rows_opts[] = {16, 32};
+    const uint32_t thr_opts[] = {256, 512};
+    for (uint32_t fused = 1; fused <= 2; ++fused)
+        for (uint32_t W : rows_opts)
+            for (uint32_t th : thr_opts)
+                for (uint32_t kind = 1; kind <= (fused == 2 ? 2u : 1u); ++kind) {
+                    Tuning t = user;
+                    t.fused = fused;
+                    t.fill_W = W;
+                    t.fill_threads = th;
+                    t.scan_kind = fused == 2 ? (kind == 1 ? 2u : 1u) : user.scan_kind;
+                    cands.push_back(t);
+                }
+
+    double best = 1e30;
+    Tuning chosen = user;
+    ht_status st_out = HT_OK;
+    for (const Tuning &t : cands) {
+        E.tune = t;
+        std::string w2;
+        if (engine_configure(E, &w2) != HT_OK)
+            continue;                            // shape does not fit this binning
+        bool ok = true;
+        float ms = 0.f;
+        for (uint32_t r = 0; r < reps + 2 && ok; ++r) {
+            if (r == 2 && cudaEventRecord(t0, st) != cudaSuccess)
+                ok = false;
+            ok = ok && engine_vote(E, E.last_hit_off, E.last_n_hits0, n_events, 0u, st) == cudaSuccess &&
+                 engine_scan(E, n_events, nullptr, 0u, d_counts, st) == cudaSuccess;
+        }
+        ok = ok && cudaEventRecord(t1, st) == cudaSuccess && cudaEventSynchronize(t1) == cudaSuccess &&
+             cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess;
+        if (!ok) {
+            *why = std::string("autotune run failed: ") + cudaGetErrorString(cudaGetLastError());
+            st_out = HT_E_CUDA;
+            break;
+        }
+        const double us = 1e3 * ms / reps / n_events;
+        if (us < best) {
+            best = us;
+            chosen = t;
+        }
+    }
+    E.tune = st_out == HT_OK ? chosen : user;
+    std::string w3;
+    if (engine_configure(E, &w3) != HT_OK && st_out == HT_OK) {
+        *why = w3;
+        st_out = HT_E_CUDA;
+    }
+    // leave M_H and the peak state as a fill with the chosen tuning leaves them
+    if (st_out == HT_OK && engine_vote(E, E.last_hit_off, E.last_n_hits0, n_events, 0u, st) != cudaSuccess) {
+        *why = "autotune final fill failed";
+        st_out = HT_E_CUDA;
+    }
+    cudaStreamSynchronize(st);
+    E.prof.on = prof_on;
+    cudaFree(d_counts);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (best_us)
+        *best_us = best;
+    return st_out;
 }
 
 } // namespace hte

@@ -73,6 +73,9 @@ struct Engine {
     uint32_t fused_grid_used = 0;
     uint32_t fused_events = 0;
     bool ctr_dirty = false;      // counters hold an unconsumed fused fill's peaks
+    const uint32_t *last_hit_off = nullptr;   // what the last fill binned
+    uint32_t last_n_hits0 = 0, last_n_events = 0;
+    bool last_accumulate = false;
 
     float *d_edges = nullptr;
     uint32_t *d_M = nullptr;
@@ -107,6 +110,16 @@ ht_status engine_configure(Engine &E, std::string *why);
 cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *z,
                         const uint32_t *d_hit_off, uint32_t n_hits0, uint32_t n_events,
                         uint32_t n_total, uint32_t flags, cudaStream_t st);
+
+// The voting part of engine_fill alone, on the hits engine_fill last binned
+// (the autotuner re-runs it under each candidate tuning).
+cudaError_t engine_vote(Engine &E, const uint32_t *d_hit_off, uint32_t n_hits0, uint32_t n_events, uint32_t flags,
+                        cudaStream_t st);
+
+// Time candidate tunings on the hits of the last fill (vote + maxima, reps
+// times each) and keep the fastest; M_H and the peak state end as after a
+// fill with the chosen tuning.  *best_us receives its time per event.
+ht_status engine_autotune(Engine &E, uint32_t reps, cudaStream_t st, double *best_us, std::string *why);
 
 // Step 2: peaks of every event into out[e * capacity ...], totals into counts[e].
 cudaError_t engine_scan(Engine &E, uint32_t n_events, htk::Peak *out, uint32_t capacity,

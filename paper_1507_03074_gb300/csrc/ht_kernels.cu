@@ -748,6 +748,53 @@ __device__ __forceinline__ RowRef tile_row(const uint32_t *tile, uint32_t r, uin
     return x;
 }
 
+// Copy tile row r (u16 or u32 counters, swizzled) into a plain u32 row.
+__device__ __forceinline__ void copy_tile_row(uint32_t *dst, const uint32_t *tile, uint32_t r, uint32_t pitch,
+                                              bool u16, uint32_t nb)
+{
+    const uint32_t *row = tile + r * pitch;
+    if (u16) {
+        const uint32_t sw = row_hash(r) & 0x1Eu;
+        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x)
+            dst[j] = (row[(j >> 1) ^ sw] >> ((j & 1u) << 4)) & 0xffffu;
+    } else {
+        const uint32_t sw = row_hash(r) & 0x1Cu;
+        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x)
+            dst[j] = row[j ^ sw];
+    }
+}
+
+// Peak tests of one pass of the fused fill (taken only when a row to test
+// holds a cell >= T; kept out of line so the vote loop keeps its registers):
+// the pending last row of the previous pass (carry[1], with carry[0] above
+// it when up_ok), then the tile rows r_first .. r_last marked in rows.
+__device__ __noinline__ void fused_test_rows(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss,
+                                             uint4 *pbuf, uint32_t &buf_n, uint32_t &nseq, uint32_t &total,
+                                             const ChunkList &inner, const uint32_t *tile, const uint32_t *carry,
+                                             uint32_t pitch, bool u16, bool pend, bool up_ok, uint64_t rows,
+                                             uint32_t r_first, int32_t r_last, uint32_t iA, uint32_t row_lin_base,
+                                             uint32_t e)
+{
+    const uint32_t nb = g.nb;
+    const RowRef none{nullptr, 0u, 0u};
+    if (pend) {
+        const RowRef up = up_ok ? RowRef{carry, 1u, 0u} : none;
+        test_row_ref(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, up, RowRef{carry + nb, 1u, 0u},
+                     tile_row(tile, 0, pitch, u16), row_lin_base - nb, e);
+    }
+    for (int32_t rr = (int32_t)r_first; rr <= r_last; ++rr) {
+        if (!((rows >> rr) & 1ull))
+            continue;
+        RowRef up = none, dn = none;
+        if (iA + rr > 0)
+            up = rr > 0 ? tile_row(tile, rr - 1, pitch, u16) : RowRef{carry + nb, 1u, 0u};
+        if (iA + rr + 1 < g.na)
+            dn = tile_row(tile, rr + 1, pitch, u16);
+        test_row_ref(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, up, tile_row(tile, rr, pitch, u16), dn,
+                     row_lin_base + (uint32_t)rr * nb, e);
+    }
+}
+
 __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, ScanArgs a)
 {
     extern __shared__ uint4 sm4[];
@@ -847,42 +894,21 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
             for (int32_t rr = (int32_t)r_first; rr <= r_last; ++rr)
                 want |= 1ull << rr;
             const uint32_t row_lin_base = (uint32_t)((uint64_t)s * g.na + iA) * nb;
-            if ((test_pend && pend_hot) || (hotm & want)) {
-                const RowRef none{nullptr, 0u, 0u};
-                if (test_pend && pend_hot) {
-                    RowRef up{carry, 1u, 0u}, row{carry + nb, 1u, 0u};
-                    if (!carry0 || (gP % g.na) == 0)
-                        up = none;
-                    test_row_ref(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, up, row,
-                                 tile_row(tile, 0, pitch, u16), row_lin_base - nb, e);
-                }
-                for (int32_t rr = (int32_t)r_first; rr <= r_last; ++rr) {
-                    if (!((hotm >> rr) & 1ull))
-                        continue;
-                    RowRef up = none, dn = none;
-                    if (iA + rr > 0)
-                        up = rr > 0 ? tile_row(tile, rr - 1, pitch, u16) : RowRef{carry + nb, 1u, 0u};
-                    if (iA + rr + 1 < g.na)
-                        dn = tile_row(tile, rr + 1, pitch, u16);
-                    test_row_ref(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, up,
-                                 tile_row(tile, rr, pitch, u16), dn, row_lin_base + (uint32_t)rr * nb, e);
-                }
-            }
+            if ((test_pend && pend_hot) || (hotm & want))
+                fused_test_rows(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, carry, pitch, u16,
+                                test_pend && pend_hot, carry0 && (gP % g.na) != 0, hotm & want, r_first, r_last,
+                                iA, row_lin_base, e);
             // ---- carry the last two rows; clear the tile --------------------
             __syncthreads();
             if (pr >= 2) {
-                const RowRef ra_ = tile_row(tile, pr - 2, pitch, u16), rb_ = tile_row(tile, pr - 1, pitch, u16);
-                for (uint32_t j = tid; j < nb; j += bd) {
-                    carry[j] = ra_.get(j);
-                    carry[nb + j] = rb_.get(j);
-                }
+                copy_tile_row(carry, tile, pr - 2, pitch, u16, nb);
+                copy_tile_row(carry + nb, tile, pr - 1, pitch, u16, nb);
                 carry0 = true;
             } else {
-                const RowRef rb_ = tile_row(tile, 0, pitch, u16);
-                for (uint32_t j = tid; j < nb; j += bd) {
+                for (uint32_t j = tid; j < nb; j += bd)
                     carry[j] = carry[nb + j];
-                    carry[nb + j] = rb_.get(j);
-                }
+                __syncthreads();
+                copy_tile_row(carry + nb, tile, 0, pitch, u16, nb);
                 carry0 = carry1;
             }
             carry1 = true;

@@ -124,6 +124,7 @@ def lib():
         "ht_profile_read": ([P, P, U32, P], I),
         "ht_compute_b_thresholds": ([ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), P], I),
         "ht_set_tuning": ([P, ctypes.POINTER(c_tuning)], I),
+        "ht_autotune": ([P, U32, ctypes.POINTER(c_tuning), ctypes.POINTER(ctypes.c_double)], I),
         "ht_get_tuning": ([P, ctypes.POINTER(c_tuning)], I),
     }
     for name, (args, res) in sig.items():
@@ -240,6 +241,13 @@ class Context:
         if kw:
             raise TypeError(f"unknown tuning fields {sorted(kw)}")
         check(lib().ht_set_tuning(self._h, ctypes.byref(t)))
+
+    def autotune(self, reps: int = 5):
+        """ht_autotune: time launch shapes on the last fill's hits and keep the
+        fastest.  Returns (chosen tuning dict, microseconds per event)."""
+        t, us = c_tuning(), ctypes.c_double()
+        check(lib().ht_autotune(self._h, reps, ctypes.byref(t), ctypes.byref(us)))
+        return {n: int(getattr(t, n)) for n in TUNING_FIELDS}, float(us.value)
 
     def get_tuning(self) -> dict:
         t = c_tuning()

@@ -405,3 +405,26 @@ def test_fused_state_sequences(ht, paper_ref, tuning):
         pk, n = ctx.find_maxima(capacity=1 << 16)
         assert n == n_ref
         assert_peaks_equal(pk, pk_ref)
+
+
+def test_autotune_keeps_results(ht, paper_ref):
+    ev, M_ref, pk_ref, n_ref = paper_ref
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    with ht.Context(b, r, threshold=10, max_hits=6000) as ctx:
+        with pytest.raises(ht.HTError):
+            ctx.autotune()                        # nothing filled yet
+        ctx.fill(ev.x, ev.y, ev.z)
+        chosen, us = ctx.autotune(reps=3)
+        assert us > 0 and chosen["fill_fused_scan"] in (1, 2)
+        assert np.array_equal(ctx.matrix(), M_ref)
+        pk, n = ctx.find_maxima(capacity=1 << 16)
+        assert n == n_ref
+        assert_peaks_equal(pk, pk_ref)
+        # later fills run with the chosen shapes
+        ctx.fill(ev.x[::-1].copy(), ev.y[::-1].copy(), ev.z[::-1].copy())
+        pk, n = ctx.find_maxima(capacity=1 << 16)
+        assert n == n_ref
+        assert_peaks_equal(pk, pk_ref)
+        ctx.fill(ev.x[:100], ev.y[:100], ev.z[:100], accumulate=True)
+        with pytest.raises(ht.HTError):
+            ctx.autotune()                        # last fill accumulated
