@@ -193,23 +193,29 @@ __device__ __forceinline__ void flush_rows(const Geom &g, uint32_t *tile, uint32
 // Select, from hit `pos` on in [pos, h1), the hits admitted to slice
 // (ts, ps) into hs[0 .. returned count), kSelHPT hits per thread and
 // iteration (codes and records loaded up front, so one global latency per
-// iteration), stopping before fewer than kSelHPT * blockDim free entries
-// would remain.  Advances `pos` (uniform) by at least kSelHPT * blockDim
-// while pos < h1: the caller guarantees cap >= kSelHPT * blockDim.
+// iteration), stopping at the first block of hits whose admitted hits no
+// longer fit in cap.  Advances `pos` (uniform) by at least kSelHPT *
+// blockDim while pos < h1: the caller guarantees cap >= kSelHPT * blockDim.
 constexpr uint32_t kSelHPT = 2;
 
 __device__ __forceinline__ uint32_t select_hits(const Geom &g, const Work &w, float4 *hs, uint32_t cap,
                                                 uint32_t &pos, uint32_t h1, uint32_t ts, uint32_t ps,
-                                                uint32_t *s_n)
+                                                uint32_t *s_cnt /* 3 words */)
 {
     const uint32_t tid = threadIdx.x, bd = blockDim.x, lane = tid & 31u;
     const uint32_t lt = (1u << lane) - 1u;
     __syncthreads();
     if (tid == 0)
-        *s_n = 0;
+        s_cnt[0] = s_cnt[1] = s_cnt[2] = 0u;
     __syncthreads();
     uint32_t n = 0;
-    while (pos < h1 && n + kSelHPT * bd <= cap) {
+    // Each block of kSelHPT * blockDim hits is counted first and taken only
+    // if it fits; one block always fits an empty buffer (cap >= that size).
+    // Block i counts in s_cnt[i % 3]; s_cnt[(i + 1) % 3] is cleared at the
+    // start of block i (its last readers finished before block i-1's barrier).
+    for (uint32_t it = 0; pos < h1; ++it) {
+        if (tid == 0)
+            s_cnt[(it + 1) % 3] = 0u;
         uint32_t code[kSelHPT];
         float4 hv[kSelHPT];
 #pragma unroll
@@ -226,18 +232,20 @@ __device__ __forceinline__ uint32_t select_hits(const Geom &g, const Work &w, fl
         }
         uint32_t base = 0;
         if (lane == 0 && tot)
-            base = atomicAdd(s_n, tot);
+            base = atomicAdd(&s_cnt[it % 3], tot);
         base = __shfl_sync(0xffffffffu, base, 0);
+        __syncthreads();     // every warp has added its count
+        const uint32_t total = s_cnt[it % 3];
+        if (n + total > cap)
+            break;           // uniform: the block does not fit; leave pos on it
 #pragma unroll
         for (uint32_t q = 0; q < kSelHPT; ++q) {
             if (m[q] & (1u << lane))
-                hs[base + __popc(m[q] & lt)] = hv[q];
+                hs[n + base + __popc(m[q] & lt)] = hv[q];
             base += __popc(m[q]);
         }
+        n += total;
         pos += kSelHPT * bd;
-        __syncthreads();     // every warp has added its count
-        n = *s_n;
-        __syncthreads();     // every thread has read it before the next atomics
     }
     return n;
 }
@@ -245,7 +253,7 @@ __device__ __forceinline__ uint32_t select_hits(const Geom &g, const Work &w, fl
 __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
 {
     extern __shared__ uint4 sm4[];
-    __shared__ uint32_t s_n;
+    __shared__ uint32_t s_sel[3];
     uint32_t *tile = reinterpret_cast<uint32_t *>(sm4);
     float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
     float *beta = reinterpret_cast<float *>(hs + c.HC);
@@ -294,7 +302,7 @@ __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
                 uint32_t pos = h0;
                 bool first = true;
                 while (first || pos < h1) {
-                    const uint32_t nsel = select_hits(g, w, hs, c.HC, pos, h1, ts, ps, &s_n);
+                    const uint32_t nsel = select_hits(g, w, hs, c.HC, pos, h1, ts, ps, s_sel);
                     if (first && pos >= h1) {
                         cached_es = es;   // the whole selection fits: keep it
                         cached_n = nsel;
@@ -805,7 +813,7 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
     float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
     uint32_t *carry = reinterpret_cast<uint32_t *>(hs + c.HC);   // [2][nb]
     float *beta = reinterpret_cast<float *>(carry + 2 * g.nb);     // nb + 1 thresholds
-    __shared__ uint32_t s_n, s_hot[2];
+    __shared__ uint32_t s_sel[3], s_hot[2];
 
     const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb;
     for (uint32_t k = tid; k < c.tile_words / 4; k += bd)
@@ -861,7 +869,7 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
                 uint32_t pos = h0;
                 bool first = true;
                 while (first || pos < h1) {
-                    const uint32_t nsel = select_hits(g, w, hs, c.HC, pos, h1, ts, ps, &s_n);
+                    const uint32_t nsel = select_hits(g, w, hs, c.HC, pos, h1, ts, ps, s_sel);
                     if (first && pos >= h1) {
                         cached_es = es;
                         cached_n = nsel;
