@@ -247,6 +247,7 @@ __device__ __forceinline__ uint32_t select_hits(const Geom &g, const Work &w, fl
         n += total;
         pos += kSelHPT * bd;
     }
+    __syncthreads();         // the staged hits are visible to every thread
     return n;
 }
 
