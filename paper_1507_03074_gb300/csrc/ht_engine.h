@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ht.h"
+#include "ht.h"   // include/ht.h (the build adds include/ to the search path)
 #include "ht_internal.h"
 
 namespace hte {

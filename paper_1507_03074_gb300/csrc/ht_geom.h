@@ -4,7 +4,7 @@
 #include <cstdint>
 #include <string>
 
-#include "../../include/ht.h"
+#include "ht.h"   // include/ht.h (the build adds include/ to the search path)
 
 namespace htg {
 
