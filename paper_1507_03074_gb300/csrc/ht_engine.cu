@@ -12,7 +12,8 @@ static uint32_t round_up(uint32_t v, uint32_t m) { return (v + m - 1) / m * m; }
 
 static const size_t kSmemMax = 227 * 1024;     // per CTA on sm_100-class parts
 static const uint32_t kScanThreads = 256;
-static const uint32_t kPeakBuf = 1024;         // K: entries buffered per scan / fused CTA
+static const uint32_t kPeakBuf = 1024;         // K: entries buffered per scan / seam CTA
+static const uint32_t kFusedPeakBuf = 512;     // K of a fused-fill CTA (at least its block)
 
 const char *const kKernelNames[K_NKINDS] = {"k_bin", "k_fill_priv", "k_fill_scan", "k_seam", "k_clear",
                                              "k_fill_naive", "k_scan", "k_order"};
@@ -164,27 +165,37 @@ ht_status engine_configure(Engine &E, std::string *why)
     E.naive_grid = (uint32_t)E.num_sms * 16;
 
     // --- fused fill + maxima ---------------------------------------------------
+    // A smaller peak buffer than the scan's (the tile needs the room); k_seam
+    // keeps kPeakBuf in its own launch.
     E.fused_ok = false;
-    E.fused_K = kPeakBuf;
-    if (E.fill_priv_ok && t.fused != 2 && W <= 64 && b.n_b <= 4096 && f.threads / 2 + 1 < kPeakBuf) {
+    E.fused_K = std::max<uint32_t>(kFusedPeakBuf, f.threads);
+    if (E.fill_priv_ok && t.fused != 2 && W <= 64 && b.n_b <= 4096) {
         htk::ScanArgs tmp{};
-        tmp.K = kPeakBuf;
+        tmp.K = E.fused_K;
         htk::FillCfg ff = f;
-        // smaller staging so that two CTAs share an SM, unless tuned explicitly
-        while (!t.fill_HC && ff.HC > 2 * ff.threads && 2 * htk::fill_scan_smem_bytes(ff, tmp, b.n_b) > kSmemMax)
-            ff.HC /= 2;
-        E.fused_fill = ff;
-        if (htk::fill_scan_smem_bytes(ff, tmp, b.n_b) <= kSmemMax) {
-            int occ = 0;
-            cudaError_t e = htk::fill_scan_occupancy(ff, tmp, b.n_b, &occ);
-            if (e == cudaSuccess && occ >= 1) {
-                if (t.fill_blocks_per_sm)
-                    occ = std::min<int>(occ, (int)t.fill_blocks_per_sm);
-                E.fused_ok = true;
-                E.fused_grid = (uint32_t)E.num_sms * (uint32_t)occ;
-            } else {
+        // two CTAs per SM if a staging size (a multiple of the block, at
+        // least two blocks' worth) allows it, unless tuned explicitly
+        int occ = 0;
+        auto occupancy = [&](const htk::FillCfg &c) {
+            int o = 0;
+            if (htk::fill_scan_smem_bytes(c, tmp, b.n_b) > kSmemMax ||
+                htk::fill_scan_occupancy(c, tmp, b.n_b, &o) != cudaSuccess) {
                 cudaGetLastError();
+                return 0;
             }
+            return o;
+        };
+        occ = occupancy(ff);
+        while (!t.fill_HC && occ < 2 && ff.HC > 2 * ff.threads) {
+            ff.HC -= ff.threads;
+            occ = occupancy(ff);
+        }
+        E.fused_fill = ff;
+        if (occ >= 1) {
+            if (t.fill_blocks_per_sm)
+                occ = std::min<int>(occ, (int)t.fill_blocks_per_sm);
+            E.fused_ok = true;
+            E.fused_grid = (uint32_t)E.num_sms * (uint32_t)occ;
         }
     }
     if (t.fused == 1 && !E.fused_ok) {
@@ -248,7 +259,8 @@ ht_status engine_configure(Engine &E, std::string *why)
     uint32_t seq = chunks_for((G_max + scan_grid - 1) / scan_grid + 1, g.nb, s.K, 2 * kScanThreads);
     if (E.fused_ok) {
         const uint64_t fused_rows = ((items_max + fused_grid - 1) / fused_grid) * f.W + 1;
-        seq = std::max(seq, chunks_for(fused_rows, g.nb, kPeakBuf, f.threads / 2 + 1));
+        const uint32_t per_round = std::max(f.threads / 2 + 1, htk::fused_round(f.threads, E.fused_K));
+        seq = std::max(seq, chunks_for(fused_rows, g.nb, E.fused_K, per_round));
     }
     s.seq_max = seq;
     const size_t desc_b = (size_t)grid_cap * seq * 8, bnd_b = (size_t)grid_cap * htk::kSeamChunks * 8;
@@ -528,6 +540,7 @@ cudaError_t engine_vote(Engine &E, const uint32_t *d_hit_off, uint32_t n_hits0, 
         ++E.launches;
         if (e == cudaSuccess) {
             ProfScope ps(E, K_SEAM, st);
+            a.K = kPeakBuf;
             e = htk::launch_seam(E.geom, w, ff, a, grid, st);
             ++E.launches;
         }

@@ -79,6 +79,12 @@ enum : uint32_t { CTR_STATUS = 0, CTR_ENTRIES = 1, CTR_OTICKET = 2, CTR_SPARE = 
 constexpr uint32_t kLdgUPT = 4;
 // Candidate cells (>= threshold) a streaming-scan CTA lists before testing them.
 constexpr uint32_t kCand = 1024;
+// Candidate cells a fused-fill CTA lists per pass (and keeps for the pass's
+// last row); a pass with more falls back to testing whole rows.
+constexpr uint32_t kFusedCand = 256;
+// Peaks the fused fill tests per block round: at most this many per round,
+// so every chunk but the last holds at least K - fused_round(threads, K).
+__host__ __device__ constexpr uint32_t fused_round(uint32_t threads, uint32_t K) { return threads < K / 2 ? threads : K / 2; }
 enum ScanKind { SCAN_DIRECT = 0, SCAN_BULK = 1, SCAN_LDG = 2 };
 cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, int kind, cudaStream_t st);
 cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const OrderArgs &o,

@@ -459,6 +459,33 @@ __device__ __forceinline__ void compact_round(ScanSmem &ss, uint4 *pbuf, uint32_
     __syncthreads();
 }
 
+// Ordered compaction of one entry per thread (has = 0 or 1): appends the
+// entries to pbuf in thread order and counts them for their events.
+__device__ __forceinline__ void compact_entry(ScanSmem &ss, uint4 *pbuf, uint32_t &buf_n, uint32_t has,
+                                              const uint4 &ent, uint32_t *ev_count)
+{
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+    const uint32_t nw = (blockDim.x + 31) >> 5;
+    const uint32_t incl = warp_incl_scan(has);
+    if (lane == 31u)
+        ss.wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = lane < nw ? ss.wsum[lane] : 0u;
+        const uint32_t vi = warp_incl_scan(v);
+        ss.wsum[lane] = vi - v;
+        if (lane == 31u)
+            ss.round_total = vi;
+    }
+    __syncthreads();
+    if (has) {
+        pbuf[buf_n + ss.wsum[warp] + incl - 1] = ent;
+        atomicAdd(&ev_count[ent.y], 1u);
+    }
+    buf_n += ss.round_total;
+    __syncthreads();
+}
+
 // Detailed pass over global rows [ra, rb): candidates, neighbour tests and
 // ordered compaction.  Rows [ra - 1, rb + 1) (clipped) are readable at
 // base + (gr - b_first) * nb.  Each thread takes VEC consecutive cells.
@@ -708,10 +735,12 @@ __device__ void test_row_ref(const Geom &g, const ScanArgs &a, ScanSmem &ss, uin
 }
 
 // Flush the tile rows of one pass to M_H without clearing them; mark rows
-// holding a cell >= T in hot[] (bit r of word r / 32).
+// holding a cell >= T in hot[] (bit r of word r / 32) and list those cells,
+// as r * n_b + j, in cand[] (up to cap; *n_cand counts them all).
 template <bool U16>
 __device__ __forceinline__ void flush_rows_mark(const Geom &g, const uint32_t *tile, uint32_t *dst,
-                                                uint32_t rows, uint32_t pitch, uint32_t *hot)
+                                                uint32_t rows, uint32_t pitch, uint32_t *hot, uint32_t *cand,
+                                                uint32_t *n_cand, uint32_t cap)
 {
     const uint32_t tid = threadIdx.x, bd = blockDim.x, T = g.threshold;
     if ((g.nb & 3u) == 0) {
@@ -729,8 +758,17 @@ __device__ __forceinline__ void flush_rows_mark(const Geom &g, const uint32_t *t
                 v = *reinterpret_cast<const uint4 *>(&tile[r * pitch + ((4u * c4) ^ (row_hash(r) & 0x1Cu))]);
             }
             reinterpret_cast<uint4 *>(dst)[u] = v;
-            if (max(max(v.x, v.y), max(v.z, v.w)) >= T)
+            if (max(max(v.x, v.y), max(v.z, v.w)) >= T) {
                 atomicOr(&hot[r >> 5], 1u << (r & 31u));
+                const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (uint32_t m = 0; m < 4; ++m)
+                    if (vv[m] >= T) {
+                        const uint32_t p = atomicAdd(n_cand, 1u);
+                        if (p < cap)
+                            cand[p] = r * g.nb + 4u * c4 + m;
+                    }
+            }
         }
     } else {
         const uint32_t units = rows * g.nb;
@@ -742,8 +780,144 @@ __device__ __forceinline__ void flush_rows_mark(const Geom &g, const uint32_t *t
             else
                 v = tile[r * pitch + (j ^ (row_hash(r) & 0x1Cu))];
             dst[u] = v;
-            if (v >= T)
+            if (v >= T) {
                 atomicOr(&hot[r >> 5], 1u << (r & 31u));
+                const uint32_t p = atomicAdd(n_cand, 1u);
+                if (p < cap)
+                    cand[p] = u;
+            }
+        }
+    }
+}
+
+// A cell of a row kept as plain u32 (kind 1), u16 tile (kind 2) or u32 tile
+// (kind 3) with row swizzle sw.  Arguments in registers: no local memory.
+__device__ __forceinline__ uint32_t cell_at(const uint32_t *p, uint32_t kind, uint32_t sw, uint32_t j)
+{
+    if (kind == 1u)
+        return p[j];
+    if (kind == 2u)
+        return (p[(j >> 1) ^ sw] >> ((j & 1u) << 4)) & 0xffffu;
+    return p[j ^ sw];
+}
+
+// Peak test of cell j with value v; up / dn absent when their kind is 0.
+__device__ __forceinline__ bool peak_at(const uint32_t *rp, uint32_t rk, uint32_t rs, const uint32_t *up,
+                                        uint32_t uk, uint32_t us, const uint32_t *dp, uint32_t dk, uint32_t ds,
+                                        uint32_t j, uint32_t nb, uint32_t v)
+{
+    const bool hl = j > 0, hr = j + 1 < nb;
+    if (uk) {
+        if (hl && !(v > cell_at(up, uk, us, j - 1))) return false;
+        if (!(v > cell_at(up, uk, us, j))) return false;
+        if (hr && !(v > cell_at(up, uk, us, j + 1))) return false;
+    }
+    if (hl && !(v > cell_at(rp, rk, rs, j - 1))) return false;
+    if (hr && !(v >= cell_at(rp, rk, rs, j + 1))) return false;
+    if (dk) {
+        if (hl && !(v >= cell_at(dp, dk, ds, j - 1))) return false;
+        if (!(v >= cell_at(dp, dk, ds, j))) return false;
+        if (hr && !(v >= cell_at(dp, dk, ds, j + 1))) return false;
+    }
+    return true;
+}
+
+// Sort the n <= kFusedCand candidate keys of a pass into srt (keys are
+// distinct: the rank of a key is the number of smaller ones), then find
+// lo / hi, the first positions holding a key >= t_lo / >= t_hi (n if none).
+__device__ __forceinline__ void rank_sort_bounds(const uint32_t *cand, uint32_t *srt, uint32_t n, uint32_t t_lo,
+                                                 uint32_t t_hi, uint32_t *s_bounds)
+{
+    const uint32_t tid = threadIdx.x, bd = blockDim.x;
+    if (tid == 0)
+        s_bounds[0] = s_bounds[1] = n;
+    for (uint32_t k = tid; k < n; k += bd) {
+        const uint32_t key = cand[k];
+        uint32_t rank = 0;
+        for (uint32_t m = 0; m < n; ++m)
+            rank += cand[m] < key;
+        srt[rank] = key;
+    }
+    __syncthreads();
+    for (uint32_t k = tid; k < n; k += bd) {
+        const uint32_t key = srt[k], prev = k ? srt[k - 1] : 0u;
+        if (key >= t_lo && (k == 0 || prev < t_lo))
+            s_bounds[0] = k;
+        if (key >= t_hi && (k == 0 || prev < t_hi))
+            s_bounds[1] = k;
+    }
+    __syncthreads();
+}
+
+// Peak tests of one fused-fill pass from candidate lists, one cell per
+// thread: first the np pending cells (columns of the previous pass's last
+// row, held in carry[1] with carry[0] above when up_ok and tile row 0 below),
+// then the sorted keys srt[lo, hi) (r * n_b + j for tile row r).  Peaks are
+// appended in linear order.
+__device__ __forceinline__ void fused_test_cands(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss,
+                                                 uint4 *pbuf, uint32_t &buf_n, uint32_t &nseq, uint32_t &total,
+                                                 const ChunkList &inner, const uint32_t *tile,
+                                                 const uint32_t *carry, uint32_t pitch, bool u16,
+                                                 const uint32_t *pl, uint32_t np, bool up_ok, const uint32_t *srt,
+                                                 uint32_t lo, uint32_t hi, uint32_t iA, uint32_t row_lin_base,
+                                                 uint32_t e)
+{
+    const uint32_t tid = threadIdx.x, nb = g.nb;
+    const uint32_t tk = u16 ? 2u : 3u, swm = u16 ? 0x1Eu : 0x1Cu;
+    const uint32_t m = np + (hi > lo ? hi - lo : 0u);
+    const uint32_t rc = fused_round(blockDim.x, a.K);
+    for (uint32_t base = 0; base < m; base += rc) {
+        const uint32_t k = base + tid;
+        uint32_t has = 0;
+        uint4 ent = make_uint4(0u, 0u, 0u, 0u);
+        if (tid < rc && k < m) {
+            const uint32_t *rp, *up = nullptr, *dp = nullptr;
+            uint32_t rk, rs = 0, uk = 0, us = 0, dk = 0, ds = 0, j, lin;
+            if (k < np) {
+                j = pl[k];
+                rp = carry + nb;
+                rk = 1u;
+                if (up_ok) {
+                    up = carry;
+                    uk = 1u;
+                }
+                dp = tile;
+                dk = tk;
+                ds = row_hash(0) & swm;
+                lin = row_lin_base - nb + j;
+            } else {
+                const uint32_t key = srt[lo + k - np];
+                const uint32_t r = key / nb;
+                j = key - r * nb;
+                rp = tile + r * pitch;
+                rk = tk;
+                rs = row_hash(r) & swm;
+                if (r > 0) {
+                    up = rp - pitch;
+                    uk = tk;
+                    us = row_hash(r - 1) & swm;
+                } else if (iA > 0) {
+                    up = carry + nb;
+                    uk = 1u;
+                }
+                if (iA + r + 1 < g.na) {
+                    dp = rp + pitch;
+                    dk = tk;
+                    ds = row_hash(r + 1) & swm;
+                }
+                lin = row_lin_base + key;
+            }
+            const uint32_t v = cell_at(rp, rk, rs, j);
+            if (peak_at(rp, rk, rs, up, uk, us, dp, dk, ds, j, nb, v)) {
+                has = 1;
+                ent = make_uint4(lin, e, v, 0u);
+            }
+        }
+        if (__syncthreads_or(has)) {
+            if (buf_n + rc > a.K)
+                flush_chunk(a, ss, pbuf, buf_n, nseq, inner, w.status);
+            compact_entry(ss, pbuf, buf_n, has, ent, a.ev_count);
+            total += ss.round_total;
         }
     }
 }
@@ -773,11 +947,12 @@ __device__ __forceinline__ void copy_tile_row(uint32_t *dst, const uint32_t *til
     }
 }
 
-// Peak tests of one pass of the fused fill (taken only when a row to test
-// holds a cell >= T; kept out of line so the vote loop keeps its registers):
-// the pending last row of the previous pass (carry[1], with carry[0] above
-// it when up_ok), then the tile rows r_first .. r_last marked in rows.
-__device__ __noinline__ void fused_test_rows(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss,
+// Whole-row peak tests of one pass of the fused fill, the fallback when a
+// pass lists more than kFusedCand cells >= T: the pending last row of the
+// previous pass (carry[1], with carry[0] above it when up_ok), then the tile
+// rows r_first .. r_last marked in rows.  Inlined: an out-of-line call makes
+// the kernel keep its parameters in local memory.
+__device__ __forceinline__ void fused_test_rows(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss,
                                              uint4 *pbuf, uint32_t &buf_n, uint32_t &nseq, uint32_t &total,
                                              const ChunkList &inner, const uint32_t *tile, const uint32_t *carry,
                                              uint32_t pitch, bool u16, bool pend, bool up_ok, uint64_t rows,
@@ -807,14 +982,17 @@ __device__ __noinline__ void fused_test_rows(const Geom &g, const Work &w, const
 __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, ScanArgs a)
 {
     extern __shared__ uint4 sm4[];
-    // layout: ScanSmem (256 B) | K peak entries | tile | HC staged hits | 2 carried rows
+    // layout: ScanSmem (256 B) | K peak entries | tile | HC staged hits | 2 carried rows |
+    //         B thresholds | 3 candidate lists (pass cells, sorted, pending row)
     ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
     uint4 *pbuf = sm4 + 16;
     uint32_t *tile = reinterpret_cast<uint32_t *>(pbuf + a.K);
     float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
     uint32_t *carry = reinterpret_cast<uint32_t *>(hs + c.HC);   // [2][nb]
     float *beta = reinterpret_cast<float *>(carry + 2 * g.nb);     // nb + 1 thresholds
-    __shared__ uint32_t s_sel[3], s_hot[2];
+    uint32_t *cand = reinterpret_cast<uint32_t *>(beta + c.beta_words);
+    uint32_t *srt = cand + kFusedCand, *pl = srt + kFusedCand;
+    __shared__ uint32_t s_sel[3], s_hot[2], s_nc, s_bounds[2];
 
     const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb;
     for (uint32_t k = tid; k < c.tile_words / 4; k += bd)
@@ -830,8 +1008,11 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
     uint32_t cached_n = 0;
     uint32_t buf_n = 0, nseq = 0, total = 0;
 
-    // carry state: carry[1] holds global row gP, carry[0] row gP - 1
-    bool carry1 = false, carry0 = false, pend = false, pend_hot = false;
+    // carry state: carry[1] holds global row gP, carry[0] row gP - 1.  Row
+    // gP is pending when it still needs its test: pend_mode 1 with its np_pend
+    // cells >= T listed in pl, 2 with a cell >= T but no list (overflow).
+    bool carry1 = false, carry0 = false;
+    uint32_t pend_mode = 0, np_pend = 0;
     uint64_t gP = 0;
 
     for (uint64_t item = it0; item < it1; ++item) {
@@ -885,28 +1066,61 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
                 }
             }
             if (tid == 0)
-                s_hot[0] = s_hot[1] = 0u;
+                s_hot[0] = s_hot[1] = s_nc = 0u;
             __syncthreads();
-            // ---- write the pass to M_H, mark rows holding a cell >= T -------
+            // ---- write the pass to M_H; list the cells >= T, mark their rows -
             if (u16)
-                flush_rows_mark<true>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, s_hot);
+                flush_rows_mark<true>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, s_hot, cand, &s_nc,
+                                      kFusedCand);
             else
-                flush_rows_mark<false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, s_hot);
+                flush_rows_mark<false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, s_hot, cand, &s_nc,
+                                       kFusedCand);
             __syncthreads();
             const uint64_t hotm = (uint64_t)s_hot[0] | ((uint64_t)s_hot[1] << 32);
+            const uint32_t n_c = s_nc;
             // ---- rows to test now, in order ----------------------------------
-            const bool test_pend = pend && carry1 && gP + 1 == gA;
+            const bool test_pend = pend_mode != 0 && carry1 && gP + 1 == gA;
+            const bool up_ok = carry0 && (gP % g.na) != 0;
             const uint32_t r_first = (iA == 0 || carry1) ? 0u : 1u;   // else row 0 is the seam
             const bool last_is_end = iA + pr - 1 == g.na - 1;
             const int32_t r_last = last_is_end ? (int32_t)pr - 1 : (int32_t)pr - 2;
-            uint64_t want = 0;
-            for (int32_t rr = (int32_t)r_first; rr <= r_last; ++rr)
-                want |= 1ull << rr;
+            const uint64_t want = r_last < (int32_t)r_first ? 0ull
+                                : ((~0ull >> (63 - r_last)) >> r_first) << r_first;
+            // the last row waits for the next pass unless it ends the slice or is the seam row
+            const bool pend_next = !last_is_end && pr - 1 >= r_first;
             const uint32_t row_lin_base = (uint32_t)((uint64_t)s * g.na + iA) * nb;
-            if ((test_pend && pend_hot) || (hotm & want))
-                fused_test_rows(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, carry, pitch, u16,
-                                test_pend && pend_hot, carry0 && (gP % g.na) != 0, hotm & want, r_first, r_last,
-                                iA, row_lin_base, e);
+            const bool fits = n_c <= kFusedCand;
+            uint32_t lo = 0, hi = 0;
+            if (fits && n_c) {
+                rank_sort_bounds(cand, srt, n_c, r_first * nb, (uint32_t)(r_last + 1) * nb, s_bounds);
+                lo = s_bounds[0];
+                hi = s_bounds[1];
+            }
+            if (fits && pend_mode != 2) {
+                // candidate lists: the pending row's cells, then rows r_first .. r_last
+                const uint32_t np = test_pend ? np_pend : 0u;
+                if (np || hi > lo)
+                    fused_test_cands(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, carry, pitch, u16, pl,
+                                     np, up_ok, srt, lo, hi, iA, row_lin_base, e);
+            } else if (test_pend || (hotm & want)) {
+                // too many candidates: test whole rows (a pending row holds a cell >= T)
+                fused_test_rows(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, carry, pitch, u16, test_pend,
+                                up_ok, hotm & want, r_first, r_last, iA, row_lin_base, e);
+            }
+            uint32_t next_mode = 0;
+            if (pend_next) {
+                if (fits) {
+                    if (n_c > hi) {
+                        __syncthreads();
+                        for (uint32_t q = hi + tid; q < n_c; q += bd)
+                            pl[q - hi] = srt[q] - (pr - 1) * nb;
+                        np_pend = n_c - hi;
+                        next_mode = 1;
+                    }
+                } else if ((hotm >> (pr - 1)) & 1ull) {
+                    next_mode = 2;
+                }
+            }
             // ---- carry the last two rows; clear the tile --------------------
             __syncthreads();
             if (pr >= 2) {
@@ -922,8 +1136,7 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
             }
             carry1 = true;
             gP = gA + pr - 1;
-            pend = !last_is_end;
-            pend_hot = (hotm >> (pr - 1)) & 1ull;
+            pend_mode = next_mode;
             __syncthreads();
             for (uint32_t q = tid; q < pr * pitch / 4; q += bd)
                 reinterpret_cast<uint4 *>(tile)[q] = make_uint4(0u, 0u, 0u, 0u);
@@ -1001,33 +1214,6 @@ __device__ void sort_u32(uint32_t *s, uint32_t n)
             __syncthreads();
         }
     }
-}
-
-// Ordered compaction of one entry per thread (has = 0 or 1): appends the
-// entries to pbuf in thread order and counts them for their events.
-__device__ __forceinline__ void compact_entry(ScanSmem &ss, uint4 *pbuf, uint32_t &buf_n, uint32_t has,
-                                              const uint4 &ent, uint32_t *ev_count)
-{
-    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
-    const uint32_t nw = (blockDim.x + 31) >> 5;
-    const uint32_t incl = warp_incl_scan(has);
-    if (lane == 31u)
-        ss.wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t v = lane < nw ? ss.wsum[lane] : 0u;
-        const uint32_t vi = warp_incl_scan(v);
-        ss.wsum[lane] = vi - v;
-        if (lane == 31u)
-            ss.round_total = vi;
-    }
-    __syncthreads();
-    if (has) {
-        pbuf[buf_n + ss.wsum[warp] + incl - 1] = ent;
-        atomicAdd(&ev_count[ent.y], 1u);
-    }
-    buf_n += ss.round_total;
-    __syncthreads();
 }
 
 // Test sorted candidate cells (run-local indices from global row g0) against
@@ -1235,7 +1421,7 @@ cudaError_t launch_bin(const Geom &g, const Work &w, uint32_t grid, cudaStream_t
 size_t fill_scan_smem_bytes(const FillCfg &c, const ScanArgs &a, uint32_t nb)
 {
     return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)c.tile_words * 4 + (size_t)c.HC * 16 +
-           (size_t)2 * nb * 4 + (size_t)c.beta_words * 4;
+           (size_t)2 * nb * 4 + (size_t)c.beta_words * 4 + (size_t)3 * kFusedCand * 4;
 }
 
 cudaError_t launch_fill_scan(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,

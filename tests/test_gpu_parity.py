@@ -56,9 +56,11 @@ def random_hits(n, seed, rmax=1100.0):
     return x, y, z
 
 
-def run_gpu(ht, b, r, T, x, y, z, naive=False, device=True, capacity=1 << 20, max_hits=None):
+def run_gpu(ht, b, r, T, x, y, z, naive=False, device=True, capacity=1 << 20, max_hits=None, tuning=None):
     import torch
     with ht.Context(b, r, threshold=T, max_hits=max_hits or max(len(x), 1)) as ctx:
+        if tuning:
+            ctx.set_tuning(**tuning)
         if device:
             ctx.fill(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), torch.from_numpy(z).cuda(),
                      naive=naive)
@@ -105,19 +107,27 @@ def test_fill_and_maxima_match_oracle(ht, case, naive):
     assert np.all(pk["event"] == 0)
 
 
-def test_u32_counter_tiles(ht):
+U32_TUNINGS = [None, dict(fill_fused_scan=2), dict(fill_fused_scan=1, fill_rows=2, fill_threads=256),
+               dict(fill_fused_scan=1, fill_rows=4, fill_threads=256)]
+
+
+@pytest.mark.parametrize("tuning", U32_TUNINGS, ids=[str(t) for t in U32_TUNINGS])
+def test_u32_counter_tiles(ht, tuning):
     # > 65535 hits in one slice: the fill switches that slice to u32 counters
+    # (half the rows per pass; one row per pass with 2-row strips).  T = 3
+    # lists more cells per pass than the fused fill's candidate lists hold.
     b, r = ht.Binning(1, 1, 64, 96), ht.Ranges()
     x, y, z = random_hits(70000, 9, rmax=400.0)
     # half the hits on one circle so that cells exceed 16 bits
     x[:35000], y[:35000] = np.float32(300.0), np.float32(250.0)
     M_ref, _ = oracle.fill(_ob(b), _orr(r), x, y, z)
     assert M_ref.max() >= 35000
-    pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, 50)
-    M, pk, n, _ = run_gpu(ht, b, r, 50, x, y, z)
-    assert np.array_equal(M, M_ref)
-    assert n == n_ref
-    assert_peaks_equal(pk, pk_ref)
+    for T in (50, 3):
+        pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, T)
+        M, pk, n, _ = run_gpu(ht, b, r, T, x, y, z, tuning=tuning)
+        assert np.array_equal(M, M_ref)
+        assert n == n_ref
+        assert_peaks_equal(pk, pk_ref)
 
 
 def test_empty_event_clears_in_place(ht):
@@ -367,6 +377,23 @@ def test_peaks_on_seams(ht, tuning):
             ctx.fill(x, y, z)
             pk, n = ctx.find_maxima(capacity=4096)
             assert np.array_equal(ctx.matrix(), M_ref)
+        assert n == n_ref, (T, n, n_ref)
+        assert_peaks_equal(pk, pk_ref)
+
+
+@pytest.mark.parametrize("tuning", FUSED_TUNINGS[1:4], ids=[str(t) for t in FUSED_TUNINGS[1:4]])
+def test_fused_candidate_overflow(ht, paper_ref, tuning):
+    # low thresholds on the paper-scale event: some passes list more cells
+    # >= T than the fused fill's candidate lists hold (whole-row fallback,
+    # also for the pending row of the next pass), others fewer
+    ev, M_ref = paper_ref[0], paper_ref[1]
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    for T in (3, 5, 7):
+        pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, T)
+        with ht.Context(b, r, threshold=T, max_hits=6000) as ctx:
+            ctx.set_tuning(**tuning)
+            ctx.fill(ev.x, ev.y, ev.z)
+            pk, n = ctx.find_maxima(capacity=1 << 20)
         assert n == n_ref, (T, n, n_ref)
         assert_peaks_equal(pk, pk_ref)
 
