@@ -133,6 +133,39 @@ ht_status ht_fill(ht_ctx *ctx, const float *x, const float *y, const float *z, u
 ht_status ht_find_maxima(ht_ctx *ctx, ht_peak *out, uint32_t capacity, uint32_t *n_found,
                          uint32_t flags, void *stream);
 
+/* Step 2 without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that may not call cudaMalloc / cudaFree --
+ * code whose device memory is owned by a framework's caching allocator or a
+ * fixed-budget pool (a raw allocation there can fail against, or take from,
+ * the pool's reservation), or loops that cannot afford the device-wide
+ * synchronisation of cudaFree.  Such callers cannot create an ht_ctx, which
+ * allocates M_H and its scratch.
+ *
+ * M: device, n_events vote matrices of the binning back to back (event e at
+ * M + e * n_cells, layout as above); read only.  out: device, n_events *
+ * capacity peaks (event e's at out + e * capacity, ascending linear index,
+ * the first `capacity` of the event, each with its event number); counts:
+ * device, n_events totals (a total above capacity means out holds only the
+ * first capacity).  The caller owns all three.  Same peak rule as
+ * ht_find_maxima.  stream: cudaStream_t as void*, NULL = the default stream;
+ * the call runs its kernels there and returns once they have finished.
+ *
+ * Scratch: one static device array of 5,337,344 bytes in the library, which
+ * every GPU that loads the library holds until the process exits.  Limits:
+ * 1 <= n_events <= 4096 (else HT_E_INVAL); at most 262,144 peaks per call in
+ * total and 128 chunks of the scan per CTA (else HT_E_NOMEM after the run,
+ * with out and counts incomplete).  Every call shares the array and clears
+ * its counters first; calls that overlap on the GPU (from several host
+ * threads, or on several streams) race on it and must be serialised by the
+ * caller.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  No cudaMalloc, cudaFree or other allocating
+ * call is made.  Errors: HT_E_INVAL (NULL pointer, bad binning, n_events or
+ * capacity), HT_E_NOMEM (scratch limit), HT_E_CUDA. */
+ht_status ht_find_maxima_noalloc(const ht_binning *binning, const ht_ranges *ranges, uint32_t threshold,
+                                 const uint32_t *M, uint32_t n_events, ht_peak *out, uint32_t capacity,
+                                 uint32_t *counts, void *stream);
+
 /* Wait for the context's stream (or `stream`) and report any device-side
  * failure flagged by its kernels (HT_E_TIMEOUT). */
 ht_status ht_sync(ht_ctx *ctx, void *stream);

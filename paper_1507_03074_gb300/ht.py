@@ -126,6 +126,8 @@ def lib():
         "ht_set_tuning": ([P, ctypes.POINTER(c_tuning)], I),
         "ht_autotune": ([P, U32, ctypes.POINTER(c_tuning), ctypes.POINTER(ctypes.c_double)], I),
         "ht_get_tuning": ([P, ctypes.POINTER(c_tuning)], I),
+        "ht_find_maxima_noalloc": ([ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), U32, P, U32, P, U32, P, P],
+                                   I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -162,6 +164,23 @@ def compute_b_thresholds(binning: Binning, ranges: Ranges = Ranges()):
     b, r = binning.c(), ranges.c()
     check(lib().ht_compute_b_thresholds(ctypes.byref(b), ctypes.byref(r), beta.ctypes.data_as(ctypes.c_void_p)))
     return beta
+
+
+def find_maxima_noalloc(binning: Binning, ranges: Ranges, threshold: int, M, n_events: int, out, capacity: int,
+                        counts, stream=None):
+    """ht_find_maxima_noalloc: Step 2 on n_events device matrices ``M`` (CUDA
+    tensor) into the CUDA tensors ``out`` (>= n_events*capacity*32 bytes) and
+    ``counts`` (>= n_events int32), with the library's static scratch."""
+    if out.numel() * out.element_size() < n_events * capacity * 32:
+        raise ValueError("out is smaller than n_events * capacity * 32 bytes")
+    if counts.numel() * counts.element_size() < n_events * 4:
+        raise ValueError("counts is smaller than n_events * 4 bytes")
+    if M.numel() * M.element_size() < n_events * binning.n_cells * 4:
+        raise ValueError("M is smaller than n_events matrices")
+    b, r = binning.c(), ranges.c()
+    check(lib().ht_find_maxima_noalloc(ctypes.byref(b), ctypes.byref(r), threshold, ctypes.c_void_p(M.data_ptr()),
+                                       n_events, ctypes.c_void_p(out.data_ptr()), capacity,
+                                       ctypes.c_void_p(counts.data_ptr()), _stream_ptr(stream)))
 
 
 def last_error() -> str:
