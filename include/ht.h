@@ -241,6 +241,59 @@ ht_status ht_get_tuning(ht_ctx *ctx, ht_tuning *tuning);
 ht_status ht_autotune(ht_ctx *ctx, uint32_t reps, ht_tuning *chosen, double *us_per_event);
 
 /* ------------------------------------------------------------------------ */
+/* Batches: many independent events in one fill + maxima launch sequence.   */
+/* ------------------------------------------------------------------------ */
+/* The paper processes its events one after another (Sec. 4); the
+ * arithmetic of each event here is unchanged (an event's M_H and peaks are
+ * identical alone and in any batch).  A batch holds max_events resident
+ * vote matrices (event e at e * n_cells), device staging for max_hits hits
+ * in total and room for `capacity` peaks over the whole batch.  Each run
+ * enqueues the hit copies, then the kernels of steps 1 and 2 for all events
+ * at once: a CUDA graph captured for that event count on the first run with
+ * it (later runs with the same count replay it), then the result copies. */
+ht_status ht_batch_create(const ht_binning *binning, const ht_ranges *ranges, uint32_t threshold,
+                          uint32_t max_events, uint32_t max_hits, uint32_t capacity, ht_batch **out);
+ht_status ht_batch_destroy(ht_batch *batch);
+
+/* Steps 1 + 2 for n_events (1..max_events) events whose hits are
+ * concatenated: event e owns hits [hit_off[e], hit_off[e+1]) of x, y, z,
+ * with hit_off[0] = 0 and hit_off[n_events] = n_hits <= max_hits.
+ * Peaks come in one list ordered by (event, linear index), each with its
+ * event number: event e's at out + sum of counts[e' < e] as long as the
+ * total fits `capacity` (the batch's); counts[e] is event e's total.
+ * HT_MEM_HOST: every array is host memory (copied at once; the caller may
+ * reuse them on return); blocks; writes min(total, capacity) peaks and
+ * returns HT_TRUNCATED when the total exceeds capacity.
+ * HT_MEM_DEVICE: every array (hit_off included) is device memory; the call
+ * only enqueues on `stream` (NULL = the batch's own stream); the caller
+ * checks counts for truncation; ht_batch_sync reports device-side failures.
+ * Errors: HT_E_INVAL, HT_E_CUDA (batch poisoned), HT_E_NOMEM (peak scratch),
+ * HT_E_TIMEOUT, HT_E_STATE. */
+ht_status ht_batch_run(ht_batch *batch, const float *x, const float *y, const float *z, const uint32_t *hit_off,
+                       uint32_t n_events, uint32_t n_hits, ht_peak *out, uint32_t *counts, uint32_t flags,
+                       void *stream);
+ht_status ht_batch_sync(ht_batch *batch, void *stream);
+
+/* Copy event e's M_H from the last run (n_cells cells) to host memory
+ * (blocking).  For tests. */
+ht_status ht_batch_copy_matrix(ht_batch *batch, uint32_t event, uint32_t *dst, uint64_t n_cells);
+
+/* Launch shapes of the batch (see ht_tuning); drops the captured graphs. */
+ht_status ht_batch_set_tuning(ht_batch *batch, const ht_tuning *tuning);
+ht_status ht_batch_get_tuning(ht_batch *batch, ht_tuning *tuning);
+
+/* ht_autotune for a batch: times candidate shapes on the hits of the last
+ * run (its events), keeps the fastest and drops the captured graphs; the
+ * result of the last run stays valid.  us_per_event is the device time of
+ * fill + maxima per event.  Blocks. */
+ht_status ht_batch_autotune(ht_batch *batch, uint32_t reps, ht_tuning *chosen, double *us_per_event);
+
+/* Per-kernel device times of the batch's runs that are not replayed from a
+ * graph (see ht_profile; with profiling on, runs do not use graphs). */
+ht_status ht_batch_profile(ht_batch *batch, int enable);
+ht_status ht_batch_profile_read(ht_batch *batch, ht_kernel_time *out, uint32_t cap, uint32_t *n);
+
+/* ------------------------------------------------------------------------ */
 /* Host-only helpers (no device needed).                                     */
 /* ------------------------------------------------------------------------ */
 

@@ -278,30 +278,10 @@ ht_status ht_set_tuning(ht_ctx *ctx, const ht_tuning *t)
         return s;
     if (!t)
         return set_err(HT_E_INVAL, "tuning is NULL");
-    if (t->scan_kind > HT_SCAN_DIRECT)
-        return set_err(HT_E_INVAL, "unknown scan_kind");
     CK(cudaStreamSynchronize(ctx->stream));
-    hte::Tuning old = ctx->E.tune;
-    hte::Tuning &n = ctx->E.tune;
-    n.fill_W = t->fill_rows;
-    n.fill_threads = t->fill_threads;
-    n.fill_HC = t->fill_hits_staged;
-    n.fill_blocks_per_sm = t->fill_blocks_per_sm;
-    n.scan_kind = t->scan_kind;
-    n.scan_stage_bytes = t->scan_stage_bytes;
-    n.scan_slots = t->scan_slots;
-    n.scan_blocks_per_sm = t->scan_blocks_per_sm;
-    n.fused = t->fill_fused_scan;
     std::string why;
-    s = hte::engine_configure(ctx->E, &why);
-    if (s != HT_OK) {
-        ctx->E.tune = old;
-        std::string why2;
-        if (hte::engine_configure(ctx->E, &why2) != HT_OK)
-            ctx->poisoned = true;
-        return set_err(s, why);
-    }
-    return HT_OK;
+    s = hte::engine_set_tuning(ctx->E, *t, &ctx->poisoned, &why);
+    return s == HT_OK ? HT_OK : set_err(s, why);
 }
 
 ht_status ht_get_tuning(ht_ctx *ctx, ht_tuning *t)
@@ -311,17 +291,7 @@ ht_status ht_get_tuning(ht_ctx *ctx, ht_tuning *t)
         return s;
     if (!t)
         return set_err(HT_E_INVAL, "tuning is NULL");
-    const hte::Engine &E = ctx->E;
-    t->fill_rows = E.fill.W;
-    t->fill_threads = E.fill.threads;
-    t->fill_hits_staged = E.fill.HC;
-    t->fill_blocks_per_sm = E.num_sms ? E.fill_grid / (uint32_t)E.num_sms : 0;
-    t->scan_kind = E.scan_kind == htk::SCAN_BULK ? HT_SCAN_BULK
-                 : E.scan_kind == htk::SCAN_LDG ? HT_SCAN_STREAM : HT_SCAN_DIRECT;
-    t->scan_stage_bytes = E.scan.slot_words * 4;
-    t->scan_slots = E.scan.S;
-    t->scan_blocks_per_sm = E.num_sms ? E.scan_grid_max / (uint32_t)E.num_sms : 0;
-    t->fill_fused_scan = E.fused_ok ? 1u : 2u;
+    hte::engine_get_tuning(ctx->E, t);
     return HT_OK;
 }
 
@@ -357,18 +327,7 @@ ht_status ht_profile_read(ht_ctx *ctx, ht_kernel_time *out, uint32_t cap, uint32
         return s;
     if (!n || (cap && !out))
         return set_err(HT_E_INVAL, "NULL argument");
-    CK(hte::prof_collect(ctx->E));
-    uint32_t k = 0;
-    for (int i = 0; i < hte::K_NKINDS; ++i) {
-        if (k < cap) {
-            std::memset(&out[k], 0, sizeof(ht_kernel_time));
-            std::strncpy(out[k].name, hte::kKernelNames[i], sizeof(out[k].name) - 1);
-            out[k].launches = ctx->E.prof.n[i];
-            out[k].total_ms = ctx->E.prof.ms[i];
-        }
-        ++k;
-    }
-    *n = k;
+    CK(hte::prof_read(ctx->E, out, cap, n));
     return HT_OK;
 }
 

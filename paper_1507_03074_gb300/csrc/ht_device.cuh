@@ -38,7 +38,7 @@ struct Geom {
 struct Work {
     const float *x, *y, *z;     // concatenated hits
     const uint32_t *hit_off;    // [n_events + 1] or nullptr: one event, n_hits0 hits
-    uint32_t n_hits0;
+    uint32_t n_hits0;           // with hit_off: the bound every offset is clamped to (staging size)
     uint32_t n_events;
     float4 *hits4;              // per hit: {x, x^2 + y^2, 2y, 0}
     uint32_t *codes;            // per hit: (itheta << 16) | iphi, or kDropped
@@ -59,13 +59,15 @@ struct Peak {
     uint32_t event;
 };
 
+// Hit range of event e, clamped to [0, n_hits0] so that offsets written by
+// a caller on the device can never send a kernel outside the staging.
 __device__ __forceinline__ uint32_t ev_hit_begin(const Work &w, uint32_t e)
 {
-    return w.hit_off ? w.hit_off[e] : 0u;
+    return w.hit_off ? min(w.hit_off[e], w.n_hits0) : 0u;
 }
 __device__ __forceinline__ uint32_t ev_hit_end(const Work &w, uint32_t e)
 {
-    return w.hit_off ? w.hit_off[e + 1] : w.n_hits0;
+    return w.hit_off ? max(min(w.hit_off[e + 1], w.n_hits0), ev_hit_begin(w, e)) : w.n_hits0;
 }
 
 // ---------------------------------------------------------------------------

@@ -560,7 +560,7 @@ cudaError_t engine_vote(Engine &E, const uint32_t *d_hit_off, uint32_t n_hits0, 
 }
 
 cudaError_t engine_scan(Engine &E, uint32_t n_events, htk::Peak *out, uint32_t capacity,
-                        uint32_t *counts, cudaStream_t st)
+                        uint32_t *counts, cudaStream_t st, bool compact)
 {
     htk::Work w = make_work(E, nullptr, nullptr, nullptr, nullptr, 0, n_events);
     htk::ScanArgs a = E.scan;
@@ -571,6 +571,7 @@ cudaError_t engine_scan(Engine &E, uint32_t n_events, htk::Peak *out, uint32_t c
     o.ev_count = E.d_ctr + htk::CTR_EVENTS;
     o.ticket = E.d_ctr + htk::CTR_OTICKET;
     o.g_count = E.d_ctr + htk::CTR_ENTRIES;
+    o.compact = compact ? 1u : 0u;
     cudaError_t e;
     if (E.fused_valid && E.fused_events == n_events) {
         // the fused fill already found the peaks: only order them
@@ -697,6 +698,66 @@ ht_status engine_autotune(Engine &E, uint32_t reps, cudaStream_t st, double *bes
     if (best_us)
         *best_us = best;
     return st_out;
+}
+
+ht_status engine_set_tuning(Engine &E, const ht_tuning &t, bool *poisoned, std::string *why)
+{
+    if (t.scan_kind > HT_SCAN_DIRECT) {
+        *why = "unknown scan_kind";
+        return HT_E_INVAL;
+    }
+    Tuning old = E.tune;
+    Tuning &n = E.tune;
+    n.fill_W = t.fill_rows;
+    n.fill_threads = t.fill_threads;
+    n.fill_HC = t.fill_hits_staged;
+    n.fill_blocks_per_sm = t.fill_blocks_per_sm;
+    n.scan_kind = t.scan_kind;
+    n.scan_stage_bytes = t.scan_stage_bytes;
+    n.scan_slots = t.scan_slots;
+    n.scan_blocks_per_sm = t.scan_blocks_per_sm;
+    n.fused = t.fill_fused_scan;
+    ht_status s = engine_configure(E, why);
+    if (s != HT_OK) {
+        E.tune = old;
+        std::string why2;
+        if (engine_configure(E, &why2) != HT_OK)
+            *poisoned = true;
+    }
+    return s;
+}
+
+void engine_get_tuning(const Engine &E, ht_tuning *t)
+{
+    t->fill_rows = E.fill.W;
+    t->fill_threads = E.fill.threads;
+    t->fill_hits_staged = E.fill.HC;
+    t->fill_blocks_per_sm = E.num_sms ? E.fill_grid / (uint32_t)E.num_sms : 0;
+    t->scan_kind = E.scan_kind == htk::SCAN_BULK ? HT_SCAN_BULK
+                 : E.scan_kind == htk::SCAN_LDG ? HT_SCAN_STREAM : HT_SCAN_DIRECT;
+    t->scan_stage_bytes = E.scan.slot_words * 4;
+    t->scan_slots = E.scan.S;
+    t->scan_blocks_per_sm = E.num_sms ? E.scan_grid_max / (uint32_t)E.num_sms : 0;
+    t->fill_fused_scan = E.fused_ok ? 1u : 2u;
+}
+
+cudaError_t prof_read(Engine &E, ht_kernel_time *out, uint32_t cap, uint32_t *n)
+{
+    cudaError_t e = prof_collect(E);
+    if (e != cudaSuccess)
+        return e;
+    uint32_t k = 0;
+    for (int i = 0; i < K_NKINDS; ++i) {
+        if (k < cap) {
+            std::memset(&out[k], 0, sizeof(ht_kernel_time));
+            std::strncpy(out[k].name, kKernelNames[i], sizeof(out[k].name) - 1);
+            out[k].launches = E.prof.n[i];
+            out[k].total_ms = E.prof.ms[i];
+        }
+        ++k;
+    }
+    *n = k;
+    return cudaSuccess;
 }
 
 } // namespace hte

@@ -122,13 +122,24 @@ cudaError_t engine_vote(Engine &E, const uint32_t *d_hit_off, uint32_t n_hits0, 
 ht_status engine_autotune(Engine &E, uint32_t reps, cudaStream_t st, double *best_us, std::string *why);
 
 // Step 2: peaks of every event into out[e * capacity ...], totals into counts[e].
+// compact: one list ordered by (event, linear index) in out[0 .. capacity)
+// instead of capacity entries per event.
 cudaError_t engine_scan(Engine &E, uint32_t n_events, htk::Peak *out, uint32_t capacity,
-                        uint32_t *counts, cudaStream_t st);
+                        uint32_t *counts, cudaStream_t st, bool compact = false);
 
 // Grow the peak-entry scratch to the bound that holds for any matrix (no two
 // peaks are neighbours): needed once M_H is written by something else than
 // engine_fill (ht_set_matrix).
 ht_status engine_ensure_any_matrix(Engine &E, std::string *why);
+
+// ABI tuning <-> engine: apply (re-deriving the shapes; on failure the old
+// tuning is restored, and *poisoned is set if even that fails) / report the
+// shapes in use.
+ht_status engine_set_tuning(Engine &E, const ht_tuning &t, bool *poisoned, std::string *why);
+void engine_get_tuning(const Engine &E, ht_tuning *t);
+
+// Per-kernel totals into the ABI's records (waits for recorded events).
+cudaError_t prof_read(Engine &E, ht_kernel_time *out, uint32_t cap, uint32_t *n);
 
 // Device status word (bits of htk::ST_*).
 inline uint32_t *engine_status(Engine &E) { return E.d_ctr + htk::CTR_STATUS; }

@@ -51,6 +51,7 @@ struct OrderArgs {
     uint32_t *ev_count;
     uint32_t *ticket;     // last-CTA detection (reset by k_order)
     uint32_t *g_count;    // entries used (reset by the last CTA)
+    uint32_t compact;     // 1: one list out[rank] over all events, else out[e][capacity]
 };
 
 cudaError_t launch_bin(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);

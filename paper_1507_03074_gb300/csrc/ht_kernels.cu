@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) k_bin(Geom g, Work w)
         for (uint32_t i = CTR_ENTRIES + threadIdx.x; i < CTR_EVENTS + w.n_events; i += blockDim.x)
             w.ctr[i] = 0u;
     __syncthreads();
-    const uint32_t n = w.hit_off ? w.hit_off[w.n_events] : w.n_hits0;
+    const uint32_t n = w.hit_off ? min(w.hit_off[w.n_events], w.n_hits0) : w.n_hits0;
     for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
         const float x = w.x[h], y = w.y[h];
         float r2;
@@ -1363,7 +1363,7 @@ __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, Order
                 break;
             const uint4 en = a.entries[d.x + k];
             const uint32_t e = en.y;
-            const uint32_t pos = P + k - ev_base[e];
+            const uint32_t pos = o.compact ? P + k : P + k - ev_base[e];
             if (pos < o.capacity) {
                 const uint32_t lin = en.x;
                 const uint32_t s = lin / (g.na * g.nb);
@@ -1378,7 +1378,7 @@ __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, Order
                 pk.a_c = a_centre(g, i);
                 pk.b_c = b_centre(g, j);
                 pk.event = e;
-                o.out[(size_t)e * o.capacity + pos] = pk;
+                o.out[o.compact ? (size_t)pos : (size_t)e * o.capacity + pos] = pk;
             }
         }
         P += d.y;

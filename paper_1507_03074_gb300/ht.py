@@ -128,6 +128,16 @@ def lib():
         "ht_get_tuning": ([P, ctypes.POINTER(c_tuning)], I),
         "ht_find_maxima_noalloc": ([ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), U32, P, U32, P, U32, P, P],
                                    I),
+        "ht_batch_create": ([ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), U32, U32, U32, U32, P], I),
+        "ht_batch_destroy": ([P], I),
+        "ht_batch_run": ([P, P, P, P, P, U32, U32, P, P, U32, P], I),
+        "ht_batch_sync": ([P, P], I),
+        "ht_batch_copy_matrix": ([P, U32, P, U64], I),
+        "ht_batch_set_tuning": ([P, ctypes.POINTER(c_tuning)], I),
+        "ht_batch_get_tuning": ([P, ctypes.POINTER(c_tuning)], I),
+        "ht_batch_autotune": ([P, U32, ctypes.POINTER(c_tuning), ctypes.POINTER(ctypes.c_double)], I),
+        "ht_batch_profile": ([P, I], I),
+        "ht_batch_profile_read": ([P, P, U32, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -340,3 +350,108 @@ class Context:
         ep = np.zeros(self.binning.n_phi + 1, np.float32)
         check(lib().ht_get_edges(self._h, et.ctypes.data_as(ctypes.c_void_p), ep.ctypes.data_as(ctypes.c_void_p)))
         return et, ep
+
+
+class Batch:
+    """Many events per launch sequence (ht_batch_*)."""
+
+    def __init__(self, binning: Binning, ranges: Ranges = Ranges(), threshold: int = 10, max_events: int = 128,
+                 max_hits: int = 1 << 20, capacity: int = 1 << 18):
+        self.binning, self.ranges, self.threshold = binning, ranges, threshold
+        self.max_events, self.max_hits, self.capacity = max_events, max_hits, capacity
+        self._h = ctypes.c_void_p()
+        b, r = binning.c(), ranges.c()
+        check(lib().ht_batch_create(ctypes.byref(b), ctypes.byref(r), threshold, max_events, max_hits, capacity,
+                                    ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            lib().ht_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @staticmethod
+    def concat(events):
+        """(x, y, z, hit_off) of a list of (x, y, z) host arrays."""
+        n = [len(e[0]) for e in events]
+        off = np.zeros(len(events) + 1, np.uint32)
+        off[1:] = np.cumsum(n)
+        cat = [np.ascontiguousarray(np.concatenate([e[k] for e in events]) if events else np.zeros(0),
+                                    dtype=np.float32) for k in range(3)]
+        return cat[0], cat[1], cat[2], off
+
+    def run(self, x, y, z, hit_off):
+        """Host mode: returns (peaks of all events ordered by (event, linear
+        index), counts per event); the peaks stop at capacity."""
+        pk, counts, status = self.run_raw(x, y, z, hit_off)
+        return pk, counts
+
+    def run_raw(self, x, y, z, hit_off):
+        """Host mode: (peaks, counts, status) with HT_TRUNCATED allowed."""
+        off = np.ascontiguousarray(hit_off, dtype=np.uint32)
+        n_events = off.size - 1
+        xa, ya, za = (np.ascontiguousarray(a, dtype=np.float32) for a in (x, y, z))
+        out = np.zeros(self.capacity, PEAK_DTYPE)
+        counts = np.zeros(max(n_events, 1), np.uint32)
+        s = check(lib().ht_batch_run(self._h, xa.ctypes.data_as(ctypes.c_void_p), ya.ctypes.data_as(ctypes.c_void_p),
+                                     za.ctypes.data_as(ctypes.c_void_p), off.ctypes.data_as(ctypes.c_void_p),
+                                     n_events, int(off[-1]), out.ctypes.data_as(ctypes.c_void_p),
+                                     counts.ctypes.data_as(ctypes.c_void_p), HT_MEM_HOST, None),
+                  ok=(HT_OK, HT_TRUNCATED))
+        total = int(counts[:n_events].sum())
+        return out[: min(total, self.capacity)].copy(), counts[:n_events].copy(), s
+
+    def run_device(self, x, y, z, hit_off, n_hits: int, out, counts, stream=None):
+        """Device mode: CUDA tensors (x, y, z float32; hit_off, counts int32;
+        out >= capacity * 32 bytes); only enqueues."""
+        n_events = hit_off.numel() - 1
+        if out.numel() * out.element_size() < self.capacity * 32:
+            raise ValueError("out is smaller than capacity * 32 bytes")
+        p = [ctypes.c_void_p(t.data_ptr()) for t in (x, y, z, hit_off, out, counts)]
+        check(lib().ht_batch_run(self._h, p[0], p[1], p[2], p[3], n_events, n_hits, p[4], p[5], HT_MEM_DEVICE,
+                                 _stream_ptr(stream)))
+
+    def sync(self, stream=None):
+        check(lib().ht_batch_sync(self._h, _stream_ptr(stream)))
+
+    def matrix(self, event: int) -> np.ndarray:
+        M = np.zeros(self.binning.shape(), np.uint32)
+        check(lib().ht_batch_copy_matrix(self._h, event, M.ctypes.data_as(ctypes.c_void_p), M.size))
+        return M
+
+    def set_tuning(self, **kw):
+        t = c_tuning(*[int(kw.pop(n, 0)) for n in TUNING_FIELDS])
+        if kw:
+            raise TypeError(f"unknown tuning fields {sorted(kw)}")
+        check(lib().ht_batch_set_tuning(self._h, ctypes.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = c_tuning()
+        check(lib().ht_batch_get_tuning(self._h, ctypes.byref(t)))
+        return {n: int(getattr(t, n)) for n in TUNING_FIELDS}
+
+    def autotune(self, reps: int = 3):
+        t, us = c_tuning(), ctypes.c_double()
+        check(lib().ht_batch_autotune(self._h, reps, ctypes.byref(t), ctypes.byref(us)))
+        return {n: int(getattr(t, n)) for n in TUNING_FIELDS}, float(us.value)
+
+    def profile(self, enable: bool = True):
+        check(lib().ht_batch_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        arr = (c_kernel_time * 16)()
+        n = ctypes.c_uint32()
+        check(lib().ht_batch_profile_read(self._h, ctypes.cast(arr, ctypes.c_void_p), 16, ctypes.byref(n)))
+        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
+                for i in range(min(n.value, 16))}

@@ -1,0 +1,171 @@
+"""Batches (ht_batch_*): every event's M_H and peaks equal the oracle's and
+the single-event context's, whatever the batch around it; graph replays,
+changing event counts, device-side inputs, truncation and the autotuner."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1507_03074_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+PEAK_FIELDS = ("itheta", "iphi", "ia", "ib", "votes", "a_c", "b_c")
+
+
+@pytest.fixture(scope="module")
+def ht():
+    import torch
+    from paper_1507_03074_gb300 import build
+    build.build()
+    from paper_1507_03074_gb300 import ht as _ht
+    torch.cuda.init()
+    return _ht
+
+
+def _ob(b):
+    return oracle.Binning(b.n_theta, b.n_phi, b.n_a, b.n_b, b.win_theta, b.win_phi)
+
+
+def _orr(r):
+    return oracle.Ranges(**r.__dict__)
+
+
+def _oracle_event(b, r, T, ev):
+    M, _ = oracle.fill(_ob(b), _orr(r), ev[0], ev[1], ev[2])
+    pk, n = oracle.find_maxima(_ob(b), _orr(r), M, T)
+    return M, pk, n
+
+
+def _split(pk, counts):
+    off = np.concatenate([[0], np.cumsum(counts, dtype=np.int64)]).astype(np.int64)
+    return [pk[off[e]:off[e + 1]] for e in range(len(counts))]
+
+
+def _check_events(events, pk, counts, refs, ev_ids=None):
+    parts = _split(pk, counts)
+    for e, (M_ref, pk_ref, n_ref) in enumerate(refs):
+        assert counts[e] == n_ref, e
+        got = parts[e]
+        for f in PEAK_FIELDS:
+            assert np.array_equal(got[f], pk_ref[f]), (e, f)
+        assert np.all(got["event"] == e)
+
+
+@pytest.fixture(scope="module")
+def uneven():
+    # 6 events, 40 .. 5000 hits (one tiny), paper-scale binning
+    evs = [(e.x, e.y, e.z) for e in synth.batch_events(5, seed0=1000, lo=500, hi=5000)]
+    t = synth.make_event(3, 4, seed=77)
+    evs.insert(2, (t.x, t.y, t.z))
+    b = oracle.Binning(*synth.PAPER_BINNING)
+    refs = []
+    for ev in evs:
+        M, _ = oracle.fill(b, oracle.Ranges(), *ev)
+        pk, n = oracle.find_maxima(b, oracle.Ranges(), M, 10)
+        refs.append((M, pk, n))
+    return evs, refs
+
+
+def test_batch_matches_oracle_and_replays(ht, uneven):
+    evs, refs = uneven
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    with ht.Batch(b, r, threshold=10, max_events=8, max_hits=40000, capacity=1 << 16) as B:
+        x, y, z, off = ht.Batch.concat(evs)
+        for rep in range(3):                       # direct + capture, then graph replays
+            pk, counts = B.run(x, y, z, off)
+            _check_events(evs, pk, counts, refs)
+        for e in (0, 2, len(evs) - 1):
+            assert np.array_equal(B.matrix(e), refs[e][0])
+        # a different set with the same event count replays the same graph
+        rev = evs[::-1]
+        x2, y2, z2, off2 = ht.Batch.concat(rev)
+        pk, counts = B.run(x2, y2, z2, off2)
+        _check_events(rev, pk, counts, refs[::-1])
+        # fewer events, then back
+        pk, counts = B.run(*ht.Batch.concat(evs[:3]))
+        _check_events(evs[:3], pk, counts, refs[:3])
+        pk, counts = B.run(x, y, z, off)
+        _check_events(evs, pk, counts, refs)
+
+
+def test_event_alone_equals_event_in_batch(ht, uneven):
+    evs, refs = uneven
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    with ht.Context(b, r, threshold=10, max_hits=6000) as ctx:
+        ctx.fill(*evs[1])
+        alone, n_alone = ctx.find_maxima(capacity=1 << 14)
+        M_alone = ctx.matrix()
+    with ht.Batch(b, r, threshold=10, max_events=8, max_hits=40000, capacity=1 << 16) as B:
+        pk, counts = B.run(*ht.Batch.concat(evs))
+        mine = _split(pk, counts)[1]
+        assert counts[1] == n_alone
+        for f in PEAK_FIELDS:
+            assert np.array_equal(mine[f], alone[f])
+        assert np.array_equal(B.matrix(1), M_alone)
+
+
+def test_batch_device_mode_and_truncation(ht, uneven):
+    import torch
+    evs, refs = uneven
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    x, y, z, off = ht.Batch.concat(evs)
+    total = sum(n for _, _, n in refs)
+    with ht.Batch(b, r, threshold=10, max_events=8, max_hits=40000, capacity=1 << 16) as B:
+        dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
+        doff = torch.from_numpy(off.astype(np.int32)).cuda()
+        out = torch.zeros((1 << 16) * 8, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(len(evs), dtype=torch.int32, device="cuda")
+        s = torch.cuda.Stream()
+        for _ in range(2):
+            B.run_device(dx, dy, dz, doff, int(off[-1]), out, cnt, stream=s)
+            B.sync(stream=s)
+            counts = cnt.cpu().numpy().astype(np.uint32)
+            pk = out.cpu().numpy().view(ht.PEAK_DTYPE)[:total]
+            _check_events(evs, pk, counts, refs)
+    # a batch with room for fewer peaks than the events hold
+    with ht.Batch(b, r, threshold=10, max_events=8, max_hits=40000, capacity=100) as B:
+        pk, counts, status = B.run_raw(x, y, z, off)
+        assert status == ht.HT_TRUNCATED and int(counts.sum()) == total and len(pk) == 100
+        full = np.concatenate([p for _, p, _ in refs])
+        for f in PEAK_FIELDS:
+            assert np.array_equal(pk[f], full[:100][f])
+
+
+def test_batch_ragged_binning_and_autotune(ht):
+    # n_b not a multiple of 4 (direct scan) and several strips per slice
+    b = ht.Binning(3, 5, 37, 29)
+    r = ht.Ranges(a_min=-1500.0, a_max=1700.0, b_min=-900.0, b_max=2100.0)
+    rng = np.random.default_rng(5)
+    evs = []
+    for n in (700, 50, 0, 1200):
+        rad, ph = rng.uniform(20.0, 1100.0, n), rng.uniform(-np.pi, np.pi, n)
+        evs.append(((rad * np.cos(ph)).astype(np.float32), (rad * np.sin(ph)).astype(np.float32),
+                    rng.uniform(-2500, 2500, n).astype(np.float32)))
+    refs = [_oracle_event(b, r, 2, ev) for ev in evs]
+    with ht.Batch(b, r, threshold=2, max_events=4, max_hits=4000, capacity=1 << 16) as B:
+        x, y, z, off = ht.Batch.concat(evs)
+        pk, counts = B.run(x, y, z, off)
+        _check_events(evs, pk, counts, refs)
+        chosen, us = B.autotune(reps=2)
+        assert us > 0
+        for _ in range(2):
+            pk, counts = B.run(x, y, z, off)
+            _check_events(evs, pk, counts, refs)
+        for e in range(len(evs)):
+            assert np.array_equal(B.matrix(e), refs[e][0])
+
+
+def test_batch_rejects_bad_arguments(ht):
+    b, r = ht.Binning(*synth.TINY_BINNING), ht.Ranges()
+    ev = synth.tiny_event()
+    with ht.Batch(b, r, threshold=8, max_events=2, max_hits=1000, capacity=64) as B:
+        x, y, z, off = ht.Batch.concat([(ev.x, ev.y, ev.z)] * 3)
+        with pytest.raises(ht.HTError):
+            B.run(x, y, z, off)                    # 3 events > max_events
+        x, y, z, off = ht.Batch.concat([(ev.x, ev.y, ev.z)] * 2)
+        bad = off.copy()
+        bad[1] = bad[2] + 1                        # decreasing offsets
+        with pytest.raises(ht.HTError):
+            B.run(x, y, z, bad)
+        pk, counts = B.run(x, y, z, off)           # still usable
+        assert counts[0] == counts[1]
