@@ -294,6 +294,63 @@ ht_status ht_batch_profile(ht_batch *batch, int enable);
 ht_status ht_batch_profile_read(ht_batch *batch, ht_kernel_time *out, uint32_t cap, uint32_t *n);
 
 /* ------------------------------------------------------------------------ */
+/* Serving: a request loop with continuous batching.                         */
+/* ------------------------------------------------------------------------ */
+/* Not in the paper (its events are processed one after another, Sec. 4);
+ * the arithmetic of every event is unchanged: a request's peaks are those
+ * ht_find_maxima returns for the event alone.  ht_submit copies the hits and
+ * returns at once.  A worker thread keeps "lanes": for one (binning,
+ * ranges, threshold) a lane holds the resident vote matrices of a
+ * micro-batch of events, staging and its own stream.  Whenever a lane is
+ * free the worker takes the waiting requests of its binning (oldest first,
+ * up to max_batch events and the lane's hit room) and runs them as one
+ * batch; lanes of several binnings and several lanes of one binning run at
+ * the same time.  A lane is created when a request needs one and its device
+ * memory fits hbm_budget_bytes (idle lanes of other binnings are freed to
+ * make room); otherwise the request waits for a lane.  M_H stays resident
+ * in a lane and is overwritten in place by every fill. */
+typedef struct {
+    uint64_t hbm_budget_bytes;   /* device memory for all lanes; 0 = 80% of the free memory at creation */
+    uint32_t n_streams;          /* lanes per binning (micro-batches in flight); 0 = 4 */
+    uint32_t max_batch;          /* events per micro-batch; 0 = 16 */
+    uint32_t max_hits_per_event; /* 0 = 65536 */
+    uint32_t queue_depth;        /* waiting requests before ht_submit answers HT_E_BUSY; 0 = 65536 */
+} ht_server_cfg;
+
+/* Create on the current CUDA device (cfg NULL = all defaults). */
+ht_status ht_server_create(const ht_server_cfg *cfg, ht_server **out);
+/* Finishes the requests on the GPU, drops the waiting ones, frees all lanes. */
+ht_status ht_server_destroy(ht_server *server);
+
+/* Queue one event (host arrays, copied before return).  *ticket names it
+ * for ht_poll.  Errors: HT_E_INVAL (binning, n_hits > max_hits_per_event,
+ * NULL), HT_E_BUSY (queue_depth requests already waiting), HT_E_STATE. */
+ht_status ht_submit(ht_server *server, const ht_binning *binning, const ht_ranges *ranges, uint32_t threshold,
+                    const float *x, const float *y, const float *z, uint32_t n_hits, uint64_t *ticket);
+
+/* Wait up to timeout_us for the request's result; HT_PENDING if it is not
+ * ready by then (the ticket stays valid).  On completion writes
+ * min(total, capacity) peaks (event field 0) to out and the total to
+ * *n_found, forgets the ticket and returns HT_OK, HT_TRUNCATED (total >
+ * capacity, or more peaks than its micro-batch could hold), or the
+ * request's error (HT_E_NOMEM: its matrix never fits the budget).
+ * HT_E_INVAL for an unknown ticket. */
+ht_status ht_poll(ht_server *server, uint64_t ticket, ht_peak *out, uint32_t capacity, uint32_t *n_found,
+                  uint32_t timeout_us);
+
+/* Counters; latency = submit to result ready (host steady clock) over the
+ * requests completed since the last reset (reset != 0 restarts them). */
+typedef struct {
+    uint64_t submitted, completed, waiting, in_flight;
+    uint64_t micro_batches;      /* dispatched micro-batches */
+    double mean_batch;           /* events per micro-batch */
+    uint32_t lanes;
+    uint64_t lane_bytes;         /* device memory held by the lanes */
+    double p50_us, p99_us, mean_us, max_us;
+} ht_server_stats;
+ht_status ht_server_get_stats(ht_server *server, ht_server_stats *stats, int reset);
+
+/* ------------------------------------------------------------------------ */
 /* Host-only helpers (no device needed).                                     */
 /* ------------------------------------------------------------------------ */
 

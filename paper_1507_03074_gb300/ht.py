@@ -48,6 +48,19 @@ class c_tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in TUNING_FIELDS]
 
 
+class c_server_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("n_streams", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32), ("max_hits_per_event", ctypes.c_uint32),
+                ("queue_depth", ctypes.c_uint32)]
+
+
+class c_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("waiting", ctypes.c_uint64),
+                ("in_flight", ctypes.c_uint64), ("micro_batches", ctypes.c_uint64), ("mean_batch", ctypes.c_double),
+                ("lanes", ctypes.c_uint32), ("lane_bytes", ctypes.c_uint64), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double)]
+
+
 class c_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
@@ -138,6 +151,12 @@ def lib():
         "ht_batch_autotune": ([P, U32, ctypes.POINTER(c_tuning), ctypes.POINTER(ctypes.c_double)], I),
         "ht_batch_profile": ([P, I], I),
         "ht_batch_profile_read": ([P, P, U32, P], I),
+        "ht_server_create": ([ctypes.POINTER(c_server_cfg), P], I),
+        "ht_server_destroy": ([P], I),
+        "ht_submit": ([P, ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), U32, P, P, P, U32,
+                       ctypes.POINTER(ctypes.c_uint64)], I),
+        "ht_poll": ([P, ctypes.c_uint64, P, U32, P, U32], I),
+        "ht_server_get_stats": ([P, ctypes.POINTER(c_server_stats), I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -455,3 +474,53 @@ class Batch:
         check(lib().ht_batch_profile_read(self._h, ctypes.cast(arr, ctypes.c_void_p), 16, ctypes.byref(n)))
         return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
                 for i in range(min(n.value, 16))}
+
+
+class Server:
+    """Request loop with continuous batching (ht_server_*, ht_submit, ht_poll)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, n_streams: int = 0, max_batch: int = 0,
+                 max_hits_per_event: int = 0, queue_depth: int = 0):
+        cfg = c_server_cfg(hbm_budget_bytes, n_streams, max_batch, max_hits_per_event, queue_depth)
+        self._h = ctypes.c_void_p()
+        check(lib().ht_server_create(ctypes.byref(cfg), ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            lib().ht_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, binning: Binning, ranges: Ranges, threshold: int, x, y, z) -> int:
+        xa, ya, za = (np.ascontiguousarray(a, dtype=np.float32) for a in (x, y, z))
+        b, r, t = binning.c(), ranges.c(), ctypes.c_uint64()
+        check(lib().ht_submit(self._h, ctypes.byref(b), ctypes.byref(r), threshold,
+                              xa.ctypes.data_as(ctypes.c_void_p), ya.ctypes.data_as(ctypes.c_void_p),
+                              za.ctypes.data_as(ctypes.c_void_p), xa.size, ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int, capacity: int = 1 << 14, timeout_us: int = 0):
+        """None while pending, else (status, peaks, total); raises on an error status."""
+        buf = np.zeros(max(capacity, 1), PEAK_DTYPE)
+        n = ctypes.c_uint32()
+        s = check(lib().ht_poll(self._h, ticket, buf.ctypes.data_as(ctypes.c_void_p), capacity, ctypes.byref(n),
+                                timeout_us), ok=(HT_OK, HT_TRUNCATED, HT_PENDING))
+        if s == HT_PENDING:
+            return None
+        return s, buf[: min(n.value, capacity)].copy(), int(n.value)
+
+    def stats(self, reset: bool = False) -> dict:
+        st = c_server_stats()
+        check(lib().ht_server_get_stats(self._h, ctypes.byref(st), 1 if reset else 0))
+        return {n: getattr(st, n) for n, _ in c_server_stats._fields_}

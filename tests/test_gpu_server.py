@@ -1,0 +1,103 @@
+"""Serving (ht_server_*): every request's peaks equal those of the event
+processed alone (ht_find_maxima through a context), whether it ran in a
+micro-batch with others, next to other binnings, or after lanes were freed
+and re-created under a tight memory budget."""
+import numpy as np
+import pytest
+
+from paper_1507_03074_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+PEAK_FIELDS = ("itheta", "iphi", "ia", "ib", "votes", "a_c", "b_c", "event")
+
+
+@pytest.fixture(scope="module")
+def ht():
+    import torch
+    from paper_1507_03074_gb300 import build
+    build.build()
+    from paper_1507_03074_gb300 import ht as _ht
+    torch.cuda.init()
+    return _ht
+
+
+def _alone(ht, b, r, T, ev):
+    with ht.Context(b, r, threshold=T, max_hits=max(len(ev[0]), 1)) as ctx:
+        ctx.fill(*ev)
+        return ctx.find_maxima(capacity=1 << 16)
+
+
+def _same(got, want):
+    assert len(got) == len(want)
+    for f in PEAK_FIELDS:
+        assert np.array_equal(got[f], want[f]), f
+
+
+def _wait(S, t, capacity=1 << 16):
+    res = S.poll(t, capacity=capacity, timeout_us=20_000_000)
+    assert res is not None, "request still pending after 20 s"
+    return res
+
+
+def test_server_mix_equals_alone(ht):
+    bA, TA = ht.Binning(*synth.PAPER_BINNING), 10
+    bB, TB = ht.Binning(2, 8, 256, 256), 6
+    r = ht.Ranges()
+    evA = [(e.x, e.y, e.z) for e in synth.batch_events(12, seed0=3000, lo=200, hi=5000)]
+    evB = [(e.x, e.y, e.z) for e in synth.batch_events(8, seed0=3100, lo=200, hi=3000)]
+    refA = [_alone(ht, bA, r, TA, ev) for ev in evA]
+    refB = [_alone(ht, bB, r, TB, ev) for ev in evB]
+    with ht.Server(n_streams=2, max_batch=4) as S:
+        # a burst: requests pile up behind the busy lanes and run in micro-batches
+        tickets = []
+        for i in range(max(len(evA), len(evB))):
+            if i < len(evA):
+                tickets.append(("A", i, S.submit(bA, r, TA, *evA[i])))
+            if i < len(evB):
+                tickets.append(("B", i, S.submit(bB, r, TB, *evB[i])))
+        for kind, i, t in tickets:
+            status, pk, n = _wait(S, t)
+            want, n_want = (refA if kind == "A" else refB)[i]
+            assert status == ht.HT_OK and n == n_want, (kind, i)
+            _same(pk, want)
+        st = S.stats(reset=True)
+        assert st["completed"] == len(tickets) and st["waiting"] == 0 and st["in_flight"] == 0
+        assert 1 <= st["micro_batches"] <= len(tickets) and st["lanes"] >= 2
+        assert st["p50_us"] > 0 and st["p99_us"] >= st["p50_us"]
+        # one at a time: each request alone in the server
+        for i in (0, 5, 11):
+            status, pk, n = _wait(S, S.submit(bA, r, TA, *evA[i]))
+            assert n == refA[i][1]
+            _same(pk, refA[i][0])
+        # truncation at poll time
+        status, pk, n = _wait(S, S.submit(bA, r, TA, *evA[0]), capacity=3)
+        assert status == ht.HT_TRUNCATED and n == refA[0][1] and len(pk) == 3
+        _same(pk, refA[0][0][:3])
+        with pytest.raises(ht.HTError):
+            S.poll(123456789)                     # unknown ticket
+
+
+def test_server_memory_budget(ht):
+    r = ht.Ranges()
+    bins = [ht.Binning(*synth.PAPER_BINNING), ht.Binning(4, 16, 512, 512), ht.Binning(4, 16, 1024, 512)]
+    evs = [(e.x, e.y, e.z) for e in synth.batch_events(6, seed0=3200, lo=300, hi=2000)]
+    refs = {(k, i): _alone(ht, b, r, 8, evs[i]) for k, b in enumerate(bins) for i in range(len(evs))}
+    budget = 700 << 20     # one lane of the paper binning plus one small one at a time
+    with ht.Server(hbm_budget_bytes=budget, n_streams=1, max_batch=2, max_hits_per_event=8192) as S:
+        tickets = [(k, i, S.submit(b, r, 8, *evs[i])) for i in range(len(evs)) for k, b in enumerate(bins)]
+        for k, i, t in tickets:
+            status, pk, n = _wait(S, t)
+            assert n == refs[(k, i)][1], (k, i)
+            _same(pk, refs[(k, i)][0])
+        st = S.stats()
+        assert st["lane_bytes"] <= budget * 1.25
+        # a binning whose matrix alone exceeds the budget is refused
+        big = ht.Binning(8, 32, 2048, 2048)
+        t = S.submit(big, r, 10, *evs[0])
+        with pytest.raises(ht.HTError) as err:
+            _wait(S, t)
+        assert err.value.status == ht.HT_E_NOMEM
+        # and the server keeps serving
+        status, pk, n = _wait(S, S.submit(bins[1], r, 8, *evs[2]))
+        _same(pk, refs[(1, 2)][0])
