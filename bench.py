@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--naive", action="store_true", help="time the naive global-atomic fill")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--serving-seconds", type=float, default=1.5, help="arrival window per serving rate")
     return ap.parse_args()
 
 
@@ -306,9 +308,187 @@ def run_ours(args, rank, world):
         "clocks": clk.summary(),
     }
     ctx.close()
+    if not args.no_extras and world == 1:
+        res["batched"] = run_batched()
+        res["serving"] = run_serving(args.serving_seconds)
     if not args.no_cpu_baseline and world == 1:
         res["cpu_baseline"] = cpu_baseline(budget_s=10.0)
     return res
+
+
+# ---------------------------------------------------------------------------
+# Batched vs per-event (100 uneven events) and the serving stream
+# ---------------------------------------------------------------------------
+
+def _pct(v, q):
+    return round(float(np.percentile(v, q)), 4)
+
+
+def run_batched(n_events=100, reps=5):
+    """100 independent events, hit counts uniform in 500..5000 (seeds 1000+i),
+    binning 4x16x1024x1024, threshold 10: one batch launch sequence (graph
+    replay) against the same events one per launch sequence."""
+    import torch
+    from paper_1507_03074_gb300 import ht
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    evs = synth.batch_events(n_events, seed0=1000)
+    host = [(e.x, e.y, e.z) for e in evs]
+    x, y, z, off = ht.Batch.concat(host)
+    n_hits = int(off[-1])
+    st = torch.cuda.Stream()
+    res = {"workload": f"{n_events} events, hits U(500..5000) (total {n_hits}), M_H 4x16x1024x1024 u32, threshold 10"}
+    # per event, through a context
+    with ht.Context(b, r, threshold=THRESHOLD, max_hits=max(e.n_hits for e in evs)) as ctx:
+        M = torch.empty(b.n_cells, dtype=torch.int32, device="cuda")
+        votes = 0
+        dev = [tuple(torch.from_numpy(a).cuda() for a in ev) for ev in host]
+        out = torch.empty(4096 * 8, dtype=torch.int32, device="cuda")
+        cnt = torch.empty(1, dtype=torch.int32, device="cuda")
+        for d in dev:
+            ctx.fill(*d, stream=st)
+            ctx.matrix_into(M, stream=st)
+            st.synchronize()
+            votes += int(M.to(torch.int64).sum().item())
+        del M
+        for ev in host[:10]:
+            ctx.fill(*ev)
+            ctx.find_maxima(capacity=4096)
+        lat = []
+        t0 = time.perf_counter()
+        for ev in host:
+            ts = time.perf_counter()
+            ctx.fill(*ev)
+            ctx.find_maxima(capacity=4096)
+            lat.append((time.perf_counter() - ts) * 1e3)
+        t_host = time.perf_counter() - t0
+        a, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for d in dev[:10]:
+            ctx.fill(*d, stream=st)
+            ctx.find_maxima(capacity=4096, out=out, count=cnt, stream=st)
+        a.record(st)
+        for d in dev:
+            ctx.fill(*d, stream=st)
+            ctx.find_maxima(capacity=4096, out=out, count=cnt, stream=st)
+        e_.record(st)
+        st.synchronize()
+        t_dev = a.elapsed_time(e_) / 1e3
+    res["per_event"] = {"e2e_events_per_s": round(n_events / t_host, 1),
+                        "device_events_per_s": round(n_events / t_dev, 1),
+                        "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99)},
+                        "api": "ht_fill + ht_find_maxima per event"}
+    # one batch
+    with ht.Batch(b, r, threshold=THRESHOLD, max_events=n_events, max_hits=n_hits + 64, capacity=1 << 17) as B:
+        for _ in range(2):
+            B.run(x, y, z, off)
+        tuning, _ = B.autotune(reps=2)
+        for _ in range(2):
+            B.run(x, y, z, off)
+        lat_b = []
+        for _ in range(reps):
+            ts = time.perf_counter()
+            pk, counts = B.run(x, y, z, off)
+            lat_b.append((time.perf_counter() - ts) * 1e3)
+        dx, dy, dz = (torch.from_numpy(v).cuda() for v in (x, y, z))
+        doff = torch.from_numpy(off.astype(np.int32)).cuda()
+        bout = torch.empty((1 << 17) * 8, dtype=torch.int32, device="cuda")
+        bcnt = torch.empty(n_events, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            B.run_device(dx, dy, dz, doff, n_hits, bout, bcnt, stream=st)
+        a.record(st)
+        for _ in range(reps):
+            B.run_device(dx, dy, dz, doff, n_hits, bout, bcnt, stream=st)
+        e_.record(st)
+        st.synchronize()
+        t_bdev = a.elapsed_time(e_) / 1e3 / reps
+        B.profile(True)
+        B.run(x, y, z, off)
+        prof = B.profile_read()
+        B.profile(False)
+    t_b = float(np.median(lat_b)) / 1e3
+    res["batched"] = {"e2e_events_per_s": round(n_events / t_b, 1),
+                      "device_events_per_s": round(n_events / t_bdev, 1),
+                      "gvotes_per_s": round(votes / t_bdev / 1e9, 3),
+                      "latency_ms": {"p50": _pct(lat_b, 50), "p99": _pct(lat_b, 99),
+                                     "note": "every event of a batch is ready when the batch is"},
+                      "kernels_us_per_batch": {k: round(ms / n * 1e3, 1) for k, (n, ms) in prof.items() if n},
+                      "tuning": tuning, "api": "ht_batch_run (graph replay)"}
+    res["votes_per_event"] = int(votes / n_events)
+    return res
+
+
+def run_serving(seconds=1.5, rates=(1000, 10000, 50000), pool_per_kind=48):
+    """Poisson arrivals at each rate for `seconds`; hit counts lognormal
+    (median 3000, sigma 1, clipped 200..50000); 90% binning 4x16x1024x1024,
+    10% 8x32x2048x2048; threshold 10.  Requests reuse a pool of seeded events
+    with the stream's first hit counts.  Latency is the server's own
+    submit-to-ready time; the sustained rate counts completions over the
+    time from the first submit to the last completion."""
+    import ctypes
+    import queue
+    import threading
+    from paper_1507_03074_gb300 import ht
+    bins = {False: ht.Binning(*synth.PAPER_BINNING), True: ht.Binning(*synth.UPGRADE_BINNING)}
+    r = ht.Ranges()
+    _, n0, up0, _ = synth.serving_stream(1000.0, 4 * pool_per_kind, seed=3000)
+    pools = {False: [], True: []}
+    for k in range(len(n0)):
+        kind = bool(up0[k])
+        if len(pools[kind]) < (pool_per_kind if not kind else pool_per_kind // 4):
+            t, nz = synth.split_hits(int(n0[k]))
+            e = synth.make_event(t, nz, seed=3000 + k)
+            pools[kind].append((e.x, e.y, e.z))
+    L = ht.lib()
+    sys.setswitchinterval(1e-4)          # let the polling thread run beside the arrival loop
+    out = {"workload": "Poisson arrivals; hits lognormal(median 3000, sigma 1) clipped 200..50000; "
+                       "90% 4x16x1024x1024 / 10% 8x32x2048x2048 u32; threshold 10", "rates": []}
+    with ht.Server() as S:
+        # warm-up: lanes of both binnings
+        warm = [S.submit(bins[k], r, THRESHOLD, *pools[k][i]) for k in (False, True) for i in range(4)]
+        for t in warm:
+            S.poll(t, timeout_us=60_000_000)
+        S.stats(reset=True)
+        for rate in rates:
+            n = max(1, int(rate * seconds))
+            arr, _, up, _ = synth.serving_stream(float(rate), n, seed=3001)
+            tickets = queue.Queue()
+            done_t = [0.0]
+
+            def poller():
+                buf = np.zeros(4096, ht.PEAK_DTYPE)
+                nf = ctypes.c_uint32()
+                while True:
+                    t = tickets.get()
+                    if t is None:
+                        break
+                    L.ht_poll(S._h, t, buf.ctypes.data_as(ctypes.c_void_p), 4096, ctypes.byref(nf), 60_000_000)
+                    done_t[0] = time.perf_counter()
+
+            th = threading.Thread(target=poller)
+            th.start()
+            busy = 0
+            t0 = time.perf_counter()
+            for i in range(n):
+                while time.perf_counter() - t0 < arr[i]:
+                    pass
+                kind = bool(up[i])
+                ev = pools[kind][i % len(pools[kind])]
+                try:
+                    tickets.put(S.submit(bins[kind], r, THRESHOLD, *ev))
+                except ht.HTError:
+                    busy += 1
+            t_sub = time.perf_counter() - t0
+            tickets.put(None)
+            th.join()
+            span = done_t[0] - t0
+            st = S.stats(reset=True)
+            out["rates"].append({
+                "offered_events_per_s": rate, "submitted_events_per_s": round((n - busy) / t_sub, 1),
+                "sustained_events_per_s": round((n - busy) / span, 1), "requests": n, "refused_busy": busy,
+                "latency_ms": {"p50": round(st["p50_us"] / 1e3, 4), "p99": round(st["p99_us"] / 1e3, 4),
+                               "max": round(st["max_us"] / 1e3, 4)},
+                "mean_micro_batch": round(st["mean_batch"], 2), "lanes": st["lanes"],
+                "lane_gib": round(st["lane_bytes"] / 2**30, 2)})
+    return out
 
 
 def _oracle_event(ob, orr, e):
