@@ -200,9 +200,9 @@ __device__ __forceinline__ int vote_bin(const Geom &g, float twoA, float x, floa
 // the bin is max{k : beta[k] <= B} and the vote is in range iff
 // beta[0] <= B < beta[nb] (NaN fails).  Identical to the division rule for
 // every float B; an estimate from 1/dB is corrected by table compares.
-__device__ __forceinline__ int bin_from_thresholds(const Geom &g, const float *beta, float B)
+__device__ __forceinline__ int bin_from_thresholds(const Geom &g, const float *beta, float b_lo, float b_hi, float B)
 {
-    if (!(B >= beta[0] && B < beta[g.nb]))
+    if (!(B >= b_lo && B < b_hi))   // b_lo = beta[0], b_hi = beta[n_b]
         return -1;
     int j = (int)((B - g.b_min) * g.inv_db);
     j = max(0, min(j, (int)g.nb - 1));
@@ -215,12 +215,12 @@ __device__ __forceinline__ int bin_from_thresholds(const Geom &g, const float *b
 
 // The vote of one (hit, A bin) with the threshold table: B = (r2 - (2A) x) / d
 // by IEEE division, then its bin (or -1).
-__device__ __forceinline__ int vote_bin_tab(const Geom &g, const float *beta, float twoA, float x, float r2,
-                                            float d)
+__device__ __forceinline__ int vote_bin_tab(const Geom &g, const float *beta, float b_lo, float b_hi, float twoA,
+                                            float x, float r2, float d)
 {
     const float num = __fsub_rn(r2, __fmul_rn(twoA, x));
     const float B = __fdiv_rn(num, d);
-    return bin_from_thresholds(g, beta, B);
+    return bin_from_thresholds(g, beta, b_lo, b_hi, B);
 }
 
 // ---------------------------------------------------------------------------

@@ -123,10 +123,11 @@ __device__ __forceinline__ void vote_rows(const Geom &g, uint32_t *tile, const f
     const float twoA = __fmul_rn(2.0f, a_centre(g, i));
     const uint32_t rowbase = r * pitch;
     const uint32_t sw = U16 ? (row_hash(r) & 0x1Eu) : (row_hash(r) & 0x1Cu);
+    const float b_lo = beta[0], b_hi = beta[g.nb];   // the in-range test of every vote
 #pragma unroll 4
     for (uint32_t h = hl; h < nc; h += hstride) {
         const float4 hv = hs[h];
-        const int j = vote_bin_tab(g, beta, twoA, hv.x, hv.y, hv.z);
+        const int j = vote_bin_tab(g, beta, b_lo, b_hi, twoA, hv.x, hv.y, hv.z);
         if (j >= 0) {
             if (U16) {
                 const uint32_t word = rowbase + ((uint32_t(j) >> 1) ^ sw);
@@ -138,41 +139,77 @@ __device__ __forceinline__ void vote_rows(const Geom &g, uint32_t *tile, const f
     }
 }
 
-template <bool U16>
-__device__ __forceinline__ void flush_rows(const Geom &g, uint32_t *tile, uint32_t *dst, uint32_t rows,
-                                           uint32_t pitch, bool accumulate)
+// Cells >= T found while flushing: hot[] marks their rows (bit r of word
+// r / 32), cand[] lists them as r * n_b + j (up to cap; *n counts them all).
+struct FlushList {
+    uint32_t *hot;
+    uint32_t *cand;
+    uint32_t *n;
+    uint32_t cap;
+};
+
+template <bool LIST>
+__device__ __forceinline__ void list_cells(const Geom &g, const FlushList &L, uint32_t r, uint32_t j0,
+                                           const uint32_t *v, uint32_t n)
 {
-    const uint32_t tid = threadIdx.x, bd = blockDim.x;
-    if ((g.nb & 3u) == 0) {
-        const uint32_t q = g.nb >> 2;  // 16-byte units per row
+    if (!LIST)
+        return;
+    uint32_t mx = 0;
+    for (uint32_t m = 0; m < n; ++m)
+        mx = max(mx, v[m]);
+    if (mx < g.threshold)
+        return;
+    atomicOr(&L.hot[r >> 5], 1u << (r & 31u));
+    for (uint32_t m = 0; m < n; ++m)
+        if (v[m] >= g.threshold) {
+            const uint32_t p = atomicAdd(L.n, 1u);
+            if (p < L.cap)
+                L.cand[p] = r * g.nb + j0 + m;
+        }
+}
+
+// Write the tile rows of one pass to M_H (dst = the pass's first row) and
+// clear them; with LIST, list the cells >= T; with accumulate, add to M_H.
+// The tile keeps row r's logical word w at physical word w ^ sw(r) (sw even
+// in u16 mode, a multiple of 4 in u32 mode).  When n_b is a multiple of 4
+// each step moves 4 cells: consecutive threads write consecutive 16-byte
+// pieces of the row, so every store instruction of a warp covers 512
+// contiguous bytes.
+template <bool U16, bool LIST>
+__device__ __forceinline__ void flush_tile(const Geom &g, uint32_t *tile, uint32_t *dst, uint32_t rows,
+                                           uint32_t pitch, bool accumulate, const FlushList &L)
+{
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb;
+    if ((nb & 3u) == 0) {
+        const uint32_t q = nb >> 2;  // 16-byte units per row
         const uint32_t qs = (q & (q - 1)) ? 32u : (uint32_t)(__ffs(q) - 1);
         const uint32_t units = rows * q;
         for (uint32_t u = tid; u < units; u += bd) {
             const uint32_t r = qs < 32u ? u >> qs : u / q, c4 = u - r * q;
-            uint4 v;
+            uint32_t v[4];
             if (U16) {
-                const uint32_t sw = row_hash(r) & 0x1Eu;
-                uint2 *p = reinterpret_cast<uint2 *>(&tile[r * pitch + ((2u * c4) ^ sw)]);
+                uint2 *p = reinterpret_cast<uint2 *>(&tile[r * pitch + ((2u * c4) ^ (row_hash(r) & 0x1Eu))]);
                 const uint2 pr = *p;
                 *p = make_uint2(0u, 0u);
-                v = make_uint4(pr.x & 0xffffu, pr.x >> 16, pr.y & 0xffffu, pr.y >> 16);
+                v[0] = pr.x & 0xffffu; v[1] = pr.x >> 16; v[2] = pr.y & 0xffffu; v[3] = pr.y >> 16;
             } else {
-                const uint32_t sw = row_hash(r) & 0x1Cu;
-                uint4 *p = reinterpret_cast<uint4 *>(&tile[r * pitch + ((4u * c4) ^ sw)]);
-                v = *p;
+                uint4 *p = reinterpret_cast<uint4 *>(&tile[r * pitch + ((4u * c4) ^ (row_hash(r) & 0x1Cu))]);
+                const uint4 pr = *p;
                 *p = make_uint4(0u, 0u, 0u, 0u);
+                v[0] = pr.x; v[1] = pr.y; v[2] = pr.z; v[3] = pr.w;
             }
             uint4 *o = reinterpret_cast<uint4 *>(dst) + u;
             if (accumulate) {
                 const uint4 old = *o;
-                v.x += old.x; v.y += old.y; v.z += old.z; v.w += old.w;
+                v[0] += old.x; v[1] += old.y; v[2] += old.z; v[3] += old.w;
             }
-            *o = v;
+            *o = make_uint4(v[0], v[1], v[2], v[3]);
+            list_cells<LIST>(g, L, r, 4u * c4, v, 4);
         }
     } else {
-        const uint32_t units = rows * g.nb;
+        const uint32_t units = rows * nb;
         for (uint32_t u = tid; u < units; u += bd) {
-            const uint32_t r = u / g.nb, j = u - r * g.nb;
+            const uint32_t r = u / nb, j = u - r * nb;
             uint32_t v;
             if (U16) {
                 const uint32_t word = r * pitch + ((j >> 1) ^ (row_hash(r) & 0x1Eu));
@@ -181,7 +218,9 @@ __device__ __forceinline__ void flush_rows(const Geom &g, uint32_t *tile, uint32
                 const uint32_t word = r * pitch + (j ^ (row_hash(r) & 0x1Cu));
                 v = tile[word];
             }
-            dst[u] = accumulate ? dst[u] + v : v;
+            v = accumulate ? dst[u] + v : v;
+            dst[u] = v;
+            list_cells<LIST>(g, L, r, j, &v, 1);
         }
         __syncthreads();
         // clear the tile after every thread has read its cells
@@ -319,9 +358,9 @@ __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
             }
             __syncthreads();
             if (u16)
-                flush_rows<true>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, c.accumulate != 0);
+                flush_tile<true, false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, c.accumulate != 0, FlushList{});
             else
-                flush_rows<false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, c.accumulate != 0);
+                flush_tile<false, false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, c.accumulate != 0, FlushList{});
         }
     }
 }
@@ -652,22 +691,25 @@ __global__ void __launch_bounds__(256) k_scan_direct(Geom g, Work w, ScanArgs a)
 //
 // Like k_fill_priv, a CTA owns a contiguous range of (event, slice, strip)
 // items, votes each strip pass into a shared-memory tile and writes it to
-// M_H (which stays complete in HBM).  Before the tile is cleared, the rows of
-// the pass are tested for peaks from shared memory:
-//   - a row whose 8-neighbourhood lies in the tile (or outside the slice) is
-//     tested at once; the pass's last row waits for the next pass of the
-//     same slice, bridged by two carried rows (u32 copies of the last rows);
+// M_H, clearing the tile as it goes.  While writing, it lists the cells of
+// the pass that hold >= T votes; only those are tested against their
+// neighbours, which are read back from M_H -- rows this CTA has just
+// written, still in L2:
+//   - a row whose lower neighbour is written (every row of the pass but the
+//     last, and the last when it ends the slice) is tested at once; the last
+//     row's cells wait for the next pass of the same slice;
 //   - the first row of the CTA's range, when it is not a slice's first row,
 //     and the previous CTA's last row form the seam between two CTAs; k_seam
 //     tests both once the whole of M_H is written.
-// Peaks go, in linear order, into per-CTA interior chunks; k_seam adds the
-// seam chunks, which k_order places before the CTA's interior chunks.
+// A pass that lists more than kFusedCand cells tests its rows whole.  Peaks
+// go, in linear order, into per-CTA interior chunks; k_seam adds the seam
+// chunks, which k_order places before the CTA's interior chunks.
 // ---------------------------------------------------------------------------
 
 // A row of cells in one of the places the fused kernel keeps them.
 struct RowRef {
     const uint32_t *p;   // row start (u32 array) or tile row base (words)
-    uint32_t kind;       // 0 absent, 1 u32 shared, 2 u16 tile, 3 u32 tile, 4 u32 global
+    uint32_t kind;       // 0 absent, 1 u32 shared, 2 u16 tile, 3 u32 tile, 4 u32 global (via L2)
     uint32_t sw;         // tile swizzle of the row
     __device__ __forceinline__ uint32_t get(uint32_t j) const
     {
@@ -734,90 +776,23 @@ __device__ void test_row_ref(const Geom &g, const ScanArgs &a, ScanSmem &ss, uin
     }
 }
 
-// Flush the tile rows of one pass to M_H without clearing them; mark rows
-// holding a cell >= T in hot[] (bit r of word r / 32) and list those cells,
-// as r * n_b + j, in cand[] (up to cap; *n_cand counts them all).
-template <bool U16>
-__device__ __forceinline__ void flush_rows_mark(const Geom &g, const uint32_t *tile, uint32_t *dst,
-                                                uint32_t rows, uint32_t pitch, uint32_t *hot, uint32_t *cand,
-                                                uint32_t *n_cand, uint32_t cap)
-{
-    const uint32_t tid = threadIdx.x, bd = blockDim.x, T = g.threshold;
-    if ((g.nb & 3u) == 0) {
-        const uint32_t q = g.nb >> 2;
-        const uint32_t qs = (q & (q - 1)) ? 32u : (uint32_t)(__ffs(q) - 1);
-        const uint32_t units = rows * q;
-        for (uint32_t u = tid; u < units; u += bd) {
-            const uint32_t r = qs < 32u ? u >> qs : u / q, c4 = u - r * q;
-            uint4 v;
-            if (U16) {
-                const uint2 pr = *reinterpret_cast<const uint2 *>(
-                    &tile[r * pitch + ((2u * c4) ^ (row_hash(r) & 0x1Eu))]);
-                v = make_uint4(pr.x & 0xffffu, pr.x >> 16, pr.y & 0xffffu, pr.y >> 16);
-            } else {
-                v = *reinterpret_cast<const uint4 *>(&tile[r * pitch + ((4u * c4) ^ (row_hash(r) & 0x1Cu))]);
-            }
-            reinterpret_cast<uint4 *>(dst)[u] = v;
-            if (max(max(v.x, v.y), max(v.z, v.w)) >= T) {
-                atomicOr(&hot[r >> 5], 1u << (r & 31u));
-                const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (uint32_t m = 0; m < 4; ++m)
-                    if (vv[m] >= T) {
-                        const uint32_t p = atomicAdd(n_cand, 1u);
-                        if (p < cap)
-                            cand[p] = r * g.nb + 4u * c4 + m;
-                    }
-            }
-        }
-    } else {
-        const uint32_t units = rows * g.nb;
-        for (uint32_t u = tid; u < units; u += bd) {
-            const uint32_t r = u / g.nb, j = u - r * g.nb;
-            uint32_t v;
-            if (U16)
-                v = (tile[r * pitch + ((j >> 1) ^ (row_hash(r) & 0x1Eu))] >> ((j & 1u) << 4)) & 0xffffu;
-            else
-                v = tile[r * pitch + (j ^ (row_hash(r) & 0x1Cu))];
-            dst[u] = v;
-            if (v >= T) {
-                atomicOr(&hot[r >> 5], 1u << (r & 31u));
-                const uint32_t p = atomicAdd(n_cand, 1u);
-                if (p < cap)
-                    cand[p] = u;
-            }
-        }
-    }
-}
-
-// A cell of a row kept as plain u32 (kind 1), u16 tile (kind 2) or u32 tile
-// (kind 3) with row swizzle sw.  Arguments in registers: no local memory.
-__device__ __forceinline__ uint32_t cell_at(const uint32_t *p, uint32_t kind, uint32_t sw, uint32_t j)
-{
-    if (kind == 1u)
-        return p[j];
-    if (kind == 2u)
-        return (p[(j >> 1) ^ sw] >> ((j & 1u) << 4)) & 0xffffu;
-    return p[j ^ sw];
-}
-
-// Peak test of cell j with value v; up / dn absent when their kind is 0.
-__device__ __forceinline__ bool peak_at(const uint32_t *rp, uint32_t rk, uint32_t rs, const uint32_t *up,
-                                        uint32_t uk, uint32_t us, const uint32_t *dp, uint32_t dk, uint32_t ds,
-                                        uint32_t j, uint32_t nb, uint32_t v)
+// Peak test with the neighbours read through L2 (rows of this CTA, written
+// before the last block barrier); up / dn are null outside the slice.
+__device__ __forceinline__ bool is_peak_l2(const uint32_t *row, const uint32_t *up, const uint32_t *dn, uint32_t j,
+                                           uint32_t nb, uint32_t v)
 {
     const bool hl = j > 0, hr = j + 1 < nb;
-    if (uk) {
-        if (hl && !(v > cell_at(up, uk, us, j - 1))) return false;
-        if (!(v > cell_at(up, uk, us, j))) return false;
-        if (hr && !(v > cell_at(up, uk, us, j + 1))) return false;
+    if (up) {
+        if (hl && !(v > __ldcg(up + j - 1))) return false;
+        if (!(v > __ldcg(up + j))) return false;
+        if (hr && !(v > __ldcg(up + j + 1))) return false;
     }
-    if (hl && !(v > cell_at(rp, rk, rs, j - 1))) return false;
-    if (hr && !(v >= cell_at(rp, rk, rs, j + 1))) return false;
-    if (dk) {
-        if (hl && !(v >= cell_at(dp, dk, ds, j - 1))) return false;
-        if (!(v >= cell_at(dp, dk, ds, j))) return false;
-        if (hr && !(v >= cell_at(dp, dk, ds, j + 1))) return false;
+    if (hl && !(v > __ldcg(row + j - 1))) return false;
+    if (hr && !(v >= __ldcg(row + j + 1))) return false;
+    if (dn) {
+        if (hl && !(v >= __ldcg(dn + j - 1))) return false;
+        if (!(v >= __ldcg(dn + j))) return false;
+        if (hr && !(v >= __ldcg(dn + j + 1))) return false;
     }
     return true;
 }
@@ -850,20 +825,16 @@ __device__ __forceinline__ void rank_sort_bounds(const uint32_t *cand, uint32_t 
 }
 
 // Peak tests of one fused-fill pass from candidate lists, one cell per
-// thread: first the np pending cells (columns of the previous pass's last
-// row, held in carry[1] with carry[0] above when up_ok and tile row 0 below),
-// then the sorted keys srt[lo, hi) (r * n_b + j for tile row r).  Peaks are
-// appended in linear order.
+// thread: first the np pending cells (columns of row iA - 1, the previous
+// pass's last row), then the sorted keys srt[lo, hi) (r * n_b + j for row
+// iA + r).  Ms is the slice's M_H; peaks are appended in linear order.
 __device__ __forceinline__ void fused_test_cands(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss,
                                                  uint4 *pbuf, uint32_t &buf_n, uint32_t &nseq, uint32_t &total,
-                                                 const ChunkList &inner, const uint32_t *tile,
-                                                 const uint32_t *carry, uint32_t pitch, bool u16,
-                                                 const uint32_t *pl, uint32_t np, bool up_ok, const uint32_t *srt,
-                                                 uint32_t lo, uint32_t hi, uint32_t iA, uint32_t row_lin_base,
-                                                 uint32_t e)
+                                                 const ChunkList &inner, const uint32_t *Ms, const uint32_t *pl,
+                                                 uint32_t np, const uint32_t *srt, uint32_t lo, uint32_t hi,
+                                                 uint32_t iA, uint32_t slice_lin0, uint32_t e)
 {
     const uint32_t tid = threadIdx.x, nb = g.nb;
-    const uint32_t tk = u16 ? 2u : 3u, swm = u16 ? 0x1Eu : 0x1Cu;
     const uint32_t m = np + (hi > lo ? hi - lo : 0u);
     const uint32_t rc = fused_round(blockDim.x, a.K);
     for (uint32_t base = 0; base < m; base += rc) {
@@ -871,46 +842,21 @@ __device__ __forceinline__ void fused_test_cands(const Geom &g, const Work &w, c
         uint32_t has = 0;
         uint4 ent = make_uint4(0u, 0u, 0u, 0u);
         if (tid < rc && k < m) {
-            const uint32_t *rp, *up = nullptr, *dp = nullptr;
-            uint32_t rk, rs = 0, uk = 0, us = 0, dk = 0, ds = 0, j, lin;
+            uint32_t i, j;
             if (k < np) {
+                i = iA - 1;
                 j = pl[k];
-                rp = carry + nb;
-                rk = 1u;
-                if (up_ok) {
-                    up = carry;
-                    uk = 1u;
-                }
-                dp = tile;
-                dk = tk;
-                ds = row_hash(0) & swm;
-                lin = row_lin_base - nb + j;
             } else {
                 const uint32_t key = srt[lo + k - np];
                 const uint32_t r = key / nb;
+                i = iA + r;
                 j = key - r * nb;
-                rp = tile + r * pitch;
-                rk = tk;
-                rs = row_hash(r) & swm;
-                if (r > 0) {
-                    up = rp - pitch;
-                    uk = tk;
-                    us = row_hash(r - 1) & swm;
-                } else if (iA > 0) {
-                    up = carry + nb;
-                    uk = 1u;
-                }
-                if (iA + r + 1 < g.na) {
-                    dp = rp + pitch;
-                    dk = tk;
-                    ds = row_hash(r + 1) & swm;
-                }
-                lin = row_lin_base + key;
             }
-            const uint32_t v = cell_at(rp, rk, rs, j);
-            if (peak_at(rp, rk, rs, up, uk, us, dp, dk, ds, j, nb, v)) {
+            const uint32_t *row = Ms + (size_t)i * nb;
+            const uint32_t v = __ldcg(row + j);
+            if (is_peak_l2(row, i > 0 ? row - nb : nullptr, i + 1 < g.na ? row + nb : nullptr, j, nb, v)) {
                 has = 1;
-                ent = make_uint4(lin, e, v, 0u);
+                ent = make_uint4(slice_lin0 + i * nb + j, e, v, 0u);
             }
         }
         if (__syncthreads_or(has)) {
@@ -922,74 +868,46 @@ __device__ __forceinline__ void fused_test_cands(const Geom &g, const Work &w, c
     }
 }
 
-__device__ __forceinline__ RowRef tile_row(const uint32_t *tile, uint32_t r, uint32_t pitch, bool u16)
+// Whole-row test of slice row i from M_H through L2.
+__device__ __forceinline__ void test_row_l2(const Geom &g, const ScanArgs &a, ScanSmem &ss, uint4 *pbuf,
+                                            uint32_t &buf_n, uint32_t &nseq, uint32_t &total, const ChunkList &L,
+                                            uint32_t *status, const uint32_t *Ms, uint32_t i, uint32_t slice_lin0,
+                                            uint32_t e)
 {
-    RowRef x;
-    x.p = tile + r * pitch;
-    x.kind = u16 ? 2u : 3u;
-    x.sw = u16 ? (row_hash(r) & 0x1Eu) : (row_hash(r) & 0x1Cu);
-    return x;
-}
-
-// Copy tile row r (u16 or u32 counters, swizzled) into a plain u32 row.
-__device__ __forceinline__ void copy_tile_row(uint32_t *dst, const uint32_t *tile, uint32_t r, uint32_t pitch,
-                                              bool u16, uint32_t nb)
-{
-    const uint32_t *row = tile + r * pitch;
-    if (u16) {
-        const uint32_t sw = row_hash(r) & 0x1Eu;
-        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x)
-            dst[j] = (row[(j >> 1) ^ sw] >> ((j & 1u) << 4)) & 0xffffu;
-    } else {
-        const uint32_t sw = row_hash(r) & 0x1Cu;
-        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x)
-            dst[j] = row[j ^ sw];
-    }
-}
-
-// Whole-row peak tests of one pass of the fused fill, the fallback when a
-// pass lists more than kFusedCand cells >= T: the pending last row of the
-// previous pass (carry[1], with carry[0] above it when up_ok), then the tile
-// rows r_first .. r_last marked in rows.  Inlined: an out-of-line call makes
-// the kernel keep its parameters in local memory.
-__device__ __forceinline__ void fused_test_rows(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss,
-                                             uint4 *pbuf, uint32_t &buf_n, uint32_t &nseq, uint32_t &total,
-                                             const ChunkList &inner, const uint32_t *tile, const uint32_t *carry,
-                                             uint32_t pitch, bool u16, bool pend, bool up_ok, uint64_t rows,
-                                             uint32_t r_first, int32_t r_last, uint32_t iA, uint32_t row_lin_base,
-                                             uint32_t e)
-{
-    const uint32_t nb = g.nb;
-    const RowRef none{nullptr, 0u, 0u};
-    if (pend) {
-        const RowRef up = up_ok ? RowRef{carry, 1u, 0u} : none;
-        test_row_ref(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, up, RowRef{carry + nb, 1u, 0u},
-                     tile_row(tile, 0, pitch, u16), row_lin_base - nb, e);
-    }
-    for (int32_t rr = (int32_t)r_first; rr <= r_last; ++rr) {
-        if (!((rows >> rr) & 1ull))
-            continue;
-        RowRef up = none, dn = none;
-        if (iA + rr > 0)
-            up = rr > 0 ? tile_row(tile, rr - 1, pitch, u16) : RowRef{carry + nb, 1u, 0u};
-        if (iA + rr + 1 < g.na)
-            dn = tile_row(tile, rr + 1, pitch, u16);
-        test_row_ref(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, up, tile_row(tile, rr, pitch, u16), dn,
-                     row_lin_base + (uint32_t)rr * nb, e);
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb, T = g.threshold;
+    const uint32_t *row = Ms + (size_t)i * nb;
+    const uint32_t *up = i > 0 ? row - nb : nullptr, *dn = i + 1 < g.na ? row + nb : nullptr;
+    const uint32_t per_round = bd / 2 + 1;    // no two peaks are neighbours
+    for (uint32_t j0 = 0; j0 < nb; j0 += bd) {
+        const uint32_t j = j0 + tid;
+        uint32_t cnt = 0, pj[1], pv[1];
+        if (j < nb) {
+            const uint32_t v = __ldcg(row + j);
+            if (v >= T && is_peak_l2(row, up, dn, j, nb, v)) {
+                pj[0] = j;
+                pv[0] = v;
+                cnt = 1;
+            }
+        }
+        if (__syncthreads_or(cnt)) {
+            if (buf_n + per_round > a.K)
+                flush_chunk(a, ss, pbuf, buf_n, nseq, L, status);
+            compact_round(ss, pbuf, buf_n, cnt, pj, pv, slice_lin0 + i * nb, e, a.ev_count);
+            total += ss.round_total;
+        }
     }
 }
 
 __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, ScanArgs a)
 {
     extern __shared__ uint4 sm4[];
-    // layout: ScanSmem (256 B) | K peak entries | tile | HC staged hits | 2 carried rows |
-    //         B thresholds | 3 candidate lists (pass cells, sorted, pending row)
+    // layout: ScanSmem (256 B) | K peak entries | tile | HC staged hits | B thresholds |
+    //         3 candidate lists (pass cells, sorted, pending row)
     ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
     uint4 *pbuf = sm4 + 16;
     uint32_t *tile = reinterpret_cast<uint32_t *>(pbuf + a.K);
     float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
-    uint32_t *carry = reinterpret_cast<uint32_t *>(hs + c.HC);   // [2][nb]
-    float *beta = reinterpret_cast<float *>(carry + 2 * g.nb);     // nb + 1 thresholds
+    float *beta = reinterpret_cast<float *>(hs + c.HC);            // nb + 1 thresholds
     uint32_t *cand = reinterpret_cast<uint32_t *>(beta + c.beta_words);
     uint32_t *srt = cand + kFusedCand, *pl = srt + kFusedCand;
     __shared__ uint32_t s_sel[3], s_hot[2], s_nc, s_bounds[2];
@@ -1008,12 +926,12 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
     uint32_t cached_n = 0;
     uint32_t buf_n = 0, nseq = 0, total = 0;
 
-    // carry state: carry[1] holds global row gP, carry[0] row gP - 1.  Row
-    // gP is pending when it still needs its test: pend_mode 1 with its np_pend
-    // cells >= T listed in pl, 2 with a cell >= T but no list (overflow).
-    bool carry1 = false, carry0 = false;
-    uint32_t pend_mode = 0, np_pend = 0;
+    // gP: the last row (global row index) this CTA wrote.  It is pending
+    // when it still needs its test: pend_mode 1 with its np_pend cells >= T
+    // listed in pl, 2 with a cell >= T but no list (too many).
+    bool have_prev = false;
     uint64_t gP = 0;
+    uint32_t pend_mode = 0, np_pend = 0;
 
     for (uint64_t item = it0; item < it1; ++item) {
         const uint32_t k = (uint32_t)(item % c.strips);
@@ -1027,6 +945,8 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
         const bool u16 = (h1 - h0) < 65536u;
         const uint32_t rpass = u16 ? c.W : c.W / 2;
         const uint32_t pitch = u16 ? c.pitch16 : c.pitch32;
+        const uint32_t slice_lin0 = s * g.na * nb;
+        const uint32_t *Ms = w.M + (size_t)e * w.n_cells + slice_lin0;
         uint32_t *Mrow = w.M + (size_t)e * w.n_cells + ((size_t)s * g.na + i0) * g.nb;
         const uint32_t r = tid % rpass, hl = tid / rpass, hstride = bd / rpass;
 
@@ -1034,17 +954,16 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
             const uint32_t pr = min(rpass, rows - p0);
             const uint32_t iA = i0 + p0;
             const uint64_t gA = es * g.na + iA;
-            if (carry1 && gP + 1 != gA)
-                carry1 = carry0 = false;          // a new slice starts
+            const bool prev_adj = have_prev && gP + 1 == gA;   // row iA - 1 is this CTA's
             // ---- vote -------------------------------------------------------
             const uint32_t i = iA + r;
             if (cached_es == es) {
                 __syncthreads();
                 if (r < pr) {
                     if (u16)
-                        vote_rows<true>(g, tile, hs, beta,cached_n, r, i, hl, hstride, pitch);
+                        vote_rows<true>(g, tile, hs, beta, cached_n, r, i, hl, hstride, pitch);
                     else
-                        vote_rows<false>(g, tile, hs, beta,cached_n, r, i, hl, hstride, pitch);
+                        vote_rows<false>(g, tile, hs, beta, cached_n, r, i, hl, hstride, pitch);
                 }
             } else {
                 cached_es = ~0ull;
@@ -1059,36 +978,33 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
                     first = false;
                     if (r < pr) {
                         if (u16)
-                            vote_rows<true>(g, tile, hs, beta,nsel, r, i, hl, hstride, pitch);
+                            vote_rows<true>(g, tile, hs, beta, nsel, r, i, hl, hstride, pitch);
                         else
-                            vote_rows<false>(g, tile, hs, beta,nsel, r, i, hl, hstride, pitch);
+                            vote_rows<false>(g, tile, hs, beta, nsel, r, i, hl, hstride, pitch);
                     }
                 }
             }
             if (tid == 0)
                 s_hot[0] = s_hot[1] = s_nc = 0u;
             __syncthreads();
-            // ---- write the pass to M_H; list the cells >= T, mark their rows -
+            // ---- write the pass to M_H and clear the tile; list cells >= T ---
+            const FlushList fl{s_hot, cand, &s_nc, kFusedCand};
             if (u16)
-                flush_rows_mark<true>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, s_hot, cand, &s_nc,
-                                      kFusedCand);
+                flush_tile<true, true>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, false, fl);
             else
-                flush_rows_mark<false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, s_hot, cand, &s_nc,
-                                       kFusedCand);
-            __syncthreads();
+                flush_tile<false, true>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, false, fl);
+            __syncthreads();   // M_H rows of the pass and the lists visible to the block
             const uint64_t hotm = (uint64_t)s_hot[0] | ((uint64_t)s_hot[1] << 32);
             const uint32_t n_c = s_nc;
             // ---- rows to test now, in order ----------------------------------
-            const bool test_pend = pend_mode != 0 && carry1 && gP + 1 == gA;
-            const bool up_ok = carry0 && (gP % g.na) != 0;
-            const uint32_t r_first = (iA == 0 || carry1) ? 0u : 1u;   // else row 0 is the seam
+            const bool test_pend = pend_mode != 0 && prev_adj;
+            const uint32_t r_first = (iA == 0 || prev_adj) ? 0u : 1u;   // else row 0 is the seam
             const bool last_is_end = iA + pr - 1 == g.na - 1;
             const int32_t r_last = last_is_end ? (int32_t)pr - 1 : (int32_t)pr - 2;
             const uint64_t want = r_last < (int32_t)r_first ? 0ull
                                 : ((~0ull >> (63 - r_last)) >> r_first) << r_first;
             // the last row waits for the next pass unless it ends the slice or is the seam row
             const bool pend_next = !last_is_end && pr - 1 >= r_first;
-            const uint32_t row_lin_base = (uint32_t)((uint64_t)s * g.na + iA) * nb;
             const bool fits = n_c <= kFusedCand;
             uint32_t lo = 0, hi = 0;
             if (fits && n_c) {
@@ -1100,18 +1016,22 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
                 // candidate lists: the pending row's cells, then rows r_first .. r_last
                 const uint32_t np = test_pend ? np_pend : 0u;
                 if (np || hi > lo)
-                    fused_test_cands(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, carry, pitch, u16, pl,
-                                     np, up_ok, srt, lo, hi, iA, row_lin_base, e);
+                    fused_test_cands(g, w, a, ss, pbuf, buf_n, nseq, total, inner, Ms, pl, np, srt, lo, hi, iA,
+                                     slice_lin0, e);
             } else if (test_pend || (hotm & want)) {
                 // too many candidates: test whole rows (a pending row holds a cell >= T)
-                fused_test_rows(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, carry, pitch, u16, test_pend,
-                                up_ok, hotm & want, r_first, r_last, iA, row_lin_base, e);
+                if (test_pend)
+                    test_row_l2(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, Ms, iA - 1, slice_lin0, e);
+                for (int32_t rr = (int32_t)r_first; rr <= r_last; ++rr)
+                    if ((hotm >> rr) & 1ull)
+                        test_row_l2(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, Ms, iA + (uint32_t)rr,
+                                    slice_lin0, e);
             }
             uint32_t next_mode = 0;
             if (pend_next) {
                 if (fits) {
                     if (n_c > hi) {
-                        __syncthreads();
+                        __syncthreads();   // the pending list of this pass was read
                         for (uint32_t q = hi + tid; q < n_c; q += bd)
                             pl[q - hi] = srt[q] - (pr - 1) * nb;
                         np_pend = n_c - hi;
@@ -1121,25 +1041,10 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
                     next_mode = 2;
                 }
             }
-            // ---- carry the last two rows; clear the tile --------------------
-            __syncthreads();
-            if (pr >= 2) {
-                copy_tile_row(carry, tile, pr - 2, pitch, u16, nb);
-                copy_tile_row(carry + nb, tile, pr - 1, pitch, u16, nb);
-                carry0 = true;
-            } else {
-                for (uint32_t j = tid; j < nb; j += bd)
-                    carry[j] = carry[nb + j];
-                __syncthreads();
-                copy_tile_row(carry + nb, tile, 0, pitch, u16, nb);
-                carry0 = carry1;
-            }
-            carry1 = true;
+            have_prev = true;
             gP = gA + pr - 1;
             pend_mode = next_mode;
-            __syncthreads();
-            for (uint32_t q = tid; q < pr * pitch / 4; q += bd)
-                reinterpret_cast<uint4 *>(tile)[q] = make_uint4(0u, 0u, 0u, 0u);
+            __syncthreads();   // lists and counters free for the next pass
         }
     }
     flush_chunk(a, ss, pbuf, buf_n, nseq, inner, w.status);
@@ -1421,7 +1326,7 @@ cudaError_t launch_bin(const Geom &g, const Work &w, uint32_t grid, cudaStream_t
 size_t fill_scan_smem_bytes(const FillCfg &c, const ScanArgs &a, uint32_t nb)
 {
     return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)c.tile_words * 4 + (size_t)c.HC * 16 +
-           (size_t)2 * nb * 4 + (size_t)c.beta_words * 4 + (size_t)3 * kFusedCand * 4;
+           (size_t)c.beta_words * 4 + (size_t)3 * kFusedCand * 4;
 }
 
 cudaError_t launch_fill_scan(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
