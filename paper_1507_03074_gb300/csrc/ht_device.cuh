@@ -40,12 +40,18 @@ struct Work {
     const uint32_t *hit_off;    // [n_events + 1] or nullptr: one event, n_hits0 hits
     uint32_t n_hits0;           // with hit_off: the bound every offset is clamped to (staging size)
     uint32_t n_events;
-    float4 *hits4;              // per hit: {x, x^2 + y^2, 2y, 0}
+    float4 *hits4;              // per hit: {x, x^2 + y^2, 2y, event (bits)}
     uint32_t *codes;            // per hit: (itheta << 16) | iphi, or kDropped
     uint32_t *M;                // vote matrices
     uint64_t n_cells;           // per event
     uint32_t *status;
-    uint32_t *ctr;              // counter block; k_bin zeroes words [1, 4 + n_events)
+    uint32_t *ctr;              // counter block (htk::CTR_*)
+    // hits grouped by (event, slice) unit u = e * n_slices + s
+    uint32_t *slice_cnt;        // [n_events * n_slices] hits per unit (k_bin counts, k_scatter clears)
+    uint32_t *slice_fill;       // [n_events * n_slices] scatter cursors (k_bin's last block clears)
+    uint32_t *slice_off;        // [n_events * n_slices + 1] exclusive prefix of slice_cnt
+    float4 *list;               // list_cap hit records {x, x^2 + y^2, 2y, event}, unit by unit
+    uint32_t list_cap;
 };
 
 constexpr uint32_t kDropped = 0xffffffffu;
@@ -263,6 +269,14 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
             smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+
+// One arrival (release semantics, CTA scope) on a barrier initialised with
+// the number of arriving threads.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)

@@ -3,6 +3,7 @@
 #include "ht_geom.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 
@@ -15,8 +16,8 @@ static const uint32_t kScanThreads = 256;
 static const uint32_t kPeakBuf = 1024;         // K: entries buffered per scan / seam CTA
 static const uint32_t kFusedPeakBuf = 512;     // K of a fused-fill CTA (at least its block)
 
-const char *const kKernelNames[K_NKINDS] = {"k_bin", "k_fill_priv", "k_fill_scan", "k_seam", "k_clear",
-                                             "k_fill_naive", "k_scan", "k_order"};
+const char *const kKernelNames[K_NKINDS] = {"k_bin", "k_scatter", "k_fill_priv", "k_fill_scan", "k_fill_ws",
+                                             "k_seam", "k_clear", "k_fill_naive", "k_scan", "k_order"};
 
 // ---------------------------------------------------------------------------
 // Profiling
@@ -122,11 +123,11 @@ ht_status engine_configure(Engine &E, std::string *why)
         *why = "fill_threads must be 256, 512 or 1024";
         return HT_E_INVAL;
     }
-    if (t.fused > 2) {
-        *why = "fused must be 0 (auto), 1 (on) or 2 (off)";
+    if (t.fused > 3) {
+        *why = "fused must be 0 (auto), 1 (on), 2 (off) or 3 (warp-specialised)";
         return HT_E_INVAL;
     }
-    f.HC = std::max(t.fill_HC ? t.fill_HC : 2048u, 2 * f.threads);   // select_hits needs HC >= 2 * threads
+    f.HC = std::max(t.fill_HC ? t.fill_HC : 2048u, 2 * f.threads);   // hits staged per chunk
     f.pitch16 = round_up((b.n_b + 1) / 2, 32);
     f.pitch32 = round_up(b.n_b, 32);
     f.beta_words = round_up(b.n_b + 1, 4);
@@ -198,6 +199,32 @@ ht_status engine_configure(Engine &E, std::string *why)
             E.fused_grid = (uint32_t)E.num_sms * (uint32_t)occ;
         }
     }
+    // --- warp-specialised fused fill: two tiles, one CTA per SM -------------------
+    E.ws_ok = false;
+    if (E.fill_priv_ok && (t.fused == 0 || t.fused == 3) && W <= 64 && b.n_b <= 4096 &&
+        (!t.fill_threads || t.fill_threads == htk::kWsThreads / 2)) {
+        htk::ScanArgs tmp{};
+        tmp.K = E.fused_K;
+        htk::FillCfg wf = f;
+        wf.threads = htk::kWsThreads / 2;
+        wf.HC = std::max(wf.HC, 2 * wf.threads);
+        while (!t.fill_HC && wf.HC > 2 * wf.threads && htk::fill_ws_smem_bytes(wf, tmp) > kSmemMax)
+            wf.HC -= wf.threads;
+        int occ = 0;
+        if (wf.threads % W == 0 && htk::fill_ws_smem_bytes(wf, tmp) <= kSmemMax &&
+            htk::fill_ws_occupancy(wf, tmp, &occ) == cudaSuccess && occ >= 1) {
+            E.ws_ok = true;
+            E.ws_fill = wf;
+            E.ws_grid = (uint32_t)E.num_sms * (uint32_t)occ;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (t.fused == 3 && !E.ws_ok) {
+        *why = "the warp-specialised fused fill does not fit this binning and tuning";
+        return HT_E_INVAL;
+    }
+    E.use_ws = E.ws_ok;
     if (t.fused == 1 && !E.fused_ok) {
         *why = "the fused fill does not fit this binning and tuning";
         return HT_E_INVAL;
@@ -255,12 +282,27 @@ ht_status engine_configure(Engine &E, std::string *why)
     const uint32_t scan_grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.scan_grid_max, G_max));
     const uint64_t items_max = (uint64_t)E.max_events * g.n_slices * f.strips;
     const uint32_t fused_grid = E.fused_ok ? (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.fused_grid, items_max)) : 0;
-    const uint32_t grid_cap = std::max(scan_grid, fused_grid);
+    const uint32_t ws_grid = E.ws_ok ? (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.ws_grid, items_max)) : 0;
+    const uint32_t grid_cap = std::max(std::max(scan_grid, fused_grid), ws_grid);
     uint32_t seq = chunks_for((G_max + scan_grid - 1) / scan_grid + 1, g.nb, s.K, 2 * kScanThreads);
+    // the cost-balanced split gives a CTA at most `spread` times the items of
+    // an even split (every strip costs at least its n_b-per-row writing share)
+    const double hits_per_unit = (double)std::max<uint32_t>(E.max_hits, 1) * E.max_admit /
+                                 ((double)E.max_events * g.n_slices);
+    const double spread = 1.0 + htk::kVoteWeight * hits_per_unit / g.nb;
+    auto rows_per_cta = [&](uint32_t grid) {
+        return (uint64_t)(std::ceil((double)items_max / grid * spread) + 2) * f.W + 1;
+    };
     if (E.fused_ok) {
-        const uint64_t fused_rows = ((items_max + fused_grid - 1) / fused_grid) * f.W + 1;
+        const uint64_t fused_rows = rows_per_cta(fused_grid);
         const uint32_t per_round = std::max(f.threads / 2 + 1, htk::fused_round(f.threads, E.fused_K));
         seq = std::max(seq, chunks_for(fused_rows, g.nb, E.fused_K, per_round));
+    }
+    if (E.ws_ok) {
+        const uint64_t ws_rows = rows_per_cta(ws_grid);
+        const uint32_t wt = E.ws_fill.threads;
+        const uint32_t per_round = std::max(wt / 2 + 1, htk::fused_round(wt, E.fused_K));
+        seq = std::max(seq, chunks_for(ws_rows, g.nb, E.fused_K, per_round));
     }
     s.seq_max = seq;
     const size_t desc_b = (size_t)grid_cap * seq * 8, bnd_b = (size_t)grid_cap * htk::kSeamChunks * 8;
@@ -376,10 +418,15 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
     size_t acc = 0;
     const size_t hits_cap = (size_t)std::max<uint32_t>(max_hits, 1);
     const uint32_t ctr_words = engine_ctr_words(E);
+    const size_t units = (size_t)max_events * g.n_slices;
+    const uint64_t list_cap = std::min<uint64_t>((uint64_t)hits_cap * E.max_admit, 0xffffffffull);
+    E.list_cap = (uint32_t)list_cap;
     if ((e = dalloc(&E.d_edges, (E.et.size() + E.ep.size() + E.bth.size()) * 4, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_M, (size_t)E.n_cells * 4 * max_events + 256, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_hits4, hits_cap * 16, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_codes, hits_cap * 4, &acc)) != cudaSuccess ||
+        (e = dalloc(&E.d_slice, (3 * units + 1) * 4, &acc)) != cudaSuccess ||
+        (e = dalloc(&E.d_list, (size_t)list_cap * 16, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_entries, (size_t)s.entries_cap * 16, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_ctr, (size_t)ctr_words * 4, &acc)) != cudaSuccess) {
         std::snprintf(buf, sizeof buf, "device allocation of %zu bytes failed: %s", acc,
@@ -399,6 +446,7 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
         (e = cudaMemcpy(E.d_edges + E.et.size() + E.ep.size(), E.bth.data(), E.bth.size() * 4,
                         cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(E.d_ctr, 0, (size_t)ctr_words * 4)) != cudaSuccess ||
+        (e = cudaMemset(E.d_slice, 0, (3 * units + 1) * 4)) != cudaSuccess ||
         (e = cudaMemset(E.d_M, 0, (size_t)E.n_cells * 4 * max_events)) != cudaSuccess) {
         std::snprintf(buf, sizeof buf, "device initialisation failed: %s", cudaGetErrorString(e));
         *why = buf;
@@ -450,6 +498,8 @@ void engine_destroy(Engine &E)
     cudaFree(E.d_M);
     cudaFree(E.d_hits4);
     cudaFree(E.d_codes);
+    cudaFree(E.d_slice);
+    cudaFree(E.d_list);
     cudaFree(E.d_entries);
     cudaFree(E.d_book);
     cudaFree(E.d_ctr);
@@ -457,6 +507,8 @@ void engine_destroy(Engine &E)
     E.d_M = nullptr;
     E.d_hits4 = nullptr;
     E.d_codes = nullptr;
+    E.d_slice = nullptr;
+    E.d_list = nullptr;
     E.d_entries = nullptr;
     E.d_book = nullptr;
     E.d_ctr = nullptr;
@@ -479,6 +531,12 @@ static htk::Work make_work(Engine &E, const float *x, const float *y, const floa
     w.n_cells = E.n_cells;
     w.status = engine_status(E);
     w.ctr = E.d_ctr;
+    const size_t units = (size_t)E.max_events * E.geom.n_slices;
+    w.slice_cnt = E.d_slice;
+    w.slice_fill = E.d_slice + units;
+    w.slice_off = E.d_slice + 2 * units;
+    w.list = E.d_list;
+    w.list_cap = E.list_cap;
     return w;
 }
 
@@ -493,6 +551,14 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
         ProfScope ps(E, K_BIN, st);
         const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((n_total + 255) / 256, E.num_sms * 8));
         e = htk::launch_bin(E.geom, w, grid, st);
+    }
+    if (e != cudaSuccess)
+        return e;
+    ++E.launches;
+    {
+        ProfScope ps(E, K_SCATTER, st);
+        const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((n_total + 255) / 256, E.num_sms * 8));
+        e = htk::launch_scatter(E.geom, w, grid, st);
     }
     if (e != cudaSuccess)
         return e;
@@ -527,15 +593,17 @@ cudaError_t engine_vote(Engine &E, const uint32_t *d_hit_off, uint32_t n_hits0, 
     htk::FillCfg f = E.fill;
     f.accumulate = accumulate ? 1u : 0u;
     const uint64_t items = (uint64_t)n_events * E.geom.n_slices * f.strips;
-    if (E.fused_ok && !accumulate) {
+    if ((E.use_ws || E.fused_ok) && !accumulate) {
         htk::ScanArgs a = E.scan;
         a.K = E.fused_K;
-        htk::FillCfg ff = E.fused_fill;
+        htk::FillCfg ff = E.use_ws ? E.ws_fill : E.fused_fill;
         ff.accumulate = 0u;
-        const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.fused_grid, items));
+        const uint32_t grid =
+            (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.use_ws ? E.ws_grid : E.fused_grid, items));
         {
-            ProfScope ps(E, K_FILL_SCAN, st);
-            e = htk::launch_fill_scan(E.geom, w, ff, a, grid, st);
+            ProfScope ps(E, E.use_ws ? K_FILL_WS : K_FILL_SCAN, st);
+            e = E.use_ws ? htk::launch_fill_ws(E.geom, w, ff, a, grid, st)
+                         : htk::launch_fill_scan(E.geom, w, ff, a, grid, st);
         }
         ++E.launches;
         if (e == cudaSuccess) {
@@ -638,10 +706,12 @@ ht_status engine_autotune(Engine &E, uint32_t reps, cudaStream_t st, double *bes
     std::vector<Tuning> cands;
     const uint32_t rows_opts[] = {16, 32};
     const uint32_t thr_opts[] = {256, 512};
-    for (uint32_t fused = 1; fused <= 2; ++fused)
+    for (uint32_t fused = 1; fused <= 3; ++fused)
         for (uint32_t W : rows_opts)
             for (uint32_t th : thr_opts)
                 for (uint32_t kind = 1; kind <= (fused == 2 ? 2u : 1u); ++kind) {
+                    if (fused == 3 && th != htk::kWsThreads / 2)
+                        continue;                // one group size for the warp-specialised kernel
                     Tuning t = user;
                     t.fused = fused;
                     t.fill_W = W;
@@ -738,7 +808,7 @@ void engine_get_tuning(const Engine &E, ht_tuning *t)
     t->scan_stage_bytes = E.scan.slot_words * 4;
     t->scan_slots = E.scan.S;
     t->scan_blocks_per_sm = E.num_sms ? E.scan_grid_max / (uint32_t)E.num_sms : 0;
-    t->fill_fused_scan = E.fused_ok ? 1u : 2u;
+    t->fill_fused_scan = E.use_ws ? 3u : E.fused_ok ? 1u : 2u;
 }
 
 cudaError_t prof_read(Engine &E, ht_kernel_time *out, uint32_t cap, uint32_t *n)

@@ -23,12 +23,14 @@ struct Tuning {
     uint32_t scan_stage_bytes = 0;    // bulk-copy stage size
     uint32_t scan_slots = 0;          // bulk-copy ring depth (2..8)
     uint32_t scan_blocks_per_sm = 0;  // cap below the occupancy limit
-    uint32_t fused = 0;               // 0 auto (on when possible), 1 on, 2 off
+    uint32_t fused = 0;               // 0 auto, 1 fused (one thread group), 2 off, 3 fused warp-specialised
 };
 
 // Optional per-kernel timing with CUDA events recorded on the launching
 // stream around every launch (enabled by ht_profile).
-enum KernelKind { K_BIN, K_FILL_PRIV, K_FILL_SCAN, K_SEAM, K_CLEAR, K_FILL_NAIVE, K_SCAN, K_ORDER, K_NKINDS };
+enum KernelKind {
+    K_BIN, K_SCATTER, K_FILL_PRIV, K_FILL_SCAN, K_FILL_WS, K_SEAM, K_CLEAR, K_FILL_NAIVE, K_SCAN, K_ORDER, K_NKINDS
+};
 extern const char *const kKernelNames[K_NKINDS];
 
 struct Prof {
@@ -60,6 +62,10 @@ struct Engine {
     htk::FillCfg fused_fill{};   // its tile / staging shape
     uint32_t fused_grid = 0;
     uint32_t fused_K = 0;
+    bool ws_ok = false;          // the warp-specialised fused kernel fits
+    htk::FillCfg ws_fill{};      // its shape (threads = one group)
+    uint32_t ws_grid = 0;
+    bool use_ws = false;         // fills run the warp-specialised kernel
     htk::ScanArgs scan{};
     int scan_kind = 0;            // htk::ScanKind in use
     uint32_t scan_grid_max = 0;
@@ -81,6 +87,9 @@ struct Engine {
     uint32_t *d_M = nullptr;
     float4 *d_hits4 = nullptr;
     uint32_t *d_codes = nullptr;
+    uint32_t *d_slice = nullptr;  // unit counts | scatter cursors | offsets (3 * units + 1)
+    float4 *d_list = nullptr;     // hit records unit by unit
+    uint32_t list_cap = 0;
     uint4 *d_entries = nullptr;
     void *d_book = nullptr;       // desc | desc_bnd | cta arrays
     uint32_t *d_ctr = nullptr;    // counter block (htk::CTR_*)

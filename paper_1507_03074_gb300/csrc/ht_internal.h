@@ -55,6 +55,7 @@ struct OrderArgs {
 };
 
 cudaError_t launch_bin(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
+cudaError_t launch_scatter(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
 size_t fill_smem_bytes(const FillCfg &c);
 cudaError_t launch_fill_priv(const Geom &g, const Work &w, const FillCfg &c, uint32_t grid,
                              cudaStream_t st);
@@ -62,6 +63,13 @@ size_t fill_scan_smem_bytes(const FillCfg &c, const ScanArgs &a, uint32_t nb);
 cudaError_t launch_fill_scan(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
                              cudaStream_t st);
 cudaError_t fill_scan_occupancy(const FillCfg &c, const ScanArgs &a, uint32_t nb, int *blocks_per_sm);
+// Warp-specialised fused fill: kWsThreads threads, two tiles (c.threads is
+// the vote group's size, kWsThreads / 2).
+constexpr uint32_t kWsThreads = 1024;
+size_t fill_ws_smem_bytes(const FillCfg &c, const ScanArgs &a);
+cudaError_t launch_fill_ws(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
+                           cudaStream_t st);
+cudaError_t fill_ws_occupancy(const FillCfg &c, const ScanArgs &a, int *blocks_per_sm);
 cudaError_t launch_seam(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
                         cudaStream_t st);
 cudaError_t launch_clear(uint32_t *M, uint64_t words, uint32_t grid, cudaStream_t st);
@@ -71,9 +79,14 @@ size_t scan_smem_bytes(const ScanArgs &a);
 constexpr uint32_t kSeamChunks = 8;
 
 // Layout of the counter block: [0] status, [1] entries used, [2] order
-// ticket, [3] spare, [4 ..) peaks per event.  k_bin zeroes
-// words [1, 4 + n_events) before every fill.
-enum : uint32_t { CTR_STATUS = 0, CTR_ENTRIES = 1, CTR_OTICKET = 2, CTR_SPARE = 3, CTR_EVENTS = 4 };
+// ticket, [3] binning ticket (reset by k_bin's last block), [4 ..) peaks per
+// event.  k_bin zeroes words 1, 2 and [4, 4 + n_events) before every fill.
+enum : uint32_t { CTR_STATUS = 0, CTR_ENTRIES = 1, CTR_OTICKET = 2, CTR_BTICKET = 3, CTR_EVENTS = 4 };
+
+// Cost model of the balanced split of (event, slice, strip) work items over
+// the fill CTAs: a strip of r rows in a slice of h hits costs
+// r * (n_b + kVoteWeight * h) (writing a cell ~ 1, one vote ~ kVoteWeight).
+constexpr uint32_t kVoteWeight = 6;
 
 // Scan variants: bulk-copy (TMA) ring, register streaming, direct (any n_b).
 // The streaming variant keeps kLdgUPT 16-byte loads per thread in flight.

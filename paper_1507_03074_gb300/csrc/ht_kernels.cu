@@ -30,6 +30,9 @@
 #include "ht_device.cuh"
 #include "ht_internal.h"
 
+#include <atomic>
+#include <utility>
+
 namespace htk {
 
 // ---------------------------------------------------------------------------
@@ -46,6 +49,43 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
     }
     return v;
 }
+
+// Thread groups that share the block-level helpers below: the whole block
+// (barrier 0), or a warp-aligned range of FIRST .. FIRST + N - 1 threads
+// synchronising on named barrier ID (the warp-specialised fill runs two
+// such groups side by side, each with its own barrier).
+struct BlockGroup {
+    static __device__ __forceinline__ uint32_t rank() { return threadIdx.x; }
+    static __device__ __forceinline__ uint32_t size() { return blockDim.x; }
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+    static __device__ __forceinline__ int sync_or(int p) { return __syncthreads_or(p); }
+};
+
+template <uint32_t ID, uint32_t FIRST, uint32_t N>
+struct WarpGroup {
+    static_assert(FIRST % 32 == 0 && N % 32 == 0 && ID >= 1 && ID < 16, "warp-aligned group, named barrier 1..15");
+    static __device__ __forceinline__ uint32_t rank() { return threadIdx.x - FIRST; }
+    static __device__ __forceinline__ uint32_t size() { return N; }
+    static __device__ __forceinline__ void sync() { asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(N) : "memory"); }
+    static __device__ __forceinline__ int sync_or(int p)
+    {
+        uint32_t r;
+        asm volatile("{\n\t.reg .pred pi, po;\n\t"
+                     "setp.ne.u32 pi, %1, 0;\n\t"
+                     "bar.red.or.pred po, %2, %3, pi;\n\t"
+                     "selp.u32 %0, 1, 0, po;\n\t}"
+                     : "=r"(r)
+                     : "r"((uint32_t)p), "n"(ID), "n"(N)
+                     : "memory");
+        return (int)r;
+    }
+};
+
+// Programmatic dependent launch: every kernel here is launched so that it may
+// start while the previous kernel of its stream finishes; it runs only
+// set-up that touches no global data of earlier kernels before this wait
+// (a no-op when the launch had no such dependency).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Exclusive scan of n values in shared memory (in place); returns the total.
 // All threads of the block must call it.  wsum: >= 33 words of scratch.
@@ -87,22 +127,121 @@ __device__ uint32_t block_exclusive_scan(uint32_t *a, uint32_t n, uint32_t *wsum
 __global__ void __launch_bounds__(256) k_bin(Geom g, Work w)
 {
     __shared__ float et[1025], ep[1025];
-    for (uint32_t i = threadIdx.x; i <= g.nt; i += blockDim.x)
+    __shared__ uint32_t s_last, s_wsum[40];
+    extern __shared__ uint32_t s_off[];   // n_events + 1 hit offsets (batches)
+    const uint32_t tid = threadIdx.x, bd = blockDim.x;
+    for (uint32_t i = tid; i <= g.nt; i += bd)
         et[i] = g.et[i];
-    for (uint32_t i = threadIdx.x; i <= g.np; i += blockDim.x)
+    for (uint32_t i = tid; i <= g.np; i += bd)
         ep[i] = g.ep[i];
-    if (blockIdx.x == 0 && w.ctr)   // fresh counters for the fill and scan that follow
-        for (uint32_t i = CTR_ENTRIES + threadIdx.x; i < CTR_EVENTS + w.n_events; i += blockDim.x)
-            w.ctr[i] = 0u;
+    grid_dep_wait();   // counters and hits of earlier kernels
+    if (blockIdx.x == 0) {   // fresh counters for the fill and scan that follow
+        if (tid == 0)
+            w.ctr[CTR_ENTRIES] = w.ctr[CTR_OTICKET] = 0u;
+        for (uint32_t i = tid; i < w.n_events; i += bd)
+            w.ctr[CTR_EVENTS + i] = 0u;
+    }
+    if (w.hit_off)
+        for (uint32_t i = tid; i <= w.n_events; i += bd)
+            s_off[i] = w.hit_off[i];
     __syncthreads();
-    const uint32_t n = w.hit_off ? min(w.hit_off[w.n_events], w.n_hits0) : w.n_hits0;
-    for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
+    const uint32_t n = w.hit_off ? min(s_off[w.n_events], w.n_hits0) : w.n_hits0;
+    for (uint32_t h = blockIdx.x * bd + tid; h < n; h += gridDim.x * bd) {
         const float x = w.x[h], y = w.y[h];
         float r2;
         const uint32_t code = bin_code(g, et, ep, x, y, w.z[h], r2);
-        w.hits4[h] = make_float4(x, r2, __fmul_rn(2.0f, y), 0.0f);
+        uint32_t e = 0;
+        if (w.hit_off) {   // the last event whose first hit is <= h
+            uint32_t lo = 0, hi = w.n_events - 1;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= h)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            e = lo;
+        }
+        w.hits4[h] = make_float4(x, r2, __fmul_rn(2.0f, y), __uint_as_float(e));
         w.codes[h] = code;
+        for_each_slice(g, code, [&](uint32_t s) { atomicAdd(&w.slice_cnt[e * g.n_slices + s], 1u); });
     }
+    // the last block to finish turns the counts into unit offsets
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(&w.ctr[CTR_BTICKET], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last)
+        return;
+    __threadfence();
+    const uint32_t U = w.n_events * g.n_slices;
+    constexpr uint32_t PER = 8;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < U; base += PER * bd) {
+        uint32_t v[PER], sum = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < PER; ++q) {
+            const uint32_t u = base + tid * PER + q;
+            v[q] = u < U ? __ldcg(&w.slice_cnt[u]) : 0u;
+            sum += v[q];
+        }
+        const uint32_t incl = warp_incl_scan(sum);
+        const uint32_t warp = tid >> 5, lane = tid & 31u, nw = (bd + 31) >> 5;
+        if (lane == 31u)
+            s_wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t t = lane < nw ? s_wsum[lane] : 0u;
+            const uint32_t ti = warp_incl_scan(t);
+            s_wsum[lane] = ti - t;
+            if (lane == 31u)
+                s_wsum[32] = ti;
+        }
+        __syncthreads();
+        uint32_t run = carry + s_wsum[warp] + incl - sum;
+#pragma unroll
+        for (uint32_t q = 0; q < PER; ++q) {
+            const uint32_t u = base + tid * PER + q;
+            if (u < U) {
+                w.slice_off[u] = run;
+                w.slice_fill[u] = 0u;
+            }
+            run += v[q];
+        }
+        carry += s_wsum[32];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        w.slice_off[U] = carry;
+        w.ctr[CTR_BTICKET] = 0u;
+    }
+}
+
+// Hits into their units' lists (after k_bin), then clear the unit counts
+// for the next binning.
+__global__ void __launch_bounds__(256) k_scatter(Geom g, Work w)
+{
+    grid_dep_wait();
+    const uint32_t n = w.hit_off ? min(__ldg(&w.hit_off[w.n_events]), w.n_hits0) : w.n_hits0;
+    const uint32_t stride = gridDim.x * blockDim.x, t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint32_t h = t0; h < n; h += stride) {
+        const uint32_t code = w.codes[h];
+        if (code == kDropped)
+            continue;
+        const float4 hv = w.hits4[h];
+        const uint32_t e = __float_as_uint(hv.w);
+        for_each_slice(g, code, [&](uint32_t s) {
+            const uint32_t u = e * g.n_slices + s;
+            const uint32_t idx = w.slice_off[u] + atomicAdd(&w.slice_fill[u], 1u);
+            if (idx < w.list_cap)
+                w.list[idx] = hv;
+        });
+    }
+    const uint32_t U = w.n_events * g.n_slices;
+    for (uint32_t u = t0; u < U; u += stride)
+        w.slice_cnt[u] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -175,36 +314,49 @@ __device__ __forceinline__ void list_cells(const Geom &g, const FlushList &L, ui
 // each step moves 4 cells: consecutive threads write consecutive 16-byte
 // pieces of the row, so every store instruction of a warp covers 512
 // contiguous bytes.
-template <bool U16, bool LIST>
+template <bool U16, bool LIST, bool ACC, class G = BlockGroup>
 __device__ __forceinline__ void flush_tile(const Geom &g, uint32_t *tile, uint32_t *dst, uint32_t rows,
-                                           uint32_t pitch, bool accumulate, const FlushList &L)
+                                           uint32_t pitch, const FlushList &L)
 {
-    const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb;
+    const uint32_t tid = G::rank(), bd = G::size(), nb = g.nb;
+    // one 16-byte unit (4 cells) of row r, column group c4: read + clear the
+    // tile words, write (or add to) M_H at o, list the cells >= T
+    auto unit = [&](uint32_t r, uint32_t c4, uint4 *o) {
+        uint32_t v[4];
+        if (U16) {
+            uint2 *p = reinterpret_cast<uint2 *>(&tile[r * pitch + ((2u * c4) ^ (row_hash(r) & 0x1Eu))]);
+            const uint2 pr = *p;
+            *p = make_uint2(0u, 0u);
+            v[0] = pr.x & 0xffffu; v[1] = pr.x >> 16; v[2] = pr.y & 0xffffu; v[3] = pr.y >> 16;
+        } else {
+            uint4 *p = reinterpret_cast<uint4 *>(&tile[r * pitch + ((4u * c4) ^ (row_hash(r) & 0x1Cu))]);
+            const uint4 pr = *p;
+            *p = make_uint4(0u, 0u, 0u, 0u);
+            v[0] = pr.x; v[1] = pr.y; v[2] = pr.z; v[3] = pr.w;
+        }
+        if (ACC) {
+            const uint4 old = *o;
+            v[0] += old.x; v[1] += old.y; v[2] += old.z; v[3] += old.w;
+        }
+        *o = make_uint4(v[0], v[1], v[2], v[3]);
+        list_cells<LIST>(g, L, r, 4u * c4, v, 4);
+    };
     if ((nb & 3u) == 0) {
         const uint32_t q = nb >> 2;  // 16-byte units per row
-        const uint32_t qs = (q & (q - 1)) ? 32u : (uint32_t)(__ffs(q) - 1);
-        const uint32_t units = rows * q;
-        for (uint32_t u = tid; u < units; u += bd) {
-            const uint32_t r = qs < 32u ? u >> qs : u / q, c4 = u - r * q;
-            uint32_t v[4];
-            if (U16) {
-                uint2 *p = reinterpret_cast<uint2 *>(&tile[r * pitch + ((2u * c4) ^ (row_hash(r) & 0x1Eu))]);
-                const uint2 pr = *p;
-                *p = make_uint2(0u, 0u);
-                v[0] = pr.x & 0xffffu; v[1] = pr.x >> 16; v[2] = pr.y & 0xffffu; v[3] = pr.y >> 16;
-            } else {
-                uint4 *p = reinterpret_cast<uint4 *>(&tile[r * pitch + ((4u * c4) ^ (row_hash(r) & 0x1Cu))]);
-                const uint4 pr = *p;
-                *p = make_uint4(0u, 0u, 0u, 0u);
-                v[0] = pr.x; v[1] = pr.y; v[2] = pr.z; v[3] = pr.w;
+        if (bd % q == 0) {
+            // the group covers whole rows: each thread keeps its column group
+            // and steps down bd / q rows at a time
+            const uint32_t rstep = bd / q, c4 = tid % q;
+            uint4 *o = reinterpret_cast<uint4 *>(dst) + tid;
+            for (uint32_t r = tid / q; r < rows; r += rstep, o += bd)
+                unit(r, c4, o);
+        } else {
+            const uint32_t qs = (q & (q - 1)) ? 32u : (uint32_t)(__ffs(q) - 1);
+            const uint32_t units = rows * q;
+            for (uint32_t u = tid; u < units; u += bd) {
+                const uint32_t r = qs < 32u ? u >> qs : u / q;
+                unit(r, u - r * q, reinterpret_cast<uint4 *>(dst) + u);
             }
-            uint4 *o = reinterpret_cast<uint4 *>(dst) + u;
-            if (accumulate) {
-                const uint4 old = *o;
-                v[0] += old.x; v[1] += old.y; v[2] += old.z; v[3] += old.w;
-            }
-            *o = make_uint4(v[0], v[1], v[2], v[3]);
-            list_cells<LIST>(g, L, r, 4u * c4, v, 4);
         }
     } else {
         const uint32_t units = rows * nb;
@@ -218,82 +370,115 @@ __device__ __forceinline__ void flush_tile(const Geom &g, uint32_t *tile, uint32
                 const uint32_t word = r * pitch + (j ^ (row_hash(r) & 0x1Cu));
                 v = tile[word];
             }
-            v = accumulate ? dst[u] + v : v;
+            v = ACC ? dst[u] + v : v;
             dst[u] = v;
             list_cells<LIST>(g, L, r, j, &v, 1);
         }
-        __syncthreads();
+        G::sync();
         // clear the tile after every thread has read its cells
         for (uint32_t k = tid; k < rows * pitch; k += bd)
             tile[k] = 0u;
     }
 }
 
-// Select, from hit `pos` on in [pos, h1), the hits admitted to slice
-// (ts, ps) into hs[0 .. returned count), kSelHPT hits per thread and
-// iteration (codes and records loaded up front, so one global latency per
-// iteration), stopping at the first block of hits whose admitted hits no
-// longer fit in cap.  Advances `pos` (uniform) by at least kSelHPT *
-// blockDim while pos < h1: the caller guarantees cap >= kSelHPT * blockDim.
-constexpr uint32_t kSelHPT = 2;
-
-__device__ __forceinline__ uint32_t select_hits(const Geom &g, const Work &w, float4 *hs, uint32_t cap,
-                                                uint32_t &pos, uint32_t h1, uint32_t ts, uint32_t ps,
-                                                uint32_t *s_cnt /* 3 words */)
+// Copy up to cap hit records of a unit's list, from list index pos on (pos
+// < end), into hs; advances pos.  All threads of the group call it.
+template <class G = BlockGroup>
+__device__ __forceinline__ uint32_t stage_hits(const Work &w, float4 *hs, uint32_t cap, uint32_t &pos, uint32_t end)
 {
-    const uint32_t tid = threadIdx.x, bd = blockDim.x, lane = tid & 31u;
-    const uint32_t lt = (1u << lane) - 1u;
-    __syncthreads();
-    if (tid == 0)
-        s_cnt[0] = s_cnt[1] = s_cnt[2] = 0u;
-    __syncthreads();
-    uint32_t n = 0;
-    // Each block of kSelHPT * blockDim hits is counted first and taken only
-    // if it fits; one block always fits an empty buffer (cap >= that size).
-    // Block i counts in s_cnt[i % 3]; s_cnt[(i + 1) % 3] is cleared at the
-    // start of block i (its last readers finished before block i-1's barrier).
-    for (uint32_t it = 0; pos < h1; ++it) {
-        if (tid == 0)
-            s_cnt[(it + 1) % 3] = 0u;
-        uint32_t code[kSelHPT];
-        float4 hv[kSelHPT];
+    G::sync();   // the previous readers of hs are done
+    const uint32_t n = min(cap, end - pos);
+    constexpr uint32_t U = 4;
+    for (uint32_t k0 = 0; k0 < n; k0 += U * G::size()) {
+        float4 v[U];
 #pragma unroll
-        for (uint32_t q = 0; q < kSelHPT; ++q) {
-            const uint32_t h = pos + q * bd + tid;
-            code[q] = h < h1 ? w.codes[h] : kDropped;
-            hv[q] = h < h1 ? w.hits4[h] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (uint32_t q = 0; q < U; ++q) {
+            const uint32_t k = k0 + q * G::size() + G::rank();
+            if (k < n)
+                v[q] = __ldg(&w.list[pos + k]);
         }
-        uint32_t m[kSelHPT], tot = 0;
 #pragma unroll
-        for (uint32_t q = 0; q < kSelHPT; ++q) {
-            m[q] = __ballot_sync(0xffffffffu, admits(g, code[q], ts, ps));
-            tot += __popc(m[q]);
+        for (uint32_t q = 0; q < U; ++q) {
+            const uint32_t k = k0 + q * G::size() + G::rank();
+            if (k < n)
+                hs[k] = v[q];
         }
-        uint32_t base = 0;
-        if (lane == 0 && tot)
-            base = atomicAdd(&s_cnt[it % 3], tot);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        __syncthreads();     // every warp has added its count
-        const uint32_t total = s_cnt[it % 3];
-        if (n + total > cap)
-            break;           // uniform: the block does not fit; leave pos on it
-#pragma unroll
-        for (uint32_t q = 0; q < kSelHPT; ++q) {
-            if (m[q] & (1u << lane))
-                hs[n + base + __popc(m[q] & lt)] = hv[q];
-            base += __popc(m[q]);
-        }
-        n += total;
-        pos += kSelHPT * bd;
     }
-    __syncthreads();         // the staged hits are visible to every thread
+    pos += n;
+    G::sync();
     return n;
 }
+
+// The work items [it0, it1) of CTA `cta` of `grid`: the (event, slice,
+// strip) items in order, cut where the estimated cost -- kVoteWeight per
+// (hit, row) vote plus one per cell written -- reaches cta / grid of the
+// total.  A unit u = (event, slice) costs n_a (n_b + kVoteWeight hits(u)), so
+// the cost before unit u is n_a (n_b u + kVoteWeight slice_off[u]); a cut
+// inside a unit falls on a strip boundary.  Every thread of the group calls
+// it and gets the same result; s_res: 2 shared words.
+template <class G = BlockGroup>
+__device__ __forceinline__ void cta_items(const Geom &g, const Work &w, const FillCfg &c, uint32_t cta,
+                                          uint32_t grid, uint64_t &it0, uint64_t &it1, unsigned long long *s_res)
+{
+    const uint32_t U = w.n_events * g.n_slices;
+    const uint64_t items = (uint64_t)U * c.strips;
+    auto cost = [&](uint32_t u) {
+        return (uint64_t)g.na * ((uint64_t)g.nb * u + (uint64_t)kVoteWeight * __ldcg(&w.slice_off[u]));
+    };
+    const uint64_t total = cost(U);
+    const uint64_t T0 = (total / grid) * cta + ((total % grid) * cta) / grid;
+    const uint64_t T1 = (total / grid) * (cta + 1) + ((total % grid) * (cta + 1)) / grid;
+    if (G::rank() == 0)
+        s_res[0] = s_res[1] = items;
+    G::sync();
+    for (uint32_t u = G::rank(); u < U; u += G::size()) {
+        const uint64_t a = cost(u), b = cost(u + 1);
+        const uint64_t per = (b - a + c.strips - 1) / c.strips;   // one strip, rounded up
+        const uint64_t last = c.strips - 1;
+        if (a <= T0 && T0 < b) {
+            const uint64_t k = (T0 - a) / per;
+            s_res[0] = (uint64_t)u * c.strips + (k < last ? k : last);
+        }
+        if (a <= T1 && T1 < b) {
+            const uint64_t k = (T1 - a) / per;
+            s_res[1] = (uint64_t)u * c.strips + (k < last ? k : last);
+        }
+    }
+    G::sync();
+    it0 = s_res[0];
+    it1 = cta + 1 == grid ? items : (uint64_t)s_res[1];
+    G::sync();   // s_res may be reused
+}
+
+// Walks the (event, slice, strip) work items it0, it0 + 1, ... of a CTA with
+// one 64-bit decomposition at the start and carries afterwards (a 64-bit
+// division per item and thread costs more than a strip's flush setup).
+struct ItemCursor {
+    uint32_t k, s, e;   // strip, slice, event
+    uint64_t es;        // e * n_slices + s
+    __device__ __forceinline__ ItemCursor(const Geom &g, const FillCfg &c, uint64_t item)
+    {
+        k = (uint32_t)(item % c.strips);
+        es = item / c.strips;
+        s = (uint32_t)(es % g.n_slices);
+        e = (uint32_t)(es / g.n_slices);
+    }
+    __device__ __forceinline__ void next(const Geom &g, const FillCfg &c)
+    {
+        if (++k == c.strips) {
+            k = 0;
+            ++es;
+            if (++s == g.n_slices) {
+                s = 0;
+                ++e;
+            }
+        }
+    }
+};
 
 __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
 {
     extern __shared__ uint4 sm4[];
-    __shared__ uint32_t s_sel[3];
     uint32_t *tile = reinterpret_cast<uint32_t *>(sm4);
     float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
     float *beta = reinterpret_cast<float *>(hs + c.HC);
@@ -303,24 +488,25 @@ __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
         sm4[k] = make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t k = tid; k <= g.nb; k += bd)
         beta[k] = g.bth[k];
+    grid_dep_wait();   // the unit lists of k_scatter
 
-    const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
-    const uint64_t it0 = items * blockIdx.x / gridDim.x, it1 = items * (blockIdx.x + 1) / gridDim.x;
-    uint64_t cached_es = ~0ull;   // (event, slice) whose whole selection is in hs
+    __shared__ unsigned long long s_rng[2];
+    uint64_t it0, it1;
+    cta_items(g, w, c, blockIdx.x, gridDim.x, it0, it1, s_rng);
+    uint64_t cached_es = ~0ull;   // (event, slice) whose whole hit list is in hs
     uint32_t cached_n = 0;
 
-    for (uint64_t item = it0; item < it1; ++item) {
-        const uint32_t k = (uint32_t)(item % c.strips);
-        const uint64_t es = item / c.strips;
-        const uint32_t s = (uint32_t)(es % g.n_slices);
-        const uint32_t e = (uint32_t)(es / g.n_slices);
-        const uint32_t ts = s / g.np, ps = s - ts * g.np;
-        const uint32_t h0 = ev_hit_begin(w, e), h1 = ev_hit_end(w, e);
+    ItemCursor cur(g, c, it0);
+    for (uint64_t item = it0; item < it1; ++item, cur.next(g, c)) {
+        const uint32_t k = cur.k;
+        const uint64_t es = cur.es;
+        const uint32_t s = cur.s;
+        const uint32_t e = cur.e;
+        const uint32_t l0 = __ldg(&w.slice_off[es]), l1 = __ldg(&w.slice_off[es + 1]);   // the unit's hits
         const uint32_t i0 = k * c.W;
         const uint32_t rows = min(c.W, g.na - i0);
-        // u16 counters are exact while the slice holds < 65536 hits; the
-        // event's hit count bounds that.
-        const bool u16 = (h1 - h0) < 65536u;
+        // u16 counters are exact while the slice holds < 65536 hits
+        const bool u16 = (l1 - l0) < 65536u;
         const uint32_t rpass = u16 ? c.W : c.W / 2;
         const uint32_t pitch = u16 ? c.pitch16 : c.pitch32;
         uint32_t *Mrow = w.M + (size_t)e * w.n_cells + ((size_t)s * g.na + i0) * g.nb;
@@ -339,11 +525,11 @@ __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
                 }
             } else {
                 cached_es = ~0ull;       // hs is about to be overwritten
-                uint32_t pos = h0;
+                uint32_t pos = l0;
                 bool first = true;
-                while (first || pos < h1) {
-                    const uint32_t nsel = select_hits(g, w, hs, c.HC, pos, h1, ts, ps, s_sel);
-                    if (first && pos >= h1) {
+                while (first || pos < l1) {
+                    const uint32_t nsel = stage_hits(w, hs, c.HC, pos, l1);
+                    if (first && pos >= l1) {
                         cached_es = es;   // the whole selection fits: keep it
                         cached_n = nsel;
                     }
@@ -357,10 +543,18 @@ __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
                 }
             }
             __syncthreads();
-            if (u16)
-                flush_tile<true, false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, c.accumulate != 0, FlushList{});
-            else
-                flush_tile<false, false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, c.accumulate != 0, FlushList{});
+            uint32_t *dst = Mrow + (size_t)p0 * g.nb;
+            if (c.accumulate) {
+                if (u16)
+                    flush_tile<true, false, true>(g, tile, dst, pr, pitch, FlushList{});
+                else
+                    flush_tile<false, false, true>(g, tile, dst, pr, pitch, FlushList{});
+            } else {
+                if (u16)
+                    flush_tile<true, false, false>(g, tile, dst, pr, pitch, FlushList{});
+                else
+                    flush_tile<false, false, false>(g, tile, dst, pr, pitch, FlushList{});
+            }
         }
     }
 }
@@ -370,6 +564,7 @@ __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
 // ---------------------------------------------------------------------------
 __global__ void k_clear(uint32_t *M, uint64_t words)
 {
+    grid_dep_wait();
     const uint64_t n4 = words >> 2;
     uint4 *M4 = reinterpret_cast<uint4 *>(M);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -382,6 +577,7 @@ __global__ void k_clear(uint32_t *M, uint64_t words)
 // 1-D grid over hits, a thread block over A, one atomicAdd per vote.
 __global__ void k_fill_naive(Geom g, Work w)
 {
+    grid_dep_wait();
     for (uint32_t e = 0; e < w.n_events; ++e) {
         const uint32_t h0 = ev_hit_begin(w, e), h1 = ev_hit_end(w, e);
         uint32_t *M = w.M + (size_t)e * w.n_cells;
@@ -445,42 +641,44 @@ __device__ __forceinline__ ChunkList interior_list(const ScanArgs &a, uint32_t c
 }
 
 // Flush the CTA's buffered peaks as one chunk of list L.
+template <class G = BlockGroup>
 __device__ __forceinline__ void flush_chunk(const ScanArgs &a, ScanSmem &ss, const uint4 *pbuf,
                                             uint32_t &buf_n, uint32_t &nseq, const ChunkList &L,
                                             uint32_t *status)
 {
     if (buf_n == 0)
         return;
-    if (threadIdx.x == 0) {
+    if (G::rank() == 0) {
         ss.chunk_base = atomicAdd(a.g_count, buf_n);
         if (nseq < L.cap)
             L.desc[nseq] = make_uint2(ss.chunk_base, buf_n);
         if (nseq >= L.cap || ss.chunk_base + buf_n > a.entries_cap)
             atomicOr(status, (uint32_t)ST_SCRATCH_OVERFLOW);
     }
-    __syncthreads();
+    G::sync();
     const uint32_t base = ss.chunk_base;
-    for (uint32_t k = threadIdx.x; k < buf_n; k += blockDim.x)
+    for (uint32_t k = G::rank(); k < buf_n; k += G::size())
         if (base + k < a.entries_cap)
             a.entries[base + k] = pbuf[k];
     nseq += 1;
     buf_n = 0;
-    __syncthreads();
+    G::sync();
 }
 
 // Ordered compaction of one round: each thread holds cnt peaks in pj/pv
 // (columns of the row starting at row_lin0); appends them to pbuf in
 // thread order and counts them for their event.
+template <class G = BlockGroup>
 __device__ __forceinline__ void compact_round(ScanSmem &ss, uint4 *pbuf, uint32_t &buf_n, uint32_t cnt,
                                               const uint32_t *pj, const uint32_t *pv, uint32_t row_lin0,
                                               uint32_t event, uint32_t *ev_count)
 {
-    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
-    const uint32_t nw = (blockDim.x + 31) >> 5;
+    const uint32_t tid = G::rank(), warp = tid >> 5, lane = tid & 31u;
+    const uint32_t nw = (G::size() + 31) >> 5;
     const uint32_t incl = warp_incl_scan(cnt);
     if (lane == 31u)
         ss.wsum[warp] = incl;
-    __syncthreads();
+    G::sync();
     if (warp == 0) {
         const uint32_t v = lane < nw ? ss.wsum[lane] : 0u;
         const uint32_t vi = warp_incl_scan(v);
@@ -490,25 +688,26 @@ __device__ __forceinline__ void compact_round(ScanSmem &ss, uint4 *pbuf, uint32_
             atomicAdd(&ev_count[event], vi);
         }
     }
-    __syncthreads();
+    G::sync();
     const uint32_t pos = buf_n + ss.wsum[warp] + incl - cnt;
     for (uint32_t k = 0; k < cnt; ++k)
         pbuf[pos + k] = make_uint4(row_lin0 + pj[k], event, pv[k], 0u);
     buf_n += ss.round_total;
-    __syncthreads();
+    G::sync();
 }
 
 // Ordered compaction of one entry per thread (has = 0 or 1): appends the
 // entries to pbuf in thread order and counts them for their events.
+template <class G = BlockGroup>
 __device__ __forceinline__ void compact_entry(ScanSmem &ss, uint4 *pbuf, uint32_t &buf_n, uint32_t has,
                                               const uint4 &ent, uint32_t *ev_count)
 {
-    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
-    const uint32_t nw = (blockDim.x + 31) >> 5;
+    const uint32_t tid = G::rank(), warp = tid >> 5, lane = tid & 31u;
+    const uint32_t nw = (G::size() + 31) >> 5;
     const uint32_t incl = warp_incl_scan(has);
     if (lane == 31u)
         ss.wsum[warp] = incl;
-    __syncthreads();
+    G::sync();
     if (warp == 0) {
         const uint32_t v = lane < nw ? ss.wsum[lane] : 0u;
         const uint32_t vi = warp_incl_scan(v);
@@ -516,13 +715,13 @@ __device__ __forceinline__ void compact_entry(ScanSmem &ss, uint4 *pbuf, uint32_
         if (lane == 31u)
             ss.round_total = vi;
     }
-    __syncthreads();
+    G::sync();
     if (has) {
         pbuf[buf_n + ss.wsum[warp] + incl - 1] = ent;
         atomicAdd(&ev_count[ent.y], 1u);
     }
     buf_n += ss.round_total;
-    __syncthreads();
+    G::sync();
 }
 
 // Detailed pass over global rows [ra, rb): candidates, neighbour tests and
@@ -573,6 +772,7 @@ __device__ void scan_rows_slow(const Geom &g, const Work &w, const ScanArgs &a, 
 // TMA-staged scan (n_b % 4 == 0).
 __global__ void __launch_bounds__(256) k_scan_tma(Geom g, Work w, ScanArgs a)
 {
+    grid_dep_wait();
     extern __shared__ uint4 sm4[];
     // layout: [0, 192) ScanSmem | [192, 256) 8 mbarriers | K peak entries | S stage slots
     ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
@@ -659,6 +859,7 @@ __global__ void __launch_bounds__(256) k_scan_tma(Geom g, Work w, ScanArgs a)
 // Direct-load scan for any n_b (no staging).
 __global__ void __launch_bounds__(256) k_scan_direct(Geom g, Work w, ScanArgs a)
 {
+    grid_dep_wait();
     extern __shared__ uint4 sm4[];
     ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
     uint4 *pbuf = sm4 + 16;
@@ -800,10 +1001,11 @@ __device__ __forceinline__ bool is_peak_l2(const uint32_t *row, const uint32_t *
 // Sort the n <= kFusedCand candidate keys of a pass into srt (keys are
 // distinct: the rank of a key is the number of smaller ones), then find
 // lo / hi, the first positions holding a key >= t_lo / >= t_hi (n if none).
+template <class G = BlockGroup>
 __device__ __forceinline__ void rank_sort_bounds(const uint32_t *cand, uint32_t *srt, uint32_t n, uint32_t t_lo,
                                                  uint32_t t_hi, uint32_t *s_bounds)
 {
-    const uint32_t tid = threadIdx.x, bd = blockDim.x;
+    const uint32_t tid = G::rank(), bd = G::size();
     if (tid == 0)
         s_bounds[0] = s_bounds[1] = n;
     for (uint32_t k = tid; k < n; k += bd) {
@@ -813,7 +1015,7 @@ __device__ __forceinline__ void rank_sort_bounds(const uint32_t *cand, uint32_t 
             rank += cand[m] < key;
         srt[rank] = key;
     }
-    __syncthreads();
+    G::sync();
     for (uint32_t k = tid; k < n; k += bd) {
         const uint32_t key = srt[k], prev = k ? srt[k - 1] : 0u;
         if (key >= t_lo && (k == 0 || prev < t_lo))
@@ -821,22 +1023,23 @@ __device__ __forceinline__ void rank_sort_bounds(const uint32_t *cand, uint32_t 
         if (key >= t_hi && (k == 0 || prev < t_hi))
             s_bounds[1] = k;
     }
-    __syncthreads();
+    G::sync();
 }
 
 // Peak tests of one fused-fill pass from candidate lists, one cell per
 // thread: first the np pending cells (columns of row iA - 1, the previous
 // pass's last row), then the sorted keys srt[lo, hi) (r * n_b + j for row
 // iA + r).  Ms is the slice's M_H; peaks are appended in linear order.
+template <class G = BlockGroup>
 __device__ __forceinline__ void fused_test_cands(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss,
                                                  uint4 *pbuf, uint32_t &buf_n, uint32_t &nseq, uint32_t &total,
                                                  const ChunkList &inner, const uint32_t *Ms, const uint32_t *pl,
                                                  uint32_t np, const uint32_t *srt, uint32_t lo, uint32_t hi,
                                                  uint32_t iA, uint32_t slice_lin0, uint32_t e)
 {
-    const uint32_t tid = threadIdx.x, nb = g.nb;
+    const uint32_t tid = G::rank(), nb = g.nb;
     const uint32_t m = np + (hi > lo ? hi - lo : 0u);
-    const uint32_t rc = fused_round(blockDim.x, a.K);
+    const uint32_t rc = fused_round(G::size(), a.K);
     for (uint32_t base = 0; base < m; base += rc) {
         const uint32_t k = base + tid;
         uint32_t has = 0;
@@ -859,22 +1062,23 @@ __device__ __forceinline__ void fused_test_cands(const Geom &g, const Work &w, c
                 ent = make_uint4(slice_lin0 + i * nb + j, e, v, 0u);
             }
         }
-        if (__syncthreads_or(has)) {
+        if (G::sync_or(has)) {
             if (buf_n + rc > a.K)
-                flush_chunk(a, ss, pbuf, buf_n, nseq, inner, w.status);
-            compact_entry(ss, pbuf, buf_n, has, ent, a.ev_count);
+                flush_chunk<G>(a, ss, pbuf, buf_n, nseq, inner, w.status);
+            compact_entry<G>(ss, pbuf, buf_n, has, ent, a.ev_count);
             total += ss.round_total;
         }
     }
 }
 
 // Whole-row test of slice row i from M_H through L2.
+template <class G = BlockGroup>
 __device__ __forceinline__ void test_row_l2(const Geom &g, const ScanArgs &a, ScanSmem &ss, uint4 *pbuf,
                                             uint32_t &buf_n, uint32_t &nseq, uint32_t &total, const ChunkList &L,
                                             uint32_t *status, const uint32_t *Ms, uint32_t i, uint32_t slice_lin0,
                                             uint32_t e)
 {
-    const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb, T = g.threshold;
+    const uint32_t tid = G::rank(), bd = G::size(), nb = g.nb, T = g.threshold;
     const uint32_t *row = Ms + (size_t)i * nb;
     const uint32_t *up = i > 0 ? row - nb : nullptr, *dn = i + 1 < g.na ? row + nb : nullptr;
     const uint32_t per_round = bd / 2 + 1;    // no two peaks are neighbours
@@ -889,10 +1093,10 @@ __device__ __forceinline__ void test_row_l2(const Geom &g, const ScanArgs &a, Sc
                 cnt = 1;
             }
         }
-        if (__syncthreads_or(cnt)) {
+        if (G::sync_or(cnt)) {
             if (buf_n + per_round > a.K)
-                flush_chunk(a, ss, pbuf, buf_n, nseq, L, status);
-            compact_round(ss, pbuf, buf_n, cnt, pj, pv, slice_lin0 + i * nb, e, a.ev_count);
+                flush_chunk<G>(a, ss, pbuf, buf_n, nseq, L, status);
+            compact_round<G>(ss, pbuf, buf_n, cnt, pj, pv, slice_lin0 + i * nb, e, a.ev_count);
             total += ss.round_total;
         }
     }
@@ -910,18 +1114,20 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
     float *beta = reinterpret_cast<float *>(hs + c.HC);            // nb + 1 thresholds
     uint32_t *cand = reinterpret_cast<uint32_t *>(beta + c.beta_words);
     uint32_t *srt = cand + kFusedCand, *pl = srt + kFusedCand;
-    __shared__ uint32_t s_sel[3], s_hot[2], s_nc, s_bounds[2];
+    __shared__ uint32_t s_hot[2], s_nc, s_bounds[2];
 
     const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb;
     for (uint32_t k = tid; k < c.tile_words / 4; k += bd)
         sm4[16 + a.K + k] = make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t k = tid; k <= nb; k += bd)
         beta[k] = g.bth[k];
+    grid_dep_wait();   // the unit lists of k_scatter
     const uint32_t cta = blockIdx.x;
     const ChunkList inner = interior_list(a, cta);
 
-    const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
-    const uint64_t it0 = items * cta / gridDim.x, it1 = items * (cta + 1) / gridDim.x;
+    __shared__ unsigned long long s_rng[2];
+    uint64_t it0, it1;
+    cta_items(g, w, c, cta, gridDim.x, it0, it1, s_rng);
     uint64_t cached_es = ~0ull;
     uint32_t cached_n = 0;
     uint32_t buf_n = 0, nseq = 0, total = 0;
@@ -933,16 +1139,16 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
     uint64_t gP = 0;
     uint32_t pend_mode = 0, np_pend = 0;
 
-    for (uint64_t item = it0; item < it1; ++item) {
-        const uint32_t k = (uint32_t)(item % c.strips);
-        const uint64_t es = item / c.strips;
-        const uint32_t s = (uint32_t)(es % g.n_slices);
-        const uint32_t e = (uint32_t)(es / g.n_slices);
-        const uint32_t ts = s / g.np, ps = s - ts * g.np;
-        const uint32_t h0 = ev_hit_begin(w, e), h1 = ev_hit_end(w, e);
+    ItemCursor cur(g, c, it0);
+    for (uint64_t item = it0; item < it1; ++item, cur.next(g, c)) {
+        const uint32_t k = cur.k;
+        const uint64_t es = cur.es;
+        const uint32_t s = cur.s;
+        const uint32_t e = cur.e;
+        const uint32_t l0 = __ldg(&w.slice_off[es]), l1 = __ldg(&w.slice_off[es + 1]);   // the unit's hits
         const uint32_t i0 = k * c.W;
         const uint32_t rows = min(c.W, g.na - i0);
-        const bool u16 = (h1 - h0) < 65536u;
+        const bool u16 = (l1 - l0) < 65536u;
         const uint32_t rpass = u16 ? c.W : c.W / 2;
         const uint32_t pitch = u16 ? c.pitch16 : c.pitch32;
         const uint32_t slice_lin0 = s * g.na * nb;
@@ -967,11 +1173,11 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
                 }
             } else {
                 cached_es = ~0ull;
-                uint32_t pos = h0;
+                uint32_t pos = l0;
                 bool first = true;
-                while (first || pos < h1) {
-                    const uint32_t nsel = select_hits(g, w, hs, c.HC, pos, h1, ts, ps, s_sel);
-                    if (first && pos >= h1) {
+                while (first || pos < l1) {
+                    const uint32_t nsel = stage_hits(w, hs, c.HC, pos, l1);
+                    if (first && pos >= l1) {
                         cached_es = es;
                         cached_n = nsel;
                     }
@@ -990,9 +1196,9 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
             // ---- write the pass to M_H and clear the tile; list cells >= T ---
             const FlushList fl{s_hot, cand, &s_nc, kFusedCand};
             if (u16)
-                flush_tile<true, true>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, false, fl);
+                flush_tile<true, true, false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, fl);
             else
-                flush_tile<false, true>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, false, fl);
+                flush_tile<false, true, false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, fl);
             __syncthreads();   // M_H rows of the pass and the lists visible to the block
             const uint64_t hotm = (uint64_t)s_hot[0] | ((uint64_t)s_hot[1] << 32);
             const uint32_t n_c = s_nc;
@@ -1056,6 +1262,233 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
 }
 
 // ---------------------------------------------------------------------------
+// k_fill_ws: the fused fill with warp specialisation, one CTA per SM.
+//
+// 1024 threads in two groups of 16 warps: the vote group stages hits and
+// votes strip passes into one of two shared-memory tiles while the flush
+// group writes the other tile to M_H, clears it and tests the pass's
+// candidate cells (exactly as k_fill_scan does).  Tiles change hands through
+// mbarriers -- FULL[b] (512 vote arrivals: tile b holds a pass) and EMPTY[b]
+// (512 flush arrivals: tile b is clear again) -- with bounded waits, so the
+// votes of pass p + 1 run while pass p streams to HBM.  Each group keeps to
+// its own named barrier; a wait that gives up makes its whole group leave
+// (decided by a group-wide vote) after flagging ST_WAIT_TIMEOUT, and the
+// other group's waits then give up too.
+// ---------------------------------------------------------------------------
+using VoteGroup = WarpGroup<1, 0, 512>;
+using FlushGroup = WarpGroup<2, 512, 512>;
+
+// Geometry of one (event, slice, strip) work item.
+struct ItemInfo {
+    uint64_t es;
+    uint32_t s, e, l0, l1, i0, rows, rpass, pitch;   // l0, l1: the unit's hit list
+    bool u16;
+};
+
+__device__ __forceinline__ ItemInfo item_info(const Geom &g, const Work &w, const FillCfg &c, const ItemCursor &cur)
+{
+    ItemInfo t;
+    const uint32_t k = cur.k;
+    t.es = cur.es;
+    t.s = cur.s;
+    t.e = cur.e;
+    t.l0 = __ldg(&w.slice_off[t.es]);
+    t.l1 = __ldg(&w.slice_off[t.es + 1]);
+    t.i0 = k * c.W;
+    t.rows = min(c.W, g.na - t.i0);
+    t.u16 = (t.l1 - t.l0) < 65536u;
+    t.rpass = t.u16 ? c.W : c.W / 2;
+    t.pitch = t.u16 ? c.pitch16 : c.pitch32;
+    return t;
+}
+
+__global__ void __launch_bounds__(1024, 1) k_fill_ws(Geom g, Work w, FillCfg c, ScanArgs a)
+{
+    extern __shared__ uint4 sm4[];
+    // layout: ScanSmem (256 B) | K peak entries | 2 tiles | HC staged hits | B thresholds |
+    //         3 candidate lists | 4 mbarriers (FULL 0, FULL 1, EMPTY 0, EMPTY 1)
+    ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
+    uint4 *pbuf = sm4 + 16;
+    uint32_t *tiles = reinterpret_cast<uint32_t *>(pbuf + a.K);
+    float4 *hs = reinterpret_cast<float4 *>(tiles + 2 * (size_t)c.tile_words);
+    float *beta = reinterpret_cast<float *>(hs + c.HC);
+    uint32_t *cand = reinterpret_cast<uint32_t *>(beta + c.beta_words);
+    uint32_t *srt = cand + kFusedCand, *pl = srt + kFusedCand;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(pl + kFusedCand);
+    __shared__ uint32_t s_hot[2], s_nc, s_bounds[2];
+
+    const uint32_t tid = threadIdx.x, nb = g.nb;
+    for (uint32_t k = tid; k < c.tile_words / 2; k += blockDim.x)
+        reinterpret_cast<uint4 *>(tiles)[k] = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t k = tid; k <= nb; k += blockDim.x)
+        beta[k] = g.bth[k];
+    if (tid == 0) {
+        for (uint32_t q = 0; q < 4; ++q)
+            mbar_init(&bars[q], VoteGroup::size());
+        fence_mbar_init();
+    }
+    __syncthreads();   // the last block-wide barrier: the groups part here
+    grid_dep_wait();   // the unit lists of k_scatter
+
+    const uint32_t cta = blockIdx.x;
+    __shared__ unsigned long long s_rng[2][2];
+
+    if (tid < VoteGroup::size()) {
+        // ---------------- vote group ----------------
+        const uint32_t vr = VoteGroup::rank();
+        uint64_t it0, it1;
+        cta_items<VoteGroup>(g, w, c, cta, gridDim.x, it0, it1, s_rng[0]);
+        uint64_t cached_es = ~0ull;
+        uint32_t cached_n = 0, p = 0;
+        ItemCursor cur(g, c, it0);
+        for (uint64_t item = it0; item < it1; ++item, cur.next(g, c)) {
+            const ItemInfo t = item_info(g, w, c, cur);
+            const uint32_t r = vr % t.rpass, hl = vr / t.rpass, hstride = VoteGroup::size() / t.rpass;
+            for (uint32_t p0 = 0; p0 < t.rows; p0 += t.rpass, ++p) {
+                const uint32_t pr = min(t.rpass, t.rows - p0);
+                const uint32_t b = p & 1u;
+                uint32_t *tile = tiles + (size_t)b * c.tile_words;
+                if (p >= 2) {
+                    const bool ok = mbar_wait_bounded(&bars[2 + b], ((p >> 1) - 1u) & 1u);
+                    if (VoteGroup::sync_or(!ok)) {
+                        if (vr == 0)
+                            atomicOr(w.status, (uint32_t)ST_WAIT_TIMEOUT);
+                        return;
+                    }
+                }
+                const uint32_t i = t.i0 + p0 + r;
+                if (cached_es == t.es) {
+                    if (r < pr) {
+                        if (t.u16)
+                            vote_rows<true>(g, tile, hs, beta, cached_n, r, i, hl, hstride, t.pitch);
+                        else
+                            vote_rows<false>(g, tile, hs, beta, cached_n, r, i, hl, hstride, t.pitch);
+                    }
+                } else {
+                    cached_es = ~0ull;
+                    uint32_t pos = t.l0;
+                    bool first = true;
+                    while (first || pos < t.l1) {
+                        const uint32_t nsel = stage_hits<VoteGroup>(w, hs, c.HC, pos, t.l1);
+                        if (first && pos >= t.l1) {
+                            cached_es = t.es;
+                            cached_n = nsel;
+                        }
+                        first = false;
+                        if (r < pr) {
+                            if (t.u16)
+                                vote_rows<true>(g, tile, hs, beta, nsel, r, i, hl, hstride, t.pitch);
+                            else
+                                vote_rows<false>(g, tile, hs, beta, nsel, r, i, hl, hstride, t.pitch);
+                        }
+                    }
+                }
+                mbar_arrive(&bars[b]);   // tile b holds pass p
+            }
+        }
+        return;
+    }
+
+    // ---------------- flush + test group ----------------
+    const uint32_t fr = FlushGroup::rank();
+    uint64_t it0, it1;
+    cta_items<FlushGroup>(g, w, c, cta, gridDim.x, it0, it1, s_rng[1]);
+    const ChunkList inner = interior_list(a, cta);
+    uint32_t buf_n = 0, nseq = 0, total = 0, p = 0;
+    bool have_prev = false, alive = true;
+    uint64_t gP = 0;
+    uint32_t pend_mode = 0, np_pend = 0;
+    ItemCursor cur(g, c, it0);
+    for (uint64_t item = it0; item < it1 && alive; ++item, cur.next(g, c)) {
+        const ItemInfo t = item_info(g, w, c, cur);
+        const uint32_t slice_lin0 = t.s * g.na * nb;
+        const uint32_t *Ms = w.M + (size_t)t.e * w.n_cells + slice_lin0;
+        uint32_t *Mrow = w.M + (size_t)t.e * w.n_cells + ((size_t)t.s * g.na + t.i0) * nb;
+        for (uint32_t p0 = 0; p0 < t.rows; p0 += t.rpass, ++p) {
+            const uint32_t pr = min(t.rpass, t.rows - p0);
+            const uint32_t iA = t.i0 + p0;
+            const uint64_t gA = t.es * g.na + iA;
+            const bool prev_adj = have_prev && gP + 1 == gA;
+            const uint32_t b = p & 1u;
+            uint32_t *tile = tiles + (size_t)b * c.tile_words;
+            const bool ok = mbar_wait_bounded(&bars[b], (p >> 1) & 1u);
+            if (FlushGroup::sync_or(!ok)) {
+                if (fr == 0)
+                    atomicOr(w.status, (uint32_t)ST_WAIT_TIMEOUT);
+                alive = false;
+                break;
+            }
+            if (fr == 0)
+                s_hot[0] = s_hot[1] = s_nc = 0u;
+            FlushGroup::sync();
+            // ---- write the pass to M_H and clear the tile; list cells >= T ---
+            const FlushList fl{s_hot, cand, &s_nc, kFusedCand};
+            if (t.u16)
+                flush_tile<true, true, false, FlushGroup>(g, tile, Mrow + (size_t)p0 * nb, pr, t.pitch, fl);
+            else
+                flush_tile<false, true, false, FlushGroup>(g, tile, Mrow + (size_t)p0 * nb, pr, t.pitch, fl);
+            mbar_arrive(&bars[2 + b]);   // tile b is clear
+            FlushGroup::sync();          // M_H rows of the pass and the lists visible to the group
+            const uint64_t hotm = (uint64_t)s_hot[0] | ((uint64_t)s_hot[1] << 32);
+            const uint32_t n_c = s_nc;
+            // ---- rows to test now, in order (as in k_fill_scan) --------------
+            const bool test_pend = pend_mode != 0 && prev_adj;
+            const uint32_t r_first = (iA == 0 || prev_adj) ? 0u : 1u;
+            const bool last_is_end = iA + pr - 1 == g.na - 1;
+            const int32_t r_last = last_is_end ? (int32_t)pr - 1 : (int32_t)pr - 2;
+            const uint64_t want = r_last < (int32_t)r_first ? 0ull
+                                : ((~0ull >> (63 - r_last)) >> r_first) << r_first;
+            const bool pend_next = !last_is_end && pr - 1 >= r_first;
+            const bool fits = n_c <= kFusedCand;
+            uint32_t lo = 0, hi = 0;
+            if (fits && n_c) {
+                rank_sort_bounds<FlushGroup>(cand, srt, n_c, r_first * nb, (uint32_t)(r_last + 1) * nb, s_bounds);
+                lo = s_bounds[0];
+                hi = s_bounds[1];
+            }
+            if (fits && pend_mode != 2) {
+                const uint32_t np = test_pend ? np_pend : 0u;
+                if (np || hi > lo)
+                    fused_test_cands<FlushGroup>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, Ms, pl, np, srt, lo,
+                                                 hi, iA, slice_lin0, t.e);
+            } else if (test_pend || (hotm & want)) {
+                if (test_pend)
+                    test_row_l2<FlushGroup>(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, Ms, iA - 1,
+                                            slice_lin0, t.e);
+                for (int32_t rr = (int32_t)r_first; rr <= r_last; ++rr)
+                    if ((hotm >> rr) & 1ull)
+                        test_row_l2<FlushGroup>(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, Ms,
+                                                iA + (uint32_t)rr, slice_lin0, t.e);
+            }
+            uint32_t next_mode = 0;
+            if (pend_next) {
+                if (fits) {
+                    if (n_c > hi) {
+                        FlushGroup::sync();   // the pending list of this pass was read
+                        for (uint32_t q = hi + fr; q < n_c; q += FlushGroup::size())
+                            pl[q - hi] = srt[q] - (pr - 1) * nb;
+                        np_pend = n_c - hi;
+                        next_mode = 1;
+                    }
+                } else if ((hotm >> (pr - 1)) & 1ull) {
+                    next_mode = 2;
+                }
+            }
+            have_prev = true;
+            gP = gA + pr - 1;
+            pend_mode = next_mode;
+            FlushGroup::sync();   // lists and counters free for the next pass
+        }
+    }
+    flush_chunk<FlushGroup>(a, ss, pbuf, buf_n, nseq, inner, w.status);
+    if (fr == 0) {
+        a.cta_nbnd[cta] = 0u;
+        a.cta_nseq[cta] = min(nseq, a.seq_max);
+        a.cta_total[cta] = total;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_seam: after k_fill_scan (same grid), the two rows at the seam of each
 // fused-fill CTA whose range starts inside a slice: the previous CTA's last
 // row P and this CTA's first row Q, tested from M_H in HBM (all written by
@@ -1064,22 +1497,48 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_seam(Geom g, Work w, FillCfg c, ScanArgs a)
 {
+    grid_dep_wait();
     extern __shared__ uint4 sm4[];
+    // layout: ScanSmem (256 B) | K peak entries | rows P-1, P, Q, Q+1 (n_b words each)
     ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
     uint4 *pbuf = sm4 + 16;
+    uint32_t *rows = reinterpret_cast<uint32_t *>(pbuf + a.K);
     const uint32_t tid = threadIdx.x, cta = blockIdx.x, nb = g.nb;
-    const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
-    const uint64_t it0 = items * cta / gridDim.x;
+    __shared__ unsigned long long s_rng[2];
+    uint64_t it0, it1;
+    cta_items(g, w, c, cta, gridDim.x, it0, it1, s_rng);
     const uint64_t es = it0 / c.strips;
     const uint32_t iQ = (uint32_t)(it0 % c.strips) * c.W;   // first row of the range
     uint32_t nbnd = 0, total = 0, buf_n = 0;
-    if (iQ > 0) {
+    if (iQ > 0 && it0 < it1) {   // an empty range has no seam of its own
         const uint32_t s = (uint32_t)(es % g.n_slices), ev = (uint32_t)(es / g.n_slices);
         const uint32_t *base = w.M + (size_t)ev * w.n_cells + ((size_t)s * g.na + iQ) * nb;
+        // the four rows around the seam into shared memory: every thread
+        // issues its loads before it stores any, so the block pays about one
+        // memory latency instead of one per loop step
+        const uint32_t r0 = iQ >= 2 ? 0u : 1u, r1 = iQ + 1 < g.na ? 4u : 3u;
+        const uint32_t *src = base - 2 * (ptrdiff_t)nb;
+        constexpr uint32_t U = 8;
+        const uint32_t k0 = r0 * nb, k1 = r1 * nb, step = U * blockDim.x;
+        for (uint32_t kb = k0; kb < k1; kb += step) {
+            uint32_t v[U];
+#pragma unroll
+            for (uint32_t q = 0; q < U; ++q) {
+                const uint32_t k = kb + q * blockDim.x + tid;
+                v[q] = k < k1 ? __ldcg(src + k) : 0u;
+            }
+#pragma unroll
+            for (uint32_t q = 0; q < U; ++q) {
+                const uint32_t k = kb + q * blockDim.x + tid;
+                if (k < k1)
+                    rows[k] = v[q];
+            }
+        }
+        __syncthreads();
         const RowRef none{nullptr, 0u, 0u};
-        const RowRef rP{base - nb, 4u, 0u}, rQ{base, 4u, 0u};
-        const RowRef upP = iQ >= 2 ? RowRef{base - 2 * nb, 4u, 0u} : none;
-        const RowRef dnQ = iQ + 1 < g.na ? RowRef{base + nb, 4u, 0u} : none;
+        const RowRef rP{rows + nb, 1u, 0u}, rQ{rows + 2 * nb, 1u, 0u};
+        const RowRef upP = iQ >= 2 ? RowRef{rows, 1u, 0u} : none;
+        const RowRef dnQ = iQ + 1 < g.na ? RowRef{rows + 3 * nb, 1u, 0u} : none;
         const uint32_t lin_Q = (s * g.na + iQ) * nb;
         const ChunkList seam_list{a.desc_bnd + (size_t)cta * kSeamChunks, kSeamChunks};
         // two rows hold at most n_b peaks: with K >= n_b a few chunks suffice
@@ -1161,6 +1620,7 @@ __device__ void test_candidates(const Geom &g, const Work &w, const ScanArgs &a,
 
 __global__ void __launch_bounds__(256) k_scan_ldg(Geom g, Work w, ScanArgs a)
 {
+    grid_dep_wait();
     extern __shared__ uint4 sm4[];
     ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
     uint4 *pbuf = sm4 + 16;
@@ -1235,11 +1695,15 @@ __global__ void __launch_bounds__(256) k_scan_ldg(Geom g, Work w, ScanArgs a)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, OrderArgs o)
 {
+    grid_dep_wait();
     extern __shared__ uint32_t smo[];
     uint32_t *ev_base = smo;                  // n_events + 1
     uint32_t *red = ev_base + w.n_events + 1; // 40
     __shared__ uint32_t s_last;
     const uint32_t tid = threadIdx.x, bd = blockDim.x, c = blockIdx.x;
+    // this CTA's chunk counts and first descriptor, loaded ahead of the prefix
+    const uint32_t nbnd = a.cta_nbnd[c], nseq = a.cta_nseq[c];
+    const uint2 d0 = nbnd ? a.desc_bnd[(size_t)c * kSeamChunks] : nseq ? a.desc[(size_t)c * a.seq_max] : make_uint2(0u, 0u);
 
     // rank of this CTA's first entry
     uint32_t part = 0;
@@ -1258,10 +1722,10 @@ __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, Order
     block_exclusive_scan(ev_base, w.n_events, red);
 
     // the CTA's seam chunks come before its interior chunks
-    const uint32_t nbnd = a.cta_nbnd[c], nseq = a.cta_nseq[c];
     uint32_t P = prefix;
     for (uint32_t q = 0; q < nbnd + nseq; ++q) {
-        const uint2 d = q < nbnd ? a.desc_bnd[(size_t)c * kSeamChunks + q]
+        const uint2 d = q == 0 ? d0
+                      : q < nbnd ? a.desc_bnd[(size_t)c * kSeamChunks + q]
                                  : a.desc[(size_t)c * a.seq_max + (q - nbnd)];
         for (uint32_t k = tid; k < d.y; k += bd) {
             if (d.x + k >= a.entries_cap)
@@ -1317,10 +1781,74 @@ __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, Order
 // ---------------------------------------------------------------------------
 namespace htk {
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) only when a launch needs
+// more than was already allowed for the kernel on this device: the attribute
+// call is a driver round trip that would otherwise cost every launch.
+static cudaError_t allow_smem(const void *kernel, size_t bytes)
+{
+    constexpr int kSlots = 16, kDevs = 64;
+    static std::atomic<const void *> keys[kSlots];
+    static std::atomic<int> allowed[kSlots][kDevs];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs)
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int slot = -1;
+    for (int i = 0; i < kSlots && slot < 0; ++i) {
+        const void *k = keys[i].load(std::memory_order_acquire);
+        if (k == kernel)
+            slot = i;
+        else if (!k) {
+            const void *expect = nullptr;
+            if (keys[i].compare_exchange_strong(expect, kernel) || expect == kernel)
+                slot = i;
+        }
+    }
+    if (slot < 0)
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    std::atomic<int> &a = allowed[slot][dev];
+    if ((int)bytes <= a.load(std::memory_order_acquire))
+        return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) {
+        int cur = a.load();
+        while ((int)bytes > cur && !a.compare_exchange_weak(cur, (int)bytes)) {
+        }
+    }
+    return e;
+}
+
+// Launch with programmatic stream serialisation allowed (see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), uint32_t grid, uint32_t block, size_t smem,
+                              cudaStream_t st, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 cudaError_t launch_bin(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st)
 {
-    k_bin<<<grid, 256, 0, st>>>(g, w);
-    return cudaGetLastError();
+    const size_t smem = w.hit_off ? ((size_t)w.n_events + 1) * 4 : 0;
+    if (smem > 32 * 1024) {
+        cudaError_t e = allow_smem((const void *)k_bin, smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    return launch_pdl(k_bin, grid, 256, smem, st, g, w);
+}
+
+cudaError_t launch_scatter(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st)
+{
+    return launch_pdl(k_scatter, grid, 256, 0, st, g, w);
 }
 
 size_t fill_scan_smem_bytes(const FillCfg &c, const ScanArgs &a, uint32_t nb)
@@ -1333,28 +1861,51 @@ cudaError_t launch_fill_scan(const Geom &g, const Work &w, const FillCfg &c, con
                              cudaStream_t st)
 {
     const size_t smem = fill_scan_smem_bytes(c, a, g.nb);
-    cudaError_t e = cudaFuncSetAttribute(k_fill_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem((const void *)k_fill_scan, smem);
     if (e != cudaSuccess)
         return e;
-    k_fill_scan<<<grid, c.threads, smem, st>>>(g, w, c, a);
-    return cudaGetLastError();
+    return launch_pdl(k_fill_scan, grid, c.threads, smem, st, g, w, c, a);
+}
+
+size_t fill_ws_smem_bytes(const FillCfg &c, const ScanArgs &a)
+{
+    return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)2 * c.tile_words * 4 + (size_t)c.HC * 16 +
+           (size_t)c.beta_words * 4 + (size_t)3 * kFusedCand * 4 + 4 * sizeof(uint64_t);
+}
+
+cudaError_t launch_fill_ws(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
+                           cudaStream_t st)
+{
+    const size_t smem = fill_ws_smem_bytes(c, a);
+    cudaError_t e = allow_smem((const void *)k_fill_ws, smem);
+    if (e != cudaSuccess)
+        return e;
+    return launch_pdl(k_fill_ws, grid, kWsThreads, smem, st, g, w, c, a);
+}
+
+cudaError_t fill_ws_occupancy(const FillCfg &c, const ScanArgs &a, int *blocks_per_sm)
+{
+    const size_t smem = fill_ws_smem_bytes(c, a);
+    cudaError_t e = allow_smem((const void *)k_fill_ws, smem);
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fill_ws, kWsThreads, smem);
 }
 
 cudaError_t launch_seam(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
                         cudaStream_t st)
 {
-    const size_t smem = 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4);
-    cudaError_t e = cudaFuncSetAttribute(k_seam, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)4 * g.nb * 4;
+    cudaError_t e = allow_smem((const void *)k_seam, smem);
     if (e != cudaSuccess)
         return e;
-    k_seam<<<grid, 256, smem, st>>>(g, w, c, a);
-    return cudaGetLastError();
+    return launch_pdl(k_seam, grid, 256, smem, st, g, w, c, a);
 }
 
 cudaError_t fill_scan_occupancy(const FillCfg &c, const ScanArgs &a, uint32_t nb, int *blocks_per_sm)
 {
     const size_t smem = fill_scan_smem_bytes(c, a, nb);
-    cudaError_t e = cudaFuncSetAttribute(k_fill_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem((const void *)k_fill_scan, smem);
     if (e != cudaSuccess)
         return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fill_scan, c.threads, smem);
@@ -1369,24 +1920,21 @@ cudaError_t launch_fill_priv(const Geom &g, const Work &w, const FillCfg &c, uin
                              cudaStream_t st)
 {
     const size_t smem = fill_smem_bytes(c);
-    cudaError_t e = cudaFuncSetAttribute(k_fill_priv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem((const void *)k_fill_priv, smem);
     if (e != cudaSuccess)
         return e;
-    k_fill_priv<<<grid, c.threads, smem, st>>>(g, w, c);
-    return cudaGetLastError();
+    return launch_pdl(k_fill_priv, grid, c.threads, smem, st, g, w, c);
 }
 
 cudaError_t launch_clear(uint32_t *M, uint64_t words, uint32_t grid, cudaStream_t st)
 {
-    k_clear<<<grid, 512, 0, st>>>(M, words);
-    return cudaGetLastError();
+    return launch_pdl(k_clear, grid, 512, 0, st, M, words);
 }
 
 cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st)
 {
     const uint32_t threads = g.na >= 1024 ? 1024 : ((g.na + 31) / 32) * 32;
-    k_fill_naive<<<grid, threads, 0, st>>>(g, w);
-    return cudaGetLastError();
+    return launch_pdl(k_fill_naive, grid, threads, 0, st, g, w);
 }
 
 size_t scan_smem_bytes(const ScanArgs &a)
@@ -1410,16 +1958,14 @@ static const void *scan_kernel(int kind)
 cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, int kind, cudaStream_t st)
 {
     const size_t smem = scan_smem_bytes(a);
-    cudaError_t e = cudaFuncSetAttribute(scan_kernel(kind), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem((const void *)scan_kernel(kind), smem);
     if (e != cudaSuccess)
         return e;
     if (kind == SCAN_BULK)
-        k_scan_tma<<<a.grid, 256, smem, st>>>(g, w, a);
-    else if (kind == SCAN_LDG)
-        k_scan_ldg<<<a.grid, 256, smem, st>>>(g, w, a);
-    else
-        k_scan_direct<<<a.grid, 256, smem, st>>>(g, w, a);
-    return cudaGetLastError();
+        return launch_pdl(k_scan_tma, a.grid, 256, smem, st, g, w, a);
+    if (kind == SCAN_LDG)
+        return launch_pdl(k_scan_ldg, a.grid, 256, smem, st, g, w, a);
+    return launch_pdl(k_scan_direct, a.grid, 256, smem, st, g, w, a);
 }
 
 cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const OrderArgs &o,
@@ -1427,18 +1973,17 @@ cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const 
 {
     const size_t smem = (w.n_events + 1 + 40) * sizeof(uint32_t);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_smem((const void *)k_order, smem);
         if (e != cudaSuccess)
             return e;
     }
-    k_order<<<a.grid, 256, smem, st>>>(g, w, a, o);
-    return cudaGetLastError();
+    return launch_pdl(k_order, a.grid, 256, smem, st, g, w, a, o);
 }
 
 cudaError_t scan_occupancy(int kind, size_t smem, int *blocks_per_sm)
 {
     const void *k = scan_kernel(kind);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem((const void *)k, smem);
     if (e != cudaSuccess)
         return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, 256, smem);
@@ -1447,7 +1992,7 @@ cudaError_t scan_occupancy(int kind, size_t smem, int *blocks_per_sm)
 cudaError_t fill_occupancy(const FillCfg &c, int *blocks_per_sm)
 {
     const size_t smem = fill_smem_bytes(c);
-    cudaError_t e = cudaFuncSetAttribute(k_fill_priv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem((const void *)k_fill_priv, smem);
     if (e != cudaSuccess)
         return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fill_priv, c.threads, smem);

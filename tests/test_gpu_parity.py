@@ -108,7 +108,8 @@ def test_fill_and_maxima_match_oracle(ht, case, naive):
 
 
 U32_TUNINGS = [None, dict(fill_fused_scan=2), dict(fill_fused_scan=1, fill_rows=2, fill_threads=256),
-               dict(fill_fused_scan=1, fill_rows=4, fill_threads=256)]
+               dict(fill_fused_scan=1, fill_rows=4, fill_threads=256), dict(fill_fused_scan=3, fill_rows=2),
+               dict(fill_fused_scan=3, fill_rows=8)]
 
 
 @pytest.mark.parametrize("tuning", U32_TUNINGS, ids=[str(t) for t in U32_TUNINGS])
@@ -290,7 +291,8 @@ TUNINGS = [
     dict(fill_rows=8, fill_threads=256), dict(fill_rows=64, fill_threads=1024, fill_hits_staged=4096),
     dict(fill_rows=16, fill_blocks_per_sm=1, scan_blocks_per_sm=1, scan_kind=2),
     dict(fill_fused_scan=2, scan_kind=2), dict(fill_fused_scan=2, scan_kind=1),
-    dict(fill_fused_scan=1, fill_rows=4, fill_threads=256),
+    dict(fill_fused_scan=1, fill_rows=4, fill_threads=256), dict(fill_fused_scan=3, fill_rows=16),
+    dict(fill_fused_scan=3, fill_rows=32, fill_hits_staged=1024),
 ]
 
 
@@ -337,7 +339,8 @@ def test_bad_tuning_rejected(ht):
 
 FUSED_TUNINGS = [dict(fill_fused_scan=2), dict(fill_fused_scan=1), dict(fill_fused_scan=1, fill_rows=4,
                  fill_threads=256), dict(fill_fused_scan=1, fill_rows=64, fill_threads=1024),
-                 dict(fill_fused_scan=1, fill_rows=8, fill_blocks_per_sm=1)]
+                 dict(fill_fused_scan=1, fill_rows=8, fill_blocks_per_sm=1), dict(fill_fused_scan=3),
+                 dict(fill_fused_scan=3, fill_rows=4), dict(fill_fused_scan=3, fill_rows=64)]
 
 
 def _track(A, B, theta, branch):
@@ -381,7 +384,8 @@ def test_peaks_on_seams(ht, tuning):
         assert_peaks_equal(pk, pk_ref)
 
 
-@pytest.mark.parametrize("tuning", FUSED_TUNINGS[1:4], ids=[str(t) for t in FUSED_TUNINGS[1:4]])
+@pytest.mark.parametrize("tuning", FUSED_TUNINGS[1:4] + FUSED_TUNINGS[5:7],
+                         ids=[str(t) for t in FUSED_TUNINGS[1:4] + FUSED_TUNINGS[5:7]])
 def test_fused_candidate_overflow(ht, paper_ref, tuning):
     # low thresholds on the paper-scale event: some passes list more cells
     # >= T than the fused fill's candidate lists hold (whole-row fallback,
@@ -398,7 +402,8 @@ def test_fused_candidate_overflow(ht, paper_ref, tuning):
         assert_peaks_equal(pk, pk_ref)
 
 
-@pytest.mark.parametrize("tuning", FUSED_TUNINGS[1:3], ids=[str(t) for t in FUSED_TUNINGS[1:3]])
+@pytest.mark.parametrize("tuning", FUSED_TUNINGS[1:3] + FUSED_TUNINGS[5:6],
+                         ids=[str(t) for t in FUSED_TUNINGS[1:3] + FUSED_TUNINGS[5:6]])
 def test_fused_state_sequences(ht, paper_ref, tuning):
     ev, M_ref, pk_ref, n_ref = paper_ref
     ev2 = synth.paper_event(seed=12)
@@ -442,7 +447,7 @@ def test_autotune_keeps_results(ht, paper_ref):
             ctx.autotune()                        # nothing filled yet
         ctx.fill(ev.x, ev.y, ev.z)
         chosen, us = ctx.autotune(reps=3)
-        assert us > 0 and chosen["fill_fused_scan"] in (1, 2)
+        assert us > 0 and chosen["fill_fused_scan"] in (1, 2, 3)
         assert np.array_equal(ctx.matrix(), M_ref)
         pk, n = ctx.find_maxima(capacity=1 << 16)
         assert n == n_ref
