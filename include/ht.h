@@ -213,13 +213,14 @@ ht_status ht_profile_read(ht_ctx *ctx, ht_kernel_time *out, uint32_t cap, uint32
  *                      (register streaming), HT_SCAN_DIRECT (scalar)
  *   scan_stage_bytes   bulk-copy stage size; scan_slots: ring depth (2..8)
  *   scan_blocks_per_sm cap on resident scan CTAs per SM
- *   fill_fused_scan    1: ht_fill also finds the peaks of each vote tile as
- *                      it writes it (M_H is still written in full), so
- *                      ht_find_maxima only orders them; 3: the same with
- *                      two tiles per SM, one voted into while the other is
- *                      written (warp-specialised, 1024 threads); 2: never;
- *                      0: 3 when it fits, else 1 when it fits (both only
- *                      for non-accumulating, non-naive fills)
+ *   fill_fused_scan    1: ht_fill also lists the cells >= threshold of each
+ *                      vote tile as it writes it (M_H is still written in
+ *                      full) and tests only those, so ht_find_maxima only
+ *                      orders the peaks; 3: the same with two tiles per SM,
+ *                      one voted into while the other is written
+ *                      (warp-specialised, 1024 threads); 2: never (a full
+ *                      scan in ht_find_maxima); 0: 1 when it fits (both
+ *                      fused modes only for non-accumulating, non-naive fills)
  * ht_set_tuning waits for the device, re-derives the shapes and returns
  * HT_E_INVAL for an impossible value; ht_get_tuning reports the shapes in
  * effect (0 fields filled in). */

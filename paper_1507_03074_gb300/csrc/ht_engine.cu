@@ -17,7 +17,7 @@ static const uint32_t kPeakBuf = 1024;         // K: entries buffered per scan /
 static const uint32_t kFusedPeakBuf = 512;     // K of a fused-fill CTA (at least its block)
 
 const char *const kKernelNames[K_NKINDS] = {"k_bin", "k_scatter", "k_fill_priv", "k_fill_scan", "k_fill_ws",
-                                             "k_seam", "k_clear", "k_fill_naive", "k_scan", "k_order"};
+                                             "k_peaks", "k_clear", "k_fill_naive", "k_scan", "k_order"};
 
 // ---------------------------------------------------------------------------
 // Profiling
@@ -100,13 +100,13 @@ static cudaError_t dalloc(T **p, size_t bytes, size_t *acc)
     return cudaMalloc(reinterpret_cast<void **>(p), bytes ? bytes : 16);
 }
 
-// Chunk descriptors a CTA owning `rows` rows may need: no two peaks are
-// neighbours, so a row holds at most ceil(n_b / 2) peaks; every chunk but
-// the last holds at least K - per_round entries.
-static uint32_t chunks_for(uint64_t rows, uint32_t nb, uint32_t K, uint32_t per_round)
+// Chunk descriptors a CTA owning `rows` rows may need when a row yields at
+// most per_row entries (peaks: ceil(n_b / 2), as no two peaks are
+// neighbours; fused-fill candidates: n_b); every chunk but the last holds at
+// least K - per_round entries.
+static uint32_t chunks_for(uint64_t rows, uint32_t per_row, uint32_t K, uint32_t per_round)
 {
-    const uint64_t peaks = rows * ((nb + 1) / 2);
-    return (uint32_t)std::min<uint64_t>(peaks / (K - per_round) + 2, 1u << 20);
+    return (uint32_t)std::min<uint64_t>(rows * per_row / (K - per_round) + 2, 1u << 20);
 }
 
 ht_status engine_configure(Engine &E, std::string *why)
@@ -201,7 +201,7 @@ ht_status engine_configure(Engine &E, std::string *why)
     }
     // --- warp-specialised fused fill: two tiles, one CTA per SM -------------------
     E.ws_ok = false;
-    if (E.fill_priv_ok && (t.fused == 0 || t.fused == 3) && W <= 64 && b.n_b <= 4096 &&
+    if (E.fill_priv_ok && t.fused == 3 && W <= 64 && b.n_b <= 4096 &&
         (!t.fill_threads || t.fill_threads == htk::kWsThreads / 2)) {
         htk::ScanArgs tmp{};
         tmp.K = E.fused_K;
@@ -284,7 +284,7 @@ ht_status engine_configure(Engine &E, std::string *why)
     const uint32_t fused_grid = E.fused_ok ? (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.fused_grid, items_max)) : 0;
     const uint32_t ws_grid = E.ws_ok ? (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.ws_grid, items_max)) : 0;
     const uint32_t grid_cap = std::max(std::max(scan_grid, fused_grid), ws_grid);
-    uint32_t seq = chunks_for((G_max + scan_grid - 1) / scan_grid + 1, g.nb, s.K, 2 * kScanThreads);
+    uint32_t seq = chunks_for((G_max + scan_grid - 1) / scan_grid + 1, (g.nb + 1) / 2, s.K, 2 * kScanThreads);
     // the cost-balanced split gives a CTA at most `spread` times the items of
     // an even split (every strip costs at least its n_b-per-row writing share)
     const double hits_per_unit = (double)std::max<uint32_t>(E.max_hits, 1) * E.max_admit /
@@ -295,14 +295,11 @@ ht_status engine_configure(Engine &E, std::string *why)
     };
     if (E.fused_ok) {
         const uint64_t fused_rows = rows_per_cta(fused_grid);
-        const uint32_t per_round = std::max(f.threads / 2 + 1, htk::fused_round(f.threads, E.fused_K));
-        seq = std::max(seq, chunks_for(fused_rows, g.nb, E.fused_K, per_round));
+        seq = std::max(seq, chunks_for(fused_rows, g.nb, E.fused_K, htk::fused_round(f.threads, E.fused_K)));
     }
     if (E.ws_ok) {
         const uint64_t ws_rows = rows_per_cta(ws_grid);
-        const uint32_t wt = E.ws_fill.threads;
-        const uint32_t per_round = std::max(wt / 2 + 1, htk::fused_round(wt, E.fused_K));
-        seq = std::max(seq, chunks_for(ws_rows, g.nb, E.fused_K, per_round));
+        seq = std::max(seq, chunks_for(ws_rows, g.nb, E.fused_K, htk::fused_round(E.ws_fill.threads, E.fused_K)));
     }
     s.seq_max = seq;
     const size_t desc_b = (size_t)grid_cap * seq * 8, bnd_b = (size_t)grid_cap * htk::kSeamChunks * 8;
@@ -407,13 +404,14 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
         return st;
     }
 
-    // A peak holds >= threshold votes and no two peaks are neighbours, so
-    // peaks <= min(votes / T, ceil(n_a/2) ceil(n_b/2) per slice).
+    // Entries are the fused fill's candidates (cells >= T) or the scan's
+    // peaks; both hold >= T votes each, so there are at most votes / T of
+    // them (and no more than the cells).
     htk::ScanArgs &s = E.scan;
     const uint64_t slack = 2ull * 1024;
     const uint64_t by_votes = (uint64_t)std::max<uint32_t>(max_hits, 1) * E.max_admit * g.na / threshold + 1;
-    const uint64_t by_space = (uint64_t)g.n_slices * ((g.na + 1) / 2) * ((g.nb + 1) / 2) * max_events;
-    s.entries_cap = (uint32_t)std::min<uint64_t>(std::min(by_votes, by_space) + slack, 0xffffffffull);
+    const uint64_t by_cells = E.n_cells * max_events;
+    s.entries_cap = (uint32_t)std::min<uint64_t>(std::min(by_votes, by_cells) + slack, 0xffffffffull);
 
     size_t acc = 0;
     const size_t hits_cap = (size_t)std::max<uint32_t>(max_hits, 1);
@@ -607,9 +605,8 @@ cudaError_t engine_vote(Engine &E, const uint32_t *d_hit_off, uint32_t n_hits0, 
         }
         ++E.launches;
         if (e == cudaSuccess) {
-            ProfScope ps(E, K_SEAM, st);
-            a.K = kPeakBuf;
-            e = htk::launch_seam(E.geom, w, ff, a, grid, st);
+            ProfScope ps(E, K_PEAKS, st);
+            e = htk::launch_peaks(E.geom, w, a, grid, st);
             ++E.launches;
         }
         if (e == cudaSuccess) {

@@ -29,7 +29,7 @@ struct Tuning {
 // Optional per-kernel timing with CUDA events recorded on the launching
 // stream around every launch (enabled by ht_profile).
 enum KernelKind {
-    K_BIN, K_SCATTER, K_FILL_PRIV, K_FILL_SCAN, K_FILL_WS, K_SEAM, K_CLEAR, K_FILL_NAIVE, K_SCAN, K_ORDER, K_NKINDS
+    K_BIN, K_SCATTER, K_FILL_PRIV, K_FILL_SCAN, K_FILL_WS, K_PEAKS, K_CLEAR, K_FILL_NAIVE, K_SCAN, K_ORDER, K_NKINDS
 };
 extern const char *const kKernelNames[K_NKINDS];
 

@@ -70,8 +70,8 @@ size_t fill_ws_smem_bytes(const FillCfg &c, const ScanArgs &a);
 cudaError_t launch_fill_ws(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
                            cudaStream_t st);
 cudaError_t fill_ws_occupancy(const FillCfg &c, const ScanArgs &a, int *blocks_per_sm);
-cudaError_t launch_seam(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
-                        cudaStream_t st);
+// After a fused fill (same grid): test its candidate entries, keep the peaks.
+cudaError_t launch_peaks(const Geom &g, const Work &w, const ScanArgs &a, uint32_t grid, cudaStream_t st);
 cudaError_t launch_clear(uint32_t *M, uint64_t words, uint32_t grid, cudaStream_t st);
 cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
 size_t scan_smem_bytes(const ScanArgs &a);
@@ -93,11 +93,11 @@ constexpr uint32_t kVoteWeight = 6;
 constexpr uint32_t kLdgUPT = 4;
 // Candidate cells (>= threshold) a streaming-scan CTA lists before testing them.
 constexpr uint32_t kCand = 1024;
-// Candidate cells a fused-fill CTA lists per pass (and keeps for the pass's
-// last row); a pass with more falls back to testing whole rows.
+// Candidate cells a fused-fill CTA lists per pass; a pass with more emits
+// its rows' cells >= T read back from M_H.
 constexpr uint32_t kFusedCand = 256;
-// Peaks the fused fill tests per block round: at most this many per round,
-// so every chunk but the last holds at least K - fused_round(threads, K).
+// Entries the fused fill emits per group round: at most this many per
+// round, so every chunk but the last holds at least K - fused_round(threads, K).
 __host__ __device__ constexpr uint32_t fused_round(uint32_t threads, uint32_t K) { return threads < K / 2 ? threads : K / 2; }
 enum ScanKind { SCAN_DIRECT = 0, SCAN_BULK = 1, SCAN_LDG = 2 };
 cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, int kind, cudaStream_t st);

@@ -282,7 +282,8 @@ __device__ __forceinline__ void vote_rows(const Geom &g, uint32_t *tile, const f
 // r / 32), cand[] lists them as r * n_b + j (up to cap; *n counts them all).
 struct FlushList {
     uint32_t *hot;
-    uint32_t *cand;
+    uint32_t *cand;     // r * n_b + j
+    uint32_t *candv;    // the cell's votes
     uint32_t *n;
     uint32_t cap;
 };
@@ -302,8 +303,10 @@ __device__ __forceinline__ void list_cells(const Geom &g, const FlushList &L, ui
     for (uint32_t m = 0; m < n; ++m)
         if (v[m] >= g.threshold) {
             const uint32_t p = atomicAdd(L.n, 1u);
-            if (p < L.cap)
+            if (p < L.cap) {
                 L.cand[p] = r * g.nb + j0 + m;
+                L.candv[p] = v[m];
+            }
         }
 }
 
@@ -668,7 +671,7 @@ __device__ __forceinline__ void flush_chunk(const ScanArgs &a, ScanSmem &ss, con
 // Ordered compaction of one round: each thread holds cnt peaks in pj/pv
 // (columns of the row starting at row_lin0); appends them to pbuf in
 // thread order and counts them for their event.
-template <class G = BlockGroup>
+template <class G = BlockGroup, bool COUNT = true>
 __device__ __forceinline__ void compact_round(ScanSmem &ss, uint4 *pbuf, uint32_t &buf_n, uint32_t cnt,
                                               const uint32_t *pj, const uint32_t *pv, uint32_t row_lin0,
                                               uint32_t event, uint32_t *ev_count)
@@ -685,7 +688,8 @@ __device__ __forceinline__ void compact_round(ScanSmem &ss, uint4 *pbuf, uint32_
         ss.wsum[lane] = vi - v;
         if (lane == 31u) {
             ss.round_total = vi;
-            atomicAdd(&ev_count[event], vi);
+            if (COUNT)
+                atomicAdd(&ev_count[event], vi);
         }
     }
     G::sync();
@@ -698,7 +702,7 @@ __device__ __forceinline__ void compact_round(ScanSmem &ss, uint4 *pbuf, uint32_
 
 // Ordered compaction of one entry per thread (has = 0 or 1): appends the
 // entries to pbuf in thread order and counts them for their events.
-template <class G = BlockGroup>
+template <class G = BlockGroup, bool COUNT = true>
 __device__ __forceinline__ void compact_entry(ScanSmem &ss, uint4 *pbuf, uint32_t &buf_n, uint32_t has,
                                               const uint4 &ent, uint32_t *ev_count)
 {
@@ -718,7 +722,8 @@ __device__ __forceinline__ void compact_entry(ScanSmem &ss, uint4 *pbuf, uint32_
     G::sync();
     if (has) {
         pbuf[buf_n + ss.wsum[warp] + incl - 1] = ent;
-        atomicAdd(&ev_count[ent.y], 1u);
+        if (COUNT)
+            atomicAdd(&ev_count[ent.y], 1u);
     }
     buf_n += ss.round_total;
     G::sync();
@@ -888,233 +893,154 @@ __global__ void __launch_bounds__(256) k_scan_direct(Geom g, Work w, ScanArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// k_fill_scan: Step 1 and Step 2 in one pass over shared-memory tiles.
+// The fused fill: Step 1 plus the first half of Step 2.
 //
 // Like k_fill_priv, a CTA owns a contiguous range of (event, slice, strip)
 // items, votes each strip pass into a shared-memory tile and writes it to
 // M_H, clearing the tile as it goes.  While writing, it lists the cells of
-// the pass that hold >= T votes; only those are tested against their
-// neighbours, which are read back from M_H -- rows this CTA has just
-// written, still in L2:
-//   - a row whose lower neighbour is written (every row of the pass but the
-//     last, and the last when it ends the slice) is tested at once; the last
-//     row's cells wait for the next pass of the same slice;
-//   - the first row of the CTA's range, when it is not a slice's first row,
-//     and the previous CTA's last row form the seam between two CTAs; k_seam
-//     tests both once the whole of M_H is written.
-// A pass that lists more than kFusedCand cells tests its rows whole.  Peaks
-// go, in linear order, into per-CTA interior chunks; k_seam adds the seam
-// chunks, which k_order places before the CTA's interior chunks.
+// the pass that hold >= T votes and appends them, in linear order, to its
+// chunks of candidate entries -- the cells a full scan would have to look
+// at.  k_peaks then tests only those candidates against their neighbours,
+// once the whole of M_H is written (no row waits for another CTA), and
+// compacts each chunk in place to the peaks; k_order places the chunks.
+// A pass listing more than kFusedCand cells emits its rows' cells >= T from
+// M_H instead (read back through L2).
 // ---------------------------------------------------------------------------
 
-// A row of cells in one of the places the fused kernel keeps them.
-struct RowRef {
-    const uint32_t *p;   // row start (u32 array) or tile row base (words)
-    uint32_t kind;       // 0 absent, 1 u32 shared, 2 u16 tile, 3 u32 tile, 4 u32 global (via L2)
-    uint32_t sw;         // tile swizzle of the row
-    __device__ __forceinline__ uint32_t get(uint32_t j) const
-    {
-        switch (kind) {
-        case 1:
-            return p[j];
-        case 2: {
-            const uint32_t wv = p[(j >> 1) ^ sw];
-            return (wv >> ((j & 1u) << 4)) & 0xffffu;
-        }
-        case 3:
-            return p[j ^ sw];
-        default:
-            return __ldcg(p + j);
-        }
-    }
-};
-
-__device__ __forceinline__ bool is_peak_ref(const RowRef &row, const RowRef &up, const RowRef &dn, uint32_t j,
-                                            uint32_t nb, uint32_t v)
-{
-    const bool hl = j > 0, hr = j + 1 < nb;
-    if (up.kind) {
-        if (hl && !(v > up.get(j - 1))) return false;
-        if (!(v > up.get(j))) return false;
-        if (hr && !(v > up.get(j + 1))) return false;
-    }
-    if (hl && !(v > row.get(j - 1))) return false;
-    if (hr && !(v >= row.get(j + 1))) return false;
-    if (dn.kind) {
-        if (hl && !(v >= dn.get(j - 1))) return false;
-        if (!(v >= dn.get(j))) return false;
-        if (hr && !(v >= dn.get(j + 1))) return false;
-    }
-    return true;
-}
-
-// Test one row (cells >= T against their neighbours) and append its peaks
-// in column order.  All threads of the block call it.
-__device__ void test_row_ref(const Geom &g, const ScanArgs &a, ScanSmem &ss, uint4 *pbuf, uint32_t &buf_n,
-                             uint32_t &nseq, uint32_t &total, const ChunkList &L, uint32_t *status,
-                             const RowRef &up, const RowRef &row, const RowRef &dn, uint32_t row_lin0, uint32_t ev)
-{
-    const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb, T = g.threshold;
-    const uint32_t rounds = (nb + bd - 1) / bd;
-    const uint32_t per_round = bd / 2 + 1;    // no two peaks are neighbours
-    for (uint32_t rd = 0; rd < rounds; ++rd) {
-        const uint32_t j = rd * bd + tid;
-        uint32_t cnt = 0, pj[1], pv[1];
-        if (j < nb) {
-            const uint32_t v = row.get(j);
-            if (v >= T && is_peak_ref(row, up, dn, j, nb, v)) {
-                pj[0] = j;
-                pv[0] = v;
-                cnt = 1;
-            }
-        }
-        if (__syncthreads_or(cnt)) {
-            if (buf_n + per_round > a.K)
-                flush_chunk(a, ss, pbuf, buf_n, nseq, L, status);
-            compact_round(ss, pbuf, buf_n, cnt, pj, pv, row_lin0, ev, a.ev_count);
-            total += ss.round_total;
-        }
-    }
-}
-
-// Peak test with the neighbours read through L2 (rows of this CTA, written
-// before the last block barrier); up / dn are null outside the slice.
+// Peak test with the neighbours read through L2; up / dn are null outside
+// the slice.  All eight loads are issued before any comparison, so a test
+// costs one memory latency.
 __device__ __forceinline__ bool is_peak_l2(const uint32_t *row, const uint32_t *up, const uint32_t *dn, uint32_t j,
                                            uint32_t nb, uint32_t v)
 {
     const bool hl = j > 0, hr = j + 1 < nb;
-    if (up) {
-        if (hl && !(v > __ldcg(up + j - 1))) return false;
-        if (!(v > __ldcg(up + j))) return false;
-        if (hr && !(v > __ldcg(up + j + 1))) return false;
-    }
-    if (hl && !(v > __ldcg(row + j - 1))) return false;
-    if (hr && !(v >= __ldcg(row + j + 1))) return false;
-    if (dn) {
-        if (hl && !(v >= __ldcg(dn + j - 1))) return false;
-        if (!(v >= __ldcg(dn + j))) return false;
-        if (hr && !(v >= __ldcg(dn + j + 1))) return false;
-    }
-    return true;
+    const uint32_t ul = up && hl ? __ldcg(up + j - 1) : 0u, uc = up ? __ldcg(up + j) : 0u,
+                   ur = up && hr ? __ldcg(up + j + 1) : 0u;
+    const uint32_t rl = hl ? __ldcg(row + j - 1) : 0u, rr = hr ? __ldcg(row + j + 1) : 0u;
+    const uint32_t dl = dn && hl ? __ldcg(dn + j - 1) : 0u, dc = dn ? __ldcg(dn + j) : 0u,
+                   dr = dn && hr ? __ldcg(dn + j + 1) : 0u;
+    // absent neighbours read as 0: v > 0 and v >= 0 hold for every v >= 1
+    return v > ul && v > uc && v > ur && v > rl && v >= rr && v >= dl && v >= dc && v >= dr;
 }
 
-// Sort the n <= kFusedCand candidate keys of a pass into srt (keys are
-// distinct: the rank of a key is the number of smaller ones), then find
-// lo / hi, the first positions holding a key >= t_lo / >= t_hi (n if none).
-template <class G = BlockGroup>
-__device__ __forceinline__ void rank_sort_bounds(const uint32_t *cand, uint32_t *srt, uint32_t n, uint32_t t_lo,
-                                                 uint32_t t_hi, uint32_t *s_bounds)
+// Append the candidate cells of one pass (rows iA .. iA + pr - 1 of slice
+// unit `slice_lin0`) to the CTA's candidate chunks, in linear order.  n_c
+// cells were listed as r * n_b + j in cand / candv (up to kFusedCand); with
+// more, the rows marked in hotm are read back from M_H.  Entries are
+// {lin within event, event, votes, 0}.  All threads of the group call it.
+template <class G>
+__device__ __forceinline__ void emit_pass(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss, uint4 *pbuf,
+                                          uint32_t &buf_n, uint32_t &nseq, uint32_t &total, const ChunkList &inner,
+                                          const uint32_t *cand, const uint32_t *candv, uint32_t *srt, uint32_t *srtv,
+                                          uint32_t n_c, uint64_t hotm, uint32_t pr, uint32_t iA, uint32_t slice_lin0,
+                                          uint32_t e, const uint32_t *Ms)
 {
-    const uint32_t tid = G::rank(), bd = G::size();
-    if (tid == 0)
-        s_bounds[0] = s_bounds[1] = n;
-    for (uint32_t k = tid; k < n; k += bd) {
-        const uint32_t key = cand[k];
-        uint32_t rank = 0;
-        for (uint32_t m = 0; m < n; ++m)
-            rank += cand[m] < key;
-        srt[rank] = key;
-    }
-    G::sync();
-    for (uint32_t k = tid; k < n; k += bd) {
-        const uint32_t key = srt[k], prev = k ? srt[k - 1] : 0u;
-        if (key >= t_lo && (k == 0 || prev < t_lo))
-            s_bounds[0] = k;
-        if (key >= t_hi && (k == 0 || prev < t_hi))
-            s_bounds[1] = k;
-    }
-    G::sync();
-}
-
-// Peak tests of one fused-fill pass from candidate lists, one cell per
-// thread: first the np pending cells (columns of row iA - 1, the previous
-// pass's last row), then the sorted keys srt[lo, hi) (r * n_b + j for row
-// iA + r).  Ms is the slice's M_H; peaks are appended in linear order.
-template <class G = BlockGroup>
-__device__ __forceinline__ void fused_test_cands(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss,
-                                                 uint4 *pbuf, uint32_t &buf_n, uint32_t &nseq, uint32_t &total,
-                                                 const ChunkList &inner, const uint32_t *Ms, const uint32_t *pl,
-                                                 uint32_t np, const uint32_t *srt, uint32_t lo, uint32_t hi,
-                                                 uint32_t iA, uint32_t slice_lin0, uint32_t e)
-{
-    const uint32_t tid = G::rank(), nb = g.nb;
-    const uint32_t m = np + (hi > lo ? hi - lo : 0u);
-    const uint32_t rc = fused_round(G::size(), a.K);
-    for (uint32_t base = 0; base < m; base += rc) {
-        const uint32_t k = base + tid;
-        uint32_t has = 0;
-        uint4 ent = make_uint4(0u, 0u, 0u, 0u);
-        if (tid < rc && k < m) {
-            uint32_t i, j;
-            if (k < np) {
-                i = iA - 1;
-                j = pl[k];
-            } else {
-                const uint32_t key = srt[lo + k - np];
-                const uint32_t r = key / nb;
-                i = iA + r;
-                j = key - r * nb;
-            }
-            const uint32_t *row = Ms + (size_t)i * nb;
-            const uint32_t v = __ldcg(row + j);
-            if (is_peak_l2(row, i > 0 ? row - nb : nullptr, i + 1 < g.na ? row + nb : nullptr, j, nb, v)) {
-                has = 1;
-                ent = make_uint4(slice_lin0 + i * nb + j, e, v, 0u);
-            }
+    const uint32_t tid = G::rank(), bd = G::size(), nb = g.nb;
+    const uint32_t lin0 = slice_lin0 + iA * nb;
+    if (n_c <= kFusedCand) {
+        // distinct keys: the rank of a key is the number of smaller ones
+        for (uint32_t k = tid; k < n_c; k += bd) {
+            const uint32_t key = cand[k];
+            uint32_t rank = 0;
+            for (uint32_t m = 0; m < n_c; ++m)
+                rank += cand[m] < key;
+            srt[rank] = key;
+            srtv[rank] = candv[k];
         }
-        if (G::sync_or(has)) {
+        G::sync();
+        const uint32_t rc = fused_round(bd, a.K);
+        for (uint32_t base = 0; base < n_c; base += rc) {
+            const uint32_t k = base + tid;
+            const uint32_t has = (tid < rc && k < n_c) ? 1u : 0u;
+            const uint4 ent = has ? make_uint4(lin0 + srt[k], e, srtv[k], 0u) : make_uint4(0u, 0u, 0u, 0u);
             if (buf_n + rc > a.K)
                 flush_chunk<G>(a, ss, pbuf, buf_n, nseq, inner, w.status);
-            compact_entry<G>(ss, pbuf, buf_n, has, ent, a.ev_count);
+            compact_entry<G, false>(ss, pbuf, buf_n, has, ent, nullptr);
             total += ss.round_total;
+        }
+        return;
+    }
+    // rounds of rc threads, like the candidate rounds: a chunk is flushed
+    // only when fewer than rc entries are free
+    const uint32_t T = g.threshold, per_round = fused_round(bd, a.K);
+    for (uint32_t r = 0; r < pr; ++r) {
+        if (!((hotm >> r) & 1ull))
+            continue;
+        const uint32_t *row = Ms + (size_t)(iA + r) * nb;
+        for (uint32_t j0 = 0; j0 < nb; j0 += per_round) {
+            const uint32_t j = j0 + tid;
+            uint32_t cnt = 0, pj[1], pv[1];
+            if (tid < per_round && j < nb) {
+                const uint32_t v = __ldcg(row + j);
+                if (v >= T) {
+                    pj[0] = j;
+                    pv[0] = v;
+                    cnt = 1;
+                }
+            }
+            if (G::sync_or(cnt)) {
+                if (buf_n + per_round > a.K)
+                    flush_chunk<G>(a, ss, pbuf, buf_n, nseq, inner, w.status);
+                compact_round<G, false>(ss, pbuf, buf_n, cnt, pj, pv, lin0 + r * nb, e, nullptr);
+                total += ss.round_total;
+            }
         }
     }
 }
 
-// Whole-row test of slice row i from M_H through L2.
-template <class G = BlockGroup>
-__device__ __forceinline__ void test_row_l2(const Geom &g, const ScanArgs &a, ScanSmem &ss, uint4 *pbuf,
-                                            uint32_t &buf_n, uint32_t &nseq, uint32_t &total, const ChunkList &L,
-                                            uint32_t *status, const uint32_t *Ms, uint32_t i, uint32_t slice_lin0,
-                                            uint32_t e)
+// Write one pass from the tile to M_H, clear the tile, and emit its
+// candidates (emit_pass).  empty_bar: arrived on once the tile is clear
+// (the warp-specialised fill), or null.  All threads of the group call it.
+template <class G, bool U16>
+__device__ __forceinline__ void flush_emit_pass(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss,
+                                                uint4 *pbuf, uint32_t &buf_n, uint32_t &nseq, uint32_t &total,
+                                                const ChunkList &inner, uint32_t *tile, uint32_t pitch, uint32_t *dst,
+                                                uint32_t pr, uint32_t iA, uint32_t slice_lin0, uint32_t e,
+                                                const uint32_t *Ms, uint32_t *lists, uint32_t *s_hot, uint32_t *s_nc,
+                                                uint64_t *empty_bar)
 {
-    const uint32_t tid = G::rank(), bd = G::size(), nb = g.nb, T = g.threshold;
-    const uint32_t *row = Ms + (size_t)i * nb;
-    const uint32_t *up = i > 0 ? row - nb : nullptr, *dn = i + 1 < g.na ? row + nb : nullptr;
-    const uint32_t per_round = bd / 2 + 1;    // no two peaks are neighbours
-    for (uint32_t j0 = 0; j0 < nb; j0 += bd) {
-        const uint32_t j = j0 + tid;
-        uint32_t cnt = 0, pj[1], pv[1];
-        if (j < nb) {
-            const uint32_t v = __ldcg(row + j);
-            if (v >= T && is_peak_l2(row, up, dn, j, nb, v)) {
-                pj[0] = j;
-                pv[0] = v;
-                cnt = 1;
-            }
-        }
-        if (G::sync_or(cnt)) {
-            if (buf_n + per_round > a.K)
-                flush_chunk<G>(a, ss, pbuf, buf_n, nseq, L, status);
-            compact_round<G>(ss, pbuf, buf_n, cnt, pj, pv, slice_lin0 + i * nb, e, a.ev_count);
-            total += ss.round_total;
-        }
+    uint32_t *cand = lists, *candv = lists + kFusedCand, *srt = lists + 2 * kFusedCand, *srtv = lists + 3 * kFusedCand;
+    if (G::rank() == 0)
+        s_hot[0] = s_hot[1] = *s_nc = 0u;
+    G::sync();
+    flush_tile<U16, true, false, G>(g, tile, dst, pr, pitch, FlushList{s_hot, cand, candv, s_nc, kFusedCand});
+    if (empty_bar)
+        mbar_arrive(empty_bar);   // the tile is clear
+    G::sync();                    // M_H rows of the pass and the lists visible to the group
+    const uint64_t hotm = (uint64_t)s_hot[0] | ((uint64_t)s_hot[1] << 32);
+    const uint32_t n_c = *s_nc;
+    if (n_c)
+        emit_pass<G>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, cand, candv, srt, srtv, n_c, hotm, pr, iA,
+                     slice_lin0, e, Ms);
+    G::sync();                    // lists and counters free for the next pass
+}
+
+// The CTA's candidate bookkeeping once its range is done.
+template <class G>
+__device__ __forceinline__ void finish_candidates(const Work &w, const ScanArgs &a, ScanSmem &ss, const uint4 *pbuf,
+                                                  uint32_t &buf_n, uint32_t &nseq, uint32_t total,
+                                                  const ChunkList &inner, uint32_t cta)
+{
+    flush_chunk<G>(a, ss, pbuf, buf_n, nseq, inner, w.status);
+    if (G::rank() == 0) {
+        a.cta_nbnd[cta] = 0u;
+        a.cta_nseq[cta] = min(nseq, a.seq_max);
+        a.cta_total[cta] = total;
     }
 }
 
 __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, ScanArgs a)
 {
     extern __shared__ uint4 sm4[];
-    // layout: ScanSmem (256 B) | K peak entries | tile | HC staged hits | B thresholds |
-    //         3 candidate lists (pass cells, sorted, pending row)
+    // layout: ScanSmem (256 B) | K entries | tile | HC staged hits | B thresholds |
+    //         candidate lists (keys, votes, sorted keys, sorted votes)
     ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
     uint4 *pbuf = sm4 + 16;
     uint32_t *tile = reinterpret_cast<uint32_t *>(pbuf + a.K);
     float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
-    float *beta = reinterpret_cast<float *>(hs + c.HC);            // nb + 1 thresholds
-    uint32_t *cand = reinterpret_cast<uint32_t *>(beta + c.beta_words);
-    uint32_t *srt = cand + kFusedCand, *pl = srt + kFusedCand;
-    __shared__ uint32_t s_hot[2], s_nc, s_bounds[2];
+    float *beta = reinterpret_cast<float *>(hs + c.HC);
+    uint32_t *lists = reinterpret_cast<uint32_t *>(beta + c.beta_words);
+    __shared__ uint32_t s_hot[2], s_nc;
 
     const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb;
     for (uint32_t k = tid; k < c.tile_words / 4; k += bd)
@@ -1131,13 +1057,6 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
     uint64_t cached_es = ~0ull;
     uint32_t cached_n = 0;
     uint32_t buf_n = 0, nseq = 0, total = 0;
-
-    // gP: the last row (global row index) this CTA wrote.  It is pending
-    // when it still needs its test: pend_mode 1 with its np_pend cells >= T
-    // listed in pl, 2 with a cell >= T but no list (too many).
-    bool have_prev = false;
-    uint64_t gP = 0;
-    uint32_t pend_mode = 0, np_pend = 0;
 
     ItemCursor cur(g, c, it0);
     for (uint64_t item = it0; item < it1; ++item, cur.next(g, c)) {
@@ -1159,8 +1078,6 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
         for (uint32_t p0 = 0; p0 < rows; p0 += rpass) {
             const uint32_t pr = min(rpass, rows - p0);
             const uint32_t iA = i0 + p0;
-            const uint64_t gA = es * g.na + iA;
-            const bool prev_adj = have_prev && gP + 1 == gA;   // row iA - 1 is this CTA's
             // ---- vote -------------------------------------------------------
             const uint32_t i = iA + r;
             if (cached_es == es) {
@@ -1190,75 +1107,18 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
                     }
                 }
             }
-            if (tid == 0)
-                s_hot[0] = s_hot[1] = s_nc = 0u;
-            __syncthreads();
-            // ---- write the pass to M_H and clear the tile; list cells >= T ---
-            const FlushList fl{s_hot, cand, &s_nc, kFusedCand};
+            // ---- write the pass, clear the tile, emit its candidates --------
             if (u16)
-                flush_tile<true, true, false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, fl);
+                flush_emit_pass<BlockGroup, true>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, pitch,
+                                                  Mrow + (size_t)p0 * nb, pr, iA, slice_lin0, e, Ms, lists, s_hot,
+                                                  &s_nc, nullptr);
             else
-                flush_tile<false, true, false>(g, tile, Mrow + (size_t)p0 * g.nb, pr, pitch, fl);
-            __syncthreads();   // M_H rows of the pass and the lists visible to the block
-            const uint64_t hotm = (uint64_t)s_hot[0] | ((uint64_t)s_hot[1] << 32);
-            const uint32_t n_c = s_nc;
-            // ---- rows to test now, in order ----------------------------------
-            const bool test_pend = pend_mode != 0 && prev_adj;
-            const uint32_t r_first = (iA == 0 || prev_adj) ? 0u : 1u;   // else row 0 is the seam
-            const bool last_is_end = iA + pr - 1 == g.na - 1;
-            const int32_t r_last = last_is_end ? (int32_t)pr - 1 : (int32_t)pr - 2;
-            const uint64_t want = r_last < (int32_t)r_first ? 0ull
-                                : ((~0ull >> (63 - r_last)) >> r_first) << r_first;
-            // the last row waits for the next pass unless it ends the slice or is the seam row
-            const bool pend_next = !last_is_end && pr - 1 >= r_first;
-            const bool fits = n_c <= kFusedCand;
-            uint32_t lo = 0, hi = 0;
-            if (fits && n_c) {
-                rank_sort_bounds(cand, srt, n_c, r_first * nb, (uint32_t)(r_last + 1) * nb, s_bounds);
-                lo = s_bounds[0];
-                hi = s_bounds[1];
-            }
-            if (fits && pend_mode != 2) {
-                // candidate lists: the pending row's cells, then rows r_first .. r_last
-                const uint32_t np = test_pend ? np_pend : 0u;
-                if (np || hi > lo)
-                    fused_test_cands(g, w, a, ss, pbuf, buf_n, nseq, total, inner, Ms, pl, np, srt, lo, hi, iA,
-                                     slice_lin0, e);
-            } else if (test_pend || (hotm & want)) {
-                // too many candidates: test whole rows (a pending row holds a cell >= T)
-                if (test_pend)
-                    test_row_l2(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, Ms, iA - 1, slice_lin0, e);
-                for (int32_t rr = (int32_t)r_first; rr <= r_last; ++rr)
-                    if ((hotm >> rr) & 1ull)
-                        test_row_l2(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, Ms, iA + (uint32_t)rr,
-                                    slice_lin0, e);
-            }
-            uint32_t next_mode = 0;
-            if (pend_next) {
-                if (fits) {
-                    if (n_c > hi) {
-                        __syncthreads();   // the pending list of this pass was read
-                        for (uint32_t q = hi + tid; q < n_c; q += bd)
-                            pl[q - hi] = srt[q] - (pr - 1) * nb;
-                        np_pend = n_c - hi;
-                        next_mode = 1;
-                    }
-                } else if ((hotm >> (pr - 1)) & 1ull) {
-                    next_mode = 2;
-                }
-            }
-            have_prev = true;
-            gP = gA + pr - 1;
-            pend_mode = next_mode;
-            __syncthreads();   // lists and counters free for the next pass
+                flush_emit_pass<BlockGroup, false>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, pitch,
+                                                   Mrow + (size_t)p0 * nb, pr, iA, slice_lin0, e, Ms, lists, s_hot,
+                                                   &s_nc, nullptr);
         }
     }
-    flush_chunk(a, ss, pbuf, buf_n, nseq, inner, w.status);
-    if (tid == 0) {
-        a.cta_nbnd[cta] = 0u;
-        a.cta_nseq[cta] = min(nseq, a.seq_max);
-        a.cta_total[cta] = total;
-    }
+    finish_candidates<BlockGroup>(w, a, ss, pbuf, buf_n, nseq, total, inner, cta);
 }
 
 // ---------------------------------------------------------------------------
@@ -1266,14 +1126,14 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
 //
 // 1024 threads in two groups of 16 warps: the vote group stages hits and
 // votes strip passes into one of two shared-memory tiles while the flush
-// group writes the other tile to M_H, clears it and tests the pass's
-// candidate cells (exactly as k_fill_scan does).  Tiles change hands through
-// mbarriers -- FULL[b] (512 vote arrivals: tile b holds a pass) and EMPTY[b]
-// (512 flush arrivals: tile b is clear again) -- with bounded waits, so the
-// votes of pass p + 1 run while pass p streams to HBM.  Each group keeps to
-// its own named barrier; a wait that gives up makes its whole group leave
-// (decided by a group-wide vote) after flagging ST_WAIT_TIMEOUT, and the
-// other group's waits then give up too.
+// group writes the other tile to M_H, clears it and emits its candidates
+// (exactly as k_fill_scan does).  Tiles change hands through mbarriers --
+// FULL[b] (512 vote arrivals: tile b holds a pass) and EMPTY[b] (512 flush
+// arrivals: tile b is clear again) -- with bounded waits, so the votes of
+// pass p + 1 run while pass p streams to HBM.  Each group keeps to its own
+// named barrier; a wait that gives up makes its whole group leave (decided
+// by a group-wide vote) after flagging ST_WAIT_TIMEOUT, and the other
+// group's waits then give up too.
 // ---------------------------------------------------------------------------
 using VoteGroup = WarpGroup<1, 0, 512>;
 using FlushGroup = WarpGroup<2, 512, 512>;
@@ -1305,17 +1165,16 @@ __device__ __forceinline__ ItemInfo item_info(const Geom &g, const Work &w, cons
 __global__ void __launch_bounds__(1024, 1) k_fill_ws(Geom g, Work w, FillCfg c, ScanArgs a)
 {
     extern __shared__ uint4 sm4[];
-    // layout: ScanSmem (256 B) | K peak entries | 2 tiles | HC staged hits | B thresholds |
-    //         3 candidate lists | 4 mbarriers (FULL 0, FULL 1, EMPTY 0, EMPTY 1)
+    // layout: ScanSmem (256 B) | K entries | 2 tiles | HC staged hits | B thresholds |
+    //         candidate lists | 4 mbarriers (FULL 0, FULL 1, EMPTY 0, EMPTY 1)
     ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
     uint4 *pbuf = sm4 + 16;
     uint32_t *tiles = reinterpret_cast<uint32_t *>(pbuf + a.K);
     float4 *hs = reinterpret_cast<float4 *>(tiles + 2 * (size_t)c.tile_words);
     float *beta = reinterpret_cast<float *>(hs + c.HC);
-    uint32_t *cand = reinterpret_cast<uint32_t *>(beta + c.beta_words);
-    uint32_t *srt = cand + kFusedCand, *pl = srt + kFusedCand;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(pl + kFusedCand);
-    __shared__ uint32_t s_hot[2], s_nc, s_bounds[2];
+    uint32_t *lists = reinterpret_cast<uint32_t *>(beta + c.beta_words);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(lists + 4 * kFusedCand);
+    __shared__ uint32_t s_hot[2], s_nc;
 
     const uint32_t tid = threadIdx.x, nb = g.nb;
     for (uint32_t k = tid; k < c.tile_words / 2; k += blockDim.x)
@@ -1389,15 +1248,13 @@ __global__ void __launch_bounds__(1024, 1) k_fill_ws(Geom g, Work w, FillCfg c, 
         return;
     }
 
-    // ---------------- flush + test group ----------------
+    // ---------------- flush + emit group ----------------
     const uint32_t fr = FlushGroup::rank();
     uint64_t it0, it1;
     cta_items<FlushGroup>(g, w, c, cta, gridDim.x, it0, it1, s_rng[1]);
     const ChunkList inner = interior_list(a, cta);
     uint32_t buf_n = 0, nseq = 0, total = 0, p = 0;
-    bool have_prev = false, alive = true;
-    uint64_t gP = 0;
-    uint32_t pend_mode = 0, np_pend = 0;
+    bool alive = true;
     ItemCursor cur(g, c, it0);
     for (uint64_t item = it0; item < it1 && alive; ++item, cur.next(g, c)) {
         const ItemInfo t = item_info(g, w, c, cur);
@@ -1406,9 +1263,6 @@ __global__ void __launch_bounds__(1024, 1) k_fill_ws(Geom g, Work w, FillCfg c, 
         uint32_t *Mrow = w.M + (size_t)t.e * w.n_cells + ((size_t)t.s * g.na + t.i0) * nb;
         for (uint32_t p0 = 0; p0 < t.rows; p0 += t.rpass, ++p) {
             const uint32_t pr = min(t.rpass, t.rows - p0);
-            const uint32_t iA = t.i0 + p0;
-            const uint64_t gA = t.es * g.na + iA;
-            const bool prev_adj = have_prev && gP + 1 == gA;
             const uint32_t b = p & 1u;
             uint32_t *tile = tiles + (size_t)b * c.tile_words;
             const bool ok = mbar_wait_bounded(&bars[b], (p >> 1) & 1u);
@@ -1418,138 +1272,75 @@ __global__ void __launch_bounds__(1024, 1) k_fill_ws(Geom g, Work w, FillCfg c, 
                 alive = false;
                 break;
             }
-            if (fr == 0)
-                s_hot[0] = s_hot[1] = s_nc = 0u;
-            FlushGroup::sync();
-            // ---- write the pass to M_H and clear the tile; list cells >= T ---
-            const FlushList fl{s_hot, cand, &s_nc, kFusedCand};
             if (t.u16)
-                flush_tile<true, true, false, FlushGroup>(g, tile, Mrow + (size_t)p0 * nb, pr, t.pitch, fl);
+                flush_emit_pass<FlushGroup, true>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, t.pitch,
+                                                  Mrow + (size_t)p0 * nb, pr, t.i0 + p0, slice_lin0, t.e, Ms, lists,
+                                                  s_hot, &s_nc, &bars[2 + b]);
             else
-                flush_tile<false, true, false, FlushGroup>(g, tile, Mrow + (size_t)p0 * nb, pr, t.pitch, fl);
-            mbar_arrive(&bars[2 + b]);   // tile b is clear
-            FlushGroup::sync();          // M_H rows of the pass and the lists visible to the group
-            const uint64_t hotm = (uint64_t)s_hot[0] | ((uint64_t)s_hot[1] << 32);
-            const uint32_t n_c = s_nc;
-            // ---- rows to test now, in order (as in k_fill_scan) --------------
-            const bool test_pend = pend_mode != 0 && prev_adj;
-            const uint32_t r_first = (iA == 0 || prev_adj) ? 0u : 1u;
-            const bool last_is_end = iA + pr - 1 == g.na - 1;
-            const int32_t r_last = last_is_end ? (int32_t)pr - 1 : (int32_t)pr - 2;
-            const uint64_t want = r_last < (int32_t)r_first ? 0ull
-                                : ((~0ull >> (63 - r_last)) >> r_first) << r_first;
-            const bool pend_next = !last_is_end && pr - 1 >= r_first;
-            const bool fits = n_c <= kFusedCand;
-            uint32_t lo = 0, hi = 0;
-            if (fits && n_c) {
-                rank_sort_bounds<FlushGroup>(cand, srt, n_c, r_first * nb, (uint32_t)(r_last + 1) * nb, s_bounds);
-                lo = s_bounds[0];
-                hi = s_bounds[1];
-            }
-            if (fits && pend_mode != 2) {
-                const uint32_t np = test_pend ? np_pend : 0u;
-                if (np || hi > lo)
-                    fused_test_cands<FlushGroup>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, Ms, pl, np, srt, lo,
-                                                 hi, iA, slice_lin0, t.e);
-            } else if (test_pend || (hotm & want)) {
-                if (test_pend)
-                    test_row_l2<FlushGroup>(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, Ms, iA - 1,
-                                            slice_lin0, t.e);
-                for (int32_t rr = (int32_t)r_first; rr <= r_last; ++rr)
-                    if ((hotm >> rr) & 1ull)
-                        test_row_l2<FlushGroup>(g, a, ss, pbuf, buf_n, nseq, total, inner, w.status, Ms,
-                                                iA + (uint32_t)rr, slice_lin0, t.e);
-            }
-            uint32_t next_mode = 0;
-            if (pend_next) {
-                if (fits) {
-                    if (n_c > hi) {
-                        FlushGroup::sync();   // the pending list of this pass was read
-                        for (uint32_t q = hi + fr; q < n_c; q += FlushGroup::size())
-                            pl[q - hi] = srt[q] - (pr - 1) * nb;
-                        np_pend = n_c - hi;
-                        next_mode = 1;
-                    }
-                } else if ((hotm >> (pr - 1)) & 1ull) {
-                    next_mode = 2;
-                }
-            }
-            have_prev = true;
-            gP = gA + pr - 1;
-            pend_mode = next_mode;
-            FlushGroup::sync();   // lists and counters free for the next pass
+                flush_emit_pass<FlushGroup, false>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, t.pitch,
+                                                   Mrow + (size_t)p0 * nb, pr, t.i0 + p0, slice_lin0, t.e, Ms, lists,
+                                                   s_hot, &s_nc, &bars[2 + b]);
         }
     }
-    flush_chunk<FlushGroup>(a, ss, pbuf, buf_n, nseq, inner, w.status);
-    if (fr == 0) {
-        a.cta_nbnd[cta] = 0u;
-        a.cta_nseq[cta] = min(nseq, a.seq_max);
-        a.cta_total[cta] = total;
-    }
+    finish_candidates<FlushGroup>(w, a, ss, pbuf, buf_n, nseq, total, inner, cta);
+    (void)fr;
 }
 
 // ---------------------------------------------------------------------------
-// k_seam: after k_fill_scan (same grid), the two rows at the seam of each
-// fused-fill CTA whose range starts inside a slice: the previous CTA's last
-// row P and this CTA's first row Q, tested from M_H in HBM (all written by
-// now).  Their peaks become the CTA's seam chunks, ordered before its
-// interior chunks.
+// k_peaks: after a fused fill (same grid), each CTA tests its candidate
+// entries against their neighbours in the now complete M_H and compacts
+// every chunk in place to its peaks (order kept), counting them per event.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_seam(Geom g, Work w, FillCfg c, ScanArgs a)
+__global__ void __launch_bounds__(256) k_peaks(Geom g, Work w, ScanArgs a)
 {
     grid_dep_wait();
-    extern __shared__ uint4 sm4[];
-    // layout: ScanSmem (256 B) | K peak entries | rows P-1, P, Q, Q+1 (n_b words each)
-    ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
-    uint4 *pbuf = sm4 + 16;
-    uint32_t *rows = reinterpret_cast<uint32_t *>(pbuf + a.K);
-    const uint32_t tid = threadIdx.x, cta = blockIdx.x, nb = g.nb;
-    __shared__ unsigned long long s_rng[2];
-    uint64_t it0, it1;
-    cta_items(g, w, c, cta, gridDim.x, it0, it1, s_rng);
-    const uint64_t es = it0 / c.strips;
-    const uint32_t iQ = (uint32_t)(it0 % c.strips) * c.W;   // first row of the range
-    uint32_t nbnd = 0, total = 0, buf_n = 0;
-    if (iQ > 0 && it0 < it1) {   // an empty range has no seam of its own
-        const uint32_t s = (uint32_t)(es % g.n_slices), ev = (uint32_t)(es / g.n_slices);
-        const uint32_t *base = w.M + (size_t)ev * w.n_cells + ((size_t)s * g.na + iQ) * nb;
-        // the four rows around the seam into shared memory: every thread
-        // issues its loads before it stores any, so the block pays about one
-        // memory latency instead of one per loop step
-        const uint32_t r0 = iQ >= 2 ? 0u : 1u, r1 = iQ + 1 < g.na ? 4u : 3u;
-        const uint32_t *src = base - 2 * (ptrdiff_t)nb;
-        constexpr uint32_t U = 8;
-        const uint32_t k0 = r0 * nb, k1 = r1 * nb, step = U * blockDim.x;
-        for (uint32_t kb = k0; kb < k1; kb += step) {
-            uint32_t v[U];
-#pragma unroll
-            for (uint32_t q = 0; q < U; ++q) {
-                const uint32_t k = kb + q * blockDim.x + tid;
-                v[q] = k < k1 ? __ldcg(src + k) : 0u;
+    __shared__ uint32_t s_wsum[40];
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, cta = blockIdx.x;
+    const uint32_t warp = tid >> 5, lane = tid & 31u, nw = (bd + 31) >> 5;
+    const uint32_t nseq = a.cta_nseq[cta], sl = g.na * g.nb;
+    uint32_t total = 0;
+    for (uint32_t q = 0; q < nseq; ++q) {
+        uint2 *dp = &a.desc[(size_t)cta * a.seq_max + q];
+        const uint2 d = *dp;
+        uint32_t kept = 0;
+        for (uint32_t base = 0; base < d.y; base += bd) {
+            const uint32_t k = base + tid;
+            uint32_t has = 0;
+            uint4 en = make_uint4(0u, 0u, 0u, 0u);
+            if (k < d.y && d.x + k < a.entries_cap) {
+                en = a.entries[d.x + k];
+                const uint32_t s = en.x / sl, rem = en.x - s * sl, i = rem / g.nb, j = rem - i * g.nb;
+                const uint32_t *row = w.M + (size_t)en.y * w.n_cells + (size_t)(s * g.na + i) * g.nb;
+                has = is_peak_l2(row, i > 0 ? row - g.nb : nullptr, i + 1 < g.na ? row + g.nb : nullptr, j, g.nb,
+                                 en.z) ? 1u : 0u;
             }
-#pragma unroll
-            for (uint32_t q = 0; q < U; ++q) {
-                const uint32_t k = kb + q * blockDim.x + tid;
-                if (k < k1)
-                    rows[k] = v[q];
+            // stable compaction: every read of this round happens before the
+            // barrier, every write after, and no write passes its own read
+            const uint32_t incl = warp_incl_scan(has);
+            if (lane == 31u)
+                s_wsum[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t v = lane < nw ? s_wsum[lane] : 0u;
+                const uint32_t vi = warp_incl_scan(v);
+                s_wsum[lane] = vi - v;
+                if (lane == 31u)
+                    s_wsum[32] = vi;
             }
+            __syncthreads();
+            if (has) {
+                a.entries[d.x + kept + s_wsum[warp] + incl - 1] = en;
+                atomicAdd(&a.ev_count[en.y], 1u);
+            }
+            kept += s_wsum[32];
+            __syncthreads();
         }
-        __syncthreads();
-        const RowRef none{nullptr, 0u, 0u};
-        const RowRef rP{rows + nb, 1u, 0u}, rQ{rows + 2 * nb, 1u, 0u};
-        const RowRef upP = iQ >= 2 ? RowRef{rows, 1u, 0u} : none;
-        const RowRef dnQ = iQ + 1 < g.na ? RowRef{rows + 3 * nb, 1u, 0u} : none;
-        const uint32_t lin_Q = (s * g.na + iQ) * nb;
-        const ChunkList seam_list{a.desc_bnd + (size_t)cta * kSeamChunks, kSeamChunks};
-        // two rows hold at most n_b peaks: with K >= n_b a few chunks suffice
-        test_row_ref(g, a, ss, pbuf, buf_n, nbnd, total, seam_list, w.status, upP, rP, rQ, lin_Q - nb, ev);
-        test_row_ref(g, a, ss, pbuf, buf_n, nbnd, total, seam_list, w.status, rP, rQ, dnQ, lin_Q, ev);
-        flush_chunk(a, ss, pbuf, buf_n, nbnd, seam_list, w.status);
+        if (tid == 0)
+            dp->y = kept;
+        total += kept;
     }
-    if (tid == 0) {
-        a.cta_nbnd[cta] = min(nbnd, kSeamChunks);
-        a.cta_total[cta] += total;
-    }
+    if (tid == 0)
+        a.cta_total[cta] = total;
 }
 
 // Ascending bitonic sort of n <= kCand words in shared memory (block-wide).
@@ -1854,7 +1645,7 @@ cudaError_t launch_scatter(const Geom &g, const Work &w, uint32_t grid, cudaStre
 size_t fill_scan_smem_bytes(const FillCfg &c, const ScanArgs &a, uint32_t nb)
 {
     return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)c.tile_words * 4 + (size_t)c.HC * 16 +
-           (size_t)c.beta_words * 4 + (size_t)3 * kFusedCand * 4;
+           (size_t)c.beta_words * 4 + (size_t)4 * kFusedCand * 4;
 }
 
 cudaError_t launch_fill_scan(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
@@ -1870,7 +1661,7 @@ cudaError_t launch_fill_scan(const Geom &g, const Work &w, const FillCfg &c, con
 size_t fill_ws_smem_bytes(const FillCfg &c, const ScanArgs &a)
 {
     return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)2 * c.tile_words * 4 + (size_t)c.HC * 16 +
-           (size_t)c.beta_words * 4 + (size_t)3 * kFusedCand * 4 + 4 * sizeof(uint64_t);
+           (size_t)c.beta_words * 4 + (size_t)4 * kFusedCand * 4 + 4 * sizeof(uint64_t);
 }
 
 cudaError_t launch_fill_ws(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
@@ -1892,14 +1683,9 @@ cudaError_t fill_ws_occupancy(const FillCfg &c, const ScanArgs &a, int *blocks_p
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fill_ws, kWsThreads, smem);
 }
 
-cudaError_t launch_seam(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
-                        cudaStream_t st)
+cudaError_t launch_peaks(const Geom &g, const Work &w, const ScanArgs &a, uint32_t grid, cudaStream_t st)
 {
-    const size_t smem = 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)4 * g.nb * 4;
-    cudaError_t e = allow_smem((const void *)k_seam, smem);
-    if (e != cudaSuccess)
-        return e;
-    return launch_pdl(k_seam, grid, 256, smem, st, g, w, c, a);
+    return launch_pdl(k_peaks, grid, 256, 0, st, g, w, a);
 }
 
 cudaError_t fill_scan_occupancy(const FillCfg &c, const ScanArgs &a, uint32_t nb, int *blocks_per_sm)
