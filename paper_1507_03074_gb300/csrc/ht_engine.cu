@@ -131,6 +131,7 @@ ht_status engine_configure(Engine &E, std::string *why)
     f.pitch16 = round_up((b.n_b + 1) / 2, 32);
     f.pitch32 = round_up(b.n_b, 32);
     f.beta_words = round_up(b.n_b + 1, 4);
+    f.dyn = 1;   // the last items are handed out at run time (htk::dyn_items)
     const size_t beta_bytes = (size_t)f.beta_words * 4;
     uint32_t W = t.fill_W;
     if (W && (W & (W - 1))) {
@@ -206,6 +207,7 @@ ht_status engine_configure(Engine &E, std::string *why)
         htk::ScanArgs tmp{};
         tmp.K = E.fused_K;
         htk::FillCfg wf = f;
+        wf.dyn = 0;   // both thread groups walk the same static range
         wf.threads = htk::kWsThreads / 2;
         wf.HC = std::max(wf.HC, 2 * wf.threads);
         while (!t.fill_HC && wf.HC > 2 * wf.threads && htk::fill_ws_smem_bytes(wf, tmp) > kSmemMax)
@@ -283,7 +285,9 @@ ht_status engine_configure(Engine &E, std::string *why)
     const uint64_t items_max = (uint64_t)E.max_events * g.n_slices * f.strips;
     const uint32_t fused_grid = E.fused_ok ? (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.fused_grid, items_max)) : 0;
     const uint32_t ws_grid = E.ws_ok ? (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.ws_grid, items_max)) : 0;
-    const uint32_t grid_cap = std::max(std::max(scan_grid, fused_grid), ws_grid);
+    // the fused fill's candidate lists: one per CTA plus one per handed-out item
+    const uint32_t fused_lists = fused_grid + (uint32_t)htk::dyn_items(items_max, fused_grid);
+    const uint32_t grid_cap = std::max(std::max(scan_grid, fused_lists), ws_grid);
     uint32_t seq = chunks_for((G_max + scan_grid - 1) / scan_grid + 1, (g.nb + 1) / 2, s.K, 2 * kScanThreads);
     // the cost-balanced split gives a CTA at most `spread` times the items of
     // an even split (every strip costs at least its n_b-per-row writing share)
@@ -598,6 +602,7 @@ cudaError_t engine_vote(Engine &E, const uint32_t *d_hit_off, uint32_t n_hits0, 
         ff.accumulate = 0u;
         const uint32_t grid =
             (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.use_ws ? E.ws_grid : E.fused_grid, items));
+        const uint32_t lists = grid + (ff.dyn ? (uint32_t)htk::dyn_items(items, grid) : 0u);
         {
             ProfScope ps(E, E.use_ws ? K_FILL_WS : K_FILL_SCAN, st);
             e = E.use_ws ? htk::launch_fill_ws(E.geom, w, ff, a, grid, st)
@@ -606,13 +611,13 @@ cudaError_t engine_vote(Engine &E, const uint32_t *d_hit_off, uint32_t n_hits0, 
         ++E.launches;
         if (e == cudaSuccess) {
             ProfScope ps(E, K_PEAKS, st);
-            e = htk::launch_peaks(E.geom, w, a, grid, st);
+            e = htk::launch_peaks(E.geom, w, a, lists, st);
             ++E.launches;
         }
         if (e == cudaSuccess) {
             E.fused_valid = true;
             E.ctr_dirty = true;
-            E.fused_grid_used = grid;
+            E.fused_grid_used = lists;
             E.fused_events = n_events;
         }
         return e;

@@ -22,7 +22,19 @@ struct FillCfg {
     uint32_t threads;     // block size
     uint32_t accumulate;  // add the tile to M_H instead of storing it
     uint32_t beta_words;  // shared-memory copy of the B-bin thresholds (n_b + 1, rounded to 4)
+    uint32_t dyn;         // 1: the last dyn_items() items are handed out at run time (see below)
 };
+
+// The fills split the first items - dyn_items(items, grid) work items over
+// their CTAs by estimated cost, and hand the rest out one at a time to the
+// CTAs that finish first (an atomic counter), which absorbs the spread of
+// the static split.  In the fused fill every handed-out item gets its own
+// list of candidate chunks, numbered grid + its rank, so the lists stay in
+// linear order.
+__host__ __device__ constexpr uint64_t dyn_items(uint64_t items, uint32_t grid)
+{
+    return items / 8 < 2ull * grid ? items / 8 : 2ull * grid;
+}
 
 // Scan (and its chunk bookkeeping).  Shared with k_order.
 struct ScanArgs {
@@ -79,9 +91,13 @@ size_t scan_smem_bytes(const ScanArgs &a);
 constexpr uint32_t kSeamChunks = 8;
 
 // Layout of the counter block: [0] status, [1] entries used, [2] order
-// ticket, [3] binning ticket (reset by k_bin's last block), [4 ..) peaks per
-// event.  k_bin zeroes words 1, 2 and [4, 4 + n_events) before every fill.
-enum : uint32_t { CTR_STATUS = 0, CTR_ENTRIES = 1, CTR_OTICKET = 2, CTR_BTICKET = 3, CTR_EVENTS = 4 };
+// ticket, [3] binning ticket (reset by k_bin's last block), [4] next
+// handed-out fill item and [5] fill CTAs done with them (both reset by the
+// last such CTA), [6 ..) peaks per event.  k_bin zeroes words 1, 2 and
+// [6, 6 + n_events) before every fill.
+enum : uint32_t {
+    CTR_STATUS = 0, CTR_ENTRIES = 1, CTR_OTICKET = 2, CTR_BTICKET = 3, CTR_DYN = 4, CTR_DYN_DONE = 5, CTR_EVENTS = 6
+};
 
 // Cost model of the balanced split of (event, slice, strip) work items over
 // the fill CTAs: a strip of r rows in a slice of h hits costs

@@ -421,14 +421,19 @@ __device__ __forceinline__ uint32_t stage_hits(const Work &w, float4 *hs, uint32
 // it and gets the same result; s_res: 2 shared words.
 template <class G = BlockGroup>
 __device__ __forceinline__ void cta_items(const Geom &g, const Work &w, const FillCfg &c, uint32_t cta,
-                                          uint32_t grid, uint64_t &it0, uint64_t &it1, unsigned long long *s_res)
+                                          uint32_t grid, uint64_t n_static, uint64_t &it0, uint64_t &it1,
+                                          unsigned long long *s_res)
 {
     const uint32_t U = w.n_events * g.n_slices;
-    const uint64_t items = (uint64_t)U * c.strips;
     auto cost = [&](uint32_t u) {
         return (uint64_t)g.na * ((uint64_t)g.nb * u + (uint64_t)kVoteWeight * __ldcg(&w.slice_off[u]));
     };
-    const uint64_t total = cost(U);
+    // the cost of the first n_static items
+    const uint32_t us = (uint32_t)(n_static / c.strips), ks = (uint32_t)(n_static % c.strips);
+    uint64_t total = cost(us);
+    if (ks)
+        total += ks * ((cost(us + 1) - total + c.strips - 1) / c.strips);
+    const uint64_t items = n_static;
     const uint64_t T0 = (total / grid) * cta + ((total % grid) * cta) / grid;
     const uint64_t T1 = (total / grid) * (cta + 1) + ((total % grid) * (cta + 1)) / grid;
     if (G::rank() == 0)
@@ -448,9 +453,33 @@ __device__ __forceinline__ void cta_items(const Geom &g, const Work &w, const Fi
         }
     }
     G::sync();
-    it0 = s_res[0];
-    it1 = cta + 1 == grid ? items : (uint64_t)s_res[1];
+    it0 = min((uint64_t)s_res[0], items);
+    it1 = cta + 1 == grid ? items : min((uint64_t)s_res[1], items);
     G::sync();   // s_res may be reused
+}
+
+// Hand out the next run-time item (see dyn_items): returns its rank, or
+// n_dyn once none is left -- after which the last CTA to find none resets
+// both counters for the next fill.  All threads of the block call it.
+__device__ __forceinline__ uint32_t next_dyn_item(const Work &w, uint32_t n_dyn, uint32_t *s_word)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t d = n_dyn;
+        if (n_dyn)
+            d = atomicAdd(&w.ctr[CTR_DYN], 1u);
+        if (d >= n_dyn) {
+            d = n_dyn;
+            __threadfence();
+            if (atomicAdd(&w.ctr[CTR_DYN_DONE], 1u) == gridDim.x - 1) {
+                w.ctr[CTR_DYN] = 0u;
+                w.ctr[CTR_DYN_DONE] = 0u;
+            }
+        }
+        *s_word = d;
+    }
+    __syncthreads();
+    return *s_word;
 }
 
 // Walks the (event, slice, strip) work items it0, it0 + 1, ... of a CTA with
@@ -494,13 +523,15 @@ __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
     grid_dep_wait();   // the unit lists of k_scatter
 
     __shared__ unsigned long long s_rng[2];
+    __shared__ uint32_t s_dyn;
+    const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
+    const uint64_t n_dyn = c.dyn ? dyn_items(items, gridDim.x) : 0, n_static = items - n_dyn;
     uint64_t it0, it1;
-    cta_items(g, w, c, blockIdx.x, gridDim.x, it0, it1, s_rng);
+    cta_items(g, w, c, blockIdx.x, gridDim.x, n_static, it0, it1, s_rng);
     uint64_t cached_es = ~0ull;   // (event, slice) whose whole hit list is in hs
     uint32_t cached_n = 0;
 
-    ItemCursor cur(g, c, it0);
-    for (uint64_t item = it0; item < it1; ++item, cur.next(g, c)) {
+    auto do_item = [&](const ItemCursor &cur) {
         const uint32_t k = cur.k;
         const uint64_t es = cur.es;
         const uint32_t s = cur.s;
@@ -559,7 +590,13 @@ __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
                     flush_tile<false, false, false>(g, tile, dst, pr, pitch, FlushList{});
             }
         }
-    }
+    };
+    ItemCursor cur(g, c, it0);
+    for (uint64_t item = it0; item < it1; ++item, cur.next(g, c))
+        do_item(cur);
+    if (c.dyn)
+        for (uint32_t d; (d = next_dyn_item(w, (uint32_t)n_dyn, &s_dyn)) < n_dyn;)
+            do_item(ItemCursor(g, c, n_static + d));
 }
 
 // ---------------------------------------------------------------------------
@@ -1049,17 +1086,19 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
         beta[k] = g.bth[k];
     grid_dep_wait();   // the unit lists of k_scatter
     const uint32_t cta = blockIdx.x;
-    const ChunkList inner = interior_list(a, cta);
+    ChunkList inner = interior_list(a, cta);
 
     __shared__ unsigned long long s_rng[2];
+    __shared__ uint32_t s_dyn;
+    const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
+    const uint64_t n_dyn = c.dyn ? dyn_items(items, gridDim.x) : 0, n_static = items - n_dyn;
     uint64_t it0, it1;
-    cta_items(g, w, c, cta, gridDim.x, it0, it1, s_rng);
+    cta_items(g, w, c, cta, gridDim.x, n_static, it0, it1, s_rng);
     uint64_t cached_es = ~0ull;
     uint32_t cached_n = 0;
     uint32_t buf_n = 0, nseq = 0, total = 0;
 
-    ItemCursor cur(g, c, it0);
-    for (uint64_t item = it0; item < it1; ++item, cur.next(g, c)) {
+    auto do_item = [&](const ItemCursor &cur) {
         const uint32_t k = cur.k;
         const uint64_t es = cur.es;
         const uint32_t s = cur.s;
@@ -1117,8 +1156,21 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
                                                    Mrow + (size_t)p0 * nb, pr, iA, slice_lin0, e, Ms, lists, s_hot,
                                                    &s_nc, nullptr);
         }
-    }
+    };
+    ItemCursor cur(g, c, it0);
+    for (uint64_t item = it0; item < it1; ++item, cur.next(g, c))
+        do_item(cur);
     finish_candidates<BlockGroup>(w, a, ss, pbuf, buf_n, nseq, total, inner, cta);
+    if (c.dyn) {
+        // handed-out items, each with its own list of chunks
+        for (uint32_t d; (d = next_dyn_item(w, (uint32_t)n_dyn, &s_dyn)) < n_dyn;) {
+            const uint32_t list = gridDim.x + d;
+            inner = interior_list(a, list);
+            buf_n = nseq = total = 0;
+            do_item(ItemCursor(g, c, n_static + d));
+            finish_candidates<BlockGroup>(w, a, ss, pbuf, buf_n, nseq, total, inner, list);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1196,7 +1248,8 @@ __global__ void __launch_bounds__(1024, 1) k_fill_ws(Geom g, Work w, FillCfg c, 
         // ---------------- vote group ----------------
         const uint32_t vr = VoteGroup::rank();
         uint64_t it0, it1;
-        cta_items<VoteGroup>(g, w, c, cta, gridDim.x, it0, it1, s_rng[0]);
+        cta_items<VoteGroup>(g, w, c, cta, gridDim.x, (uint64_t)w.n_events * g.n_slices * c.strips, it0, it1,
+                             s_rng[0]);
         uint64_t cached_es = ~0ull;
         uint32_t cached_n = 0, p = 0;
         ItemCursor cur(g, c, it0);
@@ -1251,7 +1304,8 @@ __global__ void __launch_bounds__(1024, 1) k_fill_ws(Geom g, Work w, FillCfg c, 
     // ---------------- flush + emit group ----------------
     const uint32_t fr = FlushGroup::rank();
     uint64_t it0, it1;
-    cta_items<FlushGroup>(g, w, c, cta, gridDim.x, it0, it1, s_rng[1]);
+    cta_items<FlushGroup>(g, w, c, cta, gridDim.x, (uint64_t)w.n_events * g.n_slices * c.strips, it0, it1,
+                          s_rng[1]);
     const ChunkList inner = interior_list(a, cta);
     uint32_t buf_n = 0, nseq = 0, total = 0, p = 0;
     bool alive = true;
