@@ -92,7 +92,8 @@ enum {
     HT_MEM_HOST = 0,         /* pointers are host memory (default) */
     HT_MEM_DEVICE = 1,       /* pointers are device memory; call is async */
     HT_ACCUMULATE = 2,       /* ht_fill: add to M_H instead of overwriting it */
-    HT_FILL_NAIVE = 4        /* ht_fill: clear + one global atomic per vote */
+    HT_FILL_NAIVE = 4,       /* ht_fill: clear + one global atomic per vote */
+    HT_PEAKS_ONLY = 8        /* ht_fill: find the peaks without writing M_H to device memory */
 };
 
 /* Thread-local text of the last failure (never NULL). */
@@ -118,7 +119,11 @@ ht_status ht_destroy(ht_ctx *ctx);
  * (the caller may reuse its arrays at once).  HT_MEM_DEVICE: device arrays,
  * kept valid by the caller until the stream has run the work.
  * HT_FILL_NAIVE selects the reference-design fill (explicit clear, then one
- * global atomicAdd per vote).  n_hits may be 0 (M_H becomes all zero).
+ * global atomicAdd per vote).  HT_PEAKS_ONLY keeps every vote tile in shared
+ * memory: the next ht_find_maxima returns the same peaks, but M_H is left as
+ * it was (ht_copy_matrix does not show this fill); not with HT_ACCUMULATE or
+ * HT_FILL_NAIVE; the first such fill allocates a small edge-row buffer and
+ * waits for the device.  n_hits may be 0 (M_H becomes all zero).
  * Errors: HT_E_INVAL (NULL pointer with n_hits > 0, n_hits > max_hits, or
  * accumulated hits beyond max_hits), HT_E_CUDA, HT_E_STATE. */
 ht_status ht_fill(ht_ctx *ctx, const float *x, const float *y, const float *z, uint32_t n_hits,

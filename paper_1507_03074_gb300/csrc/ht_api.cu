@@ -150,8 +150,19 @@ ht_status ht_fill(ht_ctx *ctx, const float *x, const float *y, const float *z, u
     ht_status s = check_ctx(ctx);
     if (s != HT_OK)
         return s;
-    if (flags & ~(uint32_t)(HT_MEM_DEVICE | HT_ACCUMULATE | HT_FILL_NAIVE))
+    if (flags & ~(uint32_t)(HT_MEM_DEVICE | HT_ACCUMULATE | HT_FILL_NAIVE | HT_PEAKS_ONLY))
         return set_err(HT_E_INVAL, "unknown flag");
+    if ((flags & HT_PEAKS_ONLY) && (flags & (HT_ACCUMULATE | HT_FILL_NAIVE)))
+        return set_err(HT_E_INVAL, "HT_PEAKS_ONLY does not combine with HT_ACCUMULATE or HT_FILL_NAIVE");
+    if (flags & HT_PEAKS_ONLY) {
+        std::string why;
+        s = hte::engine_ensure_edges(ctx->E, &why);
+        if (s != HT_OK) {
+            if (s == HT_E_CUDA)
+                ctx->poisoned = true;
+            return set_err(s, why);
+        }
+    }
     if (n_hits && (!x || !y || !z))
         return set_err(HT_E_INVAL, "hit arrays must not be NULL");
     const bool accumulate = (flags & HT_ACCUMULATE) != 0;

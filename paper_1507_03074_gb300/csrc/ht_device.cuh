@@ -52,6 +52,10 @@ struct Work {
     uint32_t *slice_off;        // [n_events * n_slices + 1] exclusive prefix of slice_cnt
     float4 *list;               // list_cap hit records {x, x^2 + y^2, 2y, event}, unit by unit
     uint32_t list_cap;
+    // peaks-only fills: the first and last row of every strip pass,
+    // [unit][edge_pass][2][n_b] (pass p of a unit covers rows p * rpass ..)
+    uint32_t *edge;
+    uint32_t edge_pass;
 };
 
 constexpr uint32_t kDropped = 0xffffffffu;

@@ -17,7 +17,8 @@ static const uint32_t kPeakBuf = 1024;         // K: entries buffered per scan /
 static const uint32_t kFusedPeakBuf = 512;     // K of a fused-fill CTA (at least its block)
 
 const char *const kKernelNames[K_NKINDS] = {"k_bin", "k_scatter", "k_fill_priv", "k_fill_scan", "k_fill_ws",
-                                             "k_peaks", "k_clear", "k_fill_naive", "k_scan", "k_order"};
+                                             "k_fill_peaks", "k_peaks", "k_clear", "k_fill_naive", "k_scan",
+                                             "k_order"};
 
 // ---------------------------------------------------------------------------
 // Profiling
@@ -502,6 +503,7 @@ void engine_destroy(Engine &E)
     cudaFree(E.d_codes);
     cudaFree(E.d_slice);
     cudaFree(E.d_list);
+    cudaFree(E.d_edge);
     cudaFree(E.d_entries);
     cudaFree(E.d_book);
     cudaFree(E.d_ctr);
@@ -511,6 +513,8 @@ void engine_destroy(Engine &E)
     E.d_codes = nullptr;
     E.d_slice = nullptr;
     E.d_list = nullptr;
+    E.d_edge = nullptr;
+    E.edge_pass = 0;
     E.d_entries = nullptr;
     E.d_book = nullptr;
     E.d_ctr = nullptr;
@@ -539,6 +543,8 @@ static htk::Work make_work(Engine &E, const float *x, const float *y, const floa
     w.slice_off = E.d_slice + 2 * units;
     w.list = E.d_list;
     w.list_cap = E.list_cap;
+    w.edge = E.d_edge;
+    w.edge_pass = E.edge_pass;
     return w;
 }
 
@@ -595,23 +601,26 @@ cudaError_t engine_vote(Engine &E, const uint32_t *d_hit_off, uint32_t n_hits0, 
     htk::FillCfg f = E.fill;
     f.accumulate = accumulate ? 1u : 0u;
     const uint64_t items = (uint64_t)n_events * E.geom.n_slices * f.strips;
+    const bool peaks_only = (flags & HT_PEAKS_ONLY) && E.fused_ok && E.d_edge &&
+                            E.edge_pass * std::max<uint32_t>(1, E.fused_fill.W / 2) >= E.geom.na;
     if ((E.use_ws || E.fused_ok) && !accumulate) {
         htk::ScanArgs a = E.scan;
         a.K = E.fused_K;
-        htk::FillCfg ff = E.use_ws ? E.ws_fill : E.fused_fill;
+        const bool ws = E.use_ws && !peaks_only;
+        htk::FillCfg ff = ws ? E.ws_fill : E.fused_fill;
         ff.accumulate = 0u;
-        const uint32_t grid =
-            (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.use_ws ? E.ws_grid : E.fused_grid, items));
+        const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(ws ? E.ws_grid : E.fused_grid, items));
         const uint32_t lists = grid + (ff.dyn ? (uint32_t)htk::dyn_items(items, grid) : 0u);
         {
-            ProfScope ps(E, E.use_ws ? K_FILL_WS : K_FILL_SCAN, st);
-            e = E.use_ws ? htk::launch_fill_ws(E.geom, w, ff, a, grid, st)
-                         : htk::launch_fill_scan(E.geom, w, ff, a, grid, st);
+            ProfScope ps(E, ws ? K_FILL_WS : peaks_only ? K_FILL_PEAKS : K_FILL_SCAN, st);
+            e = ws ? htk::launch_fill_ws(E.geom, w, ff, a, grid, st)
+               : peaks_only ? htk::launch_fill_peaks(E.geom, w, ff, a, grid, st)
+                            : htk::launch_fill_scan(E.geom, w, ff, a, grid, st);
         }
         ++E.launches;
         if (e == cudaSuccess) {
             ProfScope ps(E, K_PEAKS, st);
-            e = htk::launch_peaks(E.geom, w, a, lists, st);
+            e = htk::launch_peaks(E.geom, w, ff, a, lists, peaks_only, st);
             ++E.launches;
         }
         if (e == cudaSuccess) {
@@ -830,6 +839,32 @@ cudaError_t prof_read(Engine &E, ht_kernel_time *out, uint32_t cap, uint32_t *n)
     }
     *n = k;
     return cudaSuccess;
+}
+
+ht_status engine_ensure_edges(Engine &E, std::string *why)
+{
+    // passes per unit at the smallest pass height (u32 tiles: W / 2 rows)
+    const uint32_t rpass_min = std::max<uint32_t>(1, E.fused_fill.W / 2);
+    const uint32_t passes = (E.geom.na + rpass_min - 1) / rpass_min;
+    if (E.d_edge && E.edge_pass >= passes)
+        return HT_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        *why = std::string("synchronise before allocation: ") + cudaGetErrorString(e);
+        return HT_E_CUDA;
+    }
+    cudaFree(E.d_edge);
+    E.d_edge = nullptr;
+    E.edge_pass = 0;
+    const size_t bytes = (size_t)E.max_events * E.geom.n_slices * passes * 2 * E.geom.nb * 4;
+    if ((e = cudaMalloc(&E.d_edge, bytes)) != cudaSuccess) {
+        cudaGetLastError();
+        *why = std::string("edge-row buffer allocation failed: ") + cudaGetErrorString(e);
+        return HT_E_NOMEM;
+    }
+    E.edge_pass = passes;
+    E.device_bytes += bytes;
+    return HT_OK;
 }
 
 } // namespace hte

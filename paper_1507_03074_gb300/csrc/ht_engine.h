@@ -29,7 +29,8 @@ struct Tuning {
 // Optional per-kernel timing with CUDA events recorded on the launching
 // stream around every launch (enabled by ht_profile).
 enum KernelKind {
-    K_BIN, K_SCATTER, K_FILL_PRIV, K_FILL_SCAN, K_FILL_WS, K_PEAKS, K_CLEAR, K_FILL_NAIVE, K_SCAN, K_ORDER, K_NKINDS
+    K_BIN, K_SCATTER, K_FILL_PRIV, K_FILL_SCAN, K_FILL_WS, K_FILL_PEAKS, K_PEAKS, K_CLEAR, K_FILL_NAIVE, K_SCAN,
+    K_ORDER, K_NKINDS
 };
 extern const char *const kKernelNames[K_NKINDS];
 
@@ -87,6 +88,8 @@ struct Engine {
     uint32_t *d_M = nullptr;
     float4 *d_hits4 = nullptr;
     uint32_t *d_codes = nullptr;
+    uint32_t *d_edge = nullptr;   // peaks-only fills: edge rows of every pass (allocated on first use)
+    uint32_t edge_pass = 0;       // passes per unit the edge buffer holds
     uint32_t *d_slice = nullptr;  // unit counts | scatter cursors | offsets (3 * units + 1)
     float4 *d_list = nullptr;     // hit records unit by unit
     uint32_t list_cap = 0;
@@ -149,6 +152,10 @@ void engine_get_tuning(const Engine &E, ht_tuning *t);
 
 // Per-kernel totals into the ABI's records (waits for recorded events).
 cudaError_t prof_read(Engine &E, ht_kernel_time *out, uint32_t cap, uint32_t *n);
+
+// Allocate the edge-row buffer of peaks-only fills (once; synchronises the
+// device the first time).
+ht_status engine_ensure_edges(Engine &E, std::string *why);
 
 // Device status word (bits of htk::ST_*).
 inline uint32_t *engine_status(Engine &E) { return E.d_ctr + htk::CTR_STATUS; }

@@ -82,8 +82,13 @@ size_t fill_ws_smem_bytes(const FillCfg &c, const ScanArgs &a);
 cudaError_t launch_fill_ws(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
                            cudaStream_t st);
 cudaError_t fill_ws_occupancy(const FillCfg &c, const ScanArgs &a, int *blocks_per_sm);
-// After a fused fill (same grid): test its candidate entries, keep the peaks.
-cudaError_t launch_peaks(const Geom &g, const Work &w, const ScanArgs &a, uint32_t grid, cudaStream_t st);
+// After a fused fill (same grid): test its candidate entries, keep the peaks
+// (peaks_only: after k_fill_peaks, finishing the edge-flagged tests).
+cudaError_t launch_peaks(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
+                         bool peaks_only, cudaStream_t st);
+// The fused fill without writing M_H (same shapes and grid as k_fill_scan).
+cudaError_t launch_fill_peaks(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
+                              cudaStream_t st);
 cudaError_t launch_clear(uint32_t *M, uint64_t words, uint32_t grid, cudaStream_t st);
 cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
 size_t scan_smem_bytes(const ScanArgs &a);

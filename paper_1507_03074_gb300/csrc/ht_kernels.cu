@@ -1174,6 +1174,228 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
 }
 
 // ---------------------------------------------------------------------------
+// k_fill_peaks: the fused fill without M_H in HBM (peaks-only fills).
+//
+// The passes are voted as in k_fill_scan, but the tile is not written out:
+// its cells >= T are tested at once against the neighbours the tile holds,
+// and the pass's first and last rows go to a small edge buffer.  A cell on
+// the first (last) row of its pass whose row above (below) belongs to
+// another pass is emitted with a flag; k_peaks finishes its test from the
+// edge rows.  The output is the same ordered peak list; M_H is left as it
+// was.
+// ---------------------------------------------------------------------------
+
+// Votes of cell (r, j) of a tile (u16 or u32 counters, row swizzle).
+__device__ __forceinline__ uint32_t tile_cell(const uint32_t *tile, uint32_t pitch, bool u16, uint32_t r, uint32_t j)
+{
+    if (u16)
+        return (tile[r * pitch + ((j >> 1) ^ (row_hash(r) & 0x1Eu))] >> ((j & 1u) << 4)) & 0xffffu;
+    return tile[r * pitch + (j ^ (row_hash(r) & 0x1Cu))];
+}
+
+// Test of cell (r, j) with votes v against the neighbours inside the tile
+// rows 0 .. pr - 1 (rule of Sec. 3 as read: > neighbours before it, >= after).
+__device__ __forceinline__ bool tile_peak(const uint32_t *tile, uint32_t pitch, bool u16, uint32_t pr, uint32_t nb,
+                                          uint32_t r, uint32_t j, uint32_t v)
+{
+    const bool hl = j > 0, hr = j + 1 < nb;
+    if (r > 0) {
+        if (hl && !(v > tile_cell(tile, pitch, u16, r - 1, j - 1))) return false;
+        if (!(v > tile_cell(tile, pitch, u16, r - 1, j))) return false;
+        if (hr && !(v > tile_cell(tile, pitch, u16, r - 1, j + 1))) return false;
+    }
+    if (hl && !(v > tile_cell(tile, pitch, u16, r, j - 1))) return false;
+    if (hr && !(v >= tile_cell(tile, pitch, u16, r, j + 1))) return false;
+    if (r + 1 < pr) {
+        if (hl && !(v >= tile_cell(tile, pitch, u16, r + 1, j - 1))) return false;
+        if (!(v >= tile_cell(tile, pitch, u16, r + 1, j))) return false;
+        if (hr && !(v >= tile_cell(tile, pitch, u16, r + 1, j + 1))) return false;
+    }
+    return true;
+}
+
+// Edge-flag bits of a peaks-only entry (in its .w): its test still needs
+// the row above / below, which lies in another pass.
+enum : uint32_t { EDGE_UP = 1u, EDGE_DN = 2u };
+
+__global__ void __launch_bounds__(1024) k_fill_peaks(Geom g, Work w, FillCfg c, ScanArgs a)
+{
+    extern __shared__ uint4 sm4[];
+    // layout as k_fill_scan
+    ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
+    uint4 *pbuf = sm4 + 16;
+    uint32_t *tile = reinterpret_cast<uint32_t *>(pbuf + a.K);
+    float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
+    float *beta = reinterpret_cast<float *>(hs + c.HC);
+    uint32_t *lists = reinterpret_cast<uint32_t *>(beta + c.beta_words);
+    uint32_t *cand = lists, *candv = lists + kFusedCand, *srt = lists + 2 * kFusedCand, *srtv = lists + 3 * kFusedCand;
+    __shared__ uint32_t s_hot[2], s_nc;
+
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb, T = g.threshold;
+    for (uint32_t k = tid; k < c.tile_words / 4; k += bd)
+        sm4[16 + a.K + k] = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t k = tid; k <= nb; k += bd)
+        beta[k] = g.bth[k];
+    grid_dep_wait();   // the unit lists of k_scatter
+    const uint32_t cta = blockIdx.x;
+    ChunkList inner = interior_list(a, cta);
+
+    __shared__ unsigned long long s_rng[2];
+    __shared__ uint32_t s_dyn;
+    const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
+    const uint64_t n_dyn = c.dyn ? dyn_items(items, gridDim.x) : 0, n_static = items - n_dyn;
+    uint64_t it0, it1;
+    cta_items(g, w, c, cta, gridDim.x, n_static, it0, it1, s_rng);
+    uint64_t cached_es = ~0ull;
+    uint32_t cached_n = 0;
+    uint32_t buf_n = 0, nseq = 0, total = 0;
+    const uint32_t rc = fused_round(bd, a.K);
+
+    auto do_item = [&](const ItemCursor &cur) {
+        const uint32_t k = cur.k;
+        const uint64_t es = cur.es;
+        const uint32_t s = cur.s;
+        const uint32_t e = cur.e;
+        const uint32_t l0 = __ldg(&w.slice_off[es]), l1 = __ldg(&w.slice_off[es + 1]);
+        const uint32_t i0 = k * c.W;
+        const uint32_t rows = min(c.W, g.na - i0);
+        const bool u16 = (l1 - l0) < 65536u;
+        const uint32_t rpass = u16 ? c.W : c.W / 2;
+        const uint32_t pitch = u16 ? c.pitch16 : c.pitch32;
+        const uint32_t slice_lin0 = s * g.na * nb;
+        const uint32_t r = tid % rpass, hl = tid / rpass, hstride = bd / rpass;
+
+        for (uint32_t p0 = 0; p0 < rows; p0 += rpass) {
+            const uint32_t pr = min(rpass, rows - p0);
+            const uint32_t iA = i0 + p0;
+            // ---- vote -------------------------------------------------------
+            const uint32_t i = iA + r;
+            if (cached_es == es) {
+                __syncthreads();
+                if (r < pr) {
+                    if (u16)
+                        vote_rows<true>(g, tile, hs, beta, cached_n, r, i, hl, hstride, pitch);
+                    else
+                        vote_rows<false>(g, tile, hs, beta, cached_n, r, i, hl, hstride, pitch);
+                }
+            } else {
+                cached_es = ~0ull;
+                uint32_t pos = l0;
+                bool first = true;
+                while (first || pos < l1) {
+                    const uint32_t nsel = stage_hits(w, hs, c.HC, pos, l1);
+                    if (first && pos >= l1) {
+                        cached_es = es;
+                        cached_n = nsel;
+                    }
+                    first = false;
+                    if (r < pr) {
+                        if (u16)
+                            vote_rows<true>(g, tile, hs, beta, nsel, r, i, hl, hstride, pitch);
+                        else
+                            vote_rows<false>(g, tile, hs, beta, nsel, r, i, hl, hstride, pitch);
+                    }
+                }
+            }
+            if (tid == 0)
+                s_hot[0] = s_hot[1] = s_nc = 0u;
+            __syncthreads();
+            // ---- list the cells >= T; the edge rows to the edge buffer -------
+            const uint32_t pass = iA / rpass;
+            uint32_t *edge = w.edge + ((size_t)es * w.edge_pass + pass) * 2 * nb;
+            for (uint32_t u = tid; u < pr * nb; u += bd) {
+                const uint32_t rr = u / nb, j = u - rr * nb;
+                const uint32_t v = tile_cell(tile, pitch, u16, rr, j);
+                if (rr == 0)
+                    edge[j] = v;
+                if (rr == pr - 1)
+                    edge[nb + j] = v;
+                if (v >= T) {
+                    atomicOr(&s_hot[rr >> 5], 1u << (rr & 31u));
+                    const uint32_t q = atomicAdd(&s_nc, 1u);
+                    if (q < kFusedCand) {
+                        cand[q] = u;
+                        candv[q] = v;
+                    }
+                }
+            }
+            __syncthreads();
+            const uint32_t n_c = s_nc;
+            const uint64_t hotm = (uint64_t)s_hot[0] | ((uint64_t)s_hot[1] << 32);
+            const bool up_out = iA > 0, dn_out = iA + pr < g.na;   // neighbours in other passes
+            // ---- test against the tile, emit peaks and flagged edge cells ----
+            if (n_c) {
+                const bool fits = n_c <= kFusedCand;
+                if (fits) {
+                    for (uint32_t q = tid; q < n_c; q += bd) {
+                        const uint32_t key = cand[q];
+                        uint32_t rank = 0;
+                        for (uint32_t m = 0; m < n_c; ++m)
+                            rank += cand[m] < key;
+                        srt[rank] = key;
+                        srtv[rank] = candv[q];
+                    }
+                    __syncthreads();
+                }
+                // rounds of rc cells: the sorted list, or every cell of the hot rows
+                const uint32_t m_total = fits ? n_c : pr * nb;
+                for (uint32_t base = 0; base < m_total; base += rc) {
+                    const uint32_t q = base + tid;
+                    uint32_t has = 0;
+                    uint4 ent = make_uint4(0u, 0u, 0u, 0u);
+                    if (tid < rc && q < m_total) {
+                        uint32_t key, v;
+                        bool ok = true;
+                        if (fits) {
+                            key = srt[q];
+                            v = srtv[q];
+                        } else {
+                            key = q;
+                            const uint32_t rr = q / nb;
+                            ok = (hotm >> rr) & 1ull;
+                            v = ok ? tile_cell(tile, pitch, u16, rr, q - rr * nb) : 0u;
+                            ok = ok && v >= T;
+                        }
+                        if (ok) {
+                            const uint32_t rr = key / nb, j = key - rr * nb;
+                            if (tile_peak(tile, pitch, u16, pr, nb, rr, j, v)) {
+                                const uint32_t flags = (rr == 0 && up_out ? EDGE_UP : 0u) |
+                                                       (rr == pr - 1 && dn_out ? EDGE_DN : 0u);
+                                has = 1;
+                                ent = make_uint4(slice_lin0 + iA * nb + key, e, v, flags);
+                            }
+                        }
+                    }
+                    if (__syncthreads_or(has)) {
+                        if (buf_n + rc > a.K)
+                            flush_chunk(a, ss, pbuf, buf_n, nseq, inner, w.status);
+                        compact_entry<BlockGroup, false>(ss, pbuf, buf_n, has, ent, nullptr);
+                        total += ss.round_total;
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- clear the tile ------------------------------------------------
+            for (uint32_t q = tid; q < pr * pitch / 4; q += bd)
+                reinterpret_cast<uint4 *>(tile)[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    ItemCursor cur(g, c, it0);
+    for (uint64_t item = it0; item < it1; ++item, cur.next(g, c))
+        do_item(cur);
+    finish_candidates<BlockGroup>(w, a, ss, pbuf, buf_n, nseq, total, inner, cta);
+    if (c.dyn) {
+        for (uint32_t d; (d = next_dyn_item(w, (uint32_t)n_dyn, &s_dyn)) < n_dyn;) {
+            const uint32_t list = gridDim.x + d;
+            inner = interior_list(a, list);
+            buf_n = nseq = total = 0;
+            do_item(ItemCursor(g, c, n_static + d));
+            finish_candidates<BlockGroup>(w, a, ss, pbuf, buf_n, nseq, total, inner, list);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_fill_ws: the fused fill with warp specialisation, one CTA per SM.
 //
 // 1024 threads in two groups of 16 warps: the vote group stages hits and
@@ -1345,7 +1567,7 @@ __global__ void __launch_bounds__(1024, 1) k_fill_ws(Geom g, Work w, FillCfg c, 
 // entries against their neighbours in the now complete M_H and compacts
 // every chunk in place to its peaks (order kept), counting them per event.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_peaks(Geom g, Work w, ScanArgs a)
+__global__ void __launch_bounds__(256) k_peaks(Geom g, Work w, FillCfg c, ScanArgs a, uint32_t peaks_only)
 {
     grid_dep_wait();
     __shared__ uint32_t s_wsum[40];
@@ -1364,9 +1586,29 @@ __global__ void __launch_bounds__(256) k_peaks(Geom g, Work w, ScanArgs a)
             if (k < d.y && d.x + k < a.entries_cap) {
                 en = a.entries[d.x + k];
                 const uint32_t s = en.x / sl, rem = en.x - s * sl, i = rem / g.nb, j = rem - i * g.nb;
-                const uint32_t *row = w.M + (size_t)en.y * w.n_cells + (size_t)(s * g.na + i) * g.nb;
-                has = is_peak_l2(row, i > 0 ? row - g.nb : nullptr, i + 1 < g.na ? row + g.nb : nullptr, j, g.nb,
-                                 en.z) ? 1u : 0u;
+                if (!peaks_only) {
+                    const uint32_t *row = w.M + (size_t)en.y * w.n_cells + (size_t)(s * g.na + i) * g.nb;
+                    has = is_peak_l2(row, i > 0 ? row - g.nb : nullptr, i + 1 < g.na ? row + g.nb : nullptr, j,
+                                     g.nb, en.z) ? 1u : 0u;
+                } else {
+                    // the rows above / below from the edge rows of the neighbouring passes
+                    const uint32_t u = en.y * g.n_slices + s;
+                    const bool u16 = (__ldg(&w.slice_off[u + 1]) - __ldg(&w.slice_off[u])) < 65536u;
+                    const uint32_t rpass = u16 ? c.W : c.W / 2, pass = i / rpass;
+                    const uint32_t *eu = w.edge + (size_t)u * w.edge_pass * 2 * g.nb;
+                    const uint32_t *up = (en.w & EDGE_UP) ? eu + ((size_t)(pass - 1) * 2 + 1) * g.nb : nullptr;
+                    const uint32_t *dn = (en.w & EDGE_DN) ? eu + ((size_t)(pass + 1) * 2) * g.nb : nullptr;
+                    const bool hl = j > 0, hr = j + 1 < g.nb;
+                    const uint32_t v = en.z;
+                    bool ok = true;
+                    if (up)
+                        ok = (!hl || v > __ldcg(up + j - 1)) && v > __ldcg(up + j) && (!hr || v > __ldcg(up + j + 1));
+                    if (dn)
+                        ok = ok && (!hl || v >= __ldcg(dn + j - 1)) && v >= __ldcg(dn + j) &&
+                             (!hr || v >= __ldcg(dn + j + 1));
+                    has = ok ? 1u : 0u;
+                    en.w = 0u;
+                }
             }
             // stable compaction: every read of this round happens before the
             // barrier, every write after, and no write passes its own read
@@ -1737,9 +1979,20 @@ cudaError_t fill_ws_occupancy(const FillCfg &c, const ScanArgs &a, int *blocks_p
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fill_ws, kWsThreads, smem);
 }
 
-cudaError_t launch_peaks(const Geom &g, const Work &w, const ScanArgs &a, uint32_t grid, cudaStream_t st)
+cudaError_t launch_peaks(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
+                         bool peaks_only, cudaStream_t st)
 {
-    return launch_pdl(k_peaks, grid, 256, 0, st, g, w, a);
+    return launch_pdl(k_peaks, grid, 256, 0, st, g, w, c, a, peaks_only ? 1u : 0u);
+}
+
+cudaError_t launch_fill_peaks(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
+                              cudaStream_t st)
+{
+    const size_t smem = fill_scan_smem_bytes(c, a, g.nb);
+    cudaError_t e = allow_smem((const void *)k_fill_peaks, smem);
+    if (e != cudaSuccess)
+        return e;
+    return launch_pdl(k_fill_peaks, grid, c.threads, smem, st, g, w, c, a);
 }
 
 cudaError_t fill_scan_occupancy(const FillCfg &c, const ScanArgs &a, uint32_t nb, int *blocks_per_sm)

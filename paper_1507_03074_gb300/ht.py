@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libht_gb300.so")
 
 HT_OK, HT_PENDING, HT_TRUNCATED = 0, 1, 2
 HT_E_INVAL, HT_E_NOMEM, HT_E_CUDA, HT_E_BUSY, HT_E_TIMEOUT, HT_E_STATE = -1, -2, -3, -4, -5, -6
-HT_MEM_HOST, HT_MEM_DEVICE, HT_ACCUMULATE, HT_FILL_NAIVE = 0, 1, 2, 4
+HT_MEM_HOST, HT_MEM_DEVICE, HT_ACCUMULATE, HT_FILL_NAIVE, HT_PEAKS_ONLY = 0, 1, 2, 4, 8
 STATUS_NAMES = {0: "HT_OK", 1: "HT_PENDING", 2: "HT_TRUNCATED", -1: "HT_E_INVAL", -2: "HT_E_NOMEM",
                 -3: "HT_E_CUDA", -4: "HT_E_BUSY", -5: "HT_E_TIMEOUT", -6: "HT_E_STATE"}
 
@@ -314,14 +314,15 @@ class Context:
         return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
                 for i in range(min(n.value, 16))}
 
-    def fill(self, x, y, z, accumulate: bool = False, naive: bool = False, stream=None):
+    def fill(self, x, y, z, accumulate: bool = False, naive: bool = False, peaks_only: bool = False, stream=None):
         n = int(x.numel() if _is_torch(x) else np.asarray(x).size)
         px, mx, kx = _ptr_and_mem(x, np.float32)
         py, my, ky = _ptr_and_mem(y, np.float32)
         pz, mz, kz = _ptr_and_mem(z, np.float32)
         if not (mx == my == mz):
             raise ValueError("x, y, z must all be host or all be device arrays")
-        flags = mx | (HT_ACCUMULATE if accumulate else 0) | (HT_FILL_NAIVE if naive else 0)
+        flags = (mx | (HT_ACCUMULATE if accumulate else 0) | (HT_FILL_NAIVE if naive else 0) |
+                 (HT_PEAKS_ONLY if peaks_only else 0))
         check(lib().ht_fill(self._h, px, py, pz, n, flags, _stream_ptr(stream)))
         self._keep = (kx, ky, kz)
 

@@ -460,3 +460,58 @@ def test_autotune_keeps_results(ht, paper_ref):
         ctx.fill(ev.x[:100], ev.y[:100], ev.z[:100], accumulate=True)
         with pytest.raises(ht.HTError):
             ctx.autotune()                        # last fill accumulated
+
+
+# ---------------------------------------------------------------------------
+# Peaks-only fills: M_H never written, the same peaks
+# ---------------------------------------------------------------------------
+
+PEAKS_ONLY_TUNINGS = [dict(), dict(fill_rows=4, fill_threads=256), dict(fill_rows=2, fill_threads=256),
+                      dict(fill_rows=64, fill_threads=1024)]
+
+
+@pytest.mark.parametrize("tuning", PEAKS_ONLY_TUNINGS, ids=[str(t) for t in PEAKS_ONLY_TUNINGS])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_peaks_only_matches_oracle(ht, case, tuning):
+    name, bins, rng, T, (x, y, z) = case
+    b, r = ht.Binning(*bins), ht.Ranges(**rng)
+    M_ref, _ = oracle.fill(_ob(b), _orr(r), x, y, z)
+    pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, T)
+    with ht.Context(b, r, threshold=T, max_hits=max(len(x), 1)) as ctx:
+        ctx.set_tuning(**tuning)
+        ctx.set_matrix(np.full(b.shape(), 7, np.uint32))      # a marker M_H must keep
+        ctx.fill(x, y, z, peaks_only=True)
+        pk, n = ctx.find_maxima(capacity=1 << 20)
+        assert n == n_ref
+        assert_peaks_equal(pk, pk_ref)
+        assert np.all(ctx.matrix() == 7)
+        # a normal fill afterwards writes M_H again
+        ctx.fill(x, y, z)
+        assert np.array_equal(ctx.matrix(), M_ref)
+
+
+def test_peaks_only_low_threshold_and_u32(ht, paper_ref):
+    ev, M_ref = paper_ref[0], paper_ref[1]
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    for T in (3, 5):          # passes with more cells >= T than the lists hold
+        pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, T)
+        with ht.Context(b, r, threshold=T, max_hits=6000) as ctx:
+            ctx.fill(ev.x, ev.y, ev.z, peaks_only=True)
+            pk, n = ctx.find_maxima(capacity=1 << 20)
+        assert n == n_ref, (T, n, n_ref)
+        assert_peaks_equal(pk, pk_ref)
+    b = ht.Binning(1, 1, 64, 96)    # u32 tiles (half-height passes)
+    x, y, z = random_hits(70000, 9, rmax=400.0)
+    x[:35000], y[:35000] = np.float32(300.0), np.float32(250.0)
+    M2, _ = oracle.fill(_ob(b), _orr(r), x, y, z)
+    for tun in (dict(), dict(fill_rows=2, fill_threads=256)):
+        pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M2, 3)
+        with ht.Context(b, r, threshold=3, max_hits=x.size) as ctx:
+            ctx.set_tuning(**tun)
+            ctx.fill(x, y, z, peaks_only=True)
+            pk, n = ctx.find_maxima(capacity=1 << 20)
+        assert n == n_ref
+        assert_peaks_equal(pk, pk_ref)
+    with ht.Context(b, r, threshold=3, max_hits=x.size) as ctx:
+        with pytest.raises(ht.HTError):
+            ctx.fill(x, y, z, peaks_only=True, accumulate=True)
