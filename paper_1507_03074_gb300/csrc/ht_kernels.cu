@@ -254,32 +254,9 @@ __device__ __forceinline__ uint32_t row_hash(uint32_t r)
     return (r * 0x9E3779B9u) >> 27;  // 5 bits
 }
 
-template <bool U16>
-__device__ __forceinline__ void vote_rows(const Geom &g, uint32_t *tile, const float4 *hs, const float *beta,
-                                          uint32_t nc, uint32_t r, uint32_t i, uint32_t hl, uint32_t hstride,
-                                          uint32_t pitch)
-{
-    const float twoA = __fmul_rn(2.0f, a_centre(g, i));
-    const uint32_t rowbase = r * pitch;
-    const uint32_t sw = U16 ? (row_hash(r) & 0x1Eu) : (row_hash(r) & 0x1Cu);
-    const float b_lo = beta[0], b_hi = beta[g.nb];   // the in-range test of every vote
-#pragma unroll 4
-    for (uint32_t h = hl; h < nc; h += hstride) {
-        const float4 hv = hs[h];
-        const int j = vote_bin_tab(g, beta, b_lo, b_hi, twoA, hv.x, hv.y, hv.z);
-        if (j >= 0) {
-            if (U16) {
-                const uint32_t word = rowbase + ((uint32_t(j) >> 1) ^ sw);
-                atomicAdd(&tile[word], 1u << ((uint32_t(j) & 1u) << 4));
-            } else {
-                atomicAdd(&tile[rowbase + (uint32_t(j) ^ sw)], 1u);
-            }
-        }
-    }
-}
-
-// Cells >= T found while flushing: hot[] marks their rows (bit r of word
-// r / 32), cand[] lists them as r * n_b + j (up to cap; *n counts them all).
+// Cells >= T of one pass: hot[] marks their rows (bit r of word r / 32),
+// cand[] lists them as r * n_b + j (up to cap; *n counts them all), candv[]
+// holds their votes where the lister knows them.
 struct FlushList {
     uint32_t *hot;
     uint32_t *cand;     // r * n_b + j
@@ -287,6 +264,63 @@ struct FlushList {
     uint32_t *n;
     uint32_t cap;
 };
+
+// Votes of tile cell (r, j) (u16 or u32 counters, row swizzle as vote_rows).
+__device__ __forceinline__ uint32_t tile_cell(const uint32_t *tile, uint32_t pitch, bool u16, uint32_t r, uint32_t j)
+{
+    if (u16)
+        return (tile[r * pitch + ((j >> 1) ^ (row_hash(r) & 0x1Eu))] >> ((j & 1u) << 4)) & 0xffffu;
+    return tile[r * pitch + (j ^ (row_hash(r) & 0x1Cu))];
+}
+
+// A cell of row r that just reached T: mark the row, list the cell.
+__device__ __forceinline__ void note_candidate(const FlushList &L, uint32_t r, uint32_t key)
+{
+    atomicOr(&L.hot[r >> 5], 1u << (r & 31u));
+    const uint32_t p = atomicAdd(L.n, 1u);
+    if (p < L.cap)
+        L.cand[p] = key;
+}
+
+// Votes of hits hs[hl], hs[hl + hstride], .. < nc into tile row r (A bin i).
+// With LIST, a vote that lifts its cell from T - 1 to T lists the cell
+// (note_candidate): votes are +1 increments and T >= 1 (the context
+// rejects T = 0), so every cell >= T is listed exactly once.
+template <bool U16, bool LIST = false>
+__device__ __forceinline__ void vote_rows(const Geom &g, uint32_t *tile, const float4 *hs, const float *beta,
+                                          uint32_t nc, uint32_t r, uint32_t i, uint32_t hl, uint32_t hstride,
+                                          uint32_t pitch, const FlushList &L = FlushList{})
+{
+    const float twoA = __fmul_rn(2.0f, a_centre(g, i));
+    const uint32_t rowbase = r * pitch;
+    const uint32_t sw = U16 ? (row_hash(r) & 0x1Eu) : (row_hash(r) & 0x1Cu);
+    const float b_lo = beta[0], b_hi = beta[g.nb];   // the in-range test of every vote
+    const uint32_t tm1 = g.threshold - 1u;
+#pragma unroll 4
+    for (uint32_t h = hl; h < nc; h += hstride) {
+        const float4 hv = hs[h];
+        const int j = vote_bin_tab(g, beta, b_lo, b_hi, twoA, hv.x, hv.y, hv.z);
+        if (j >= 0) {
+            if (U16) {
+                const uint32_t word = rowbase + ((uint32_t(j) >> 1) ^ sw);
+                const uint32_t sh = (uint32_t(j) & 1u) << 4;
+                if (LIST) {
+                    if (((atomicAdd(&tile[word], 1u << sh) >> sh) & 0xffffu) == tm1)
+                        note_candidate(L, r, r * g.nb + uint32_t(j));
+                } else {
+                    atomicAdd(&tile[word], 1u << sh);
+                }
+            } else {
+                if (LIST) {
+                    if (atomicAdd(&tile[rowbase + (uint32_t(j) ^ sw)], 1u) == tm1)
+                        note_candidate(L, r, r * g.nb + uint32_t(j));
+                } else {
+                    atomicAdd(&tile[rowbase + (uint32_t(j) ^ sw)], 1u);
+                }
+            }
+        }
+    }
+}
 
 template <bool LIST>
 __device__ __forceinline__ void list_cells(const Geom &g, const FlushList &L, uint32_t r, uint32_t j0,
@@ -410,6 +444,48 @@ __device__ __forceinline__ uint32_t stage_hits(const Work &w, float4 *hs, uint32
     pos += n;
     G::sync();
     return n;
+}
+
+// The votes of one strip pass: tile rows 0 .. pr - 1 are A bins i - r ..,
+// from the hits of list entries l0 .. l1 of unit es.  Hits are staged HC at
+// a time; when a unit's hits fit they stay staged for its later passes
+// (cached_es / cached_n).  SYNC: a cached pass starts with a group barrier
+// (the previous pass's readers of the tile are done); without it the caller
+// orders the tile by other means.  All threads of the group call it.
+template <class G, bool SYNC, bool LIST>
+__device__ __forceinline__ void vote_pass(const Geom &g, const Work &w, uint32_t *tile, float4 *hs, const float *beta,
+                                          uint32_t HC, uint64_t es, uint32_t l0, uint32_t l1, uint64_t &cached_es,
+                                          uint32_t &cached_n, bool u16, uint32_t r, uint32_t pr, uint32_t i,
+                                          uint32_t hl, uint32_t hstride, uint32_t pitch, const FlushList &L)
+{
+    if (cached_es == es) {
+        if (SYNC)
+            G::sync();
+        if (r < pr) {
+            if (u16)
+                vote_rows<true, LIST>(g, tile, hs, beta, cached_n, r, i, hl, hstride, pitch, L);
+            else
+                vote_rows<false, LIST>(g, tile, hs, beta, cached_n, r, i, hl, hstride, pitch, L);
+        }
+        return;
+    }
+    cached_es = ~0ull;   // hs is about to be overwritten
+    uint32_t pos = l0;
+    bool first = true;
+    while (first || pos < l1) {
+        const uint32_t nsel = stage_hits<G>(w, hs, HC, pos, l1);
+        if (first && pos >= l1) {
+            cached_es = es;   // the whole list fits: keep it
+            cached_n = nsel;
+        }
+        first = false;
+        if (r < pr) {
+            if (u16)
+                vote_rows<true, LIST>(g, tile, hs, beta, nsel, r, i, hl, hstride, pitch, L);
+            else
+                vote_rows<false, LIST>(g, tile, hs, beta, nsel, r, i, hl, hstride, pitch, L);
+        }
+    }
 }
 
 // The work items [it0, it1) of CTA `cta` of `grid`: the (event, slice,
@@ -549,33 +625,8 @@ __global__ void __launch_bounds__(1024) k_fill_priv(Geom g, Work w, FillCfg c)
         for (uint32_t p0 = 0; p0 < rows; p0 += rpass) {
             const uint32_t pr = min(rpass, rows - p0);
             const uint32_t i = i0 + p0 + r;
-            if (cached_es == es) {
-                __syncthreads();
-                if (r < pr) {
-                    if (u16)
-                        vote_rows<true>(g, tile, hs, beta,cached_n, r, i, hl, hstride, pitch);
-                    else
-                        vote_rows<false>(g, tile, hs, beta,cached_n, r, i, hl, hstride, pitch);
-                }
-            } else {
-                cached_es = ~0ull;       // hs is about to be overwritten
-                uint32_t pos = l0;
-                bool first = true;
-                while (first || pos < l1) {
-                    const uint32_t nsel = stage_hits(w, hs, c.HC, pos, l1);
-                    if (first && pos >= l1) {
-                        cached_es = es;   // the whole selection fits: keep it
-                        cached_n = nsel;
-                    }
-                    first = false;
-                    if (r < pr) {
-                        if (u16)
-                            vote_rows<true>(g, tile, hs, beta,nsel, r, i, hl, hstride, pitch);
-                        else
-                            vote_rows<false>(g, tile, hs, beta,nsel, r, i, hl, hstride, pitch);
-                    }
-                }
-            }
+            vote_pass<BlockGroup, true, false>(g, w, tile, hs, beta, c.HC, es, l0, l1, cached_es, cached_n, u16, r, pr,
+                                               i, hl, hstride, pitch, FlushList{});
             __syncthreads();
             uint32_t *dst = Mrow + (size_t)p0 * g.nb;
             if (c.accumulate) {
@@ -1025,6 +1076,24 @@ __device__ __forceinline__ void emit_pass(const Geom &g, const Work &w, const Sc
     }
 }
 
+// Rank-sort the n_c (<= kFusedCand) distinct keys r * n_b + j of cand into
+// srt, with their votes read from the tile into srtv.  All threads of the
+// group call it; the caller synchronises before srt / srtv are read.
+template <class G, bool U16>
+__device__ __forceinline__ void sort_tile_candidates(const Geom &g, const uint32_t *tile, uint32_t pitch,
+                                                     const uint32_t *cand, uint32_t n_c, uint32_t *srt, uint32_t *srtv)
+{
+    for (uint32_t k = G::rank(); k < n_c; k += G::size()) {
+        const uint32_t key = cand[k];
+        uint32_t rank = 0;
+        for (uint32_t m = 0; m < n_c; ++m)
+            rank += cand[m] < key;
+        const uint32_t rr = key / g.nb;
+        srt[rank] = key;
+        srtv[rank] = tile_cell(tile, pitch, U16, rr, key - rr * g.nb);
+    }
+}
+
 // Write one pass from the tile to M_H, clear the tile, and emit its
 // candidates (emit_pass).  empty_bar: arrived on once the tile is clear
 // (the warp-specialised fill), or null.  All threads of the group call it.
@@ -1119,33 +1188,8 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
             const uint32_t iA = i0 + p0;
             // ---- vote -------------------------------------------------------
             const uint32_t i = iA + r;
-            if (cached_es == es) {
-                __syncthreads();
-                if (r < pr) {
-                    if (u16)
-                        vote_rows<true>(g, tile, hs, beta, cached_n, r, i, hl, hstride, pitch);
-                    else
-                        vote_rows<false>(g, tile, hs, beta, cached_n, r, i, hl, hstride, pitch);
-                }
-            } else {
-                cached_es = ~0ull;
-                uint32_t pos = l0;
-                bool first = true;
-                while (first || pos < l1) {
-                    const uint32_t nsel = stage_hits(w, hs, c.HC, pos, l1);
-                    if (first && pos >= l1) {
-                        cached_es = es;
-                        cached_n = nsel;
-                    }
-                    first = false;
-                    if (r < pr) {
-                        if (u16)
-                            vote_rows<true>(g, tile, hs, beta, nsel, r, i, hl, hstride, pitch);
-                        else
-                            vote_rows<false>(g, tile, hs, beta, nsel, r, i, hl, hstride, pitch);
-                    }
-                }
-            }
+            vote_pass<BlockGroup, true, false>(g, w, tile, hs, beta, c.HC, es, l0, l1, cached_es, cached_n, u16, r, pr,
+                                               i, hl, hstride, pitch, FlushList{});
             // ---- write the pass, clear the tile, emit its candidates --------
             if (u16)
                 flush_emit_pass<BlockGroup, true>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, pitch,
@@ -1176,22 +1220,15 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
 // ---------------------------------------------------------------------------
 // k_fill_peaks: the fused fill without M_H in HBM (peaks-only fills).
 //
-// The passes are voted as in k_fill_scan, but the tile is not written out:
-// its cells >= T are tested at once against the neighbours the tile holds,
-// and the pass's first and last rows go to a small edge buffer.  A cell on
-// the first (last) row of its pass whose row above (below) belongs to
-// another pass is emitted with a flag; k_peaks finishes its test from the
-// edge rows.  The output is the same ordered peak list; M_H is left as it
-// was.
+// The passes are voted as in k_fill_scan, but the tile is not written out.
+// The votes themselves list the cells that reach T (vote_rows with LIST),
+// so no pass scans its tile for candidates: the listed cells are tested at
+// once against the neighbours the tile holds, and the pass's first and last
+// rows go to a small edge buffer.  A cell on the first (last) row of its
+// pass whose row above (below) belongs to another pass is emitted with a
+// flag; k_peaks finishes its test from the edge rows.  The output is the
+// same ordered peak list; M_H is left as it was.
 // ---------------------------------------------------------------------------
-
-// Votes of cell (r, j) of a tile (u16 or u32 counters, row swizzle).
-__device__ __forceinline__ uint32_t tile_cell(const uint32_t *tile, uint32_t pitch, bool u16, uint32_t r, uint32_t j)
-{
-    if (u16)
-        return (tile[r * pitch + ((j >> 1) ^ (row_hash(r) & 0x1Eu))] >> ((j & 1u) << 4)) & 0xffffu;
-    return tile[r * pitch + (j ^ (row_hash(r) & 0x1Cu))];
-}
 
 // Test of cell (r, j) with votes v against the neighbours inside the tile
 // rows 0 .. pr - 1 (rule of Sec. 3 as read: > neighbours before it, >= after).
@@ -1214,6 +1251,36 @@ __device__ __forceinline__ bool tile_peak(const uint32_t *tile, uint32_t pitch, 
     return true;
 }
 
+// Copy the first and last rows of a voted pass (tile rows 0 and rows - 1)
+// to edge[0, n_b) and edge[n_b, 2 n_b), 4 cells per thread and step when
+// n_b % 4 == 0.  The tile is left as it is.
+template <bool U16>
+__device__ __forceinline__ void edge_rows(const Geom &g, const uint32_t *tile, uint32_t rows, uint32_t pitch,
+                                          uint32_t *edge)
+{
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb;
+    if ((nb & 3u) == 0) {
+        const uint32_t q = nb >> 2;
+        for (uint32_t u = tid; u < 2 * q; u += bd) {
+            const uint32_t side = u >= q, c4 = u - side * q, r = side ? rows - 1 : 0;
+            uint4 v;
+            if (U16) {
+                const uint2 pr =
+                    *reinterpret_cast<const uint2 *>(&tile[r * pitch + ((2u * c4) ^ (row_hash(r) & 0x1Eu))]);
+                v = make_uint4(pr.x & 0xffffu, pr.x >> 16, pr.y & 0xffffu, pr.y >> 16);
+            } else {
+                v = *reinterpret_cast<const uint4 *>(&tile[r * pitch + ((4u * c4) ^ (row_hash(r) & 0x1Cu))]);
+            }
+            reinterpret_cast<uint4 *>(edge)[u] = v;
+        }
+    } else {
+        for (uint32_t u = tid; u < 2 * nb; u += bd) {
+            const uint32_t side = u >= nb, j = u - side * nb;
+            edge[u] = tile_cell(tile, pitch, U16, side ? rows - 1 : 0, j);
+        }
+    }
+}
+
 // Edge-flag bits of a peaks-only entry (in its .w): its test still needs
 // the row above / below, which lies in another pass.
 enum : uint32_t { EDGE_UP = 1u, EDGE_DN = 2u };
@@ -1228,10 +1295,12 @@ __global__ void __launch_bounds__(1024) k_fill_peaks(Geom g, Work w, FillCfg c, 
     float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
     float *beta = reinterpret_cast<float *>(hs + c.HC);
     uint32_t *lists = reinterpret_cast<uint32_t *>(beta + c.beta_words);
-    uint32_t *cand = lists, *candv = lists + kFusedCand, *srt = lists + 2 * kFusedCand, *srtv = lists + 3 * kFusedCand;
+    uint32_t *cand = lists, *srt = lists + 2 * kFusedCand, *srtv = lists + 3 * kFusedCand;
     __shared__ uint32_t s_hot[2], s_nc;
 
     const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb, T = g.threshold;
+    if (tid == 0)
+        s_hot[0] = s_hot[1] = s_nc = 0u;
     for (uint32_t k = tid; k < c.tile_words / 4; k += bd)
         sm4[16 + a.K + k] = make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t k = tid; k <= nb; k += bd)
@@ -1270,71 +1339,28 @@ __global__ void __launch_bounds__(1024) k_fill_peaks(Geom g, Work w, FillCfg c, 
             const uint32_t iA = i0 + p0;
             // ---- vote -------------------------------------------------------
             const uint32_t i = iA + r;
-            if (cached_es == es) {
-                __syncthreads();
-                if (r < pr) {
-                    if (u16)
-                        vote_rows<true>(g, tile, hs, beta, cached_n, r, i, hl, hstride, pitch);
-                    else
-                        vote_rows<false>(g, tile, hs, beta, cached_n, r, i, hl, hstride, pitch);
-                }
-            } else {
-                cached_es = ~0ull;
-                uint32_t pos = l0;
-                bool first = true;
-                while (first || pos < l1) {
-                    const uint32_t nsel = stage_hits(w, hs, c.HC, pos, l1);
-                    if (first && pos >= l1) {
-                        cached_es = es;
-                        cached_n = nsel;
-                    }
-                    first = false;
-                    if (r < pr) {
-                        if (u16)
-                            vote_rows<true>(g, tile, hs, beta, nsel, r, i, hl, hstride, pitch);
-                        else
-                            vote_rows<false>(g, tile, hs, beta, nsel, r, i, hl, hstride, pitch);
-                    }
-                }
-            }
-            if (tid == 0)
-                s_hot[0] = s_hot[1] = s_nc = 0u;
-            __syncthreads();
-            // ---- list the cells >= T; the edge rows to the edge buffer -------
-            const uint32_t pass = iA / rpass;
-            uint32_t *edge = w.edge + ((size_t)es * w.edge_pass + pass) * 2 * nb;
-            for (uint32_t u = tid; u < pr * nb; u += bd) {
-                const uint32_t rr = u / nb, j = u - rr * nb;
-                const uint32_t v = tile_cell(tile, pitch, u16, rr, j);
-                if (rr == 0)
-                    edge[j] = v;
-                if (rr == pr - 1)
-                    edge[nb + j] = v;
-                if (v >= T) {
-                    atomicOr(&s_hot[rr >> 5], 1u << (rr & 31u));
-                    const uint32_t q = atomicAdd(&s_nc, 1u);
-                    if (q < kFusedCand) {
-                        cand[q] = u;
-                        candv[q] = v;
-                    }
-                }
-            }
-            __syncthreads();
+            const FlushList L{s_hot, lists, nullptr, &s_nc, kFusedCand};
+            vote_pass<BlockGroup, true, true>(g, w, tile, hs, beta, c.HC, es, l0, l1, cached_es, cached_n, u16, r, pr,
+                                              i, hl, hstride, pitch, L);
+            __syncthreads();   // the pass's votes and their candidate list are complete
             const uint32_t n_c = s_nc;
             const uint64_t hotm = (uint64_t)s_hot[0] | ((uint64_t)s_hot[1] << 32);
+            // ---- the pass's first and last rows to the edge buffer ------------
+            const uint32_t pass = iA / rpass;
+            uint32_t *edge = w.edge + ((size_t)es * w.edge_pass + pass) * 2 * nb;
+            if (u16)
+                edge_rows<true>(g, tile, pr, pitch, edge);
+            else
+                edge_rows<false>(g, tile, pr, pitch, edge);
             const bool up_out = iA > 0, dn_out = iA + pr < g.na;   // neighbours in other passes
             // ---- test against the tile, emit peaks and flagged edge cells ----
             if (n_c) {
                 const bool fits = n_c <= kFusedCand;
                 if (fits) {
-                    for (uint32_t q = tid; q < n_c; q += bd) {
-                        const uint32_t key = cand[q];
-                        uint32_t rank = 0;
-                        for (uint32_t m = 0; m < n_c; ++m)
-                            rank += cand[m] < key;
-                        srt[rank] = key;
-                        srtv[rank] = candv[q];
-                    }
+                    if (u16)
+                        sort_tile_candidates<BlockGroup, true>(g, tile, pitch, cand, n_c, srt, srtv);
+                    else
+                        sort_tile_candidates<BlockGroup, false>(g, tile, pitch, cand, n_c, srt, srtv);
                     __syncthreads();
                 }
                 // rounds of rc cells: the sorted list, or every cell of the hot rows
@@ -1375,9 +1401,11 @@ __global__ void __launch_bounds__(1024) k_fill_peaks(Geom g, Work w, FillCfg c, 
                 }
             }
             __syncthreads();
-            // ---- clear the tile ------------------------------------------------
+            // ---- clear the tile and the lists for the next pass ----------------
             for (uint32_t q = tid; q < pr * pitch / 4; q += bd)
                 reinterpret_cast<uint4 *>(tile)[q] = make_uint4(0u, 0u, 0u, 0u);
+            if (tid == 0)
+                s_hot[0] = s_hot[1] = s_nc = 0u;   // the next votes start with a barrier
         }
     };
     ItemCursor cur(g, c, it0);
@@ -1491,32 +1519,8 @@ __global__ void __launch_bounds__(1024, 1) k_fill_ws(Geom g, Work w, FillCfg c, 
                     }
                 }
                 const uint32_t i = t.i0 + p0 + r;
-                if (cached_es == t.es) {
-                    if (r < pr) {
-                        if (t.u16)
-                            vote_rows<true>(g, tile, hs, beta, cached_n, r, i, hl, hstride, t.pitch);
-                        else
-                            vote_rows<false>(g, tile, hs, beta, cached_n, r, i, hl, hstride, t.pitch);
-                    }
-                } else {
-                    cached_es = ~0ull;
-                    uint32_t pos = t.l0;
-                    bool first = true;
-                    while (first || pos < t.l1) {
-                        const uint32_t nsel = stage_hits<VoteGroup>(w, hs, c.HC, pos, t.l1);
-                        if (first && pos >= t.l1) {
-                            cached_es = t.es;
-                            cached_n = nsel;
-                        }
-                        first = false;
-                        if (r < pr) {
-                            if (t.u16)
-                                vote_rows<true>(g, tile, hs, beta, nsel, r, i, hl, hstride, t.pitch);
-                            else
-                                vote_rows<false>(g, tile, hs, beta, nsel, r, i, hl, hstride, t.pitch);
-                        }
-                    }
-                }
+                vote_pass<VoteGroup, false, false>(g, w, tile, hs, beta, c.HC, t.es, t.l0, t.l1, cached_es, cached_n,
+                                                   t.u16, r, pr, i, hl, hstride, t.pitch, FlushList{});
                 mbar_arrive(&bars[b]);   // tile b holds pass p
             }
         }

@@ -490,6 +490,27 @@ def test_peaks_only_matches_oracle(ht, case, tuning):
         assert np.array_equal(ctx.matrix(), M_ref)
 
 
+@pytest.mark.parametrize("T", [1, 2, 1 << 20])
+def test_threshold_edges_both_fills(ht, T):
+    """T = 1 (every voted cell a candidate), T = 2 and a threshold no cell
+    reaches: the fused fill and the peaks-only fill both give the oracle's
+    peaks.  T = 0 is rejected by the context."""
+    name, bins, rng, _, (x, y, z) = CASES[2]
+    assert name == "ragged_nb"
+    b, r = ht.Binning(*bins), ht.Ranges(**rng)
+    M_ref, _ = oracle.fill(_ob(b), _orr(r), x, y, z)
+    pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, T)
+    for po in (False, True):
+        with ht.Context(b, r, threshold=T, max_hits=max(len(x), 1)) as ctx:
+            ctx.fill(x, y, z, peaks_only=po)
+            pk, n = ctx.find_maxima(capacity=1 << 20)
+        assert n == n_ref, (po, n, n_ref)
+        assert_peaks_equal(pk, pk_ref)
+    if T == 1:
+        with pytest.raises(ht.HTError):
+            ht.Context(b, r, threshold=0, max_hits=16)
+
+
 def test_peaks_only_low_threshold_and_u32(ht, paper_ref):
     ev, M_ref = paper_ref[0], paper_ref[1]
     b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
