@@ -326,6 +326,9 @@ def run_ours(args, rank, world):
         "roofline": roofline,
         "clocks": clk.summary(),
     }
+    if not args.no_extras and world == 1:
+        res["peaks_only"] = run_peaks_only(ctx, dev, out, cnt, cap, st, args.steps, args.warmup, peaks)
+        res["readout"] = run_readout(ctx, events, b, r)
     ctx.close()
     if not args.no_extras and world == 1:
         res["batched"] = run_batched()
@@ -333,6 +336,61 @@ def run_ours(args, rank, world):
     if not args.no_cpu_baseline and world == 1:
         res["cpu_baseline"] = cpu_baseline(budget_s=10.0)
     return res
+
+
+# ---------------------------------------------------------------------------
+# Track read-out of the pool events' peaks against the generator's truth
+# ---------------------------------------------------------------------------
+def run_readout(ctx, events, b, r):
+    from paper_1507_03074_gb300 import ht, readout
+
+    per = []
+    for e in events:
+        ctx.fill(e.x, e.y, e.z)
+        pk, _ = ctx.find_maxima(capacity=1 << 16)
+        per.append(readout.match(ht.track_params(b, r, pk, synth.B_FIELD_T), e, b, r))
+    out = readout.summarise(per)
+    out["note"] = ("peaks read out on the host in FP64 (rho, varphi, p_T) and matched to the generator's tracks "
+                   "(centre within 1.5 cells in A and B, theta bin within one); findable = centre in the A/B range")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Peaks-only fills (M_H not written), the same resident events
+# ---------------------------------------------------------------------------
+def run_peaks_only(ctx, dev, out, cnt, cap, st, K, W, peaks_ref):
+    import torch
+
+    def step(k):
+        ctx.fill(*dev[k % N_POOL], peaks_only=True, stream=st)
+        ctx.find_maxima(capacity=cap, out=out, count=cnt, stream=st)
+
+    same = True
+    for k in range(N_POOL):          # the peak counts of the plain path
+        step(k)
+        st.synchronize()
+        same = same and int(cnt.item()) == peaks_ref[k]
+    for k in range(W):
+        step(k)
+    st.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        ev0.record(st)
+        for k in range(K):
+            step(k)
+        ev1.record(st)
+    st.synchronize()
+    ms = ev0.elapsed_time(ev1) / K
+    ctx.profile(True)
+    for k in range(max(1, K // 4)):
+        step(k)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    return {"events_per_s": round(1e3 / ms, 1), "ms_per_step": round(ms, 4),
+            "kernels": {kn: {"launches": n, "avg_us": round(t / n * 1e3, 2)} for kn, (n, t) in prof.items() if n},
+            "same_peak_counts": bool(same),
+            "note": "HT_PEAKS_ONLY: peaks found in the fill's shared-memory tiles, M_H not written; "
+                    "device-resident events, K steps between two CUDA events"}
 
 
 # ---------------------------------------------------------------------------

@@ -380,6 +380,36 @@ ht_status ht_compute_edges(const ht_binning *binning, const ht_ranges *ranges, f
  * float B. */
 ht_status ht_compute_b_thresholds(const ht_binning *binning, const ht_ranges *ranges, float *beta);
 
+/* ------------------------------------------------------------------------ */
+/* Track read-out (host, FP64; no device needed).                            */
+/* ------------------------------------------------------------------------ */
+
+/* The track parameters of one peak (Sec. 2, Fig. 1).  (a, b) is the centre
+ * of the peak's (A, B) cell, a_min + (ia + 0.5) (a_max - a_min) / n_a and
+ * likewise for b, evaluated in double from the FP32 ranges; rho =
+ * sqrt(a^2 + b^2) is the circle radius and varphi = atan2(b, a) the azimuth
+ * of the circle centre (the paper's tan^-1(B/A), read over all four
+ * quadrants); pt = 0.3 * b_field * rho / 1000 is the transverse momentum
+ * (GeV) of a unit charge in a solenoid of b_field tesla (rho in mm).  theta
+ * is the centre of the peak's polar-angle bin, theta_min + (itheta + 0.5)
+ * (theta_max - theta_min) / n_theta, and eta = -ln tan(theta / 2); phi_c
+ * the centre of its azimuth bin. */
+typedef struct {
+    double a, b;             /* mm */
+    double rho;              /* mm */
+    double varphi;           /* rad, in [-pi, pi] */
+    double pt;               /* GeV */
+    double theta, eta, phi_c;
+    uint32_t votes, event;   /* copied from the peak */
+} ht_track;
+
+/* Read out n peaks (host memory) into out[0 .. n) (host memory, caller-
+ * owned).  HT_E_INVAL (nothing written) for a NULL pointer with n > 0, an
+ * invalid binning or ranges, b_field_t not finite and > 0, or a peak whose
+ * cell lies outside the binning. */
+ht_status ht_track_params(const ht_binning *binning, const ht_ranges *ranges, const ht_peak *peaks, uint32_t n,
+                          double b_field_t, ht_track *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -4,10 +4,11 @@ TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
 package.  The CUDA library never calls it and shares no code with it.
 
-The arithmetic lives in ``ht_oracle.c`` (scalar C, compiled with
-``-O2 -ffp-contract=off`` so every float operation is one IEEE binary32
-round-to-nearest operation in source order).  This module only compiles it,
-loads it with ctypes and marshals numpy arrays.
+The arithmetic of Steps 1 and 2 lives in ``ht_oracle.c`` (scalar C, compiled
+with ``-O2 -ffp-contract=off`` so every float operation is one IEEE binary32
+round-to-nearest operation in source order); this module compiles it, loads
+it with ctypes and marshals numpy arrays.  The track read-out of the peaks
+(``track_params``) is plain numpy in float64.
 
 Paper passages followed (arXiv 1507.03074):
   * Sec. 2: circles x^2 + y^2 - 2Ax - 2By = 0 through hit and interaction
@@ -16,6 +17,8 @@ Paper passages followed (arXiv 1507.03074):
   * Sec. 2: binning 4 x 16 x 1024 x 1024.
   * Sec. 3: "for each A, the corresponding B is evaluated"; each maxima
     thread compares one element with its neighbours.
+  * Sec. 2, Fig. 1: a peak's circle centre (A, B) gives the track's
+    rho = sqrt(A^2 + B^2) and varphi = tan^-1(B/A).
 """
 from __future__ import annotations
 
@@ -222,3 +225,37 @@ def bins_f32_vs_f64(b: Binning, r: Ranges, x, y, z, diff_cap: int = 4096):
         raise ValueError("bad binning")
     st = dict(zip(("candidates", "votes32", "votes64", "ndiff", "maxdist"), map(int, stats)))
     return st, diffs[: min(st["ndiff"], diff_cap)]
+
+
+def _snap_quarter(a: float) -> float:
+    """An angle within 1e-6 of a multiple of pi/4 (in units of pi/4) is that multiple."""
+    q = float(a) / (np.pi / 4.0)
+    m = round(q)
+    return m * (np.pi / 4.0) if abs(q - m) < 1e-6 else float(a)
+
+
+def track_params(b: Binning, r: Ranges, peaks, b_field_t: float = 2.0) -> dict:
+    """Track read-out of peaks in float64 (Sec. 2, Fig. 1).
+
+    The peak's cell centre (A, B) -- a_min + (ia + 1/2) (a_max - a_min) / n_a,
+    likewise for B -- is the circle centre: rho = sqrt(A^2 + B^2) is the
+    radius and varphi = tan^-1(B/A), taken over four quadrants (atan2), the
+    azimuth of the centre.  A unit charge in a solenoid of b_field_t tesla
+    has p_T = 0.3 b_field_t rho (GeV, T, m).  theta / phi_c are the centres of
+    the peak's polar / azimuth bins and eta = -ln tan(theta / 2).  Returns a
+    dict of float64 arrays.
+    """
+    r = Ranges(*(float(np.float32(v)) for v in (r.theta_min, r.theta_max, r.phi_min, r.phi_max, r.a_min, r.a_max,
+                                                  r.b_min, r.b_max)))   # the ranges are binary32 values
+    ia = np.asarray(peaks["ia"], np.float64)
+    ib = np.asarray(peaks["ib"], np.float64)
+    it = np.asarray(peaks["itheta"], np.float64)
+    ip = np.asarray(peaks["iphi"], np.float64)
+    a = r.a_min + (ia + 0.5) * ((r.a_max - r.a_min) / b.n_a)
+    bb = r.b_min + (ib + 0.5) * ((r.b_max - r.b_min) / b.n_b)
+    t0, t1 = _snap_quarter(r.theta_min), _snap_quarter(r.theta_max)
+    f0, f1 = _snap_quarter(r.phi_min), _snap_quarter(r.phi_max)
+    theta = t0 + (it + 0.5) * ((t1 - t0) / b.n_theta)
+    rho = np.sqrt(a * a + bb * bb)
+    return dict(a=a, b=bb, rho=rho, varphi=np.arctan2(bb, a), pt=0.3 * b_field_t * rho / 1000.0, theta=theta,
+                eta=-np.log(np.tan(0.5 * theta)), phi_c=f0 + (ip + 0.5) * ((f1 - f0) / b.n_phi))

@@ -70,6 +70,11 @@ PEAK_DTYPE = np.dtype([("itheta", np.uint32), ("iphi", np.uint32), ("ia", np.uin
                        ("b_c", np.float32), ("event", np.uint32)])
 assert PEAK_DTYPE.itemsize == 32
 
+TRACK_DTYPE = np.dtype([("a", np.float64), ("b", np.float64), ("rho", np.float64), ("varphi", np.float64),
+                        ("pt", np.float64), ("theta", np.float64), ("eta", np.float64), ("phi_c", np.float64),
+                        ("votes", np.uint32), ("event", np.uint32)])
+assert TRACK_DTYPE.itemsize == 72
+
 
 @dataclass(frozen=True)
 class Binning:
@@ -157,6 +162,7 @@ def lib():
                        ctypes.POINTER(ctypes.c_uint64)], I),
         "ht_poll": ([P, ctypes.c_uint64, P, U32, P, U32], I),
         "ht_server_get_stats": ([P, ctypes.POINTER(c_server_stats), I], I),
+        "ht_track_params": ([ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), P, U32, ctypes.c_double, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -193,6 +199,17 @@ def compute_b_thresholds(binning: Binning, ranges: Ranges = Ranges()):
     b, r = binning.c(), ranges.c()
     check(lib().ht_compute_b_thresholds(ctypes.byref(b), ctypes.byref(r), beta.ctypes.data_as(ctypes.c_void_p)))
     return beta
+
+
+def track_params(binning: Binning, ranges: Ranges, peaks, b_field_t: float = 2.0):
+    """ht_track_params: rho, varphi, p_T, theta, eta of each peak in FP64
+    (host only).  ``peaks`` is an array of PEAK_DTYPE; returns TRACK_DTYPE."""
+    pk = np.ascontiguousarray(peaks, dtype=PEAK_DTYPE)
+    out = np.zeros(pk.size, TRACK_DTYPE)
+    b, r = binning.c(), ranges.c()
+    check(lib().ht_track_params(ctypes.byref(b), ctypes.byref(r), pk.ctypes.data_as(ctypes.c_void_p), pk.size,
+                                float(b_field_t), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
 
 
 def find_maxima_noalloc(binning: Binning, ranges: Ranges, threshold: int, M, n_events: int, out, capacity: int,
