@@ -49,6 +49,7 @@ extern "C" {
 typedef struct ht_ctx ht_ctx;
 typedef struct ht_batch ht_batch;
 typedef struct ht_server ht_server;
+typedef struct ht_sectors ht_sectors;
 
 /* Sizes of M_H (Sec. 2: the four Hough dimensions, binned 4 x 16 x 1024 x
  * 1024 for (theta, phi, A, B)) and the slice admission half-windows.
@@ -379,6 +380,48 @@ ht_status ht_compute_edges(const ht_binning *binning, const ht_ranges *ranges, f
  * beta[1..n_b-1] that are <= B -- identical to the division rule for every
  * float B. */
 ht_status ht_compute_b_thresholds(const ht_binning *binning, const ht_ranges *ranges, float *beta);
+
+/* ------------------------------------------------------------------------ */
+/* Phi sectors (Sec. 4).                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Sec. 4 splits the transverse plane into phi sectors that are read out
+ * independently, runs one Hough transform with its own M_H(A, B, theta) per
+ * sector and merges the results.  Here the n_sectors sectors are contexts on
+ * the current device, each on its own stream: sector k owns phi bins
+ * [k m, (k + 1) m) of the binning (m = n_phi / n_sectors), with exactly the
+ * unsplit binning's edges for them, so its matrix equals those phi bins of
+ * the unsplit M_H and the merged peaks equal the unsplit peaks.
+ * Requirements: n_phi % n_sectors == 0 and win_phi == 0 (a phi window would
+ * need the neighbouring sector's hits); otherwise as ht_create.  max_hits
+ * bounds one fill.  Errors: HT_E_INVAL, HT_E_NOMEM, HT_E_CUDA. */
+ht_status ht_sectors_create(const ht_binning *binning, const ht_ranges *ranges, uint32_t threshold,
+                            uint32_t n_sectors, uint32_t max_hits, ht_sectors **out);
+
+/* Wait for the sectors' work and free everything.  NULL is a no-op. */
+ht_status ht_sectors_destroy(ht_sectors *sec);
+
+/* Step 1 for every sector: the hits (flags and memory as ht_fill; every
+ * sector receives all n_hits hits and keeps those in its phi range, as a
+ * sector's own read-out would deliver them) are voted by the n_sectors
+ * contexts concurrently, forked from and joined back into `stream` (NULL =
+ * the object's stream).  HT_MEM_HOST copies the hits once to pinned staging
+ * and one device copy before returning.  Flags: HT_MEM_DEVICE,
+ * HT_ACCUMULATE, HT_FILL_NAIVE, HT_PEAKS_ONLY.  Errors as ht_fill. */
+ht_status ht_sectors_fill(ht_sectors *sec, const float *x, const float *y, const float *z, uint32_t n_hits,
+                          uint32_t flags, void *stream);
+
+/* Step 2 for every sector, concurrently, then the merge: the sectors' peaks
+ * in the unsplit binning's numbering (iphi + k m) and ascending linear
+ * index of the unsplit M_H.  Memory, capacity and truncation as
+ * ht_find_maxima (HT_MEM_DEVICE: out and n_found on the device, enqueued
+ * only).  Errors as ht_find_maxima. */
+ht_status ht_sectors_find_maxima(ht_sectors *sec, ht_peak *out, uint32_t capacity, uint32_t *n_found,
+                                 uint32_t flags, void *stream);
+
+/* Copy sector k's matrix (n_theta x m x n_a x n_b cells) to host memory;
+ * waits for the object's work.  Errors: HT_E_INVAL, HT_E_CUDA. */
+ht_status ht_sectors_copy_matrix(ht_sectors *sec, uint32_t sector, uint32_t *dst, uint64_t n_cells);
 
 /* ------------------------------------------------------------------------ */
 /* Track read-out (host, FP64; no device needed).                            */

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libht_gb300.so")
 OBJDIR = os.path.join(HERE, "_build")
 SOURCES = ["ht_kernels.cu", "ht_engine.cu", "ht_api.cu", "ht_batch.cu", "ht_server.cu", "ht_noalloc.cu",
-           "ht_geom.cpp", "ht_readout.cpp"]
+           "ht_sectors.cu", "ht_geom.cpp", "ht_readout.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
               "-I", os.path.join(ROOT, "include")]

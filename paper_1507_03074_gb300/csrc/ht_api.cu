@@ -22,10 +22,6 @@ ht_status set_err(ht_status s, const std::string &msg)
 
 } // namespace
 
-namespace hte {
-// Shared with the batch and server objects.
-ht_status report(ht_status s, const std::string &msg) { return set_err(s, msg); }
-} // namespace hte
 
 struct ht_ctx {
     hte::Engine E;
@@ -41,6 +37,12 @@ struct ht_ctx {
     uint32_t acc_hits = 0;
     bool poisoned = false;
 };
+
+namespace hte {
+// Shared with the batch, server and sector objects.
+ht_status report(ht_status s, const std::string &msg) { return set_err(s, msg); }
+Engine &ctx_engine(ht_ctx *c) { return c->E; }
+} // namespace hte
 
 static ht_status cuda_fail(ht_ctx *c, cudaError_t e, const char *what)
 {

@@ -841,6 +841,12 @@ cudaError_t prof_read(Engine &E, ht_kernel_time *out, uint32_t cap, uint32_t *n)
     return cudaSuccess;
 }
 
+cudaError_t engine_set_phi_edges(Engine &E, const float *ep)
+{
+    std::copy(ep, ep + E.ep.size(), E.ep.begin());
+    return cudaMemcpy(E.d_edges + E.et.size(), E.ep.data(), E.ep.size() * 4, cudaMemcpyHostToDevice);
+}
+
 ht_status engine_ensure_edges(Engine &E, std::string *why)
 {
     // passes per unit at the smallest pass height (u32 tiles: W / 2 rows)

@@ -157,6 +157,12 @@ cudaError_t prof_read(Engine &E, ht_kernel_time *out, uint32_t cap, uint32_t *n)
 // device the first time).
 ht_status engine_ensure_edges(Engine &E, std::string *why);
 
+// Replace the phi edge table (n_phi + 1 pseudo-angles, host memory) on the
+// host and on the device (synchronous copy).  A sector context takes its
+// slice of the full circle's table, so that it bins hits exactly as the
+// unsplit matrix does.
+cudaError_t engine_set_phi_edges(Engine &E, const float *ep);
+
 // Device status word (bits of htk::ST_*).
 inline uint32_t *engine_status(Engine &E) { return E.d_ctr + htk::CTR_STATUS; }
 

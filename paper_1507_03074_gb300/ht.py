@@ -163,6 +163,11 @@ def lib():
         "ht_poll": ([P, ctypes.c_uint64, P, U32, P, U32], I),
         "ht_server_get_stats": ([P, ctypes.POINTER(c_server_stats), I], I),
         "ht_track_params": ([ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), P, U32, ctypes.c_double, P], I),
+        "ht_sectors_create": ([ctypes.POINTER(c_binning), ctypes.POINTER(c_ranges), U32, U32, U32, P], I),
+        "ht_sectors_destroy": ([P], I),
+        "ht_sectors_fill": ([P, P, P, P, U32, U32, P], I),
+        "ht_sectors_find_maxima": ([P, P, U32, P, U32, P], I),
+        "ht_sectors_copy_matrix": ([P, U32, P, U64], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -387,6 +392,70 @@ class Context:
         ep = np.zeros(self.binning.n_phi + 1, np.float32)
         check(lib().ht_get_edges(self._h, et.ctypes.data_as(ctypes.c_void_p), ep.ctypes.data_as(ctypes.c_void_p)))
         return et, ep
+
+
+class Sectors:
+    """Phi sectors (ht_sectors_*): one context per sector, forked and joined
+    on the device, peaks merged into the unsplit numbering and order."""
+
+    def __init__(self, binning: Binning, ranges: Ranges = Ranges(), threshold: int = 10, n_sectors: int = 4,
+                 max_hits: int = 65536):
+        self.binning, self.ranges, self.n_sectors = binning, ranges, n_sectors
+        self._h = ctypes.c_void_p()
+        b, r = binning.c(), ranges.c()
+        check(lib().ht_sectors_create(ctypes.byref(b), ctypes.byref(r), threshold, n_sectors, max_hits,
+                                      ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            lib().ht_sectors_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def fill(self, x, y, z, accumulate: bool = False, naive: bool = False, peaks_only: bool = False, stream=None):
+        n = int(x.numel() if _is_torch(x) else np.asarray(x).size)
+        px, mx, kx = _ptr_and_mem(x, np.float32)
+        py, my, ky = _ptr_and_mem(y, np.float32)
+        pz, mz, kz = _ptr_and_mem(z, np.float32)
+        if not (mx == my == mz):
+            raise ValueError("x, y, z must all be host or all be device arrays")
+        flags = (mx | (HT_ACCUMULATE if accumulate else 0) | (HT_FILL_NAIVE if naive else 0) |
+                 (HT_PEAKS_ONLY if peaks_only else 0))
+        check(lib().ht_sectors_fill(self._h, px, py, pz, n, flags, _stream_ptr(stream)))
+        self._keep = (kx, ky, kz)
+
+    def find_maxima(self, capacity: int = 1 << 16, out=None, count=None, stream=None):
+        """As Context.find_maxima, over all sectors (merged)."""
+        L = lib()
+        if out is not None:
+            if out.numel() * out.element_size() < capacity * 32:
+                raise ValueError("out is smaller than capacity * 32 bytes")
+            check(L.ht_sectors_find_maxima(self._h, ctypes.c_void_p(out.data_ptr()), capacity,
+                                           ctypes.c_void_p(count.data_ptr()), HT_MEM_DEVICE, _stream_ptr(stream)))
+            return None
+        buf = np.zeros(max(capacity, 1), PEAK_DTYPE)
+        n = ctypes.c_uint32()
+        check(L.ht_sectors_find_maxima(self._h, buf.ctypes.data_as(ctypes.c_void_p), capacity, ctypes.byref(n),
+                                       HT_MEM_HOST, _stream_ptr(stream)), ok=(HT_OK, HT_TRUNCATED))
+        return buf[: min(n.value, capacity)], int(n.value)
+
+    def matrix(self, sector: int) -> np.ndarray:
+        """Sector k's M_H: (n_theta, n_phi / n_sectors, n_a, n_b) uint32."""
+        b = self.binning
+        M = np.zeros((b.n_theta, b.n_phi // self.n_sectors, b.n_a, b.n_b), np.uint32)
+        check(lib().ht_sectors_copy_matrix(self._h, sector, M.ctypes.data_as(ctypes.c_void_p), M.size))
+        return M
 
 
 class Batch:
