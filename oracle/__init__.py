@@ -64,6 +64,8 @@ def _load():
         lib.ho_fill_slices.restype = ctypes.c_int64
         lib.ho_find_maxima.argtypes = [P, P, P, ctypes.c_uint32, P, P, ctypes.c_int64]
         lib.ho_find_maxima.restype = ctypes.c_int64
+        lib.ho_find_maxima4d.argtypes = [P, P, P, ctypes.c_uint32, P, P, ctypes.c_int64]
+        lib.ho_find_maxima4d.restype = ctypes.c_int64
         lib.ho_bins_f32_vs_f64.argtypes = [P, P, P, P, P, ctypes.c_int64, P, P, ctypes.c_int64]
         lib.ho_bins_f32_vs_f64.restype = ctypes.c_int
         _lib = lib
@@ -188,8 +190,11 @@ PEAK_DTYPE = np.dtype([("itheta", np.uint32), ("iphi", np.uint32), ("ia", np.uin
                        ("b_c", np.float32)])
 
 
-def find_maxima(b: Binning, r: Ranges, M: np.ndarray, threshold: int, cap: int | None = None):
-    """Step 2: peaks (structured array, ascending linear index) and total count."""
+def find_maxima(b: Binning, r: Ranges, M: np.ndarray, threshold: int, cap: int | None = None, dims: int = 2):
+    """Step 2: peaks (structured array, ascending linear index) and total count.
+    dims=2: the 8 (A, B) neighbours of the slice; dims=4: the up to 80
+    neighbours in (theta, phi, A, B), phi not wrapping."""
+    assert dims in (2, 4)
     lib = _load()
     M = np.ascontiguousarray(M, dtype=np.uint32)
     assert M.size == b.n_cells
@@ -199,7 +204,8 @@ def find_maxima(b: Binning, r: Ranges, M: np.ndarray, threshold: int, cap: int |
         cap = int(min(cap, int(M.sum(dtype=np.uint64)) // max(1, threshold) + 1))
     ids = np.zeros((cap, 5), np.uint32)
     cen = np.zeros((cap, 2), np.float32)
-    n = lib.ho_find_maxima(_p(_bins(b)), _p(_rng(r)), _p(M), threshold, _p(ids), _p(cen), cap)
+    fn = lib.ho_find_maxima if dims == 2 else lib.ho_find_maxima4d
+    n = fn(_p(_bins(b)), _p(_rng(r)), _p(M), threshold, _p(ids), _p(cen), cap)
     if n < 0:
         raise ValueError("bad binning")
     k = min(n, cap)

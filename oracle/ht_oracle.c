@@ -449,6 +449,65 @@ int64_t ho_find_maxima(const uint32_t *bins, const float *rng, const uint32_t *M
     return found;
 }
 
+/* The 4-D variant of the maxima rule: a cell c with v >= threshold is a peak
+ * iff it beats every one of its up to 80 neighbours in (theta, phi, A, B) --
+ * the cells whose four indices each differ from c's by at most one, other
+ * than c; indices outside the matrix are absent and phi does not wrap --
+ * strictly when the neighbour comes before c in linear order, else with
+ * >=.  Output as ho_find_maxima. */
+int64_t ho_find_maxima4d(const uint32_t *bins, const float *rng, const uint32_t *M,
+                         uint32_t threshold, uint32_t *ids, float *cen, int64_t cap)
+{
+    ho_geom g;
+    if (ho_geom_init(&g, bins, rng))
+        return -1;
+    int64_t found = 0;
+    for (long t = 0; t < (long)g.nt; ++t) {
+        for (long f = 0; f < (long)g.np; ++f) {
+            for (long i = 0; i < (long)g.na; ++i) {
+                for (long j = 0; j < (long)g.nb; ++j) {
+                    const uint64_t lin = (((uint64_t)t * g.np + f) * g.na + i) * g.nb + j;
+                    uint32_t v = M[lin];
+                    if (v < threshold)
+                        continue;
+                    int peak = 1;
+                    for (long dt = -1; dt <= 1 && peak; ++dt)
+                        for (long df = -1; df <= 1 && peak; ++df)
+                            for (long di = -1; di <= 1 && peak; ++di)
+                                for (long dj = -1; dj <= 1 && peak; ++dj) {
+                                    if (!dt && !df && !di && !dj)
+                                        continue;
+                                    long tt = t + dt, ff = f + df, ii = i + di, jj = j + dj;
+                                    if (tt < 0 || tt >= (long)g.nt || ff < 0 || ff >= (long)g.np || ii < 0 ||
+                                        ii >= (long)g.na || jj < 0 || jj >= (long)g.nb)
+                                        continue;
+                                    uint32_t w = M[(((uint64_t)tt * g.np + ff) * g.na + ii) * g.nb + jj];
+                                    int before = dt < 0 || (dt == 0 && (df < 0 || (df == 0 && (di < 0 ||
+                                                                                               (di == 0 && dj < 0)))));
+                                    if (before ? !(v > w) : !(v >= w))
+                                        peak = 0;
+                                }
+                    if (!peak)
+                        continue;
+                    if (found < cap) {
+                        uint32_t *o = ids + 5 * found;
+                        o[0] = (uint32_t)t;
+                        o[1] = (uint32_t)f;
+                        o[2] = (uint32_t)i;
+                        o[3] = (uint32_t)j;
+                        o[4] = v;
+                        cen[2 * found] = g.a_min + ((float)i + 0.5f) * g.da;
+                        cen[2 * found + 1] = g.b_min + ((float)j + 0.5f) * g.db;
+                    }
+                    ++found;
+                }
+            }
+        }
+    }
+    ho_geom_free(&g);
+    return found;
+}
+
 /* FP64 variant of the B-bin rule for every admitted (hit, slice, A bin):
  * counts the candidates, the votes cast in FP32, the votes cast in FP64, the
  * candidates whose bin (or in/out decision) differs, and the largest bin
