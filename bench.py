@@ -328,6 +328,7 @@ def run_ours(args, rank, world):
     }
     if not args.no_extras and world == 1:
         res["peaks_only"] = run_peaks_only(ctx, dev, out, cnt, cap, st, args.steps, args.warmup, peaks)
+        res["maxima_4d"] = run_maxima4d(ctx, dev, out, cnt, cap, st, args.steps, args.warmup)
         res["readout"] = run_readout(ctx, events, b, r)
         res["sectors"] = run_sectors(dev, b, r, max_hits, args.steps, args.warmup, peaks)
     ctx.close()
@@ -375,6 +376,44 @@ def run_sectors(dev, b, r, max_hits, K, W, peaks_ref, n_sectors=4):
             "same_peak_counts": bool(same),
             "note": "one M_H(A,B,theta) context per phi sector, forked onto its own stream and joined; "
                     "merged peaks identical to the unsplit ones (tested); device-resident events"}
+
+
+# ---------------------------------------------------------------------------
+# The 4-D (80-neighbour) maxima rule: the 2-D pipeline plus the k_peaks4d filter
+# ---------------------------------------------------------------------------
+def run_maxima4d(ctx, dev, out, cnt, cap, st, K, W):
+    import torch
+
+    def step(k):
+        ctx.fill(*dev[k % N_POOL], stream=st)
+        ctx.find_maxima(capacity=cap, out=out, count=cnt, stream=st, four_d=True)
+
+    n4 = []
+    for k in range(N_POOL):
+        step(k)
+        st.synchronize()
+        n4.append(int(cnt.item()))
+    for k in range(W):
+        step(k)
+    st.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        ev0.record(st)
+        for k in range(K):
+            step(k)
+        ev1.record(st)
+    st.synchronize()
+    ms = ev0.elapsed_time(ev1) / K
+    ctx.profile(True)
+    for k in range(max(1, K // 4)):
+        step(k)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    return {"events_per_s": round(1e3 / ms, 1), "ms_per_step": round(ms, 4),
+            "peaks_per_event": float(np.mean(n4)),
+            "kernels": {kn: {"launches": n, "avg_us": round(t / n * 1e3, 2)} for kn, (n, t) in prof.items() if n},
+            "note": "HT_MAXIMA_4D: 80 neighbours in (theta, phi, A, B); the 2-D peaks filtered against the "
+                    "adjacent slices by one CTA; device-resident events"}
 
 
 # ---------------------------------------------------------------------------

@@ -94,7 +94,8 @@ enum {
     HT_MEM_DEVICE = 1,       /* pointers are device memory; call is async */
     HT_ACCUMULATE = 2,       /* ht_fill: add to M_H instead of overwriting it */
     HT_FILL_NAIVE = 4,       /* ht_fill: clear + one global atomic per vote */
-    HT_PEAKS_ONLY = 8        /* ht_fill: find the peaks without writing M_H to device memory */
+    HT_PEAKS_ONLY = 8,       /* ht_fill: find the peaks without writing M_H to device memory */
+    HT_MAXIMA_4D = 16        /* ht_find_maxima: the 80-neighbour rule in (theta, phi, A, B) */
 };
 
 /* Thread-local text of the last failure (never NULL). */
@@ -130,12 +131,19 @@ ht_status ht_destroy(ht_ctx *ctx);
 ht_status ht_fill(ht_ctx *ctx, const float *x, const float *y, const float *z, uint32_t n_hits,
                   uint32_t flags, void *stream);
 
-/* Step 2 (Sec. 2, Sec. 3): threshold + local-maxima scan of M_H.
+/* Step 2 (Sec. 2, Sec. 3): threshold + local-maxima scan of M_H.  A cell
+ * with v >= threshold is a peak iff it is > each neighbour with a smaller
+ * linear index and >= each one with a larger index; the neighbours are its
+ * 8 cells in the (A, B) plane of its (theta, phi) slice, or with
+ * HT_MAXIMA_4D the up to 80 cells whose four indices each differ by at
+ * most one (phi does not wrap; not after an HT_PEAKS_ONLY fill, whose M_H
+ * is not in device memory; the first such call allocates a list buffer and
+ * waits for the device).
  * HT_MEM_HOST: blocks until done; writes min(total, capacity) peaks to out
  * and the total to *n_found; returns HT_TRUNCATED if total > capacity.
  * HT_MEM_DEVICE: out (capacity entries) and n_found are device pointers; the
  * call only enqueues; *n_found receives the total (may exceed capacity).
- * Errors: HT_E_INVAL, HT_E_CUDA, HT_E_TIMEOUT, HT_E_STATE. */
+ * Errors: HT_E_INVAL, HT_E_NOMEM, HT_E_CUDA, HT_E_TIMEOUT, HT_E_STATE. */
 ht_status ht_find_maxima(ht_ctx *ctx, ht_peak *out, uint32_t capacity, uint32_t *n_found,
                          uint32_t flags, void *stream);
 

@@ -35,6 +35,9 @@ struct ht_ctx {
     cudaEvent_t ev_in = nullptr;
     bool ev_in_pending = false;
     uint32_t acc_hits = 0;
+    bool last_peaks_only = false;  // the last fill left M_H as it was
+    htk::Peak *d_p2 = nullptr;     // the 2-D peak list of 4-D scans (E.scan.entries_cap entries)
+    uint32_t p2_cap = 0;
     bool poisoned = false;
 };
 
@@ -136,6 +139,7 @@ ht_status ht_destroy(ht_ctx *ctx)
     cudaFree(ctx->d_in);
     cudaFree(ctx->d_small);
     cudaFree(ctx->d_peaks);
+    cudaFree(ctx->d_p2);
     cudaFreeHost(ctx->h_in);
     cudaFreeHost(ctx->h_small);
     if (ctx->ev_in)
@@ -190,6 +194,7 @@ ht_status ht_fill(ht_ctx *ctx, const float *x, const float *y, const float *z, u
     }
     CK(hte::engine_fill(ctx->E, px, py, pz, nullptr, n_hits, 1, n_hits, flags & ~(uint32_t)HT_MEM_DEVICE, st));
     ctx->acc_hits = (uint32_t)acc;
+    ctx->last_peaks_only = (flags & HT_PEAKS_ONLY) != 0;
     return HT_OK;
 }
 
@@ -199,13 +204,31 @@ ht_status ht_find_maxima(ht_ctx *ctx, ht_peak *out, uint32_t capacity, uint32_t 
     ht_status s = check_ctx(ctx);
     if (s != HT_OK)
         return s;
-    if (flags & ~(uint32_t)HT_MEM_DEVICE)
+    if (flags & ~(uint32_t)(HT_MEM_DEVICE | HT_MAXIMA_4D))
         return set_err(HT_E_INVAL, "unknown flag");
     if (!n_found || (capacity && !out))
         return set_err(HT_E_INVAL, "out (capacity > 0) and n_found must not be NULL");
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    const bool four = (flags & HT_MAXIMA_4D) != 0;
+    if (four) {
+        if (ctx->last_peaks_only)
+            return set_err(HT_E_INVAL, "HT_MAXIMA_4D reads M_H, which a peaks-only fill does not write");
+        if (ctx->p2_cap < ctx->E.scan.entries_cap) {
+            CK(cudaStreamSynchronize(st));
+            cudaFree(ctx->d_p2);
+            ctx->d_p2 = nullptr;
+            ctx->p2_cap = 0;
+            CK(cudaMalloc(&ctx->d_p2, (size_t)ctx->E.scan.entries_cap * sizeof(htk::Peak)));
+            ctx->p2_cap = ctx->E.scan.entries_cap;
+        }
+    }
+    // the 2-D list's total goes to d_small[2] (d_small[0] holds the result's)
+    auto scan = [&](htk::Peak *dst, uint32_t cap, uint32_t *cnt) {
+        return four ? hte::engine_scan4d(ctx->E, ctx->d_p2, ctx->p2_cap, ctx->d_small + 2, dst, cap, cnt, st)
+                    : hte::engine_scan(ctx->E, 1, dst, cap, cnt, st);
+    };
     if (flags & HT_MEM_DEVICE) {
-        CK(hte::engine_scan(ctx->E, 1, reinterpret_cast<htk::Peak *>(out), capacity, n_found, st));
+        CK(scan(reinterpret_cast<htk::Peak *>(out), capacity, n_found));
         return HT_OK;
     }
     if (capacity > ctx->peaks_cap) {
@@ -216,7 +239,7 @@ ht_status ht_find_maxima(ht_ctx *ctx, ht_peak *out, uint32_t capacity, uint32_t 
         CK(cudaMalloc(&ctx->d_peaks, (size_t)capacity * sizeof(htk::Peak)));
         ctx->peaks_cap = capacity;
     }
-    CK(hte::engine_scan(ctx->E, 1, ctx->d_peaks, capacity, ctx->d_small, st));
+    CK(scan(ctx->d_peaks, capacity, ctx->d_small));
     CK(cudaMemcpyAsync(ctx->h_small, ctx->d_small, 4, cudaMemcpyDeviceToHost, st));
     s = read_status(ctx, st);   // synchronises the stream
     if (s != HT_OK)
@@ -274,6 +297,7 @@ ht_status ht_set_matrix(ht_ctx *ctx, const uint32_t *src, uint64_t n_cells, uint
     std::string why;
     if ((s = hte::engine_ensure_any_matrix(ctx->E, &why)) != HT_OK)
         return set_err(s, why);
+    ctx->last_peaks_only = false;
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
     const cudaMemcpyKind kind = (flags & HT_MEM_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaMemcpyAsync(ctx->E.d_M, src, n_cells * 4, kind, st));

@@ -18,7 +18,7 @@ static const uint32_t kFusedPeakBuf = 512;     // K of a fused-fill CTA (at leas
 
 const char *const kKernelNames[K_NKINDS] = {"k_bin", "k_scatter", "k_fill_priv", "k_fill_scan", "k_fill_ws",
                                              "k_fill_peaks", "k_peaks", "k_clear", "k_fill_naive", "k_scan",
-                                             "k_order"};
+                                             "k_order", "k_peaks4d"};
 
 // ---------------------------------------------------------------------------
 // Profiling
@@ -681,6 +681,21 @@ cudaError_t engine_scan(Engine &E, uint32_t n_events, htk::Peak *out, uint32_t c
     }
     ++E.launches;
     E.ctr_dirty = false;   // the order kernel's last CTA zeroes them
+    return e;
+}
+
+cudaError_t engine_scan4d(Engine &E, htk::Peak *p2, uint32_t p2_cap, uint32_t *p2_count, htk::Peak *out,
+                          uint32_t capacity, uint32_t *counts, cudaStream_t st)
+{
+    cudaError_t e = engine_scan(E, 1, p2, p2_cap, p2_count, st);
+    if (e != cudaSuccess)
+        return e;
+    {
+        ProfScope ps(E, K_PEAKS4D, st);
+        e = htk::launch_peaks4d(E.geom, E.d_M, p2, p2_count, p2_cap, out, capacity, counts,
+                                E.d_ctr + htk::CTR_STATUS, st);
+    }
+    ++E.launches;
     return e;
 }
 

@@ -30,7 +30,7 @@ struct Tuning {
 // stream around every launch (enabled by ht_profile).
 enum KernelKind {
     K_BIN, K_SCATTER, K_FILL_PRIV, K_FILL_SCAN, K_FILL_WS, K_FILL_PEAKS, K_PEAKS, K_CLEAR, K_FILL_NAIVE, K_SCAN,
-    K_ORDER, K_NKINDS
+    K_ORDER, K_PEAKS4D, K_NKINDS
 };
 extern const char *const kKernelNames[K_NKINDS];
 
@@ -162,6 +162,14 @@ ht_status engine_ensure_edges(Engine &E, std::string *why);
 // slice of the full circle's table, so that it bins hits exactly as the
 // unsplit matrix does.
 cudaError_t engine_set_phi_edges(Engine &E, const float *ep);
+
+// Step 2 with the 4-D neighbourhood for one event: the 2-D peaks into
+// p2 (p2_cap entries, total in *p2_count), then those that also beat their
+// neighbours in the adjacent (theta, phi) slices, in order, into out
+// (capacity entries, total in *counts).  p2_cap must be >= the engine's
+// entry bound (E.scan.entries_cap).
+cudaError_t engine_scan4d(Engine &E, htk::Peak *p2, uint32_t p2_cap, uint32_t *p2_count, htk::Peak *out,
+                          uint32_t capacity, uint32_t *counts, cudaStream_t st);
 
 // Device status word (bits of htk::ST_*).
 inline uint32_t *engine_status(Engine &E) { return E.d_ctr + htk::CTR_STATUS; }

@@ -124,6 +124,9 @@ enum ScanKind { SCAN_DIRECT = 0, SCAN_BULK = 1, SCAN_LDG = 2 };
 cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, int kind, cudaStream_t st);
 cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const OrderArgs &o,
                          cudaStream_t st);
+// The 4-D filter of a 2-D peak list (k_peaks4d, one CTA).
+cudaError_t launch_peaks4d(const Geom &g, const uint32_t *M, const Peak *in, const uint32_t *n_in, uint32_t cap_in,
+                           Peak *out, uint32_t cap_out, uint32_t *n_out, uint32_t *status, cudaStream_t st);
 cudaError_t scan_occupancy(int kind, size_t smem, int *blocks_per_sm);
 cudaError_t fill_occupancy(const FillCfg &c, int *blocks_per_sm);
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libht_gb300.so")
 
 HT_OK, HT_PENDING, HT_TRUNCATED = 0, 1, 2
 HT_E_INVAL, HT_E_NOMEM, HT_E_CUDA, HT_E_BUSY, HT_E_TIMEOUT, HT_E_STATE = -1, -2, -3, -4, -5, -6
-HT_MEM_HOST, HT_MEM_DEVICE, HT_ACCUMULATE, HT_FILL_NAIVE, HT_PEAKS_ONLY = 0, 1, 2, 4, 8
+HT_MEM_HOST, HT_MEM_DEVICE, HT_ACCUMULATE, HT_FILL_NAIVE, HT_PEAKS_ONLY, HT_MAXIMA_4D = 0, 1, 2, 4, 8, 16
 STATUS_NAMES = {0: "HT_OK", 1: "HT_PENDING", 2: "HT_TRUNCATED", -1: "HT_E_INVAL", -2: "HT_E_NOMEM",
                 -3: "HT_E_CUDA", -4: "HT_E_BUSY", -5: "HT_E_TIMEOUT", -6: "HT_E_STATE"}
 
@@ -348,21 +348,23 @@ class Context:
         check(lib().ht_fill(self._h, px, py, pz, n, flags, _stream_ptr(stream)))
         self._keep = (kx, ky, kz)
 
-    def find_maxima(self, capacity: int = 1 << 16, out=None, count=None, stream=None):
+    def find_maxima(self, capacity: int = 1 << 16, out=None, count=None, stream=None, four_d: bool = False):
         """Host mode (out is None): returns (peaks structured array, total).
         Device mode: ``out`` is a CUDA tensor of >= capacity*32 bytes and
-        ``count`` a CUDA int32 tensor; the call only enqueues."""
+        ``count`` a CUDA int32 tensor; the call only enqueues.  four_d: the
+        80-neighbour rule (HT_MAXIMA_4D)."""
         L = lib()
+        f4 = HT_MAXIMA_4D if four_d else 0
         if out is not None:
             if out.numel() * out.element_size() < capacity * 32:
                 raise ValueError("out is smaller than capacity * 32 bytes")
             check(L.ht_find_maxima(self._h, ctypes.c_void_p(out.data_ptr()), capacity,
-                                   ctypes.c_void_p(count.data_ptr()), HT_MEM_DEVICE, _stream_ptr(stream)))
+                                   ctypes.c_void_p(count.data_ptr()), HT_MEM_DEVICE | f4, _stream_ptr(stream)))
             return None
         buf = np.zeros(max(capacity, 1), PEAK_DTYPE)
         n = ctypes.c_uint32()
         check(L.ht_find_maxima(self._h, buf.ctypes.data_as(ctypes.c_void_p), capacity, ctypes.byref(n),
-                               HT_MEM_HOST, _stream_ptr(stream)), ok=(HT_OK, HT_TRUNCATED))
+                               HT_MEM_HOST | f4, _stream_ptr(stream)), ok=(HT_OK, HT_TRUNCATED))
         return buf[: min(n.value, capacity)].copy(), int(n.value)
 
     def sync(self, stream=None):
