@@ -232,9 +232,13 @@ ht_status ht_profile_read(ht_ctx *ctx, ht_kernel_time *out, uint32_t cap, uint32
  *                      full) and tests only those, so ht_find_maxima only
  *                      orders the peaks; 3: the same with two tiles per SM,
  *                      one voted into while the other is written
- *                      (warp-specialised, 1024 threads); 2: never (a full
- *                      scan in ht_find_maxima); 0: 1 when it fits (both
- *                      fused modes only for non-accumulating, non-naive fills)
+ *                      (warp-specialised, 1024 threads); 4: as 1, but each
+ *                      tile leaves through two u32 staging buffers in shared
+ *                      memory and bulk async copies (cp.async.bulk), so the
+ *                      stores drain while the next votes run (1024 threads
+ *                      by default; n_b a multiple of 4); 2: never (a full
+ *                      scan in ht_find_maxima); 0: 1 when it fits (the fused
+ *                      modes only for non-accumulating, non-naive fills)
  * ht_set_tuning waits for the device, re-derives the shapes and returns
  * HT_E_INVAL for an impossible value; ht_get_tuning reports the shapes in
  * effect (0 fields filled in). */

@@ -275,6 +275,36 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
+// 1-D bulk copy this CTA's shared memory -> global, in the issuing thread's
+// current bulk async-group.  dst, src 16-byte aligned; bytes a multiple of
+// 16.  The source must have been written before a fence.proxy.async by the
+// writing threads and a barrier.
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Close the issuing thread's current bulk async-group.
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Wait until at most N of the issuing thread's bulk async-groups are still
+// reading their shared-memory sources (the writes may still be in flight).
+template <int N>
+__device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+// Wait until at most N of the issuing thread's bulk async-groups are
+// incomplete (their writes performed).
+template <int N>
+__device__ __forceinline__ void bulk_wait()
+{
+    asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // One arrival (release semantics, CTA scope) on a barrier initialised with
 // the number of arriving threads.
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)

@@ -124,8 +124,8 @@ ht_status engine_configure(Engine &E, std::string *why)
         *why = "fill_threads must be 256, 512 or 1024";
         return HT_E_INVAL;
     }
-    if (t.fused > 3) {
-        *why = "fused must be 0 (auto), 1 (on), 2 (off) or 3 (warp-specialised)";
+    if (t.fused > 4) {
+        *why = "fused must be 0 (auto), 1 (on), 2 (off), 3 (warp-specialised) or 4 (bulk-copy stores)";
         return HT_E_INVAL;
     }
     f.HC = std::max(t.fill_HC ? t.fill_HC : 2048u, 2 * f.threads);   // hits staged per chunk
@@ -176,6 +176,23 @@ ht_status engine_configure(Engine &E, std::string *why)
         htk::ScanArgs tmp{};
         tmp.K = E.fused_K;
         htk::FillCfg ff = f;
+        const bool bulk = t.fused == 4;
+        if (bulk) {
+            // one CTA of 1024 threads per SM: the tile, two u32 staging
+            // buffers of W / 2 rows and as many staged hits as still fit
+            ff.bulk = 1;
+            ff.threads = t.fill_threads ? t.fill_threads : 1024;
+            ff.dyn = 1;
+            E.fused_K = std::max<uint32_t>(kFusedPeakBuf, ff.threads);
+            tmp.K = E.fused_K;
+            if (t.fill_HC) {
+                ff.HC = t.fill_HC;   // as asked (no two-blocks minimum here)
+            } else {
+                ff.HC = 2048;
+                while (ff.HC > 256 && htk::fill_scan_smem_bytes(ff, tmp, b.n_b) > kSmemMax)
+                    ff.HC -= 256;
+            }
+        }
         // two CTAs per SM if a staging size (a multiple of the block, at
         // least two blocks' worth) allows it, unless tuned explicitly
         int occ = 0;
@@ -189,10 +206,12 @@ ht_status engine_configure(Engine &E, std::string *why)
             return o;
         };
         occ = occupancy(ff);
-        while (!t.fill_HC && occ < 2 && ff.HC > 2 * ff.threads) {
+        while (!bulk && !t.fill_HC && occ < 2 && ff.HC > 2 * ff.threads) {
             ff.HC -= ff.threads;
             occ = occupancy(ff);
         }
+        if (bulk && ((b.n_b & 3u) || ff.threads % W || W < 2))
+            occ = 0;   // rows must start on 16 bytes; the block must cover whole rows
         E.fused_fill = ff;
         if (occ >= 1) {
             if (t.fill_blocks_per_sm)
@@ -228,7 +247,7 @@ ht_status engine_configure(Engine &E, std::string *why)
         return HT_E_INVAL;
     }
     E.use_ws = E.ws_ok;
-    if (t.fused == 1 && !E.fused_ok) {
+    if ((t.fused == 1 || t.fused == 4) && !E.fused_ok) {
         *why = "the fused fill does not fit this binning and tuning";
         return HT_E_INVAL;
     }
@@ -300,7 +319,8 @@ ht_status engine_configure(Engine &E, std::string *why)
     };
     if (E.fused_ok) {
         const uint64_t fused_rows = rows_per_cta(fused_grid);
-        seq = std::max(seq, chunks_for(fused_rows, g.nb, E.fused_K, htk::fused_round(f.threads, E.fused_K)));
+        seq = std::max(seq, chunks_for(fused_rows, g.nb, E.fused_K,
+                                       htk::fused_round(E.fused_fill.threads, E.fused_K)));
     }
     if (E.ws_ok) {
         const uint64_t ws_rows = rows_per_cta(ws_grid);
@@ -732,16 +752,18 @@ ht_status engine_autotune(Engine &E, uint32_t reps, cudaStream_t st, double *bes
     std::vector<Tuning> cands;
     const uint32_t rows_opts[] = {16, 32};
     const uint32_t thr_opts[] = {256, 512};
-    for (uint32_t fused = 1; fused <= 3; ++fused)
+    for (uint32_t fused = 1; fused <= 4; ++fused)
         for (uint32_t W : rows_opts)
             for (uint32_t th : thr_opts)
                 for (uint32_t kind = 1; kind <= (fused == 2 ? 2u : 1u); ++kind) {
                     if (fused == 3 && th != htk::kWsThreads / 2)
                         continue;                // one group size for the warp-specialised kernel
+                    if (fused == 4 && th != thr_opts[0])
+                        continue;                // the bulk-store kernel: its own block size (1024)
                     Tuning t = user;
                     t.fused = fused;
                     t.fill_W = W;
-                    t.fill_threads = th;
+                    t.fill_threads = fused == 4 ? 0u : th;
                     t.scan_kind = fused == 2 ? (kind == 1 ? 2u : 1u) : user.scan_kind;
                     cands.push_back(t);
                 }
@@ -834,7 +856,7 @@ void engine_get_tuning(const Engine &E, ht_tuning *t)
     t->scan_stage_bytes = E.scan.slot_words * 4;
     t->scan_slots = E.scan.S;
     t->scan_blocks_per_sm = E.num_sms ? E.scan_grid_max / (uint32_t)E.num_sms : 0;
-    t->fill_fused_scan = E.use_ws ? 3u : E.fused_ok ? 1u : 2u;
+    t->fill_fused_scan = E.use_ws ? 3u : E.fused_ok ? (E.fused_fill.bulk ? 4u : 1u) : 2u;
 }
 
 cudaError_t prof_read(Engine &E, ht_kernel_time *out, uint32_t cap, uint32_t *n)

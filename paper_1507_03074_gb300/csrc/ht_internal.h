@@ -23,7 +23,12 @@ struct FillCfg {
     uint32_t accumulate;  // add the tile to M_H instead of storing it
     uint32_t beta_words;  // shared-memory copy of the B-bin thresholds (n_b + 1, rounded to 4)
     uint32_t dyn;         // 1: the last dyn_items() items are handed out at run time (see below)
+    uint32_t bulk;        // fused fill: 1 = passes leave through u32 staging and bulk copies (k_fill_bulk)
 };
+
+// Shared-memory words of the fused fill's two u32 staging buffers (half a
+// u16 pass, W / 2 rows of n_b cells, each), or 0 without bulk copies.
+__host__ __device__ constexpr uint32_t staging_words(const FillCfg &c, uint32_t nb) { return c.bulk ? c.W * nb : 0u; }
 
 // The fills split the first items - dyn_items(items, grid) work items over
 // their CTAs by estimated cost, and hand the rest out one at a time to the

@@ -344,8 +344,9 @@ __device__ __forceinline__ void list_cells(const Geom &g, const FlushList &L, ui
         }
 }
 
-// Write the tile rows of one pass to M_H (dst = the pass's first row) and
-// clear them; with LIST, list the cells >= T; with accumulate, add to M_H.
+// Write tile rows r0 .. r0 + rows - 1 of one pass to dst (M_H, or a staging
+// buffer, from its first row on) and clear them; with LIST, list the cells
+// >= T (as pass rows r0 + r); with accumulate, add to M_H.
 // The tile keeps row r's logical word w at physical word w ^ sw(r) (sw even
 // in u16 mode, a multiple of 4 in u32 mode).  When n_b is a multiple of 4
 // each step moves 4 cells: consecutive threads write consecutive 16-byte
@@ -353,12 +354,13 @@ __device__ __forceinline__ void list_cells(const Geom &g, const FlushList &L, ui
 // contiguous bytes.
 template <bool U16, bool LIST, bool ACC, class G = BlockGroup>
 __device__ __forceinline__ void flush_tile(const Geom &g, uint32_t *tile, uint32_t *dst, uint32_t rows,
-                                           uint32_t pitch, const FlushList &L)
+                                           uint32_t pitch, const FlushList &L, uint32_t r0 = 0)
 {
     const uint32_t tid = G::rank(), bd = G::size(), nb = g.nb;
-    // one 16-byte unit (4 cells) of row r, column group c4: read + clear the
-    // tile words, write (or add to) M_H at o, list the cells >= T
-    auto unit = [&](uint32_t r, uint32_t c4, uint4 *o) {
+    // one 16-byte unit (4 cells) of row r0 + r, column group c4: read + clear
+    // the tile words, write (or add to) the output at o, list the cells >= T
+    auto unit = [&](uint32_t rl, uint32_t c4, uint4 *o) {
+        const uint32_t r = r0 + rl;
         uint32_t v[4];
         if (U16) {
             uint2 *p = reinterpret_cast<uint2 *>(&tile[r * pitch + ((2u * c4) ^ (row_hash(r) & 0x1Eu))]);
@@ -398,7 +400,7 @@ __device__ __forceinline__ void flush_tile(const Geom &g, uint32_t *tile, uint32
     } else {
         const uint32_t units = rows * nb;
         for (uint32_t u = tid; u < units; u += bd) {
-            const uint32_t r = u / nb, j = u - r * nb;
+            const uint32_t rl = u / nb, j = u - rl * nb, r = r0 + rl;
             uint32_t v;
             if (U16) {
                 const uint32_t word = r * pitch + ((j >> 1) ^ (row_hash(r) & 0x1Eu));
@@ -412,9 +414,9 @@ __device__ __forceinline__ void flush_tile(const Geom &g, uint32_t *tile, uint32
             list_cells<LIST>(g, L, r, j, &v, 1);
         }
         G::sync();
-        // clear the tile after every thread has read its cells
+        // clear the rows after every thread has read its cells
         for (uint32_t k = tid; k < rows * pitch; k += bd)
-            tile[k] = 0u;
+            tile[r0 * pitch + k] = 0u;
     }
 }
 
@@ -1014,14 +1016,16 @@ __device__ __forceinline__ bool is_peak_l2(const uint32_t *row, const uint32_t *
 // Append the candidate cells of one pass (rows iA .. iA + pr - 1 of slice
 // unit `slice_lin0`) to the CTA's candidate chunks, in linear order.  n_c
 // cells were listed as r * n_b + j in cand / candv (up to kFusedCand); with
-// more, the rows marked in hotm are read back from M_H.  Entries are
-// {lin within event, event, votes, 0}.  All threads of the group call it.
-template <class G>
+// more, the rows marked in hotm are read back: pass row r from rowsA + r n_b
+// when r < split, else from rowsB + (r - split) n_b -- M_H in global memory,
+// or (SMEM) the shared staging buffers.  Entries are {lin within event,
+// event, votes, 0}.  All threads of the group call it.
+template <class G, bool SMEM = false>
 __device__ __forceinline__ void emit_pass(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss, uint4 *pbuf,
                                           uint32_t &buf_n, uint32_t &nseq, uint32_t &total, const ChunkList &inner,
                                           const uint32_t *cand, const uint32_t *candv, uint32_t *srt, uint32_t *srtv,
                                           uint32_t n_c, uint64_t hotm, uint32_t pr, uint32_t iA, uint32_t slice_lin0,
-                                          uint32_t e, const uint32_t *Ms)
+                                          uint32_t e, const uint32_t *rowsA, const uint32_t *rowsB, uint32_t split)
 {
     const uint32_t tid = G::rank(), bd = G::size(), nb = g.nb;
     const uint32_t lin0 = slice_lin0 + iA * nb;
@@ -1054,12 +1058,12 @@ __device__ __forceinline__ void emit_pass(const Geom &g, const Work &w, const Sc
     for (uint32_t r = 0; r < pr; ++r) {
         if (!((hotm >> r) & 1ull))
             continue;
-        const uint32_t *row = Ms + (size_t)(iA + r) * nb;
+        const uint32_t *row = r < split ? rowsA + (size_t)r * nb : rowsB + (size_t)(r - split) * nb;
         for (uint32_t j0 = 0; j0 < nb; j0 += per_round) {
             const uint32_t j = j0 + tid;
             uint32_t cnt = 0, pj[1], pv[1];
             if (tid < per_round && j < nb) {
-                const uint32_t v = __ldcg(row + j);
+                const uint32_t v = SMEM ? row[j] : __ldcg(row + j);
                 if (v >= T) {
                     pj[0] = j;
                     pv[0] = v;
@@ -1117,8 +1121,56 @@ __device__ __forceinline__ void flush_emit_pass(const Geom &g, const Work &w, co
     const uint32_t n_c = *s_nc;
     if (n_c)
         emit_pass<G>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, cand, candv, srt, srtv, n_c, hotm, pr, iA,
-                     slice_lin0, e, Ms);
+                     slice_lin0, e, Ms + (size_t)iA * g.nb, nullptr, pr);
     G::sync();                    // lists and counters free for the next pass
+}
+
+// The same through the u32 staging buffers stg[0], stg[1] (hrows rows of
+// n_b cells each; k_fill_bulk): the pass leaves in halves of hrows rows.
+// Each half waits until the bulk copy that last read its buffer is done
+// (thread 0's async-groups, all but the newest), is converted into the
+// buffer while the candidates are listed, and is copied to M_H by thread 0
+// with one bulk copy (the half's rows are contiguous in the buffer and in
+// M_H); the threads then go on while the copy drains.  *bsel alternates the
+// buffers across halves.  Hot rows of an overflowing pass are read back
+// from the buffers.  dst: the pass's first M_H row.  All threads of the
+// block call it.
+template <bool U16>
+__device__ __forceinline__ void bulk_flush_emit_pass(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss,
+                                                     uint4 *pbuf, uint32_t &buf_n, uint32_t &nseq, uint32_t &total,
+                                                     const ChunkList &inner, uint32_t *tile, uint32_t pitch,
+                                                     uint32_t *dst, uint32_t pr, uint32_t iA, uint32_t slice_lin0,
+                                                     uint32_t e, uint32_t *stg, uint32_t hrows, uint32_t &bsel,
+                                                     uint32_t *lists, uint32_t *s_hot, uint32_t *s_nc)
+{
+    uint32_t *cand = lists, *candv = lists + kFusedCand, *srt = lists + 2 * kFusedCand, *srtv = lists + 3 * kFusedCand;
+    const uint32_t tid = threadIdx.x, nb = g.nb;
+    if (tid == 0)
+        s_hot[0] = s_hot[1] = *s_nc = 0u;
+    const uint32_t b0 = bsel;   // the first half's buffer; the second takes the other
+    for (uint32_t h0 = 0; h0 < pr; h0 += hrows) {
+        const uint32_t nr = min(hrows, pr - h0);
+        uint32_t *S = stg + (size_t)bsel * hrows * nb;
+        if (tid == 0)
+            bulk_wait_read<1>();   // the copy that last read buffer bsel is done
+        __syncthreads();           // (first half: the votes and the counter reset are done too)
+        flush_tile<U16, true, false, BlockGroup>(g, tile, S, nr, pitch,
+                                                 FlushList{s_hot, cand, candv, s_nc, kFusedCand}, h0);
+        fence_proxy_async_smem();  // the buffer's generic writes, visible to the bulk copies
+        __syncthreads();
+        if (tid == 0) {
+            bulk_store(dst + (size_t)h0 * nb, S, nr * nb * 4u);
+            bulk_commit();
+        }
+        bsel ^= 1u;
+    }
+    const uint64_t hotm = (uint64_t)s_hot[0] | ((uint64_t)s_hot[1] << 32);
+    const uint32_t n_c = *s_nc;
+    if (n_c)
+        emit_pass<BlockGroup, true>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, cand, candv, srt, srtv, n_c, hotm,
+                                    pr, iA, slice_lin0, e, stg + (size_t)b0 * hrows * nb,
+                                    stg + (size_t)(b0 ^ 1u) * hrows * nb, hrows);
+    __syncthreads();               // lists and counters free for the next pass
 }
 
 // The CTA's candidate bookkeeping once its range is done.
@@ -1135,15 +1187,21 @@ __device__ __forceinline__ void finish_candidates(const Work &w, const ScanArgs 
     }
 }
 
-__global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, ScanArgs a)
+// The body of both fused fills.  BULK (k_fill_bulk): the passes leave
+// through two u32 staging buffers and bulk copies (bulk_flush_emit_pass),
+// so the stores drain while the next votes run; else (k_fill_scan) the
+// threads store each pass to M_H themselves (flush_emit_pass).
+template <bool BULK>
+__device__ __forceinline__ void fill_scan_body(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a)
 {
     extern __shared__ uint4 sm4[];
-    // layout: ScanSmem (256 B) | K entries | tile | HC staged hits | B thresholds |
-    //         candidate lists (keys, votes, sorted keys, sorted votes)
+    // layout: ScanSmem (256 B) | K entries | tile | [BULK: 2 staging buffers] | HC staged hits |
+    //         B thresholds | candidate lists (keys, votes, sorted keys, sorted votes)
     ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
     uint4 *pbuf = sm4 + 16;
     uint32_t *tile = reinterpret_cast<uint32_t *>(pbuf + a.K);
-    float4 *hs = reinterpret_cast<float4 *>(tile + c.tile_words);
+    uint32_t *stg = tile + c.tile_words;
+    float4 *hs = reinterpret_cast<float4 *>(stg + (BULK ? staging_words(c, g.nb) : 0u));
     float *beta = reinterpret_cast<float *>(hs + c.HC);
     uint32_t *lists = reinterpret_cast<uint32_t *>(beta + c.beta_words);
     __shared__ uint32_t s_hot[2], s_nc;
@@ -1166,6 +1224,7 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
     uint64_t cached_es = ~0ull;
     uint32_t cached_n = 0;
     uint32_t buf_n = 0, nseq = 0, total = 0;
+    uint32_t bsel = 0;   // BULK: the staging buffer of the next half pass
 
     auto do_item = [&](const ItemCursor &cur) {
         const uint32_t k = cur.k;
@@ -1191,14 +1250,24 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
             vote_pass<BlockGroup, true, false>(g, w, tile, hs, beta, c.HC, es, l0, l1, cached_es, cached_n, u16, r, pr,
                                                i, hl, hstride, pitch, FlushList{});
             // ---- write the pass, clear the tile, emit its candidates --------
-            if (u16)
+            if (BULK) {
+                if (u16)
+                    bulk_flush_emit_pass<true>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, pitch,
+                                               Mrow + (size_t)p0 * nb, pr, iA, slice_lin0, e, stg, c.W / 2, bsel,
+                                               lists, s_hot, &s_nc);
+                else
+                    bulk_flush_emit_pass<false>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, pitch,
+                                                Mrow + (size_t)p0 * nb, pr, iA, slice_lin0, e, stg, c.W / 2, bsel,
+                                                lists, s_hot, &s_nc);
+            } else if (u16) {
                 flush_emit_pass<BlockGroup, true>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, pitch,
                                                   Mrow + (size_t)p0 * nb, pr, iA, slice_lin0, e, Ms, lists, s_hot,
                                                   &s_nc, nullptr);
-            else
+            } else {
                 flush_emit_pass<BlockGroup, false>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, tile, pitch,
                                                    Mrow + (size_t)p0 * nb, pr, iA, slice_lin0, e, Ms, lists, s_hot,
                                                    &s_nc, nullptr);
+            }
         }
     };
     ItemCursor cur(g, c, it0);
@@ -1215,6 +1284,18 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
             finish_candidates<BlockGroup>(w, a, ss, pbuf, buf_n, nseq, total, inner, list);
         }
     }
+    if (BULK && threadIdx.x == 0)
+        bulk_wait<0>();   // the last copies have written M_H (and read the staging) before the CTA ends
+}
+
+__global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, ScanArgs a)
+{
+    fill_scan_body<false>(g, w, c, a);
+}
+
+__global__ void __launch_bounds__(1024) k_fill_bulk(Geom g, Work w, FillCfg c, ScanArgs a)
+{
+    fill_scan_body<true>(g, w, c, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -1944,18 +2025,21 @@ cudaError_t launch_scatter(const Geom &g, const Work &w, uint32_t grid, cudaStre
 
 size_t fill_scan_smem_bytes(const FillCfg &c, const ScanArgs &a, uint32_t nb)
 {
-    return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)c.tile_words * 4 + (size_t)c.HC * 16 +
-           (size_t)c.beta_words * 4 + (size_t)4 * kFusedCand * 4;
+    return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)c.tile_words * 4 +
+           (size_t)staging_words(c, nb) * 4 + (size_t)c.HC * 16 + (size_t)c.beta_words * 4 +
+           (size_t)4 * kFusedCand * 4;
 }
 
 cudaError_t launch_fill_scan(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
                              cudaStream_t st)
 {
     const size_t smem = fill_scan_smem_bytes(c, a, g.nb);
-    cudaError_t e = allow_smem((const void *)k_fill_scan, smem);
+    const void *k = c.bulk ? (const void *)k_fill_bulk : (const void *)k_fill_scan;
+    cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess)
         return e;
-    return launch_pdl(k_fill_scan, grid, c.threads, smem, st, g, w, c, a);
+    return c.bulk ? launch_pdl(k_fill_bulk, grid, c.threads, smem, st, g, w, c, a)
+                  : launch_pdl(k_fill_scan, grid, c.threads, smem, st, g, w, c, a);
 }
 
 size_t fill_ws_smem_bytes(const FillCfg &c, const ScanArgs &a)
@@ -2002,10 +2086,11 @@ cudaError_t launch_fill_peaks(const Geom &g, const Work &w, const FillCfg &c, co
 cudaError_t fill_scan_occupancy(const FillCfg &c, const ScanArgs &a, uint32_t nb, int *blocks_per_sm)
 {
     const size_t smem = fill_scan_smem_bytes(c, a, nb);
-    cudaError_t e = allow_smem((const void *)k_fill_scan, smem);
+    const void *k = c.bulk ? (const void *)k_fill_bulk : (const void *)k_fill_scan;
+    cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fill_scan, c.threads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, c.threads, smem);
 }
 
 size_t fill_smem_bytes(const FillCfg &c)

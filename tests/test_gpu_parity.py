@@ -107,9 +107,33 @@ def test_fill_and_maxima_match_oracle(ht, case, naive):
     assert np.all(pk["event"] == 0)
 
 
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_bulk_store_fill_matches_oracle(ht, case):
+    """The fused fill whose passes leave through shared-memory staging and
+    bulk async copies (fill_fused_scan=4): bit-exact M_H and peaks, or a
+    refusal when n_b is not a multiple of 4."""
+    name, bins, rng, T, (x, y, z) = case
+    b, r = ht.Binning(*bins), ht.Ranges(**rng)
+    M_ref, votes = oracle.fill(_ob(b), _orr(r), x, y, z)
+    pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, T)
+    with ht.Context(b, r, threshold=T, max_hits=max(len(x), 1)) as ctx:
+        if b.n_b % 4:
+            with pytest.raises(ht.HTError):
+                ctx.set_tuning(fill_fused_scan=4)
+            return
+        ctx.set_tuning(fill_fused_scan=4)
+        assert ctx.get_tuning()["fill_fused_scan"] == 4
+        for _ in range(2):
+            ctx.fill(x, y, z)
+            pk, n = ctx.find_maxima(capacity=1 << 20)
+            assert n == n_ref
+            assert_peaks_equal(pk, pk_ref)
+        assert np.array_equal(ctx.matrix(), M_ref)
+
+
 U32_TUNINGS = [None, dict(fill_fused_scan=2), dict(fill_fused_scan=1, fill_rows=2, fill_threads=256),
                dict(fill_fused_scan=1, fill_rows=4, fill_threads=256), dict(fill_fused_scan=3, fill_rows=2),
-               dict(fill_fused_scan=3, fill_rows=8)]
+               dict(fill_fused_scan=3, fill_rows=8), dict(fill_fused_scan=4), dict(fill_fused_scan=4, fill_rows=4)]
 
 
 @pytest.mark.parametrize("tuning", U32_TUNINGS, ids=[str(t) for t in U32_TUNINGS])
@@ -293,6 +317,8 @@ TUNINGS = [
     dict(fill_fused_scan=2, scan_kind=2), dict(fill_fused_scan=2, scan_kind=1),
     dict(fill_fused_scan=1, fill_rows=4, fill_threads=256), dict(fill_fused_scan=3, fill_rows=16),
     dict(fill_fused_scan=3, fill_rows=32, fill_hits_staged=1024),
+    dict(fill_fused_scan=4), dict(fill_fused_scan=4, fill_rows=16), dict(fill_fused_scan=4, fill_rows=8, fill_threads=512),
+    dict(fill_fused_scan=4, fill_hits_staged=64),
 ]
 
 
@@ -340,7 +366,8 @@ def test_bad_tuning_rejected(ht):
 FUSED_TUNINGS = [dict(fill_fused_scan=2), dict(fill_fused_scan=1), dict(fill_fused_scan=1, fill_rows=4,
                  fill_threads=256), dict(fill_fused_scan=1, fill_rows=64, fill_threads=1024),
                  dict(fill_fused_scan=1, fill_rows=8, fill_blocks_per_sm=1), dict(fill_fused_scan=3),
-                 dict(fill_fused_scan=3, fill_rows=4), dict(fill_fused_scan=3, fill_rows=64)]
+                 dict(fill_fused_scan=3, fill_rows=4), dict(fill_fused_scan=3, fill_rows=64),
+                 dict(fill_fused_scan=4), dict(fill_fused_scan=4, fill_rows=4)]
 
 
 def _track(A, B, theta, branch):
@@ -384,8 +411,8 @@ def test_peaks_on_seams(ht, tuning):
         assert_peaks_equal(pk, pk_ref)
 
 
-@pytest.mark.parametrize("tuning", FUSED_TUNINGS[1:4] + FUSED_TUNINGS[5:7],
-                         ids=[str(t) for t in FUSED_TUNINGS[1:4] + FUSED_TUNINGS[5:7]])
+@pytest.mark.parametrize("tuning", FUSED_TUNINGS[1:4] + FUSED_TUNINGS[5:7] + FUSED_TUNINGS[8:],
+                         ids=[str(t) for t in FUSED_TUNINGS[1:4] + FUSED_TUNINGS[5:7] + FUSED_TUNINGS[8:]])
 def test_fused_candidate_overflow(ht, paper_ref, tuning):
     # low thresholds on the paper-scale event: some passes list more cells
     # >= T than the fused fill's candidate lists hold (whole-row fallback,
@@ -402,8 +429,8 @@ def test_fused_candidate_overflow(ht, paper_ref, tuning):
         assert_peaks_equal(pk, pk_ref)
 
 
-@pytest.mark.parametrize("tuning", FUSED_TUNINGS[1:3] + FUSED_TUNINGS[5:6],
-                         ids=[str(t) for t in FUSED_TUNINGS[1:3] + FUSED_TUNINGS[5:6]])
+@pytest.mark.parametrize("tuning", FUSED_TUNINGS[1:3] + FUSED_TUNINGS[5:6] + FUSED_TUNINGS[8:9],
+                         ids=[str(t) for t in FUSED_TUNINGS[1:3] + FUSED_TUNINGS[5:6] + FUSED_TUNINGS[8:9]])
 def test_fused_state_sequences(ht, paper_ref, tuning):
     ev, M_ref, pk_ref, n_ref = paper_ref
     ev2 = synth.paper_event(seed=12)
@@ -447,7 +474,7 @@ def test_autotune_keeps_results(ht, paper_ref):
             ctx.autotune()                        # nothing filled yet
         ctx.fill(ev.x, ev.y, ev.z)
         chosen, us = ctx.autotune(reps=3)
-        assert us > 0 and chosen["fill_fused_scan"] in (1, 2, 3)
+        assert us > 0 and chosen["fill_fused_scan"] in (1, 2, 3, 4)
         assert np.array_equal(ctx.matrix(), M_ref)
         pk, n = ctx.find_maxima(capacity=1 << 16)
         assert n == n_ref
