@@ -287,7 +287,7 @@ def run_ours(args, rank, world):
     hbm_peak, peak_src = measured_peaks()
     cells_bytes = b.n_cells * 4
     algo = {"k_fill_priv": cells_bytes, "k_fill_scan": cells_bytes, "k_fill_ws": cells_bytes, "k_scan": cells_bytes,
-            "k_clear": cells_bytes, "k_fill_naive": None, "k_bin": None, "k_scatter": None, "k_seam": None,
+            "k_clear": cells_bytes, "k_fill_naive": None, "k_bin": None, "k_scatter": None,
             "k_order": None}
     n_dom, ms_dom = prof[dom]
     avg_s = ms_dom / n_dom / 1e3
