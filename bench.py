@@ -307,7 +307,7 @@ def run_ours(args, rank, world):
         "data": "synthetic (seeded helix events; the paper's dataset is not available)",
         "config": {"workload": WORKLOAD, "events_resident": N_POOL, "fill": "naive" if args.naive else "privatised",
                    "tuning": tuning,
-                   "l2": "inputs larger than L2: each step writes a 256 MiB M_H (L2 126 MB), read back at its candidates",
+                   "l2": "inputs larger than L2: each step writes a 256 MiB M_H (L2 129 MB), read back at its candidates",
                    "parallelism": f"replicas x{world}"},
         "gvotes_per_s": round(value * mean_votes / 1e9, 3),
         "votes_per_event": int(mean_votes), "peaks_per_event": float(np.mean(peaks)),
