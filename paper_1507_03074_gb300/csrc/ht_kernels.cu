@@ -344,15 +344,16 @@ __device__ __forceinline__ void list_cells(const Geom &g, const FlushList &L, ui
         }
 }
 
-// Write tile rows r0 .. r0 + rows - 1 of one pass to dst (M_H, or a staging
-// buffer, from its first row on) and clear them; with LIST, list the cells
-// >= T (as pass rows r0 + r); with accumulate, add to M_H.
+// Write tile rows r0 .. r0 + rows - 1 of one pass to dst (M_H, or with
+// !GDST a shared-memory staging buffer, from its first row on) and clear
+// them; with LIST, list the cells >= T (as pass rows r0 + r); with
+// accumulate, add to M_H.
 // The tile keeps row r's logical word w at physical word w ^ sw(r) (sw even
 // in u16 mode, a multiple of 4 in u32 mode).  When n_b is a multiple of 4
 // each step moves 4 cells: consecutive threads write consecutive 16-byte
 // pieces of the row, so every store instruction of a warp covers 512
 // contiguous bytes.
-template <bool U16, bool LIST, bool ACC, class G = BlockGroup>
+template <bool U16, bool LIST, bool ACC, class G = BlockGroup, bool GDST = true>
 __device__ __forceinline__ void flush_tile(const Geom &g, uint32_t *tile, uint32_t *dst, uint32_t rows,
                                            uint32_t pitch, const FlushList &L, uint32_t r0 = 0)
 {
@@ -377,7 +378,13 @@ __device__ __forceinline__ void flush_tile(const Geom &g, uint32_t *tile, uint32
             const uint4 old = *o;
             v[0] += old.x; v[1] += old.y; v[2] += old.z; v[3] += old.w;
         }
-        *o = make_uint4(v[0], v[1], v[2], v[3]);
+        // to M_H a streaming store (evict-first): M_H is written once per fill and
+        // read back only at the candidates, so its lines should not displace
+        // other data in L2; a staging buffer in shared memory takes a plain store
+        if (GDST)
+            __stcs(o, make_uint4(v[0], v[1], v[2], v[3]));
+        else
+            *o = make_uint4(v[0], v[1], v[2], v[3]);
         list_cells<LIST>(g, L, r, 4u * c4, v, 4);
     };
     if ((nb & 3u) == 0) {
@@ -1154,8 +1161,8 @@ __device__ __forceinline__ void bulk_flush_emit_pass(const Geom &g, const Work &
         if (tid == 0)
             bulk_wait_read<1>();   // the copy that last read buffer bsel is done
         __syncthreads();           // (first half: the votes and the counter reset are done too)
-        flush_tile<U16, true, false, BlockGroup>(g, tile, S, nr, pitch,
-                                                 FlushList{s_hot, cand, candv, s_nc, kFusedCand}, h0);
+        flush_tile<U16, true, false, BlockGroup, false>(g, tile, S, nr, pitch,
+                                                        FlushList{s_hot, cand, candv, s_nc, kFusedCand}, h0);
         fence_proxy_async_smem();  // the buffer's generic writes, visible to the bulk copies
         __syncthreads();
         if (tid == 0) {
