@@ -180,6 +180,14 @@ ht_status ht_find_maxima_noalloc(const ht_binning *binning, const ht_ranges *ran
                                  const uint32_t *M, uint32_t n_events, ht_peak *out, uint32_t capacity,
                                  uint32_t *counts, void *stream);
 
+/* Exercise the failure path of the kernels' bounded waits: one device
+ * thread waits on a barrier that nothing completes, gives up after
+ * limit_ms (1 .. 1000) and flags the timeout as a real wait would.  Waits
+ * for the context's stream; returns HT_E_TIMEOUT (the expected outcome; the
+ * context stays usable and its counters are reset), or HT_E_INVAL /
+ * HT_E_CUDA / HT_E_STATE. */
+ht_status ht_check_wait_timeout(ht_ctx *ctx, uint32_t limit_ms);
+
 /* Wait for the context's stream (or `stream`) and report any device-side
  * failure flagged by its kernels (HT_E_TIMEOUT). */
 ht_status ht_sync(ht_ctx *ctx, void *stream);

@@ -263,6 +263,17 @@ ht_status ht_sync(ht_ctx *ctx, void *stream)
     return read_status(ctx, st);
 }
 
+ht_status ht_check_wait_timeout(ht_ctx *ctx, uint32_t limit_ms)
+{
+    ht_status s = check_ctx(ctx);
+    if (s != HT_OK)
+        return s;
+    if (limit_ms < 1 || limit_ms > 1000)
+        return set_err(HT_E_INVAL, "limit_ms must be 1 .. 1000");
+    CK(htk::launch_wait_probe(hte::engine_status(ctx->E), limit_ms, ctx->stream));
+    return read_status(ctx, ctx->stream);   // HT_E_TIMEOUT, counters reset
+}
+
 ht_status ht_copy_matrix(ht_ctx *ctx, uint32_t *dst, uint64_t n_cells, uint32_t flags, void *stream)
 {
     ht_status s = check_ctx(ctx);

@@ -129,6 +129,9 @@ enum ScanKind { SCAN_DIRECT = 0, SCAN_BULK = 1, SCAN_LDG = 2 };
 cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, int kind, cudaStream_t st);
 cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const OrderArgs &o,
                          cudaStream_t st);
+// One bounded wait that nothing ends (k_wait_probe): flags ST_WAIT_TIMEOUT
+// after limit_ms (at most about a second).
+cudaError_t launch_wait_probe(uint32_t *status, uint32_t limit_ms, cudaStream_t st);
 // The 4-D filter of a 2-D peak list (k_peaks4d, one CTA).
 cudaError_t launch_peaks4d(const Geom &g, const uint32_t *M, const Peak *in, const uint32_t *n_in, uint32_t cap_in,
                            Peak *out, uint32_t cap_out, uint32_t *n_out, uint32_t *status, cudaStream_t st);

@@ -2250,6 +2250,37 @@ cudaError_t launch_peaks4d(const Geom &g, const uint32_t *M, const Peak *in, con
     return launch_pdl(k_peaks4d, 1u, 1024u, (size_t)0, st, g, M, in, n_in, cap_in, out, cap_out, n_out, status);
 }
 
+// ---------------------------------------------------------------------------
+// k_wait_probe: the failure path of the bounded waits, on demand.  One
+// thread waits on a shared-memory mbarrier that nothing arrives at, giving
+// up after limit_ns (at most kWaitNs) or kWaitIters polls, and flags
+// ST_WAIT_TIMEOUT exactly as a real wait that gave up does.
+// ---------------------------------------------------------------------------
+__global__ void k_wait_probe(uint32_t *status, uint64_t limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0)
+        return;
+    mbar_init(&bar, 1u);   // one arrival expected, none will come
+    fence_mbar_init();
+    const uint64_t t0 = global_ns();
+    bool done = false;
+    for (uint32_t it = 0; it < kWaitIters && !done; ++it) {
+        done = mbar_try_wait(&bar, 0u);
+        if ((it & 255u) == 255u && global_ns() - t0 > limit_ns)
+            break;
+    }
+    if (!done)
+        atomicOr(status, (uint32_t)ST_WAIT_TIMEOUT);
+}
+
+cudaError_t launch_wait_probe(uint32_t *status, uint32_t limit_ms, cudaStream_t st)
+{
+    const uint64_t ns = (uint64_t)limit_ms * 1000000ull;
+    k_wait_probe<<<1, 32, 0, st>>>(status, ns < kWaitNs ? ns : kWaitNs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const OrderArgs &o,
                          cudaStream_t st)
 {

@@ -132,6 +132,7 @@ def lib():
         "ht_fill": ([P, P, P, P, U32, U32, P], I),
         "ht_find_maxima": ([P, P, U32, P, U32, P], I),
         "ht_sync": ([P, P], I),
+        "ht_check_wait_timeout": ([P, U32], I),
         "ht_copy_matrix": ([P, P, U64, U32, P], I),
         "ht_get_edges": ([P, P, P], I),
         "ht_launch_count": ([P], U64),
@@ -369,6 +370,11 @@ class Context:
 
     def sync(self, stream=None):
         check(lib().ht_sync(self._h, _stream_ptr(stream)))
+
+    def check_wait_timeout(self, limit_ms: int = 50) -> int:
+        """ht_check_wait_timeout: run one bounded device wait that nothing
+        ends; returns its status (HT_E_TIMEOUT expected)."""
+        return int(lib().ht_check_wait_timeout(self._h, limit_ms))
 
     def matrix(self) -> np.ndarray:
         M = np.zeros(self.binning.shape(), np.uint32)

@@ -563,3 +563,26 @@ def test_peaks_only_low_threshold_and_u32(ht, paper_ref):
     with ht.Context(b, r, threshold=3, max_hits=x.size) as ctx:
         with pytest.raises(ht.HTError):
             ctx.fill(x, y, z, peaks_only=True, accumulate=True)
+
+
+def test_bounded_wait_gives_up_and_context_survives(ht):
+    """A device wait that nothing ends (ht_check_wait_timeout) gives up
+    after its limit, is reported as HT_E_TIMEOUT, and the context goes on
+    working: the next fill and scan are still bit-exact."""
+    import time
+    ev = synth.tiny_event()
+    b = ht.Binning(*synth.TINY_BINNING)
+    M_ref, _ = oracle.fill(_ob(b), _orr(ht.Ranges()), ev.x, ev.y, ev.z)
+    pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(ht.Ranges()), M_ref, 8)
+    with ht.Context(b, ht.Ranges(), threshold=8, max_hits=1024) as ctx:
+        t0 = time.perf_counter()
+        st = ctx.check_wait_timeout(50)
+        dt = time.perf_counter() - t0
+        assert st == ht.HT_E_TIMEOUT and "wait" in ht.last_error()
+        assert dt < 5.0
+        assert ctx.check_wait_timeout(0) == ht.HT_E_INVAL
+        ctx.fill(ev.x, ev.y, ev.z)
+        pk, n = ctx.find_maxima(capacity=1024)
+        assert n == n_ref
+        assert_peaks_equal(pk, pk_ref)
+        assert np.array_equal(ctx.matrix(), M_ref)
