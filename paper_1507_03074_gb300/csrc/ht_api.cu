@@ -37,6 +37,7 @@ struct ht_ctx {
     uint32_t acc_hits = 0;
     bool last_peaks_only = false;  // the last fill left M_H as it was
     htk::Peak *d_p2 = nullptr;     // the 2-D peak list of 4-D scans (E.scan.entries_cap entries)
+    uint8_t *d_keep = nullptr;     // and its keep flags
     uint32_t p2_cap = 0;
     bool poisoned = false;
 };
@@ -140,6 +141,7 @@ ht_status ht_destroy(ht_ctx *ctx)
     cudaFree(ctx->d_small);
     cudaFree(ctx->d_peaks);
     cudaFree(ctx->d_p2);
+    cudaFree(ctx->d_keep);
     cudaFreeHost(ctx->h_in);
     cudaFreeHost(ctx->h_small);
     if (ctx->ev_in)
@@ -216,15 +218,19 @@ ht_status ht_find_maxima(ht_ctx *ctx, ht_peak *out, uint32_t capacity, uint32_t 
         if (ctx->p2_cap < ctx->E.scan.entries_cap) {
             CK(cudaStreamSynchronize(st));
             cudaFree(ctx->d_p2);
+            cudaFree(ctx->d_keep);
             ctx->d_p2 = nullptr;
+            ctx->d_keep = nullptr;
             ctx->p2_cap = 0;
             CK(cudaMalloc(&ctx->d_p2, (size_t)ctx->E.scan.entries_cap * sizeof(htk::Peak)));
+            CK(cudaMalloc(&ctx->d_keep, (size_t)ctx->E.scan.entries_cap));
             ctx->p2_cap = ctx->E.scan.entries_cap;
         }
     }
     // the 2-D list's total goes to d_small[2] (d_small[0] holds the result's)
     auto scan = [&](htk::Peak *dst, uint32_t cap, uint32_t *cnt) {
-        return four ? hte::engine_scan4d(ctx->E, ctx->d_p2, ctx->p2_cap, ctx->d_small + 2, dst, cap, cnt, st)
+        return four ? hte::engine_scan4d(ctx->E, ctx->d_p2, ctx->d_keep, ctx->p2_cap, ctx->d_small + 2, dst, cap, cnt,
+                                         st)
                     : hte::engine_scan(ctx->E, 1, dst, cap, cnt, st);
     };
     if (flags & HT_MEM_DEVICE) {

@@ -704,16 +704,17 @@ cudaError_t engine_scan(Engine &E, uint32_t n_events, htk::Peak *out, uint32_t c
     return e;
 }
 
-cudaError_t engine_scan4d(Engine &E, htk::Peak *p2, uint32_t p2_cap, uint32_t *p2_count, htk::Peak *out,
-                          uint32_t capacity, uint32_t *counts, cudaStream_t st)
+cudaError_t engine_scan4d(Engine &E, htk::Peak *p2, uint8_t *keep, uint32_t p2_cap, uint32_t *p2_count,
+                          htk::Peak *out, uint32_t capacity, uint32_t *counts, cudaStream_t st)
 {
     cudaError_t e = engine_scan(E, 1, p2, p2_cap, p2_count, st);
     if (e != cudaSuccess)
         return e;
     {
         ProfScope ps(E, K_PEAKS4D, st);
-        e = htk::launch_peaks4d(E.geom, E.d_M, p2, p2_count, p2_cap, out, capacity, counts,
-                                E.d_ctr + htk::CTR_STATUS, st);
+        e = htk::launch_peaks4d(E.geom, E.d_M, p2, p2_count, p2_cap, keep, out, capacity, counts,
+                                E.d_ctr + htk::CTR_P4TICKET, E.d_ctr + htk::CTR_STATUS, (uint32_t)E.num_sms * 2u,
+                                st);
     }
     ++E.launches;
     return e;

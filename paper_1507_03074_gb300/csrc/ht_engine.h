@@ -167,9 +167,9 @@ cudaError_t engine_set_phi_edges(Engine &E, const float *ep);
 // p2 (p2_cap entries, total in *p2_count), then those that also beat their
 // neighbours in the adjacent (theta, phi) slices, in order, into out
 // (capacity entries, total in *counts).  p2_cap must be >= the engine's
-// entry bound (E.scan.entries_cap).
-cudaError_t engine_scan4d(Engine &E, htk::Peak *p2, uint32_t p2_cap, uint32_t *p2_count, htk::Peak *out,
-                          uint32_t capacity, uint32_t *counts, cudaStream_t st);
+// entry bound (E.scan.entries_cap); keep holds p2_cap flags.
+cudaError_t engine_scan4d(Engine &E, htk::Peak *p2, uint8_t *keep, uint32_t p2_cap, uint32_t *p2_count,
+                          htk::Peak *out, uint32_t capacity, uint32_t *counts, cudaStream_t st);
 
 // Device status word (bits of htk::ST_*).
 inline uint32_t *engine_status(Engine &E) { return E.d_ctr + htk::CTR_STATUS; }

@@ -106,7 +106,8 @@ constexpr uint32_t kSeamChunks = 8;
 // last such CTA), [6 ..) peaks per event.  k_bin zeroes words 1, 2 and
 // [6, 6 + n_events) before every fill.
 enum : uint32_t {
-    CTR_STATUS = 0, CTR_ENTRIES = 1, CTR_OTICKET = 2, CTR_BTICKET = 3, CTR_DYN = 4, CTR_DYN_DONE = 5, CTR_EVENTS = 6
+    CTR_STATUS = 0, CTR_ENTRIES = 1, CTR_OTICKET = 2, CTR_BTICKET = 3, CTR_DYN = 4, CTR_DYN_DONE = 5,
+    CTR_P4TICKET = 6, CTR_EVENTS = 7
 };
 
 // Cost model of the balanced split of (event, slice, strip) work items over
@@ -132,9 +133,11 @@ cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const 
 // One bounded wait that nothing ends (k_wait_probe): flags ST_WAIT_TIMEOUT
 // after limit_ms (at most about a second).
 cudaError_t launch_wait_probe(uint32_t *status, uint32_t limit_ms, cudaStream_t st);
-// The 4-D filter of a 2-D peak list (k_peaks4d, one CTA).
+// The 4-D filter of a 2-D peak list (k_peaks4d): keep holds cap_in flags;
+// ticket is a zero counter word (reset by the kernel).
 cudaError_t launch_peaks4d(const Geom &g, const uint32_t *M, const Peak *in, const uint32_t *n_in, uint32_t cap_in,
-                           Peak *out, uint32_t cap_out, uint32_t *n_out, uint32_t *status, cudaStream_t st);
+                           uint8_t *keep, Peak *out, uint32_t cap_out, uint32_t *n_out, uint32_t *ticket,
+                           uint32_t *status, uint32_t grid, cudaStream_t st);
 cudaError_t scan_occupancy(int kind, size_t smem, int *blocks_per_sm);
 cudaError_t fill_occupancy(const FillCfg &c, int *blocks_per_sm);
 

@@ -2157,98 +2157,7 @@ cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, int kin
     return launch_pdl(k_scan_direct, a.grid, 256, smem, st, g, w, a);
 }
 
-// ---------------------------------------------------------------------------
-// k_peaks4d: the 4-D (80-neighbour) maxima rule as a filter of the 2-D list.
-//
-// A cell's 8 neighbours in its own (A, B) slice are among its 80 neighbours
-// in (theta, phi, A, B), so every 4-D peak is a 2-D peak: the filter takes
-// the 2-D peaks (ascending linear index) and keeps those that also beat the
-// up to 72 cells of the adjacent slices -- strictly the ones in an earlier
-// slice (smaller linear index), with >= the ones in a later slice; phi does
-// not wrap.  One CTA walks the list in rounds of blockDim.x peaks and
-// compacts the kept ones in order (warp ballots, then a scan of the warp
-// totals).  The peaks are few and each reads 72 cells from L2 / HBM, so the
-// filter is latency- rather than bandwidth-bound.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool beats_adjacent_slices(const Geom &g, const uint32_t *M, const Peak &p)
-{
-    const int nt = (int)g.nt, np = (int)g.np, na = (int)g.na, nb = (int)g.nb;
-    const int t = (int)p.itheta, f = (int)p.iphi, i = (int)p.ia, j = (int)p.ib;
-    const uint32_t v = p.votes;
-    for (int dt = -1; dt <= 1; ++dt) {
-        const int tt = t + dt;
-        if (tt < 0 || tt >= nt)
-            continue;
-        for (int df = -1; df <= 1; ++df) {
-            const int ff = f + df;
-            if ((dt == 0 && df == 0) || ff < 0 || ff >= np)
-                continue;
-            const bool before = dt < 0 || (dt == 0 && df < 0);
-            const uint32_t *S = M + ((size_t)tt * np + ff) * (size_t)na * nb;
-            uint32_t w[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {   // issue the slice's loads together
-                const int ii = i + k / 3 - 1, jj = j + k % 3 - 1;
-                // an absent cell reads as 0, which a peak (v >= T >= 1) always beats
-                w[k] = (ii >= 0 && ii < na && jj >= 0 && jj < nb) ? S[(size_t)ii * nb + jj] : 0u;
-            }
-#pragma unroll
-            for (int k = 0; k < 9; ++k)
-                if (before ? !(v > w[k]) : !(v >= w[k]))
-                    return false;
-        }
-    }
-    return true;
-}
 
-__global__ void __launch_bounds__(1024) k_peaks4d(Geom g, const uint32_t *M, const Peak *in, const uint32_t *n_in,
-                                                  uint32_t cap_in, Peak *out, uint32_t cap_out, uint32_t *n_out,
-                                                  uint32_t *status)
-{
-    __shared__ uint32_t s_warp[32], s_total;
-    grid_dep_wait();   // the 2-D list of k_order
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5, nw = (blockDim.x + 31) / 32;
-    const uint32_t n_all = *n_in;
-    if (n_all > cap_in && tid == 0)
-        atomicOr(status, (uint32_t)ST_SCRATCH_OVERFLOW);   // the 2-D list was cut: the filter would miss peaks
-    const uint32_t n = min(n_all, cap_in);
-    uint32_t base = 0;
-    for (uint32_t r0 = 0; r0 < n; r0 += blockDim.x) {
-        const uint32_t q = r0 + tid;
-        Peak p{};
-        bool keep = false;
-        if (q < n) {
-            p = in[q];
-            keep = beats_adjacent_slices(g, M, p);
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0)
-            s_warp[wid] = __popc(bal);
-        __syncthreads();
-        if (wid == 0) {
-            const uint32_t c = lane < nw ? s_warp[lane] : 0u;
-            const uint32_t incl = warp_incl_scan(c);
-            if (lane < nw)
-                s_warp[lane] = incl - c;   // exclusive prefix of the warp totals
-            if (lane == 31)
-                s_total = incl;            // the round's total
-        }
-        __syncthreads();
-        const uint32_t pos = base + s_warp[wid] + __popc(bal & ((1u << lane) - 1u));
-        if (keep && pos < cap_out)
-            out[pos] = p;
-        base += s_total;
-        __syncthreads();   // s_warp, s_total free for the next round
-    }
-    if (tid == 0)
-        *n_out = base;
-}
-
-cudaError_t launch_peaks4d(const Geom &g, const uint32_t *M, const Peak *in, const uint32_t *n_in, uint32_t cap_in,
-                           Peak *out, uint32_t cap_out, uint32_t *n_out, uint32_t *status, cudaStream_t st)
-{
-    return launch_pdl(k_peaks4d, 1u, 1024u, (size_t)0, st, g, M, in, n_in, cap_in, out, cap_out, n_out, status);
-}
 
 // ---------------------------------------------------------------------------
 // k_wait_probe: the failure path of the bounded waits, on demand.  One
@@ -2279,6 +2188,100 @@ cudaError_t launch_wait_probe(uint32_t *status, uint32_t limit_ms, cudaStream_t 
     const uint64_t ns = (uint64_t)limit_ms * 1000000ull;
     k_wait_probe<<<1, 32, 0, st>>>(status, ns < kWaitNs ? ns : kWaitNs);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// k_peaks4d: the 4-D (80-neighbour) maxima rule as a filter of the 2-D list.
+//
+// A cell's 8 neighbours in its own (A, B) slice are among its 80 neighbours
+// in (theta, phi, A, B), so every 4-D peak is a 2-D peak: the filter takes
+// the 2-D peaks (ascending linear index) and keeps those that also beat the
+// up to 72 cells of the adjacent slices -- strictly the ones in an earlier
+// slice (smaller linear index), with >= the ones in a later slice; phi does
+// not wrap.  One warp per peak: its lanes read the 72 cells at once (three
+// rounds of 32) and a warp vote decides; the keep flags go to `keep`, and
+// the last CTA to finish (ticket) compacts the kept peaks in order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_peaks4d(Geom g, const uint32_t *M, const Peak *in, const uint32_t *n_in,
+                                                 uint32_t cap_in, uint8_t *keep, Peak *out, uint32_t cap_out,
+                                                 uint32_t *n_out, uint32_t *ticket, uint32_t *status)
+{
+    __shared__ uint32_t s_warp[32], s_total, s_last;
+    grid_dep_wait();   // the 2-D list of k_order
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5, nw = blockDim.x >> 5;
+    const uint32_t n_all = __ldcg(n_in);
+    const uint32_t n = min(n_all, cap_in);
+    const int nt = (int)g.nt, np = (int)g.np, na = (int)g.na, nb = (int)g.nb;
+    for (uint32_t q = blockIdx.x * nw + wid; q < n; q += gridDim.x * nw) {
+        const Peak p = in[q];
+        const int t = (int)p.itheta, f = (int)p.iphi, i = (int)p.ia, j = (int)p.ib;
+        bool ok = true;
+#pragma unroll
+        for (uint32_t round = 0; round < 3; ++round) {
+            const uint32_t k = lane + 32u * round;   // neighbour k: slice k / 9, cell k % 9
+            if (k < 72u) {
+                const uint32_t sl = k / 9u, cell = k - sl * 9u;
+                const uint32_t ts = sl < 4u ? sl : sl + 1u;   // the 3 x 3 (theta, phi) offsets but (0, 0)
+                const int dt = (int)(ts / 3u) - 1, df = (int)(ts % 3u) - 1;
+                const int tt = t + dt, ff = f + df, ii = i + (int)(cell / 3u) - 1, jj = j + (int)(cell % 3u) - 1;
+                if (tt >= 0 && tt < nt && ff >= 0 && ff < np && ii >= 0 && ii < na && jj >= 0 && jj < nb) {
+                    const uint32_t w = M[(((size_t)tt * np + ff) * na + ii) * (size_t)nb + jj];
+                    const bool before = dt < 0 || (dt == 0 && df < 0);
+                    ok = ok && (before ? p.votes > w : p.votes >= w);
+                }
+            }
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (lane == 0)
+            keep[q] = ok ? 1u : 0u;
+    }
+    // the last CTA to finish compacts the kept peaks in order
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last)
+        return;
+    __threadfence();
+    if (n_all > cap_in && tid == 0)
+        atomicOr(status, (uint32_t)ST_SCRATCH_OVERFLOW);   // the 2-D list was cut: the filter would miss peaks
+    uint32_t base = 0;
+    for (uint32_t r0 = 0; r0 < n; r0 += blockDim.x) {
+        const uint32_t q = r0 + tid;
+        const bool kq = q < n && __ldcg(&keep[q]) != 0u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, kq);
+        if (lane == 0)
+            s_warp[wid] = __popc(bal);
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t c = lane < nw ? s_warp[lane] : 0u;
+            const uint32_t incl = warp_incl_scan(c);
+            if (lane < nw)
+                s_warp[lane] = incl - c;   // exclusive prefix of the warp totals
+            if (lane == 31)
+                s_total = incl;
+        }
+        __syncthreads();
+        const uint32_t pos = base + s_warp[wid] + __popc(bal & ((1u << lane) - 1u));
+        if (kq && pos < cap_out)
+            out[pos] = in[q];
+        base += s_total;
+        __syncthreads();   // s_warp, s_total free for the next round
+    }
+    if (tid == 0) {
+        *n_out = base;
+        *ticket = 0u;
+    }
+}
+
+cudaError_t launch_peaks4d(const Geom &g, const uint32_t *M, const Peak *in, const uint32_t *n_in, uint32_t cap_in,
+                           uint8_t *keep, Peak *out, uint32_t cap_out, uint32_t *n_out, uint32_t *ticket,
+                           uint32_t *status, uint32_t grid, cudaStream_t st)
+{
+    return launch_pdl(k_peaks4d, grid, 256u, (size_t)0, st, g, M, in, n_in, cap_in, keep, out, cap_out, n_out,
+                      ticket, status);
 }
 
 cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const OrderArgs &o,
