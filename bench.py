@@ -583,6 +583,22 @@ def run_batched(n_events=100, reps=5):
         e_.record(st)
         st.synchronize()
         t_bdev = a.elapsed_time(e_) / 1e3 / reps
+        # the same batch with peaks-only fills (the matrices not written)
+        pk_po, counts_po = B.run(x, y, z, off, peaks_only=True)
+        same_po = bool(np.array_equal(counts_po, counts))
+        lat_po = []
+        for _ in range(reps):
+            ts = time.perf_counter()
+            B.run(x, y, z, off, peaks_only=True)
+            lat_po.append((time.perf_counter() - ts) * 1e3)
+        for _ in range(2):
+            B.run_device(dx, dy, dz, doff, n_hits, bout, bcnt, stream=st, peaks_only=True)
+        a.record(st)
+        for _ in range(reps):
+            B.run_device(dx, dy, dz, doff, n_hits, bout, bcnt, stream=st, peaks_only=True)
+        e_.record(st)
+        st.synchronize()
+        t_podev = a.elapsed_time(e_) / 1e3 / reps
         B.profile(True)
         B.run(x, y, z, off)
         prof = B.profile_read()
@@ -595,6 +611,10 @@ def run_batched(n_events=100, reps=5):
                                      "note": "every event of a batch is ready when the batch is"},
                       "kernels_us_per_batch": {k: round(ms / n * 1e3, 1) for k, (n, ms) in prof.items() if n},
                       "tuning": tuning, "api": "ht_batch_run (graph replay)"}
+    res["batched_peaks_only"] = {"e2e_events_per_s": round(n_events / (float(np.median(lat_po)) / 1e3), 1),
+                                 "device_events_per_s": round(n_events / t_podev, 1),
+                                 "same_counts": same_po,
+                                 "api": "ht_batch_run(..., HT_PEAKS_ONLY) (graph replay)"}
     res["votes_per_event"] = int(votes / n_events)
     return res
 

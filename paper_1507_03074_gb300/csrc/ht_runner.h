@@ -32,6 +32,7 @@ struct Runner {
     struct Graph {
         uint32_t n_events;
         bool to_host;
+        bool peaks_only;
         cudaGraphExec_t exec;
     };
     std::vector<Graph> graphs;
@@ -46,9 +47,11 @@ void runner_drop_graphs(Runner &R);
 // Enqueue one run of n_events events on st.  The hits are in the pinned
 // staging (host_in) or in the device staging already; the offsets likewise.
 // to_host: peaks and counts into the mapped pinned outputs, plus the status
-// word into h_counts[max_events]; else into d_out / d_counts.
+// word into h_counts[max_events]; else into d_out / d_counts.  peaks_only:
+// the fill keeps its tiles in shared memory (M_H is not written; the edge
+// rows must have been allocated, engine_ensure_edges).
 cudaError_t runner_enqueue(Runner &R, uint32_t n_events, uint32_t n_hits, bool host_in, bool to_host,
-                           cudaStream_t st);
+                           cudaStream_t st, bool peaks_only = false);
 
 // After a failed status word: zero the counters (stream-ordered) and map the
 // status bits to an ABI code and message.

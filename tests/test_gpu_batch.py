@@ -88,6 +88,37 @@ def test_batch_matches_oracle_and_replays(ht, uneven):
         _check_events(evs, pk, counts, refs)
 
 
+def test_batch_peaks_only(ht, uneven):
+    """HT_PEAKS_ONLY runs: the same peaks, the matrices left as the last
+    normal run wrote them; normal and peaks-only runs alternate on their own
+    captured graphs, with host and device memory."""
+    import torch
+    evs, refs = uneven
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    x, y, z, off = ht.Batch.concat(evs)
+    with ht.Batch(b, r, threshold=10, max_events=8, max_hits=40000, capacity=1 << 16) as B:
+        pk, counts = B.run(x, y, z, off)                      # normal: writes the matrices
+        _check_events(evs, pk, counts, refs)
+        rev = evs[::-1]
+        for _ in range(3):                                     # peaks-only, then graph replays
+            pk, counts = B.run(*ht.Batch.concat(rev), peaks_only=True)
+            _check_events(rev, pk, counts, refs[::-1])
+        assert np.array_equal(B.matrix(0), refs[0][0])         # still the normal run's matrix
+        pk, counts = B.run(*ht.Batch.concat(evs[:3]), peaks_only=True)
+        _check_events(evs[:3], pk, counts, refs[:3])
+        pk, counts = B.run(x, y, z, off)                       # normal again
+        _check_events(evs, pk, counts, refs)
+        dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
+        doff = torch.from_numpy(off.astype(np.int32)).cuda()
+        out = torch.zeros((1 << 16) * 8, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(len(evs), dtype=torch.int32, device="cuda")
+        B.run_device(dx, dy, dz, doff, int(off[-1]), out, cnt, peaks_only=True)
+        B.sync()
+        total = sum(n for _, _, n in refs)
+        _check_events(evs, out.cpu().numpy().view(ht.PEAK_DTYPE)[:total], cnt.cpu().numpy().astype(np.uint32),
+                      refs)
+
+
 def test_event_alone_equals_event_in_batch(ht, uneven):
     evs, refs = uneven
     b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
