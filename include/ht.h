@@ -164,7 +164,7 @@ ht_status ht_find_maxima(ht_ctx *ctx, ht_peak *out, uint32_t capacity, uint32_t 
  * ht_find_maxima.  stream: cudaStream_t as void*, NULL = the default stream;
  * the call runs its kernels there and returns once they have finished.
  *
- * Scratch: one static device array of 5,337,344 bytes in the library, which
+ * Scratch: one static device array of 5,267,712 bytes in the library, which
  * every GPU that loads the library holds until the process exits.  Limits:
  * 1 <= n_events <= 4096 (else HT_E_INVAL); at most 262,144 peaks per call in
  * total and 128 chunks of the scan per CTA (else HT_E_NOMEM after the run,

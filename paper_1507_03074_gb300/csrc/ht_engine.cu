@@ -327,9 +327,9 @@ ht_status engine_configure(Engine &E, std::string *why)
         seq = std::max(seq, chunks_for(ws_rows, g.nb, E.fused_K, htk::fused_round(E.ws_fill.threads, E.fused_K)));
     }
     s.seq_max = seq;
-    const size_t desc_b = (size_t)grid_cap * seq * 8, bnd_b = (size_t)grid_cap * htk::kSeamChunks * 8;
-    const size_t cta_b = (size_t)grid_cap * 3 * 4;
-    const size_t need = desc_b + bnd_b + cta_b;
+    const size_t desc_b = (size_t)grid_cap * seq * 8;
+    const size_t cta_b = (size_t)grid_cap * 2 * 4;
+    const size_t need = desc_b + cta_b;
     if (need > E.book_bytes || grid_cap != E.grid_cap) {
         if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
             *why = std::string("synchronise before re-allocation: ") + cudaGetErrorString(e);
@@ -354,11 +354,9 @@ ht_status engine_configure(Engine &E, std::string *why)
     }
     char *p = static_cast<char *>(E.d_book);
     s.desc = reinterpret_cast<uint2 *>(p);
-    s.desc_bnd = reinterpret_cast<uint2 *>(p + desc_b);
-    uint32_t *cta = reinterpret_cast<uint32_t *>(p + desc_b + bnd_b);
+    uint32_t *cta = reinterpret_cast<uint32_t *>(p + desc_b);
     s.cta_nseq = cta;
     s.cta_total = cta + grid_cap;
-    s.cta_nbnd = cta + 2 * grid_cap;
     s.grid = scan_grid;
     E.fused_valid = false;
     return HT_OK;

@@ -94,7 +94,7 @@ struct Engine {
     float4 *d_list = nullptr;     // hit records unit by unit
     uint32_t list_cap = 0;
     uint4 *d_entries = nullptr;
-    void *d_book = nullptr;       // desc | desc_bnd | cta arrays
+    void *d_book = nullptr;       // desc | cta arrays
     uint32_t *d_ctr = nullptr;    // counter block (htk::CTR_*)
     size_t device_bytes = 0;
     uint64_t launches = 0;

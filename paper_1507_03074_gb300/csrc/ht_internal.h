@@ -55,9 +55,7 @@ struct ScanArgs {
     uint32_t *g_count;    // entries used (reset by k_order)
     uint2 *desc;          // [grid][seq_max] {base, n}
     uint32_t *cta_nseq;   // [grid] interior chunks
-    uint32_t *cta_total;  // [grid] entries (seam + interior)
-    uint32_t *cta_nbnd;   // [grid] seam chunks (fused fill only; 0 otherwise)
-    uint2 *desc_bnd;      // [grid][kSeamChunks] seam chunks {base, n}
+    uint32_t *cta_total;  // [grid] entries
     uint32_t *ev_count;   // [n_events] peaks per event (reset by k_order)
 };
 
@@ -97,8 +95,6 @@ cudaError_t launch_fill_peaks(const Geom &g, const Work &w, const FillCfg &c, co
 cudaError_t launch_clear(uint32_t *M, uint64_t words, uint32_t grid, cudaStream_t st);
 cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
 size_t scan_smem_bytes(const ScanArgs &a);
-// Chunks a fused-fill CTA may need for its seam rows (n_b <= 4096).
-constexpr uint32_t kSeamChunks = 8;
 
 // Layout of the counter block: [0] status, [1] entries used, [2] order
 // ticket, [3] binning ticket (reset by k_bin's last block), [4] next

@@ -728,8 +728,8 @@ struct ScanSmem {
     uint32_t pad;
 };
 
-// Where a CTA registers its chunks: the interior list (a.desc row of the
-// CTA, seq_max entries) or the seam list (a.desc_bnd row, kSeamChunks).
+// Where a CTA (or a handed-out fill item) registers its chunks: its row of
+// a.desc, seq_max entries.
 struct ChunkList {
     uint2 *desc;
     uint32_t cap;
@@ -954,7 +954,6 @@ __global__ void __launch_bounds__(256) k_scan_tma(Geom g, Work w, ScanArgs a)
     if (tid == 0) {
         a.cta_nseq[blockIdx.x] = min(nseq, a.seq_max);
         a.cta_total[blockIdx.x] = total;
-        a.cta_nbnd[blockIdx.x] = 0u;
     }
 }
 
@@ -985,7 +984,6 @@ __global__ void __launch_bounds__(256) k_scan_direct(Geom g, Work w, ScanArgs a)
     if (tid == 0) {
         a.cta_nseq[blockIdx.x] = min(nseq, a.seq_max);
         a.cta_total[blockIdx.x] = total;
-        a.cta_nbnd[blockIdx.x] = 0u;
     }
 }
 
@@ -1188,7 +1186,6 @@ __device__ __forceinline__ void finish_candidates(const Work &w, const ScanArgs 
 {
     flush_chunk<G>(a, ss, pbuf, buf_n, nseq, inner, w.status);
     if (G::rank() == 0) {
-        a.cta_nbnd[cta] = 0u;
         a.cta_nseq[cta] = min(nseq, a.seq_max);
         a.cta_total[cta] = total;
     }
@@ -1865,7 +1862,6 @@ __global__ void __launch_bounds__(256) k_scan_ldg(Geom g, Work w, ScanArgs a)
     if (tid == 0) {
         a.cta_nseq[blockIdx.x] = min(nseq, a.seq_max);
         a.cta_total[blockIdx.x] = total;
-        a.cta_nbnd[blockIdx.x] = 0u;
     }
 }
 
@@ -1881,8 +1877,8 @@ __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, Order
     __shared__ uint32_t s_last;
     const uint32_t tid = threadIdx.x, bd = blockDim.x, c = blockIdx.x;
     // this CTA's chunk counts and first descriptor, loaded ahead of the prefix
-    const uint32_t nbnd = a.cta_nbnd[c], nseq = a.cta_nseq[c];
-    const uint2 d0 = nbnd ? a.desc_bnd[(size_t)c * kSeamChunks] : nseq ? a.desc[(size_t)c * a.seq_max] : make_uint2(0u, 0u);
+    const uint32_t nseq = a.cta_nseq[c];
+    const uint2 d0 = nseq ? a.desc[(size_t)c * a.seq_max] : make_uint2(0u, 0u);
 
     // rank of this CTA's first entry
     uint32_t part = 0;
@@ -1900,12 +1896,9 @@ __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, Order
     __syncthreads();
     block_exclusive_scan(ev_base, w.n_events, red);
 
-    // the CTA's seam chunks come before its interior chunks
     uint32_t P = prefix;
-    for (uint32_t q = 0; q < nbnd + nseq; ++q) {
-        const uint2 d = q == 0 ? d0
-                      : q < nbnd ? a.desc_bnd[(size_t)c * kSeamChunks + q]
-                                 : a.desc[(size_t)c * a.seq_max + (q - nbnd)];
+    for (uint32_t q = 0; q < nseq; ++q) {
+        const uint2 d = q == 0 ? d0 : a.desc[(size_t)c * a.seq_max + q];
         for (uint32_t k = tid; k < d.y; k += bd) {
             if (d.x + k >= a.entries_cap)
                 break;

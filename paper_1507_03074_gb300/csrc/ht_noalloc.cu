@@ -37,16 +37,14 @@ constexpr uint32_t kPeakBuf = 1024;        // K: entries buffered per scan CTA
 constexpr uint32_t kThreads = 256;         // scan block size
 
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
-// layout: counter block | cta_nseq | cta_total | cta_nbnd | desc_bnd | desc | entries
+// layout: counter block | cta_nseq | cta_total | desc | entries
 constexpr size_t kOffCtr = 0;
 constexpr size_t kOffNseq = align256(kOffCtr + (size_t)(htk::CTR_EVENTS + kMaxEvents) * 4);
 constexpr size_t kOffTotal = align256(kOffNseq + (size_t)kMaxGrid * 4);
-constexpr size_t kOffNbnd = align256(kOffTotal + (size_t)kMaxGrid * 4);
-constexpr size_t kOffBnd = align256(kOffNbnd + (size_t)kMaxGrid * 4);
-constexpr size_t kOffDesc = align256(kOffBnd + (size_t)kMaxGrid * htk::kSeamChunks * 8);
+constexpr size_t kOffDesc = align256(kOffTotal + (size_t)kMaxGrid * 4);
 constexpr size_t kOffEntries = align256(kOffDesc + (size_t)kMaxGrid * kMaxSeq * 8);
 constexpr size_t kScratchBytes = align256(kOffEntries + (size_t)kMaxEntries * 16);
-static_assert(kScratchBytes == 5337344, "the static scratch is stated as 5,337,344 bytes");
+static_assert(kScratchBytes == 5267712, "the static scratch is stated as 5,267,712 bytes");
 
 // The scratch.  In host code this name is only a handle for
 // cudaGetSymbolAddress, never a device address.
@@ -169,8 +167,6 @@ extern "C" ht_status ht_find_maxima_noalloc(const ht_binning *binning, const ht_
     a.desc = reinterpret_cast<uint2 *>(base + kOffDesc);
     a.cta_nseq = reinterpret_cast<uint32_t *>(base + kOffNseq);
     a.cta_total = reinterpret_cast<uint32_t *>(base + kOffTotal);
-    a.cta_nbnd = reinterpret_cast<uint32_t *>(base + kOffNbnd);
-    a.desc_bnd = reinterpret_cast<uint2 *>(base + kOffBnd);
     a.ev_count = ctr + htk::CTR_EVENTS;
 
     htk::OrderArgs o{};
