@@ -359,6 +359,7 @@ def run_ours(args, rank, world):
         res["maxima_4d"] = run_maxima4d(ctx, dev, out, cnt, cap, st, args.steps, args.warmup)
         res["readout"] = run_readout(ctx, events, b, r)
         res["sectors"] = run_sectors(dev, b, r, max_hits, args.steps, args.warmup, peaks)
+        res["components"] = run_components(dev, b, r, max_hits, float(np.mean(votes)), hbm_peak)
     ctx.close()
     if not args.no_extras and world == 1:
         res["batched"] = run_batched()
@@ -366,6 +367,56 @@ def run_ours(args, rank, world):
     if not args.no_cpu_baseline and world == 1:
         res["cpu_baseline"] = cpu_baseline(budget_s=10.0)
     return res
+
+
+# ---------------------------------------------------------------------------
+# The step's components against their own rooflines: the two-kernel path
+# (privatised fill, then the standalone streaming scan) against HBM, and the
+# paper's naive fill (one global atomic per vote) against measured L2 atomics
+# ---------------------------------------------------------------------------
+def run_components(dev, b, r, max_hits, mean_votes, hbm_peak, steps=200):
+    import torch
+    from paper_1507_03074_gb300 import ht
+
+    st = torch.cuda.Stream()
+    out = torch.empty(65536 * 8, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int32, device="cuda")
+    cells_bytes = b.n_cells * 4
+
+    def profile(tuning, naive):
+        with ht.Context(b, r, threshold=THRESHOLD, max_hits=max_hits) as ctx:
+            ctx.set_tuning(**tuning)
+            for k in range(10):
+                ctx.fill(*dev[k % N_POOL], naive=naive, stream=st)
+                ctx.find_maxima(capacity=65536, out=out, count=cnt, stream=st)
+            st.synchronize()
+            ctx.profile(True)
+            for k in range(steps):
+                ctx.fill(*dev[k % N_POOL], naive=naive, stream=st)
+                ctx.find_maxima(capacity=65536, out=out, count=cnt, stream=st)
+            p = ctx.profile_read()
+            ctx.profile(False)
+        return {kn: t / n * 1e3 for kn, (n, t) in p.items() if n}
+
+    two = profile({"fill_fused_scan": 2}, False)
+    naive = profile({"fill_fused_scan": 2}, True)
+    l2_res = ht.measure_atomics(32 << 20)
+    l2_hbm = ht.measure_atomics(256 << 20)
+    fill_us, scan_us = two.get("k_fill_priv"), two.get("k_scan")
+    nv_us = naive.get("k_fill_naive")
+    return {
+        "fill_priv": {"avg_us": round(fill_us, 2), "gbs_written": round(cells_bytes / fill_us / 1e3, 1),
+                      "frac_of_hbm": round(cells_bytes / fill_us / 1e3 / hbm_peak, 4)},
+        "scan_stream": {"avg_us": round(scan_us, 2), "gbs_read": round(cells_bytes / scan_us / 1e3, 1),
+                        "frac_of_hbm": round(cells_bytes / scan_us / 1e3 / hbm_peak, 4)},
+        "fill_naive": {"avg_us": round(nv_us, 2), "clear_us": round(naive.get("k_clear", 0.0), 2),
+                       "gvotes_per_s": round(mean_votes / nv_us / 1e3, 3),
+                       "frac_of_l2_atomics_256mib": round(mean_votes / nv_us * 1e6 / l2_hbm, 4)},
+        "l2_atomics": {"gupdates_per_s_32mib": round(l2_res / 1e9, 2), "gupdates_per_s_256mib": round(l2_hbm / 1e9, 2),
+                       "note": "ht_measure_atomics: red.global.add at pseudo-random words, 8 x 256 threads per SM"},
+        "note": "per-kernel CUDA-event averages over 200 events (fill_fused_scan=2: k_fill_priv then k_scan; "
+                "HT_FILL_NAIVE: k_clear then k_fill_naive); bytes = 4 per M_H cell; peak = measured HBM copy",
+    }
 
 
 # ---------------------------------------------------------------------------

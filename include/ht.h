@@ -180,6 +180,16 @@ ht_status ht_find_maxima_noalloc(const ht_binning *binning, const ht_ranges *ran
                                  const uint32_t *M, uint32_t n_events, ht_peak *out, uint32_t capacity,
                                  uint32_t *counts, void *stream);
 
+/* Measurement helper (no counterpart in the paper): the rate of L2 atomic
+ * increments (reductions, result unused) at pseudo-random 4-byte words of a
+ * device buffer of footprint_bytes (a power of two, 4 KiB .. 16 GiB),
+ * updates_per_thread (1 .. 4096) per thread of 8 CTAs x 256 threads per SM,
+ * timed with CUDA events after one warm-up launch on the current device.
+ * The roofline the naive fill's votes are compared with.  *updates_per_s
+ * receives the rate.  Blocks; allocates and frees the buffer.  Errors:
+ * HT_E_INVAL, HT_E_NOMEM, HT_E_CUDA. */
+ht_status ht_measure_atomics(uint64_t footprint_bytes, uint32_t updates_per_thread, double *updates_per_s);
+
 /* Exercise the failure path of the kernels' bounded waits: one device
  * thread waits on a barrier that nothing completes, gives up after
  * limit_ms (1 .. 1000) and flags the timeout as a real wait would.  Waits

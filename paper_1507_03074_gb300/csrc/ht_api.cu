@@ -269,6 +269,49 @@ ht_status ht_sync(ht_ctx *ctx, void *stream)
     return read_status(ctx, st);
 }
 
+ht_status ht_measure_atomics(uint64_t footprint_bytes, uint32_t updates_per_thread, double *updates_per_s)
+{
+    if (!updates_per_s || footprint_bytes < 4096 || footprint_bytes > (1ull << 34) ||
+        (footprint_bytes & (footprint_bytes - 1)) || updates_per_thread < 1 || updates_per_thread > 4096)
+        return set_err(HT_E_INVAL, "footprint_bytes: a power of two in 4 KiB .. 16 GiB; updates_per_thread 1 .. 4096");
+    int dev = 0, sms = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return set_err(HT_E_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+    uint32_t *buf = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    const uint32_t grid = (uint32_t)sms * 8u;
+    const uint32_t mask = (uint32_t)(footprint_bytes / 4 - 1);
+    float ms = 0.f;
+    if ((e = cudaMalloc(&buf, footprint_bytes)) == cudaSuccess &&
+        (e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) == cudaSuccess &&
+        (e = cudaEventCreate(&a)) == cudaSuccess && (e = cudaEventCreate(&b)) == cudaSuccess &&
+        (e = cudaMemsetAsync(buf, 0, footprint_bytes, st)) == cudaSuccess &&
+        (e = htk::launch_atomic_rate(buf, mask, updates_per_thread, 1u, grid, st)) == cudaSuccess &&   // warm-up
+        (e = cudaEventRecord(a, st)) == cudaSuccess &&
+        (e = htk::launch_atomic_rate(buf, mask, updates_per_thread, 2u, grid, st)) == cudaSuccess &&
+        (e = cudaEventRecord(b, st)) == cudaSuccess && (e = cudaEventSynchronize(b)) == cudaSuccess)
+        e = cudaEventElapsedTime(&ms, a, b);
+    if (st)
+        cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (a)
+        cudaEventDestroy(a);
+    if (b)
+        cudaEventDestroy(b);
+    if (st)
+        cudaStreamDestroy(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(e == cudaErrorMemoryAllocation ? HT_E_NOMEM : HT_E_CUDA,
+                       std::string("atomic rate measurement: ") + cudaGetErrorString(e));
+    }
+    *updates_per_s = (double)grid * 256.0 * updates_per_thread / (ms * 1e-3);
+    return HT_OK;
+}
+
 ht_status ht_check_wait_timeout(ht_ctx *ctx, uint32_t limit_ms)
 {
     ht_status s = check_ctx(ctx);

@@ -126,6 +126,10 @@ enum ScanKind { SCAN_DIRECT = 0, SCAN_BULK = 1, SCAN_LDG = 2 };
 cudaError_t launch_scan(const Geom &g, const Work &w, const ScanArgs &a, int kind, cudaStream_t st);
 cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const OrderArgs &o,
                          cudaStream_t st);
+// L2 atomic increments at pseudo-random words of buf (mask + 1 words,
+// per_thread per thread, 256 threads per CTA).
+cudaError_t launch_atomic_rate(uint32_t *buf, uint32_t mask, uint32_t per_thread, uint32_t seed, uint32_t grid,
+                               cudaStream_t st);
 // One bounded wait that nothing ends (k_wait_probe): flags ST_WAIT_TIMEOUT
 // after limit_ms (at most about a second).
 cudaError_t launch_wait_probe(uint32_t *status, uint32_t limit_ms, cudaStream_t st);

@@ -2277,6 +2277,28 @@ cudaError_t launch_peaks4d(const Geom &g, const uint32_t *M, const Peak *in, con
                       ticket, status);
 }
 
+// ---------------------------------------------------------------------------
+// k_atomic_rate: the L2-atomic roofline the naive fill is measured against.
+// Every thread adds 1 to per_thread words of buf picked by a linear
+// congruential sequence of its own (masked to the footprint, a power of two
+// words); the results are unused, so the adds are reductions performed in L2.
+// ---------------------------------------------------------------------------
+__global__ void k_atomic_rate(uint32_t *buf, uint32_t mask, uint32_t per_thread, uint32_t seed)
+{
+    uint32_t x = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u ^ seed;
+    for (uint32_t i = 0; i < per_thread; ++i) {
+        x = x * 1664525u + 1013904223u;
+        atomicAdd(&buf[(x >> 4) & mask], 1u);
+    }
+}
+
+cudaError_t launch_atomic_rate(uint32_t *buf, uint32_t mask, uint32_t per_thread, uint32_t seed, uint32_t grid,
+                               cudaStream_t st)
+{
+    k_atomic_rate<<<grid, 256, 0, st>>>(buf, mask, per_thread, seed);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const OrderArgs &o,
                          cudaStream_t st)
 {

@@ -133,6 +133,7 @@ def lib():
         "ht_find_maxima": ([P, P, U32, P, U32, P], I),
         "ht_sync": ([P, P], I),
         "ht_check_wait_timeout": ([P, U32], I),
+        "ht_measure_atomics": ([U64, U32, ctypes.POINTER(ctypes.c_double)], I),
         "ht_copy_matrix": ([P, P, U64, U32, P], I),
         "ht_get_edges": ([P, P, P], I),
         "ht_launch_count": ([P], U64),
@@ -205,6 +206,14 @@ def compute_b_thresholds(binning: Binning, ranges: Ranges = Ranges()):
     b, r = binning.c(), ranges.c()
     check(lib().ht_compute_b_thresholds(ctypes.byref(b), ctypes.byref(r), beta.ctypes.data_as(ctypes.c_void_p)))
     return beta
+
+
+def measure_atomics(footprint_bytes: int, updates_per_thread: int = 64) -> float:
+    """ht_measure_atomics: L2 atomic increments per second at random words of
+    a footprint_bytes device buffer."""
+    r = ctypes.c_double()
+    check(lib().ht_measure_atomics(int(footprint_bytes), int(updates_per_thread), ctypes.byref(r)))
+    return float(r.value)
 
 
 def track_params(binning: Binning, ranges: Ranges, peaks, b_field_t: float = 2.0):

@@ -586,3 +586,15 @@ def test_bounded_wait_gives_up_and_context_survives(ht):
         assert n == n_ref
         assert_peaks_equal(pk, pk_ref)
         assert np.array_equal(ctx.matrix(), M_ref)
+
+
+def test_measure_atomics(ht):
+    """The L2-atomic roofline helper: a positive rate, an L2-resident
+    footprint no slower than one 8x larger, bad sizes refused."""
+    small = ht.measure_atomics(32 << 20, 16)
+    big = ht.measure_atomics(256 << 20, 16)
+    assert small > 1e9 and big > 1e8
+    assert small > 0.5 * big
+    for fp, per in ((3 << 20, 16), (1024, 16), (32 << 20, 0), (32 << 20, 5000)):
+        with pytest.raises(ht.HTError):
+            ht.measure_atomics(fp, per)
