@@ -1044,18 +1044,18 @@ __device__ __forceinline__ void emit_pass(const Geom &g, const Work &w, const Sc
             srt[rank] = key;
             srtv[rank] = candv[k];
         }
-        G::sync();
-        const uint32_t rc = fused_round(bd, a.K);
-        for (uint32_t base = 0; base < n_c; base += rc) {
-            const uint32_t k = base + tid;
-            const uint32_t has = (tid < rc && k < n_c) ? 1u : 0u;
-            const uint4 ent = has ? make_uint4(lin0 + srt[k], e, srtv[k], 0u) : make_uint4(0u, 0u, 0u, 0u);
-            if (buf_n + rc > a.K)
-                flush_chunk<G>(a, ss, pbuf, buf_n, nseq, inner, w.status);
-            compact_entry<G, false>(ss, pbuf, buf_n, has, ent, nullptr);
-            total += ss.round_total;
-        }
-        return;
+        // the sorted list is dense: append it to the chunk buffer as it is
+        // (n_c <= kFusedCand <= K; a chunk is flushed with more than
+        // K - kFusedCand entries, so the chunk bound of the rounds below holds)
+        if (buf_n + n_c > a.K)
+            flush_chunk<G>(a, ss, pbuf, buf_n, nseq, inner, w.status);   // its barriers order srt / srtv too
+        else
+            G::sync();
+        for (uint32_t k = tid; k < n_c; k += bd)
+            pbuf[buf_n + k] = make_uint4(lin0 + srt[k], e, srtv[k], 0u);
+        buf_n += n_c;
+        total += n_c;
+        return;   // the caller's barrier follows before pbuf or the lists are used again
     }
     // rounds of rc threads, like the candidate rounds: a chunk is flushed
     // only when fewer than rc entries are free
