@@ -360,6 +360,7 @@ def run_ours(args, rank, world):
         res["readout"] = run_readout(ctx, events, b, r)
         res["sectors"] = run_sectors(dev, b, r, max_hits, args.steps, args.warmup, peaks)
         res["components"] = run_components(dev, b, r, max_hits, float(np.mean(votes)), hbm_peak)
+        res["upgrade"] = run_upgrade(hbm_peak)
     ctx.close()
     if not args.no_extras and world == 1:
         res["batched"] = run_batched()
@@ -417,6 +418,51 @@ def run_components(dev, b, r, max_hits, mean_votes, hbm_peak, steps=200):
         "note": "per-kernel CUDA-event averages over 200 events (fill_fused_scan=2: k_fill_priv then k_scan; "
                 "HT_FILL_NAIVE: k_clear then k_fill_naive); bytes = 4 per M_H cell; peak = measured HBM copy",
     }
+
+
+# ---------------------------------------------------------------------------
+# High-occupancy upgrade-like events: 50 000 hits, M_H 8x32x2048x2048 u32 (4 GiB)
+# ---------------------------------------------------------------------------
+def run_upgrade(hbm_peak, n_events=4, steps=20):
+    import torch
+    from paper_1507_03074_gb300 import ht
+
+    b, r = ht.Binning(*synth.UPGRADE_BINNING), ht.Ranges()
+    evs = [synth.upgrade_event(i) for i in range(n_events)]
+    st = torch.cuda.Stream()
+    out = torch.empty(65536 * 8, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int32, device="cuda")
+    with ht.Context(b, r, threshold=THRESHOLD, max_hits=max(e.n_hits for e in evs)) as ctx:
+        dev = [tuple(torch.from_numpy(a).cuda() for a in (e.x, e.y, e.z)) for e in evs]
+
+        def step(k):
+            ctx.fill(*dev[k % n_events], stream=st)
+            ctx.find_maxima(capacity=65536, out=out, count=cnt, stream=st)
+
+        for k in range(3):
+            step(k)
+        st.synchronize()
+        a, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            a.record(st)
+            for k in range(steps):
+                step(k)
+            e_.record(st)
+        st.synchronize()
+        ms = a.elapsed_time(e_) / steps
+        ctx.profile(True)
+        for k in range(4):
+            step(k)
+        prof = ctx.profile_read()
+        ctx.profile(False)
+    kern = {kn: t / n * 1e3 for kn, (n, t) in prof.items() if n}
+    fill_us = kern.get("k_fill_scan")
+    cells_bytes = b.n_cells * 4
+    return {"workload": "50 000 hits (3750 tracks + 5000 noise), M_H 8x32x2048x2048 u32 (4 GiB), threshold 10",
+            "events_per_s": round(1e3 / ms, 2), "ms_per_event": round(ms, 4),
+            "kernels_us": {kn: round(v, 1) for kn, v in kern.items()},
+            "fill_gbs": round(cells_bytes / fill_us / 1e3, 1) if fill_us else None,
+            "fill_frac_of_hbm": round(cells_bytes / fill_us / 1e3 / hbm_peak, 4) if fill_us else None}
 
 
 # ---------------------------------------------------------------------------
