@@ -208,7 +208,7 @@ def run_ours(args, rank, world):
     st.synchronize()
 
     # votes per pool event (outside the timed region)
-    votes, peaks = [], []
+    votes, peaks, cands = [], [], []
     for k in range(N_POOL):
         ctx.fill(*dev[k], naive=args.naive, stream=st)
         ctx.find_maxima(capacity=cap, out=out, count=cnt, stream=st)
@@ -216,6 +216,7 @@ def run_ours(args, rank, world):
         st.synchronize()
         votes.append(int(M.to(torch.int64).sum().item()))
         peaks.append(int(cnt.item()))
+        cands.append(ctx.last_admitted() * b.n_a)
     ctx.sync()
     del M
     # pick launch shapes on this workload (outside the timed region)
@@ -332,6 +333,8 @@ def run_ours(args, rank, world):
                    "l2": "inputs larger than L2: each step writes a 256 MiB M_H (L2 129 MB), read back at its candidates",
                    "parallelism": f"replicas x{world}"},
         "gvotes_per_s": round(value * mean_votes / 1e9, 3),
+        "gcandidates_per_s": round(value * float(np.mean(cands)) / 1e9, 3),
+        "candidates_per_event": int(np.mean(cands)),
         "votes_per_event": int(mean_votes), "peaks_per_event": float(np.mean(peaks)),
         "latency_ms": {"device_p50": round(float(np.percentile(per_step, 50)), 4),
                        "device_p99": round(float(np.percentile(per_step, 99)), 4),

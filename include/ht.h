@@ -190,6 +190,12 @@ ht_status ht_find_maxima_noalloc(const ht_binning *binning, const ht_ranges *ran
  * HT_E_INVAL, HT_E_NOMEM, HT_E_CUDA. */
 ht_status ht_measure_atomics(uint64_t footprint_bytes, uint32_t updates_per_thread, double *updates_per_s);
 
+/* Admitted (hit, slice) records of the last fill (its unit lists' total
+ * length; times n_a: the (hit, slice, A) candidate evaluations).  Waits for
+ * the device; 0 before any fill.  Errors: HT_E_INVAL, HT_E_CUDA,
+ * HT_E_STATE. */
+ht_status ht_last_admitted(ht_ctx *ctx, uint64_t *records);
+
 /* Exercise the failure path of the kernels' bounded waits: one device
  * thread waits on a barrier that nothing completes, gives up after
  * limit_ms (1 .. 1000) and flags the timeout as a real wait would.  Waits

@@ -323,6 +323,27 @@ ht_status ht_check_wait_timeout(ht_ctx *ctx, uint32_t limit_ms)
     return read_status(ctx, ctx->stream);   // HT_E_TIMEOUT, counters reset
 }
 
+ht_status ht_last_admitted(ht_ctx *ctx, uint64_t *records)
+{
+    ht_status s = check_ctx(ctx);
+    if (s != HT_OK)
+        return s;
+    if (!records)
+        return set_err(HT_E_INVAL, "records must not be NULL");
+    if (!ctx->E.last_n_events) {
+        *records = 0;
+        return HT_OK;
+    }
+    // the unit lists' total length: the last offset of the last fill's units
+    const uint64_t units = (uint64_t)ctx->E.last_n_events * ctx->E.geom.n_slices;
+    const size_t max_units = (size_t)ctx->E.max_events * ctx->E.geom.n_slices;
+    const uint32_t *d_off = ctx->E.d_slice + 2 * max_units;
+    CK(cudaDeviceSynchronize());   // the fill may have run on any stream
+    CK(cudaMemcpy(ctx->h_small + 2, d_off + units, 4, cudaMemcpyDeviceToHost));
+    *records = ctx->h_small[2];
+    return HT_OK;
+}
+
 ht_status ht_copy_matrix(ht_ctx *ctx, uint32_t *dst, uint64_t n_cells, uint32_t flags, void *stream)
 {
     ht_status s = check_ctx(ctx);

@@ -133,6 +133,7 @@ def lib():
         "ht_find_maxima": ([P, P, U32, P, U32, P], I),
         "ht_sync": ([P, P], I),
         "ht_check_wait_timeout": ([P, U32], I),
+        "ht_last_admitted": ([P, ctypes.POINTER(ctypes.c_uint64)], I),
         "ht_measure_atomics": ([U64, U32, ctypes.POINTER(ctypes.c_double)], I),
         "ht_copy_matrix": ([P, P, U64, U32, P], I),
         "ht_get_edges": ([P, P, P], I),
@@ -379,6 +380,12 @@ class Context:
 
     def sync(self, stream=None):
         check(lib().ht_sync(self._h, _stream_ptr(stream)))
+
+    def last_admitted(self) -> int:
+        """ht_last_admitted: admitted (hit, slice) records of the last fill."""
+        n = ctypes.c_uint64()
+        check(lib().ht_last_admitted(self._h, ctypes.byref(n)))
+        return int(n.value)
 
     def check_wait_timeout(self, limit_ms: int = 50) -> int:
         """ht_check_wait_timeout: run one bounded device wait that nothing

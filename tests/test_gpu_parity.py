@@ -598,3 +598,15 @@ def test_measure_atomics(ht):
     for fp, per in ((3 << 20, 16), (1024, 16), (32 << 20, 0), (32 << 20, 5000)):
         with pytest.raises(ht.HTError):
             ht.measure_atomics(fp, per)
+
+
+def test_last_admitted_counts_the_oracle_admissions(ht):
+    """ht_last_admitted: the admitted (hit, slice) records of the last fill
+    equal the oracle's admission count (windows included)."""
+    for name, bins, rng, T, (x, y, z) in (CASES[1], CASES[4]):
+        b, r = ht.Binning(*bins), ht.Ranges(**rng)
+        _, cnt = oracle.admit(_ob(b), _orr(r), x, y, z)
+        with ht.Context(b, r, threshold=T, max_hits=max(len(x), 1)) as ctx:
+            assert ctx.last_admitted() == 0
+            ctx.fill(x, y, z)
+            assert ctx.last_admitted() == int(np.asarray(cnt).sum()), name
