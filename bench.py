@@ -65,12 +65,17 @@ def parse():
 # ---------------------------------------------------------------------------
 
 def dist_init(n):
+    """Rank and world size from the launcher's environment; one process per
+    GPU over NCCL (gloo where no GPU is visible, e.g. the CPU reference arm)."""
     rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
     if world > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
     return rank, world
 
 
@@ -81,13 +86,21 @@ def barrier(world):
 
 
 def max_over_ranks(v, world):
+    """The largest of every rank's v (the slowest replica's time)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_event_seeds(rank, n=None):
+    """Seeds of a replica's resident events: disjoint across ranks."""
+    n = N_POOL if n is None else n
+    return [1 + rank * 1000 + k for k in range(n)]
 
 
 # ---------------------------------------------------------------------------
@@ -193,7 +206,7 @@ def run_ours(args, rank, world):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
-    events = [synth.paper_event(seed=1 + rank * 1000 + k) for k in range(N_POOL)]
+    events = [synth.paper_event(seed=sd) for sd in rank_event_seeds(rank)]
     max_hits = max(e.n_hits for e in events)
     ctx = ht.Context(b, r, threshold=THRESHOLD, max_hits=max_hits)
     st = torch.cuda.Stream()
