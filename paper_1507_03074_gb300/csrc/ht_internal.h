@@ -113,7 +113,7 @@ constexpr uint32_t kVoteWeight = 6;
 
 // Scan variants: bulk-copy (TMA) ring, register streaming, direct (any n_b).
 // The streaming variant keeps kLdgUPT 16-byte loads per thread in flight.
-constexpr uint32_t kLdgUPT = 4;
+constexpr uint32_t kLdgUPT = 8;
 // Candidate cells (>= threshold) a streaming-scan CTA lists before testing them.
 constexpr uint32_t kCand = 1024;
 // Candidate cells a fused-fill CTA lists per pass; a pass with more emits
