@@ -1034,6 +1034,21 @@ __device__ __forceinline__ void emit_pass(const Geom &g, const Work &w, const Sc
 {
     const uint32_t tid = G::rank(), bd = G::size(), nb = g.nb;
     const uint32_t lin0 = slice_lin0 + iA * nb;
+    if (n_c <= 32u) {
+        // few candidates: the first warp ranks them and writes them in order
+        if (buf_n + n_c > a.K)
+            flush_chunk<G>(a, ss, pbuf, buf_n, nseq, inner, w.status);
+        if (tid < n_c) {
+            const uint32_t key = cand[tid];
+            uint32_t rank = 0;
+            for (uint32_t m = 0; m < n_c; ++m)
+                rank += cand[m] < key;
+            pbuf[buf_n + rank] = make_uint4(lin0 + key, e, candv[tid], 0u);
+        }
+        buf_n += n_c;
+        total += n_c;
+        return;   // the caller's barrier follows before pbuf or the lists are used again
+    }
     if (n_c <= kFusedCand) {
         // distinct keys: the rank of a key is the number of smaller ones
         for (uint32_t k = tid; k < n_c; k += bd) {
@@ -1117,7 +1132,7 @@ __device__ __forceinline__ void flush_emit_pass(const Geom &g, const Work &w, co
     uint32_t *cand = lists, *candv = lists + kFusedCand, *srt = lists + 2 * kFusedCand, *srtv = lists + 3 * kFusedCand;
     if (G::rank() == 0)
         s_hot[0] = s_hot[1] = *s_nc = 0u;
-    G::sync();
+    G::sync();   // the pass's votes are complete (and the counters zero)
     flush_tile<U16, true, false, G>(g, tile, dst, pr, pitch, FlushList{s_hot, cand, candv, s_nc, kFusedCand});
     if (empty_bar)
         mbar_arrive(empty_bar);   // the tile is clear
