@@ -1264,10 +1264,11 @@ __device__ __forceinline__ void fill_scan_body(const Geom &g, const Work &w, con
         for (uint32_t p0 = 0; p0 < rows; p0 += rpass) {
             const uint32_t pr = min(rpass, rows - p0);
             const uint32_t iA = i0 + p0;
-            // ---- vote -------------------------------------------------------
+            // ---- vote (no barrier first: the previous pass, the previous item's
+            // hand-out or the set-up ended with one) ---------------------------
             const uint32_t i = iA + r;
-            vote_pass<BlockGroup, true, false>(g, w, tile, hs, beta, c.HC, es, l0, l1, cached_es, cached_n, u16, r, pr,
-                                               i, hl, hstride, pitch, FlushList{});
+            vote_pass<BlockGroup, false, false>(g, w, tile, hs, beta, c.HC, es, l0, l1, cached_es, cached_n, u16, r, pr,
+                                                i, hl, hstride, pitch, FlushList{});
             // ---- write the pass, clear the tile, emit its candidates --------
             if (BULK) {
                 if (u16)
