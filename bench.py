@@ -381,6 +381,8 @@ def run_ours(args, rank, world):
     if not args.no_extras and world == 1:
         res["batched"] = run_batched()
         res["serving"] = run_serving(args.serving_seconds)
+        res["serving_peaks_only"] = run_serving(args.serving_seconds, rates=(10000, 50000), peaks_only=True,
+                                                per_event=False)
     if not args.no_cpu_baseline and world == 1:
         res["cpu_baseline"] = cpu_baseline(budget_s=10.0)
     return res
@@ -732,7 +734,8 @@ def run_batched(n_events=100, reps=5):
     return res
 
 
-def run_serving(seconds=1.5, rates=(1000, 10000, 50000), pool_per_kind=48, warmup_s=1.0):
+def run_serving(seconds=1.5, rates=(1000, 10000, 50000), pool_per_kind=48, warmup_s=1.0, peaks_only=False,
+                per_event=True):
     """Poisson arrivals at each rate for `seconds`; hit counts lognormal
     (median 3000, sigma 1, clipped 200..50000); 90% binning 4x16x1024x1024,
     10% 8x32x2048x2048; threshold 10.  Requests reuse a pool of seeded events
@@ -758,7 +761,9 @@ def run_serving(seconds=1.5, rates=(1000, 10000, 50000), pool_per_kind=48, warmu
     sys.setswitchinterval(1e-4)          # let the polling thread run beside the arrival loop
     out = {"workload": "Poisson arrivals; hits lognormal(median 3000, sigma 1) clipped 200..50000; "
                        "90% 4x16x1024x1024 / 10% 8x32x2048x2048 u32; threshold 10", "rates": []}
-    with ht.Server() as S:
+    if peaks_only:
+        out["workload"] += "; peaks-only lanes (HT_PEAKS_ONLY: the matrices are not written)"
+    with ht.Server(peaks_only=peaks_only) as S:
         # warm-up: lanes of both binnings
         warm = [S.submit(bins[k], r, THRESHOLD, *pools[k][i]) for k in (False, True) for i in range(4)]
         for t in warm:
@@ -822,6 +827,8 @@ def run_serving(seconds=1.5, rates=(1000, 10000, 50000), pool_per_kind=48, warmu
                                "max": round(st["max_us"] / 1e3, 4)},
                 "mean_micro_batch": round(st["mean_batch"], 2), "lanes": st["lanes"],
                 "lane_gib": round(st["lane_bytes"] / 2**30, 2)})
+    if not per_event:
+        return out
     # the plain per-event path on the same streams: one context per binning,
     # each arrival filled and scanned on its own (blocking), in arrival order;
     # latency = completion - arrival (queueing included)

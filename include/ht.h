@@ -363,6 +363,8 @@ typedef struct {
     uint32_t max_batch;          /* events per micro-batch; 0 = 16 */
     uint32_t max_hits_per_event; /* 0 = 65536 */
     uint32_t queue_depth;        /* waiting requests before ht_submit answers HT_E_BUSY; 0 = 65536 */
+    uint32_t flags;              /* 0, or HT_PEAKS_ONLY: every micro-batch runs peaks-only fills (the
+                                    same peaks; the lanes' matrices are not written) */
 } ht_server_cfg;
 
 /* Create on the current CUDA device (cfg NULL = all defaults). */

@@ -236,6 +236,12 @@ Lane *make_lane(ht_server *s, const Key &k, bool *never)
         hte::runner_destroy(l->R);
         return nullptr;
     }
+    if ((c.flags & HT_PEAKS_ONLY) && hte::engine_ensure_edges(l->R.E, &why) != HT_OK) {
+        cudaGetLastError();
+        cudaStreamDestroy(l->st);
+        hte::runner_destroy(l->R);
+        return nullptr;
+    }
     l->bytes = std::max<uint64_t>(need, l->R.E.device_bytes);
     l->last_used = Clock::now();
     std::lock_guard<std::mutex> g(s->mu);
@@ -263,7 +269,8 @@ bool dispatch(ht_server *s, Lane &l, std::vector<Request *> &&reqs)
     l.reqs = std::move(reqs);
     l.busy = true;
     l.complete.store(false, std::memory_order_relaxed);
-    cudaError_t e = hte::runner_enqueue(R, (uint32_t)l.reqs.size(), off, true, true, l.st);
+    cudaError_t e = hte::runner_enqueue(R, (uint32_t)l.reqs.size(), off, true, true, l.st,
+                                        (s->cfg.flags & HT_PEAKS_ONLY) != 0);
     if (e == cudaSuccess)
         e = cudaLaunchHostFunc(l.st, lane_done, &l);
     return e == cudaSuccess;
@@ -436,6 +443,8 @@ ht_status ht_server_create(const ht_server_cfg *cfg, ht_server **out)
         c.max_hits_per_event = 65536;
     if (!c.queue_depth)
         c.queue_depth = 65536;
+    if (c.flags & ~(uint32_t)HT_PEAKS_ONLY)
+        return hte::report(HT_E_INVAL, "server flags: 0 or HT_PEAKS_ONLY");
     if (c.n_streams > 64 || c.max_batch > 4096 || c.max_hits_per_event > (1u << 24))
         return hte::report(HT_E_INVAL, "n_streams <= 64, max_batch <= 4096, max_hits_per_event <= 2^24");
     ht_server *s = new (std::nothrow) ht_server();

@@ -101,3 +101,28 @@ def test_server_memory_budget(ht):
         # and the server keeps serving
         status, pk, n = _wait(S, S.submit(bins[1], r, 8, *evs[2]))
         _same(pk, refs[(1, 2)][0])
+
+
+def test_server_peaks_only_equals_alone(ht):
+    """A peaks-only server (HT_PEAKS_ONLY lanes): the same peaks as the event
+    processed alone with its matrix written, for two binnings in a burst."""
+    bA, TA = ht.Binning(*synth.PAPER_BINNING), 10
+    bB, TB = ht.Binning(2, 8, 256, 256), 6
+    r = ht.Ranges()
+    evA = [(e.x, e.y, e.z) for e in synth.batch_events(10, seed0=3200, lo=200, hi=5000)]
+    evB = [(e.x, e.y, e.z) for e in synth.batch_events(6, seed0=3300, lo=200, hi=3000)]
+    refA = [_alone(ht, bA, r, TA, ev) for ev in evA]
+    refB = [_alone(ht, bB, r, TB, ev) for ev in evB]
+    with ht.Server(n_streams=2, max_batch=4, peaks_only=True) as S:
+        tickets = [("A", i, S.submit(bA, r, TA, *ev)) for i, ev in enumerate(evA)]
+        tickets += [("B", i, S.submit(bB, r, TB, *ev)) for i, ev in enumerate(evB)]
+        for kind, i, t in tickets:
+            status, pk, n = _wait(S, t)
+            want_pk, want_n = (refA if kind == "A" else refB)[i]
+            assert n == want_n
+            _same(pk, want_pk)
+    # any other flag is refused at creation
+    import ctypes
+    cfg = ht.c_server_cfg(0, 0, 0, 0, 0, ht.HT_FILL_NAIVE)
+    h = ctypes.c_void_p()
+    assert ht.lib().ht_server_create(ctypes.byref(cfg), ctypes.byref(h)) == ht.HT_E_INVAL
