@@ -6,15 +6,22 @@ M_H binned 4 x 16 x 1024 x 1024), synthetic and seeded: 396 helix tracks +
 through the whole hot path: slice admission + counting sort, vote fill
 (privatised), threshold + local-maxima scan and ordered compaction.
 
-  value   events/s with hits already resident in HBM (device pointers),
-          CUDA events on the launching stream around the timed steps.
+  value   events/s with hits already resident in HBM (device pointers).
+          Events go round-robin to --contexts contexts, each with its own
+          stream, so that one event's small kernels and its fill's ragged
+          end overlap the next event's work; every event still runs through
+          its own per-event launches.  CUDA events on a stream that forks to
+          and joins the launching streams bracket the timed steps; every
+          step's peak count is checked.  `one_context` is the same with one
+          context (one event at a time).
   e2e     the same through the C ABI with host buffers: every step copies
           its hits host->device (ht_fill from host arrays) and its peak list
           and count come back into that step's own slot of pinned host memory
           (ht_find_maxima writing there); the calls are issued back to back
-          and the host waits once, at the end.  The blocking per-call path
-          (ht_find_maxima into host memory, one round trip per event) is
-          reported beside it with its latencies.
+          over the same contexts and the host waits once, at the end.  The
+          blocking per-call path (one context, ht_find_maxima into host
+          memory, one round trip per event) is reported beside it with its
+          latencies.
   roofline  the dominant kernel's algorithmic bytes / live launch time.
   cpu_baseline  the CPU oracle on a bounded sample of the same workload.
 
@@ -57,6 +64,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--serving-seconds", type=float, default=1.5, help="arrival window per serving rate")
+    ap.add_argument("--contexts", type=int, default=8, help="contexts (events in flight) of the timed steps")
     return ap.parse_args()
 
 
@@ -235,34 +243,71 @@ def run_ours(args, rank, world):
     # pick launch shapes on this workload (outside the timed region)
     tuning = ctx.get_tuning() if args.no_autotune else ctx.autotune(reps=5)[0]
 
-    def step(k):
+    # events in flight: one context (and stream) per event slot, round-robin
+    C = max(1, args.contexts)
+    ctxs = [ctx] + [ht.Context(b, r, threshold=THRESHOLD, max_hits=max_hits) for _ in range(C - 1)]
+    for c in ctxs[1:]:
+        c.set_tuning(**tuning)
+    sts = [st] + [torch.cuda.Stream() for _ in range(C - 1)]
+    with torch.cuda.stream(st):
+        outs = [out] + [torch.empty(cap * 8, dtype=torch.int32, device="cuda") for _ in range(C - 1)]
+        cnts = [cnt] + [torch.empty(1, dtype=torch.int32, device="cuda") for _ in range(C - 1)]
+    st.synchronize()
+
+    def step(k, count=None):
+        c = k % C
+        ctxs[c].fill(*dev[k % N_POOL], naive=args.naive, stream=sts[c])
+        ctxs[c].find_maxima(capacity=cap, out=outs[c], count=cnts[c] if count is None else count, stream=sts[c])
+
+    def step1(k):
         ctx.fill(*dev[k % N_POOL], naive=args.naive, stream=st)
         ctx.find_maxima(capacity=cap, out=out, count=cnt, stream=st)
 
-    for k in range(args.warmup):
+    for k in range(max(args.warmup, C)):
         step(k)
-    st.synchronize()
+    torch.cuda.synchronize()
 
     # ---- device-resident timed region --------------------------------------
-    # The headline: K steps between two CUDA events on the launching stream,
-    # nothing else recorded in between (per-step marks and per-kernel events
-    # would sit between the dependent launches).
+    # The headline: K steps between two CUDA events on a stream that forks to
+    # and joins the contexts' streams, nothing else recorded in between
+    # (per-step marks and per-kernel events would sit between the dependent
+    # launches).  Each step's peak count lands in its own word.
     K = args.steps
+    step_counts = torch.full((K,), -1, dtype=torch.int32, device="cuda")
+    count_views = [step_counts[k:k + 1] for k in range(K)]
+    main = torch.cuda.Stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
-        launches0 = ctx.launches
-        with torch.cuda.stream(st):
-            ev0.record(st)
-            for k in range(K):
-                step(k)
-            ev1.record(st)
-        st.synchronize()
-        launches = ctx.launches - launches0
+        launches0 = sum(c.launches for c in ctxs)
+        ev0.record(main)
+        for s in sts:
+            s.wait_stream(main)
+        for k in range(K):
+            step(k, count_views[k])
+        for s in sts:
+            main.wait_stream(s)
+        ev1.record(main)
+        main.synchronize()
+        launches = sum(c.launches for c in ctxs) - launches0
         torch.cuda.synchronize()
+        got = step_counts.cpu().numpy()
+        steps_ok = all(int(got[k]) == peaks[k % N_POOL] for k in range(K))
         barrier(world)
-        # per-step latency and per-kernel device times: the same steps again
+        # the same steps with one context: one event at a time on one stream
+        for k in range(args.warmup):
+            step1(k)
+        e1a, e1b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e1a.record(st)
+            for k in range(K):
+                step1(k)
+            e1b.record(st)
+        st.synchronize()
+        one_ms = e1a.elapsed_time(e1b)
+        barrier(world)
+        # per-step latency and per-kernel device times: one context again
         # with a CUDA event after every step and around every kernel
         K1 = max(1, K // 4)
         marks = [torch.cuda.Event(enable_timing=True) for _ in range(K1 + 1)]
@@ -270,7 +315,7 @@ def run_ours(args, rank, world):
         with torch.cuda.stream(st):
             marks[0].record(st)
             for k in range(K1):
-                step(k)
+                step1(k)
                 marks[k + 1].record(st)
         st.synchronize()
         prof = ctx.profile_read()
@@ -291,18 +336,22 @@ def run_ours(args, rank, world):
             e2e_times.append(time.perf_counter() - ts)
             n_peaks_e2e += len(pk)
         e2e_s = time.perf_counter() - t0
-        # the same calls pipelined: each step's peaks and count land in its own
-        # slot of pinned host memory; one wait at the end
+        # the same calls pipelined over the contexts (each on its own stream
+        # with its own pinned staging): each step's peaks and count land in
+        # its own slot of pinned host memory; one wait at the end
         slot_cap = 1024
         res_pk = torch.zeros((K2, slot_cap * 8), dtype=torch.int32, pin_memory=True)
         res_n = torch.zeros(K2, dtype=torch.int32, pin_memory=True)
-        ctx.sync()
+        for c in ctxs:
+            c.sync()
         t0 = time.perf_counter()
         for k in range(K2):
             e = events[k % N_POOL]
-            ctx.fill(e.x, e.y, e.z)
-            ctx.find_maxima(capacity=slot_cap, out=res_pk[k], count=res_n[k:k + 1])
-        ctx.sync()
+            c = ctxs[k % C]
+            c.fill(e.x, e.y, e.z)
+            c.find_maxima(capacity=slot_cap, out=res_pk[k], count=res_n[k:k + 1])
+        for c in ctxs:
+            c.sync()
         e2e_pipe_s = time.perf_counter() - t0
         got_n = res_n.numpy().astype(np.int64)
         pipe_ok = all(int(got_n[k]) == peaks[k % N_POOL] for k in range(K2))
@@ -311,10 +360,12 @@ def run_ours(args, rank, world):
     per_step = [marks[k].elapsed_time(marks[k + 1]) for k in range(K1)]
 
     t_dev = max_over_ranks(total_ms / 1e3, world)
+    t_one = max_over_ranks(one_ms / 1e3, world)
     t_e2e = max_over_ranks(e2e_s, world)
     t_e2e_pipe = max_over_ranks(e2e_pipe_s, world)
     if rank != 0:
-        ctx.close()
+        for c in ctxs:
+            c.close()
         return None
 
     kern = {kname: {"launches": n, "avg_us": (ms / n * 1e3 if n else None)} for kname, (n, ms) in prof.items() if n}
@@ -327,31 +378,40 @@ def run_ours(args, rank, world):
             "k_order": None}
     n_dom, ms_dom = prof[dom]
     avg_s = ms_dom / n_dom / 1e3
+    value = K * world / t_dev
     roofline = None
     if algo.get(dom):
         ach = algo[dom] / avg_s / 1e9
         roofline = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
                     "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": profiled_traffic(dom),
                     "algorithmic_bytes_per_launch": algo[dom], "avg_launch_us": round(avg_s * 1e6, 2),
-                    "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+                    "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "note": "launch time from the one-context pass (the kernel alone on the GPU)",
+                    "in_flight": {"gbs": round(algo[dom] * value / world / 1e9, 1),
+                                  "frac": round(algo[dom] * value / world / 1e9 / hbm_peak, 4),
+                                  "note": "M_H bytes of every timed event / the timed region, events in flight"}}
     mean_votes = float(np.mean(votes))
-    value = K * world / t_dev
+
     res = {
         "metric": METRIC, "value": round(value, 2), "unit": "events/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(t_dev * 1e3 / K, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 vote arithmetic, u32 counters",
         "data": "synthetic (seeded helix events; the paper's dataset is not available)",
         "config": {"workload": WORKLOAD, "events_resident": N_POOL, "fill": "naive" if args.naive else "privatised",
-                   "tuning": tuning,
+                   "contexts_in_flight": C, "tuning": tuning,
                    "l2": "inputs larger than L2: each step writes a 256 MiB M_H (L2 129 MB), read back at its candidates",
                    "parallelism": f"replicas x{world}"},
+        "results_checked": bool(steps_ok),
+        "one_context": {"value": round(K * world / t_one, 2), "unit": "events/s",
+                        "ms_per_step": round(t_one * 1e3 / K, 4),
+                        "note": "the same K steps through one context on one stream: one event at a time"},
         "gvotes_per_s": round(value * mean_votes / 1e9, 3),
         "gcandidates_per_s": round(value * float(np.mean(cands)) / 1e9, 3),
         "candidates_per_event": int(np.mean(cands)),
         "votes_per_event": int(mean_votes), "peaks_per_event": float(np.mean(peaks)),
         "latency_ms": {"device_p50": round(float(np.percentile(per_step, 50)), 4),
                        "device_p99": round(float(np.percentile(per_step, 99)), 4),
-                       "note": "device latencies and kernel times from a second pass of K/4 steps with "
+                       "note": "device latencies and kernel times from a one-context pass of K/4 steps with "
                                "an event per step and per kernel",
                               "e2e_p50": round(float(np.percentile(e2e_times, 50)) * 1e3, 4),
                        "e2e_p99": round(float(np.percentile(e2e_times, 99)) * 1e3, 4)},
@@ -359,7 +419,7 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": int(12 * np.mean([e.n_hits for e in events])),
                 "d2h_bytes_per_step": int(4 + 32 * n_peaks_pipe / K2),
                 "api": "ht_fill(host x,y,z) + ht_find_maxima(out, count in pinned host memory), "
-                       "issued back to back, one wait at the end",
+                       "issued back to back round-robin over the contexts, one wait at the end",
                 "results_checked": bool(pipe_ok),
                 "blocking_per_call": {"value": round(K2 * world / t_e2e, 2), "unit": "events/s",
                                       "d2h_bytes_per_step": int(4 + 4 + 32 * n_peaks_e2e / K2),
@@ -371,13 +431,14 @@ def run_ours(args, rank, world):
         "clocks": clk.summary(),
     }
     if not args.no_extras and world == 1:
-        res["peaks_only"] = run_peaks_only(ctx, dev, out, cnt, cap, st, args.steps, args.warmup, peaks)
-        res["maxima_4d"] = run_maxima4d(ctx, dev, out, cnt, cap, st, args.steps, args.warmup)
+        res["peaks_only"] = run_peaks_only(ctxs, dev, outs, cnts, cap, sts, args.steps, args.warmup, peaks)
+        res["maxima_4d"] = run_maxima4d(ctxs, dev, outs, cnts, cap, sts, args.steps, args.warmup)
         res["readout"] = run_readout(ctx, events, b, r)
         res["sectors"] = run_sectors(dev, b, r, max_hits, args.steps, args.warmup, peaks)
         res["components"] = run_components(dev, b, r, max_hits, float(np.mean(votes)), hbm_peak)
         res["upgrade"] = run_upgrade(hbm_peak)
-    ctx.close()
+    for c in ctxs:
+        c.close()
     if not args.no_extras and world == 1:
         res["batched"] = run_batched()
         res["serving"] = run_serving(args.serving_seconds)
@@ -524,39 +585,59 @@ def run_sectors(dev, b, r, max_hits, K, W, peaks_ref, n_sectors=4):
 # ---------------------------------------------------------------------------
 # The 4-D (80-neighbour) maxima rule: the 2-D pipeline plus the k_peaks4d filter
 # ---------------------------------------------------------------------------
-def run_maxima4d(ctx, dev, out, cnt, cap, st, K, W):
+def timed_in_flight(sts, step, K, W):
+    """Milliseconds per step of K steps (after W) issued by step(k) onto the
+    streams sts, between two CUDA events on a stream that forks to and joins
+    all of them."""
     import torch
 
-    def step(k):
-        ctx.fill(*dev[k % N_POOL], stream=st)
-        ctx.find_maxima(capacity=cap, out=out, count=cnt, stream=st, four_d=True)
-
-    n4 = []
-    for k in range(N_POOL):
-        step(k)
-        st.synchronize()
-        n4.append(int(cnt.item()))
     for k in range(W):
         step(k)
-    st.synchronize()
+    torch.cuda.synchronize()
+    main = torch.cuda.Stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(st):
-        ev0.record(st)
-        for k in range(K):
-            step(k)
-        ev1.record(st)
-    st.synchronize()
-    ms = ev0.elapsed_time(ev1) / K
+    ev0.record(main)
+    for s in sts:
+        s.wait_stream(main)
+    for k in range(K):
+        step(k)
+    for s in sts:
+        main.wait_stream(s)
+    ev1.record(main)
+    main.synchronize()
+    return ev0.elapsed_time(ev1) / K
+
+
+def run_maxima4d(ctxs, dev, outs, cnts, cap, sts, K, W):
+    C = len(ctxs)
+
+    def run_on(c, k):
+        ctxs[c].fill(*dev[k % N_POOL], stream=sts[c])
+        ctxs[c].find_maxima(capacity=cap, out=outs[c], count=cnts[c], stream=sts[c], four_d=True)
+
+    def step(k):
+        run_on(k % C, k)
+
+    ctx, st = ctxs[0], sts[0]
+    n4 = []
+    for k in range(N_POOL):
+        ctx.fill(*dev[k], stream=st)
+        ctx.find_maxima(capacity=cap, out=outs[0], count=cnts[0], stream=st, four_d=True)
+        st.synchronize()
+        n4.append(int(cnts[0].item()))
+    ms = timed_in_flight(sts, step, K, W)
+    ms1 = timed_in_flight(sts[:1], lambda k: run_on(0, k), K, W)
     ctx.profile(True)
     for k in range(max(1, K // 4)):
-        step(k)
+        run_on(0, k)
     prof = ctx.profile_read()
     ctx.profile(False)
-    return {"events_per_s": round(1e3 / ms, 1), "ms_per_step": round(ms, 4),
+    return {"events_per_s": round(1e3 / ms, 1), "ms_per_step": round(ms, 4), "contexts_in_flight": C,
+            "one_context_events_per_s": round(1e3 / ms1, 1),
             "peaks_per_event": float(np.mean(n4)),
             "kernels": {kn: {"launches": n, "avg_us": round(t / n * 1e3, 2)} for kn, (n, t) in prof.items() if n},
             "note": "HT_MAXIMA_4D: 80 neighbours in (theta, phi, A, B); the 2-D peaks filtered against the "
-                    "adjacent slices by one CTA; device-resident events"}
+                    "adjacent slices by one CTA; device-resident events; kernel times from one context"}
 
 
 # ---------------------------------------------------------------------------
@@ -579,39 +660,36 @@ def run_readout(ctx, events, b, r):
 # ---------------------------------------------------------------------------
 # Peaks-only fills (M_H not written), the same resident events
 # ---------------------------------------------------------------------------
-def run_peaks_only(ctx, dev, out, cnt, cap, st, K, W, peaks_ref):
-    import torch
+def run_peaks_only(ctxs, dev, outs, cnts, cap, sts, K, W, peaks_ref):
+    C = len(ctxs)
+
+    def run_on(c, k):
+        ctxs[c].fill(*dev[k % N_POOL], peaks_only=True, stream=sts[c])
+        ctxs[c].find_maxima(capacity=cap, out=outs[c], count=cnts[c], stream=sts[c])
 
     def step(k):
-        ctx.fill(*dev[k % N_POOL], peaks_only=True, stream=st)
-        ctx.find_maxima(capacity=cap, out=out, count=cnt, stream=st)
+        run_on(k % C, k)
 
+    ctx, st = ctxs[0], sts[0]
     same = True
     for k in range(N_POOL):          # the peak counts of the plain path
-        step(k)
+        ctx.fill(*dev[k], peaks_only=True, stream=st)
+        ctx.find_maxima(capacity=cap, out=outs[0], count=cnts[0], stream=st)
         st.synchronize()
-        same = same and int(cnt.item()) == peaks_ref[k]
-    for k in range(W):
-        step(k)
-    st.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(st):
-        ev0.record(st)
-        for k in range(K):
-            step(k)
-        ev1.record(st)
-    st.synchronize()
-    ms = ev0.elapsed_time(ev1) / K
+        same = same and int(cnts[0].item()) == peaks_ref[k]
+    ms = timed_in_flight(sts, step, K, W)
+    ms1 = timed_in_flight(sts[:1], lambda k: run_on(0, k), K, W)
     ctx.profile(True)
     for k in range(max(1, K // 4)):
-        step(k)
+        run_on(0, k)
     prof = ctx.profile_read()
     ctx.profile(False)
-    return {"events_per_s": round(1e3 / ms, 1), "ms_per_step": round(ms, 4),
+    return {"events_per_s": round(1e3 / ms, 1), "ms_per_step": round(ms, 4), "contexts_in_flight": C,
+            "one_context_events_per_s": round(1e3 / ms1, 1),
             "kernels": {kn: {"launches": n, "avg_us": round(t / n * 1e3, 2)} for kn, (n, t) in prof.items() if n},
             "same_peak_counts": bool(same),
             "note": "HT_PEAKS_ONLY: peaks found in the fill's shared-memory tiles, M_H not written; "
-                    "device-resident events, K steps between two CUDA events"}
+                    "device-resident events, K steps between two CUDA events; kernel times from one context"}
 
 
 # ---------------------------------------------------------------------------
@@ -674,6 +752,44 @@ def run_batched(n_events=100, reps=5):
                         "device_events_per_s": round(n_events / t_dev, 1),
                         "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99)},
                         "api": "ht_fill + ht_find_maxima per event"}
+    # the same per-event calls with events in flight: 8 contexts, each on its
+    # own stream, the events round-robin
+    C = 8
+    ctxs = [ht.Context(b, r, threshold=THRESHOLD, max_hits=max(e.n_hits for e in evs)) for _ in range(C)]
+    sts = [torch.cuda.Stream() for _ in range(C)]
+    outs = [torch.empty(4096 * 8, dtype=torch.int32, device="cuda") for _ in range(C)]
+    cnts = [torch.empty(1, dtype=torch.int32, device="cuda") for _ in range(C)]
+
+    def step(k):
+        c = k % C
+        ctxs[c].fill(*dev[k % n_events], stream=sts[c])
+        ctxs[c].find_maxima(capacity=4096, out=outs[c], count=cnts[c], stream=sts[c])
+
+    ms_fl = timed_in_flight(sts, step, n_events * reps, 2 * C)
+    slot = 1024
+    res_pk = torch.zeros((n_events, slot * 8), dtype=torch.int32, pin_memory=True)
+    res_n = torch.zeros(n_events, dtype=torch.int32, pin_memory=True)
+    t_fl = []
+    for _ in range(reps):
+        for c in ctxs:
+            c.sync()
+        t0 = time.perf_counter()
+        for k, ev in enumerate(host):
+            c = ctxs[k % C]
+            c.fill(*ev)
+            c.find_maxima(capacity=slot, out=res_pk[k], count=res_n[k:k + 1])
+        for c in ctxs:
+            c.sync()
+        t_fl.append(time.perf_counter() - t0)
+    counts_fl = res_n.numpy().copy()
+    for c in ctxs:
+        c.close()
+    res["per_event_in_flight"] = {"e2e_events_per_s": round(n_events / float(np.median(t_fl)), 1),
+                                  "device_events_per_s": round(1e3 / ms_fl, 1), "contexts": C,
+                                  "latency_ms": {"p50_batch_of_100": round(float(np.median(t_fl)) * 1e3, 4),
+                                                 "note": "all 100 events issued at once: each is ready when "
+                                                         "its context reaches it"},
+                                  "api": "ht_fill + ht_find_maxima per event, round-robin over the contexts"}
     # one batch
     with ht.Batch(b, r, threshold=THRESHOLD, max_events=n_events, max_hits=n_hits + 64, capacity=1 << 17) as B:
         for _ in range(2):
@@ -730,6 +846,7 @@ def run_batched(n_events=100, reps=5):
                                  "device_events_per_s": round(n_events / t_podev, 1),
                                  "same_counts": same_po,
                                  "api": "ht_batch_run(..., HT_PEAKS_ONLY) (graph replay)"}
+    res["per_event_in_flight"]["same_counts"] = bool(np.array_equal(counts_fl, counts))
     res["votes_per_event"] = int(votes / n_events)
     return res
 
