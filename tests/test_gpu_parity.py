@@ -226,6 +226,51 @@ def test_device_mode_on_torch_stream(ht):
     assert np.array_equal(Md.cpu().numpy().view(np.uint32).reshape(b.shape()), M_ref)
 
 
+def test_contexts_in_flight(ht):
+    # Several contexts on their own streams, events issued round-robin with no
+    # waits in between (the bench's events in flight): every event's peaks and
+    # the last M_H of every context equal the oracle's; odd rounds take the
+    # peaks-only fill.  Ragged binning, a few thousand hits per event.
+    import torch
+    b = ht.Binning(3, 6, 200, 136)
+    r = ht.Ranges(a_min=-1800.0, a_max=1600.0, b_min=-1700.0, b_max=1900.0)
+    T, C, n_ev, cap = 5, 4, 12, 8192
+    evs = [random_hits(2000 + 150 * k, 700 + k) for k in range(n_ev)]
+    refs = []
+    for x, y, z in evs:
+        M_ref, _ = oracle.fill(_ob(b), _orr(r), x, y, z)
+        refs.append((M_ref,) + tuple(oracle.find_maxima(_ob(b), _orr(r), M_ref, T)))
+    ctxs = [ht.Context(b, r, threshold=T, max_hits=4096) for _ in range(C)]
+    sts = [torch.cuda.Stream() for _ in range(C)]
+    try:
+        dev = [tuple(torch.from_numpy(a).cuda() for a in e) for e in evs]
+        outs = [torch.zeros(cap * 8, dtype=torch.int32, device="cuda") for _ in range(n_ev)]
+        cnts = torch.zeros(n_ev, dtype=torch.int32, device="cuda")
+        Ms = [torch.zeros(b.n_cells, dtype=torch.int32, device="cuda") for _ in range(C)]
+        torch.cuda.synchronize()
+        for k in range(n_ev):
+            c = k % C
+            po = (k // C) % 2 == 1 and k < n_ev - C   # the last round writes M_H
+            ctxs[c].fill(*dev[k], peaks_only=po, stream=sts[c])
+            ctxs[c].find_maxima(capacity=cap, out=outs[k], count=cnts[k:k + 1], stream=sts[c])
+        for c in range(C):
+            ctxs[c].matrix_into(Ms[c], stream=sts[c])
+        torch.cuda.synchronize()
+        for c in ctxs:
+            c.sync()
+        got_n = cnts.cpu().numpy()
+        for k in range(n_ev):
+            _, pk_ref, n_ref = refs[k]
+            assert int(got_n[k]) == n_ref, k
+            assert_peaks_equal(outs[k].cpu().numpy().view(ht.PEAK_DTYPE)[:n_ref], pk_ref)
+        for c in range(C):
+            k = n_ev - C + c
+            assert np.array_equal(Ms[c].cpu().numpy().view(np.uint32).reshape(b.shape()), refs[k][0]), c
+    finally:
+        for c in ctxs:
+            c.close()
+
+
 # ---------------------------------------------------------------------------
 # The scan alone on hand-built and random matrices
 # ---------------------------------------------------------------------------
