@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--serving-seconds", type=float, default=1.5, help="arrival window per serving rate")
     ap.add_argument("--contexts", type=int, default=8, help="contexts (events in flight) of the timed steps")
+    ap.add_argument("--components-only", action="store_true",
+                    help="print only the component timings (two-kernel path, naive fill, L2 atomics), "
+                         "--steps events each")
     return ap.parse_args()
 
 
@@ -240,6 +243,13 @@ def run_ours(args, rank, world):
         cands.append(ctx.last_admitted() * b.n_a)
     ctx.sync()
     del M
+    if args.components_only:
+        res = None
+        if rank == 0:
+            res = {"components": run_components(dev, b, r, max_hits, float(np.mean(votes)), measured_peaks()[0],
+                                                steps=args.steps)}
+        ctx.close()
+        return res
     # pick launch shapes on this workload (outside the timed region)
     tuning = ctx.get_tuning() if args.no_autotune else ctx.autotune(reps=5)[0]
 
@@ -491,10 +501,11 @@ def run_components(dev, b, r, max_hits, mean_votes, hbm_peak, steps=200):
                         "frac_of_hbm": round(cells_bytes / scan_us / 1e3 / hbm_peak, 4)},
         "fill_naive": {"avg_us": round(nv_us, 2), "clear_us": round(naive.get("k_clear", 0.0), 2),
                        "gvotes_per_s": round(mean_votes / nv_us / 1e3, 3),
+                       "frac_of_l2_atomics_32mib": round(mean_votes / nv_us * 1e6 / l2_res, 4),
                        "frac_of_l2_atomics_256mib": round(mean_votes / nv_us * 1e6 / l2_hbm, 4)},
         "l2_atomics": {"gupdates_per_s_32mib": round(l2_res / 1e9, 2), "gupdates_per_s_256mib": round(l2_hbm / 1e9, 2),
                        "note": "ht_measure_atomics: red.global.add at pseudo-random words, 8 x 256 threads per SM"},
-        "note": "per-kernel CUDA-event averages over 200 events (fill_fused_scan=2: k_fill_priv then k_scan; "
+        "note": f"per-kernel CUDA-event averages over {steps} events (fill_fused_scan=2: k_fill_priv then k_scan; "
                 "HT_FILL_NAIVE: k_clear then k_fill_naive); bytes = 4 per M_H cell; peak = measured HBM copy",
     }
 
