@@ -65,10 +65,15 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--serving-seconds", type=float, default=1.5, help="arrival window per serving rate")
     ap.add_argument("--contexts", type=int, default=8, help="contexts (events in flight) of the timed steps")
+    ap.add_argument("--peaks-only", action="store_true",
+                    help="time the peaks-only fills (HT_PEAKS_ONLY: M_H not written) in the headline steps")
     ap.add_argument("--components-only", action="store_true",
                     help="print only the component timings (two-kernel path, naive fill, L2 atomics), "
                          "--steps events each")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.naive and a.peaks_only:
+        ap.error("--naive and --peaks-only exclude each other")
+    return a
 
 
 # ---------------------------------------------------------------------------
@@ -187,7 +192,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("ht_kernels.cu", "ht_device.cuh"):
+    for f in ("ht_kernels.cu", "ht_device.cuh", "ht_internal.h"):
         with open(os.path.join(ROOT, "paper_1507_03074_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -266,11 +271,11 @@ def run_ours(args, rank, world):
 
     def step(k, count=None):
         c = k % C
-        ctxs[c].fill(*dev[k % N_POOL], naive=args.naive, stream=sts[c])
+        ctxs[c].fill(*dev[k % N_POOL], naive=args.naive, peaks_only=args.peaks_only, stream=sts[c])
         ctxs[c].find_maxima(capacity=cap, out=outs[c], count=cnts[c] if count is None else count, stream=sts[c])
 
     def step1(k):
-        ctx.fill(*dev[k % N_POOL], naive=args.naive, stream=st)
+        ctx.fill(*dev[k % N_POOL], naive=args.naive, peaks_only=args.peaks_only, stream=st)
         ctx.find_maxima(capacity=cap, out=out, count=cnt, stream=st)
 
     for k in range(max(args.warmup, C)):
@@ -408,7 +413,7 @@ def run_ours(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 vote arithmetic, u32 counters",
         "data": "synthetic (seeded helix events; the paper's dataset is not available)",
         "config": {"workload": WORKLOAD, "events_resident": N_POOL, "fill": "naive" if args.naive else "privatised",
-                   "contexts_in_flight": C, "tuning": tuning,
+                   "contexts_in_flight": C, "peaks_only": bool(args.peaks_only), "tuning": tuning,
                    "l2": "inputs larger than L2: each step writes a 256 MiB M_H (L2 129 MB), read back at its candidates",
                    "parallelism": f"replicas x{world}"},
         "results_checked": bool(steps_ok),

@@ -133,6 +133,7 @@ ht_status engine_configure(Engine &E, std::string *why)
     f.pitch32 = round_up(b.n_b, 32);
     f.beta_words = round_up(b.n_b + 1, 4);
     f.dyn = 1;   // the last items are handed out at run time (htk::dyn_items)
+    f.vote_weight = htk::kVoteWeight;
     const size_t beta_bytes = (size_t)f.beta_words * 4;
     uint32_t W = t.fill_W;
     if (W && (W & (W - 1))) {
@@ -313,7 +314,7 @@ ht_status engine_configure(Engine &E, std::string *why)
     // an even split (every strip costs at least its n_b-per-row writing share)
     const double hits_per_unit = (double)std::max<uint32_t>(E.max_hits, 1) * E.max_admit /
                                  ((double)E.max_events * g.n_slices);
-    const double spread = 1.0 + htk::kVoteWeight * hits_per_unit / g.nb;
+    const double spread = 1.0 + std::max(htk::kVoteWeight, htk::kPeaksVoteWeight) * hits_per_unit / g.nb;
     auto rows_per_cta = [&](uint32_t grid) {
         return (uint64_t)(std::ceil((double)items_max / grid * spread) + 2) * f.W + 1;
     };
@@ -627,6 +628,7 @@ cudaError_t engine_vote(Engine &E, const uint32_t *d_hit_off, uint32_t n_hits0, 
         const bool ws = E.use_ws && !peaks_only;
         htk::FillCfg ff = ws ? E.ws_fill : E.fused_fill;
         ff.accumulate = 0u;
+        ff.vote_weight = peaks_only ? htk::kPeaksVoteWeight : htk::kVoteWeight;
         const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(ws ? E.ws_grid : E.fused_grid, items));
         const uint32_t lists = grid + (ff.dyn ? (uint32_t)htk::dyn_items(items, grid) : 0u);
         {

@@ -24,6 +24,7 @@ struct FillCfg {
     uint32_t beta_words;  // shared-memory copy of the B-bin thresholds (n_b + 1, rounded to 4)
     uint32_t dyn;         // 1: the last dyn_items() items are handed out at run time (see below)
     uint32_t bulk;        // fused fill: 1 = passes leave through u32 staging and bulk copies (k_fill_bulk)
+    uint32_t vote_weight; // cost of one vote against one cell written, in the static split (cta_items)
 };
 
 // Shared-memory words of the fused fill's two u32 staging buffers (half a
@@ -108,8 +109,12 @@ enum : uint32_t {
 
 // Cost model of the balanced split of (event, slice, strip) work items over
 // the fill CTAs: a strip of r rows in a slice of h hits costs
-// r * (n_b + kVoteWeight * h) (writing a cell ~ 1, one vote ~ kVoteWeight).
+// r * (n_b + v * h) (writing a cell ~ 1, one vote ~ v = FillCfg::vote_weight).
+// The fills that write M_H take kVoteWeight; the peaks-only fill, whose
+// cells cost only their clearing, weighs votes more (kPeaksVoteWeight; 6,
+// 12 and 24 were measured on paper-scale events, 24 balancing its CTAs best).
 constexpr uint32_t kVoteWeight = 6;
+constexpr uint32_t kPeaksVoteWeight = 24;
 
 // Scan variants: bulk-copy (TMA) ring, register streaming, direct (any n_b).
 // The streaming variant keeps kLdgUPT 16-byte loads per thread in flight.

@@ -498,11 +498,11 @@ __device__ __forceinline__ void vote_pass(const Geom &g, const Work &w, uint32_t
 }
 
 // The work items [it0, it1) of CTA `cta` of `grid`: the (event, slice,
-// strip) items in order, cut where the estimated cost -- kVoteWeight per
-// (hit, row) vote plus one per cell written -- reaches cta / grid of the
-// total.  A unit u = (event, slice) costs n_a (n_b + kVoteWeight hits(u)), so
-// the cost before unit u is n_a (n_b u + kVoteWeight slice_off[u]); a cut
-// inside a unit falls on a strip boundary.  Every thread of the group calls
+// strip) items in order, cut where the estimated cost -- v = c.vote_weight
+// per (hit, row) vote plus one per cell written -- reaches cta / grid of the
+// total.  A unit u = (event, slice) costs n_a (n_b + v hits(u)), so the cost
+// before unit u is n_a (n_b u + v slice_off[u]); a cut inside a unit falls
+// on a strip boundary.  Every thread of the group calls
 // it and gets the same result; s_res: 2 shared words.
 template <class G = BlockGroup>
 __device__ __forceinline__ void cta_items(const Geom &g, const Work &w, const FillCfg &c, uint32_t cta,
@@ -511,7 +511,7 @@ __device__ __forceinline__ void cta_items(const Geom &g, const Work &w, const Fi
 {
     const uint32_t U = w.n_events * g.n_slices;
     auto cost = [&](uint32_t u) {
-        return (uint64_t)g.na * ((uint64_t)g.nb * u + (uint64_t)kVoteWeight * __ldcg(&w.slice_off[u]));
+        return (uint64_t)g.na * ((uint64_t)g.nb * u + (uint64_t)c.vote_weight * __ldcg(&w.slice_off[u]));
     };
     // the cost of the first n_static items
     const uint32_t us = (uint32_t)(n_static / c.strips), ks = (uint32_t)(n_static % c.strips);
