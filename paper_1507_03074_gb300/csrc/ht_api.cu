@@ -5,6 +5,7 @@
 // on the device, and pinned host staging for host-side hits and results.
 #include "ht_engine.h"
 #include "ht_geom.h"
+#include "ht_trace.h"
 
 #include <cstdio>
 #include <cstring>
@@ -155,6 +156,7 @@ ht_status ht_destroy(ht_ctx *ctx)
 ht_status ht_fill(ht_ctx *ctx, const float *x, const float *y, const float *z, uint32_t n_hits,
                   uint32_t flags, void *stream)
 {
+    hte::TraceRange tr("ht_fill");
     ht_status s = check_ctx(ctx);
     if (s != HT_OK)
         return s;
@@ -203,6 +205,7 @@ ht_status ht_fill(ht_ctx *ctx, const float *x, const float *y, const float *z, u
 ht_status ht_find_maxima(ht_ctx *ctx, ht_peak *out, uint32_t capacity, uint32_t *n_found,
                          uint32_t flags, void *stream)
 {
+    hte::TraceRange tr("ht_find_maxima");
     ht_status s = check_ctx(ctx);
     if (s != HT_OK)
         return s;
@@ -415,6 +418,7 @@ ht_status ht_get_tuning(ht_ctx *ctx, ht_tuning *t)
 
 ht_status ht_autotune(ht_ctx *ctx, uint32_t reps, ht_tuning *chosen, double *us_per_event)
 {
+    hte::TraceRange tr("ht_autotune");
     ht_status s = check_ctx(ctx);
     if (s != HT_OK)
         return s;

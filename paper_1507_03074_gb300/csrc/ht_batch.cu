@@ -9,6 +9,7 @@
 // an event count serves every later run with that count: hits are copied to
 // fixed staging buffers before the graph and the results out after it.
 #include "ht_runner.h"
+#include "ht_trace.h"
 
 #include <cstdio>
 #include <cstring>
@@ -280,6 +281,7 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
                        uint32_t n_events, uint32_t n_hits, ht_peak *out, uint32_t *counts, uint32_t flags,
                        void *stream)
 {
+    hte::TraceRange tr("ht_batch_run");
     ht_status s = check_batch(b);
     if (s != HT_OK)
         return s;
@@ -412,6 +414,7 @@ ht_status ht_batch_get_tuning(ht_batch *b, ht_tuning *t)
 
 ht_status ht_batch_autotune(ht_batch *b, uint32_t reps, ht_tuning *chosen, double *us_per_event)
 {
+    hte::TraceRange tr("ht_batch_autotune");
     ht_status s = check_batch(b);
     if (s != HT_OK)
         return s;

@@ -13,6 +13,7 @@
 // peaks are the unsplit peaks of those bins.
 #include "ht_engine.h"
 #include "ht_geom.h"
+#include "ht_trace.h"
 
 #include <cstdio>
 #include <cstring>
@@ -256,6 +257,7 @@ ht_status ht_sectors_create(const ht_binning *binning, const ht_ranges *ranges, 
 ht_status ht_sectors_fill(ht_sectors *sec, const float *x, const float *y, const float *z, uint32_t n_hits,
                           uint32_t flags, void *stream)
 {
+    hte::TraceRange tr("ht_sectors_fill");
     ht_status s = check_sec(sec);
     if (s != HT_OK)
         return s;
@@ -299,6 +301,7 @@ ht_status ht_sectors_fill(ht_sectors *sec, const float *x, const float *y, const
 ht_status ht_sectors_find_maxima(ht_sectors *sec, ht_peak *out, uint32_t capacity, uint32_t *n_found,
                                  uint32_t flags, void *stream)
 {
+    hte::TraceRange tr("ht_sectors_find_maxima");
     ht_status s = check_sec(sec);
     if (s != HT_OK)
         return s;

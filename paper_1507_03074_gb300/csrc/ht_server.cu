@@ -15,6 +15,7 @@
 // function.
 #include "ht_geom.h"
 #include "ht_runner.h"
+#include "ht_trace.h"
 
 #include <algorithm>
 #include <atomic>
@@ -137,6 +138,7 @@ uint32_t lane_hits(const ht_server_cfg &c, uint32_t events)
 // Results of a finished micro-batch into its requests.
 void harvest(ht_server *s, Lane &l)
 {
+    hte::TraceRange tr("ht_server harvest");
     hte::Runner &R = l.R;
     std::string why;
     const uint32_t status = R.h_counts[R.E.max_events];
@@ -253,6 +255,7 @@ Lane *make_lane(ht_server *s, const Key &k, bool *never)
 // Stage a micro-batch into the lane and enqueue it.
 bool dispatch(ht_server *s, Lane &l, std::vector<Request *> &&reqs)
 {
+    hte::TraceRange tr("ht_server micro-batch");
     hte::Runner &R = l.R;
     const size_t mh = R.E.max_hits;
     uint32_t off = 0;

@@ -9,6 +9,7 @@ ht_find_maxima -> find_maxima, ...).
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 from dataclasses import dataclass
 
@@ -285,12 +286,60 @@ def _ptr_and_mem(a, dtype):
     return arr.ctypes.data_as(ctypes.c_void_p), HT_MEM_HOST, arr
 
 
+def _gpu_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name(torch.cuda.current_device())
+    except Exception:
+        return "unknown"
+
+
+def _tuning_key(kind: str, binning: Binning, ranges: Ranges, threshold: int, sizes: str) -> str:
+    """Key of a cached launch-shape choice: GPU name, object kind, binning,
+    ranges, threshold and sizes."""
+    b, r = binning, ranges
+    return (f"{_gpu_name()}|{kind}|{b.n_theta}x{b.n_phi}x{b.n_a}x{b.n_b}+{b.win_theta},{b.win_phi}|"
+            f"{r.theta_min},{r.theta_max},{r.phi_min},{r.phi_max},{r.a_min},{r.a_max},{r.b_min},{r.b_max}|"
+            f"T{threshold}|{sizes}")
+
+
+def _load_cache(path: str) -> dict:
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def _cached_autotune(path, key: str, run, apply):
+    """Launch shapes from the JSON cache at `path` (None: $HT_TUNING_CACHE,
+    unset: no cache).  A hit applies the stored shapes without timing; a miss
+    times them (run() -> (tuning, us)) and stores the choice."""
+    path = path if path is not None else os.environ.get("HT_TUNING_CACHE")
+    if path:
+        hit = _load_cache(path).get(key)
+        if isinstance(hit, dict) and isinstance(hit.get("tuning"), dict) and set(hit["tuning"]) <= set(TUNING_FIELDS):
+            tun = {n: int(v) for n, v in hit["tuning"].items()}
+            apply(tun)
+            return tun, float(hit.get("us_per_event", 0.0))
+    tun, us = run()
+    if path:
+        d = _load_cache(path)
+        d[key] = {"tuning": tun, "us_per_event": us}
+        tmp = f"{path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    return tun, us
+
+
 class Context:
     """One event at a time (ht_create / ht_fill / ht_find_maxima)."""
 
     def __init__(self, binning: Binning, ranges: Ranges = Ranges(), threshold: int = 10,
                  max_hits: int = 65536):
-        self.binning, self.ranges, self.threshold = binning, ranges, threshold
+        self.binning, self.ranges, self.threshold, self.max_hits = binning, ranges, threshold, max_hits
         self._h = ctypes.c_void_p()
         b, r = binning.c(), ranges.c()
         check(lib().ht_create(ctypes.byref(b), ctypes.byref(r), threshold, max_hits, ctypes.byref(self._h)))
@@ -323,12 +372,18 @@ class Context:
             raise TypeError(f"unknown tuning fields {sorted(kw)}")
         check(lib().ht_set_tuning(self._h, ctypes.byref(t)))
 
-    def autotune(self, reps: int = 5):
+    def autotune(self, reps: int = 5, cache: str | None = None):
         """ht_autotune: time launch shapes on the last fill's hits and keep the
-        fastest.  Returns (chosen tuning dict, microseconds per event)."""
-        t, us = c_tuning(), ctypes.c_double()
-        check(lib().ht_autotune(self._h, reps, ctypes.byref(t), ctypes.byref(us)))
-        return {n: int(getattr(t, n)) for n in TUNING_FIELDS}, float(us.value)
+        fastest.  Returns (chosen tuning dict, microseconds per event).
+        cache: a JSON file of earlier choices keyed by (GPU name, binning,
+        ranges, threshold, max_hits) -- a hit applies the stored shapes
+        without timing (default $HT_TUNING_CACHE; unset: no cache)."""
+        def run():
+            t, us = c_tuning(), ctypes.c_double()
+            check(lib().ht_autotune(self._h, reps, ctypes.byref(t), ctypes.byref(us)))
+            return {n: int(getattr(t, n)) for n in TUNING_FIELDS}, float(us.value)
+        key = _tuning_key("context", self.binning, self.ranges, self.threshold, f"H{self.max_hits}")
+        return _cached_autotune(cache, key, run, lambda t: self.set_tuning(**t))
 
     def get_tuning(self) -> dict:
         t = c_tuning()
@@ -573,10 +628,15 @@ class Batch:
         check(lib().ht_batch_get_tuning(self._h, ctypes.byref(t)))
         return {n: int(getattr(t, n)) for n in TUNING_FIELDS}
 
-    def autotune(self, reps: int = 3):
-        t, us = c_tuning(), ctypes.c_double()
-        check(lib().ht_batch_autotune(self._h, reps, ctypes.byref(t), ctypes.byref(us)))
-        return {n: int(getattr(t, n)) for n in TUNING_FIELDS}, float(us.value)
+    def autotune(self, reps: int = 3, cache: str | None = None):
+        """ht_batch_autotune on the last run's events; cache as Context.autotune
+        (keyed by GPU name, binning, ranges, threshold, max_events, max_hits)."""
+        def run():
+            t, us = c_tuning(), ctypes.c_double()
+            check(lib().ht_batch_autotune(self._h, reps, ctypes.byref(t), ctypes.byref(us)))
+            return {n: int(getattr(t, n)) for n in TUNING_FIELDS}, float(us.value)
+        key = _tuning_key("batch", self.binning, self.ranges, self.threshold, f"E{self.max_events}H{self.max_hits}")
+        return _cached_autotune(cache, key, run, lambda t: self.set_tuning(**t))
 
     def profile(self, enable: bool = True):
         check(lib().ht_batch_profile(self._h, 1 if enable else 0))
