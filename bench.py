@@ -410,10 +410,12 @@ def run_ours(args, rank, world):
     res = {
         "metric": METRIC, "value": round(value, 2), "unit": "events/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(t_dev * 1e3 / K, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 vote arithmetic, u32 counters",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded helix events; the paper's dataset is not available)",
         "config": {"workload": WORKLOAD, "events_resident": N_POOL, "fill": "naive" if args.naive else "privatised",
-                   "contexts_in_flight": C, "peaks_only": bool(args.peaks_only), "tuning": tuning,
+                   "contexts_in_flight": C, "peaks_only": bool(args.peaks_only),
+                   "arithmetic": "f32 vote arithmetic (IEEE round-to-nearest, no FMA), u32 vote counters",
+                   "tuning": tuning,
                    "l2": "inputs larger than L2: each step writes a 256 MiB M_H (L2 129 MB), read back at its candidates",
                    "parallelism": f"replicas x{world}"},
         "results_checked": bool(steps_ok),
@@ -1093,7 +1095,7 @@ def run_reference(args, rank, world):
     return {"metric": METRIC, "value": round(value, 4), "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "impl": "reference",
-            "dtype": "f32 vote arithmetic, u32 counters", "data": "synthetic",
+            "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": round(value, 4), "unit": "events/s", "cores": 1, "kind": "oracle",
                              "sample": f"{per} of {n_sl} (theta,phi) slices of a paper-scale event per step "
