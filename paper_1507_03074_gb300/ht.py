@@ -335,7 +335,9 @@ def _cached_autotune(path, key: str, run, apply):
 
 
 class Context:
-    """One event at a time (ht_create / ht_fill / ht_find_maxima)."""
+    """One event at a time (ht_create / ht_fill / ht_find_maxima).  A context
+    owns its stream, staging, M_H and counters, so several contexts fed
+    round-robin, each on its own stream, keep several events in flight."""
 
     def __init__(self, binning: Binning, ranges: Ranges = Ranges(), threshold: int = 10,
                  max_hits: int = 65536):
