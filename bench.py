@@ -10,7 +10,9 @@ through the whole hot path: slice admission + counting sort, vote fill
           Events go round-robin to --contexts contexts, each with its own
           stream, so that one event's small kernels and its fill's ragged
           end overlap the next event's work; every event still runs through
-          its own per-event launches.  CUDA events on a stream that forks to
+          its own per-event launches; the fills take the faster in flight of
+          the single-event launch shape and the same at one CTA per SM (two
+          events' fills then share every SM).  CUDA events on a stream that forks to
           and joins the launching streams bracket the timed steps; every
           step's peak count is checked.  `one_context` is the same with one
           context (one event at a time).
@@ -278,6 +280,12 @@ def run_ours(args, rank, world):
         ctx.fill(*dev[k % N_POOL], naive=args.naive, peaks_only=args.peaks_only, stream=st)
         ctx.find_maxima(capacity=cap, out=out, count=cnt, stream=st)
 
+    # the launch shape of the events in flight (outside the timed region): the
+    # single-event choice, or the same fill at one CTA per SM so that two
+    # events' fills share every SM, whichever a short in-flight run finds faster
+    tun_fl = tuning if args.no_autotune or C == 1 else pick_in_flight(ctxs, sts, step, tuning)
+    for c in ctxs:
+        c.set_tuning(**tun_fl)
     for k in range(max(args.warmup, C)):
         step(k)
     torch.cuda.synchronize()
@@ -310,7 +318,9 @@ def run_ours(args, rank, world):
         got = step_counts.cpu().numpy()
         steps_ok = all(int(got[k]) == peaks[k % N_POOL] for k in range(K))
         barrier(world)
-        # the same steps with one context: one event at a time on one stream
+        # the same steps with one context: one event at a time on one stream,
+        # at the single-event launch shape
+        ctx.set_tuning(**tuning)
         for k in range(args.warmup):
             step1(k)
         e1a, e1b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -351,6 +361,7 @@ def run_ours(args, rank, world):
             e2e_times.append(time.perf_counter() - ts)
             n_peaks_e2e += len(pk)
         e2e_s = time.perf_counter() - t0
+        ctx.set_tuning(**tun_fl)
         # the same calls pipelined over the contexts (each on its own stream
         # with its own pinned staging): each step's peaks and count land in
         # its own slot of pinned host memory; one wait at the end
@@ -401,7 +412,9 @@ def run_ours(args, rank, world):
                     "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": profiled_traffic(dom),
                     "algorithmic_bytes_per_launch": algo[dom], "avg_launch_us": round(avg_s * 1e6, 2),
                     "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                    "note": "launch time from the one-context pass (the kernel alone on the GPU)",
+                    "note": "launch time from the one-context pass: the kernel alone on the GPU at the "
+                            "single-event launch shape (config.tuning); the timed region runs "
+                            "config.in_flight_tuning",
                     "in_flight": {"gbs": round(algo[dom] * value / world / 1e9, 1),
                                   "frac": round(algo[dom] * value / world / 1e9 / hbm_peak, 4),
                                   "note": "M_H bytes of every timed event / the timed region, events in flight"}}
@@ -413,7 +426,7 @@ def run_ours(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded helix events; the paper's dataset is not available)",
         "config": {"workload": WORKLOAD, "events_resident": N_POOL, "fill": "naive" if args.naive else "privatised",
-                   "contexts_in_flight": C, "peaks_only": bool(args.peaks_only),
+                   "contexts_in_flight": C, "in_flight_tuning": tun_fl, "peaks_only": bool(args.peaks_only),
                    "arithmetic": "f32 vote arithmetic (IEEE round-to-nearest, no FMA), u32 vote counters",
                    "tuning": tuning,
                    "l2": "inputs larger than L2: each step writes a 256 MiB M_H (L2 129 MB), read back at its candidates",
@@ -447,6 +460,8 @@ def run_ours(args, rank, world):
         "roofline": roofline,
         "clocks": clk.summary(),
     }
+    for c in ctxs:
+        c.set_tuning(**tuning)
     if not args.no_extras and world == 1:
         res["peaks_only"] = run_peaks_only(ctxs, dev, outs, cnts, cap, sts, args.steps, args.warmup, peaks)
         res["maxima_4d"] = run_maxima4d(ctxs, dev, outs, cnts, cap, sts, args.steps, args.warmup)
@@ -626,6 +641,23 @@ def timed_in_flight(sts, step, K, W):
     return ev0.elapsed_time(ev1) / K
 
 
+def pick_in_flight(ctxs, sts, step, tuning, n=600):
+    """The faster, over n in-flight steps, of the single-event launch shape and
+    the same shape with one fill CTA per SM (two events' fills then share each
+    SM); leaves the contexts at the choice."""
+    cands = [dict(tuning), dict(tuning, fill_blocks_per_sm=1)]
+    best, best_ms = cands[0], None
+    for t in cands:
+        for c in ctxs:
+            c.set_tuning(**t)
+        ms = timed_in_flight(sts, step, n, len(ctxs))
+        if best_ms is None or ms < best_ms:
+            best, best_ms = t, ms
+    for c in ctxs:
+        c.set_tuning(**best)
+    return best
+
+
 def run_maxima4d(ctxs, dev, outs, cnts, cap, sts, K, W):
     C = len(ctxs)
 
@@ -643,7 +675,11 @@ def run_maxima4d(ctxs, dev, outs, cnts, cap, sts, K, W):
         ctx.find_maxima(capacity=cap, out=outs[0], count=cnts[0], stream=st, four_d=True)
         st.synchronize()
         n4.append(int(cnts[0].item()))
+    tun = ctx.get_tuning()
+    tun_fl = pick_in_flight(ctxs, sts, step, tun)
     ms = timed_in_flight(sts, step, K, W)
+    for c in ctxs:
+        c.set_tuning(**tun)
     ms1 = timed_in_flight(sts[:1], lambda k: run_on(0, k), K, W)
     ctx.profile(True)
     for k in range(max(1, K // 4)):
@@ -651,7 +687,7 @@ def run_maxima4d(ctxs, dev, outs, cnts, cap, sts, K, W):
     prof = ctx.profile_read()
     ctx.profile(False)
     return {"events_per_s": round(1e3 / ms, 1), "ms_per_step": round(ms, 4), "contexts_in_flight": C,
-            "one_context_events_per_s": round(1e3 / ms1, 1),
+            "in_flight_tuning": tun_fl, "one_context_events_per_s": round(1e3 / ms1, 1),
             "peaks_per_event": float(np.mean(n4)),
             "kernels": {kn: {"launches": n, "avg_us": round(t / n * 1e3, 2)} for kn, (n, t) in prof.items() if n},
             "note": "HT_MAXIMA_4D: 80 neighbours in (theta, phi, A, B); the 2-D peaks filtered against the "
@@ -695,7 +731,11 @@ def run_peaks_only(ctxs, dev, outs, cnts, cap, sts, K, W, peaks_ref):
         ctx.find_maxima(capacity=cap, out=outs[0], count=cnts[0], stream=st)
         st.synchronize()
         same = same and int(cnts[0].item()) == peaks_ref[k]
+    tun = ctx.get_tuning()
+    tun_fl = pick_in_flight(ctxs, sts, step, tun)
     ms = timed_in_flight(sts, step, K, W)
+    for c in ctxs:
+        c.set_tuning(**tun)
     ms1 = timed_in_flight(sts[:1], lambda k: run_on(0, k), K, W)
     ctx.profile(True)
     for k in range(max(1, K // 4)):
@@ -703,7 +743,7 @@ def run_peaks_only(ctxs, dev, outs, cnts, cap, sts, K, W, peaks_ref):
     prof = ctx.profile_read()
     ctx.profile(False)
     return {"events_per_s": round(1e3 / ms, 1), "ms_per_step": round(ms, 4), "contexts_in_flight": C,
-            "one_context_events_per_s": round(1e3 / ms1, 1),
+            "in_flight_tuning": tun_fl, "one_context_events_per_s": round(1e3 / ms1, 1),
             "kernels": {kn: {"launches": n, "avg_us": round(t / n * 1e3, 2)} for kn, (n, t) in prof.items() if n},
             "same_peak_counts": bool(same),
             "note": "HT_PEAKS_ONLY: peaks found in the fill's shared-memory tiles, M_H not written; "

@@ -226,7 +226,8 @@ def test_device_mode_on_torch_stream(ht):
     assert np.array_equal(Md.cpu().numpy().view(np.uint32).reshape(b.shape()), M_ref)
 
 
-def test_contexts_in_flight(ht):
+@pytest.mark.parametrize("tuning", [None, dict(fill_blocks_per_sm=1)], ids=["default", "one_fill_cta_per_sm"])
+def test_contexts_in_flight(ht, tuning):
     # Several contexts on their own streams, events issued round-robin with no
     # waits in between (the bench's events in flight): every event's peaks and
     # the last M_H of every context equal the oracle's; odd rounds take the
@@ -243,6 +244,9 @@ def test_contexts_in_flight(ht):
     ctxs = [ht.Context(b, r, threshold=T, max_hits=4096) for _ in range(C)]
     sts = [torch.cuda.Stream() for _ in range(C)]
     try:
+        for c in ctxs:
+            if tuning:
+                c.set_tuning(**tuning)
         dev = [tuple(torch.from_numpy(a).cuda() for a in e) for e in evs]
         outs = [torch.zeros(cap * 8, dtype=torch.int32, device="cuda") for _ in range(n_ev)]
         cnts = torch.zeros(n_ev, dtype=torch.int32, device="cuda")
@@ -364,6 +368,7 @@ TUNINGS = [
     dict(fill_fused_scan=3, fill_rows=32, fill_hits_staged=1024),
     dict(fill_fused_scan=4), dict(fill_fused_scan=4, fill_rows=16), dict(fill_fused_scan=4, fill_rows=8, fill_threads=512),
     dict(fill_fused_scan=4, fill_hits_staged=64),
+    dict(fill_blocks_per_sm=1),
 ]
 
 
