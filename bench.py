@@ -473,7 +473,7 @@ def run_ours(args, rank, world):
         c.close()
     if not args.no_extras and world == 1:
         res["batched"] = run_batched()
-        res["serving"] = run_serving(args.serving_seconds)
+        res["serving"] = run_serving(args.serving_seconds, fill_blocks_per_sm=1)
         res["serving_peaks_only"] = run_serving(args.serving_seconds, rates=(10000, 50000), peaks_only=True,
                                                 per_event=False)
     if not args.no_cpu_baseline and world == 1:
@@ -910,7 +910,7 @@ def run_batched(n_events=100, reps=5):
 
 
 def run_serving(seconds=1.5, rates=(1000, 10000, 50000), pool_per_kind=48, warmup_s=1.0, peaks_only=False,
-                per_event=True):
+                per_event=True, fill_blocks_per_sm=0):
     """Poisson arrivals at each rate for `seconds`; hit counts lognormal
     (median 3000, sigma 1, clipped 200..50000); 90% binning 4x16x1024x1024,
     10% 8x32x2048x2048; threshold 10.  Requests reuse a pool of seeded events
@@ -938,7 +938,9 @@ def run_serving(seconds=1.5, rates=(1000, 10000, 50000), pool_per_kind=48, warmu
                        "90% 4x16x1024x1024 / 10% 8x32x2048x2048 u32; threshold 10", "rates": []}
     if peaks_only:
         out["workload"] += "; peaks-only lanes (HT_PEAKS_ONLY: the matrices are not written)"
-    with ht.Server(peaks_only=peaks_only) as S:
+    if fill_blocks_per_sm:
+        out["workload"] += f"; lanes' fills at {fill_blocks_per_sm} CTA(s) per SM (ht_server_cfg.fill_blocks_per_sm)"
+    with ht.Server(peaks_only=peaks_only, fill_blocks_per_sm=fill_blocks_per_sm) as S:
         # warm-up: lanes of both binnings
         warm = [S.submit(bins[k], r, THRESHOLD, *pools[k][i]) for k in (False, True) for i in range(4)]
         for t in warm:

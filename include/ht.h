@@ -365,6 +365,9 @@ typedef struct {
     uint32_t queue_depth;        /* waiting requests before ht_submit answers HT_E_BUSY; 0 = 65536 */
     uint32_t flags;              /* 0, or HT_PEAKS_ONLY: every micro-batch runs peaks-only fills (the
                                     same peaks; the lanes' matrices are not written) */
+    uint32_t fill_blocks_per_sm; /* fill CTAs per SM in every lane, 0 = the engine's choice (2 on
+                                    GB300); 1 lets the fills of micro-batches in flight on
+                                    several lanes share every SM; at most 32 */
 } ht_server_cfg;
 
 /* Create on the current CUDA device (cfg NULL = all defaults). */

@@ -238,6 +238,17 @@ Lane *make_lane(ht_server *s, const Key &k, bool *never)
         hte::runner_destroy(l->R);
         return nullptr;
     }
+    if (c.fill_blocks_per_sm) {
+        ht_tuning t{};
+        t.fill_blocks_per_sm = c.fill_blocks_per_sm;
+        bool poisoned = false;
+        if (hte::engine_set_tuning(l->R.E, t, &poisoned, &why) != HT_OK) {
+            cudaGetLastError();
+            cudaStreamDestroy(l->st);
+            hte::runner_destroy(l->R);
+            return nullptr;
+        }
+    }
     if ((c.flags & HT_PEAKS_ONLY) && hte::engine_ensure_edges(l->R.E, &why) != HT_OK) {
         cudaGetLastError();
         cudaStreamDestroy(l->st);
@@ -448,8 +459,9 @@ ht_status ht_server_create(const ht_server_cfg *cfg, ht_server **out)
         c.queue_depth = 65536;
     if (c.flags & ~(uint32_t)HT_PEAKS_ONLY)
         return hte::report(HT_E_INVAL, "server flags: 0 or HT_PEAKS_ONLY");
-    if (c.n_streams > 64 || c.max_batch > 4096 || c.max_hits_per_event > (1u << 24))
-        return hte::report(HT_E_INVAL, "n_streams <= 64, max_batch <= 4096, max_hits_per_event <= 2^24");
+    if (c.n_streams > 64 || c.max_batch > 4096 || c.max_hits_per_event > (1u << 24) || c.fill_blocks_per_sm > 32)
+        return hte::report(HT_E_INVAL,
+                           "n_streams <= 64, max_batch <= 4096, max_hits_per_event <= 2^24, fill_blocks_per_sm <= 32");
     ht_server *s = new (std::nothrow) ht_server();
     if (!s)
         return hte::report(HT_E_NOMEM, "host allocation failed");

@@ -52,7 +52,7 @@ class c_tuning(ctypes.Structure):
 class c_server_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("n_streams", ctypes.c_uint32),
                 ("max_batch", ctypes.c_uint32), ("max_hits_per_event", ctypes.c_uint32),
-                ("queue_depth", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+                ("queue_depth", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("fill_blocks_per_sm", ctypes.c_uint32)]
 
 
 class c_server_stats(ctypes.Structure):
@@ -655,9 +655,10 @@ class Server:
     """Request loop with continuous batching (ht_server_*, ht_submit, ht_poll)."""
 
     def __init__(self, hbm_budget_bytes: int = 0, n_streams: int = 0, max_batch: int = 0,
-                 max_hits_per_event: int = 0, queue_depth: int = 0, peaks_only: bool = False):
+                 max_hits_per_event: int = 0, queue_depth: int = 0, peaks_only: bool = False,
+                 fill_blocks_per_sm: int = 0):
         cfg = c_server_cfg(hbm_budget_bytes, n_streams, max_batch, max_hits_per_event, queue_depth,
-                           HT_PEAKS_ONLY if peaks_only else 0)
+                           HT_PEAKS_ONLY if peaks_only else 0, fill_blocks_per_sm)
         self._h = ctypes.c_void_p()
         check(lib().ht_server_create(ctypes.byref(cfg), ctypes.byref(self._h)))
 

@@ -126,3 +126,28 @@ def test_server_peaks_only_equals_alone(ht):
     cfg = ht.c_server_cfg(0, 0, 0, 0, 0, ht.HT_FILL_NAIVE)
     h = ctypes.c_void_p()
     assert ht.lib().ht_server_create(ctypes.byref(cfg), ctypes.byref(h)) == ht.HT_E_INVAL
+
+
+def test_server_one_fill_cta_per_sm_equals_alone(ht):
+    """Lanes at one fill CTA per SM (the fills of micro-batches on several
+    lanes then share every SM): the same peaks as each event alone, for two
+    binnings in a burst; more than 32 CTAs per SM is refused."""
+    bA, TA = ht.Binning(*synth.PAPER_BINNING), 10
+    bB, TB = ht.Binning(2, 8, 256, 256), 6
+    r = ht.Ranges()
+    evA = [(e.x, e.y, e.z) for e in synth.batch_events(10, seed0=3400, lo=200, hi=5000)]
+    evB = [(e.x, e.y, e.z) for e in synth.batch_events(6, seed0=3500, lo=200, hi=3000)]
+    refA = [_alone(ht, bA, r, TA, ev) for ev in evA]
+    refB = [_alone(ht, bB, r, TB, ev) for ev in evB]
+    with ht.Server(n_streams=3, max_batch=4, fill_blocks_per_sm=1) as S:
+        tickets = [("A", i, S.submit(bA, r, TA, *ev)) for i, ev in enumerate(evA)]
+        tickets += [("B", i, S.submit(bB, r, TB, *ev)) for i, ev in enumerate(evB)]
+        for kind, i, t in tickets:
+            status, pk, n = _wait(S, t)
+            want_pk, want_n = (refA if kind == "A" else refB)[i]
+            assert n == want_n
+            _same(pk, want_pk)
+    import ctypes
+    cfg = ht.c_server_cfg(0, 0, 0, 0, 0, 0, 33)
+    h = ctypes.c_void_p()
+    assert ht.lib().ht_server_create(ctypes.byref(cfg), ctypes.byref(h)) == ht.HT_E_INVAL
