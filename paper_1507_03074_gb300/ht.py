@@ -652,7 +652,10 @@ class Batch:
 
 
 class Server:
-    """Request loop with continuous batching (ht_server_*, ht_submit, ht_poll)."""
+    """Request loop with continuous batching (ht_server_*, ht_submit, ht_poll).
+    The arguments are ht_server_cfg's fields (0 = default); peaks_only sets
+    HT_PEAKS_ONLY lanes, fill_blocks_per_sm = 1 lets the fills of micro-batches
+    in flight on several lanes share every SM."""
 
     def __init__(self, hbm_budget_bytes: int = 0, n_streams: int = 0, max_batch: int = 0,
                  max_hits_per_event: int = 0, queue_depth: int = 0, peaks_only: bool = False,
