@@ -823,6 +823,7 @@ def run_batched(n_events=100, reps=5):
         ctxs[c].fill(*dev[k % n_events], stream=sts[c])
         ctxs[c].find_maxima(capacity=4096, out=outs[c], count=cnts[c], stream=sts[c])
 
+    tun_fl = pick_in_flight(ctxs, sts, step, ctxs[0].get_tuning(), n=200)
     ms_fl = timed_in_flight(sts, step, n_events * reps, 2 * C)
     slot = 1024
     res_pk = torch.zeros((n_events, slot * 8), dtype=torch.int32, pin_memory=True)
@@ -844,6 +845,7 @@ def run_batched(n_events=100, reps=5):
         c.close()
     res["per_event_in_flight"] = {"e2e_events_per_s": round(n_events / float(np.median(t_fl)), 1),
                                   "device_events_per_s": round(1e3 / ms_fl, 1), "contexts": C,
+                                  "in_flight_tuning": tun_fl,
                                   "latency_ms": {"p50_batch_of_100": round(float(np.median(t_fl)) * 1e3, 4),
                                                  "note": "all 100 events issued at once: each is ready when "
                                                          "its context reaches it"},
