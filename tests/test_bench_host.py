@@ -34,3 +34,27 @@ def test_cpu_baseline_single_and_all_cores():
         ac = res["all_cores"]
         assert "unavailable" not in ac, ac
         assert ac["cores"] == cores and ac["value"] > res["value"]
+
+
+def test_pick_in_flight_keeps_the_faster_shape(monkeypatch):
+    import bench
+
+    class FakeCtx:
+        def __init__(self):
+            self.t = None
+
+        def set_tuning(self, **t):
+            self.t = dict(t)
+
+    ctxs = [FakeCtx() for _ in range(4)]
+    base = {"fill_rows": 32, "fill_blocks_per_sm": 2}
+    for one_cta_faster in (True, False):
+        def fake_timed(sts, step, n, w):
+            bps = ctxs[0].t["fill_blocks_per_sm"]
+            assert all(c.t == ctxs[0].t for c in ctxs)      # every context runs the candidate
+            return (40.0 if bps == 1 else 50.0) if one_cta_faster else (60.0 if bps == 1 else 50.0)
+        monkeypatch.setattr(bench, "timed_in_flight", fake_timed)
+        best = bench.pick_in_flight(ctxs, [None] * 4, lambda k: None, base)
+        assert best["fill_blocks_per_sm"] == (1 if one_cta_faster else 2)
+        assert all(c.t == best for c in ctxs)
+        assert best["fill_rows"] == 32
