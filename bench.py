@@ -53,13 +53,23 @@ WORKLOAD = "paper-scale event: 4990 hits (396 tracks + 238 noise), M_H 4x16x1024
 METRIC = "events/s"
 N_POOL = 8              # distinct resident events cycled through the steps
 THRESHOLD = 10
+EVENTS_PER_STEP = 64    # one step = one group of events through the whole hot path
+L2_NOTE = "inputs larger than L2: each event writes a 256 MiB M_H (L2 129 MB), read back at its candidates"
+
+
+def bench_config(events_per_step):
+    """The workload a line is measured on (the same dict in both arms)."""
+    return {"workload": WORKLOAD, "events_per_step": events_per_step, "l2": L2_NOTE,
+            "parallelism": "replicas (one per GPU, no collective)"}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--events-per-step", type=int, default=EVENTS_PER_STEP,
+                    help="paper-scale events in one step (spread round-robin over the contexts)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--naive", action="store_true", help="time the naive global-atomic fill")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -262,6 +272,7 @@ def run_ours(args, rank, world):
 
     # events in flight: one context (and stream) per event slot, round-robin
     C = max(1, args.contexts)
+    E = max(1, args.events_per_step)
     ctxs = [ctx] + [ht.Context(b, r, threshold=THRESHOLD, max_hits=max_hits) for _ in range(C - 1)]
     for c in ctxs[1:]:
         c.set_tuning(**tuning)
@@ -271,33 +282,36 @@ def run_ours(args, rank, world):
         cnts = [cnt] + [torch.empty(1, dtype=torch.int32, device="cuda") for _ in range(C - 1)]
     st.synchronize()
 
-    def step(k, count=None):
-        c = k % C
-        ctxs[c].fill(*dev[k % N_POOL], naive=args.naive, peaks_only=args.peaks_only, stream=sts[c])
+    def event(i, count=None):
+        """Event i of the run: context i % C, pool event i % N_POOL."""
+        c = i % C
+        ctxs[c].fill(*dev[i % N_POOL], naive=args.naive, peaks_only=args.peaks_only, stream=sts[c])
         ctxs[c].find_maxima(capacity=cap, out=outs[c], count=cnts[c] if count is None else count, stream=sts[c])
 
-    def step1(k):
-        ctx.fill(*dev[k % N_POOL], naive=args.naive, peaks_only=args.peaks_only, stream=st)
+    def event1(i):
+        ctx.fill(*dev[i % N_POOL], naive=args.naive, peaks_only=args.peaks_only, stream=st)
         ctx.find_maxima(capacity=cap, out=out, count=cnt, stream=st)
 
     # the launch shape of the events in flight (outside the timed region): the
     # single-event choice, or the same fill at one CTA per SM so that two
     # events' fills share every SM, whichever a short in-flight run finds faster
-    tun_fl = tuning if args.no_autotune or C == 1 else pick_in_flight(ctxs, sts, step, tuning)
+    tun_fl = tuning if args.no_autotune or C == 1 else pick_in_flight(ctxs, sts, event, tuning)
     for c in ctxs:
         c.set_tuning(**tun_fl)
-    for k in range(max(args.warmup, C)):
-        step(k)
+    for i in range(max(args.warmup * E, C)):
+        event(i)
     torch.cuda.synchronize()
 
     # ---- device-resident timed region --------------------------------------
-    # The headline: K steps between two CUDA events on a stream that forks to
-    # and joins the contexts' streams, nothing else recorded in between
-    # (per-step marks and per-kernel events would sit between the dependent
-    # launches).  Each step's peak count lands in its own word.
+    # The headline: K steps of E events each between two CUDA events on a
+    # stream that forks to and joins the contexts' streams, nothing else
+    # recorded in between (per-event marks and per-kernel events would sit
+    # between the dependent launches).  Each event's peak count lands in its
+    # own word.
     K = args.steps
-    step_counts = torch.full((K,), -1, dtype=torch.int32, device="cuda")
-    count_views = [step_counts[k:k + 1] for k in range(K)]
+    NE = K * E
+    ev_counts = torch.full((NE,), -1, dtype=torch.int32, device="cuda")
+    count_views = [ev_counts[i:i + 1] for i in range(NE)]
     main = torch.cuda.Stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
@@ -307,54 +321,54 @@ def run_ours(args, rank, world):
         ev0.record(main)
         for s in sts:
             s.wait_stream(main)
-        for k in range(K):
-            step(k, count_views[k])
+        for i in range(NE):
+            event(i, count_views[i])
         for s in sts:
             main.wait_stream(s)
         ev1.record(main)
         main.synchronize()
         launches = sum(c.launches for c in ctxs) - launches0
         torch.cuda.synchronize()
-        got = step_counts.cpu().numpy()
-        steps_ok = all(int(got[k]) == peaks[k % N_POOL] for k in range(K))
+        got = ev_counts.cpu().numpy()
+        steps_ok = all(int(got[i]) == peaks[i % N_POOL] for i in range(NE))
         barrier(world)
-        # the same steps with one context: one event at a time on one stream,
+        # the same events with one context: one event at a time on one stream,
         # at the single-event launch shape
         ctx.set_tuning(**tuning)
-        for k in range(args.warmup):
-            step1(k)
+        for i in range(args.warmup * E):
+            event1(i)
         e1a, e1b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(st):
             e1a.record(st)
-            for k in range(K):
-                step1(k)
+            for i in range(NE):
+                event1(i)
             e1b.record(st)
         st.synchronize()
         one_ms = e1a.elapsed_time(e1b)
         barrier(world)
-        # per-step latency and per-kernel device times: one context again
-        # with a CUDA event after every step and around every kernel
-        K1 = max(1, K // 4)
-        marks = [torch.cuda.Event(enable_timing=True) for _ in range(K1 + 1)]
+        # per-event latency and per-kernel device times: one context again
+        # with a CUDA event after every event and around every kernel
+        NP = min(max(NE // 4, 400), 2000)
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(NP + 1)]
         ctx.profile(True)
         with torch.cuda.stream(st):
             marks[0].record(st)
-            for k in range(K1):
-                step1(k)
-                marks[k + 1].record(st)
+            for i in range(NP):
+                event1(i)
+                marks[i + 1].record(st)
         st.synchronize()
         prof = ctx.profile_read()
         ctx.profile(False)
         torch.cuda.synchronize()
         barrier(world)
-        # e2e: host buffers through the C ABI, copies inside the timed region
-        K2 = max(1, K // 4)
+        # e2e, blocking: host buffers through the C ABI, one round trip per event
+        NB = min(max(NE // 8, 400), 3000)
         host_cap = 4096
         e2e_times = []
         n_peaks_e2e = 0
         t0 = time.perf_counter()
-        for k in range(K2):
-            e = events[k % N_POOL]
+        for i in range(NB):
+            e = events[i % N_POOL]
             ts = time.perf_counter()
             ctx.fill(e.x, e.y, e.z)
             pk, n = ctx.find_maxima(capacity=host_cap)
@@ -362,28 +376,32 @@ def run_ours(args, rank, world):
             n_peaks_e2e += len(pk)
         e2e_s = time.perf_counter() - t0
         ctx.set_tuning(**tun_fl)
-        # the same calls pipelined over the contexts (each on its own stream
-        # with its own pinned staging): each step's peaks and count land in
-        # its own slot of pinned host memory; one wait at the end
-        slot_cap = 1024
-        res_pk = torch.zeros((K2, slot_cap * 8), dtype=torch.int32, pin_memory=True)
-        res_n = torch.zeros(K2, dtype=torch.int32, pin_memory=True)
+        # e2e, pipelined: the same calls over the contexts (each on its own
+        # stream with its own pinned staging), at least as many events as the
+        # headline and at least 400 or a quarter second's worth; each event's
+        # count lands in its own word of pinned host memory and its peaks in a
+        # ring of pinned slots; one wait at the end
+        rate_est = NE / max(ev0.elapsed_time(ev1) / 1e3, 1e-9)
+        N2 = max(NE, 400, int(0.25 * rate_est))
+        slot_cap, ring = 1024, 256
+        res_pk = torch.zeros((ring, slot_cap * 8), dtype=torch.int32, pin_memory=True)
+        res_n = torch.zeros(N2, dtype=torch.int32, pin_memory=True)
         for c in ctxs:
             c.sync()
         t0 = time.perf_counter()
-        for k in range(K2):
-            e = events[k % N_POOL]
-            c = ctxs[k % C]
+        for i in range(N2):
+            e = events[i % N_POOL]
+            c = ctxs[i % C]
             c.fill(e.x, e.y, e.z)
-            c.find_maxima(capacity=slot_cap, out=res_pk[k], count=res_n[k:k + 1])
+            c.find_maxima(capacity=slot_cap, out=res_pk[i % ring], count=res_n[i:i + 1])
         for c in ctxs:
             c.sync()
         e2e_pipe_s = time.perf_counter() - t0
         got_n = res_n.numpy().astype(np.int64)
-        pipe_ok = all(int(got_n[k]) == peaks[k % N_POOL] for k in range(K2))
+        pipe_ok = all(int(got_n[i]) == peaks[i % N_POOL] for i in range(N2))
         n_peaks_pipe = int(np.minimum(got_n, slot_cap).sum())
     total_ms = ev0.elapsed_time(ev1)
-    per_step = [marks[k].elapsed_time(marks[k + 1]) for k in range(K1)]
+    per_event = [marks[i].elapsed_time(marks[i + 1]) for i in range(NP)]
 
     t_dev = max_over_ranks(total_ms / 1e3, world)
     t_one = max_over_ranks(one_ms / 1e3, world)
@@ -394,30 +412,26 @@ def run_ours(args, rank, world):
             c.close()
         return None
 
-    kern = {kname: {"launches": n, "avg_us": (ms / n * 1e3 if n else None)} for kname, (n, ms) in prof.items() if n}
+    kern = {kname: round(ms / n * 1e3, 2) for kname, (n, ms) in prof.items() if n}
     # dominant kernel: largest total device time
     dom = max(((kname, ms) for kname, (n, ms) in prof.items() if n), key=lambda t: t[1])[0]
     hbm_peak, peak_src = measured_peaks()
     cells_bytes = b.n_cells * 4
-    algo = {"k_fill_priv": cells_bytes, "k_fill_scan": cells_bytes, "k_fill_ws": cells_bytes, "k_scan": cells_bytes,
-            "k_clear": cells_bytes, "k_fill_naive": None, "k_bin": None, "k_scatter": None,
-            "k_order": None}
+    algo = {"k_fill_priv": cells_bytes, "k_fill_scan": cells_bytes, "k_fill_ws": cells_bytes,
+            "k_fill_bulk": cells_bytes, "k_fill_tma": cells_bytes, "k_scan": cells_bytes, "k_clear": cells_bytes}
     n_dom, ms_dom = prof[dom]
     avg_s = ms_dom / n_dom / 1e3
-    value = K * world / t_dev
+    value = NE * world / t_dev
     roofline = None
     if algo.get(dom):
         ach = algo[dom] / avg_s / 1e9
         roofline = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
                     "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": profiled_traffic(dom),
                     "algorithmic_bytes_per_launch": algo[dom], "avg_launch_us": round(avg_s * 1e6, 2),
-                    "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                    "note": "launch time from the one-context pass: the kernel alone on the GPU at the "
-                            "single-event launch shape (config.tuning); the timed region runs "
-                            "config.in_flight_tuning",
+                    "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst",
+                    "launch_time_from": "one-context pass, single-event launch shape",
                     "in_flight": {"gbs": round(algo[dom] * value / world / 1e9, 1),
-                                  "frac": round(algo[dom] * value / world / 1e9 / hbm_peak, 4),
-                                  "note": "M_H bytes of every timed event / the timed region, events in flight"}}
+                                  "frac": round(algo[dom] * value / world / 1e9 / hbm_peak, 4)}}
     mean_votes = float(np.mean(votes))
 
     res = {
@@ -425,57 +439,47 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": round(t_dev * 1e3 / K, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded helix events; the paper's dataset is not available)",
-        "config": {"workload": WORKLOAD, "events_resident": N_POOL, "fill": "naive" if args.naive else "privatised",
-                   "contexts_in_flight": C, "in_flight_tuning": tun_fl, "peaks_only": bool(args.peaks_only),
-                   "arithmetic": "f32 vote arithmetic (IEEE round-to-nearest, no FMA), u32 vote counters",
-                   "tuning": tuning,
-                   "l2": "inputs larger than L2: each step writes a 256 MiB M_H (L2 129 MB), read back at its candidates",
-                   "parallelism": f"replicas x{world}"},
-        "results_checked": bool(steps_ok),
-        "one_context": {"value": round(K * world / t_one, 2), "unit": "events/s",
-                        "ms_per_step": round(t_one * 1e3 / K, 4),
-                        "note": "the same K steps through one context on one stream: one event at a time"},
-        "gvotes_per_s": round(value * mean_votes / 1e9, 3),
-        "gcandidates_per_s": round(value * float(np.mean(cands)) / 1e9, 3),
-        "candidates_per_event": int(np.mean(cands)),
-        "votes_per_event": int(mean_votes), "peaks_per_event": float(np.mean(peaks)),
-        "latency_ms": {"device_p50": round(float(np.percentile(per_step, 50)), 4),
-                       "device_p99": round(float(np.percentile(per_step, 99)), 4),
-                       "note": "device latencies and kernel times from a one-context pass of K/4 steps with "
-                               "an event per step and per kernel",
-                              "e2e_p50": round(float(np.percentile(e2e_times, 50)) * 1e3, 4),
-                       "e2e_p99": round(float(np.percentile(e2e_times, 99)) * 1e3, 4)},
-        "e2e": {"value": round(K2 * world / t_e2e_pipe, 2), "unit": "events/s",
-                "h2d_bytes_per_step": int(12 * np.mean([e.n_hits for e in events])),
-                "d2h_bytes_per_step": int(4 + 32 * n_peaks_pipe / K2),
-                "api": "ht_fill(host x,y,z) + ht_find_maxima(out, count in pinned host memory), "
-                       "issued back to back round-robin over the contexts, one wait at the end",
-                "results_checked": bool(pipe_ok),
-                "blocking_per_call": {"value": round(K2 * world / t_e2e, 2), "unit": "events/s",
-                                      "d2h_bytes_per_step": int(4 + 4 + 32 * n_peaks_e2e / K2),
-                                      "api": "ht_fill(host x,y,z) + ht_find_maxima(host out), one round trip "
-                                             "per event (latencies in latency_ms.e2e_*)"}},
+        "config": bench_config(E),
         "gpu_launches": int(launches),
-        "kernels": kern,
+        "results_checked": bool(steps_ok),
+        "e2e": {"value": round(N2 * world / t_e2e_pipe, 2), "unit": "events/s", "events": N2,
+                "h2d_bytes_per_step": int(E * 12 * np.mean([e.n_hits for e in events])),
+                "d2h_bytes_per_step": int(E * (4 + 32 * n_peaks_pipe / N2)),
+                "api": "ht_fill(host) + ht_find_maxima(pinned host out), round-robin over the contexts",
+                "results_checked": bool(pipe_ok),
+                "blocking_per_call": {"value": round(NB * world / t_e2e, 2), "events": NB,
+                                      "p50_ms": round(float(np.percentile(e2e_times, 50)) * 1e3, 4),
+                                      "p99_ms": round(float(np.percentile(e2e_times, 99)) * 1e3, 4)}},
         "roofline": roofline,
         "clocks": clk.summary(),
+        "run": {"events_per_step": E, "contexts_in_flight": C, "in_flight_tuning": tun_fl, "tuning": tuning,
+                "fill": "naive" if args.naive else "privatised", "peaks_only": bool(args.peaks_only),
+                "arithmetic": "f32 vote arithmetic (IEEE round-to-nearest, no FMA), u32 vote counters"},
+        "one_context": {"value": round(NE * world / t_one, 2), "us_per_event": round(t_one * 1e6 / NE, 2)},
+        "gvotes_per_s": round(value * mean_votes / 1e9, 3),
+        "gcandidates_per_s": round(value * float(np.mean(cands)) / 1e9, 3),
+        "votes_per_event": int(mean_votes), "peaks_per_event": float(np.mean(peaks)),
+        "latency_ms": {"device_p50": round(float(np.percentile(per_event, 50)), 4),
+                       "device_p99": round(float(np.percentile(per_event, 99)), 4), "events": NP},
+        "kernels_us": kern,
     }
     for c in ctxs:
         c.set_tuning(**tuning)
+    n_x = min(max(NE, 400), 4000)     # events per timed extra
     if not args.no_extras and world == 1:
-        res["peaks_only"] = run_peaks_only(ctxs, dev, outs, cnts, cap, sts, args.steps, args.warmup, peaks)
-        res["maxima_4d"] = run_maxima4d(ctxs, dev, outs, cnts, cap, sts, args.steps, args.warmup)
+        res["peaks_only"] = run_peaks_only(ctxs, dev, outs, cnts, cap, sts, n_x, 2 * C, peaks)
+        res["maxima_4d"] = run_maxima4d(ctxs, dev, outs, cnts, cap, sts, n_x, 2 * C)
         res["readout"] = run_readout(ctx, events, b, r)
-        res["sectors"] = run_sectors(dev, b, r, max_hits, args.steps, args.warmup, peaks)
-        res["components"] = run_components(dev, b, r, max_hits, float(np.mean(votes)), hbm_peak)
+        res["sectors"] = run_sectors(dev, b, r, max_hits, n_x // 4, 2 * C, peaks)
         res["upgrade"] = run_upgrade(hbm_peak)
+        res["components"] = run_components(dev, b, r, max_hits, float(np.mean(votes)), hbm_peak)
     for c in ctxs:
         c.close()
     if not args.no_extras and world == 1:
-        res["batched"] = run_batched()
-        res["serving"] = run_serving(args.serving_seconds, fill_blocks_per_sm=1)
         res["serving_peaks_only"] = run_serving(args.serving_seconds, rates=(10000, 50000), peaks_only=True,
                                                 per_event=False)
+        res["serving"] = run_serving(args.serving_seconds, fill_blocks_per_sm=1)
+        res["batched"] = run_batched()
     if not args.no_cpu_baseline and world == 1:
         res["cpu_baseline"] = cpu_baseline(budget_s=10.0)
     return res
@@ -525,10 +529,7 @@ def run_components(dev, b, r, max_hits, mean_votes, hbm_peak, steps=200):
                        "gvotes_per_s": round(mean_votes / nv_us / 1e3, 3),
                        "frac_of_l2_atomics_32mib": round(mean_votes / nv_us * 1e6 / l2_res, 4),
                        "frac_of_l2_atomics_256mib": round(mean_votes / nv_us * 1e6 / l2_hbm, 4)},
-        "l2_atomics": {"gupdates_per_s_32mib": round(l2_res / 1e9, 2), "gupdates_per_s_256mib": round(l2_hbm / 1e9, 2),
-                       "note": "ht_measure_atomics: red.global.add at pseudo-random words, 8 x 256 threads per SM"},
-        "note": f"per-kernel CUDA-event averages over {steps} events (fill_fused_scan=2: k_fill_priv then k_scan; "
-                "HT_FILL_NAIVE: k_clear then k_fill_naive); bytes = 4 per M_H cell; peak = measured HBM copy",
+        "l2_atomics": {"gupdates_per_s_32mib": round(l2_res / 1e9, 2), "gupdates_per_s_256mib": round(l2_hbm / 1e9, 2)},
     }
 
 
@@ -570,7 +571,7 @@ def run_upgrade(hbm_peak, n_events=4, steps=20):
     kern = {kn: t / n * 1e3 for kn, (n, t) in prof.items() if n}
     fill_us = kern.get("k_fill_scan")
     cells_bytes = b.n_cells * 4
-    return {"workload": "50 000 hits (3750 tracks + 5000 noise), M_H 8x32x2048x2048 u32 (4 GiB), threshold 10",
+    return {"workload": "50 000 hits, M_H 8x32x2048x2048 u32 (4 GiB)",
             "events_per_s": round(1e3 / ms, 2), "ms_per_event": round(ms, 4),
             "kernels_us": {kn: round(v, 1) for kn, v in kern.items()},
             "fill_gbs": round(cells_bytes / fill_us / 1e3, 1) if fill_us else None,
@@ -610,9 +611,7 @@ def run_sectors(dev, b, r, max_hits, K, W, peaks_ref, n_sectors=4):
         st.synchronize()
         ms = ev0.elapsed_time(ev1) / K
     return {"n_sectors": n_sectors, "events_per_s": round(1e3 / ms, 1), "ms_per_step": round(ms, 4),
-            "same_peak_counts": bool(same),
-            "note": "one M_H(A,B,theta) context per phi sector, forked onto its own stream and joined; "
-                    "merged peaks identical to the unsplit ones (tested); device-resident events"}
+            "same_peak_counts": bool(same)}
 
 
 # ---------------------------------------------------------------------------
@@ -686,12 +685,9 @@ def run_maxima4d(ctxs, dev, outs, cnts, cap, sts, K, W):
         run_on(0, k)
     prof = ctx.profile_read()
     ctx.profile(False)
-    return {"events_per_s": round(1e3 / ms, 1), "ms_per_step": round(ms, 4), "contexts_in_flight": C,
-            "in_flight_tuning": tun_fl, "one_context_events_per_s": round(1e3 / ms1, 1),
-            "peaks_per_event": float(np.mean(n4)),
-            "kernels": {kn: {"launches": n, "avg_us": round(t / n * 1e3, 2)} for kn, (n, t) in prof.items() if n},
-            "note": "HT_MAXIMA_4D: 80 neighbours in (theta, phi, A, B); the 2-D peaks filtered against the "
-                    "adjacent slices by one CTA; device-resident events; kernel times from one context"}
+    return {"events_per_s": round(1e3 / ms, 1), "one_context_events_per_s": round(1e3 / ms1, 1),
+            "in_flight_blocks_per_sm": tun_fl.get("fill_blocks_per_sm"), "peaks_per_event": float(np.mean(n4)),
+            "kernels_us": {kn: round(t / n * 1e3, 2) for kn, (n, t) in prof.items() if n}}
 
 
 # ---------------------------------------------------------------------------
@@ -705,10 +701,7 @@ def run_readout(ctx, events, b, r):
         ctx.fill(e.x, e.y, e.z)
         pk, _ = ctx.find_maxima(capacity=1 << 16)
         per.append(readout.match(ht.track_params(b, r, pk, synth.B_FIELD_T), e, b, r))
-    out = readout.summarise(per)
-    out["note"] = ("peaks read out on the host in FP64 (rho, varphi, p_T) and matched to the generator's tracks "
-                   "(centre within 1.5 cells in A and B, theta bin within one); findable = centre in the A/B range")
-    return out
+    return readout.summarise(per)
 
 
 # ---------------------------------------------------------------------------
@@ -742,12 +735,9 @@ def run_peaks_only(ctxs, dev, outs, cnts, cap, sts, K, W, peaks_ref):
         run_on(0, k)
     prof = ctx.profile_read()
     ctx.profile(False)
-    return {"events_per_s": round(1e3 / ms, 1), "ms_per_step": round(ms, 4), "contexts_in_flight": C,
-            "in_flight_tuning": tun_fl, "one_context_events_per_s": round(1e3 / ms1, 1),
-            "kernels": {kn: {"launches": n, "avg_us": round(t / n * 1e3, 2)} for kn, (n, t) in prof.items() if n},
-            "same_peak_counts": bool(same),
-            "note": "HT_PEAKS_ONLY: peaks found in the fill's shared-memory tiles, M_H not written; "
-                    "device-resident events, K steps between two CUDA events; kernel times from one context"}
+    return {"events_per_s": round(1e3 / ms, 1), "one_context_events_per_s": round(1e3 / ms1, 1),
+            "in_flight_blocks_per_sm": tun_fl.get("fill_blocks_per_sm"), "same_peak_counts": bool(same),
+            "kernels_us": {kn: round(t / n * 1e3, 2) for kn, (n, t) in prof.items() if n}}
 
 
 # ---------------------------------------------------------------------------
@@ -770,7 +760,7 @@ def run_batched(n_events=100, reps=5):
     x, y, z, off = ht.Batch.concat(host)
     n_hits = int(off[-1])
     st = torch.cuda.Stream()
-    res = {"workload": f"{n_events} events, hits U(500..5000) (total {n_hits}), M_H 4x16x1024x1024 u32, threshold 10"}
+    res = {"workload": f"{n_events} events, hits U(500..5000), 4x16x1024x1024"}
     # per event, through a context
     with ht.Context(b, r, threshold=THRESHOLD, max_hits=max(e.n_hits for e in evs)) as ctx:
         M = torch.empty(b.n_cells, dtype=torch.int32, device="cuda")
@@ -806,10 +796,8 @@ def run_batched(n_events=100, reps=5):
         e_.record(st)
         st.synchronize()
         t_dev = a.elapsed_time(e_) / 1e3
-    res["per_event"] = {"e2e_events_per_s": round(n_events / t_host, 1),
-                        "device_events_per_s": round(n_events / t_dev, 1),
-                        "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99)},
-                        "api": "ht_fill + ht_find_maxima per event"}
+    res["per_event"] = {"e2e": round(n_events / t_host, 1), "device": round(n_events / t_dev, 1),
+                        "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99)}
     # the same per-event calls with events in flight: 8 contexts, each on its
     # own stream, the events round-robin
     C = 8
@@ -843,13 +831,10 @@ def run_batched(n_events=100, reps=5):
     counts_fl = res_n.numpy().copy()
     for c in ctxs:
         c.close()
-    res["per_event_in_flight"] = {"e2e_events_per_s": round(n_events / float(np.median(t_fl)), 1),
-                                  "device_events_per_s": round(1e3 / ms_fl, 1), "contexts": C,
-                                  "in_flight_tuning": tun_fl,
-                                  "latency_ms": {"p50_batch_of_100": round(float(np.median(t_fl)) * 1e3, 4),
-                                                 "note": "all 100 events issued at once: each is ready when "
-                                                         "its context reaches it"},
-                                  "api": "ht_fill + ht_find_maxima per event, round-robin over the contexts"}
+    res["per_event_in_flight"] = {"e2e": round(n_events / float(np.median(t_fl)), 1),
+                                  "device": round(1e3 / ms_fl, 1), "contexts": C,
+                                  "blocks_per_sm": tun_fl.get("fill_blocks_per_sm"),
+                                  "all_100_ms": round(float(np.median(t_fl)) * 1e3, 3)}
     # one batch
     with ht.Batch(b, r, threshold=THRESHOLD, max_events=n_events, max_hits=n_hits + 64, capacity=1 << 17) as B:
         for _ in range(2):
@@ -895,19 +880,14 @@ def run_batched(n_events=100, reps=5):
         prof = B.profile_read()
         B.profile(False)
     t_b = float(np.median(lat_b)) / 1e3
-    res["batched"] = {"e2e_events_per_s": round(n_events / t_b, 1),
-                      "device_events_per_s": round(n_events / t_bdev, 1),
-                      "gvotes_per_s": round(votes / t_bdev / 1e9, 3),
-                      "latency_ms": {"p50": _pct(lat_b, 50), "p99": _pct(lat_b, 99),
-                                     "note": "every event of a batch is ready when the batch is"},
-                      "kernels_us_per_batch": {k: round(ms / n * 1e3, 1) for k, (n, ms) in prof.items() if n},
-                      "tuning": tuning, "api": "ht_batch_run (graph replay)"}
-    res["batched_peaks_only"] = {"e2e_events_per_s": round(n_events / (float(np.median(lat_po)) / 1e3), 1),
-                                 "device_events_per_s": round(n_events / t_podev, 1),
-                                 "same_counts": same_po,
-                                 "api": "ht_batch_run(..., HT_PEAKS_ONLY) (graph replay)"}
+    res["batch"] = {"e2e": round(n_events / t_b, 1), "device": round(n_events / t_bdev, 1),
+                    "gvotes_per_s": round(votes / t_bdev / 1e9, 3), "p50_ms": _pct(lat_b, 50),
+                    "p99_ms": _pct(lat_b, 99), "tuning": tuning,
+                    "kernels_us": {k: round(ms / n * 1e3, 1) for k, (n, ms) in prof.items() if n}}
+    res["batch_peaks_only"] = {"e2e": round(n_events / (float(np.median(lat_po)) / 1e3), 1),
+                               "device": round(n_events / t_podev, 1), "same_counts": same_po}
     res["per_event_in_flight"]["same_counts"] = bool(np.array_equal(counts_fl, counts))
-    res["votes_per_event"] = int(votes / n_events)
+    res["unit"] = "events/s (e2e: host buffers, copies included; device: inputs resident)"
     return res
 
 
@@ -936,12 +916,10 @@ def run_serving(seconds=1.5, rates=(1000, 10000, 50000), pool_per_kind=48, warmu
             pools[kind].append((e.x, e.y, e.z))
     L = ht.lib()
     sys.setswitchinterval(1e-4)          # let the polling thread run beside the arrival loop
-    out = {"workload": "Poisson arrivals; hits lognormal(median 3000, sigma 1) clipped 200..50000; "
-                       "90% 4x16x1024x1024 / 10% 8x32x2048x2048 u32; threshold 10", "rates": []}
-    if peaks_only:
-        out["workload"] += "; peaks-only lanes (HT_PEAKS_ONLY: the matrices are not written)"
+    out = {"workload": "Poisson; hits lognormal(3000, 1) in 200..50000; 90% 4x16x1024^2 / 10% 8x32x2048^2",
+           "rates": []}
     if fill_blocks_per_sm:
-        out["workload"] += f"; lanes' fills at {fill_blocks_per_sm} CTA(s) per SM (ht_server_cfg.fill_blocks_per_sm)"
+        out["fill_blocks_per_sm"] = fill_blocks_per_sm
     with ht.Server(peaks_only=peaks_only, fill_blocks_per_sm=fill_blocks_per_sm) as S:
         # warm-up: lanes of both binnings
         warm = [S.submit(bins[k], r, THRESHOLD, *pools[k][i]) for k in (False, True) for i in range(4)]
@@ -1000,12 +978,10 @@ def run_serving(seconds=1.5, rates=(1000, 10000, 50000), pool_per_kind=48, warmu
             span = done_t[0] - t0
             st = S.stats(reset=True)
             out["rates"].append({
-                "offered_events_per_s": rate, "submitted_events_per_s": round((n - busy) / t_sub, 1),
-                "sustained_events_per_s": round((n - busy) / span, 1), "requests": n, "refused_busy": busy,
-                "latency_ms": {"p50": round(st["p50_us"] / 1e3, 4), "p99": round(st["p99_us"] / 1e3, 4),
-                               "max": round(st["max_us"] / 1e3, 4)},
-                "mean_micro_batch": round(st["mean_batch"], 2), "lanes": st["lanes"],
-                "lane_gib": round(st["lane_bytes"] / 2**30, 2)})
+                "offered": rate, "sustained": round((n - busy) / span, 1), "refused_busy": busy,
+                "p50_ms": round(st["p50_us"] / 1e3, 4), "p99_ms": round(st["p99_us"] / 1e3, 4),
+                "max_ms": round(st["max_us"] / 1e3, 4), "mean_batch": round(st["mean_batch"], 2),
+                "lanes": st["lanes"]})
     if not per_event:
         return out
     # the plain per-event path on the same streams: one context per binning,
@@ -1035,10 +1011,8 @@ def run_serving(seconds=1.5, rates=(1000, 10000, 50000), pool_per_kind=48, warmu
                 lat.append((time.perf_counter() - t0 - arr[i]) * 1e3)
             span = time.perf_counter() - t0
             out["per_event_path"].append({
-                "offered_events_per_s": rate, "requests": n, "sustained_events_per_s": round(n / span, 1),
-                "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "max": round(max(lat), 4)}})
-    out["per_event_note"] = ("per_event_path: the same Poisson streams (first <= 3000 arrivals) through one "
-                             "context per binning, ht_fill + ht_find_maxima per arrival, blocking, in order")
+                "offered": rate, "requests": n, "sustained": round(n / span, 1),
+                "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "max_ms": round(max(lat), 4)})
     return out
 
 
@@ -1108,42 +1082,46 @@ def cpu_baseline(budget_s=10.0):
 # ---------------------------------------------------------------------------
 
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands, single-threaded, on
+    whole paper-scale events (fill + maxima, the program cpu_baseline times).
+    A step of our arm is events_per_step events; here each step is a bounded
+    sample of that step (whole events until the step's time share has run),
+    so that --steps K --warmup W ends within a few minutes."""
     import oracle
     if rank != 0:
         return None
     ob, orr = oracle.Binning(*synth.PAPER_BINNING), oracle.Ranges()
-    n_sl = ob.n_slices
-    e = synth.paper_event(seed=1)
-    # calibrate: one slice (fill restricted to it + its maxima)
-    one = oracle.Binning(1, 1, ob.n_a, ob.n_b)
+    E = max(1, args.events_per_step)
+    n_ev = [0]
 
-    def slice_step(s):
-        Ms, _ = oracle.fill_slices(ob, orr, e.x, e.y, e.z, [s])
-        oracle.find_maxima(one, orr, Ms[0], THRESHOLD)
+    def one_event():
+        _oracle_event(ob, orr, synth.paper_event(seed=5000 + n_ev[0]))
+        n_ev[0] += 1
 
     t = time.perf_counter()
-    slice_step(0)
-    t_slice = max(time.perf_counter() - t, 1e-4)
-    budget_per_step = min(1.0, 120.0 / max(1, args.steps + args.warmup))
-    per = int(min(n_sl, max(1, round(budget_per_step / t_slice))))
-    for k in range(args.warmup):
-        slice_step((k * per) % n_sl)
+    one_event()
+    t_event = max(time.perf_counter() - t, 1e-4)
+    budget_per_step = min(2.0, 150.0 / max(1, args.steps + args.warmup))
+    per = int(min(E, max(1, round(budget_per_step / t_event))))
+    for _ in range(args.warmup):
+        for _ in range(per):
+            one_event()
     t0 = time.perf_counter()
     done = 0
-    for k in range(args.steps):
-        for q in range(per):
-            slice_step((k * per + q) % n_sl)
+    for _ in range(args.steps):
+        for _ in range(per):
+            one_event()
             done += 1
     dt = time.perf_counter() - t0
-    value = (done / n_sl) / dt
+    value = done / dt
     return {"metric": METRIC, "value": round(value, 4), "unit": "events/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps * E / per, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "impl": "reference",
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD},
+            "dtype": "f32", "data": "synthetic (seeded helix events; the paper's dataset is not available)",
+            "config": bench_config(E),
             "cpu_baseline": {"value": round(value, 4), "unit": "events/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{per} of {n_sl} (theta,phi) slices of a paper-scale event per step "
-                                       "(fill restricted to the slice + its maxima), extrapolated to events"},
+                             "sample": f"{per} of the {E} whole paper-scale events (fill + maxima) of each step, "
+                                       f"{done} events in {dt:.1f} s; ms_per_step scaled to {E} events"},
             "e2e": {"value": round(value, 4), "unit": "events/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 

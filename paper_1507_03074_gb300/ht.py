@@ -87,6 +87,10 @@ class Binning:
     win_phi: int = 0
 
     @property
+    def n_slices(self) -> int:
+        return self.n_theta * self.n_phi
+
+    @property
     def n_cells(self) -> int:
         return self.n_theta * self.n_phi * self.n_a * self.n_b
 
@@ -294,11 +298,29 @@ def _gpu_name() -> str:
         return "unknown"
 
 
+_BUILD_ID = None
+
+
+def _kernel_build_id() -> str:
+    """Hash of the library's CUDA and C++ sources: a cached launch shape is
+    only reused by the kernels it was timed with."""
+    global _BUILD_ID
+    if _BUILD_ID is None:
+        import hashlib
+        h = hashlib.sha256()
+        csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+        for f in sorted(os.listdir(csrc)):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+        _BUILD_ID = h.hexdigest()[:12]
+    return _BUILD_ID
+
+
 def _tuning_key(kind: str, binning: Binning, ranges: Ranges, threshold: int, sizes: str) -> str:
-    """Key of a cached launch-shape choice: GPU name, object kind, binning,
-    ranges, threshold and sizes."""
+    """Key of a cached launch-shape choice: GPU name, kernel sources, object
+    kind, binning, ranges, threshold and sizes."""
     b, r = binning, ranges
-    return (f"{_gpu_name()}|{kind}|{b.n_theta}x{b.n_phi}x{b.n_a}x{b.n_b}+{b.win_theta},{b.win_phi}|"
+    return (f"{_gpu_name()}|k{_kernel_build_id()}|{kind}|{b.n_theta}x{b.n_phi}x{b.n_a}x{b.n_b}+{b.win_theta},{b.win_phi}|"
             f"{r.theta_min},{r.theta_max},{r.phi_min},{r.phi_max},{r.a_min},{r.a_max},{r.b_min},{r.b_max}|"
             f"T{threshold}|{sizes}")
 
@@ -315,14 +337,18 @@ def _load_cache(path: str) -> dict:
 def _cached_autotune(path, key: str, run, apply):
     """Launch shapes from the JSON cache at `path` (None: $HT_TUNING_CACHE,
     unset: no cache).  A hit applies the stored shapes without timing; a miss
-    times them (run() -> (tuning, us)) and stores the choice."""
+    times them (run() -> (tuning, us)) and stores the choice.  A stored shape
+    the library refuses (apply raises HTError) counts as a miss."""
     path = path if path is not None else os.environ.get("HT_TUNING_CACHE")
     if path:
         hit = _load_cache(path).get(key)
         if isinstance(hit, dict) and isinstance(hit.get("tuning"), dict) and set(hit["tuning"]) <= set(TUNING_FIELDS):
             tun = {n: int(v) for n, v in hit["tuning"].items()}
-            apply(tun)
-            return tun, float(hit.get("us_per_event", 0.0))
+            try:
+                apply(tun)
+                return tun, float(hit.get("us_per_event", 0.0))
+            except HTError:
+                pass
     tun, us = run()
     if path:
         d = _load_cache(path)

@@ -1,10 +1,14 @@
 """Serving (ht_server_*): every request's peaks equal those of the event
-processed alone (ht_find_maxima through a context), whether it ran in a
-micro-batch with others, next to other binnings, or after lanes were freed
-and re-created under a tight memory budget."""
+processed alone (ht_find_maxima through a context) and those of the CPU
+oracle, whether it ran in a micro-batch with others, next to other binnings,
+or after lanes were freed and re-created under a tight memory budget.  The
+serving workload itself -- Poisson-stream hit counts, 4x16x1024x1024 events
+mixed with 8x32x2048x2048 events of 50 000 hits -- is checked against the
+oracle request by request."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1507_03074_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -151,3 +155,58 @@ def test_server_one_fill_cta_per_sm_equals_alone(ht):
     cfg = ht.c_server_cfg(0, 0, 0, 0, 0, 0, 33)
     h = ctypes.c_void_p()
     assert ht.lib().ht_server_create(ctypes.byref(cfg), ctypes.byref(h)) == ht.HT_E_INVAL
+
+
+# ---------------------------------------------------------------------------
+# The serving workload against the oracle
+# ---------------------------------------------------------------------------
+
+def _oracle(b, T, ev):
+    """Peaks of one event by the oracle's fill and maxima (Sec. 2)."""
+    ob, orr = oracle.Binning(*b.shape(), b.win_theta, b.win_phi), oracle.Ranges()
+    M, _ = oracle.fill(ob, orr, *ev)
+    pk, n = oracle.find_maxima(ob, orr, M, T)
+    del M
+    return pk, n
+
+
+@pytest.fixture(scope="module")
+def serving_mix(ht):
+    """24 requests of the serving stream (arrival order, hit counts lognormal
+    with median 3000 clipped to 200..50 000, 10 % of them in the upgrade
+    binning), with requests 3 and 11 replaced by 50 000-hit upgrade events;
+    each with the oracle's peaks."""
+    paper, upgrade = ht.Binning(*synth.PAPER_BINNING), ht.Binning(*synth.UPGRADE_BINNING)
+    _, n_hits, is_up, seeds = synth.serving_stream(10000.0, 24, seed=3000)
+    reqs = []
+    for i in range(24):
+        if i in (3, 11):
+            e = synth.upgrade_event(10 + i)
+            b = upgrade
+        else:
+            e = synth.make_event(*synth.split_hits(int(n_hits[i])), seed=int(seeds[i]))
+            b = upgrade if is_up[i] else paper
+        ev = (e.x, e.y, e.z)
+        reqs.append((b, ev, _oracle(b, 10, ev)))
+    assert sum(r[0] is upgrade for r in reqs) >= 2
+    assert sum(len(r[1][0]) == 50000 for r in reqs) >= 2
+    return reqs
+
+
+@pytest.mark.parametrize("cfg", [dict(n_streams=2, max_batch=4), dict(n_streams=3, max_batch=4, fill_blocks_per_sm=1),
+                                 dict(n_streams=2, max_batch=4, peaks_only=True)],
+                         ids=["default_lanes", "one_fill_cta_per_sm", "peaks_only"])
+def test_serving_mix_matches_oracle(ht, serving_mix, cfg):
+    """A burst of the serving workload: every polled result equals the
+    oracle's peak list for that event, element by element."""
+    r = ht.Ranges()
+    with ht.Server(**cfg) as S:
+        tickets = [S.submit(b, r, 10, *ev) for b, ev, _ in serving_mix]
+        for k, t in enumerate(tickets):
+            status, pk, n = _wait(S, t, capacity=1 << 17)
+            want, n_want = serving_mix[k][2]
+            assert status == ht.HT_OK and n == n_want, k
+            for f in PEAK_FIELDS[:-1]:
+                assert np.array_equal(pk[f], want[f]), (k, f)
+        st = S.stats()
+        assert st["completed"] == len(tickets) and st["lanes"] >= 2

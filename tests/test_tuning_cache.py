@@ -72,7 +72,8 @@ def test_miss_then_hit(fake, tmp_path):
     assert fake.timed == 1                     # no second timing
     assert fake.applied == [t1] and t2 == t1 and us2 == us1
     d = json.load(open(path))
-    assert len(d) == 1 and next(iter(d)).startswith("GB300-test|context|4x16x1024x1024")
+    key = next(iter(d))
+    assert len(d) == 1 and key.startswith(f"GB300-test|k{ht._kernel_build_id()}|context|4x16x1024x1024")
 
 
 def test_key_separates_configurations(fake, tmp_path, monkeypatch):
@@ -84,7 +85,10 @@ def test_key_separates_configurations(fake, tmp_path, monkeypatch):
     _ctx(b, max_hits=50000).autotune(cache=path)
     monkeypatch.setattr(ht, "_gpu_name", lambda: "another GPU")
     _ctx(b).autotune(cache=path)
-    assert fake.timed == 5 and len(json.load(open(path))) == 5
+    # other kernel sources: a shape timed with the old kernels is not reused
+    monkeypatch.setattr(ht, "_kernel_build_id", lambda: "changed")
+    _ctx(b).autotune(cache=path)
+    assert fake.timed == 6 and len(json.load(open(path))) == 6
 
 
 def test_env_default_and_no_cache(fake, tmp_path, monkeypatch):
@@ -123,3 +127,15 @@ def test_batch_cache(fake, tmp_path):
         B._h = ctypes.c_void_p()
     assert fake.timed == 1 and len(fake.applied) == 1
     assert "|batch|" in next(iter(json.load(open(path))))
+
+
+def test_refused_cached_shape_is_retuned(fake, tmp_path, monkeypatch):
+    """A cached shape that the library refuses (HT_E_INVAL from set_tuning)
+    is timed again instead of raising."""
+    path = str(tmp_path / "tuning.json")
+    b = ht.Binning(4, 16, 1024, 1024)
+    _ctx(b).autotune(cache=path)
+    monkeypatch.setattr(fake, "ht_set_tuning", lambda h, t: ht.HT_E_INVAL, raising=False)
+    monkeypatch.setattr(ht, "last_error", lambda: "refused")
+    t, us = _ctx(b).autotune(cache=path)
+    assert fake.timed == 2 and us == 61.5

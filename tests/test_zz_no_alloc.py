@@ -1,14 +1,18 @@
 """ht_find_maxima_noalloc: the maxima scan with the library's static scratch.
 
 Its peaks and counts must equal those of ht_find_maxima (through a context)
-on the same matrices, on consecutive calls that share the static scratch.
-Collected last (file name) so that it also runs after every other test.
+and those of the CPU oracle (Sec. 2: threshold plus local maxima of the
+(A, B) neighbourhood) on the same matrices, on consecutive calls that share
+the static scratch.  A call whose peaks overflow the scratch reports
+HT_E_NOMEM, and the next call still gives the right answer.  Collected last
+(file name) so that it also runs after every other test.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1507_03074_gb300 import synth
 
 
@@ -62,6 +66,19 @@ def _same(got, want):
         assert np.array_equal(got[f], want[f]), f
 
 
+def _oracle_peaks(b, r, T, M):
+    """The oracle's peak list of a device matrix (copied to the host)."""
+    ob = oracle.Binning(b.n_theta, b.n_phi, b.n_a, b.n_b, b.win_theta, b.win_phi)
+    Mh = M.cpu().numpy().view(np.uint32).reshape(b.shape())
+    return oracle.find_maxima(ob, oracle.Ranges(**r.__dict__), Mh, T)
+
+
+def _same_as_oracle(got, want):
+    assert len(got) == len(want)
+    for f in ("itheta", "iphi", "ia", "ib", "votes", "a_c", "b_c"):
+        assert np.array_equal(got[f], want[f]), f
+
+
 @pytest.mark.gpu
 def test_noalloc_matches_find_maxima():
     import torch
@@ -73,12 +90,16 @@ def test_noalloc_matches_find_maxima():
     MA, pkA, nA = _context_result(ht, b, r, 10, evA.x, evA.y, evA.z, cap)
     MB, pkB, nB = _context_result(ht, b, r, 10, evB.x, evB.y, evB.z, cap)
     assert nA > 0 and nB > 0 and nA != nB
+    refA, n_refA = _oracle_peaks(b, r, 10, MA)
+    refB, n_refB = _oracle_peaks(b, r, 10, MB)
+    assert (n_refA, n_refB) == (nA, nB)
 
     # two calls in a row on different matrices (the second sees the first's scratch)
     for M, pk, n in ((MA, pkA, nA), (MB, pkB, nB), (MA, pkA, nA)):
         got, cnt = _noalloc(ht, b, r, 10, M, 1, cap)
         assert cnt[0] == n
         _same(got[0, :n], pk)
+        _same_as_oracle(got[0, :n], refA if M is MA else refB)
 
     # both matrices in one call: per-event lists and counts
     MAB = torch.cat([MA, MB])
@@ -110,3 +131,38 @@ def test_noalloc_ragged_binning_direct_scan():
         got, cnt = _noalloc(ht, b, r, T, M, 1, 1 << 14)
         assert cnt[0] == n
         _same(got[0, :n], pk)
+        ref, n_ref = _oracle_peaks(b, r, T, M)
+        assert n_ref == n
+        _same_as_oracle(got[0, :n], ref)
+
+
+@pytest.mark.gpu
+def test_noalloc_scratch_overflow_then_recovers():
+    """524,288 isolated peaks (value T on every other row and column of a
+    1 x 1 x 2048 x 1024 matrix) exceed the 262,144 entries of the static
+    scratch: HT_E_NOMEM; the following call on an ordinary matrix, which
+    reuses the same array, equals the oracle."""
+    import torch
+    ht = _lib()
+    torch.cuda.init()
+    T = 3
+    b, r = ht.Binning(1, 1, 2048, 1024), ht.Ranges()
+    Mh = np.zeros((2048, 1024), np.uint32)
+    Mh[0::2, 0::2] = T
+    M = torch.from_numpy(Mh.view(np.int32).ravel().copy()).cuda()
+    cap = 16
+    out = torch.zeros(cap * 8, dtype=torch.int32, device="cuda")
+    counts = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(ht.HTError) as err:
+        ht.find_maxima_noalloc(b, r, T, M, 1, out, cap, counts)
+    assert err.value.status == ht.HT_E_NOMEM
+    assert "262144" in ht.last_error()
+
+    # the next call shares the array, whose counters it clears first
+    rng = np.random.default_rng(7)
+    Mr = rng.choice(np.arange(4, dtype=np.uint32), size=(2048, 1024), p=[0.5, 0.3, 0.15, 0.05])
+    Md = torch.from_numpy(Mr.view(np.int32).ravel().copy()).cuda()
+    ref, n_ref = _oracle_peaks(b, r, T, Md)
+    got, cnt = _noalloc(ht, b, r, T, Md, 1, n_ref + 8)
+    assert cnt[0] == n_ref
+    _same_as_oracle(got[0, :n_ref], ref)
