@@ -569,7 +569,7 @@ def run_upgrade(hbm_peak, n_events=4, steps=20):
         prof = ctx.profile_read()
         ctx.profile(False)
     kern = {kn: t / n * 1e3 for kn, (n, t) in prof.items() if n}
-    fill_us = kern.get("k_fill_scan")
+    fill_us = kern.get("k_fill_tma", kern.get("k_fill_scan"))
     cells_bytes = b.n_cells * 4
     return {"workload": "50 000 hits, M_H 8x32x2048x2048 u32 (4 GiB)",
             "events_per_s": round(1e3 / ms, 2), "ms_per_event": round(ms, 4),

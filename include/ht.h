@@ -260,9 +260,15 @@ ht_status ht_profile_read(ht_ctx *ctx, ht_kernel_time *out, uint32_t cap, uint32
  *                      tile leaves through two u32 staging buffers in shared
  *                      memory and bulk async copies (cp.async.bulk), so the
  *                      stores drain while the next votes run (1024 threads
- *                      by default; n_b a multiple of 4); 2: never (a full
- *                      scan in ht_find_maxima); 0: 1 when it fits (the fused
- *                      modes only for non-accumulating, non-naive fills)
+ *                      by default; n_b a multiple of 4); 5: as 1 with u32
+ *                      tiles in M_H's own layout (fill_rows rows, two in
+ *                      rotation), each pass leaving as one bulk async copy
+ *                      that no thread converts or stores, the votes listing
+ *                      the cells that reach the threshold (n_b a multiple of
+ *                      4); 2: never (a full scan in ht_find_maxima); 0: 5
+ *                      when n_b is a multiple of 4, else 1, when it fits
+ *                      (the fused modes only for non-accumulating, non-naive
+ *                      fills)
  * ht_set_tuning waits for the device, re-derives the shapes and returns
  * HT_E_INVAL for an impossible value; ht_get_tuning reports the shapes in
  * effect (0 fields filled in). */

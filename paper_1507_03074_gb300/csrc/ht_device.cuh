@@ -286,6 +286,17 @@ __device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t 
                  : "memory");
 }
 
+// bulk_store with an L2 evict-first policy: the written lines are the first
+// to leave L2 (the destination is written once and read back only in part).
+__device__ __forceinline__ void bulk_store_evict_first(void *dst, const void *src, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .b64 pol;\n\t"
+                 "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+                 "cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, pol;\n\t}" ::"l"(dst),
+                 "r"(smem_addr(src)), "r"(bytes)
+                 : "memory");
+}
+
 // Close the issuing thread's current bulk async-group.
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 

@@ -18,7 +18,7 @@ static const uint32_t kFusedPeakBuf = 512;     // K of a fused-fill CTA (at leas
 
 const char *const kKernelNames[K_NKINDS] = {"k_bin", "k_scatter", "k_fill_priv", "k_fill_scan", "k_fill_ws",
                                              "k_fill_peaks", "k_peaks", "k_clear", "k_fill_naive", "k_scan",
-                                             "k_order", "k_peaks4d"};
+                                             "k_order", "k_peaks4d", "k_fill_tma"};
 
 // ---------------------------------------------------------------------------
 // Profiling
@@ -124,8 +124,9 @@ ht_status engine_configure(Engine &E, std::string *why)
         *why = "fill_threads must be 256, 512 or 1024";
         return HT_E_INVAL;
     }
-    if (t.fused > 4) {
-        *why = "fused must be 0 (auto), 1 (on), 2 (off), 3 (warp-specialised) or 4 (bulk-copy stores)";
+    if (t.fused > 5) {
+        *why = "fused must be 0 (auto), 1 (on), 2 (off), 3 (warp-specialised), 4 (bulk-copy staging) or "
+               "5 (bulk-copy tiles)";
         return HT_E_INVAL;
     }
     f.HC = std::max(t.fill_HC ? t.fill_HC : 2048u, 2 * f.threads);   // hits staged per chunk
@@ -248,6 +249,56 @@ ht_status engine_configure(Engine &E, std::string *why)
         return HT_E_INVAL;
     }
     E.use_ws = E.ws_ok;
+    // --- fused fill with bulk-copy tiles: two u32 tiles in M_H's layout ----------
+    E.tma_ok = false;
+    // the default fused fill wherever it fits (fused 0 = auto)
+    if (E.fill_priv_ok && (t.fused == 5 || t.fused == 0) && (b.n_b & 3u) == 0 && b.n_b <= 4096) {
+        htk::FillCfg tf = f;
+        tf.threads = t.fill_threads ? t.fill_threads : 512;
+        uint32_t Wt = t.fill_W;
+        if (!Wt) {
+            // two tiles of about 64 KB together
+            Wt = 32;
+            while (Wt > 1 && (size_t)2 * Wt * b.n_b * 4 > 64 * 1024)
+                Wt >>= 1;
+        }
+        Wt = std::min<uint32_t>(Wt, 64);   // the hot-row mask holds 64 rows
+        tf.W = Wt;
+        tf.strips = (b.n_a + Wt - 1) / Wt;
+        tf.tile_words = Wt * b.n_b;
+        tf.tiles = 2;
+        tf.bulk = 0;
+        tf.dyn = 1;
+        tf.HC = std::max(t.fill_HC ? t.fill_HC : 2048u, 2 * tf.threads);
+        htk::ScanArgs tmp{};
+        tmp.K = std::max<uint32_t>(kFusedPeakBuf, tf.threads);
+        auto occupancy = [&](const htk::FillCfg &c) {
+            int o = 0;
+            if (htk::fill_tma_smem_bytes(c, tmp) > kSmemMax || htk::fill_tma_occupancy(c, tmp, &o) != cudaSuccess) {
+                cudaGetLastError();
+                return 0;
+            }
+            return o;
+        };
+        int occ = occupancy(tf);
+        while (!t.fill_HC && occ < 2 && tf.HC > 2 * tf.threads) {
+            tf.HC -= tf.threads;
+            occ = occupancy(tf);
+        }
+        if (occ >= 1) {
+            if (t.fill_blocks_per_sm)
+                occ = std::min<int>(occ, (int)t.fill_blocks_per_sm);
+            E.tma_ok = true;
+            E.tma_fill = tf;
+            E.tma_K = tmp.K;
+            E.tma_grid = (uint32_t)E.num_sms * (uint32_t)occ;
+        }
+    }
+    if (t.fused == 5 && !E.tma_ok) {
+        *why = "the bulk-copy-tile fused fill needs n_b a multiple of 4 (at most 4096) and tiles that fit";
+        return HT_E_INVAL;
+    }
+    E.use_tma = E.tma_ok;
     if ((t.fused == 1 || t.fused == 4) && !E.fused_ok) {
         *why = "the fused fill does not fit this binning and tuning";
         return HT_E_INVAL;
@@ -306,9 +357,13 @@ ht_status engine_configure(Engine &E, std::string *why)
     const uint64_t items_max = (uint64_t)E.max_events * g.n_slices * f.strips;
     const uint32_t fused_grid = E.fused_ok ? (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.fused_grid, items_max)) : 0;
     const uint32_t ws_grid = E.ws_ok ? (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.ws_grid, items_max)) : 0;
+    const uint64_t items_tma = E.tma_ok ? (uint64_t)E.max_events * g.n_slices * E.tma_fill.strips : 0;
+    const uint32_t tma_grid =
+        E.tma_ok ? (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.tma_grid, items_tma)) : 0;
     // the fused fill's candidate lists: one per CTA plus one per handed-out item
     const uint32_t fused_lists = fused_grid + (uint32_t)htk::dyn_items(items_max, fused_grid);
-    const uint32_t grid_cap = std::max(std::max(scan_grid, fused_lists), ws_grid);
+    const uint32_t tma_lists = E.tma_ok ? tma_grid + (uint32_t)htk::dyn_items(items_tma, tma_grid) : 0;
+    const uint32_t grid_cap = std::max(std::max(std::max(scan_grid, fused_lists), ws_grid), tma_lists);
     uint32_t seq = chunks_for((G_max + scan_grid - 1) / scan_grid + 1, (g.nb + 1) / 2, s.K, 2 * kScanThreads);
     // the cost-balanced split gives a CTA at most `spread` times the items of
     // an even split (every strip costs at least its n_b-per-row writing share)
@@ -322,6 +377,10 @@ ht_status engine_configure(Engine &E, std::string *why)
         const uint64_t fused_rows = rows_per_cta(fused_grid);
         seq = std::max(seq, chunks_for(fused_rows, g.nb, E.fused_K,
                                        htk::fused_round(E.fused_fill.threads, E.fused_K)));
+    }
+    if (E.tma_ok) {
+        const uint64_t tma_rows = (uint64_t)(std::ceil((double)items_tma / tma_grid * spread) + 2) * E.tma_fill.W + 1;
+        seq = std::max(seq, chunks_for(tma_rows, g.nb, E.tma_K, htk::fused_round(E.tma_fill.threads, E.tma_K)));
     }
     if (E.ws_ok) {
         const uint64_t ws_rows = rows_per_cta(ws_grid);
@@ -622,18 +681,22 @@ cudaError_t engine_vote(Engine &E, const uint32_t *d_hit_off, uint32_t n_hits0, 
     const uint64_t items = (uint64_t)n_events * E.geom.n_slices * f.strips;
     const bool peaks_only = (flags & HT_PEAKS_ONLY) && E.fused_ok && E.d_edge &&
                             E.edge_pass * std::max<uint32_t>(1, E.fused_fill.W / 2) >= E.geom.na;
-    if ((E.use_ws || E.fused_ok) && !accumulate) {
+    if ((E.use_ws || E.use_tma || E.fused_ok) && !accumulate) {
         htk::ScanArgs a = E.scan;
-        a.K = E.fused_K;
         const bool ws = E.use_ws && !peaks_only;
-        htk::FillCfg ff = ws ? E.ws_fill : E.fused_fill;
+        const bool tma = !ws && E.use_tma && !peaks_only;
+        a.K = tma ? E.tma_K : E.fused_K;
+        htk::FillCfg ff = ws ? E.ws_fill : tma ? E.tma_fill : E.fused_fill;
         ff.accumulate = 0u;
         ff.vote_weight = peaks_only ? htk::kPeaksVoteWeight : htk::kVoteWeight;
-        const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(ws ? E.ws_grid : E.fused_grid, items));
-        const uint32_t lists = grid + (ff.dyn ? (uint32_t)htk::dyn_items(items, grid) : 0u);
+        const uint64_t items_ff = (uint64_t)n_events * E.geom.n_slices * ff.strips;
+        const uint32_t grid = (uint32_t)std::max<uint64_t>(
+            1, std::min<uint64_t>(ws ? E.ws_grid : tma ? E.tma_grid : E.fused_grid, items_ff));
+        const uint32_t lists = grid + (ff.dyn ? (uint32_t)htk::dyn_items(items_ff, grid) : 0u);
         {
-            ProfScope ps(E, ws ? K_FILL_WS : peaks_only ? K_FILL_PEAKS : K_FILL_SCAN, st);
+            ProfScope ps(E, ws ? K_FILL_WS : tma ? K_FILL_TMA : peaks_only ? K_FILL_PEAKS : K_FILL_SCAN, st);
             e = ws ? htk::launch_fill_ws(E.geom, w, ff, a, grid, st)
+               : tma ? htk::launch_fill_tma(E.geom, w, ff, a, grid, st)
                : peaks_only ? htk::launch_fill_peaks(E.geom, w, ff, a, grid, st)
                             : htk::launch_fill_scan(E.geom, w, ff, a, grid, st);
         }
@@ -753,10 +816,24 @@ ht_status engine_autotune(Engine &E, uint32_t reps, cudaStream_t st, double *bes
     std::vector<Tuning> cands;
     const uint32_t rows_opts[] = {16, 32};
     const uint32_t thr_opts[] = {256, 512};
-    for (uint32_t fused = 1; fused <= 4; ++fused)
+    for (uint32_t fused = 1; fused <= 5; ++fused)
         for (uint32_t W : rows_opts)
             for (uint32_t th : thr_opts)
                 for (uint32_t kind = 1; kind <= (fused == 2 ? 2u : 1u); ++kind) {
+                    if (fused == 5) {
+                        // the bulk-copy-tile kernel: its own row counts (0 = two 64 KB tiles)
+                        if (th == thr_opts[0])
+                            continue;
+                        for (uint32_t Wt : {0u, W / 2})
+                            for (uint32_t tt : {512u, 1024u}) {
+                                Tuning t = user;
+                                t.fused = 5;
+                                t.fill_W = Wt;
+                                t.fill_threads = tt;
+                                cands.push_back(t);
+                            }
+                        continue;
+                    }
                     if (fused == 3 && th != htk::kWsThreads / 2)
                         continue;                // one group size for the warp-specialised kernel
                     if (fused == 4 && th != thr_opts[0])
@@ -857,7 +934,13 @@ void engine_get_tuning(const Engine &E, ht_tuning *t)
     t->scan_stage_bytes = E.scan.slot_words * 4;
     t->scan_slots = E.scan.S;
     t->scan_blocks_per_sm = E.num_sms ? E.scan_grid_max / (uint32_t)E.num_sms : 0;
-    t->fill_fused_scan = E.use_ws ? 3u : E.fused_ok ? (E.fused_fill.bulk ? 4u : 1u) : 2u;
+    t->fill_fused_scan = E.use_ws ? 3u : E.use_tma ? 5u : E.fused_ok ? (E.fused_fill.bulk ? 4u : 1u) : 2u;
+    if (E.use_tma) {
+        t->fill_rows = E.tma_fill.W;
+        t->fill_threads = E.tma_fill.threads;
+        t->fill_hits_staged = E.tma_fill.HC;
+        t->fill_blocks_per_sm = E.num_sms ? E.tma_grid / (uint32_t)E.num_sms : 0;
+    }
 }
 
 cudaError_t prof_read(Engine &E, ht_kernel_time *out, uint32_t cap, uint32_t *n)

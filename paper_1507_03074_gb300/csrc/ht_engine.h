@@ -23,14 +23,15 @@ struct Tuning {
     uint32_t scan_stage_bytes = 0;    // bulk-copy stage size
     uint32_t scan_slots = 0;          // bulk-copy ring depth (2..8)
     uint32_t scan_blocks_per_sm = 0;  // cap below the occupancy limit
-    uint32_t fused = 0;               // 0 auto, 1 fused (one thread group), 2 off, 3 fused warp-specialised
+    uint32_t fused = 0;               // 0 auto, 1 fused (one thread group), 2 off, 3 fused warp-specialised,
+                                      // 4 fused with bulk-copy staging, 5 fused with bulk-copy u32 tiles
 };
 
 // Optional per-kernel timing with CUDA events recorded on the launching
 // stream around every launch (enabled by ht_profile).
 enum KernelKind {
     K_BIN, K_SCATTER, K_FILL_PRIV, K_FILL_SCAN, K_FILL_WS, K_FILL_PEAKS, K_PEAKS, K_CLEAR, K_FILL_NAIVE, K_SCAN,
-    K_ORDER, K_PEAKS4D, K_NKINDS
+    K_ORDER, K_PEAKS4D, K_FILL_TMA, K_NKINDS
 };
 extern const char *const kKernelNames[K_NKINDS];
 
@@ -67,6 +68,11 @@ struct Engine {
     htk::FillCfg ws_fill{};      // its shape (threads = one group)
     uint32_t ws_grid = 0;
     bool use_ws = false;         // fills run the warp-specialised kernel
+    bool tma_ok = false;         // the bulk-copy-tile fused kernel fits
+    htk::FillCfg tma_fill{};     // its shape (two u32 tiles of W x n_b)
+    uint32_t tma_grid = 0;
+    uint32_t tma_K = 0;          // its peak buffer
+    bool use_tma = false;        // fills run the bulk-copy-tile kernel
     htk::ScanArgs scan{};
     int scan_kind = 0;            // htk::ScanKind in use
     uint32_t scan_grid_max = 0;

@@ -1021,18 +1021,23 @@ __device__ __forceinline__ bool is_peak_l2(const uint32_t *row, const uint32_t *
 // Append the candidate cells of one pass (rows iA .. iA + pr - 1 of slice
 // unit `slice_lin0`) to the CTA's candidate chunks, in linear order.  n_c
 // cells were listed as r * n_b + j in cand / candv (up to kFusedCand); with
-// more, the rows marked in hotm are read back: pass row r from rowsA + r n_b
-// when r < split, else from rowsB + (r - split) n_b -- M_H in global memory,
+// more, the rows marked in hotm are read back: pass row r from rowsA + r rs
+// when r < split, else from rowsB + (r - split) rs (rs = row_stride, or n_b
+// when it is 0) -- M_H in global memory,
 // or (SMEM) the shared staging buffers.  Entries are {lin within event,
-// event, votes, 0}.  All threads of the group call it.
-template <class G, bool SMEM = false>
+// event, votes, 0}.  TV (the tile-store fill): the votes of a listed key are
+// read from rowsA[key] (the pass's u32 tile, rows n_b apart) instead of
+// candv.  All threads of the group call it.
+template <class G, bool SMEM = false, bool TV = false>
 __device__ __forceinline__ void emit_pass(const Geom &g, const Work &w, const ScanArgs &a, ScanSmem &ss, uint4 *pbuf,
                                           uint32_t &buf_n, uint32_t &nseq, uint32_t &total, const ChunkList &inner,
                                           const uint32_t *cand, const uint32_t *candv, uint32_t *srt, uint32_t *srtv,
                                           uint32_t n_c, uint64_t hotm, uint32_t pr, uint32_t iA, uint32_t slice_lin0,
-                                          uint32_t e, const uint32_t *rowsA, const uint32_t *rowsB, uint32_t split)
+                                          uint32_t e, const uint32_t *rowsA, const uint32_t *rowsB, uint32_t split,
+                                          uint32_t row_stride = 0)
 {
     const uint32_t tid = G::rank(), bd = G::size(), nb = g.nb;
+    const size_t rs = row_stride ? row_stride : nb;   // words between consecutive rows of rowsA / rowsB
     const uint32_t lin0 = slice_lin0 + iA * nb;
     if (n_c <= 32u) {
         // few candidates: the first warp ranks them and writes them in order
@@ -1043,7 +1048,7 @@ __device__ __forceinline__ void emit_pass(const Geom &g, const Work &w, const Sc
             uint32_t rank = 0;
             for (uint32_t m = 0; m < n_c; ++m)
                 rank += cand[m] < key;
-            pbuf[buf_n + rank] = make_uint4(lin0 + key, e, candv[tid], 0u);
+            pbuf[buf_n + rank] = make_uint4(lin0 + key, e, TV ? rowsA[key] : candv[tid], 0u);
         }
         buf_n += n_c;
         total += n_c;
@@ -1057,7 +1062,7 @@ __device__ __forceinline__ void emit_pass(const Geom &g, const Work &w, const Sc
             for (uint32_t m = 0; m < n_c; ++m)
                 rank += cand[m] < key;
             srt[rank] = key;
-            srtv[rank] = candv[k];
+            srtv[rank] = TV ? rowsA[key] : candv[k];
         }
         // the sorted list is dense: append it to the chunk buffer as it is
         // (n_c <= kFusedCand <= K; a chunk is flushed with more than
@@ -1078,7 +1083,7 @@ __device__ __forceinline__ void emit_pass(const Geom &g, const Work &w, const Sc
     for (uint32_t r = 0; r < pr; ++r) {
         if (!((hotm >> r) & 1ull))
             continue;
-        const uint32_t *row = r < split ? rowsA + (size_t)r * nb : rowsB + (size_t)(r - split) * nb;
+        const uint32_t *row = r < split ? rowsA + (size_t)r * rs : rowsB + (size_t)(r - split) * rs;
         for (uint32_t j0 = 0; j0 < nb; j0 += per_round) {
             const uint32_t j = j0 + tid;
             uint32_t cnt = 0, pj[1], pv[1];
@@ -1316,6 +1321,201 @@ __global__ void __launch_bounds__(1024) k_fill_scan(Geom g, Work w, FillCfg c, S
 __global__ void __launch_bounds__(1024) k_fill_bulk(Geom g, Work w, FillCfg c, ScanArgs a)
 {
     fill_scan_body<true>(g, w, c, a);
+}
+
+// ---------------------------------------------------------------------------
+// k_fill_tma: the fused fill with the tiles leaving by bulk copies.
+//
+// The tiles hold u32 counters in M_H's own layout (rows n_b cells apart, no
+// swizzle), so a finished pass of W rows is one contiguous run of M_H and
+// leaves the SM as a single bulk copy (cp.async.bulk, shared -> global) that
+// one thread issues: no thread converts, stores or even reads the cells.
+// Two or three tiles rotate: while the copy engine drains pass p's tile, the
+// threads vote pass p + 1 into the next one; a tile is cleared once the
+// copy that read it is done.  The votes themselves list the cells that
+// reach the threshold (a returned count of T - 1), so no pass scans its
+// tile for candidates.  The candidates go the way of k_fill_scan's (ranked,
+// emitted as ordered entries, tested by k_peaks against the finished M_H).
+// Needs n_b a multiple of 4 (16-byte rows); at most 64 rows per pass.
+// ---------------------------------------------------------------------------
+
+// A thread's share of the candidates q = r * nc + h of a pass over nc staged
+// hits: q = tid, tid + blockDim, ..; (r0, h0) is its first, and each step
+// adds dr rows and dh hits (carrying into r).  Fixed for a unit's staged
+// hits, so the divisions are made once per staging, not once per pass.
+struct FlatMap {
+    uint32_t nc, r0, h0, dr, dh;
+    __device__ __forceinline__ void set(uint32_t n)
+    {
+        nc = n;
+        if (n) {
+            r0 = threadIdx.x / n;
+            h0 = threadIdx.x - r0 * n;
+            dr = blockDim.x / n;
+            dh = blockDim.x - dr * n;
+        }
+    }
+};
+
+// The votes of the staged hits hs[0 .. m.nc) into tile rows 0 .. pr - 1 (A
+// bins iA ..): candidate q = r * nc + h goes to thread q % blockDim, so a
+// warp's lanes take consecutive hits of one row (their B columns, and so
+// their banks, are spread by the hits).  A vote that lifts its cell from
+// T - 1 to T lists the cell as r * n_b + j.
+__device__ __forceinline__ void vote_flat(const Geom &g, uint32_t *tile, const float4 *hs, const float *beta,
+                                          const FlatMap &m, uint32_t pr, uint32_t iA, const FlushList &L)
+{
+    const uint32_t nb = g.nb, nc = m.nc;
+    if (nc == 0 || m.r0 >= pr)
+        return;
+    const uint32_t tm1 = g.threshold - 1u;
+    const float b_lo = beta[0], b_hi = beta[nb];
+    uint32_t r = m.r0, h = m.h0;
+#pragma unroll 2
+    while (r < pr) {
+        const float twoA = __fmul_rn(2.0f, a_centre(g, iA + r));
+        const float4 hv = hs[h];
+        const int j = vote_bin_tab(g, beta, b_lo, b_hi, twoA, hv.x, hv.y, hv.z);
+        if (j >= 0) {
+            const uint32_t key = r * nb + (uint32_t)j;
+            if (atomicAdd(&tile[key], 1u) == tm1)
+                note_candidate(L, r, key);
+        }
+        h += m.dh;
+        r += m.dr;
+        if (h >= nc) {
+            h -= nc;
+            ++r;
+        }
+    }
+}
+
+// One pass's votes from the hits of list entries l0 .. l1 of unit es,
+// staged HC at a time (kept staged, with their FlatMap, for the unit's next
+// passes when they fit, as vote_pass).  Starts with a block barrier in every
+// case: the previous pass's clearing of this tile is complete.  All threads
+// call it.
+__device__ __forceinline__ void vote_pass_flat(const Geom &g, const Work &w, uint32_t *tile, float4 *hs,
+                                               const float *beta, uint32_t HC, uint64_t es, uint32_t l0, uint32_t l1,
+                                               uint64_t &cached_es, FlatMap &cached, uint32_t pr, uint32_t iA,
+                                               const FlushList &L)
+{
+    if (cached_es == es) {
+        __syncthreads();
+        vote_flat(g, tile, hs, beta, cached, pr, iA, L);
+        return;
+    }
+    cached_es = ~0ull;   // hs is about to be overwritten
+    uint32_t pos = l0;
+    bool first = true;
+    while (first || pos < l1) {
+        const uint32_t nsel = stage_hits<BlockGroup>(w, hs, HC, pos, l1);   // starts with a barrier
+        FlatMap m;
+        m.set(nsel);
+        if (first && pos >= l1) {
+            cached_es = es;
+            cached = m;
+        }
+        first = false;
+        vote_flat(g, tile, hs, beta, m, pr, iA, L);
+    }
+}
+
+// NT tiles (2 or 3) rotate: after pass p's copy is issued, the copy of pass
+// p - (NT - 1) must have read its tile, which pass p + 1 then takes; with 3
+// tiles two copies stay in flight per CTA.
+template <int NT>
+__global__ void __launch_bounds__(1024) k_fill_tma(Geom g, Work w, FillCfg c, ScanArgs a)
+{
+    extern __shared__ uint4 sm4[];
+    // layout: ScanSmem (256 B) | K entries | NT tiles | HC staged hits | B thresholds |
+    //         candidate lists (keys, votes, sorted keys, sorted votes)
+    ScanSmem &ss = *reinterpret_cast<ScanSmem *>(sm4);
+    uint4 *pbuf = sm4 + 16;
+    uint32_t *tiles = reinterpret_cast<uint32_t *>(pbuf + a.K);
+    float4 *hs = reinterpret_cast<float4 *>(tiles + NT * c.tile_words);
+    float *beta = reinterpret_cast<float *>(hs + c.HC);
+    uint32_t *lists = reinterpret_cast<uint32_t *>(beta + c.beta_words);
+    uint32_t *cand = lists, *candv = lists + kFusedCand, *srt = lists + 2 * kFusedCand,
+             *srtv = lists + 3 * kFusedCand;
+    __shared__ uint32_t s_hot[2], s_nc;
+
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, nb = g.nb;
+    for (uint32_t k = tid; k < NT * c.tile_words / 4; k += bd)
+        reinterpret_cast<uint4 *>(tiles)[k] = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t k = tid; k <= nb; k += bd)
+        beta[k] = g.bth[k];
+    if (tid == 0)
+        s_hot[0] = s_hot[1] = s_nc = 0u;
+    grid_dep_wait();   // the unit lists of k_scatter
+    const uint32_t cta = blockIdx.x;
+    ChunkList inner = interior_list(a, cta);
+
+    __shared__ unsigned long long s_rng[2];
+    __shared__ uint32_t s_dyn;
+    const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
+    const uint64_t n_dyn = c.dyn ? dyn_items(items, gridDim.x) : 0, n_static = items - n_dyn;
+    uint64_t it0, it1;
+    cta_items(g, w, c, cta, gridDim.x, n_static, it0, it1, s_rng);
+    uint64_t cached_es = ~0ull;
+    FlatMap cached{};
+    uint32_t buf_n = 0, nseq = 0, total = 0;
+    uint32_t tsel = 0;   // the tile of the next pass
+
+    auto do_item = [&](const ItemCursor &cur) {
+        const uint64_t es = cur.es;
+        const uint32_t e = cur.e;
+        const uint32_t l0 = __ldg(&w.slice_off[es]), l1 = __ldg(&w.slice_off[es + 1]);   // the unit's hits
+        const uint32_t iA = cur.k * c.W;
+        const uint32_t pr = min(c.W, g.na - iA);
+        const uint32_t slice_lin0 = cur.s * g.na * nb;
+        uint32_t *tile = tiles + (size_t)tsel * c.tile_words;
+
+        // ---- vote (tile tsel is clear, the lists empty) ------------------------
+        vote_pass_flat(g, w, tile, hs, beta, c.HC, es, l0, l1, cached_es, cached, pr, iA,
+                       FlushList{s_hot, cand, candv, &s_nc, kFusedCand});
+        fence_proxy_async_smem();   // the tile's counts, visible to the copy engine
+        __syncthreads();            // votes and lists complete
+        // ---- the pass leaves as one bulk copy ------------------------------------
+        if (tid == 0) {
+            bulk_store_evict_first(w.M + (size_t)e * w.n_cells + slice_lin0 + (size_t)iA * nb, tile, pr * nb * 4u);
+            bulk_commit();
+        }
+        // ---- its candidates, votes read from the tile (the copy only reads it) --
+        const uint32_t n_c = s_nc;
+        const uint64_t hotm = (uint64_t)s_hot[0] | ((uint64_t)s_hot[1] << 32);
+        if (n_c)
+            emit_pass<BlockGroup, true, true>(g, w, a, ss, pbuf, buf_n, nseq, total, inner, cand, candv, srt, srtv,
+                                              n_c, hotm, pr, iA, slice_lin0, e, tile, nullptr, pr);
+        // ---- the next pass's tile: the copy that last read it is done -------------
+        const uint32_t next = tsel + 1u == (uint32_t)NT ? 0u : tsel + 1u;
+        if (tid == 0)
+            bulk_wait_read<NT - 1>();
+        __syncthreads();            // the lists are consumed; the next tile is free
+        uint4 *nt = reinterpret_cast<uint4 *>(tiles + (size_t)next * c.tile_words);
+#pragma unroll 4
+        for (uint32_t k = tid; k < c.tile_words / 4; k += bd)
+            nt[k] = make_uint4(0u, 0u, 0u, 0u);
+        if (tid == 0)
+            s_hot[0] = s_hot[1] = s_nc = 0u;
+        tsel = next;                // the next pass's votes start with a barrier
+    };
+    ItemCursor cur(g, c, it0);
+    for (uint64_t item = it0; item < it1; ++item, cur.next(g, c))
+        do_item(cur);
+    finish_candidates<BlockGroup>(w, a, ss, pbuf, buf_n, nseq, total, inner, cta);
+    if (c.dyn) {
+        // handed-out items, each with its own list of chunks
+        for (uint32_t d; (d = next_dyn_item(w, (uint32_t)n_dyn, &s_dyn)) < n_dyn;) {
+            const uint32_t list = gridDim.x + d;
+            inner = interior_list(a, list);
+            buf_n = nseq = total = 0;
+            do_item(ItemCursor(g, c, n_static + d));
+            finish_candidates<BlockGroup>(w, a, ss, pbuf, buf_n, nseq, total, inner, list);
+        }
+    }
+    if (tid == 0)
+        bulk_wait<0>();   // the last copies have written M_H (and read the tiles) before the CTA ends
 }
 
 // ---------------------------------------------------------------------------
@@ -2097,6 +2297,34 @@ cudaError_t launch_fill_peaks(const Geom &g, const Work &w, const FillCfg &c, co
     if (e != cudaSuccess)
         return e;
     return launch_pdl(k_fill_peaks, grid, c.threads, smem, st, g, w, c, a);
+}
+
+size_t fill_tma_smem_bytes(const FillCfg &c, const ScanArgs &a)
+{
+    return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)c.tiles * c.tile_words * 4 +
+           (size_t)c.HC * 16 + (size_t)c.beta_words * 4 + (size_t)4 * kFusedCand * 4;
+}
+
+cudaError_t launch_fill_tma(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
+                            cudaStream_t st)
+{
+    const size_t smem = fill_tma_smem_bytes(c, a);
+    const void *k = c.tiles == 3 ? (const void *)k_fill_tma<3> : (const void *)k_fill_tma<2>;
+    cudaError_t e = allow_smem(k, smem);
+    if (e != cudaSuccess)
+        return e;
+    return c.tiles == 3 ? launch_pdl(k_fill_tma<3>, grid, c.threads, smem, st, g, w, c, a)
+                        : launch_pdl(k_fill_tma<2>, grid, c.threads, smem, st, g, w, c, a);
+}
+
+cudaError_t fill_tma_occupancy(const FillCfg &c, const ScanArgs &a, int *blocks_per_sm)
+{
+    const size_t smem = fill_tma_smem_bytes(c, a);
+    const void *k = c.tiles == 3 ? (const void *)k_fill_tma<3> : (const void *)k_fill_tma<2>;
+    cudaError_t e = allow_smem(k, smem);
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, c.threads, smem);
 }
 
 cudaError_t fill_scan_occupancy(const FillCfg &c, const ScanArgs &a, uint32_t nb, int *blocks_per_sm)

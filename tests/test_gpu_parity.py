@@ -107,11 +107,13 @@ def test_fill_and_maxima_match_oracle(ht, case, naive):
     assert np.all(pk["event"] == 0)
 
 
+@pytest.mark.parametrize("mode", [4, 5], ids=["staging", "tiles"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_bulk_store_fill_matches_oracle(ht, case):
-    """The fused fill whose passes leave through shared-memory staging and
-    bulk async copies (fill_fused_scan=4): bit-exact M_H and peaks, or a
-    refusal when n_b is not a multiple of 4."""
+def test_bulk_store_fill_matches_oracle(ht, case, mode):
+    """The fused fills whose passes leave by bulk async copies -- through
+    shared-memory staging (fill_fused_scan=4) or as whole u32 tiles
+    (fill_fused_scan=5): bit-exact M_H and peaks, or a refusal when n_b is
+    not a multiple of 4."""
     name, bins, rng, T, (x, y, z) = case
     b, r = ht.Binning(*bins), ht.Ranges(**rng)
     M_ref, votes = oracle.fill(_ob(b), _orr(r), x, y, z)
@@ -119,10 +121,10 @@ def test_bulk_store_fill_matches_oracle(ht, case):
     with ht.Context(b, r, threshold=T, max_hits=max(len(x), 1)) as ctx:
         if b.n_b % 4:
             with pytest.raises(ht.HTError):
-                ctx.set_tuning(fill_fused_scan=4)
+                ctx.set_tuning(fill_fused_scan=mode)
             return
-        ctx.set_tuning(fill_fused_scan=4)
-        assert ctx.get_tuning()["fill_fused_scan"] == 4
+        ctx.set_tuning(fill_fused_scan=mode)
+        assert ctx.get_tuning()["fill_fused_scan"] == mode
         for _ in range(2):
             ctx.fill(x, y, z)
             pk, n = ctx.find_maxima(capacity=1 << 20)
@@ -133,7 +135,9 @@ def test_bulk_store_fill_matches_oracle(ht, case):
 
 U32_TUNINGS = [None, dict(fill_fused_scan=2), dict(fill_fused_scan=1, fill_rows=2, fill_threads=256),
                dict(fill_fused_scan=1, fill_rows=4, fill_threads=256), dict(fill_fused_scan=3, fill_rows=2),
-               dict(fill_fused_scan=3, fill_rows=8), dict(fill_fused_scan=4), dict(fill_fused_scan=4, fill_rows=4)]
+               dict(fill_fused_scan=3, fill_rows=8), dict(fill_fused_scan=4), dict(fill_fused_scan=4, fill_rows=4),
+               dict(fill_fused_scan=5), dict(fill_fused_scan=5, fill_rows=2, fill_threads=256),
+               dict(fill_fused_scan=5, fill_rows=64, fill_threads=1024)]
 
 
 @pytest.mark.parametrize("tuning", U32_TUNINGS, ids=[str(t) for t in U32_TUNINGS])
@@ -318,13 +322,45 @@ def test_random_matrix_scan(ht, shape, vmax, seed):
 
 
 # ---------------------------------------------------------------------------
-# Full-size upgrade binning (4 GiB matrix): sampled slices vs the oracle
+# Full-size upgrade binning (8 x 32 x 2048 x 2048, a 4 GiB matrix)
 # ---------------------------------------------------------------------------
 
-def test_upgrade_full_size_sampled(ht):
+def test_upgrade_full_size_complete(ht):
+    """One 50 000-hit upgrade event: the whole 4 GiB M_H (all 256 slices,
+    compared slice group by slice group on the host) and the whole peak list
+    equal the oracle's fill and maxima (Sec. 2, binning scaled up)."""
     import torch
     b, r = ht.Binning(*synth.UPGRADE_BINNING), ht.Ranges()
     ev = synth.upgrade_event(0)
+    ob, orr = _ob(b), _orr(r)
+    M_ref, votes_ref = oracle.fill(ob, orr, ev.x, ev.y, ev.z)
+    pk_ref, n_ref = oracle.find_maxima(ob, orr, M_ref, 10)
+    assert votes_ref > 50_000_000 and n_ref > 1000
+    with ht.Context(b, r, threshold=10, max_hits=ev.n_hits) as ctx:
+        ctx.fill(*(torch.from_numpy(a).cuda() for a in (ev.x, ev.y, ev.z)))
+        Md = torch.empty(b.n_cells, dtype=torch.int32, device="cuda")
+        ctx.matrix_into(Md)
+        ctx.sync()
+        pk, n = ctx.find_maxima(capacity=n_ref + 16)
+    Md = Md.view(b.n_slices, b.n_a * b.n_b)
+    Mr = M_ref.reshape(b.n_slices, b.n_a * b.n_b)
+    group = 16                                  # 256 MiB per host copy
+    for s0 in range(0, b.n_slices, group):
+        got = Md[s0:s0 + group].cpu().numpy().view(np.uint32)
+        if not np.array_equal(got, Mr[s0:s0 + group]):
+            bad = np.argwhere(got != Mr[s0:s0 + group])[0]
+            pytest.fail(f"M_H differs first at slice {s0 + bad[0]}, cell {bad[1]}")
+    del Md
+    assert n == n_ref
+    assert_peaks_equal(pk, pk_ref)
+
+
+def test_upgrade_full_size_sampled(ht):
+    """A second upgrade event: the vote total over all slices and six whole
+    slices (the busiest among them) with their peaks."""
+    import torch
+    b, r = ht.Binning(*synth.UPGRADE_BINNING), ht.Ranges()
+    ev = synth.upgrade_event(1)
     ob, orr = _ob(b), _orr(r)
     _, votes_ref = oracle.fill_slices(ob, orr, ev.x, ev.y, ev.z, np.arange(256), count_only=True)
     sl, _ = oracle.admit(ob, orr, ev.x, ev.y, ev.z)
@@ -368,6 +404,9 @@ TUNINGS = [
     dict(fill_fused_scan=3, fill_rows=32, fill_hits_staged=1024),
     dict(fill_fused_scan=4), dict(fill_fused_scan=4, fill_rows=16), dict(fill_fused_scan=4, fill_rows=8, fill_threads=512),
     dict(fill_fused_scan=4, fill_hits_staged=64),
+    dict(fill_fused_scan=5), dict(fill_fused_scan=5, fill_rows=16, fill_threads=1024),
+    dict(fill_fused_scan=5, fill_rows=4, fill_threads=256), dict(fill_fused_scan=5, fill_hits_staged=64),
+    dict(fill_fused_scan=5, fill_rows=2, fill_blocks_per_sm=1), dict(fill_fused_scan=5, fill_rows=8, fill_threads=1024),
     dict(fill_blocks_per_sm=1),
 ]
 
@@ -417,7 +456,9 @@ FUSED_TUNINGS = [dict(fill_fused_scan=2), dict(fill_fused_scan=1), dict(fill_fus
                  fill_threads=256), dict(fill_fused_scan=1, fill_rows=64, fill_threads=1024),
                  dict(fill_fused_scan=1, fill_rows=8, fill_blocks_per_sm=1), dict(fill_fused_scan=3),
                  dict(fill_fused_scan=3, fill_rows=4), dict(fill_fused_scan=3, fill_rows=64),
-                 dict(fill_fused_scan=4), dict(fill_fused_scan=4, fill_rows=4)]
+                 dict(fill_fused_scan=4), dict(fill_fused_scan=4, fill_rows=4),
+                 dict(fill_fused_scan=5), dict(fill_fused_scan=5, fill_rows=4), dict(fill_fused_scan=5, fill_rows=16),
+                 dict(fill_fused_scan=5, fill_rows=2, fill_threads=256)]
 
 
 def _track(A, B, theta, branch):
@@ -524,7 +565,7 @@ def test_autotune_keeps_results(ht, paper_ref):
             ctx.autotune()                        # nothing filled yet
         ctx.fill(ev.x, ev.y, ev.z)
         chosen, us = ctx.autotune(reps=3)
-        assert us > 0 and chosen["fill_fused_scan"] in (1, 2, 3, 4)
+        assert us > 0 and chosen["fill_fused_scan"] in (1, 2, 3, 4, 5)
         assert np.array_equal(ctx.matrix(), M_ref)
         pk, n = ctx.find_maxima(capacity=1 << 16)
         assert n == n_ref
