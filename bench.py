@@ -478,7 +478,7 @@ def run_ours(args, rank, world):
     if not args.no_extras and world == 1:
         res["serving_peaks_only"] = run_serving(args.serving_seconds, rates=(10000, 50000), peaks_only=True,
                                                 per_event=False)
-        res["serving"] = run_serving(args.serving_seconds, fill_blocks_per_sm=1)
+        res["serving"] = run_serving(args.serving_seconds)
         res["batched"] = run_batched()
     if not args.no_cpu_baseline and world == 1:
         res["cpu_baseline"] = cpu_baseline(budget_s=10.0)

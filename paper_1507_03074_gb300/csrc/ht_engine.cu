@@ -406,7 +406,10 @@ ht_status engine_configure(Engine &E, std::string *why)
             }
             E.book_bytes = need;
         }
-        if ((e = cudaMemset(E.d_book, 0, need)) != cudaSuccess) {
+        // cudaMemset of device memory is asynchronous (legacy default stream),
+        // and the objects' streams do not wait for that stream: wait here
+        if ((e = cudaMemset(E.d_book, 0, need)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(cudaStreamLegacy)) != cudaSuccess) {
             *why = std::string("scan bookkeeping initialisation failed: ") + cudaGetErrorString(e);
             return HT_E_CUDA;
         }
@@ -528,7 +531,10 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
                         cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(E.d_ctr, 0, (size_t)ctr_words * 4)) != cudaSuccess ||
         (e = cudaMemset(E.d_slice, 0, (3 * units + 1) * 4)) != cudaSuccess ||
-        (e = cudaMemset(E.d_M, 0, (size_t)E.n_cells * 4 * max_events)) != cudaSuccess) {
+        (e = cudaMemset(E.d_M, 0, (size_t)E.n_cells * 4 * max_events)) != cudaSuccess ||
+        // the memsets are asynchronous on the legacy default stream, which the
+        // objects' non-blocking streams do not wait for: finish them here
+        (e = cudaStreamSynchronize(cudaStreamLegacy)) != cudaSuccess) {
         std::snprintf(buf, sizeof buf, "device initialisation failed: %s", cudaGetErrorString(e));
         *why = buf;
         engine_destroy(E);
@@ -965,7 +971,10 @@ cudaError_t prof_read(Engine &E, ht_kernel_time *out, uint32_t cap, uint32_t *n)
 cudaError_t engine_set_phi_edges(Engine &E, const float *ep)
 {
     std::copy(ep, ep + E.ep.size(), E.ep.begin());
-    return cudaMemcpy(E.d_edges + E.et.size(), E.ep.data(), E.ep.size() * 4, cudaMemcpyHostToDevice);
+    // a pageable-source copy may still be in flight when cudaMemcpy returns,
+    // on the legacy stream the object's streams do not wait for
+    cudaError_t e = cudaMemcpy(E.d_edges + E.et.size(), E.ep.data(), E.ep.size() * 4, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? cudaStreamSynchronize(cudaStreamLegacy) : e;
 }
 
 ht_status engine_ensure_edges(Engine &E, std::string *why)

@@ -6,13 +6,16 @@
 // mapped pinned outputs) with its own stream -- through the same graph-
 // replayed kernel sequence as ht_batch_run.  Several lanes run at once, so
 // requests that arrive while others are on the GPU start as soon as a lane
-// frees up, and their work overlaps on the device.  A host function queued
-// behind each micro-batch wakes the worker, which hands the results out.
+// frees up, and their work overlaps on the device.  An event recorded behind
+// each micro-batch tells the worker that it is done; while any lane is busy,
+// or for kIdleSpin after the last activity, the worker polls those events
+// and the queue instead of sleeping, so neither a completion nor an arrival
+// waits for a thread to be woken.  Lanes of larger matrices get streams of
+// higher priority: a long fill is not stretched by the short ones that start
+// beside it (the latency tail is the long events').
 //
 // Locking: `mu` guards the queues and requests and is never held across a
-// CUDA call (a host function waits for nothing but `wake_mu`, which the
-// worker only holds to sleep), so no CUDA call can wait on a blocked host
-// function.
+// CUDA call.
 #include "ht_geom.h"
 #include "ht_runner.h"
 #include "ht_trace.h"
@@ -53,7 +56,7 @@ struct Request {
     uint32_t n = 0;
     std::vector<float> xyz;          // x | y | z
     Clock::time_point t_submit, t_done;
-    bool done = false;
+    std::atomic<bool> done{false};   // set under mu; read without it while a poller spins
     ht_status status = HT_OK;
     uint32_t n_found = 0;
     std::vector<ht_peak> peaks;      // the first min(n_found, room) peaks
@@ -66,7 +69,7 @@ struct Lane {
     uint32_t events = 0;             // micro-batch size
     uint64_t bytes = 0;              // device memory held
     bool busy = false;
-    std::atomic<bool> complete{false};
+    cudaEvent_t done_ev = nullptr;   // recorded behind the running micro-batch
     std::vector<Request *> reqs;     // the running micro-batch
     Clock::time_point last_used;
     struct ht_server *srv = nullptr;
@@ -104,13 +107,6 @@ void wake_worker(ht_server *s)
         s->wake = true;
     }
     s->wake_cv.notify_one();
-}
-
-void CUDART_CB lane_done(void *p)
-{
-    Lane *l = static_cast<Lane *>(p);
-    l->complete.store(true, std::memory_order_release);
-    wake_worker(l->srv);
 }
 
 uint64_t matrix_bytes(const Key &k)
@@ -176,7 +172,6 @@ void harvest(ht_server *s, Lane &l)
     s->done_cv.notify_all();
     l.reqs.clear();
     l.busy = false;
-    l.complete.store(false, std::memory_order_relaxed);
     l.last_used = now;
 }
 
@@ -186,10 +181,27 @@ void free_lane(ht_server *s, size_t i)
     Lane &l = *s->lanes[i];
     cudaStreamSynchronize(l.st);
     hte::runner_destroy(l.R);
+    cudaEventDestroy(l.done_ev);
     cudaStreamDestroy(l.st);
     std::lock_guard<std::mutex> g(s->mu);
     s->lane_bytes -= l.bytes;
     s->lanes.erase(s->lanes.begin() + (long)i);
+}
+
+// Stream priority of a lane: one level above the lowest per doubling of its
+// matrix beyond 64 MiB, capped at the device's highest (the 256 MiB paper
+// binning two levels up, the 4 GiB upgrade binning at the top).
+int lane_priority(const Key &k)
+{
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int up = 0;
+    for (uint64_t b = matrix_bytes(k); b > (64ull << 20); b >>= 1)
+        ++up;
+    return std::max(greatest, least - up);
 }
 
 // A new lane for key k, within the budget (freeing idle lanes of other
@@ -233,8 +245,14 @@ Lane *make_lane(ht_server *s, const Key &k, bool *never)
         cudaGetLastError();
         return nullptr;
     }
-    if (cudaStreamCreateWithFlags(&l->st, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithPriority(&l->st, cudaStreamNonBlocking, lane_priority(k)) != cudaSuccess) {
         cudaGetLastError();
+        hte::runner_destroy(l->R);
+        return nullptr;
+    }
+    if (cudaEventCreateWithFlags(&l->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamDestroy(l->st);
         hte::runner_destroy(l->R);
         return nullptr;
     }
@@ -244,6 +262,7 @@ Lane *make_lane(ht_server *s, const Key &k, bool *never)
         bool poisoned = false;
         if (hte::engine_set_tuning(l->R.E, t, &poisoned, &why) != HT_OK) {
             cudaGetLastError();
+            cudaEventDestroy(l->done_ev);
             cudaStreamDestroy(l->st);
             hte::runner_destroy(l->R);
             return nullptr;
@@ -251,6 +270,7 @@ Lane *make_lane(ht_server *s, const Key &k, bool *never)
     }
     if ((c.flags & HT_PEAKS_ONLY) && hte::engine_ensure_edges(l->R.E, &why) != HT_OK) {
         cudaGetLastError();
+        cudaEventDestroy(l->done_ev);
         cudaStreamDestroy(l->st);
         hte::runner_destroy(l->R);
         return nullptr;
@@ -282,11 +302,10 @@ bool dispatch(ht_server *s, Lane &l, std::vector<Request *> &&reqs)
     }
     l.reqs = std::move(reqs);
     l.busy = true;
-    l.complete.store(false, std::memory_order_relaxed);
     cudaError_t e = hte::runner_enqueue(R, (uint32_t)l.reqs.size(), off, true, true, l.st,
                                         (s->cfg.flags & HT_PEAKS_ONLY) != 0);
     if (e == cudaSuccess)
-        e = cudaLaunchHostFunc(l.st, lane_done, &l);
+        e = cudaEventRecord(l.done_ev, l.st);
     return e == cudaSuccess;
 }
 
@@ -403,27 +422,52 @@ bool schedule(ht_server *s)
     }
 }
 
+// How long ht_poll spins on its request before it sleeps on the condition
+// variable (at most its timeout).
+constexpr auto kPollSpin = std::chrono::microseconds(2000);
+
+// How long the worker keeps polling after its last dispatch, completion or
+// wake-up before it sleeps on the condition variable.
+constexpr auto kIdleSpin = std::chrono::microseconds(2000);
+
 void worker_main(ht_server *s)
 {
     cudaSetDevice(s->device);
+    Clock::time_point last = Clock::now();
     for (;;) {
         bool stopping;
         {
             std::lock_guard<std::mutex> g(s->mu);
             stopping = s->stop;
         }
-        for (auto &l : s->lanes)
-            if (l->busy && l->complete.load(std::memory_order_acquire))
-                harvest(s, *l);
+        for (auto &l : s->lanes) {
+            if (!l->busy)
+                continue;
+            const cudaError_t q = cudaEventQuery(l->done_ev);
+            if (q == cudaErrorNotReady)
+                continue;
+            if (q != cudaSuccess)
+                cudaGetLastError();   // a failed micro-batch: its status word reports it
+            harvest(s, *l);
+            last = Clock::now();
+        }
         bool busy_any = false;
         for (auto &l : s->lanes)
             busy_any = busy_any || l->busy;
         if (stopping && !busy_any)
             break;
-        if (!stopping)
-            schedule(s);
+        if (!stopping && schedule(s)) {
+            busy_any = true;
+            last = Clock::now();
+        }
+        if (busy_any || Clock::now() - last < kIdleSpin) {
+            std::this_thread::yield();
+            continue;
+        }
         std::unique_lock<std::mutex> lk(s->wake_mu);
         s->wake_cv.wait_for(lk, std::chrono::milliseconds(2), [&] { return s->wake; });
+        if (s->wake)
+            last = Clock::now();
         s->wake = false;
     }
     while (!s->lanes.empty())
@@ -535,13 +579,24 @@ ht_status ht_poll(ht_server *s, uint64_t ticket, ht_peak *out, uint32_t capacity
 {
     if (!s || !n_found || (capacity && !out))
         return hte::report(HT_E_INVAL, "NULL argument");
+    const Clock::time_point t_end = Clock::now() + std::chrono::microseconds(timeout_us);
+    const Clock::time_point spin_end = std::min(t_end, Clock::now() + kPollSpin);
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->tickets.find(ticket);
     if (it == s->tickets.end())
         return hte::report(HT_E_INVAL, "unknown ticket");
     Request *q = it->second;
+    // spin briefly (the result is usually near), then sleep on the condition
+    while (!q->done.load(std::memory_order_acquire) && Clock::now() < spin_end) {
+        lk.unlock();
+        std::this_thread::yield();
+        lk.lock();
+        it = s->tickets.find(ticket);   // another poller of the same ticket may have taken it
+        if (it == s->tickets.end())
+            return hte::report(HT_E_INVAL, "unknown ticket");
+    }
     if (!q->done)
-        s->done_cv.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return q->done; });
+        s->done_cv.wait_until(lk, t_end, [&] { return q->done.load(); });
     if (!q->done)
         return HT_PENDING;
     s->tickets.erase(it);

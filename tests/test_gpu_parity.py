@@ -355,6 +355,33 @@ def test_upgrade_full_size_complete(ht):
     assert_peaks_equal(pk, pk_ref)
 
 
+def test_first_fill_right_after_create_on_a_priority_stream(ht):
+    """The first fill of a new context, issued at once on a high-priority
+    stream of its own: it must not overlap the zeroing of the context's
+    buffers (4 GiB M_H, counters, bookkeeping), which creation finishes
+    before it returns.  Peaks equal the oracle's."""
+    import torch
+    b, r = ht.Binning(*synth.UPGRADE_BINNING), ht.Ranges()
+    ev = synth.upgrade_event(10)
+    M_ref, _ = oracle.fill(_ob(b), _orr(r), ev.x, ev.y, ev.z)
+    pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, 10)
+    del M_ref
+    d = [torch.from_numpy(a).cuda() for a in (ev.x, ev.y, ev.z)]
+    lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -5)
+    st = torch.cuda.Stream(priority=min(lo, hi))
+    torch.cuda.synchronize()
+    for _ in range(2):
+        with ht.Context(b, r, threshold=10, max_hits=ev.n_hits) as ctx:
+            ctx.fill(*d, stream=st)
+            out = torch.empty((n_ref + 16) * 8, dtype=torch.int32, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+            ctx.find_maxima(capacity=n_ref + 16, out=out, count=cnt, stream=st)
+            st.synchronize()
+            assert int(cnt.item()) == n_ref
+            pk = out.cpu().numpy().view(ht.PEAK_DTYPE)[:n_ref]
+        assert_peaks_equal(pk, pk_ref)
+
+
 def test_upgrade_full_size_sampled(ht):
     """A second upgrade event: the vote total over all slices and six whole
     slices (the busiest among them) with their peaks."""
