@@ -136,11 +136,26 @@ ht_status engine_configure(Engine &E, std::string *why)
     f.dyn = 1;   // the last items are handed out at run time (htk::dyn_items)
     f.vote_weight = htk::kVoteWeight;
     const size_t beta_bytes = (size_t)f.beta_words * 4;
-    uint32_t W = t.fill_W;
-    if (W && (W & (W - 1))) {
+    if (t.fill_W && (t.fill_W & (t.fill_W - 1))) {
         *why = "fill_rows must be a power of two";
         return HT_E_INVAL;
     }
+    // with the bulk-copy-tile fill (asked for, or automatic where n_b allows
+    // it) fill_rows sizes its tiles; the other fills (accumulating, peaks-only)
+    // keep their own tile height
+    bool tma_mode = (t.fused == 5 || t.fused == 0) && (b.n_b & 3u) == 0 && b.n_b <= 4096;
+    if (tma_mode && t.fill_W) {
+        // a requested tile height the bulk-copy-tile fill cannot hold leaves it to the others
+        htk::FillCfg probe = f;
+        probe.W = t.fill_W;
+        probe.tile_words = t.fill_W * b.n_b;
+        probe.tiles = 2;
+        probe.HC = 2 * f.threads;
+        htk::ScanArgs tmp{};
+        tmp.K = std::max<uint32_t>(kFusedPeakBuf, f.threads);
+        tma_mode = t.fill_W <= 64 && htk::fill_tma_smem_bytes(probe, tmp) <= kSmemMax;
+    }
+    uint32_t W = tma_mode ? 0u : t.fill_W;
     if (!W) {
         // aim at ~64 KB tiles so that two CTAs share an SM
         W = 32;
