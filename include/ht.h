@@ -269,6 +269,11 @@ ht_status ht_profile_read(ht_ctx *ctx, ht_kernel_time *out, uint32_t cap, uint32
  *                      when n_b is a multiple of 4, else 1, when it fits
  *                      (the fused modes only for non-accumulating, non-naive
  *                      fills)
+ *   fill_vote_agg      1: the bulk-copy-tile fill (fill_fused_scan 5)
+ *                      aggregates the vote increments of a warp -- lanes
+ *                      voting for the same cell find each other and one of
+ *                      them adds their number; 0: one shared-memory atomic
+ *                      per vote
  * ht_set_tuning waits for the device, re-derives the shapes and returns
  * HT_E_INVAL for an impossible value; ht_get_tuning reports the shapes in
  * effect (0 fields filled in). */
@@ -277,6 +282,7 @@ typedef struct {
     uint32_t fill_rows, fill_threads, fill_hits_staged, fill_blocks_per_sm;
     uint32_t scan_kind, scan_stage_bytes, scan_slots, scan_blocks_per_sm;
     uint32_t fill_fused_scan;
+    uint32_t fill_vote_agg;
 } ht_tuning;
 
 ht_status ht_set_tuning(ht_ctx *ctx, const ht_tuning *tuning);

@@ -124,6 +124,10 @@ ht_status engine_configure(Engine &E, std::string *why)
         *why = "fill_threads must be 256, 512 or 1024";
         return HT_E_INVAL;
     }
+    if (t.vote_agg > 1) {
+        *why = "fill_vote_agg must be 0 (plain shared-memory atomics) or 1 (warp-aggregated)";
+        return HT_E_INVAL;
+    }
     if (t.fused > 5) {
         *why = "fused must be 0 (auto), 1 (on), 2 (off), 3 (warp-specialised), 4 (bulk-copy staging) or "
                "5 (bulk-copy tiles)";
@@ -149,7 +153,6 @@ ht_status engine_configure(Engine &E, std::string *why)
         htk::FillCfg probe = f;
         probe.W = t.fill_W;
         probe.tile_words = t.fill_W * b.n_b;
-        probe.tiles = 2;
         probe.HC = 2 * f.threads;
         htk::ScanArgs tmp{};
         tmp.K = std::max<uint32_t>(kFusedPeakBuf, f.threads);
@@ -182,7 +185,6 @@ ht_status engine_configure(Engine &E, std::string *why)
         E.fill_grid = (uint32_t)E.num_sms * (uint32_t)occ;
     }
     E.clear_grid = (uint32_t)E.num_sms * 4;
-    E.naive_grid = (uint32_t)E.num_sms * 16;
 
     // --- fused fill + maxima ---------------------------------------------------
     // A smaller peak buffer than the scan's (the tile needs the room); k_seam
@@ -281,7 +283,7 @@ ht_status engine_configure(Engine &E, std::string *why)
         tf.W = Wt;
         tf.strips = (b.n_a + Wt - 1) / Wt;
         tf.tile_words = Wt * b.n_b;
-        tf.tiles = 2;
+        tf.vote_agg = t.vote_agg;
         tf.bulk = 0;
         tf.dyn = 1;
         tf.HC = std::max(t.fill_HC ? t.fill_HC : 2048u, 2 * tf.threads);
@@ -693,7 +695,7 @@ cudaError_t engine_vote(Engine &E, const uint32_t *d_hit_off, uint32_t n_hits0, 
             ++E.launches;
         }
         ProfScope ps(E, K_FILL_NAIVE, st);
-        e = htk::launch_fill_naive(E.geom, w, E.naive_grid, st);
+        e = htk::launch_fill_naive(E.geom, w, (uint32_t)E.num_sms, st);
         ++E.launches;
         return e;
     }
@@ -934,6 +936,7 @@ ht_status engine_set_tuning(Engine &E, const ht_tuning &t, bool *poisoned, std::
     n.scan_slots = t.scan_slots;
     n.scan_blocks_per_sm = t.scan_blocks_per_sm;
     n.fused = t.fill_fused_scan;
+    n.vote_agg = t.fill_vote_agg;
     ht_status s = engine_configure(E, why);
     if (s != HT_OK) {
         E.tune = old;
@@ -956,6 +959,7 @@ void engine_get_tuning(const Engine &E, ht_tuning *t)
     t->scan_slots = E.scan.S;
     t->scan_blocks_per_sm = E.num_sms ? E.scan_grid_max / (uint32_t)E.num_sms : 0;
     t->fill_fused_scan = E.use_ws ? 3u : E.use_tma ? 5u : E.fused_ok ? (E.fused_fill.bulk ? 4u : 1u) : 2u;
+    t->fill_vote_agg = E.use_tma ? E.tma_fill.vote_agg : 0u;
     if (E.use_tma) {
         t->fill_rows = E.tma_fill.W;
         t->fill_threads = E.tma_fill.threads;

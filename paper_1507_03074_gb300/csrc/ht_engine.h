@@ -25,6 +25,7 @@ struct Tuning {
     uint32_t scan_blocks_per_sm = 0;  // cap below the occupancy limit
     uint32_t fused = 0;               // 0 auto, 1 fused (one thread group), 2 off, 3 fused warp-specialised,
                                       // 4 fused with bulk-copy staging, 5 fused with bulk-copy u32 tiles
+    uint32_t vote_agg = 0;            // warp-aggregated vote increments (bulk-copy-tile fill)
 };
 
 // Optional per-kernel timing with CUDA events recorded on the launching
@@ -78,7 +79,7 @@ struct Engine {
     uint32_t scan_grid_max = 0;
     uint32_t grid_cap = 0;        // CTAs the bookkeeping arrays are sized for
     size_t book_bytes = 0;        // allocated bookkeeping
-    uint32_t clear_grid = 0, naive_grid = 0;
+    uint32_t clear_grid = 0;
     Tuning tune;
 
     // state of the last fill: peaks already found by the fused kernel

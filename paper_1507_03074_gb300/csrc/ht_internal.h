@@ -25,7 +25,7 @@ struct FillCfg {
     uint32_t dyn;         // 1: the last dyn_items() items are handed out at run time (see below)
     uint32_t bulk;        // fused fill: 1 = passes leave through u32 staging and bulk copies (k_fill_bulk)
     uint32_t vote_weight; // cost of one vote against one cell written, in the static split (cta_items)
-    uint32_t tiles;       // bulk-copy-tile fill: u32 tiles in rotation (2 or 3)
+    uint32_t vote_agg;    // bulk-copy-tile fill: warp-aggregated vote increments (match.any + one add)
 };
 
 // Shared-memory words of the fused fill's two u32 staging buffers (half a
@@ -87,7 +87,7 @@ size_t fill_ws_smem_bytes(const FillCfg &c, const ScanArgs &a);
 cudaError_t launch_fill_ws(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
                            cudaStream_t st);
 cudaError_t fill_ws_occupancy(const FillCfg &c, const ScanArgs &a, int *blocks_per_sm);
-// Fused fill whose passes leave as bulk copies of c.tiles rotating u32 tiles
+// Fused fill whose passes leave as bulk copies of two alternating u32 tiles
 // of W x n_b cells each (c.tile_words = W * n_b; n_b a multiple of 4).
 size_t fill_tma_smem_bytes(const FillCfg &c, const ScanArgs &a);
 cudaError_t launch_fill_tma(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
@@ -101,7 +101,7 @@ cudaError_t launch_peaks(const Geom &g, const Work &w, const FillCfg &c, const S
 cudaError_t launch_fill_peaks(const Geom &g, const Work &w, const FillCfg &c, const ScanArgs &a, uint32_t grid,
                               cudaStream_t st);
 cudaError_t launch_clear(uint32_t *M, uint64_t words, uint32_t grid, cudaStream_t st);
-cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
+cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t num_sms, cudaStream_t st);
 size_t scan_smem_bytes(const ScanArgs &a);
 
 // Layout of the counter block: [0] status, [1] entries used, [2] order

@@ -86,6 +86,12 @@ struct WarpGroup {
 // set-up that touches no global data of earlier kernels before this wait
 // (a no-op when the launch had no such dependency).
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel of the stream launch once every CTA of this one has
+// passed this point (its grid_dep_wait still waits for this kernel to end).
+// Only k_scatter uses it, after its own wait: what k_bin wrote is then
+// complete when the fill after k_scatter starts, so the fill may read the
+// unit offsets before its own wait.
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Exclusive scan of n values in shared memory (in place); returns the total.
 // All threads of the block must call it.  wsum: >= 33 words of scratch.
@@ -224,6 +230,7 @@ __global__ void __launch_bounds__(256) k_bin(Geom g, Work w)
 __global__ void __launch_bounds__(256) k_scatter(Geom g, Work w)
 {
     grid_dep_wait();
+    grid_dep_launch();   // k_bin is complete: the fill may start its set-up
     const uint32_t n = w.hit_off ? min(__ldg(&w.hit_off[w.n_events]), w.n_hits0) : w.n_hits0;
     const uint32_t stride = gridDim.x * blockDim.x, t0 = blockIdx.x * blockDim.x + threadIdx.x;
     for (uint32_t h = t0; h < n; h += stride) {
@@ -567,6 +574,35 @@ __device__ __forceinline__ uint32_t next_dyn_item(const Work &w, uint32_t n_dyn,
     return *s_word;
 }
 
+// The run-time items with the claim of the next one in flight: thread 0
+// claims an item (dyn_claim) while the block still works on the one before,
+// and dyn_take publishes the claim to the block, ending the hand-out as
+// next_dyn_item does (rank n_dyn: none left).  Each CTA claims until it
+// gets none, once per rank, so the counters reset as with next_dyn_item.
+__device__ __forceinline__ uint32_t dyn_claim(const Work &w, uint32_t n_dyn)
+{
+    return atomicAdd(&w.ctr[CTR_DYN], 1u);   // thread 0 only; n_dyn > 0
+}
+
+__device__ __forceinline__ uint32_t dyn_take(const Work &w, uint32_t n_dyn, uint32_t claim, uint32_t *s_word)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t d = claim;
+        if (d >= n_dyn) {
+            d = n_dyn;
+            __threadfence();
+            if (atomicAdd(&w.ctr[CTR_DYN_DONE], 1u) == gridDim.x - 1) {
+                w.ctr[CTR_DYN] = 0u;
+                w.ctr[CTR_DYN_DONE] = 0u;
+            }
+        }
+        *s_word = d;
+    }
+    __syncthreads();
+    return *s_word;
+}
+
 // Walks the (event, slice, strip) work items it0, it0 + 1, ... of a CTA with
 // one 64-bit decomposition at the start and carries afterwards (a 64-bit
 // division per item and thread costs more than a strip's flush setup).
@@ -674,24 +710,61 @@ __global__ void k_clear(uint32_t *M, uint64_t words)
         M[k] = 0u;
 }
 
-// 1-D grid over hits, a thread block over A, one atomicAdd per vote.
-__global__ void k_fill_naive(Geom g, Work w)
+// The unit (event, slice) of hit record rec of the (event, slice) lists: the
+// largest u' <= u with slice_off[u'] <= rec (slice_off[0] = 0), found by the
+// warp 32 units at a time.  Every lane returns it; the whole warp calls it.
+__device__ __forceinline__ uint32_t unit_below(const uint32_t *slice_off, uint32_t u, uint32_t rec)
 {
+    const uint32_t lane = threadIdx.x & 31u;
+    for (;;) {
+        const bool ok = lane <= u && __ldg(&slice_off[u - lane]) <= rec;
+        const uint32_t m = __ballot_sync(0xffffffffu, ok);
+        if (m)
+            return u - (uint32_t)(__ffs(m) - 1);
+        if (u < 32u)
+            return 0u;
+        u -= 32u;
+    }
+}
+
+// The paper's fill (Sec. 3): a 1-D grid over hits, a thread block over A,
+// one global atomicAdd per vote.  The hits come from k_scatter's (event,
+// slice) lists, one (hit, slice) record per block at a time, and the grid
+// (what the GPU holds at once) strides over the records from the last to
+// the first: the blocks in flight work on neighbouring records, so their
+// votes land in a few slices of M_H that stay in L2, and the first slices
+// voted are the last ones the clear wrote.  The B bin comes from the
+// threshold table in shared memory when it fits (48 KB), else from the
+// division rule; both give the same bin for every B.
+__global__ void __launch_bounds__(1024, 2) k_fill_naive(Geom g, Work w)
+{
+    extern __shared__ float s_beta[];   // n_b + 1 B-bin thresholds, or none
+    const uint32_t tid = threadIdx.x, bd = blockDim.x;
+    const bool tab = ((size_t)g.nb + 1) * 4 <= 48u * 1024u;
+    if (tab)
+        for (uint32_t k = tid; k <= g.nb; k += bd)
+            s_beta[k] = g.bth[k];
+    __syncthreads();
     grid_dep_wait();
-    for (uint32_t e = 0; e < w.n_events; ++e) {
-        const uint32_t h0 = ev_hit_begin(w, e), h1 = ev_hit_end(w, e);
-        uint32_t *M = w.M + (size_t)e * w.n_cells;
-        for (uint32_t h = h0 + blockIdx.x; h < h1; h += gridDim.x) {
-            const float4 hv = w.hits4[h];
-            for_each_slice(g, w.codes[h], [&](uint32_t s) {
-                uint32_t *Ms = M + (size_t)s * g.na * g.nb;
-                for (uint32_t i = threadIdx.x; i < g.na; i += blockDim.x) {
-                    const float twoA = __fmul_rn(2.0f, a_centre(g, i));
-                    const int j = vote_bin(g, twoA, hv.x, hv.y, hv.z);
-                    if (j >= 0)
-                        atomicAdd(&Ms[(size_t)i * g.nb + (uint32_t)j], 1u);
-                }
-            });
+    const float b_lo = tab ? s_beta[0] : 0.0f, b_hi = tab ? s_beta[g.nb] : 0.0f;
+    const uint32_t U = w.n_events * g.n_slices;
+    if (U == 0)
+        return;
+    const uint32_t n_rec = min(__ldg(&w.slice_off[U]), w.list_cap);
+    const uint64_t slice_cells = (uint64_t)g.na * g.nb;
+    uint32_t u = U - 1u;
+    for (uint32_t k = blockIdx.x; k < n_rec; k += gridDim.x) {
+        const uint32_t rec = n_rec - 1u - k;
+        u = unit_below(w.slice_off, u, rec);
+        const float4 hv = w.list[rec];
+        const uint32_t e = u / g.n_slices, s = u - e * g.n_slices;
+        uint32_t *Ms = w.M + (size_t)e * w.n_cells + (size_t)s * slice_cells;
+        for (uint32_t i = tid; i < g.na; i += bd) {
+            const float twoA = __fmul_rn(2.0f, a_centre(g, i));
+            const int j = tab ? vote_bin_tab(g, s_beta, b_lo, b_hi, twoA, hv.x, hv.y, hv.z)
+                              : vote_bin(g, twoA, hv.x, hv.y, hv.z);
+            if (j >= 0)
+                atomicAdd(&Ms[(size_t)i * g.nb + (uint32_t)j], 1u);
         }
     }
 }
@@ -1330,8 +1403,8 @@ __global__ void __launch_bounds__(1024) k_fill_bulk(Geom g, Work w, FillCfg c, S
 // swizzle), so a finished pass of W rows is one contiguous run of M_H and
 // leaves the SM as a single bulk copy (cp.async.bulk, shared -> global) that
 // one thread issues: no thread converts, stores or even reads the cells.
-// Two or three tiles rotate: while the copy engine drains pass p's tile, the
-// threads vote pass p + 1 into the next one; a tile is cleared once the
+// Two tiles alternate: while the copy engine drains pass p's tile, the
+// threads vote pass p + 1 into the other one; a tile is cleared once the
 // copy that read it is done.  The votes themselves list the cells that
 // reach the threshold (a returned count of T - 1), so no pass scans its
 // tile for candidates.  The candidates go the way of k_fill_scan's (ranked,
@@ -1361,14 +1434,18 @@ struct FlatMap {
 // bins iA ..): candidate q = r * nc + h goes to thread q % blockDim, so a
 // warp's lanes take consecutive hits of one row (their B columns, and so
 // their banks, are spread by the hits).  A vote that lifts its cell from
-// T - 1 to T lists the cell as r * n_b + j.
+// T - 1 to T lists the cell as r * n_b + j.  AGG: warp-aggregated increments
+// -- the lanes voting for the same cell find each other (match.any on the
+// cell index) and their lowest lane adds their number with one atomic; the
+// cell is listed by the add that takes it from below T to T or more.
+template <bool AGG>
 __device__ __forceinline__ void vote_flat(const Geom &g, uint32_t *tile, const float4 *hs, const float *beta,
                                           const FlatMap &m, uint32_t pr, uint32_t iA, const FlushList &L)
 {
     const uint32_t nb = g.nb, nc = m.nc;
     if (nc == 0 || m.r0 >= pr)
         return;
-    const uint32_t tm1 = g.threshold - 1u;
+    const uint32_t T = g.threshold, tm1 = T - 1u, lane = threadIdx.x & 31u;
     const float b_lo = beta[0], b_hi = beta[nb];
     uint32_t r = m.r0, h = m.h0;
 #pragma unroll 2
@@ -1378,8 +1455,17 @@ __device__ __forceinline__ void vote_flat(const Geom &g, uint32_t *tile, const f
         const int j = vote_bin_tab(g, beta, b_lo, b_hi, twoA, hv.x, hv.y, hv.z);
         if (j >= 0) {
             const uint32_t key = r * nb + (uint32_t)j;
-            if (atomicAdd(&tile[key], 1u) == tm1)
+            if (AGG) {
+                const uint32_t peers = __match_any_sync(__activemask(), key);
+                if (lane == (uint32_t)(__ffs(peers) - 1)) {
+                    const uint32_t n = (uint32_t)__popc(peers);
+                    const uint32_t old = atomicAdd(&tile[key], n);
+                    if (old < T && old + n >= T)
+                        note_candidate(L, r, key);
+                }
+            } else if (atomicAdd(&tile[key], 1u) == tm1) {
                 note_candidate(L, r, key);
+            }
         }
         h += m.dh;
         r += m.dr;
@@ -1395,6 +1481,7 @@ __device__ __forceinline__ void vote_flat(const Geom &g, uint32_t *tile, const f
 // passes when they fit, as vote_pass).  Starts with a block barrier in every
 // case: the previous pass's clearing of this tile is complete.  All threads
 // call it.
+template <bool AGG>
 __device__ __forceinline__ void vote_pass_flat(const Geom &g, const Work &w, uint32_t *tile, float4 *hs,
                                                const float *beta, uint32_t HC, uint64_t es, uint32_t l0, uint32_t l1,
                                                uint64_t &cached_es, FlatMap &cached, uint32_t pr, uint32_t iA,
@@ -1402,7 +1489,7 @@ __device__ __forceinline__ void vote_pass_flat(const Geom &g, const Work &w, uin
 {
     if (cached_es == es) {
         __syncthreads();
-        vote_flat(g, tile, hs, beta, cached, pr, iA, L);
+        vote_flat<AGG>(g, tile, hs, beta, cached, pr, iA, L);
         return;
     }
     cached_es = ~0ull;   // hs is about to be overwritten
@@ -1417,16 +1504,17 @@ __device__ __forceinline__ void vote_pass_flat(const Geom &g, const Work &w, uin
             cached = m;
         }
         first = false;
-        vote_flat(g, tile, hs, beta, m, pr, iA, L);
+        vote_flat<AGG>(g, tile, hs, beta, m, pr, iA, L);
     }
 }
 
-// NT tiles (2 or 3) rotate: after pass p's copy is issued, the copy of pass
-// p - (NT - 1) must have read its tile, which pass p + 1 then takes; with 3
-// tiles two copies stay in flight per CTA.
-template <int NT>
+// NT = 2 tiles rotate: after pass p's copy is issued, the copy of pass p - 1
+// must have read its tile, which pass p + 1 then takes.  AGG: warp-aggregated
+// vote increments (vote_flat).
+template <bool AGG>
 __global__ void __launch_bounds__(1024) k_fill_tma(Geom g, Work w, FillCfg c, ScanArgs a)
 {
+    constexpr int NT = 2;
     extern __shared__ uint4 sm4[];
     // layout: ScanSmem (256 B) | K entries | NT tiles | HC staged hits | B thresholds |
     //         candidate lists (keys, votes, sorted keys, sorted votes)
@@ -1447,16 +1535,20 @@ __global__ void __launch_bounds__(1024) k_fill_tma(Geom g, Work w, FillCfg c, Sc
         beta[k] = g.bth[k];
     if (tid == 0)
         s_hot[0] = s_hot[1] = s_nc = 0u;
-    grid_dep_wait();   // the unit lists of k_scatter
     const uint32_t cta = blockIdx.x;
     ChunkList inner = interior_list(a, cta);
 
+    // The static split reads only the unit offsets, which k_bin wrote: when
+    // k_scatter precedes this kernel it lets it launch only after k_bin has
+    // finished, and any other predecessor lets it launch only at its own
+    // end, so the split runs ahead of the wait for k_scatter's lists.
     __shared__ unsigned long long s_rng[2];
     __shared__ uint32_t s_dyn;
     const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
     const uint64_t n_dyn = c.dyn ? dyn_items(items, gridDim.x) : 0, n_static = items - n_dyn;
     uint64_t it0, it1;
     cta_items(g, w, c, cta, gridDim.x, n_static, it0, it1, s_rng);
+    grid_dep_wait();   // the unit lists of k_scatter
     uint64_t cached_es = ~0ull;
     FlatMap cached{};
     uint32_t buf_n = 0, nseq = 0, total = 0;
@@ -1472,7 +1564,7 @@ __global__ void __launch_bounds__(1024) k_fill_tma(Geom g, Work w, FillCfg c, Sc
         uint32_t *tile = tiles + (size_t)tsel * c.tile_words;
 
         // ---- vote (tile tsel is clear, the lists empty) ------------------------
-        vote_pass_flat(g, w, tile, hs, beta, c.HC, es, l0, l1, cached_es, cached, pr, iA,
+        vote_pass_flat<AGG>(g, w, tile, hs, beta, c.HC, es, l0, l1, cached_es, cached, pr, iA,
                        FlushList{s_hot, cand, candv, &s_nc, kFusedCand});
         fence_proxy_async_smem();   // the tile's counts, visible to the copy engine
         __syncthreads();            // votes and lists complete
@@ -1500,13 +1592,24 @@ __global__ void __launch_bounds__(1024) k_fill_tma(Geom g, Work w, FillCfg c, Sc
             s_hot[0] = s_hot[1] = s_nc = 0u;
         tsel = next;                // the next pass's votes start with a barrier
     };
+    // the first run-time item is claimed during the last static one, each
+    // next one during the item before it (thread 0's claim stays in flight)
+    const bool dyn = c.dyn && n_dyn > 0;
+    uint32_t claim = 0;
+    if (dyn && tid == 0 && it1 <= it0)
+        claim = dyn_claim(w, (uint32_t)n_dyn);
     ItemCursor cur(g, c, it0);
-    for (uint64_t item = it0; item < it1; ++item, cur.next(g, c))
+    for (uint64_t item = it0; item < it1; ++item, cur.next(g, c)) {
+        if (dyn && tid == 0 && item + 1 == it1)
+            claim = dyn_claim(w, (uint32_t)n_dyn);
         do_item(cur);
+    }
     finish_candidates<BlockGroup>(w, a, ss, pbuf, buf_n, nseq, total, inner, cta);
-    if (c.dyn) {
+    if (dyn) {
         // handed-out items, each with its own list of chunks
-        for (uint32_t d; (d = next_dyn_item(w, (uint32_t)n_dyn, &s_dyn)) < n_dyn;) {
+        for (uint32_t d; (d = dyn_take(w, (uint32_t)n_dyn, claim, &s_dyn)) < n_dyn;) {
+            if (tid == 0)
+                claim = dyn_claim(w, (uint32_t)n_dyn);
             const uint32_t list = gridDim.x + d;
             inner = interior_list(a, list);
             buf_n = nseq = total = 0;
@@ -2301,7 +2404,7 @@ cudaError_t launch_fill_peaks(const Geom &g, const Work &w, const FillCfg &c, co
 
 size_t fill_tma_smem_bytes(const FillCfg &c, const ScanArgs &a)
 {
-    return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)c.tiles * c.tile_words * 4 +
+    return 16 * sizeof(uint4) + (size_t)a.K * sizeof(uint4) + (size_t)2 * c.tile_words * 4 +
            (size_t)c.HC * 16 + (size_t)c.beta_words * 4 + (size_t)4 * kFusedCand * 4;
 }
 
@@ -2309,18 +2412,18 @@ cudaError_t launch_fill_tma(const Geom &g, const Work &w, const FillCfg &c, cons
                             cudaStream_t st)
 {
     const size_t smem = fill_tma_smem_bytes(c, a);
-    const void *k = c.tiles == 3 ? (const void *)k_fill_tma<3> : (const void *)k_fill_tma<2>;
+    const void *k = c.vote_agg ? (const void *)k_fill_tma<true> : (const void *)k_fill_tma<false>;
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess)
         return e;
-    return c.tiles == 3 ? launch_pdl(k_fill_tma<3>, grid, c.threads, smem, st, g, w, c, a)
-                        : launch_pdl(k_fill_tma<2>, grid, c.threads, smem, st, g, w, c, a);
+    return c.vote_agg ? launch_pdl(k_fill_tma<true>, grid, c.threads, smem, st, g, w, c, a)
+                      : launch_pdl(k_fill_tma<false>, grid, c.threads, smem, st, g, w, c, a);
 }
 
 cudaError_t fill_tma_occupancy(const FillCfg &c, const ScanArgs &a, int *blocks_per_sm)
 {
     const size_t smem = fill_tma_smem_bytes(c, a);
-    const void *k = c.tiles == 3 ? (const void *)k_fill_tma<3> : (const void *)k_fill_tma<2>;
+    const void *k = c.vote_agg ? (const void *)k_fill_tma<true> : (const void *)k_fill_tma<false>;
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess)
         return e;
@@ -2357,10 +2460,12 @@ cudaError_t launch_clear(uint32_t *M, uint64_t words, uint32_t grid, cudaStream_
     return launch_pdl(k_clear, grid, 512, 0, st, M, words);
 }
 
-cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st)
+cudaError_t launch_fill_naive(const Geom &g, const Work &w, uint32_t num_sms, cudaStream_t st)
 {
+    // a block over A; as many blocks as are resident at once (2048 threads per SM)
     const uint32_t threads = g.na >= 1024 ? 1024 : ((g.na + 31) / 32) * 32;
-    return launch_pdl(k_fill_naive, grid, threads, 0, st, g, w);
+    const size_t smem = ((size_t)g.nb + 1) * 4 <= 48u * 1024u ? ((size_t)g.nb + 1) * 4 : 0;
+    return launch_pdl(k_fill_naive, num_sms * (2048 / threads), threads, smem, st, g, w);
 }
 
 size_t scan_smem_bytes(const ScanArgs &a)

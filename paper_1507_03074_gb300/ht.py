@@ -41,7 +41,8 @@ class c_ranges(ctypes.Structure):
 
 
 TUNING_FIELDS = ("fill_rows", "fill_threads", "fill_hits_staged", "fill_blocks_per_sm",
-                 "scan_kind", "scan_stage_bytes", "scan_slots", "scan_blocks_per_sm", "fill_fused_scan")
+                 "scan_kind", "scan_stage_bytes", "scan_slots", "scan_blocks_per_sm", "fill_fused_scan",
+                 "fill_vote_agg")
 HT_SCAN_AUTO, HT_SCAN_BULK, HT_SCAN_STREAM, HT_SCAN_DIRECT = 0, 1, 2, 3
 
 

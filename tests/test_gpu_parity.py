@@ -137,7 +137,8 @@ U32_TUNINGS = [None, dict(fill_fused_scan=2), dict(fill_fused_scan=1, fill_rows=
                dict(fill_fused_scan=1, fill_rows=4, fill_threads=256), dict(fill_fused_scan=3, fill_rows=2),
                dict(fill_fused_scan=3, fill_rows=8), dict(fill_fused_scan=4), dict(fill_fused_scan=4, fill_rows=4),
                dict(fill_fused_scan=5), dict(fill_fused_scan=5, fill_rows=2, fill_threads=256),
-               dict(fill_fused_scan=5, fill_rows=64, fill_threads=1024)]
+               dict(fill_fused_scan=5, fill_rows=64, fill_threads=1024), dict(fill_fused_scan=5, fill_vote_agg=1),
+               dict(fill_fused_scan=5, fill_vote_agg=1, fill_rows=2, fill_threads=256)]
 
 
 @pytest.mark.parametrize("tuning", U32_TUNINGS, ids=[str(t) for t in U32_TUNINGS])
@@ -434,6 +435,7 @@ TUNINGS = [
     dict(fill_fused_scan=5), dict(fill_fused_scan=5, fill_rows=16, fill_threads=1024),
     dict(fill_fused_scan=5, fill_rows=4, fill_threads=256), dict(fill_fused_scan=5, fill_hits_staged=64),
     dict(fill_fused_scan=5, fill_rows=2, fill_blocks_per_sm=1), dict(fill_fused_scan=5, fill_rows=8, fill_threads=1024),
+    dict(fill_vote_agg=1), dict(fill_fused_scan=5, fill_vote_agg=1, fill_rows=4, fill_threads=256),
     dict(fill_blocks_per_sm=1),
 ]
 
@@ -456,7 +458,7 @@ def test_tuning_sweep(ht, paper_ref, tuning):
         ctx.set_tuning(**tuning)
         got = ctx.get_tuning()
         for k, v in tuning.items():
-            if k in ("scan_kind", "fill_rows", "fill_threads", "scan_slots", "fill_fused_scan"):
+            if k in ("scan_kind", "fill_rows", "fill_threads", "scan_slots", "fill_fused_scan", "fill_vote_agg"):
                 assert got[k] == v, (k, got)
         ctx.fill(ev.x, ev.y, ev.z)
         pk, n = ctx.find_maxima(capacity=1 << 16)
@@ -467,7 +469,7 @@ def test_tuning_sweep(ht, paper_ref, tuning):
 
 def test_bad_tuning_rejected(ht):
     with ht.Context(ht.Binning(*synth.TINY_BINNING), ht.Ranges(), threshold=8, max_hits=256) as ctx:
-        for bad in (dict(fill_threads=300), dict(fill_rows=12), dict(scan_kind=9)):
+        for bad in (dict(fill_threads=300), dict(fill_rows=12), dict(scan_kind=9), dict(fill_vote_agg=2)):
             with pytest.raises(ht.HTError):
                 ctx.set_tuning(**bad)
         ev = synth.tiny_event()
@@ -485,7 +487,7 @@ FUSED_TUNINGS = [dict(fill_fused_scan=2), dict(fill_fused_scan=1), dict(fill_fus
                  dict(fill_fused_scan=3, fill_rows=4), dict(fill_fused_scan=3, fill_rows=64),
                  dict(fill_fused_scan=4), dict(fill_fused_scan=4, fill_rows=4),
                  dict(fill_fused_scan=5), dict(fill_fused_scan=5, fill_rows=4), dict(fill_fused_scan=5, fill_rows=16),
-                 dict(fill_fused_scan=5, fill_rows=2, fill_threads=256)]
+                 dict(fill_fused_scan=5, fill_rows=2, fill_threads=256), dict(fill_fused_scan=5, fill_vote_agg=1)]
 
 
 def _track(A, B, theta, branch):
