@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--serving-seconds", type=float, default=1.5, help="arrival window per serving rate")
     ap.add_argument("--contexts", type=int, default=8, help="contexts (events in flight) of the timed steps")
+    ap.add_argument("--tuning", default=None,
+                    help="JSON launch shape (ht_tuning fields) for the timed steps, e.g. '{\"fill_vote_agg\": 1}'; "
+                         "implies --no-autotune")
     ap.add_argument("--peaks-only", action="store_true",
                     help="time the peaks-only fills (HT_PEAKS_ONLY: M_H not written) in the headline steps")
     ap.add_argument("--components-only", action="store_true",
@@ -268,7 +271,9 @@ def run_ours(args, rank, world):
         ctx.close()
         return res
     # pick launch shapes on this workload (outside the timed region)
-    tuning = ctx.get_tuning() if args.no_autotune else ctx.autotune(reps=5)[0]
+    if args.tuning:
+        ctx.set_tuning(**json.loads(args.tuning))
+    tuning = ctx.get_tuning() if args.no_autotune or args.tuning else ctx.autotune(reps=5)[0]
 
     # events in flight: one context (and stream) per event slot, round-robin
     C = max(1, args.contexts)
@@ -514,8 +519,30 @@ def run_components(dev, b, r, max_hits, mean_votes, hbm_peak, steps=200):
             ctx.profile(False)
         return {kn: t / n * 1e3 for kn, (n, t) in p.items() if n}
 
+    def naive_alone(reps=4 * N_POOL):
+        # the naive fill with the L2 holding only clean lines when it starts,
+        # as under ncu's cache flush: an empty fill clears M_H, a 512 MiB read
+        # writes back the dirty lines the clear left, then the event is
+        # accumulated into the zeroed matrix (no clear of its own)
+        flush = torch.empty(128 << 20, dtype=torch.float32, device="cuda")
+        empty = torch.empty(0, dtype=torch.float32, device="cuda")
+        total_ms = 0.0
+        with ht.Context(b, r, threshold=THRESHOLD, max_hits=max_hits) as ctx:
+            for k in range(reps + 2):
+                ctx.fill(empty, empty, empty, naive=True, stream=st)
+                with torch.cuda.stream(st):
+                    flush.sum()
+                ctx.profile(True)
+                ctx.fill(*dev[k % N_POOL], naive=True, accumulate=True, stream=st)
+                n, t = ctx.profile_read()["k_fill_naive"]
+                ctx.profile(False)
+                if k >= 2:
+                    total_ms += t / n
+        return total_ms / reps * 1e3
+
     two = profile({"fill_fused_scan": 2}, False)
     naive = profile({"fill_fused_scan": 2}, True)
+    alone_us = naive_alone()
     l2_res = ht.measure_atomics(32 << 20)
     l2_hbm = ht.measure_atomics(256 << 20)
     fill_us, scan_us = two.get("k_fill_priv"), two.get("k_scan")
@@ -528,7 +555,10 @@ def run_components(dev, b, r, max_hits, mean_votes, hbm_peak, steps=200):
         "fill_naive": {"avg_us": round(nv_us, 2), "clear_us": round(naive.get("k_clear", 0.0), 2),
                        "gvotes_per_s": round(mean_votes / nv_us / 1e3, 3),
                        "frac_of_l2_atomics_32mib": round(mean_votes / nv_us * 1e6 / l2_res, 4),
-                       "frac_of_l2_atomics_256mib": round(mean_votes / nv_us * 1e6 / l2_hbm, 4)},
+                       "frac_of_l2_atomics_256mib": round(mean_votes / nv_us * 1e6 / l2_hbm, 4),
+                       "alone": {"avg_us": round(alone_us, 2), "gvotes_per_s": round(mean_votes / alone_us / 1e3, 3),
+                                 "frac_of_l2_atomics_32mib": round(mean_votes / alone_us * 1e6 / l2_res, 4),
+                                 "l2_before": "clean (a 512 MiB read wrote back the clear's dirty lines)"}},
         "l2_atomics": {"gupdates_per_s_32mib": round(l2_res / 1e9, 2), "gupdates_per_s_256mib": round(l2_hbm / 1e9, 2)},
     }
 
