@@ -327,6 +327,9 @@ ht_status ht_batch_destroy(ht_batch *batch);
  * HT_PEAKS_ONLY: the same peaks without writing the matrices (as ht_fill;
  * the first such run allocates the edge rows and waits for the device;
  * ht_batch_copy_matrix does not show such a run).
+ * HT_FILL_NAIVE: the paper's fill for every event (as ht_fill: clear, then
+ * one global atomic per vote; the same matrices and peaks); not with
+ * HT_PEAKS_ONLY.
  * Errors: HT_E_INVAL, HT_E_CUDA (batch poisoned), HT_E_NOMEM (peak scratch),
  * HT_E_TIMEOUT, HT_E_STATE. */
 ht_status ht_batch_run(ht_batch *batch, const float *x, const float *y, const float *z, const uint32_t *hit_off,

@@ -86,14 +86,14 @@ void runner_destroy(Runner &R)
 }
 
 // The kernels of one run (also what a graph captures).
-static cudaError_t enqueue_compute(Runner &R, uint32_t n_events, bool to_host, bool peaks_only, cudaStream_t st)
+static cudaError_t enqueue_compute(Runner &R, uint32_t n_events, bool to_host, uint32_t fill_flags, cudaStream_t st)
 {
     Engine &E = R.E;
     const uint32_t mh = E.max_hits;
     // offsets clamped to the staging size; n_total = max_hits: nothing the
     // kernels take as arguments depends on the run
     cudaError_t e = engine_fill(E, R.d_xyz, R.d_xyz + mh, R.d_xyz + 2 * (size_t)mh, R.d_off, mh, n_events, mh,
-                                peaks_only ? (uint32_t)HT_PEAKS_ONLY : 0u, st);
+                                fill_flags, st);
     if (e != cudaSuccess)
         return e;
     return engine_scan(E, n_events, to_host ? R.h_out_dev : R.d_out, R.capacity, to_host ? R.h_counts_dev : R.d_counts,
@@ -102,21 +102,21 @@ static cudaError_t enqueue_compute(Runner &R, uint32_t n_events, bool to_host, b
 
 // Replay the graph for (n_events, to_host), or run directly and capture one
 // for the next run with that shape.
-static cudaError_t run_compute(Runner &R, uint32_t n_events, bool to_host, bool peaks_only, cudaStream_t st)
+static cudaError_t run_compute(Runner &R, uint32_t n_events, bool to_host, uint32_t fill_flags, cudaStream_t st)
 {
     if (R.E.prof.on || !R.graphs_ok)
-        return enqueue_compute(R, n_events, to_host, peaks_only, st);
+        return enqueue_compute(R, n_events, to_host, fill_flags, st);
     for (auto &g : R.graphs)
-        if (g.n_events == n_events && g.to_host == to_host && g.peaks_only == peaks_only)
+        if (g.n_events == n_events && g.to_host == to_host && g.fill_flags == fill_flags)
             return cudaGraphLaunch(g.exec, st);
-    cudaError_t e = enqueue_compute(R, n_events, to_host, peaks_only, st);
+    cudaError_t e = enqueue_compute(R, n_events, to_host, fill_flags, st);
     if (e != cudaSuccess)
         return e;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        const cudaError_t ec = enqueue_compute(R, n_events, to_host, peaks_only, st);
+        const cudaError_t ec = enqueue_compute(R, n_events, to_host, fill_flags, st);
         e = cudaStreamEndCapture(st, &graph);
         if (ec != cudaSuccess)
             e = ec;
@@ -135,12 +135,12 @@ static cudaError_t run_compute(Runner &R, uint32_t n_events, bool to_host, bool 
         cudaGraphExecDestroy(R.graphs.front().exec);
         R.graphs.erase(R.graphs.begin());
     }
-    R.graphs.push_back({n_events, to_host, peaks_only, exec});
+    R.graphs.push_back({n_events, to_host, fill_flags, exec});
     return cudaSuccess;
 }
 
 cudaError_t runner_enqueue(Runner &R, uint32_t n_events, uint32_t n_hits, bool host_in, bool to_host,
-                           cudaStream_t st, bool peaks_only)
+                           cudaStream_t st, uint32_t fill_flags)
 {
     Engine &E = R.E;
     const size_t mh = E.max_hits, bytes = (size_t)n_hits * 4;
@@ -156,7 +156,7 @@ cudaError_t runner_enqueue(Runner &R, uint32_t n_events, uint32_t n_hits, bool h
             cudaSuccess)
             return e;
     }
-    if ((e = run_compute(R, n_events, to_host, peaks_only, st)) != cudaSuccess)
+    if ((e = run_compute(R, n_events, to_host, fill_flags, st)) != cudaSuccess)
         return e;
     E.last_hit_off = R.d_off;         // what a later autotune re-times (also after a replay)
     E.last_n_hits0 = (uint32_t)mh;
@@ -287,9 +287,12 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
         return s;
     hte::Runner &R = b->R;
     hte::Engine &E = R.E;
-    if (flags & ~(uint32_t)(HT_MEM_DEVICE | HT_PEAKS_ONLY))
-        return hte::report(HT_E_INVAL, "unknown flag (batches take HT_MEM_DEVICE and HT_PEAKS_ONLY)");
+    if (flags & ~(uint32_t)(HT_MEM_DEVICE | HT_PEAKS_ONLY | HT_FILL_NAIVE))
+        return hte::report(HT_E_INVAL, "unknown flag (batches take HT_MEM_DEVICE, HT_PEAKS_ONLY and HT_FILL_NAIVE)");
+    if ((flags & HT_PEAKS_ONLY) && (flags & HT_FILL_NAIVE))
+        return hte::report(HT_E_INVAL, "HT_PEAKS_ONLY does not combine with HT_FILL_NAIVE");
     const bool po = (flags & HT_PEAKS_ONLY) != 0;
+    const uint32_t fill_flags = flags & (uint32_t)(HT_PEAKS_ONLY | HT_FILL_NAIVE);
     if (po) {
         std::string why;
         s = hte::engine_ensure_edges(E, &why);
@@ -326,7 +329,7 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
             BK(cudaMemcpyAsync(R.d_xyz + 2 * mh, z, bytes, cudaMemcpyDeviceToDevice, st));
         }
         BK(cudaMemcpyAsync(R.d_off, hit_off, off_bytes, cudaMemcpyDeviceToDevice, st));
-        BK(hte::runner_enqueue(R, n_events, n_hits, false, false, st, po));
+        BK(hte::runner_enqueue(R, n_events, n_hits, false, false, st, fill_flags));
         BK(cudaMemcpyAsync(counts, R.d_counts, (size_t)n_events * 4, cudaMemcpyDeviceToDevice, st));
         BK(cudaMemcpyAsync(out, R.d_out, (size_t)R.capacity * sizeof(htk::Peak), cudaMemcpyDeviceToDevice, st));
         BK(cudaEventRecord(b->done, st));
@@ -342,7 +345,7 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
     std::memcpy(R.h_xyz + mh, y, bytes);
     std::memcpy(R.h_xyz + 2 * mh, z, bytes);
     std::memcpy(R.h_off, hit_off, off_bytes);
-    BK(hte::runner_enqueue(R, n_events, n_hits, true, true, st, po));
+    BK(hte::runner_enqueue(R, n_events, n_hits, true, true, st, fill_flags));
     BK(cudaStreamSynchronize(st));
     if ((s = status_of(b, R.h_counts[E.max_events], st)) != HT_OK)
         return s;

@@ -32,7 +32,7 @@ struct Runner {
     struct Graph {
         uint32_t n_events;
         bool to_host;
-        bool peaks_only;
+        uint32_t fill_flags;         // HT_PEAKS_ONLY, HT_FILL_NAIVE or 0
         cudaGraphExec_t exec;
     };
     std::vector<Graph> graphs;
@@ -47,11 +47,12 @@ void runner_drop_graphs(Runner &R);
 // Enqueue one run of n_events events on st.  The hits are in the pinned
 // staging (host_in) or in the device staging already; the offsets likewise.
 // to_host: peaks and counts into the mapped pinned outputs, plus the status
-// word into h_counts[max_events]; else into d_out / d_counts.  peaks_only:
-// the fill keeps its tiles in shared memory (M_H is not written; the edge
-// rows must have been allocated, engine_ensure_edges).
+// word into h_counts[max_events]; else into d_out / d_counts.  fill_flags:
+// HT_PEAKS_ONLY (the fill keeps its tiles in shared memory, M_H is not
+// written; the edge rows must have been allocated, engine_ensure_edges),
+// HT_FILL_NAIVE (the paper's fill: clear, one global atomic per vote) or 0.
 cudaError_t runner_enqueue(Runner &R, uint32_t n_events, uint32_t n_hits, bool host_in, bool to_host,
-                           cudaStream_t st, bool peaks_only = false);
+                           cudaStream_t st, uint32_t fill_flags = 0);
 
 // After a failed status word: zero the counters (stream-ordered) and map the
 // status bits to an ABI code and message.

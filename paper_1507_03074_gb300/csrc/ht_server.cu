@@ -303,7 +303,7 @@ bool dispatch(ht_server *s, Lane &l, std::vector<Request *> &&reqs)
     l.reqs = std::move(reqs);
     l.busy = true;
     cudaError_t e = hte::runner_enqueue(R, (uint32_t)l.reqs.size(), off, true, true, l.st,
-                                        (s->cfg.flags & HT_PEAKS_ONLY) != 0);
+                                        s->cfg.flags & (uint32_t)HT_PEAKS_ONLY);
     if (e == cudaSuccess)
         e = cudaEventRecord(l.done_ev, l.st);
     return e == cudaSuccess;

@@ -605,14 +605,14 @@ class Batch:
                                     dtype=np.float32) for k in range(3)]
         return cat[0], cat[1], cat[2], off
 
-    def run(self, x, y, z, hit_off, peaks_only: bool = False):
+    def run(self, x, y, z, hit_off, peaks_only: bool = False, naive: bool = False):
         """Host mode: returns (peaks of all events ordered by (event, linear
         index), counts per event); the peaks stop at capacity.  peaks_only:
-        HT_PEAKS_ONLY (the matrices are not written)."""
-        pk, counts, status = self.run_raw(x, y, z, hit_off, peaks_only)
+        HT_PEAKS_ONLY (the matrices are not written); naive: HT_FILL_NAIVE."""
+        pk, counts, status = self.run_raw(x, y, z, hit_off, peaks_only, naive)
         return pk, counts
 
-    def run_raw(self, x, y, z, hit_off, peaks_only: bool = False):
+    def run_raw(self, x, y, z, hit_off, peaks_only: bool = False, naive: bool = False):
         """Host mode: (peaks, counts, status) with HT_TRUNCATED allowed."""
         off = np.ascontiguousarray(hit_off, dtype=np.uint32)
         n_events = off.size - 1
@@ -623,12 +623,14 @@ class Batch:
                                      za.ctypes.data_as(ctypes.c_void_p), off.ctypes.data_as(ctypes.c_void_p),
                                      n_events, int(off[-1]), out.ctypes.data_as(ctypes.c_void_p),
                                      counts.ctypes.data_as(ctypes.c_void_p),
-                                     HT_MEM_HOST | (HT_PEAKS_ONLY if peaks_only else 0), None),
+                                     HT_MEM_HOST | (HT_PEAKS_ONLY if peaks_only else 0) |
+                                     (HT_FILL_NAIVE if naive else 0), None),
                   ok=(HT_OK, HT_TRUNCATED))
         total = int(counts[:n_events].sum())
         return out[: min(total, self.capacity)].copy(), counts[:n_events].copy(), s
 
-    def run_device(self, x, y, z, hit_off, n_hits: int, out, counts, stream=None, peaks_only: bool = False):
+    def run_device(self, x, y, z, hit_off, n_hits: int, out, counts, stream=None, peaks_only: bool = False,
+                   naive: bool = False):
         """Device mode: CUDA tensors (x, y, z float32; hit_off, counts int32;
         out >= capacity * 32 bytes); only enqueues."""
         n_events = hit_off.numel() - 1
@@ -636,7 +638,8 @@ class Batch:
             raise ValueError("out is smaller than capacity * 32 bytes")
         p = [ctypes.c_void_p(t.data_ptr()) for t in (x, y, z, hit_off, out, counts)]
         check(lib().ht_batch_run(self._h, p[0], p[1], p[2], p[3], n_events, n_hits, p[4], p[5],
-                                 HT_MEM_DEVICE | (HT_PEAKS_ONLY if peaks_only else 0), _stream_ptr(stream)))
+                                 HT_MEM_DEVICE | (HT_PEAKS_ONLY if peaks_only else 0) |
+                                 (HT_FILL_NAIVE if naive else 0), _stream_ptr(stream)))
 
     def sync(self, stream=None):
         check(lib().ht_batch_sync(self._h, _stream_ptr(stream)))

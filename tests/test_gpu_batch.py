@@ -119,6 +119,40 @@ def test_batch_peaks_only(ht, uneven):
                       refs)
 
 
+def test_batch_naive_fill(ht, uneven):
+    """HT_FILL_NAIVE runs (the paper's fill, its blocks walking the unit
+    lists of every event of the batch): the oracle's matrices and peaks;
+    naive and fused runs alternate on their own captured graphs, with host
+    and device memory."""
+    import torch
+    evs, refs = uneven
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    x, y, z, off = ht.Batch.concat(evs)
+    with ht.Batch(b, r, threshold=10, max_events=8, max_hits=40000, capacity=1 << 16) as B:
+        for _ in range(3):                                     # direct, capture, replay
+            pk, counts = B.run(x, y, z, off, naive=True)
+            _check_events(evs, pk, counts, refs)
+        for e in range(len(evs)):
+            assert np.array_equal(B.matrix(e), refs[e][0]), e
+        rev = evs[::-1]
+        pk, counts = B.run(*ht.Batch.concat(rev))              # fused, then naive again
+        _check_events(rev, pk, counts, refs[::-1])
+        pk, counts = B.run(*ht.Batch.concat(rev), naive=True)
+        _check_events(rev, pk, counts, refs[::-1])
+        assert np.array_equal(B.matrix(1), refs[-2][0])
+        dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
+        doff = torch.from_numpy(off.astype(np.int32)).cuda()
+        out = torch.zeros((1 << 16) * 8, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(len(evs), dtype=torch.int32, device="cuda")
+        B.run_device(dx, dy, dz, doff, int(off[-1]), out, cnt, naive=True)
+        B.sync()
+        total = sum(n for _, _, n in refs)
+        _check_events(evs, out.cpu().numpy().view(ht.PEAK_DTYPE)[:total], cnt.cpu().numpy().astype(np.uint32),
+                      refs)
+        with pytest.raises(ht.HTError):
+            B.run(x, y, z, off, naive=True, peaks_only=True)
+
+
 def test_event_alone_equals_event_in_batch(ht, uneven):
     evs, refs = uneven
     b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
