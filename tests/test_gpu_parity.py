@@ -56,6 +56,31 @@ def random_hits(n, seed, rmax=1100.0):
     return x, y, z
 
 
+def degenerate_hits():
+    """A small event plus the hits the method's arithmetic has to drop or
+    bin on an edge: y = 0 (2y = 0: B is +-inf or NaN), x = 0, the origin
+    (rho = 0), signed zeros, both diagonals and the axes (pseudo-angles on
+    phi edges), z = 0 and z = +-rho (theta edges), NaN and inf
+    coordinates, x^2 + y^2 overflowing, subnormal coordinates."""
+    ev = synth.paper_event(seed=7, n_tracks=100, n_noise=20)
+    nan, inf = np.float32(np.nan), np.float32(np.inf)
+    pts = []
+    for rr in (30.0, 100.0, 527.5, 1000.0):
+        for (a, bb) in ((rr, 0.0), (-rr, 0.0), (0.0, rr), (0.0, -rr), (rr, rr), (-rr, rr), (-rr, -rr), (rr, -rr),
+                        (-0.0, rr), (rr, -0.0), (0.0, -0.0)):
+            rho = float(np.hypot(a, bb))
+            for zz in (0.0, rho, -rho, 0.5 * rr, -2.0 * rr):
+                pts.append((a, bb, zz))
+    pts += [(nan, 10.0, 0.0), (10.0, nan, 0.0), (10.0, 10.0, nan), (inf, 10.0, 0.0), (10.0, -inf, 5.0),
+            (10.0, 10.0, inf), (1e30, 1e30, 0.0), (-1e30, 3.0, 1.0), (1e-40, 1e-40, 0.0), (-1e-40, 7.0, 1e-40)]
+    d = np.array(pts, dtype=np.float32)
+    x = np.concatenate([ev.x, d[:, 0]]).astype(np.float32)
+    y = np.concatenate([ev.y, d[:, 1]]).astype(np.float32)
+    z = np.concatenate([ev.z, d[:, 2]]).astype(np.float32)
+    perm = np.random.default_rng(11).permutation(x.size)
+    return x[perm], y[perm], z[perm]
+
+
 def run_gpu(ht, b, r, T, x, y, z, naive=False, device=True, capacity=1 << 20, max_hits=None, tuning=None):
     import torch
     with ht.Context(b, r, threshold=T, max_hits=max_hits or max(len(x), 1)) as ctx:
@@ -87,6 +112,8 @@ def event_cases():
     yield "wide_b", (2, 2, 40, 2048), {}, 3, (ev.x, ev.y, ev.z)
     # thousands of hits per slice: the fill selects them in several chunks
     yield "dense_slices", (1, 2, 70, 128), {}, 6, random_hits(5000, 4, rmax=900.0)
+    # axes, diagonals, zeros, NaN / inf / overflowing / subnormal coordinates
+    yield "degenerate_hits", (4, 16, 256, 256), {}, 3, degenerate_hits()
 
 
 CASES = list(event_cases())
