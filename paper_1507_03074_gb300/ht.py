@@ -277,12 +277,30 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(int(stream))
 
 
+_NP_DTYPES = {np.float32: np.dtype(np.float32), np.uint32: np.dtype(np.uint32), np.int32: np.dtype(np.int32)}
+_TORCH_DTYPES = None   # numpy dtype -> the tensor dtypes accepted for it (set on first use)
+
+
+def _np_address(arr) -> int:
+    """Address of a C-contiguous numpy array's data (from its buffer when it
+    is writable, the cheap route; else through arr.ctypes)."""
+    try:
+        return ctypes.addressof(ctypes.c_char.from_buffer(arr)) if arr.size else arr.ctypes.data
+    except (TypeError, ValueError):
+        return arr.ctypes.data
+
+
 def _ptr_and_mem(a, dtype):
     """(pointer, HT_MEM_* flag, keepalive) for a numpy array or a torch tensor."""
+    if type(a) is np.ndarray and a.dtype == _NP_DTYPES[dtype] and a.flags.c_contiguous:
+        return ctypes.c_void_p(_np_address(a)), HT_MEM_HOST, a
     if _is_torch(a):
-        import torch
-        want = {np.float32: torch.float32, np.uint32: torch.int32, np.int32: torch.int32}[dtype]
-        if a.dtype != want and not (dtype == np.uint32 and a.dtype in (torch.int32, torch.uint8)):
+        global _TORCH_DTYPES
+        if _TORCH_DTYPES is None:
+            import torch
+            _TORCH_DTYPES = {np.float32: (torch.float32,), np.uint32: (torch.int32, torch.uint8),
+                             np.int32: (torch.int32,)}
+        if a.dtype not in _TORCH_DTYPES[dtype]:
             raise TypeError(f"tensor dtype {a.dtype} does not match {dtype}")
         if not a.is_contiguous():
             raise ValueError("tensor must be contiguous")
