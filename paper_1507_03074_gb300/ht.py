@@ -474,7 +474,7 @@ class Context:
             check(L.ht_find_maxima(self._h, ctypes.c_void_p(out.data_ptr()), capacity,
                                    ctypes.c_void_p(count.data_ptr()), HT_MEM_DEVICE | f4, _stream_ptr(stream)))
             return None
-        buf = np.zeros(max(capacity, 1), PEAK_DTYPE)
+        buf = np.empty(max(capacity, 1), PEAK_DTYPE)   # the call writes the first min(total, capacity)
         n = ctypes.c_uint32()
         check(L.ht_find_maxima(self._h, buf.ctypes.data_as(ctypes.c_void_p), capacity, ctypes.byref(n),
                                HT_MEM_HOST | f4, _stream_ptr(stream)), ok=(HT_OK, HT_TRUNCATED))
@@ -570,7 +570,7 @@ class Sectors:
             check(L.ht_sectors_find_maxima(self._h, ctypes.c_void_p(out.data_ptr()), capacity,
                                            ctypes.c_void_p(count.data_ptr()), HT_MEM_DEVICE, _stream_ptr(stream)))
             return None
-        buf = np.zeros(max(capacity, 1), PEAK_DTYPE)
+        buf = np.empty(max(capacity, 1), PEAK_DTYPE)   # the call writes the first min(total, capacity)
         n = ctypes.c_uint32()
         check(L.ht_sectors_find_maxima(self._h, buf.ctypes.data_as(ctypes.c_void_p), capacity, ctypes.byref(n),
                                        HT_MEM_HOST, _stream_ptr(stream)), ok=(HT_OK, HT_TRUNCATED))
@@ -635,7 +635,7 @@ class Batch:
         off = np.ascontiguousarray(hit_off, dtype=np.uint32)
         n_events = off.size - 1
         xa, ya, za = (np.ascontiguousarray(a, dtype=np.float32) for a in (x, y, z))
-        out = np.zeros(self.capacity, PEAK_DTYPE)
+        out = np.empty(self.capacity, PEAK_DTYPE)   # the call writes the first min(total, capacity)
         counts = np.zeros(max(n_events, 1), np.uint32)
         s = check(lib().ht_batch_run(self._h, xa.ctypes.data_as(ctypes.c_void_p), ya.ctypes.data_as(ctypes.c_void_p),
                                      za.ctypes.data_as(ctypes.c_void_p), off.ctypes.data_as(ctypes.c_void_p),
@@ -740,7 +740,7 @@ class Server:
 
     def poll(self, ticket: int, capacity: int = 1 << 14, timeout_us: int = 0):
         """None while pending, else (status, peaks, total); raises on an error status."""
-        buf = np.zeros(max(capacity, 1), PEAK_DTYPE)
+        buf = np.empty(max(capacity, 1), PEAK_DTYPE)   # the call writes the first min(total, capacity)
         n = ctypes.c_uint32()
         s = check(lib().ht_poll(self._h, ticket, buf.ctypes.data_as(ctypes.c_void_p), capacity, ctypes.byref(n),
                                 timeout_us), ok=(HT_OK, HT_TRUNCATED, HT_PENDING))
