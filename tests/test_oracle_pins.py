@@ -104,6 +104,28 @@ def test_admission_windows_and_drops():
     assert cnt.tolist() == [1, 0]
 
 
+def test_admission_at_the_limits():
+    """Non-finite and extreme coordinates follow the pseudo-angle formulas:
+    z = +inf gives rho / (z + rho) = 0, the polar angle's limit (the hit
+    votes exactly as at any large finite z in theta bin 0); z = -inf gives
+    inf / inf = NaN and drops the hit, as x^2 + y^2 overflowing to inf
+    (rho = inf: NaN pseudo-angles) and subnormal x, y (x^2 + y^2 underflows
+    to 0: rho = 0) do."""
+    b = Binning(4, 16, 64, 64)
+    x = np.float32([300.0, 300.0, 300.0, 1e30, 1e-40, 300.0])
+    y = np.float32([-200.0, -200.0, -200.0, 1e30, 1e-40, -200.0])
+    z = np.float32([np.inf, 1e6, -np.inf, 0.0, 0.0, -1e6])
+    sl, cnt = oracle.admit(b, R, x, y, z)
+    assert cnt.tolist() == [1, 1, 0, 0, 0, 1]
+    assert sl[0, 0] == sl[1, 0] and sl[0, 0] // b.n_phi == 0        # theta bin 0
+    assert sl[5, 0] // b.n_phi == b.n_theta - 1                        # z = -1e6: the last theta bin
+    M_inf, v_inf = oracle.fill(b, R, x[:1], y[:1], z[:1])
+    M_big, v_big = oracle.fill(b, R, x[1:2], y[1:2], z[1:2])
+    assert v_inf == v_big > 0 and np.array_equal(M_inf, M_big)
+    _, v_drop = oracle.fill(b, R, x[2:5], y[2:5], z[2:5])
+    assert v_drop == 0
+
+
 # ---------------------------------------------------------------------------
 # P-c: exact rational brute force of every (hit, A) vote on the tiny config
 # ---------------------------------------------------------------------------
