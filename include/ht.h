@@ -318,9 +318,10 @@ ht_status ht_batch_destroy(ht_batch *batch);
  * Peaks come in one list ordered by (event, linear index), each with its
  * event number: event e's at out + sum of counts[e' < e] as long as the
  * total fits `capacity` (the batch's); counts[e] is event e's total.
- * HT_MEM_HOST: every array is host memory (copied at once; the caller may
- * reuse them on return); blocks; writes min(total, capacity) peaks and
- * returns HT_TRUNCATED when the total exceeds capacity.
+ * HT_MEM_HOST: every array is host memory (the caller may reuse them on
+ * return: hits in page-locked memory are copied to the device directly,
+ * others through the batch's pinned staging); blocks; writes min(total,
+ * capacity) peaks and returns HT_TRUNCATED when the total exceeds capacity.
  * HT_MEM_DEVICE: every array (hit_off included) is device memory; the call
  * only enqueues on `stream` (NULL = the batch's own stream); the caller
  * checks counts for truncation; ht_batch_sync reports device-side failures.

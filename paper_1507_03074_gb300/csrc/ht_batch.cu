@@ -277,6 +277,17 @@ ht_status ht_batch_destroy(ht_batch *b)
     return HT_OK;
 }
 
+// Host memory the GPU can copy from directly (cudaHostAlloc'd or registered).
+static bool page_locked(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float *z, const uint32_t *hit_off,
                        uint32_t n_events, uint32_t n_hits, ht_peak *out, uint32_t *counts, uint32_t flags,
                        void *stream)
@@ -336,16 +347,26 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
         b->done_pending = true;
         return HT_OK;
     }
-    // host inputs through the pinned staging; the order kernel writes the
+    // host inputs through the pinned staging (page-locked inputs straight to
+    // the device: the call returns only once the run is done, so the caller
+    // may reuse them on return either way); the order kernel writes the
     // peaks and counts into mapped pinned memory
     if (b->done_pending)
         BK(cudaEventSynchronize(b->done));
     b->done_pending = false;
-    std::memcpy(R.h_xyz, x, bytes);
-    std::memcpy(R.h_xyz + mh, y, bytes);
-    std::memcpy(R.h_xyz + 2 * mh, z, bytes);
     std::memcpy(R.h_off, hit_off, off_bytes);
-    BK(hte::runner_enqueue(R, n_events, n_hits, true, true, st, fill_flags));
+    if (n_hits && page_locked(x) && page_locked(y) && page_locked(z)) {
+        BK(cudaMemcpyAsync(R.d_xyz, x, bytes, cudaMemcpyHostToDevice, st));
+        BK(cudaMemcpyAsync(R.d_xyz + mh, y, bytes, cudaMemcpyHostToDevice, st));
+        BK(cudaMemcpyAsync(R.d_xyz + 2 * mh, z, bytes, cudaMemcpyHostToDevice, st));
+        BK(cudaMemcpyAsync(R.d_off, R.h_off, off_bytes, cudaMemcpyHostToDevice, st));
+        BK(hte::runner_enqueue(R, n_events, n_hits, false, true, st, fill_flags));
+    } else {
+        std::memcpy(R.h_xyz, x, bytes);
+        std::memcpy(R.h_xyz + mh, y, bytes);
+        std::memcpy(R.h_xyz + 2 * mh, z, bytes);
+        BK(hte::runner_enqueue(R, n_events, n_hits, true, true, st, fill_flags));
+    }
     BK(cudaStreamSynchronize(st));
     if ((s = status_of(b, R.h_counts[E.max_events], st)) != HT_OK)
         return s;

@@ -119,6 +119,35 @@ def test_batch_peaks_only(ht, uneven):
                       refs)
 
 
+def test_batch_page_locked_inputs(ht, uneven):
+    """Hits in page-locked host memory go to the device without the staging
+    copy: the same peaks and matrices, and the arrays may be overwritten as
+    soon as the call returns."""
+    import torch
+    evs, refs = uneven
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    x, y, z, off = ht.Batch.concat(evs)
+    pinned = [torch.empty(v.size, dtype=torch.float32, pin_memory=True) for v in (x, y, z)]
+    for t, v in zip(pinned, (x, y, z)):
+        t.numpy()[:] = v
+    px, py, pz = (t.numpy() for t in pinned)
+    with ht.Batch(b, r, threshold=10, max_events=8, max_hits=40000, capacity=1 << 16) as B:
+        for _ in range(2):
+            pk, counts = B.run(px, py, pz, off)
+            _check_events(evs, pk, counts, refs)
+            for t in pinned:
+                t.numpy()[:] = np.nan            # reused at once: the run has its copy
+            pk2, counts2 = B.run(px, py, pz, off)
+            assert counts2.sum() == 0            # all-NaN hits are dropped
+            for t, v in zip(pinned, (x, y, z)):
+                t.numpy()[:] = v
+        assert np.array_equal(B.matrix(1), np.zeros_like(refs[1][0]))
+        pk, counts = B.run(px, py, pz, off)
+        _check_events(evs, pk, counts, refs)
+        for e in range(len(evs)):
+            assert np.array_equal(B.matrix(e), refs[e][0]), e
+
+
 def test_batch_naive_fill(ht, uneven):
     """HT_FILL_NAIVE runs (the paper's fill, its blocks walking the unit
     lists of every event of the batch): the oracle's matrices and peaks;
