@@ -362,9 +362,11 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
         BK(cudaMemcpyAsync(R.d_off, R.h_off, off_bytes, cudaMemcpyHostToDevice, st));
         BK(hte::runner_enqueue(R, n_events, n_hits, false, true, st, fill_flags));
     } else {
-        std::memcpy(R.h_xyz, x, bytes);
-        std::memcpy(R.h_xyz + mh, y, bytes);
-        std::memcpy(R.h_xyz + 2 * mh, z, bytes);
+        if (n_hits) {
+            std::memcpy(R.h_xyz, x, bytes);
+            std::memcpy(R.h_xyz + mh, y, bytes);
+            std::memcpy(R.h_xyz + 2 * mh, z, bytes);
+        }
         BK(hte::runner_enqueue(R, n_events, n_hits, true, true, st, fill_flags));
     }
     BK(cudaStreamSynchronize(st));
