@@ -29,9 +29,11 @@ struct ht_ctx {
     cudaStream_t stream = nullptr;
     float *d_in = nullptr;        // 3 * max_hits device staging
     float *h_in = nullptr;        // 3 * max_hits pinned staging
-    uint32_t *h_small = nullptr;  // pinned: [0] count, [1] status
-    uint32_t *d_small = nullptr;  // device: [0] count
-    htk::Peak *d_peaks = nullptr;
+    uint32_t *h_small = nullptr;  // mapped pinned: [0] count (written by the order kernel), [1] status
+    uint32_t *h_small_dev = nullptr;  // its device address
+    uint32_t *d_small = nullptr;  // device: [2] the 4-D scan's 2-D count
+    htk::Peak *h_peaks = nullptr;     // mapped pinned peaks of host-mode ht_find_maxima
+    htk::Peak *h_peaks_dev = nullptr; // their device address
     uint32_t peaks_cap = 0;
     cudaEvent_t ev_in = nullptr;
     bool ev_in_pending = false;
@@ -122,7 +124,8 @@ ht_status ht_create(const ht_binning *binning, const ht_ranges *ranges, uint32_t
         (e = cudaMalloc(&ctx->d_in, (size_t)max_hits * 12 + 64)) != cudaSuccess ||
         (e = cudaMalloc(&ctx->d_small, 16)) != cudaSuccess ||
         (e = cudaMallocHost(&ctx->h_in, (size_t)max_hits * 12 + 64)) != cudaSuccess ||
-        (e = cudaMallocHost(&ctx->h_small, 16)) != cudaSuccess) {
+        (e = cudaHostAlloc(&ctx->h_small, 16, cudaHostAllocMapped)) != cudaSuccess ||
+        (e = cudaHostGetDevicePointer((void **)&ctx->h_small_dev, ctx->h_small, 0)) != cudaSuccess) {
         cudaGetLastError();
         ht_destroy(ctx);
         return set_err(HT_E_NOMEM, std::string("allocation failed: ") + cudaGetErrorString(e));
@@ -140,7 +143,7 @@ ht_status ht_destroy(ht_ctx *ctx)
     hte::engine_destroy(ctx->E);
     cudaFree(ctx->d_in);
     cudaFree(ctx->d_small);
-    cudaFree(ctx->d_peaks);
+    cudaFreeHost(ctx->h_peaks);
     cudaFree(ctx->d_p2);
     cudaFree(ctx->d_keep);
     cudaFreeHost(ctx->h_in);
@@ -230,7 +233,7 @@ ht_status ht_find_maxima(ht_ctx *ctx, ht_peak *out, uint32_t capacity, uint32_t 
             ctx->p2_cap = ctx->E.scan.entries_cap;
         }
     }
-    // the 2-D list's total goes to d_small[2] (d_small[0] holds the result's)
+    // the 2-D list's total goes to d_small[2] (h_small[0] receives the result's)
     auto scan = [&](htk::Peak *dst, uint32_t cap, uint32_t *cnt) {
         return four ? hte::engine_scan4d(ctx->E, ctx->d_p2, ctx->d_keep, ctx->p2_cap, ctx->d_small + 2, dst, cap, cnt,
                                          st)
@@ -242,23 +245,23 @@ ht_status ht_find_maxima(ht_ctx *ctx, ht_peak *out, uint32_t capacity, uint32_t 
     }
     if (capacity > ctx->peaks_cap) {
         CK(cudaStreamSynchronize(st));
-        cudaFree(ctx->d_peaks);
-        ctx->d_peaks = nullptr;
+        cudaFreeHost(ctx->h_peaks);
+        ctx->h_peaks = ctx->h_peaks_dev = nullptr;
         ctx->peaks_cap = 0;
-        CK(cudaMalloc(&ctx->d_peaks, (size_t)capacity * sizeof(htk::Peak)));
+        CK(cudaHostAlloc(&ctx->h_peaks, (size_t)capacity * sizeof(htk::Peak), cudaHostAllocMapped));
+        CK(cudaHostGetDevicePointer((void **)&ctx->h_peaks_dev, ctx->h_peaks, 0));
         ctx->peaks_cap = capacity;
     }
-    CK(scan(ctx->d_peaks, capacity, ctx->d_small));
-    CK(cudaMemcpyAsync(ctx->h_small, ctx->d_small, 4, cudaMemcpyDeviceToHost, st));
+    // the order kernel writes the peaks and their count into mapped pinned
+    // memory: one wait, then a host copy
+    CK(scan(ctx->h_peaks_dev, capacity, ctx->h_small_dev));
     s = read_status(ctx, st);   // synchronises the stream
     if (s != HT_OK)
         return s;
     const uint32_t n = ctx->h_small[0];
     const uint32_t k = n < capacity ? n : capacity;
-    if (k) {
-        CK(cudaMemcpyAsync(out, ctx->d_peaks, (size_t)k * sizeof(ht_peak), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-    }
+    if (k)
+        std::memcpy(out, ctx->h_peaks, (size_t)k * sizeof(ht_peak));
     *n_found = n;
     return n > capacity ? HT_TRUNCATED : HT_OK;
 }
