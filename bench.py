@@ -598,6 +598,20 @@ def run_upgrade(hbm_peak, n_events=4, steps=20):
             step(k)
         prof = ctx.profile_read()
         ctx.profile(False)
+        # two events in flight: a second context (another 4 GiB M_H) on its own
+        # stream, the events alternating between them
+        with ht.Context(b, r, threshold=THRESHOLD, max_hits=max(e.n_hits for e in evs)) as ctx2:
+            ctx2.set_tuning(**ctx.get_tuning())
+            ctxs, sts = (ctx, ctx2), (st, torch.cuda.Stream())
+            outs = (out, torch.empty_like(out))
+            cnts = (cnt, torch.empty_like(cnt))
+
+            def step2(k):
+                c = k % 2
+                ctxs[c].fill(*dev[k % n_events], stream=sts[c])
+                ctxs[c].find_maxima(capacity=65536, out=outs[c], count=cnts[c], stream=sts[c])
+
+            ms2 = timed_in_flight(sts, step2, steps, 4)
     kern = {kn: t / n * 1e3 for kn, (n, t) in prof.items() if n}
     fill_us = kern.get("k_fill_tma", kern.get("k_fill_scan"))
     cells_bytes = b.n_cells * 4
@@ -605,7 +619,10 @@ def run_upgrade(hbm_peak, n_events=4, steps=20):
             "events_per_s": round(1e3 / ms, 2), "ms_per_event": round(ms, 4),
             "kernels_us": {kn: round(v, 1) for kn, v in kern.items()},
             "fill_gbs": round(cells_bytes / fill_us / 1e3, 1) if fill_us else None,
-            "fill_frac_of_hbm": round(cells_bytes / fill_us / 1e3 / hbm_peak, 4) if fill_us else None}
+            "fill_frac_of_hbm": round(cells_bytes / fill_us / 1e3 / hbm_peak, 4) if fill_us else None,
+            "in_flight": {"contexts": 2, "events_per_s": round(1e3 / ms2, 2), "ms_per_event": round(ms2, 4),
+                          "m_h_gbs": round(cells_bytes / ms2 / 1e6, 1),
+                          "frac_of_hbm": round(cells_bytes / ms2 / 1e6 / hbm_peak, 4)}}
 
 
 # ---------------------------------------------------------------------------
