@@ -540,9 +540,28 @@ def run_components(dev, b, r, max_hits, mean_votes, hbm_peak, steps=200):
                     total_ms += t / n
         return total_ms / reps * 1e3
 
+    def scan_alone(reps=4 * N_POOL):
+        # the standalone scan with the L2 holding only clean lines when it
+        # starts: a 512 MiB read between the fill and the scan writes back the
+        # rows of M_H the fill left dirty (as ncu's cache flush does)
+        flush = torch.empty(128 << 20, dtype=torch.float32, device="cuda")
+        with ht.Context(b, r, threshold=THRESHOLD, max_hits=max_hits) as ctx:
+            ctx.set_tuning(fill_fused_scan=2)
+            ctx.profile(True)
+            for k in range(reps + 2):
+                ctx.fill(*dev[k % N_POOL], stream=st)
+                with torch.cuda.stream(st):
+                    flush.sum()
+                ctx.find_maxima(capacity=65536, out=out, count=cnt, stream=st)
+            p = ctx.profile_read()
+            ctx.profile(False)
+        n, t = p["k_scan"]
+        return t / n * 1e3
+
     two = profile({"fill_fused_scan": 2}, False)
     naive = profile({"fill_fused_scan": 2}, True)
     alone_us = naive_alone()
+    scan_alone_us = scan_alone()
     l2_res = ht.measure_atomics(32 << 20)
     l2_hbm = ht.measure_atomics(256 << 20)
     fill_us, scan_us = two.get("k_fill_priv"), two.get("k_scan")
@@ -551,7 +570,11 @@ def run_components(dev, b, r, max_hits, mean_votes, hbm_peak, steps=200):
         "fill_priv": {"avg_us": round(fill_us, 2), "gbs_written": round(cells_bytes / fill_us / 1e3, 1),
                       "frac_of_hbm": round(cells_bytes / fill_us / 1e3 / hbm_peak, 4)},
         "scan_stream": {"avg_us": round(scan_us, 2), "gbs_read": round(cells_bytes / scan_us / 1e3, 1),
-                        "frac_of_hbm": round(cells_bytes / scan_us / 1e3 / hbm_peak, 4)},
+                        "frac_of_hbm": round(cells_bytes / scan_us / 1e3 / hbm_peak, 4),
+                        "alone": {"avg_us": round(scan_alone_us, 2),
+                                  "gbs_read": round(cells_bytes / scan_alone_us / 1e3, 1),
+                                  "frac_of_hbm": round(cells_bytes / scan_alone_us / 1e3 / hbm_peak, 4),
+                                  "l2_before": "clean (a 512 MiB read wrote back the fill's dirty lines)"}},
         "fill_naive": {"avg_us": round(nv_us, 2), "clear_us": round(naive.get("k_clear", 0.0), 2),
                        "gvotes_per_s": round(mean_votes / nv_us / 1e3, 3),
                        "frac_of_l2_atomics_32mib": round(mean_votes / nv_us * 1e6 / l2_res, 4),
