@@ -95,3 +95,31 @@ def test_b_thresholds_equal_division(nb, rng):
     inr = (B >= beta[0]) & (B < beta[nb])
     got = np.where(inr, np.searchsorted(beta, B, side="right") - 1, -1)
     assert np.array_equal(np.where(want >= 0, want, -1), got)
+
+
+def test_binding_pointer_marshalling():
+    """The binding hands the C ABI the address of the caller's own data when
+    it already is a C-contiguous array of the right dtype (writable or not,
+    empty included), and a converted copy otherwise; tensors are checked for
+    dtype and contiguity."""
+    import torch
+    from paper_1507_03074_gb300 import ht
+    x = np.arange(7, dtype=np.float32)
+    ro = x.copy()
+    ro.setflags(write=False)
+    for a in (x, ro, np.zeros(0, np.float32)):
+        p, mem, keep = ht._ptr_and_mem(a, np.float32)
+        assert keep is a and mem == ht.HT_MEM_HOST
+        assert p.value == (a.ctypes.data or None)
+    for a in (x.astype(np.float64), x[::2], list(range(4))):
+        p, mem, keep = ht._ptr_and_mem(a, np.float32)
+        assert keep.dtype == np.float32 and keep.flags.c_contiguous and p.value == keep.ctypes.data
+        assert np.array_equal(keep, np.asarray(a, dtype=np.float32))
+    t = torch.arange(5, dtype=torch.float32)
+    p, mem, keep = ht._ptr_and_mem(t, np.float32)
+    assert p.value == t.data_ptr() and mem == ht.HT_MEM_HOST and keep is t
+    assert ht._ptr_and_mem(torch.zeros(3, dtype=torch.uint8), np.uint32)[1] == ht.HT_MEM_HOST
+    with pytest.raises(TypeError):
+        ht._ptr_and_mem(torch.zeros(3, dtype=torch.int64), np.float32)
+    with pytest.raises(ValueError):
+        ht._ptr_and_mem(torch.zeros(4, 4)[:, 0], np.float32)
