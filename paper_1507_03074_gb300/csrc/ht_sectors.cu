@@ -39,9 +39,11 @@ struct ht_sectors {
     htk::Peak *d_sec = nullptr;       // S lists of sec_cap peaks
     uint32_t sec_cap = 0;
     uint32_t *d_cnt = nullptr;        // S counts + merged total
-    htk::Peak *d_out = nullptr;       // merged (host-memory calls)
+    htk::Peak *h_out = nullptr;       // mapped pinned: merged peaks of host-memory calls
+    htk::Peak *h_out_dev = nullptr;   // its device address
     uint32_t out_cap = 0;
-    uint32_t *h_small = nullptr;      // pinned: merged total
+    uint32_t *h_small = nullptr;      // mapped pinned: merged total of host-memory calls
+    uint32_t *h_small_dev = nullptr;  // its device address
     bool poisoned = false;
 };
 
@@ -173,7 +175,7 @@ ht_status ht_sectors_destroy(ht_sectors *sec)
     cudaFree(sec->d_in);
     cudaFree(sec->d_sec);
     cudaFree(sec->d_cnt);
-    cudaFree(sec->d_out);
+    cudaFreeHost(sec->h_out);
     cudaFreeHost(sec->h_in);
     cudaFreeHost(sec->h_small);
     delete sec;
@@ -245,7 +247,8 @@ ht_status ht_sectors_create(const ht_binning *binning, const ht_ranges *ranges, 
         (e = cudaMalloc(&sec->d_in, (size_t)max_hits * 12 + 64)) != cudaSuccess ||
         (e = cudaMalloc(&sec->d_cnt, (size_t)(n_sectors + 1) * 4)) != cudaSuccess ||
         (e = cudaMallocHost(&sec->h_in, (size_t)max_hits * 12 + 64)) != cudaSuccess ||
-        (e = cudaMallocHost(&sec->h_small, 16)) != cudaSuccess) {
+        (e = cudaHostAlloc(&sec->h_small, 16, cudaHostAllocMapped)) != cudaSuccess ||
+        (e = cudaHostGetDevicePointer((void **)&sec->h_small_dev, sec->h_small, 0)) != cudaSuccess) {
         cudaGetLastError();
         ht_sectors_destroy(sec);
         return hte::report(HT_E_NOMEM, std::string("allocation failed: ") + cudaGetErrorString(e));
@@ -322,10 +325,11 @@ ht_status ht_sectors_find_maxima(ht_sectors *sec, ht_peak *out, uint32_t capacit
     }
     if (!dev && cap > sec->out_cap) {
         SCK(cudaStreamSynchronize(st));
-        cudaFree(sec->d_out);
-        sec->d_out = nullptr;
+        cudaFreeHost(sec->h_out);
+        sec->h_out = sec->h_out_dev = nullptr;
         sec->out_cap = 0;
-        SCK(cudaMalloc(&sec->d_out, (size_t)cap * sizeof(htk::Peak)));
+        SCK(cudaHostAlloc(&sec->h_out, (size_t)cap * sizeof(htk::Peak), cudaHostAllocMapped));
+        SCK(cudaHostGetDevicePointer((void **)&sec->h_out_dev, sec->h_out, 0));
         sec->out_cap = cap;
     }
     s = fork_from(sec, st);
@@ -344,8 +348,9 @@ ht_status ht_sectors_find_maxima(ht_sectors *sec, ht_peak *out, uint32_t capacit
     s = join_into(sec, st);
     if (s != HT_OK)
         return s;
-    htk::Peak *dst = dev ? reinterpret_cast<htk::Peak *>(out) : sec->d_out;
-    uint32_t *cnt = dev ? n_found : sec->d_cnt + sec->S;
+    // host-memory calls: the merge writes peaks and total into mapped pinned memory
+    htk::Peak *dst = dev ? reinterpret_cast<htk::Peak *>(out) : sec->h_out_dev;
+    uint32_t *cnt = dev ? n_found : sec->h_small_dev;
     int nsm = 0, dv = 0;
     SCK(cudaGetDevice(&dv));
     SCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dv));
@@ -353,7 +358,6 @@ ht_status ht_sectors_find_maxima(ht_sectors *sec, ht_peak *out, uint32_t capacit
     SCK(cudaGetLastError());
     if (dev)
         return HT_OK;
-    SCK(cudaMemcpyAsync(sec->h_small, cnt, 4, cudaMemcpyDeviceToHost, st));
     SCK(cudaStreamSynchronize(st));
     for (uint32_t k = 0; k < sec->S; ++k) {
         s = ht_sync(sec->ctx[k], sec->st[k]);   // device-side failures of the sector's kernels
@@ -362,10 +366,8 @@ ht_status ht_sectors_find_maxima(ht_sectors *sec, ht_peak *out, uint32_t capacit
     }
     const uint32_t n = sec->h_small[0];
     const uint32_t kk = n < capacity ? n : capacity;
-    if (kk) {
-        SCK(cudaMemcpyAsync(out, sec->d_out, (size_t)kk * sizeof(ht_peak), cudaMemcpyDeviceToHost, st));
-        SCK(cudaStreamSynchronize(st));
-    }
+    if (kk)
+        std::memcpy(out, sec->h_out, (size_t)kk * sizeof(ht_peak));
     *n_found = n;
     return n > capacity ? HT_TRUNCATED : HT_OK;
 }
