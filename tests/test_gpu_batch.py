@@ -249,6 +249,28 @@ def test_batch_ragged_binning_and_autotune(ht):
             assert np.array_equal(B.matrix(e), refs[e][0])
 
 
+def test_batch_windows_every_fill(ht):
+    """Admission windows (a hit votes in up to 3 x 3 slices) on a batch of
+    uneven events, one of them empty: the fused fill, the paper's fill and the
+    peaks-only fill all give the oracle's peaks, and the two that write M_H
+    its matrices."""
+    b = ht.Binning(4, 16, 128, 128, 1, 1)
+    r = ht.Ranges()
+    evs = []
+    for k, (nt, nn) in enumerate(((60, 10), (0, 0), (140, 30), (25, 5))):
+        e = synth.paper_event(seed=300 + k, n_tracks=nt, n_noise=nn) if nt else None
+        evs.append((e.x, e.y, e.z) if e is not None else tuple(np.zeros(0, np.float32) for _ in range(3)))
+    refs = [_oracle_event(b, r, 5, ev) for ev in evs]
+    x, y, z, off = ht.Batch.concat(evs)
+    with ht.Batch(b, r, threshold=5, max_events=4, max_hits=8000, capacity=1 << 16) as B:
+        for kw in (dict(), dict(naive=True), dict(peaks_only=True), dict()):
+            pk, counts = B.run(x, y, z, off, **kw)
+            _check_events(evs, pk, counts, refs)
+            if not kw.get("peaks_only"):
+                for e in range(len(evs)):
+                    assert np.array_equal(B.matrix(e), refs[e][0]), (kw, e)
+
+
 def test_batch_rejects_bad_arguments(ht):
     b, r = ht.Binning(*synth.TINY_BINNING), ht.Ranges()
     ev = synth.tiny_event()
