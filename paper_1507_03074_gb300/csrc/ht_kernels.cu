@@ -2196,34 +2196,40 @@ __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, Order
     __shared__ uint32_t s_last;
     const uint32_t tid = threadIdx.x, bd = blockDim.x, c = blockIdx.x;
     // this CTA's chunk counts and first descriptor, loaded ahead of the prefix
-    const uint32_t nseq = a.cta_nseq[c];
+    const uint32_t nseq = a.cta_nseq[c], mine = a.cta_total[c];
     const uint2 d0 = nseq ? a.desc[(size_t)c * a.seq_max] : make_uint2(0u, 0u);
+    // one event or one list over all events: the rank within the event is the
+    // global rank (no per-event bases)
+    const bool global_rank = o.compact || w.n_events == 1;
 
-    // rank of this CTA's first entry
+    // rank of this CTA's first entry (a list without peaks writes nothing)
     uint32_t part = 0;
-    for (uint32_t q = tid; q < c; q += bd)
-        part += a.cta_total[q];
+    if (mine)
+        for (uint32_t q = tid; q < c; q += bd)
+            part += a.cta_total[q];
     part = warp_incl_scan(part);
     if ((tid & 31u) == 31u)
         red[tid >> 5] = part;
-    for (uint32_t e = tid; e < w.n_events; e += bd)
-        ev_base[e] = o.ev_count[e];
+    if (mine && !global_rank)
+        for (uint32_t e = tid; e < w.n_events; e += bd)
+            ev_base[e] = o.ev_count[e];
     __syncthreads();
     uint32_t prefix = 0;
     for (uint32_t q = 0; q < (bd + 31) / 32; ++q)
         prefix += red[q];
     __syncthreads();
-    block_exclusive_scan(ev_base, w.n_events, red);
+    if (mine && !global_rank)
+        block_exclusive_scan(ev_base, w.n_events, red);
 
     uint32_t P = prefix;
-    for (uint32_t q = 0; q < nseq; ++q) {
+    for (uint32_t q = 0; q < (mine ? nseq : 0u); ++q) {
         const uint2 d = q == 0 ? d0 : a.desc[(size_t)c * a.seq_max + q];
         for (uint32_t k = tid; k < d.y; k += bd) {
             if (d.x + k >= a.entries_cap)
                 break;
             const uint4 en = a.entries[d.x + k];
             const uint32_t e = en.y;
-            const uint32_t pos = o.compact ? P + k : P + k - ev_base[e];
+            const uint32_t pos = global_rank ? P + k : P + k - ev_base[e];
             if (pos < o.capacity) {
                 const uint32_t lin = en.x;
                 const uint32_t s = lin / (g.na * g.nb);
