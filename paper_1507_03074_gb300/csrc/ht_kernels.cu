@@ -25,7 +25,7 @@
 //                 (A,B) neighbours and compact peaks, in order, into per-CTA
 //                 chunks.  k_scan_direct is the same without staging, for
 //                 n_b not a multiple of 4.
-//   k_order       places every CTA's chunks at their global rank: ascending
+//   k_order       places every list's chunks at their global rank: ascending
 //                 linear index per event, expanded to 32-byte peak records.
 #include "ht_device.cuh"
 #include "ht_internal.h"
@@ -2185,75 +2185,108 @@ __global__ void __launch_bounds__(256) k_scan_ldg(Geom g, Work w, ScanArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// k_order: same grid as the scan.
+// k_order: one warp per list of chunks (a scan CTA's or a fused-fill list),
+// eight lists per CTA; a list's rank is the peak total of the lists before it.
 // ---------------------------------------------------------------------------
+// The 32-byte output record of entry {lin within event, event, votes, .}.
+__device__ __forceinline__ Peak peak_record(const Geom &g, const uint4 &en)
+{
+    const uint32_t lin = en.x;
+    const uint32_t s = lin / (g.na * g.nb);
+    const uint32_t rem = lin - s * (g.na * g.nb);
+    const uint32_t i = rem / g.nb, j = rem - i * g.nb;
+    Peak pk;
+    pk.itheta = s / g.np;
+    pk.iphi = s - pk.itheta * g.np;
+    pk.ia = i;
+    pk.ib = j;
+    pk.votes = en.z;
+    pk.a_c = a_centre(g, i);
+    pk.b_c = b_centre(g, j);
+    pk.event = en.y;
+    return pk;
+}
+
 __global__ void __launch_bounds__(256) k_order(Geom g, Work w, ScanArgs a, OrderArgs o)
 {
     grid_dep_wait();
     extern __shared__ uint32_t smo[];
     uint32_t *ev_base = smo;                  // n_events + 1
     uint32_t *red = ev_base + w.n_events + 1; // 40
-    __shared__ uint32_t s_last;
-    const uint32_t tid = threadIdx.x, bd = blockDim.x, c = blockIdx.x;
-    // this CTA's chunk counts and first descriptor, loaded ahead of the prefix
-    const uint32_t nseq = a.cta_nseq[c], mine = a.cta_total[c];
+    __shared__ uint32_t s_tot[32], s_last;
+    const uint32_t tid = threadIdx.x, bd = blockDim.x, warp = tid >> 5, lane = tid & 31u, nw = bd >> 5;
+    // one list per warp: lists c0 .. c0 + nw - 1
+    const uint32_t c0 = blockIdx.x * nw, c = c0 + warp;
+    const bool valid = c < a.grid;
+    const uint32_t nseq = valid ? a.cta_nseq[c] : 0u, mine = valid ? a.cta_total[c] : 0u;
     const uint2 d0 = nseq ? a.desc[(size_t)c * a.seq_max] : make_uint2(0u, 0u);
     // one event or one list over all events: the rank within the event is the
     // global rank (no per-event bases)
     const bool global_rank = o.compact || w.n_events == 1;
+    if (lane == 0)
+        s_tot[warp] = mine;
+    const bool any = __syncthreads_or(mine != 0);   // a CTA whose lists hold no peaks writes nothing
 
-    // rank of this CTA's first entry (a list without peaks writes nothing)
+    // rank of the CTA's first list: the totals of the lists before it
     uint32_t part = 0;
-    if (mine)
-        for (uint32_t q = tid; q < c; q += bd)
-            part += a.cta_total[q];
+    if (any)
+        for (uint32_t q0 = 0; q0 < c0; q0 += 4 * bd) {   // four loads per thread in flight
+            uint32_t v[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                const uint32_t q = q0 + k * bd + tid;
+                v[k] = q < c0 ? a.cta_total[q] : 0u;
+            }
+            part += (v[0] + v[1]) + (v[2] + v[3]);
+        }
     part = warp_incl_scan(part);
-    if ((tid & 31u) == 31u)
-        red[tid >> 5] = part;
-    if (mine && !global_rank)
+    if (lane == 31u)
+        red[warp] = part;
+    if (any && !global_rank)
         for (uint32_t e = tid; e < w.n_events; e += bd)
             ev_base[e] = o.ev_count[e];
     __syncthreads();
-    uint32_t prefix = 0;
-    for (uint32_t q = 0; q < (bd + 31) / 32; ++q)
-        prefix += red[q];
+    uint32_t P = 0;
+    for (uint32_t q = 0; q < nw; ++q)
+        P += red[q];
+    for (uint32_t q = 0; q < warp; ++q)   // the CTA's lists before this warp's
+        P += s_tot[q];
     __syncthreads();
-    if (mine && !global_rank)
+    if (any && !global_rank)
         block_exclusive_scan(ev_base, w.n_events, red);
 
-    uint32_t P = prefix;
     for (uint32_t q = 0; q < (mine ? nseq : 0u); ++q) {
         const uint2 d = q == 0 ? d0 : a.desc[(size_t)c * a.seq_max + q];
-        for (uint32_t k = tid; k < d.y; k += bd) {
+        for (uint32_t k = lane; k < d.y; k += 32u) {
             if (d.x + k >= a.entries_cap)
                 break;
             const uint4 en = a.entries[d.x + k];
             const uint32_t e = en.y;
             const uint32_t pos = global_rank ? P + k : P + k - ev_base[e];
-            if (pos < o.capacity) {
-                const uint32_t lin = en.x;
-                const uint32_t s = lin / (g.na * g.nb);
-                const uint32_t rem = lin - s * (g.na * g.nb);
-                const uint32_t i = rem / g.nb, j = rem - i * g.nb;
-                Peak pk;
-                pk.itheta = s / g.np;
-                pk.iphi = s - pk.itheta * g.np;
-                pk.ia = i;
-                pk.ib = j;
-                pk.votes = en.z;
-                pk.a_c = a_centre(g, i);
-                pk.b_c = b_centre(g, j);
-                pk.event = e;
-                o.out[o.compact ? (size_t)pos : (size_t)e * o.capacity + pos] = pk;
-            }
+            if (pos < o.capacity)
+                o.out[o.compact ? (size_t)pos : (size_t)e * o.capacity + pos] = peak_record(g, en);
         }
         P += d.y;
     }
-    if (c == 0)
+    if (global_rank) {
+        // no other CTA reads the per-event counts: the first one publishes and
+        // resets them (and the entry counter), and no CTA waits for the others
+        if (blockIdx.x == 0) {
+            for (uint32_t e = tid; e < w.n_events; e += bd) {
+                o.counts[e] = o.ev_count[e];
+                o.ev_count[e] = 0u;
+            }
+            if (tid == 0)
+                *o.g_count = 0u;
+        }
+        return;
+    }
+    if (blockIdx.x == 0)
         for (uint32_t e = tid; e < w.n_events; e += bd)
             o.counts[e] = o.ev_count[e];
 
-    // The last CTA to finish resets the counters for the next scan.
+    // Every CTA read the per-event counts: the last CTA to finish resets the
+    // counters for the next scan.
     __syncthreads();
     if (tid == 0) {
         __threadfence();
@@ -2663,7 +2696,8 @@ cudaError_t launch_order(const Geom &g, const Work &w, const ScanArgs &a, const 
         if (e != cudaSuccess)
             return e;
     }
-    return launch_pdl(k_order, a.grid, 256, smem, st, g, w, a, o);
+    // one list per warp, eight per CTA
+    return launch_pdl(k_order, (a.grid + 7) / 8, 256, smem, st, g, w, a, o);
 }
 
 cudaError_t scan_occupancy(int kind, size_t smem, int *blocks_per_sm)
