@@ -56,7 +56,21 @@ struct Work {
     // [unit][edge_pass][2][n_b] (pass p of a unit covers rows p * rpass ..)
     uint32_t *edge;
     uint32_t edge_pass;
+    // Where a fill's static split (the static items of every CTA) comes from:
+    // kSplitAfterWait: computed after the fill's dependency wait;
+    // kSplitEarly: computed before it (k_scatter let the fill launch only
+    //   after its own wait for k_bin, so the unit offsets are complete);
+    // kSplitGiven: read from split[] after the wait, where k_bin_cluster put
+    //   it for a fill of split_grid CTAs, split_strips strips per unit, vote
+    //   weight split_vw and split_n_static static items (a fill of another
+    //   shape computes its own).
+    uint32_t split_mode;
+    uint32_t split_grid, split_strips, split_vw;
+    uint64_t split_n_static;
+    uint64_t *split;            // [split_grid + 1] first static item of every fill CTA
 };
+
+constexpr uint32_t kSplitAfterWait = 0, kSplitEarly = 1, kSplitGiven = 2;
 
 constexpr uint32_t kDropped = 0xffffffffu;
 

@@ -185,6 +185,7 @@ ht_status engine_configure(Engine &E, std::string *why)
         E.fill_grid = (uint32_t)E.num_sms * (uint32_t)occ;
     }
     E.clear_grid = (uint32_t)E.num_sms * 4;
+    E.bin_cluster = htk::bin_cluster_supported(htk::kBinClusterSmem) ? 1 : 0;
 
     // --- fused fill + maxima ---------------------------------------------------
     // A smaller peak buffer than the scan's (the tile needs the room); k_seam
@@ -521,6 +522,7 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
     const uint32_t ctr_words = engine_ctr_words(E);
     const size_t units = (size_t)max_events * g.n_slices;
     const uint64_t list_cap = std::min<uint64_t>((uint64_t)hits_cap * E.max_admit, 0xffffffffull);
+    E.split_cap = (uint32_t)E.num_sms * 32 + 1;   // a fill grid of up to 32 CTAs per SM
     E.list_cap = (uint32_t)list_cap;
     if ((e = dalloc(&E.d_edges, (E.et.size() + E.ep.size() + E.bth.size()) * 4, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_M, (size_t)E.n_cells * 4 * max_events + 256, &acc)) != cudaSuccess ||
@@ -529,7 +531,8 @@ ht_status engine_create(Engine &E, const ht_binning *b, const ht_ranges *r, uint
         (e = dalloc(&E.d_slice, (3 * units + 1) * 4, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_list, (size_t)list_cap * 16, &acc)) != cudaSuccess ||
         (e = dalloc(&E.d_entries, (size_t)s.entries_cap * 16, &acc)) != cudaSuccess ||
-        (e = dalloc(&E.d_ctr, (size_t)ctr_words * 4, &acc)) != cudaSuccess) {
+        (e = dalloc(&E.d_ctr, (size_t)ctr_words * 4, &acc)) != cudaSuccess ||
+        (e = dalloc(&E.d_split, (size_t)E.split_cap * 8, &acc)) != cudaSuccess) {
         std::snprintf(buf, sizeof buf, "device allocation of %zu bytes failed: %s", acc,
                       cudaGetErrorString(e));
         *why = buf;
@@ -603,6 +606,7 @@ void engine_destroy(Engine &E)
     cudaFree(E.d_hits4);
     cudaFree(E.d_codes);
     cudaFree(E.d_slice);
+    cudaFree(E.d_split);
     cudaFree(E.d_list);
     cudaFree(E.d_edge);
     cudaFree(E.d_entries);
@@ -613,6 +617,7 @@ void engine_destroy(Engine &E)
     E.d_hits4 = nullptr;
     E.d_codes = nullptr;
     E.d_slice = nullptr;
+    E.d_split = nullptr;
     E.d_list = nullptr;
     E.d_edge = nullptr;
     E.edge_pass = 0;
@@ -646,7 +651,32 @@ static htk::Work make_work(Engine &E, const float *x, const float *y, const floa
     w.list_cap = E.list_cap;
     w.edge = E.d_edge;
     w.edge_pass = E.edge_pass;
+    w.split_mode = E.split_mode;
+    w.split_grid = E.split_grid;
+    w.split_strips = E.split_strips;
+    w.split_vw = E.split_vw;
+    w.split_n_static = E.split_n_static;
+    w.split = E.d_split;
     return w;
+}
+
+// When engine_vote's next fill for these flags is k_fill_tma: its
+// configuration and grid, so that k_bin_cluster can split its work ahead of
+// it (the fill checks the shape and splits by itself on a mismatch).
+static bool tma_fill_next(const Engine &E, uint32_t n_events, uint32_t flags, htk::FillCfg &ff, uint32_t &grid)
+{
+    if ((flags & (HT_FILL_NAIVE | HT_ACCUMULATE)) || !E.fill_priv_ok || !E.use_tma || E.use_ws)
+        return false;
+    const bool peaks_only = (flags & HT_PEAKS_ONLY) && E.fused_ok && E.d_edge &&
+                            E.edge_pass * std::max<uint32_t>(1, E.fused_fill.W / 2) >= E.geom.na;
+    if (peaks_only)
+        return false;
+    ff = E.tma_fill;
+    ff.accumulate = 0u;
+    ff.vote_weight = htk::kVoteWeight;
+    const uint64_t items = (uint64_t)n_events * E.geom.n_slices * ff.strips;
+    grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.tma_grid, items));
+    return grid + 1 <= E.split_cap;
 }
 
 cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *z,
@@ -656,6 +686,46 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
     htk::Work w = make_work(E, x, y, z, d_hit_off, n_hits0, n_events);
     cudaError_t e;
     E.fused_valid = false;
+    const size_t cl_smem = htk::bin_cluster_smem_bytes(E.geom, n_events);
+    if (n_total <= htk::kBinClusterMax * htk::kBinClusterThreads * htk::kBinClusterHPT &&
+        cl_smem <= htk::kBinClusterSmem) {
+        if (E.bin_cluster > 0) {
+            // few hits: binning and lists in one cluster launch
+            const uint32_t per = htk::kBinClusterThreads * htk::kBinClusterHPT;
+            const uint32_t cs = std::min<uint32_t>(
+                htk::kBinClusterMax,
+                std::max<uint32_t>((n_total + htk::kBinClusterThreads - 1) / htk::kBinClusterThreads,
+                                   (n_total + per - 1) / per));
+            htk::FillCfg ff{};
+            uint32_t grid = 0;
+            if (tma_fill_next(E, n_events, flags, ff, grid)) {
+                const uint64_t items = (uint64_t)n_events * E.geom.n_slices * ff.strips;
+                E.split_mode = htk::kSplitGiven;
+                E.split_grid = grid;
+                E.split_strips = ff.strips;
+                E.split_vw = ff.vote_weight;
+                E.split_n_static = items - (ff.dyn ? htk::dyn_items(items, grid) : 0);
+            } else {
+                E.split_mode = htk::kSplitAfterWait;   // the offsets come from the launch right before the fill
+            }
+            w = make_work(E, x, y, z, d_hit_off, n_hits0, n_events);
+            {
+                ProfScope ps(E, K_BIN, st);
+                e = htk::launch_bin_cluster(E.geom, w, std::max<uint32_t>(cs, 1u), st);
+            }
+            if (e != cudaSuccess)
+                return e;
+            ++E.launches;
+            E.ctr_dirty = false;
+            E.last_hit_off = d_hit_off;
+            E.last_n_hits0 = n_hits0;
+            E.last_n_events = n_events;
+            E.last_accumulate = (flags & HT_ACCUMULATE) != 0;
+            return engine_vote(E, d_hit_off, n_hits0, n_events, flags, st);
+        }
+    }
+    E.split_mode = htk::kSplitEarly;
+    w.split_mode = htk::kSplitEarly;
     {
         ProfScope ps(E, K_BIN, st);
         const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((n_total + 255) / 256, E.num_sms * 8));

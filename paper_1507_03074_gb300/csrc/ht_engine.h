@@ -87,6 +87,12 @@ struct Engine {
     uint32_t fused_grid_used = 0;
     uint32_t fused_events = 0;
     bool ctr_dirty = false;      // counters hold an unconsumed fused fill's peaks
+    int bin_cluster = -1;        // k_bin_cluster usable here (-1: not checked yet)
+    uint32_t split_mode = htk::kSplitEarly;   // Work::split_mode of the fill after the last binning
+    uint32_t split_grid = 0, split_strips = 0, split_vw = 0;
+    uint64_t split_n_static = 0;
+    uint64_t *d_split = nullptr;              // [split_cap] k_bin_cluster's split for the fill
+    uint32_t split_cap = 0;
     const uint32_t *last_hit_off = nullptr;   // what the last fill binned
     uint32_t last_n_hits0 = 0, last_n_events = 0;
     bool last_accumulate = false;

@@ -73,6 +73,16 @@ struct OrderArgs {
 
 cudaError_t launch_bin(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
 cudaError_t launch_scatter(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st);
+// k_bin + k_scatter as one cluster of cs <= kBinClusterMax CTAs of
+// kBinClusterThreads threads, each holding at most kBinClusterHPT hits: for
+// launches of at most kBinClusterMax * kBinClusterThreads * kBinClusterHPT hits
+// whose two words per unit and hit offsets fit kBinClusterSmem bytes.
+constexpr uint32_t kBinClusterMax = 8, kBinClusterThreads = 1024, kBinClusterHPT = 2;
+constexpr size_t kBinClusterSmem = 40 * 1024;
+size_t bin_cluster_smem_bytes(const Geom &g, uint32_t n_events);
+cudaError_t launch_bin_cluster(const Geom &g, const Work &w, uint32_t cs, cudaStream_t st);
+// Whether this device runs a cluster of kBinClusterMax such CTAs.
+bool bin_cluster_supported(size_t smem);
 size_t fill_smem_bytes(const FillCfg &c);
 cudaError_t launch_fill_priv(const Geom &g, const Work &w, const FillCfg &c, uint32_t grid,
                              cudaStream_t st);

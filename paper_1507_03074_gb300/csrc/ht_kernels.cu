@@ -30,6 +30,8 @@
 #include "ht_device.cuh"
 #include "ht_internal.h"
 
+#include <cooperative_groups.h>
+
 #include <atomic>
 #include <utility>
 
@@ -249,6 +251,185 @@ __global__ void __launch_bounds__(256) k_scatter(Geom g, Work w)
     const uint32_t U = w.n_events * g.n_slices;
     for (uint32_t u = t0; u < U; u += stride)
         w.slice_cnt[u] = 0u;
+}
+
+// The static split of the fill that follows (the split cta_items computes,
+// for the shape Work::split_* names), from unit offsets off[0..U) in shared
+// memory and their total: split[c] = the first static item of fill CTA c.
+// Work item cost as in cta_items: g.na * (g.nb * u + vote weight * off[u])
+// up to unit u, strictly increasing in u; a CTA boundary at cost T falls in
+// the unit u with cost(u) <= T < cost(u + 1), at the strip it reaches.
+// Int: the arithmetic type, uint32_t when every cost (and G * G) is below
+// 2^31, which spares the 64-bit divisions.
+template <typename Int>
+__device__ __forceinline__ void split_for_fill_t(const Geom &g, const Work &w, const uint32_t *off, uint32_t total,
+                                                 uint64_t tot64)
+{
+    const uint32_t U = w.n_events * g.n_slices, G = w.split_grid, S = w.split_strips;
+    const uint64_t ns = w.split_n_static;
+    auto cost = [&](uint32_t u) {
+        return (Int)((uint64_t)g.na * ((uint64_t)g.nb * u + (uint64_t)w.split_vw * (u < U ? off[u] : total)));
+    };
+    const Int tot = (Int)tot64, c_end = cost(U), q = tot / G, r = tot % G;
+    for (uint32_t c = threadIdx.x; c <= G; c += blockDim.x) {
+        uint64_t item = ns;
+        if (c == 0) {
+            item = 0;
+        } else if (c < G) {
+            const Int T = q * c + (r * c) / G;
+            if (T < c_end) {
+                uint32_t lo = 0, hi = U - 1;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (cost(mid) <= T)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                const Int a = cost(lo), b = cost(lo + 1);
+                const Int per = (b - a + S - 1) / S;
+                const Int k = (T - a) / per;
+                item = min((uint64_t)lo * S + min((uint64_t)k, (uint64_t)S - 1), ns);
+            }
+        }
+        w.split[c] = item;
+    }
+}
+
+__device__ void split_for_fill(const Geom &g, const Work &w, const uint32_t *off, uint32_t total)
+{
+    const uint32_t U = w.n_events * g.n_slices, G = w.split_grid, S = w.split_strips;
+    const uint64_t ns = w.split_n_static;
+    auto cost = [&](uint32_t u) {
+        return (uint64_t)g.na * ((uint64_t)g.nb * u + (uint64_t)w.split_vw * (u < U ? off[u] : total));
+    };
+    const bool small = cost(U) < (1ull << 31) && ns < (1ull << 31) && (uint64_t)G * (G + 1) < (1ull << 31) &&
+                       S < (1u << 30);
+    // the cost of the first ns items
+    uint64_t tot;
+    if (small) {
+        const uint32_t n32 = (uint32_t)ns, us = n32 / S, ks = n32 % S;
+        uint32_t t = (uint32_t)cost(us);
+        if (ks)
+            t += ks * (((uint32_t)cost(us + 1) - t + S - 1) / S);
+        tot = t;
+    } else {
+        const uint32_t us = (uint32_t)(ns / S), ks = (uint32_t)(ns % S);
+        tot = cost(us);
+        if (ks)
+            tot += ks * ((cost(us + 1) - tot + S - 1) / S);
+    }
+    if (small)
+        split_for_fill_t<uint32_t>(g, w, off, total, tot);
+    else
+        split_for_fill_t<uint64_t>(g, w, off, total, tot);
+}
+
+// k_bin and k_scatter in one launch for launches of few hits: one cluster of
+// up to kBinClusterMax CTAs.  Each CTA counts its hits per unit in its own
+// shared memory, then adds each nonzero count once into the first CTA's
+// totals (distributed shared memory); the value that add returns is the
+// CTA's place inside the unit.  The first CTA turns the totals into unit
+// offsets, every CTA adds them to its places and lists its hits with local
+// cursors.  Hardware cluster barriers order the phases: no global atomics
+// and no second launch.  Each thread keeps its (at most kBinClusterHPT) hits
+// in registers between counting and listing.  Dynamic shared memory: U local
+// counts, U totals (used in the first CTA), n_events + 1 hit offsets, where
+// U = n_events * n_slices.
+__global__ void __launch_bounds__(1024, 1) k_bin_cluster(Geom g, Work w)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ float et[1025], ep[1025];
+    __shared__ uint32_t s_wsum[40];
+    extern __shared__ uint32_t s_loc[];
+    const uint32_t tid = threadIdx.x, bd = blockDim.x;
+    const uint32_t rank = cl.block_rank(), cs = cl.num_blocks();
+    const uint32_t U = w.n_events * g.n_slices;
+    uint32_t *s_tot = s_loc + U, *s_off = s_tot + U;
+    uint32_t *l_tot = cl.map_shared_rank(s_tot, 0);   // the first CTA's totals
+    for (uint32_t i = tid; i <= g.nt; i += bd)
+        et[i] = g.et[i];
+    for (uint32_t i = tid; i <= g.np; i += bd)
+        ep[i] = g.ep[i];
+    for (uint32_t u = tid; u < U; u += bd)
+        s_loc[u] = s_tot[u] = 0u;
+    cl.sync();   // every CTA's totals are zero before any CTA adds into the first's
+    grid_dep_wait();     // counters and hits of earlier kernels
+    grid_dep_launch();   // the fill's set-up overlaps; it waits for this grid's end
+    if (rank == 0) {   // fresh counters for the fill and scan that follow
+        if (tid == 0)
+            w.ctr[CTR_ENTRIES] = w.ctr[CTR_OTICKET] = 0u;
+        for (uint32_t i = tid; i < w.n_events; i += bd)
+            w.ctr[CTR_EVENTS + i] = 0u;
+    }
+    if (w.hit_off)
+        for (uint32_t i = tid; i <= w.n_events; i += bd)
+            s_off[i] = w.hit_off[i];
+    __syncthreads();
+    const uint32_t n = w.hit_off ? min(s_off[w.n_events], w.n_hits0) : w.n_hits0;
+    uint32_t code[kBinClusterHPT], ev[kBinClusterHPT];
+    float4 hv[kBinClusterHPT];
+#pragma unroll
+    for (uint32_t q = 0; q < kBinClusterHPT; ++q) {
+        const uint32_t h = (q * cs + rank) * bd + tid;
+        code[q] = kDropped;
+        ev[q] = 0u;
+        hv[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (h < n) {
+            const float x = __ldg(&w.x[h]), y = __ldg(&w.y[h]);
+            float r2;
+            code[q] = bin_code(g, et, ep, x, y, __ldg(&w.z[h]), r2);
+            if (w.hit_off) {   // the last event whose first hit is <= h
+                uint32_t lo = 0, hi = w.n_events - 1;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= h)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                ev[q] = lo;
+            }
+            hv[q] = make_float4(x, r2, __fmul_rn(2.0f, y), __uint_as_float(ev[q]));
+            const uint32_t e = ev[q];
+            for_each_slice(g, code[q], [&](uint32_t s) { atomicAdd(&s_loc[e * g.n_slices + s], 1u); });
+        }
+    }
+    __syncthreads();   // this CTA's counts are complete
+    for (uint32_t u = tid; u < U; u += bd) {
+        const uint32_t c = s_loc[u];
+        if (c)
+            s_loc[u] = atomicAdd(&l_tot[u], c);   // this CTA's place inside unit u
+    }
+    cl.sync();   // every CTA's counts are in the totals
+    uint32_t total = 0;
+    if (rank == 0) {
+        total = block_exclusive_scan(s_tot, U, s_wsum);   // totals -> unit offsets
+        for (uint32_t u = tid; u < U; u += bd)
+            w.slice_off[u] = s_tot[u];
+        if (tid == 0)
+            w.slice_off[U] = total;
+    }
+    cl.sync();   // the first CTA's totals hold the offsets
+    for (uint32_t u = tid; u < U; u += bd)
+        s_loc[u] += l_tot[u];   // this CTA's first list index in unit u
+    // done with the first CTA's words: arrive now, wait before exiting, so
+    // that the first CTA's shared memory outlives every read of it
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    __syncthreads();
+#pragma unroll
+    for (uint32_t q = 0; q < kBinClusterHPT; ++q) {
+        const uint32_t e = ev[q];
+        for_each_slice(g, code[q], [&](uint32_t s) {
+            const uint32_t idx = atomicAdd(&s_loc[e * g.n_slices + s], 1u);
+            if (idx < w.list_cap)
+                w.list[idx] = hv[q];
+        });
+    }
+    if (rank == 0 && w.split_mode == kSplitGiven)
+        split_for_fill(g, w, s_tot, total);
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -1538,17 +1719,26 @@ __global__ void __launch_bounds__(1024) k_fill_tma(Geom g, Work w, FillCfg c, Sc
     const uint32_t cta = blockIdx.x;
     ChunkList inner = interior_list(a, cta);
 
-    // The static split reads only the unit offsets, which k_bin wrote: when
-    // k_scatter precedes this kernel it lets it launch only after k_bin has
-    // finished, and any other predecessor lets it launch only at its own
-    // end, so the split runs ahead of the wait for k_scatter's lists.
+    // The static split reads only the unit offsets.  When k_bin wrote them
+    // and k_scatter precedes this kernel (kSplitEarly), k_scatter lets it
+    // launch only after k_bin has finished, so the split runs ahead of the
+    // wait for k_scatter's lists; after k_bin_cluster the split is read
+    // from what that kernel wrote (kSplitGiven), or computed after the wait.
     __shared__ unsigned long long s_rng[2];
     __shared__ uint32_t s_dyn;
     const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
     const uint64_t n_dyn = c.dyn ? dyn_items(items, gridDim.x) : 0, n_static = items - n_dyn;
     uint64_t it0, it1;
-    cta_items(g, w, c, cta, gridDim.x, n_static, it0, it1, s_rng);
-    grid_dep_wait();   // the unit lists of k_scatter
+    if (w.split_mode == kSplitEarly)
+        cta_items(g, w, c, cta, gridDim.x, n_static, it0, it1, s_rng);
+    grid_dep_wait();   // the unit lists (and, after k_bin_cluster, the offsets and split)
+    if (w.split_mode == kSplitGiven && w.split_grid == gridDim.x && w.split_strips == c.strips &&
+        w.split_vw == c.vote_weight && w.split_n_static == n_static) {
+        it0 = __ldcg(&w.split[cta]);
+        it1 = __ldcg(&w.split[cta + 1]);
+    } else if (w.split_mode != kSplitEarly) {
+        cta_items(g, w, c, cta, gridDim.x, n_static, it0, it1, s_rng);
+    }
     uint64_t cached_es = ~0ull;
     FlatMap cached{};
     uint32_t buf_n = 0, nseq = 0, total = 0;
@@ -2379,6 +2569,53 @@ cudaError_t launch_bin(const Geom &g, const Work &w, uint32_t grid, cudaStream_t
 cudaError_t launch_scatter(const Geom &g, const Work &w, uint32_t grid, cudaStream_t st)
 {
     return launch_pdl(k_scatter, grid, 256, 0, st, g, w);
+}
+
+size_t bin_cluster_smem_bytes(const Geom &g, uint32_t n_events)
+{
+    return ((size_t)2 * n_events * g.n_slices + n_events + 1) * 4;
+}
+
+bool bin_cluster_supported(size_t smem)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kBinClusterMax);
+    cfg.blockDim = dim3(kBinClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kBinClusterMax;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (allow_smem((const void *)k_bin_cluster, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveClusters(&n, (const void *)k_bin_cluster, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n > 0;
+}
+
+cudaError_t launch_bin_cluster(const Geom &g, const Work &w, uint32_t cs, cudaStream_t st)
+{
+    const size_t smem = bin_cluster_smem_bytes(g, w.n_events);   // <= kBinClusterSmem, allowed by bin_cluster_supported
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(kBinClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, k_bin_cluster, g, w);
 }
 
 size_t fill_scan_smem_bytes(const FillCfg &c, const ScanArgs &a, uint32_t nb)
