@@ -713,8 +713,9 @@ def timed_in_flight(sts, step, K, W):
 def pick_in_flight(ctxs, sts, step, tuning, n=600):
     """The faster, over n in-flight steps, of the single-event launch shape and
     the same shape with one fill CTA per SM (two events' fills then share each
-    SM); leaves the contexts at the choice."""
-    cands = [dict(tuning), dict(tuning, fill_blocks_per_sm=1)]
+    SM), the binning launches left to the library's choice for each shape;
+    leaves the contexts at the choice and returns it as they report it."""
+    cands = [dict(tuning, bin_cluster=0), dict(tuning, fill_blocks_per_sm=1, bin_cluster=0)]
     best, best_ms = cands[0], None
     for t in cands:
         for c in ctxs:
@@ -724,7 +725,7 @@ def pick_in_flight(ctxs, sts, step, tuning, n=600):
             best, best_ms = t, ms
     for c in ctxs:
         c.set_tuning(**best)
-    return best
+    return ctxs[0].get_tuning()
 
 
 def run_maxima4d(ctxs, dev, outs, cnts, cap, sts, K, W):

@@ -18,7 +18,7 @@ static const uint32_t kFusedPeakBuf = 512;     // K of a fused-fill CTA (at leas
 
 const char *const kKernelNames[K_NKINDS] = {"k_bin", "k_scatter", "k_fill_priv", "k_fill_scan", "k_fill_ws",
                                              "k_fill_peaks", "k_peaks", "k_clear", "k_fill_naive", "k_scan",
-                                             "k_order", "k_peaks4d", "k_fill_tma"};
+                                             "k_order", "k_peaks4d", "k_fill_tma", "k_bin_cluster"};
 
 // ---------------------------------------------------------------------------
 // Profiling
@@ -126,6 +126,10 @@ ht_status engine_configure(Engine &E, std::string *why)
     }
     if (t.vote_agg > 1) {
         *why = "fill_vote_agg must be 0 (plain shared-memory atomics) or 1 (warp-aggregated)";
+        return HT_E_INVAL;
+    }
+    if (t.bin_cluster > 2) {
+        *why = "bin_cluster must be 0 (auto), 1 (one cluster launch) or 2 (two launches)";
         return HT_E_INVAL;
     }
     if (t.fused > 5) {
@@ -269,6 +273,7 @@ ht_status engine_configure(Engine &E, std::string *why)
     E.use_ws = E.ws_ok;
     // --- fused fill with bulk-copy tiles: two u32 tiles in M_H's layout ----------
     E.tma_ok = false;
+    E.tma_capped = false;
     // the default fused fill wherever it fits (fused 0 = auto)
     if (E.fill_priv_ok && (t.fused == 5 || t.fused == 0) && (b.n_b & 3u) == 0 && b.n_b <= 4096) {
         htk::FillCfg tf = f;
@@ -303,7 +308,9 @@ ht_status engine_configure(Engine &E, std::string *why)
             tf.HC -= tf.threads;
             occ = occupancy(tf);
         }
+        E.tma_capped = false;
         if (occ >= 1) {
+            E.tma_capped = t.fill_blocks_per_sm && (int)t.fill_blocks_per_sm < occ;
             if (t.fill_blocks_per_sm)
                 occ = std::min<int>(occ, (int)t.fill_blocks_per_sm);
             E.tma_ok = true;
@@ -687,7 +694,11 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
     cudaError_t e;
     E.fused_valid = false;
     const size_t cl_smem = htk::bin_cluster_smem_bytes(E.geom, n_events);
-    if (n_total <= htk::kBinClusterMax * htk::kBinClusterThreads * htk::kBinClusterHPT &&
+    htk::FillCfg ff{};
+    uint32_t grid = 0;
+    const bool tma_next = tma_fill_next(E, n_events, flags, ff, grid);
+    const bool want_cluster = E.tune.bin_cluster == 1 || (E.tune.bin_cluster == 0 && tma_next && !E.tma_capped);
+    if (want_cluster && n_total <= htk::kBinClusterMax * htk::kBinClusterThreads * htk::kBinClusterHPT &&
         cl_smem <= htk::kBinClusterSmem) {
         if (E.bin_cluster > 0) {
             // few hits: binning and lists in one cluster launch
@@ -696,9 +707,7 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
                 htk::kBinClusterMax,
                 std::max<uint32_t>((n_total + htk::kBinClusterThreads - 1) / htk::kBinClusterThreads,
                                    (n_total + per - 1) / per));
-            htk::FillCfg ff{};
-            uint32_t grid = 0;
-            if (tma_fill_next(E, n_events, flags, ff, grid)) {
+            if (tma_next) {
                 const uint64_t items = (uint64_t)n_events * E.geom.n_slices * ff.strips;
                 E.split_mode = htk::kSplitGiven;
                 E.split_grid = grid;
@@ -710,7 +719,7 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
             }
             w = make_work(E, x, y, z, d_hit_off, n_hits0, n_events);
             {
-                ProfScope ps(E, K_BIN, st);
+                ProfScope ps(E, K_BIN_CLUSTER, st);
                 e = htk::launch_bin_cluster(E.geom, w, std::max<uint32_t>(cs, 1u), st);
             }
             if (e != cudaSuccess)
@@ -1007,6 +1016,7 @@ ht_status engine_set_tuning(Engine &E, const ht_tuning &t, bool *poisoned, std::
     n.scan_blocks_per_sm = t.scan_blocks_per_sm;
     n.fused = t.fill_fused_scan;
     n.vote_agg = t.fill_vote_agg;
+    n.bin_cluster = t.bin_cluster;
     ht_status s = engine_configure(E, why);
     if (s != HT_OK) {
         E.tune = old;
@@ -1030,6 +1040,7 @@ void engine_get_tuning(const Engine &E, ht_tuning *t)
     t->scan_blocks_per_sm = E.num_sms ? E.scan_grid_max / (uint32_t)E.num_sms : 0;
     t->fill_fused_scan = E.use_ws ? 3u : E.use_tma ? 5u : E.fused_ok ? (E.fused_fill.bulk ? 4u : 1u) : 2u;
     t->fill_vote_agg = E.use_tma ? E.tma_fill.vote_agg : 0u;
+    t->bin_cluster = E.tune.bin_cluster ? E.tune.bin_cluster : (E.use_tma && !E.tma_capped) ? 1u : 2u;
     if (E.use_tma) {
         t->fill_rows = E.tma_fill.W;
         t->fill_threads = E.tma_fill.threads;

@@ -26,13 +26,14 @@ struct Tuning {
     uint32_t fused = 0;               // 0 auto, 1 fused (one thread group), 2 off, 3 fused warp-specialised,
                                       // 4 fused with bulk-copy staging, 5 fused with bulk-copy u32 tiles
     uint32_t vote_agg = 0;            // warp-aggregated vote increments (bulk-copy-tile fill)
+    uint32_t bin_cluster = 0;         // 0 auto, 1 k_bin_cluster when it fits, 2 k_bin + k_scatter
 };
 
 // Optional per-kernel timing with CUDA events recorded on the launching
 // stream around every launch (enabled by ht_profile).
 enum KernelKind {
     K_BIN, K_SCATTER, K_FILL_PRIV, K_FILL_SCAN, K_FILL_WS, K_FILL_PEAKS, K_PEAKS, K_CLEAR, K_FILL_NAIVE, K_SCAN,
-    K_ORDER, K_PEAKS4D, K_FILL_TMA, K_NKINDS
+    K_ORDER, K_PEAKS4D, K_FILL_TMA, K_BIN_CLUSTER, K_NKINDS
 };
 extern const char *const kKernelNames[K_NKINDS];
 
@@ -88,6 +89,7 @@ struct Engine {
     uint32_t fused_events = 0;
     bool ctr_dirty = false;      // counters hold an unconsumed fused fill's peaks
     int bin_cluster = -1;        // k_bin_cluster usable here (-1: not checked yet)
+    bool tma_capped = false;     // fill_blocks_per_sm holds the bulk-copy-tile fill below its occupancy
     uint32_t split_mode = htk::kSplitEarly;   // Work::split_mode of the fill after the last binning
     uint32_t split_grid = 0, split_strips = 0, split_vw = 0;
     uint64_t split_n_static = 0;

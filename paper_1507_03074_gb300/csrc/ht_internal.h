@@ -76,7 +76,7 @@ cudaError_t launch_scatter(const Geom &g, const Work &w, uint32_t grid, cudaStre
 // k_bin + k_scatter as one cluster of cs <= kBinClusterMax CTAs of
 // kBinClusterThreads threads, each holding at most kBinClusterHPT hits: for
 // launches of at most kBinClusterMax * kBinClusterThreads * kBinClusterHPT hits
-// whose two words per unit and hit offsets fit kBinClusterSmem bytes.
+// whose three words per unit and hit offsets fit kBinClusterSmem bytes.
 constexpr uint32_t kBinClusterMax = 8, kBinClusterThreads = 1024, kBinClusterHPT = 2;
 constexpr size_t kBinClusterSmem = 40 * 1024;
 size_t bin_cluster_smem_bytes(const Geom &g, uint32_t n_events);

@@ -327,34 +327,33 @@ __device__ void split_for_fill(const Geom &g, const Work &w, const uint32_t *off
 
 // k_bin and k_scatter in one launch for launches of few hits: one cluster of
 // up to kBinClusterMax CTAs.  Each CTA counts its hits per unit in its own
-// shared memory, then adds each nonzero count once into the first CTA's
-// totals (distributed shared memory); the value that add returns is the
-// CTA's place inside the unit.  The first CTA turns the totals into unit
-// offsets, every CTA adds them to its places and lists its hits with local
-// cursors.  Hardware cluster barriers order the phases: no global atomics
-// and no second launch.  Each thread keeps its (at most kBinClusterHPT) hits
-// in registers between counting and listing.  Dynamic shared memory: U local
-// counts, U totals (used in the first CTA), n_events + 1 hit offsets, where
-// U = n_events * n_slices.
+// shared memory; after one cluster barrier every CTA reads all the CTAs'
+// counts (distributed shared memory) and derives by itself the unit totals,
+// its own place inside every unit (the counts of the CTAs ranked below it)
+// and, by an exclusive scan of the totals, the unit offsets.  It then lists
+// its hits with local cursors.  No CTA writes another's shared memory, and
+// the only other cluster barrier (split into arrive and wait) keeps every
+// CTA's counts alive until all have read them.  Each thread keeps its (at
+// most kBinClusterHPT) hits in registers between counting and listing.
+// Dynamic shared memory: U counts, U + 1 totals / offsets, U places and
+// n_events + 1 hit offsets, where U = n_events * n_slices.
 __global__ void __launch_bounds__(1024, 1) k_bin_cluster(Geom g, Work w)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     __shared__ float et[1025], ep[1025];
     __shared__ uint32_t s_wsum[40];
-    extern __shared__ uint32_t s_loc[];
+    extern __shared__ uint32_t s_cnt[];
     const uint32_t tid = threadIdx.x, bd = blockDim.x;
     const uint32_t rank = cl.block_rank(), cs = cl.num_blocks();
     const uint32_t U = w.n_events * g.n_slices;
-    uint32_t *s_tot = s_loc + U, *s_off = s_tot + U;
-    uint32_t *l_tot = cl.map_shared_rank(s_tot, 0);   // the first CTA's totals
+    uint32_t *s_tot = s_cnt + U, *s_pl = s_tot + U + 1, *s_off = s_pl + U;
     for (uint32_t i = tid; i <= g.nt; i += bd)
         et[i] = g.et[i];
     for (uint32_t i = tid; i <= g.np; i += bd)
         ep[i] = g.ep[i];
     for (uint32_t u = tid; u < U; u += bd)
-        s_loc[u] = s_tot[u] = 0u;
-    cl.sync();   // every CTA's totals are zero before any CTA adds into the first's
+        s_cnt[u] = 0u;
     grid_dep_wait();     // counters and hits of earlier kernels
     grid_dep_launch();   // the fill's set-up overlaps; it waits for this grid's end
     if (rank == 0) {   // fresh counters for the fill and scan that follow
@@ -393,36 +392,48 @@ __global__ void __launch_bounds__(1024, 1) k_bin_cluster(Geom g, Work w)
             }
             hv[q] = make_float4(x, r2, __fmul_rn(2.0f, y), __uint_as_float(ev[q]));
             const uint32_t e = ev[q];
-            for_each_slice(g, code[q], [&](uint32_t s) { atomicAdd(&s_loc[e * g.n_slices + s], 1u); });
+            for_each_slice(g, code[q], [&](uint32_t s) { atomicAdd(&s_cnt[e * g.n_slices + s], 1u); });
         }
     }
-    __syncthreads();   // this CTA's counts are complete
+    cl.sync();   // every CTA's counts are complete (and every CTA of the cluster runs)
+    const uint32_t *r_cnt[kBinClusterMax];
+#pragma unroll
+    for (uint32_t r = 0; r < kBinClusterMax; ++r)
+        r_cnt[r] = cl.map_shared_rank(s_cnt, r < cs ? r : 0u);
     for (uint32_t u = tid; u < U; u += bd) {
-        const uint32_t c = s_loc[u];
-        if (c)
-            s_loc[u] = atomicAdd(&l_tot[u], c);   // this CTA's place inside unit u
+        uint32_t c[kBinClusterMax];
+#pragma unroll
+        for (uint32_t r = 0; r < kBinClusterMax; ++r)
+            c[r] = r < cs ? r_cnt[r][u] : 0u;
+        uint32_t tot = 0, below = 0;
+#pragma unroll
+        for (uint32_t r = 0; r < kBinClusterMax; ++r) {
+            below += r < rank ? c[r] : 0u;
+            tot += c[r];
+        }
+        s_tot[u] = tot;
+        s_pl[u] = below;
     }
-    cl.sync();   // every CTA's counts are in the totals
-    uint32_t total = 0;
-    if (rank == 0) {
-        total = block_exclusive_scan(s_tot, U, s_wsum);   // totals -> unit offsets
-        for (uint32_t u = tid; u < U; u += bd)
-            w.slice_off[u] = s_tot[u];
-        if (tid == 0)
-            w.slice_off[U] = total;
-    }
-    cl.sync();   // the first CTA's totals hold the offsets
-    for (uint32_t u = tid; u < U; u += bd)
-        s_loc[u] += l_tot[u];   // this CTA's first list index in unit u
-    // done with the first CTA's words: arrive now, wait before exiting, so
-    // that the first CTA's shared memory outlives every read of it
+    // done with the other CTAs' counts: arrive now, wait before exiting, so
+    // that every CTA's shared memory outlives every read of it
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    __syncthreads();
+    const uint32_t total = block_exclusive_scan(s_tot, U, s_wsum);   // totals -> unit offsets
+    if (tid == 0)
+        s_tot[U] = total;
+    for (uint32_t u = tid; u < U; u += bd) {
+        s_pl[u] += s_tot[u];   // this CTA's first list index in unit u
+        if (rank == 0)
+            w.slice_off[u] = s_tot[u];
+    }
+    if (rank == 0 && tid == 0)
+        w.slice_off[U] = total;
     __syncthreads();
 #pragma unroll
     for (uint32_t q = 0; q < kBinClusterHPT; ++q) {
         const uint32_t e = ev[q];
         for_each_slice(g, code[q], [&](uint32_t s) {
-            const uint32_t idx = atomicAdd(&s_loc[e * g.n_slices + s], 1u);
+            const uint32_t idx = atomicAdd(&s_pl[e * g.n_slices + s], 1u);
             if (idx < w.list_cap)
                 w.list[idx] = hv[q];
         });
@@ -2573,7 +2584,7 @@ cudaError_t launch_scatter(const Geom &g, const Work &w, uint32_t grid, cudaStre
 
 size_t bin_cluster_smem_bytes(const Geom &g, uint32_t n_events)
 {
-    return ((size_t)2 * n_events * g.n_slices + n_events + 1) * 4;
+    return ((size_t)3 * n_events * g.n_slices + 1 + n_events + 1) * 4;
 }
 
 bool bin_cluster_supported(size_t smem)

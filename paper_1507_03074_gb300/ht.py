@@ -42,7 +42,7 @@ class c_ranges(ctypes.Structure):
 
 TUNING_FIELDS = ("fill_rows", "fill_threads", "fill_hits_staged", "fill_blocks_per_sm",
                  "scan_kind", "scan_stage_bytes", "scan_slots", "scan_blocks_per_sm", "fill_fused_scan",
-                 "fill_vote_agg")
+                 "fill_vote_agg", "bin_cluster")
 HT_SCAN_AUTO, HT_SCAN_BULK, HT_SCAN_STREAM, HT_SCAN_DIRECT = 0, 1, 2, 3
 
 

@@ -46,6 +46,14 @@ def test_pick_in_flight_keeps_the_faster_shape(monkeypatch):
         def set_tuning(self, **t):
             self.t = dict(t)
 
+        def get_tuning(self):
+            # the library resolves bin_cluster 0: two launches when the fill
+            # is held below its CTAs per SM, one cluster launch otherwise
+            t = dict(self.t)
+            if t.get("bin_cluster", 0) == 0:
+                t["bin_cluster"] = 2 if t["fill_blocks_per_sm"] == 1 else 1
+            return t
+
     ctxs = [FakeCtx() for _ in range(4)]
     base = {"fill_rows": 32, "fill_blocks_per_sm": 2}
     for one_cta_faster in (True, False):
@@ -56,5 +64,7 @@ def test_pick_in_flight_keeps_the_faster_shape(monkeypatch):
         monkeypatch.setattr(bench, "timed_in_flight", fake_timed)
         best = bench.pick_in_flight(ctxs, [None] * 4, lambda k: None, base)
         assert best["fill_blocks_per_sm"] == (1 if one_cta_faster else 2)
-        assert all(c.t == best for c in ctxs)
+        assert all(c.get_tuning() == best for c in ctxs)   # the contexts stay at the choice
+        assert all(c.t["bin_cluster"] == 0 for c in ctxs)   # binning left to the library per shape
+        assert best["bin_cluster"] == (2 if one_cta_faster else 1)
         assert best["fill_rows"] == 32

@@ -88,6 +88,32 @@ def test_batch_matches_oracle_and_replays(ht, uneven):
         _check_events(evs, pk, counts, refs)
 
 
+@pytest.mark.parametrize("bin_cluster", [1, 2])
+def test_batch_binning_launches(ht, uneven, bin_cluster):
+    """Batches of at most 16384 hits: binning and unit lists in one
+    thread-block-cluster launch (1, whose CTAs also find each hit's event by
+    its offsets) or in two launches (2) -- the same peaks and matrices."""
+    evs, refs = uneven
+    keep, n = [], 0
+    for i, ev in enumerate(evs):
+        if n + len(ev[0]) <= 16384:
+            keep.append(i)
+            n += len(ev[0])
+    assert len(keep) >= 3
+    sub, subr = [evs[i] for i in keep], [refs[i] for i in keep]
+    b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    with ht.Batch(b, r, threshold=10, max_events=8, max_hits=16384, capacity=1 << 16) as B:
+        B.set_tuning(bin_cluster=bin_cluster)
+        assert B.get_tuning()["bin_cluster"] == bin_cluster
+        for rep in range(3):                       # direct + capture, then a graph replay
+            pk, counts = B.run(*ht.Batch.concat(sub))
+            _check_events(sub, pk, counts, subr)
+        for e in range(len(sub)):
+            assert np.array_equal(B.matrix(e), subr[e][0])
+        pk, counts = B.run(*ht.Batch.concat(sub[::-1]))
+        _check_events(sub[::-1], pk, counts, subr[::-1])
+
+
 def test_batch_peaks_only(ht, uneven):
     """HT_PEAKS_ONLY runs: the same peaks, the matrices left as the last
     normal run wrote them; normal and peaks-only runs alternate on their own

@@ -463,7 +463,8 @@ TUNINGS = [
     dict(fill_fused_scan=5, fill_rows=4, fill_threads=256), dict(fill_fused_scan=5, fill_hits_staged=64),
     dict(fill_fused_scan=5, fill_rows=2, fill_blocks_per_sm=1), dict(fill_fused_scan=5, fill_rows=8, fill_threads=1024),
     dict(fill_vote_agg=1), dict(fill_fused_scan=5, fill_vote_agg=1, fill_rows=4, fill_threads=256),
-    dict(fill_blocks_per_sm=1),
+    dict(fill_blocks_per_sm=1), dict(bin_cluster=2), dict(bin_cluster=1, fill_blocks_per_sm=1),
+    dict(bin_cluster=1, fill_fused_scan=2), dict(bin_cluster=1, fill_fused_scan=4),
 ]
 
 
@@ -485,7 +486,8 @@ def test_tuning_sweep(ht, paper_ref, tuning):
         ctx.set_tuning(**tuning)
         got = ctx.get_tuning()
         for k, v in tuning.items():
-            if k in ("scan_kind", "fill_rows", "fill_threads", "scan_slots", "fill_fused_scan", "fill_vote_agg"):
+            if k in ("scan_kind", "fill_rows", "fill_threads", "scan_slots", "fill_fused_scan", "fill_vote_agg",
+                     "bin_cluster"):
                 assert got[k] == v, (k, got)
         ctx.fill(ev.x, ev.y, ev.z)
         pk, n = ctx.find_maxima(capacity=1 << 16)
@@ -494,9 +496,27 @@ def test_tuning_sweep(ht, paper_ref, tuning):
     assert_peaks_equal(pk, pk_ref)
 
 
+def test_bin_cluster_auto(ht, paper_ref):
+    """bin_cluster 0 resolves to one cluster launch for the bulk-copy-tile
+    fill at its occupancy and to two launches when fill_blocks_per_sm holds
+    the fill below it; either way the peaks are the oracle's."""
+    ev, M_ref, pk_ref, n_ref = paper_ref
+    with ht.Context(ht.Binning(*synth.PAPER_BINNING), ht.Ranges(), threshold=10, max_hits=ev.n_hits) as ctx:
+        assert ctx.get_tuning()["bin_cluster"] == 1
+        for tun, want in ((dict(fill_blocks_per_sm=1), 2), (dict(fill_blocks_per_sm=1, bin_cluster=1), 1),
+                          (dict(bin_cluster=2), 2), (dict(fill_fused_scan=2), 2)):
+            ctx.set_tuning(**tun)
+            assert ctx.get_tuning()["bin_cluster"] == want, tun
+            ctx.fill(ev.x, ev.y, ev.z)
+            pk, n = ctx.find_maxima(capacity=1 << 16)
+            assert n == n_ref
+            assert_peaks_equal(pk, pk_ref)
+
+
 def test_bad_tuning_rejected(ht):
     with ht.Context(ht.Binning(*synth.TINY_BINNING), ht.Ranges(), threshold=8, max_hits=256) as ctx:
-        for bad in (dict(fill_threads=300), dict(fill_rows=12), dict(scan_kind=9), dict(fill_vote_agg=2)):
+        for bad in (dict(fill_threads=300), dict(fill_rows=12), dict(scan_kind=9), dict(fill_vote_agg=2),
+                    dict(bin_cluster=3)):
             with pytest.raises(ht.HTError):
                 ctx.set_tuning(**bad)
         ev = synth.tiny_event()
