@@ -172,9 +172,8 @@ ht_status ht_find_maxima(ht_ctx *ctx, ht_peak *out, uint32_t capacity, uint32_t 
  * its counters first; calls that overlap on the GPU (from several host
  * threads, or on several streams) race on it and must be serialised by the
  * caller.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  No cudaMalloc, cudaFree or other allocating
- * call is made.  Errors: HT_E_INVAL (NULL pointer, bad binning, n_events or
+ * (cudaGetSymbolAddress, with that device current).  No cudaMalloc, cudaFree
+ * or other allocating call is made.  Errors: HT_E_INVAL (NULL pointer, bad binning, n_events or
  * capacity), HT_E_NOMEM (scratch limit), HT_E_CUDA. */
 ht_status ht_find_maxima_noalloc(const ht_binning *binning, const ht_ranges *ranges, uint32_t threshold,
                                  const uint32_t *M, uint32_t n_events, ht_peak *out, uint32_t capacity,
