@@ -134,6 +134,29 @@ def test_fill_and_maxima_match_oracle(ht, case, naive):
     assert np.all(pk["event"] == 0)
 
 
+@pytest.mark.parametrize("bin_cluster", [1, 2], ids=["cluster", "two_launches"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_binning_launches_match_oracle(ht, case, bin_cluster):
+    """Both binnings -- one thread-block-cluster launch (k_bin_cluster, which
+    also splits the bulk-copy-tile fill's work) or k_bin + k_scatter -- on
+    every geometry: windows, partial ranges, ragged shapes, dense slices and
+    degenerate coordinates, each with the default fill of its shape, twice
+    in a row on one context."""
+    name, bins, rng, T, (x, y, z) = case
+    b, r = ht.Binning(*bins), ht.Ranges(**rng)
+    M_ref, _ = oracle.fill(_ob(b), _orr(r), x, y, z)
+    pk_ref, n_ref = oracle.find_maxima(_ob(b), _orr(r), M_ref, T)
+    with ht.Context(b, r, threshold=T, max_hits=max(len(x), 1)) as ctx:
+        ctx.set_tuning(bin_cluster=bin_cluster)
+        assert ctx.get_tuning()["bin_cluster"] == bin_cluster
+        for _ in range(2):
+            ctx.fill(x, y, z)
+            pk, n = ctx.find_maxima(capacity=1 << 20)
+            assert n == n_ref
+            assert_peaks_equal(pk, pk_ref)
+        assert np.array_equal(ctx.matrix(), M_ref)
+
+
 @pytest.mark.parametrize("mode", [4, 5], ids=["staging", "tiles"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_bulk_store_fill_matches_oracle(ht, case, mode):
