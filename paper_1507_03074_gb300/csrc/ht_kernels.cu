@@ -5,6 +5,15 @@
 //                 pseudo-angles and the edge tables (Sec. 2: the angles
 //                 select the slice a hit votes in), and the per-hit terms
 //                 x, x^2 + y^2, 2y of the vote.
+//   k_scatter     the admitted hits into per-(event, slice) unit lists.
+//   k_bin_cluster k_bin + k_scatter in one thread-block cluster for launches
+//                 of few hits (distributed shared memory for the counts),
+//                 which also writes the work split of the fill after it.
+//   k_fill_tma    Step 1 fused with the candidates of step 2 (default): the
+//                 votes of a pass of W A-rows go into a u32 shared-memory
+//                 tile laid out as M_H's rows, the tile leaves as one bulk
+//                 copy, and a vote taking a cell to T lists it.  k_peaks then
+//                 tests the listed cells against their neighbours.
 //   k_fill_priv   Step 1 (Sec. 2), privatised.  Work item = (event, slice,
 //                 strip of W A-rows); each CTA takes a contiguous range of
 //                 items.  It selects the event's hits admitted to the slice
