@@ -37,6 +37,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -205,11 +206,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def strip_comments(src):
+    """C/CUDA source without its comments, trailing blanks and empty lines
+    (the kernel sources hold no comment marker inside a string literal)."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.split("\n") if line.strip())
+
+
 def kernel_source_hash():
+    """Hash of the kernel sources' code (comments excluded), which keys the
+    committed DRAM traffic figure to the kernels it was measured on."""
     h = hashlib.sha256()
     for f in ("ht_kernels.cu", "ht_device.cuh", "ht_internal.h"):
-        with open(os.path.join(ROOT, "paper_1507_03074_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1507_03074_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -68,3 +68,22 @@ def test_pick_in_flight_keeps_the_faster_shape(monkeypatch):
         assert all(c.t["bin_cluster"] == 0 for c in ctxs)   # binning left to the library per shape
         assert best["bin_cluster"] == (2 if one_cta_faster else 1)
         assert best["fill_rows"] == 32
+
+
+def test_kernel_source_hash_ignores_comments_only():
+    """The hash that keys the committed DRAM traffic figure follows the
+    kernels' code: comment and blank-line edits keep it, a code edit changes
+    it, and the committed figure is found for the sources as they are."""
+    import bench
+
+    code = "__global__ void k(int *p)\n{\n    p[0] = 1;   // one\n}\n"
+    same = "// header\n/* block\n   comment */\n__global__ void k(int *p)\n{\n\n    p[0] = 1;\n}\n"
+    other = "__global__ void k(int *p)\n{\n    p[0] = 2;\n}\n"
+    assert bench.strip_comments(code) == bench.strip_comments(same)
+    assert bench.strip_comments(code) != bench.strip_comments(other)
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")) as f:
+        d = json.load(f)
+    assert d["kernel_source_hash"] == bench.kernel_source_hash()
+    assert bench.profiled_traffic("k_fill_tma") == d["kernels"]["k_fill_tma"]["dram_bytes_per_launch"]
