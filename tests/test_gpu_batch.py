@@ -311,3 +311,34 @@ def test_batch_rejects_bad_arguments(ht):
             B.run(x, y, z, bad)
         pk, counts = B.run(x, y, z, off)           # still usable
         assert counts[0] == counts[1]
+
+
+def test_batch_cluster_binning_at_its_unit_limit(ht):
+    """53 events of 64 (theta, phi) slices fill the one-launch binning's 40 KB
+    of counts exactly (3 words per (event, slice) unit and 1 per event, with
+    every CTA finding its hits' events by the offsets); 54 events exceed it
+    and take the two-launch binning.  Both give the oracle's matrices and
+    peaks, event by event."""
+    bins = (4, 16, 64, 64)
+    b, r = ht.Binning(*bins), ht.Ranges()
+    ob, orr = oracle.Binning(*bins), oracle.Ranges()
+    evs = [(e.x, e.y, e.z) for e in (synth.make_event(20, 20, seed=3000 + k) for k in range(54))]
+    assert sum(len(e[0]) for e in evs) <= 16384
+    refs = []
+    for ev in evs:
+        M, _ = oracle.fill(ob, orr, *ev)
+        pk, n = oracle.find_maxima(ob, orr, M, 4)
+        refs.append((M, pk, n))
+    with ht.Batch(b, r, threshold=4, max_events=54, max_hits=16384, capacity=1 << 16) as B:
+        B.set_tuning(bin_cluster=1)
+        for n_ev, cluster in ((53, True), (54, False), (53, True)):
+            B.profile(True)                        # direct launches, counted per kernel
+            pk, counts = B.run(*ht.Batch.concat(evs[:n_ev]))
+            prof = B.profile_read()
+            B.profile(False)
+            assert (prof["k_bin_cluster"][0] > 0) == cluster and (prof["k_bin"][0] > 0) != cluster, prof
+            _check_events(evs[:n_ev], pk, counts, refs[:n_ev])
+            for e in (0, n_ev // 2, n_ev - 1):
+                assert np.array_equal(B.matrix(e), refs[e][0])
+        pk, counts = B.run(*ht.Batch.concat(evs[:53]))   # captured graph of the cluster binning
+        _check_events(evs[:53], pk, counts, refs[:53])
