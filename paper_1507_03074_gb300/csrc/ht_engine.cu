@@ -690,68 +690,58 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
                         const uint32_t *d_hit_off, uint32_t n_hits0, uint32_t n_events,
                         uint32_t n_total, uint32_t flags, cudaStream_t st)
 {
-    htk::Work w = make_work(E, x, y, z, d_hit_off, n_hits0, n_events);
-    cudaError_t e;
     E.fused_valid = false;
-    const size_t cl_smem = htk::bin_cluster_smem_bytes(E.geom, n_events);
     htk::FillCfg ff{};
     uint32_t grid = 0;
     const bool tma_next = tma_fill_next(E, n_events, flags, ff, grid);
     const bool want_cluster = E.tune.bin_cluster == 1 || (E.tune.bin_cluster == 0 && tma_next && !E.tma_capped);
-    if (want_cluster && n_total <= htk::kBinClusterMax * htk::kBinClusterThreads * htk::kBinClusterHPT &&
-        cl_smem <= htk::kBinClusterSmem) {
-        if (E.bin_cluster > 0) {
-            // few hits: binning and lists in one cluster launch
-            const uint32_t per = htk::kBinClusterThreads * htk::kBinClusterHPT;
-            const uint32_t cs = std::min<uint32_t>(
-                htk::kBinClusterMax,
-                std::max<uint32_t>((n_total + htk::kBinClusterThreads - 1) / htk::kBinClusterThreads,
-                                   (n_total + per - 1) / per));
-            if (tma_next) {
-                const uint64_t items = (uint64_t)n_events * E.geom.n_slices * ff.strips;
-                E.split_mode = htk::kSplitGiven;
-                E.split_grid = grid;
-                E.split_strips = ff.strips;
-                E.split_vw = ff.vote_weight;
-                E.split_n_static = items - (ff.dyn ? htk::dyn_items(items, grid) : 0);
-            } else {
-                E.split_mode = htk::kSplitAfterWait;   // the offsets come from the launch right before the fill
-            }
-            w = make_work(E, x, y, z, d_hit_off, n_hits0, n_events);
-            {
-                ProfScope ps(E, K_BIN_CLUSTER, st);
-                e = htk::launch_bin_cluster(E.geom, w, std::max<uint32_t>(cs, 1u), st);
-            }
-            if (e != cudaSuccess)
-                return e;
-            ++E.launches;
-            E.ctr_dirty = false;
-            E.last_hit_off = d_hit_off;
-            E.last_n_hits0 = n_hits0;
-            E.last_n_events = n_events;
-            E.last_accumulate = (flags & HT_ACCUMULATE) != 0;
-            return engine_vote(E, d_hit_off, n_hits0, n_events, flags, st);
+    const bool cluster = want_cluster && E.bin_cluster > 0 &&
+                         n_total <= htk::kBinClusterMax * htk::kBinClusterThreads * htk::kBinClusterHPT &&
+                         htk::bin_cluster_smem_bytes(E.geom, n_events) <= htk::kBinClusterSmem;
+    cudaError_t e;
+    if (cluster) {
+        // few hits: binning and unit lists in one cluster launch, one CTA per
+        // kBinClusterThreads hits (two hits a thread past kBinClusterMax CTAs)
+        if (tma_next) {
+            const uint64_t items = (uint64_t)n_events * E.geom.n_slices * ff.strips;
+            E.split_mode = htk::kSplitGiven;
+            E.split_grid = grid;
+            E.split_strips = ff.strips;
+            E.split_vw = ff.vote_weight;
+            E.split_n_static = items - (ff.dyn ? htk::dyn_items(items, grid) : 0);
+        } else {
+            E.split_mode = htk::kSplitAfterWait;   // the offsets come from the launch right before the fill
         }
+        const htk::Work w = make_work(E, x, y, z, d_hit_off, n_hits0, n_events);
+        const uint32_t cs = std::min<uint32_t>(
+            htk::kBinClusterMax, std::max<uint32_t>(1u, (n_total + htk::kBinClusterThreads - 1) / htk::kBinClusterThreads));
+        {
+            ProfScope ps(E, K_BIN_CLUSTER, st);
+            e = htk::launch_bin_cluster(E.geom, w, cs, st);
+        }
+        if (e != cudaSuccess)
+            return e;
+        ++E.launches;
+    } else {
+        E.split_mode = htk::kSplitEarly;
+        const htk::Work w = make_work(E, x, y, z, d_hit_off, n_hits0, n_events);
+        const uint32_t bgrid = std::max<uint32_t>(1, std::min<uint32_t>((n_total + 255) / 256, E.num_sms * 8));
+        {
+            ProfScope ps(E, K_BIN, st);
+            e = htk::launch_bin(E.geom, w, bgrid, st);
+        }
+        if (e != cudaSuccess)
+            return e;
+        ++E.launches;
+        {
+            ProfScope ps(E, K_SCATTER, st);
+            e = htk::launch_scatter(E.geom, w, bgrid, st);
+        }
+        if (e != cudaSuccess)
+            return e;
+        ++E.launches;
     }
-    E.split_mode = htk::kSplitEarly;
-    w.split_mode = htk::kSplitEarly;
-    {
-        ProfScope ps(E, K_BIN, st);
-        const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((n_total + 255) / 256, E.num_sms * 8));
-        e = htk::launch_bin(E.geom, w, grid, st);
-    }
-    if (e != cudaSuccess)
-        return e;
-    ++E.launches;
-    {
-        ProfScope ps(E, K_SCATTER, st);
-        const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((n_total + 255) / 256, E.num_sms * 8));
-        e = htk::launch_scatter(E.geom, w, grid, st);
-    }
-    if (e != cudaSuccess)
-        return e;
-    ++E.launches;
-    E.ctr_dirty = false;   // k_bin zeroed the counters
+    E.ctr_dirty = false;   // the binning zeroed the counters
     E.last_hit_off = d_hit_off;
     E.last_n_hits0 = n_hits0;
     E.last_n_events = n_events;
