@@ -96,12 +96,18 @@ def test_batch_binning_launches(ht, uneven, bin_cluster):
     evs, refs = uneven
     keep, n = [], 0
     for i, ev in enumerate(evs):
-        if n + len(ev[0]) <= 16384:
+        if n + len(ev[0]) <= 16383:                # room for the one-hit event below
             keep.append(i)
             n += len(ev[0])
-    assert len(keep) >= 3
+    assert len(keep) >= 3 and len(keep) + 2 <= 8
     sub, subr = [evs[i] for i in keep], [refs[i] for i in keep]
+    # an empty first event and a one-hit last one: the edges of the search
+    # that finds each hit's event by the offsets
+    empty = tuple(np.zeros(0, np.float32) for _ in range(3))
+    one = tuple(a[:1].copy() for a in sub[0])
     b, r = ht.Binning(*synth.PAPER_BINNING), ht.Ranges()
+    sub = [empty] + sub + [one]
+    subr = [_oracle_event(b, r, 10, empty)] + subr + [_oracle_event(b, r, 10, one)]
     with ht.Batch(b, r, threshold=10, max_events=8, max_hits=16384, capacity=1 << 16) as B:
         B.set_tuning(bin_cluster=bin_cluster)
         assert B.get_tuning()["bin_cluster"] == bin_cluster
