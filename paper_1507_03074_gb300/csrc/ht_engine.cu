@@ -195,6 +195,7 @@ ht_status engine_configure(Engine &E, std::string *why)
     // A smaller peak buffer than the scan's (the tile needs the room); k_seam
     // keeps kPeakBuf in its own launch.
     E.fused_ok = false;
+    E.fused_capped = false;
     E.fused_K = std::max<uint32_t>(kFusedPeakBuf, f.threads);
     if (E.fill_priv_ok && t.fused != 2 && W <= 64 && b.n_b <= 4096) {
         htk::ScanArgs tmp{};
@@ -238,6 +239,7 @@ ht_status engine_configure(Engine &E, std::string *why)
             occ = 0;   // rows must start on 16 bytes; the block must cover whole rows
         E.fused_fill = ff;
         if (occ >= 1) {
+            E.fused_capped = t.fill_blocks_per_sm && (int)t.fill_blocks_per_sm < occ;
             if (t.fill_blocks_per_sm)
                 occ = std::min<int>(occ, (int)t.fill_blocks_per_sm);
             E.fused_ok = true;
@@ -667,22 +669,35 @@ static htk::Work make_work(Engine &E, const float *x, const float *y, const floa
     return w;
 }
 
-// When engine_vote's next fill for these flags is k_fill_tma: its
-// configuration and grid, so that k_bin_cluster can split its work ahead of
-// it (the fill checks the shape and splits by itself on a mismatch).
-static bool tma_fill_next(const Engine &E, uint32_t n_events, uint32_t flags, htk::FillCfg &ff, uint32_t &grid)
+// When engine_vote's next fill for these flags is one whose work split
+// k_bin_cluster can hand over -- the bulk-copy-tile fill (k_fill_tma) or the
+// peaks-only fill (k_fill_peaks) -- its configuration and grid, and whether
+// fill_blocks_per_sm holds it below its occupancy (the fill checks the shape
+// and splits by itself on a mismatch).
+static bool split_fill_next(const Engine &E, uint32_t n_events, uint32_t flags, htk::FillCfg &ff, uint32_t &grid,
+                            bool &capped)
 {
-    if ((flags & (HT_FILL_NAIVE | HT_ACCUMULATE)) || !E.fill_priv_ok || !E.use_tma || E.use_ws)
+    if ((flags & (HT_FILL_NAIVE | HT_ACCUMULATE)) || !E.fill_priv_ok)
         return false;
     const bool peaks_only = (flags & HT_PEAKS_ONLY) && E.fused_ok && E.d_edge &&
                             E.edge_pass * std::max<uint32_t>(1, E.fused_fill.W / 2) >= E.geom.na;
-    if (peaks_only)
-        return false;
-    ff = E.tma_fill;
+    uint32_t g0;
+    if (peaks_only) {
+        ff = E.fused_fill;
+        ff.vote_weight = htk::kPeaksVoteWeight;
+        g0 = E.fused_grid;
+        capped = E.fused_capped;
+    } else {
+        if (!E.use_tma || E.use_ws)
+            return false;
+        ff = E.tma_fill;
+        ff.vote_weight = htk::kVoteWeight;
+        g0 = E.tma_grid;
+        capped = E.tma_capped;
+    }
     ff.accumulate = 0u;
-    ff.vote_weight = htk::kVoteWeight;
     const uint64_t items = (uint64_t)n_events * E.geom.n_slices * ff.strips;
-    grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(E.tma_grid, items));
+    grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(g0, items));
     return grid + 1 <= E.split_cap;
 }
 
@@ -693,8 +708,9 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
     E.fused_valid = false;
     htk::FillCfg ff{};
     uint32_t grid = 0;
-    const bool tma_next = tma_fill_next(E, n_events, flags, ff, grid);
-    const bool want_cluster = E.tune.bin_cluster == 1 || (E.tune.bin_cluster == 0 && tma_next && !E.tma_capped);
+    bool capped = false;
+    const bool split_next = split_fill_next(E, n_events, flags, ff, grid, capped);
+    const bool want_cluster = E.tune.bin_cluster == 1 || (E.tune.bin_cluster == 0 && split_next && !capped);
     const bool cluster = want_cluster && E.bin_cluster > 0 &&
                          n_total <= htk::kBinClusterMax * htk::kBinClusterThreads * htk::kBinClusterHPT &&
                          htk::bin_cluster_smem_bytes(E.geom, n_events) <= htk::kBinClusterSmem;
@@ -702,7 +718,7 @@ cudaError_t engine_fill(Engine &E, const float *x, const float *y, const float *
     if (cluster) {
         // few hits: binning and unit lists in one cluster launch, one CTA per
         // kBinClusterThreads hits (two hits a thread past kBinClusterMax CTAs)
-        if (tma_next) {
+        if (split_next) {
             const uint64_t items = (uint64_t)n_events * E.geom.n_slices * ff.strips;
             E.split_mode = htk::kSplitGiven;
             E.split_grid = grid;

@@ -90,6 +90,7 @@ struct Engine {
     bool ctr_dirty = false;      // counters hold an unconsumed fused fill's peaks
     int bin_cluster = -1;        // k_bin_cluster usable here (-1: not checked yet)
     bool tma_capped = false;     // fill_blocks_per_sm holds the bulk-copy-tile fill below its occupancy
+    bool fused_capped = false;   // ... and the fused fills (the peaks-only fill among them)
     uint32_t split_mode = htk::kSplitEarly;   // Work::split_mode of the fill after the last binning
     uint32_t split_grid = 0, split_strips = 0, split_vw = 0;
     uint64_t split_n_static = 0;

@@ -1919,16 +1919,25 @@ __global__ void __launch_bounds__(1024) k_fill_peaks(Geom g, Work w, FillCfg c, 
         sm4[16 + a.K + k] = make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t k = tid; k <= nb; k += bd)
         beta[k] = g.bth[k];
-    grid_dep_wait();   // the unit lists of k_scatter
     const uint32_t cta = blockIdx.x;
     ChunkList inner = interior_list(a, cta);
 
+    // the static split as in k_fill_tma (Work::split_mode)
     __shared__ unsigned long long s_rng[2];
     __shared__ uint32_t s_dyn;
     const uint64_t items = (uint64_t)w.n_events * g.n_slices * c.strips;
     const uint64_t n_dyn = c.dyn ? dyn_items(items, gridDim.x) : 0, n_static = items - n_dyn;
     uint64_t it0, it1;
-    cta_items(g, w, c, cta, gridDim.x, n_static, it0, it1, s_rng);
+    if (w.split_mode == kSplitEarly)
+        cta_items(g, w, c, cta, gridDim.x, n_static, it0, it1, s_rng);
+    grid_dep_wait();   // the unit lists (and, after k_bin_cluster, the offsets and split)
+    if (w.split_mode == kSplitGiven && w.split_grid == gridDim.x && w.split_strips == c.strips &&
+        w.split_vw == c.vote_weight && w.split_n_static == n_static) {
+        it0 = __ldcg(&w.split[cta]);
+        it1 = __ldcg(&w.split[cta + 1]);
+    } else if (w.split_mode != kSplitEarly) {
+        cta_items(g, w, c, cta, gridDim.x, n_static, it0, it1, s_rng);
+    }
     uint64_t cached_es = ~0ull;
     uint32_t cached_n = 0;
     uint32_t buf_n = 0, nseq = 0, total = 0;
