@@ -279,15 +279,16 @@ ht_status ht_profile_read(ht_ctx *ctx, ht_kernel_time *out, uint32_t cap, uint32
  *                      bins them and builds the unit lists in one launch of
  *                      a thread-block cluster (up to 8 CTAs of 1024 threads
  *                      reading each other's counts), which also splits the
- *                      bulk-copy-tile fill's work ahead of it -- shorter
- *                      latency of one event; larger fills take two launches
- *                      anyway; 2: two launches (binning, lists) of small
- *                      CTAs that fit beside other events' kernels -- more
- *                      events per second when several contexts' events
- *                      overlap; 0: 1 for the bulk-copy-tile fill unless
- *                      fill_blocks_per_sm holds it below the CTAs per SM
- *                      that fit (the SMs are then shared with other
- *                      events), else 2
+ *                      work of the fill after it (bulk-copy-tile or
+ *                      peaks-only) ahead of it -- shorter latency of one
+ *                      event; larger fills take two launches anyway; 2: two
+ *                      launches (binning, lists) of small CTAs that fit
+ *                      beside other events' kernels -- more events per
+ *                      second when several contexts' events overlap; 0: 1
+ *                      for the bulk-copy-tile and the peaks-only fill
+ *                      unless fill_blocks_per_sm holds that fill below the
+ *                      CTAs per SM that fit (the SMs are then shared with
+ *                      other events), else 2
  * ht_set_tuning waits for the device, re-derives the shapes and returns
  * HT_E_INVAL for an impossible value; ht_get_tuning reports the shapes in
  * effect (0 fields filled in). */
